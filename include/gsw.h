@@ -1,0 +1,206 @@
+/*
+ * gsw.h -- C ABI of the GB300 implicit finite-element seismic-wave library.
+ *
+ * The library runs the per-candidate 3D wave-propagation analysis of
+ * Ichimura et al., "Development of an Estimation Method for the Seismic Motion
+ * Reproducibility of a Three-dimensional Ground Structure Model ..."
+ * (arXiv 2404.17754): Eq. (1) (linear elastodynamics) discretised with
+ * second-order tetrahedra, Newmark-beta implicit time integration solved by
+ * preconditioned conjugate gradients every step (Section 3, computational-cost
+ * paragraph), absorbing base and sides driven by the input velocity at the
+ * base (Section 2), surface receivers, and the input-wave estimate and misfit
+ * ERR of Section 2, Eq. (2).
+ *
+ * Conventions (all entry points):
+ *  - Every call returns a gsw_status.  No C++ exception crosses the ABI.
+ *    gsw_last_error() returns a message describing the last failing call on
+ *    that context.  A failed call leaves the context usable.
+ *  - Pointers are HOST pointers unless the argument name ends in "_dev"
+ *    (device memory on the context's GPU).  The library copies what it needs
+ *    from host arrays during the call; the caller keeps ownership.
+ *  - Arrays are C-contiguous.  Node-major vectors are [n_nodes][3] float64.
+ *  - Device memory is allocated through the allocator set by
+ *    gsw_set_allocator (default: cudaMallocAsync on the context's stream).
+ *  - All GPU work is issued on the stream given to gsw_create.  Calls that
+ *    return host data synchronise that stream.
+ *  - A context is not thread-safe; use one per host thread.
+ */
+#ifndef GSW_H
+#define GSW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gsw_ctx gsw_ctx;
+
+typedef enum {
+  GSW_OK = 0,
+  GSW_E_INVALID = -1,  /* bad argument or malformed mesh (message says which) */
+  GSW_E_CUDA = -2,     /* CUDA runtime error */
+  GSW_E_NOMEM = -3,    /* device allocation failed */
+  GSW_E_NOCONV = -4,   /* CG did not reach the tolerance within max_iter */
+  GSW_E_NAN = -5,      /* non-finite residual or state */
+  GSW_E_TIMEOUT = -6,  /* a bounded device-side wait gave up */
+  GSW_E_STATE = -7     /* call not valid in the model's current state */
+} gsw_status;
+
+/* Solver precision of the preconditioner's inner products (the outer CG
+ * residual, its dot products and the Newmark update are FP64 in every mode). */
+typedef enum {
+  GSW_PREC_FP64 = 0,   /* plain block-Jacobi PCG, everything FP64 */
+  GSW_PREC_FP32 = 1,   /* flexible CG; inner preconditioner EBE in FP32 */
+  GSW_PREC_FP16 = 2    /* flexible CG; inner vectors FP16, FP32 EBE arithmetic */
+} gsw_precision;
+
+typedef struct {
+  double tol;           /* relative residual ||b - A x|| / ||b|| target (1e-8) */
+  int32_t max_iter;     /* outer CG iteration cap per step -> GSW_E_NOCONV */
+  int32_t precision;    /* gsw_precision */
+  int32_t inner_iters;  /* inner preconditioner iterations (mixed modes) */
+  int32_t check_every;  /* CG iterations issued between host convergence checks */
+} gsw_solver_opts;
+
+typedef struct {
+  int64_t steps_done;     /* time steps completed since the last reset */
+  int64_t cg_iters_total; /* outer CG iterations summed over those steps */
+  int32_t cg_iters_last;  /* outer CG iterations of the last step */
+  int32_t cg_iters_max;   /* largest per-step count so far */
+  double relres_last;     /* final recursive relative residual of the last step */
+  int64_t inner_iters_total; /* inner preconditioner iterations (mixed modes) */
+  int64_t kernel_launches;   /* library kernels launched by gsw_step since the last reset */
+} gsw_stats;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the context creates its own non-blocking stream). */
+gsw_status gsw_create(gsw_ctx **out, int device, void *cuda_stream);
+void gsw_destroy(gsw_ctx *ctx);
+const char *gsw_last_error(const gsw_ctx *ctx);
+
+/* Route device allocations through caller callbacks (for example a framework's
+ * caching allocator).  alloc(bytes, stream, user) returns device memory or
+ * NULL; free_(ptr, stream, user) releases it.  Pass NULLs to restore the
+ * default.  Must be called before any model is uploaded. */
+gsw_status gsw_set_allocator(gsw_ctx *ctx, void *(*alloc)(size_t, void *, void *),
+                             void (*free_)(void *, void *, void *), void *user);
+
+/* ---- model -------------------------------------------------------------- */
+
+/* Upload one candidate ground model (Section 3: second-order tetrahedra).
+ *  xyz       [n_nodes][3] node coordinates (m); x3 is elevation, surface z = 0.
+ *  conn      [n_elem][10] node indices, VTK quadratic-tetrahedron order
+ *            (vertices 0..3, then mid-edge nodes of edges 01,12,02,03,13,23);
+ *            det[x1-x0, x2-x0, x3-x0] > 0; straight-sided (mid-edge nodes at
+ *            edge midpoints).
+ *  elem_mat  [n_elem] layer index into mat.
+ *  mat       [n_mat][4] rows (Vp, Vs, rho, h): P/S velocity, density, damping
+ *            ratio; requires Vp > Vs > 0, rho > 0, h >= 0.
+ *  faces     [n_faces][6] 6-node boundary triangles (3 vertices, then the
+ *            mid-edge nodes of edges 01, 12, 20), face_elem [n_faces] owning
+ *            element, face_tag [n_faces]: 0 free surface, 1 absorbing base
+ *            (carries the input), 2 absorbing side.
+ *  period    [2] lateral periods for laterally periodic meshes, 0 = none.
+ *  rec_xy    [n_rec][2] receiver positions on the free surface.
+ * Validation (index ranges, finiteness, material order, positive volumes,
+ * straight sides, receivers on the surface) rejects the model with
+ * GSW_E_INVALID.  On success *model_id receives a handle. */
+gsw_status gsw_model_upload(gsw_ctx *ctx, int64_t n_nodes, const double *xyz, int64_t n_elem,
+                            const int32_t *conn, const int32_t *elem_mat, int32_t n_mat,
+                            const double *mat, int64_t n_faces, const int32_t *faces,
+                            const int32_t *face_elem, const int32_t *face_tag,
+                            const double *period, int32_t n_rec, const double *rec_xy,
+                            int32_t *model_id);
+gsw_status gsw_model_free(gsw_ctx *ctx, int32_t model_id);
+/* Sizes of an uploaded model: out[0]=n_nodes, out[1]=n_elem, out[2]=n_faces,
+ * out[3]=n_rec, out[4]=device bytes held. */
+gsw_status gsw_model_info(gsw_ctx *ctx, int32_t model_id, int64_t *out);
+
+/* Time integration (Section 3: Newmark-beta, average acceleration
+ * beta = 1/4, gamma = 1/2) with increment dt and Rayleigh damping fitted to
+ * each layer's h over [f1, f2] Hz.  Allocates the step-dependent state,
+ * builds the block-Jacobi preconditioner and resets the model to rest. */
+gsw_status gsw_set_time(gsw_ctx *ctx, int32_t model_id, double dt, int32_t n_steps, double f1,
+                        double f2);
+
+/* Input velocity (Section 2: force at the base): p[n] is the incident
+ * velocity at t_{n+1} = (n+1) dt in direction dir (0 = x1, 1 = x2, 2 = x3);
+ * the base load is 2 C_base (p e_dir).  n must equal the model's n_steps. */
+gsw_status gsw_set_input(gsw_ctx *ctx, int32_t model_id, int32_t dir, const double *p, int32_t n);
+
+gsw_status gsw_set_solver(gsw_ctx *ctx, int32_t model_id, const gsw_solver_opts *opts);
+
+/* Reset the model to rest (u = v = a = 0, step 0, receivers cleared). */
+gsw_status gsw_reset(gsw_ctx *ctx, int32_t model_id);
+
+/* Advance n time steps.  On GSW_E_NOCONV / GSW_E_NAN the model stays at the
+ * last completed step and further steps return GSW_E_STATE until reset. */
+gsw_status gsw_step(gsw_ctx *ctx, int32_t model_id, int32_t n);
+
+/* Run every listed model from rest through all its steps (one directional
+ * analysis each). */
+gsw_status gsw_run(gsw_ctx *ctx, const int32_t *model_ids, int32_t n_models);
+
+/* Receiver velocity history: out [n_rec][3][n_steps] (entries of steps not
+ * yet run are zero). */
+gsw_status gsw_read_waveforms(gsw_ctx *ctx, int32_t model_id, double *out);
+/* Receiver velocities of steps step0 .. step0+count-1 only:
+ * out [n_rec][3][count] (host; pinned memory gives an asynchronous copy). */
+gsw_status gsw_read_waveform_steps(gsw_ctx *ctx, int32_t model_id, int32_t step0, int32_t count,
+                                   double *out);
+gsw_status gsw_stats_get(gsw_ctx *ctx, int32_t model_id, gsw_stats *out);
+
+/* Checkpoint / restore of the time-stepping state: u, v, a [n_nodes][3] and
+ * the step counter (receiver history up to that step is kept by the caller
+ * via gsw_read_waveforms).  Host arrays. */
+gsw_status gsw_get_state(gsw_ctx *ctx, int32_t model_id, double *u, double *v, double *a,
+                         int64_t *step);
+gsw_status gsw_set_state(gsw_ctx *ctx, int32_t model_id, const double *u, const double *v,
+                         const double *a, int64_t step);
+
+/* Kernel timing: enable = 1 clears the counters and brackets every CG
+ * operator launch (the element-by-element A p product) of subsequent steps
+ * with CUDA events on the context's stream; enable = 0 stops.  *ebe_ms and
+ * *ebe_launches (either may be NULL) receive the summed device time and the
+ * number of timed launches so far. */
+gsw_status gsw_timing(gsw_ctx *ctx, int32_t model_id, int32_t enable, double *ebe_ms,
+                      int64_t *ebe_launches);
+
+/* Operator application on device vectors [n_nodes][3] (diagnostics, tests):
+ *  which = 0: y = A x, A = K + (2/dt) C + (4/dt^2) M (the CG operator);
+ *  which = 1: y = K x;  which = 2: y = M x;  which = 3: y = C x.
+ * x_dev, y_dev device pointers; y is overwritten. */
+gsw_status gsw_apply(gsw_ctx *ctx, int32_t model_id, int32_t which, const double *x_dev,
+                     double *y_dev);
+
+/* Inverted 3x3 nodal diagonal blocks of A (the block-Jacobi preconditioner),
+ * host out [n_nodes][6] symmetric entries (xx, yy, zz, xy, xz, yz). */
+gsw_status gsw_read_preconditioner(gsw_ctx *ctx, int32_t model_id, double *out);
+
+/* Receiver interpolation: nodes [n_rec][6] and weights [n_rec][6] of the
+ * 6-node surface triangle containing each receiver. */
+gsw_status gsw_read_receivers(gsw_ctx *ctx, int32_t model_id, int32_t *nodes, double *weights);
+
+/* ---- misfit (Section 2, Eq. (2)) ----------------------------------------- */
+
+/* Input-wave estimate and ERR for one candidate and one event.
+ *  G    [n_rec][3 (i)][3 (j)][n_t] Green's functions: velocity in direction i
+ *       at receiver k for the unit pulse input in direction j.
+ *  obs  [n_rec][3][n_t] observed surface velocity.
+ *  stride, n_shifts: pulse shifts l * stride samples, l = 0..n_shifts-1.
+ *  tau  relative eigenvalue cut of the truncated pseudo-inverse.
+ * Outputs: *err (Eq. (2)) and c_out [3][n_shifts] (may be NULL).
+ * Pairs (k, i) whose observed energy is below 1e-12 of the largest are
+ * dropped from the weights and from n_obs. Host arrays; computed on the GPU. */
+gsw_status gsw_misfit(gsw_ctx *ctx, int32_t n_rec, int32_t n_t, const double *G,
+                      const double *obs, int32_t stride, int32_t n_shifts, double tau,
+                      double *err, double *c_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSW_H */

@@ -1,0 +1,756 @@
+// C ABI of the library (declared in include/gsw.h): context, model upload
+// and validation, time stepping driver, state access, misfit.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "gsw.h"
+#include "gsw_internal.cuh"
+#include "gsw_misfit.cuh"
+
+using namespace gsw;
+
+namespace {
+
+struct Model {
+  int64_t N = 0, E = 0, F = 0;
+  int n_mat = 0, n_rec = 0;
+  double period[2] = {0.0, 0.0};
+  std::vector<double> raw_mat;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  // device: mesh
+  double* xyz = nullptr;
+  int32_t* conn = nullptr;
+  double* geo = nullptr;
+  int32_t* emat = nullptr;
+  double* raw_mat_dev = nullptr;
+  MatCoef* mat = nullptr;
+  int32_t* fnode = nullptr;
+  int32_t* face_elem = nullptr;
+  int32_t* face_tag = nullptr;
+  double* fgeo = nullptr;
+  double* rec_xy = nullptr;
+  int32_t* rec_face = nullptr;
+  int32_t* rec_node = nullptr;
+  double* rec_w = nullptr;
+  int* err = nullptr;
+  // time stepping
+  bool time_set = false;
+  double dt = 0.0, f1 = 0.0, f2 = 0.0;
+  int n_steps = 0;
+  double *u = nullptr, *v = nullptr, *a = nullptr, *b = nullptr, *x = nullptr, *r = nullptr,
+         *z = nullptr, *p = nullptr, *q = nullptr, *dblk = nullptr, *dinv = nullptr,
+         *partials = nullptr, *wave = nullptr;
+  CgScalars* cg = nullptr;
+  CgScalars* cg_host = nullptr;  // pinned
+  std::vector<double> input;
+  int dir = 0;
+  bool input_set = false;
+  gsw_solver_opts opts = {1e-8, 10000, GSW_PREC_FP64, 20, 8};
+  int64_t step = 0;
+  bool failed = false;
+  gsw_stats stats = {};
+  // kernel timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;
+  int ev_used = 0;
+  double ebe_ms = 0.0;
+  int64_t ebe_count = 0;
+
+  ModelView view() const {
+    ModelView m;
+    m.N = N;
+    m.E = E;
+    m.F = F;
+    m.conn = conn;
+    m.geo = geo;
+    m.emat = emat;
+    m.mat = mat;
+    m.fnode = fnode;
+    m.fgeo = fgeo;
+    m.dt = dt;
+    return m;
+  }
+};
+
+}  // namespace
+
+struct gsw_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  void* (*alloc)(size_t, void*, void*) = nullptr;
+  void (*free_)(void*, void*, void*) = nullptr;
+  void* user = nullptr;
+  std::map<int, Model*> models;
+  int next_id = 1;
+  MisfitWork misfit;
+};
+
+namespace {
+
+gsw_status fail(gsw_ctx* c, gsw_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(ctx, GSW_E_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                                    \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+void* dev_alloc(gsw_ctx* ctx, Model* m, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (ctx->alloc) {
+    p = ctx->alloc(bytes, (void*)ctx->stream, ctx->user);
+  } else if (cudaMallocAsync(&p, bytes, ctx->stream) != cudaSuccess) {
+    p = nullptr;
+  }
+  if (p && m) {
+    m->allocs.push_back(p);
+    m->bytes += bytes;
+  }
+  return p;
+}
+
+void dev_free(gsw_ctx* ctx, void* p) {
+  if (!p) return;
+  if (ctx->free_)
+    ctx->free_(p, (void*)ctx->stream, ctx->user);
+  else
+    cudaFreeAsync(p, ctx->stream);
+}
+
+template <class T>
+gsw_status alloc_into(gsw_ctx* ctx, Model* m, T** out, size_t count) {
+  *out = (T*)dev_alloc(ctx, m, sizeof(T) * count);
+  if (!*out) return fail(ctx, GSW_E_NOMEM, "device allocation of %zu bytes failed", sizeof(T) * count);
+  return GSW_OK;
+}
+
+#define TRY(expr)               \
+  do {                          \
+    gsw_status s_ = (expr);     \
+    if (s_ != GSW_OK) return s_; \
+  } while (0)
+
+void free_model(gsw_ctx* ctx, Model* m) {
+  for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
+  for (void* p : m->allocs) dev_free(ctx, p);
+  m->allocs.clear();
+  if (m->cg_host) cudaFreeHost(m->cg_host);
+  delete m;
+}
+
+Model* find(gsw_ctx* ctx, int id) {
+  auto it = ctx->models.find(id);
+  return it == ctx->models.end() ? nullptr : it->second;
+}
+
+gsw_status check_device_err(gsw_ctx* ctx, Model* m, const char* what) {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, m->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (h) {
+    std::string msg;
+    if (h & 1) msg += " non-positive or non-finite element volume;";
+    if (h & 2) msg += " curved element (mid-edge node off the edge midpoint);";
+    if (h & 4) msg += " degenerate boundary face;";
+    if (h & 8) msg += " singular nodal diagonal block;";
+    if (h & 16) msg += " receiver outside the free surface;";
+    return fail(ctx, GSW_E_INVALID, "%s:%s", what, msg.c_str());
+  }
+  return GSW_OK;
+}
+
+// Structure-of-arrays transpose of a row-major [n][k] int32 table.
+std::vector<int32_t> soa(const int32_t* src, int64_t n, int k) {
+  std::vector<int32_t> out((size_t)n * k);
+  for (int64_t i = 0; i < n; ++i)
+    for (int j = 0; j < k; ++j) out[(size_t)j * n + i] = src[(size_t)i * k + j];
+  return out;
+}
+
+gsw_status model_state_alloc(gsw_ctx* ctx, Model* m) {
+  const size_t n3 = 3 * (size_t)m->N;
+  TRY(alloc_into(ctx, m, &m->u, n3));
+  TRY(alloc_into(ctx, m, &m->v, n3));
+  TRY(alloc_into(ctx, m, &m->a, n3));
+  TRY(alloc_into(ctx, m, &m->b, n3));
+  TRY(alloc_into(ctx, m, &m->x, n3));
+  TRY(alloc_into(ctx, m, &m->r, n3));
+  TRY(alloc_into(ctx, m, &m->z, n3));
+  TRY(alloc_into(ctx, m, &m->p, n3));
+  TRY(alloc_into(ctx, m, &m->q, n3));
+  TRY(alloc_into(ctx, m, &m->dblk, 6 * (size_t)m->N));
+  TRY(alloc_into(ctx, m, &m->dinv, 6 * (size_t)m->N));
+  ModelView mv = m->view();
+  size_t np = (size_t)ebe_blocks(mv);
+  if (np < 2 * (size_t)kMaxNodeBlocks) np = 2 * (size_t)kMaxNodeBlocks;
+  TRY(alloc_into(ctx, m, &m->partials, np));
+  TRY(alloc_into(ctx, m, &m->cg, 1));
+  if (!m->cg_host) CK(cudaMallocHost(&m->cg_host, sizeof(CgScalars)));
+  TRY(alloc_into(ctx, m, &m->wave, (size_t)m->n_rec * 3 * (size_t)(m->n_steps > 0 ? m->n_steps : 1)));
+  return GSW_OK;
+}
+
+gsw_status model_reset(gsw_ctx* ctx, Model* m) {
+  const size_t n3 = 3 * (size_t)m->N;
+  CK(cudaMemsetAsync(m->u, 0, sizeof(double) * n3, ctx->stream));
+  CK(cudaMemsetAsync(m->v, 0, sizeof(double) * n3, ctx->stream));
+  CK(cudaMemsetAsync(m->a, 0, sizeof(double) * n3, ctx->stream));
+  CK(cudaMemsetAsync(m->wave, 0, sizeof(double) * (size_t)m->n_rec * 3 * (size_t)m->n_steps, ctx->stream));
+  CK(cudaMemsetAsync(m->cg, 0, sizeof(CgScalars), ctx->stream));
+  m->step = 0;
+  m->failed = false;
+  m->stats = gsw_stats{};
+  return GSW_OK;
+}
+
+// One Newmark step: RHS (one EBE pass), PCG from the predictor, update, record.
+gsw_status step_fp64(gsw_ctx* ctx, Model* m) {
+  cudaStream_t s = ctx->stream;
+  ModelView mv = m->view();
+  const double force = 2.0 * m->input[(size_t)m->step];
+  CK(cudaMemsetAsync(m->b, 0, sizeof(double) * 3 * (size_t)m->N, s));
+  launch_ebe(kModeRhs, mv, m->u, m->v, m->a, m->b, force, m->dir, nullptr, nullptr, s);
+  // scalars: tol / max_iter travel with the state
+  CgScalars init = {};
+  init.tol = m->opts.tol;
+  init.max_iter = m->opts.max_iter;
+  CK(cudaMemcpyAsync(m->cg, &init, sizeof(CgScalars), cudaMemcpyHostToDevice, s));
+  launch_cg_init(mv, m->b, m->v, m->a, m->x, m->q, m->partials, m->cg, s);
+  launch_ebe(kModeA, mv, m->x, nullptr, nullptr, m->q, 0.0, 0, nullptr, m->cg, s);
+  launch_cg_residual(mv, m->b, m->q, m->r, m->z, m->p, m->dinv, m->partials, m->cg, s);
+  const int chunk = m->opts.check_every > 0 ? m->opts.check_every : 8;
+  int64_t launches = 5;  // rhs, init, A x0, residual (+ newmark and record below)
+  if (m->timing && (int)m->ev.size() < 2 * chunk) {
+    for (int i = (int)m->ev.size(); i < 2 * chunk; ++i) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      m->ev.push_back(e);
+    }
+  }
+  int prev_iter = 0;
+  for (;;) {
+    m->ev_used = 0;
+    for (int k = 0; k < chunk; ++k) {
+      if (m->timing) CK(cudaEventRecord(m->ev[2 * k], s));
+      launch_ebe(kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, s);
+      if (m->timing) {
+        CK(cudaEventRecord(m->ev[2 * k + 1], s));
+        m->ev_used = k + 1;
+      }
+      launch_cg_update(mv, m->x, m->r, m->z, m->p, m->q, m->dinv, m->partials, m->cg, s);
+      launch_cg_pupdate(mv, m->z, m->p, m->cg, s);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(m->cg_host, m->cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    launches += 3 * chunk;
+    if (m->timing) {
+      // time only the launches that did work: one operator product per
+      // iteration counted since the previous check (later launches in the
+      // chunk returned at entry once the solve had converged)
+      const int worked = m->cg_host->iter - prev_iter;
+      for (int k = 0; k < worked && k < m->ev_used; ++k) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, m->ev[2 * k], m->ev[2 * k + 1]));
+        m->ebe_ms += ms;
+      }
+    }
+    prev_iter = m->cg_host->iter;
+    if (m->cg_host->done) break;
+  }
+  const CgScalars& h = *m->cg_host;
+  if (h.status != 0) {
+    m->failed = true;
+    if (h.status == GSW_E_NOCONV)
+      return fail(ctx, GSW_E_NOCONV, "step %lld: CG did not reach %g in %d iterations (at %g)",
+                  (long long)m->step, m->opts.tol, h.iter, h.relres);
+    return fail(ctx, GSW_E_NAN, "step %lld: non-finite CG residual", (long long)m->step);
+  }
+  launch_newmark(mv, m->x, m->u, m->v, m->a, m->cg, s);
+  launch_record(m->v, m->rec_node, m->rec_w, m->n_rec, m->wave, m->n_steps, (int)m->step, s);
+  CK(cudaGetLastError());
+  m->stats.steps_done += 1;
+  m->stats.cg_iters_total += h.iter;
+  m->stats.cg_iters_last = h.iter;
+  if (h.iter > m->stats.cg_iters_max) m->stats.cg_iters_max = h.iter;
+  m->stats.relres_last = h.relres;
+  m->stats.kernel_launches += launches + 2;
+  if (m->timing) m->ebe_count += h.iter;
+  m->step += 1;
+  return GSW_OK;
+}
+
+bool finite_all(const double* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!isfinite(p[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+// =============================================================================
+// C ABI
+// =============================================================================
+
+extern "C" {
+
+gsw_status gsw_create(gsw_ctx** out, int device, void* cuda_stream) {
+  if (!out) return GSW_E_INVALID;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return GSW_E_CUDA;
+  gsw_ctx* ctx = new gsw_ctx();
+  ctx->device = device;
+  DeviceGuard g(device);
+  if (cuda_stream) {
+    ctx->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return GSW_E_CUDA;
+    }
+    ctx->own_stream = true;
+  }
+  *out = ctx;
+  return GSW_OK;
+}
+
+void gsw_destroy(gsw_ctx* ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& kv : ctx->models) free_model(ctx, kv.second);
+  ctx->models.clear();
+  misfit_free(ctx->misfit, ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char* gsw_last_error(const gsw_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+gsw_status gsw_set_allocator(gsw_ctx* ctx, void* (*alloc)(size_t, void*, void*),
+                             void (*free_)(void*, void*, void*), void* user) {
+  if (!ctx) return GSW_E_INVALID;
+  if (!ctx->models.empty()) return fail(ctx, GSW_E_STATE, "set the allocator before uploading models");
+  if ((alloc == nullptr) != (free_ == nullptr))
+    return fail(ctx, GSW_E_INVALID, "alloc and free must both be set or both be NULL");
+  ctx->alloc = alloc;
+  ctx->free_ = free_;
+  ctx->user = user;
+  return GSW_OK;
+}
+
+gsw_status gsw_model_upload(gsw_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_elem,
+                            const int32_t* conn, const int32_t* elem_mat, int32_t n_mat,
+                            const double* mat, int64_t n_faces, const int32_t* faces,
+                            const int32_t* face_elem, const int32_t* face_tag, const double* period,
+                            int32_t n_rec, const double* rec_xy, int32_t* model_id) {
+  if (!ctx) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  if (!model_id) return fail(ctx, GSW_E_INVALID, "model_id is NULL");
+  if (n_nodes <= 0 || n_elem <= 0 || n_faces < 0 || n_rec < 0)
+    return fail(ctx, GSW_E_INVALID, "sizes must be positive (n_nodes %lld, n_elem %lld)",
+                (long long)n_nodes, (long long)n_elem);
+  if (n_nodes > (int64_t)INT32_MAX || n_elem > (int64_t)INT32_MAX / 10)
+    return fail(ctx, GSW_E_INVALID, "mesh too large for 32-bit node indices");
+  if (!xyz || !conn || !elem_mat || !mat || (n_faces > 0 && (!faces || !face_elem || !face_tag)) ||
+      (n_rec > 0 && !rec_xy))
+    return fail(ctx, GSW_E_INVALID, "NULL array argument");
+  if (n_mat <= 0 || n_mat > kMaxMat) return fail(ctx, GSW_E_INVALID, "n_mat must be 1..%d", kMaxMat);
+  if (!finite_all(xyz, 3 * (size_t)n_nodes)) return fail(ctx, GSW_E_INVALID, "non-finite node coordinate");
+  for (int i = 0; i < n_mat; ++i) {
+    const double Vp = mat[4 * i], Vs = mat[4 * i + 1], rho = mat[4 * i + 2], h = mat[4 * i + 3];
+    if (!(Vs > 0.0 && Vp > Vs && rho > 0.0 && h >= 0.0 && isfinite(Vp) && isfinite(rho) && isfinite(h)))
+      return fail(ctx, GSW_E_INVALID, "material %d must satisfy Vp > Vs > 0, rho > 0, h >= 0", i);
+  }
+  for (int64_t i = 0; i < 10 * n_elem; ++i)
+    if (conn[i] < 0 || conn[i] >= n_nodes)
+      return fail(ctx, GSW_E_INVALID, "element %lld references node %d outside [0, %lld)",
+                  (long long)(i / 10), conn[i], (long long)n_nodes);
+  for (int64_t i = 0; i < n_elem; ++i)
+    if (elem_mat[i] < 0 || elem_mat[i] >= n_mat)
+      return fail(ctx, GSW_E_INVALID, "element %lld has material %d outside [0, %d)", (long long)i,
+                  elem_mat[i], n_mat);
+  for (int64_t i = 0; i < n_faces; ++i) {
+    if (face_elem[i] < 0 || face_elem[i] >= n_elem)
+      return fail(ctx, GSW_E_INVALID, "face %lld owner element out of range", (long long)i);
+    if (face_tag[i] < 0 || face_tag[i] > 2)
+      return fail(ctx, GSW_E_INVALID, "face %lld tag %d not in {0, 1, 2}", (long long)i, face_tag[i]);
+    for (int k = 0; k < 6; ++k)
+      if (faces[6 * i + k] < 0 || faces[6 * i + k] >= n_nodes)
+        return fail(ctx, GSW_E_INVALID, "face %lld references a node out of range", (long long)i);
+  }
+  if (n_rec > 0 && !finite_all(rec_xy, 2 * (size_t)n_rec))
+    return fail(ctx, GSW_E_INVALID, "non-finite receiver position");
+  double px = period ? period[0] : 0.0, py = period ? period[1] : 0.0;
+  if (!(px >= 0.0 && py >= 0.0)) return fail(ctx, GSW_E_INVALID, "periods must be >= 0");
+
+  Model* m = new Model();
+  m->N = n_nodes;
+  m->E = n_elem;
+  m->F = n_faces;
+  m->n_mat = n_mat;
+  m->n_rec = n_rec;
+  m->period[0] = px;
+  m->period[1] = py;
+  m->raw_mat.assign(mat, mat + 4 * n_mat);
+  cudaStream_t s = ctx->stream;
+  gsw_status st = GSW_OK;
+  auto bail = [&](gsw_status code) {
+    cudaStreamSynchronize(s);
+    free_model(ctx, m);
+    return code;
+  };
+#define TRYM(expr)                  \
+  do {                              \
+    st = (expr);                    \
+    if (st != GSW_OK) return bail(st); \
+  } while (0)
+#define CKM(call)                                                                              \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return bail(fail(ctx, GSW_E_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)));       \
+  } while (0)
+  TRYM(alloc_into(ctx, m, &m->xyz, 3 * (size_t)n_nodes));
+  TRYM(alloc_into(ctx, m, &m->conn, 10 * (size_t)n_elem));
+  TRYM(alloc_into(ctx, m, &m->geo, 10 * (size_t)n_elem));
+  TRYM(alloc_into(ctx, m, &m->emat, (size_t)n_elem));
+  TRYM(alloc_into(ctx, m, &m->raw_mat_dev, 4 * (size_t)n_mat));
+  TRYM(alloc_into(ctx, m, &m->mat, (size_t)kMaxMat));
+  TRYM(alloc_into(ctx, m, &m->fnode, 6 * (size_t)(n_faces > 0 ? n_faces : 1)));
+  TRYM(alloc_into(ctx, m, &m->face_elem, (size_t)(n_faces > 0 ? n_faces : 1)));
+  TRYM(alloc_into(ctx, m, &m->face_tag, (size_t)(n_faces > 0 ? n_faces : 1)));
+  TRYM(alloc_into(ctx, m, &m->fgeo, 6 * (size_t)(n_faces > 0 ? n_faces : 1)));
+  TRYM(alloc_into(ctx, m, &m->rec_xy, 2 * (size_t)(n_rec > 0 ? n_rec : 1)));
+  TRYM(alloc_into(ctx, m, &m->rec_face, (size_t)(n_rec > 0 ? n_rec : 1)));
+  TRYM(alloc_into(ctx, m, &m->rec_node, 6 * (size_t)(n_rec > 0 ? n_rec : 1)));
+  TRYM(alloc_into(ctx, m, &m->rec_w, 6 * (size_t)(n_rec > 0 ? n_rec : 1)));
+  TRYM(alloc_into(ctx, m, &m->err, 1));
+  std::vector<int32_t> conn_soa = soa(conn, n_elem, 10);
+  std::vector<int32_t> face_soa = n_faces > 0 ? soa(faces, n_faces, 6) : std::vector<int32_t>();
+  CKM(cudaMemcpyAsync(m->xyz, xyz, sizeof(double) * 3 * n_nodes, cudaMemcpyHostToDevice, s));
+  CKM(cudaMemcpyAsync(m->conn, conn_soa.data(), sizeof(int32_t) * 10 * n_elem, cudaMemcpyHostToDevice, s));
+  CKM(cudaMemcpyAsync(m->emat, elem_mat, sizeof(int32_t) * n_elem, cudaMemcpyHostToDevice, s));
+  CKM(cudaMemcpyAsync(m->raw_mat_dev, mat, sizeof(double) * 4 * n_mat, cudaMemcpyHostToDevice, s));
+  if (n_faces > 0) {
+    CKM(cudaMemcpyAsync(m->fnode, face_soa.data(), sizeof(int32_t) * 6 * n_faces, cudaMemcpyHostToDevice, s));
+    CKM(cudaMemcpyAsync(m->face_elem, face_elem, sizeof(int32_t) * n_faces, cudaMemcpyHostToDevice, s));
+    CKM(cudaMemcpyAsync(m->face_tag, face_tag, sizeof(int32_t) * n_faces, cudaMemcpyHostToDevice, s));
+  }
+  if (n_rec > 0)
+    CKM(cudaMemcpyAsync(m->rec_xy, rec_xy, sizeof(double) * 2 * n_rec, cudaMemcpyHostToDevice, s));
+  CKM(cudaMemsetAsync(m->err, 0, sizeof(int), s));
+  launch_material(m->mat, m->raw_mat_dev, n_mat, 0.0, 0.0, 0.0, s);
+  ModelView mv = m->view();
+  launch_geometry(mv, m->xyz, px, py, m->geo, m->err, s);
+  launch_face_geometry(mv, m->xyz, px, py, m->face_elem, m->face_tag, m->fgeo, m->err, s);
+  launch_receivers(mv, m->xyz, px, py, m->rec_xy, n_rec, m->rec_face, m->rec_node, m->rec_w, m->err, s);
+  CKM(cudaGetLastError());
+  st = check_device_err(ctx, m, "model rejected");
+  if (st != GSW_OK) return bail(st);
+  const int id = ctx->next_id++;
+  ctx->models[id] = m;
+  *model_id = id;
+  return GSW_OK;
+#undef TRYM
+#undef CKM
+}
+
+gsw_status gsw_model_free(gsw_ctx* ctx, int32_t model_id) {
+  if (!ctx) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  cudaStreamSynchronize(ctx->stream);
+  free_model(ctx, m);
+  ctx->models.erase(model_id);
+  return GSW_OK;
+}
+
+gsw_status gsw_model_info(gsw_ctx* ctx, int32_t model_id, int64_t* out) {
+  if (!ctx || !out) return GSW_E_INVALID;
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  out[0] = m->N;
+  out[1] = m->E;
+  out[2] = m->F;
+  out[3] = m->n_rec;
+  out[4] = (int64_t)m->bytes;
+  return GSW_OK;
+}
+
+gsw_status gsw_set_time(gsw_ctx* ctx, int32_t model_id, double dt, int32_t n_steps, double f1,
+                        double f2) {
+  if (!ctx) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (!(dt > 0.0) || !isfinite(dt) || n_steps <= 0 || !(f1 > 0.0) || !(f2 > f1) || !isfinite(f2))
+    return fail(ctx, GSW_E_INVALID, "need dt > 0, n_steps > 0, 0 < f1 < f2");
+  if (m->time_set && n_steps != m->n_steps) {
+    // re-size the receiver history
+    dev_free(ctx, m->wave);
+    for (auto& p : m->allocs)
+      if (p == m->wave) p = nullptr;
+    m->n_steps = n_steps;
+    TRY(alloc_into(ctx, m, &m->wave, (size_t)m->n_rec * 3 * (size_t)n_steps));
+  }
+  m->dt = dt;
+  m->f1 = f1;
+  m->f2 = f2;
+  if (!m->time_set) {
+    m->n_steps = n_steps;
+    TRY(model_state_alloc(ctx, m));
+  }
+  m->time_set = true;
+  m->input_set = false;
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemsetAsync(m->err, 0, sizeof(int), s));
+  launch_material(m->mat, m->raw_mat_dev, m->n_mat, dt, f1, f2, s);
+  launch_block_jacobi(m->view(), m->dblk, m->dinv, m->err, s);
+  CK(cudaGetLastError());
+  TRY(check_device_err(ctx, m, "preconditioner"));
+  return model_reset(ctx, m);
+}
+
+gsw_status gsw_set_input(gsw_ctx* ctx, int32_t model_id, int32_t dir, const double* p, int32_t n) {
+  if (!ctx) return GSW_E_INVALID;
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (!m->time_set) return fail(ctx, GSW_E_STATE, "call gsw_set_time first");
+  if (dir < 0 || dir > 2) return fail(ctx, GSW_E_INVALID, "dir must be 0, 1 or 2");
+  if (!p || n != m->n_steps) return fail(ctx, GSW_E_INVALID, "input length %d != n_steps %d", n, m->n_steps);
+  if (!finite_all(p, (size_t)n)) return fail(ctx, GSW_E_INVALID, "non-finite input sample");
+  m->input.assign(p, p + n);
+  m->dir = dir;
+  m->input_set = true;
+  return GSW_OK;
+}
+
+gsw_status gsw_set_solver(gsw_ctx* ctx, int32_t model_id, const gsw_solver_opts* opts) {
+  if (!ctx || !opts) return GSW_E_INVALID;
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (!(opts->tol > 0.0) || opts->max_iter <= 0)
+    return fail(ctx, GSW_E_INVALID, "need tol > 0 and max_iter > 0");
+  if (opts->precision != GSW_PREC_FP64)
+    return fail(ctx, GSW_E_INVALID, "precision mode %d is not available", opts->precision);
+  m->opts = *opts;
+  return GSW_OK;
+}
+
+gsw_status gsw_reset(gsw_ctx* ctx, int32_t model_id) {
+  if (!ctx) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (!m->time_set) return fail(ctx, GSW_E_STATE, "call gsw_set_time first");
+  return model_reset(ctx, m);
+}
+
+gsw_status gsw_step(gsw_ctx* ctx, int32_t model_id, int32_t n) {
+  if (!ctx) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (!m->time_set || !m->input_set) return fail(ctx, GSW_E_STATE, "set the time and the input first");
+  if (m->failed) return fail(ctx, GSW_E_STATE, "model failed at step %lld; reset it", (long long)m->step);
+  if (n < 0 || m->step + n > m->n_steps)
+    return fail(ctx, GSW_E_INVALID, "cannot step %d from %lld of %d", n, (long long)m->step, m->n_steps);
+  for (int i = 0; i < n; ++i) TRY(step_fp64(ctx, m));
+  return GSW_OK;
+}
+
+gsw_status gsw_run(gsw_ctx* ctx, const int32_t* model_ids, int32_t n_models) {
+  if (!ctx || (!model_ids && n_models > 0)) return GSW_E_INVALID;
+  for (int i = 0; i < n_models; ++i) {
+    Model* m = find(ctx, model_ids[i]);
+    if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_ids[i]);
+    TRY(gsw_reset(ctx, model_ids[i]));
+    TRY(gsw_step(ctx, model_ids[i], m->n_steps));
+  }
+  return GSW_OK;
+}
+
+gsw_status gsw_read_waveforms(gsw_ctx* ctx, int32_t model_id, double* out) {
+  if (!ctx || !out) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (!m->time_set) return fail(ctx, GSW_E_STATE, "call gsw_set_time first");
+  CK(cudaMemcpyAsync(out, m->wave, sizeof(double) * (size_t)m->n_rec * 3 * m->n_steps,
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return GSW_OK;
+}
+
+gsw_status gsw_read_waveform_steps(gsw_ctx* ctx, int32_t model_id, int32_t step0, int32_t count,
+                                   double* out) {
+  if (!ctx || !out) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (!m->time_set) return fail(ctx, GSW_E_STATE, "call gsw_set_time first");
+  if (step0 < 0 || count <= 0 || step0 + count > m->n_steps)
+    return fail(ctx, GSW_E_INVALID, "steps [%d, %d) outside [0, %d)", step0, step0 + count, m->n_steps);
+  if (m->n_rec == 0) return GSW_OK;
+  CK(cudaMemcpy2DAsync(out, sizeof(double) * count, m->wave + step0, sizeof(double) * m->n_steps,
+                       sizeof(double) * count, 3 * (size_t)m->n_rec, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return GSW_OK;
+}
+
+gsw_status gsw_timing(gsw_ctx* ctx, int32_t model_id, int32_t enable, double* ebe_ms, int64_t* ebe_launches) {
+  if (!ctx) return GSW_E_INVALID;
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (enable == 1) {
+    m->timing = true;
+    m->ebe_ms = 0.0;
+    m->ebe_count = 0;
+  } else if (enable == 0) {
+    m->timing = false;
+  }
+  if (ebe_ms) *ebe_ms = m->ebe_ms;
+  if (ebe_launches) *ebe_launches = m->ebe_count;
+  return GSW_OK;
+}
+
+gsw_status gsw_stats_get(gsw_ctx* ctx, int32_t model_id, gsw_stats* out) {
+  if (!ctx || !out) return GSW_E_INVALID;
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  *out = m->stats;
+  return GSW_OK;
+}
+
+gsw_status gsw_get_state(gsw_ctx* ctx, int32_t model_id, double* u, double* v, double* a, int64_t* step) {
+  if (!ctx) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (!m->time_set) return fail(ctx, GSW_E_STATE, "call gsw_set_time first");
+  const size_t bytes = sizeof(double) * 3 * (size_t)m->N;
+  if (u) CK(cudaMemcpyAsync(u, m->u, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  if (v) CK(cudaMemcpyAsync(v, m->v, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  if (a) CK(cudaMemcpyAsync(a, m->a, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (step) *step = m->step;
+  return GSW_OK;
+}
+
+gsw_status gsw_set_state(gsw_ctx* ctx, int32_t model_id, const double* u, const double* v,
+                         const double* a, int64_t step) {
+  if (!ctx || !u || !v || !a) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (!m->time_set) return fail(ctx, GSW_E_STATE, "call gsw_set_time first");
+  if (step < 0 || step > m->n_steps) return fail(ctx, GSW_E_INVALID, "step out of range");
+  const size_t n3 = 3 * (size_t)m->N;
+  if (!finite_all(u, n3) || !finite_all(v, n3) || !finite_all(a, n3))
+    return fail(ctx, GSW_E_INVALID, "non-finite state");
+  const size_t bytes = sizeof(double) * n3;
+  CK(cudaMemcpyAsync(m->u, u, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(m->v, v, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(m->a, a, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  m->step = step;
+  m->failed = false;
+  return GSW_OK;
+}
+
+gsw_status gsw_apply(gsw_ctx* ctx, int32_t model_id, int32_t which, const double* x_dev, double* y_dev) {
+  if (!ctx || !x_dev || !y_dev) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (!m->time_set) return fail(ctx, GSW_E_STATE, "call gsw_set_time first");
+  if (which < 0 || which > 3) return fail(ctx, GSW_E_INVALID, "which must be 0..3");
+  CK(cudaMemsetAsync(y_dev, 0, sizeof(double) * 3 * (size_t)m->N, ctx->stream));
+  const int mode = which == 0 ? kModeA : which == 1 ? kModeK : which == 2 ? kModeM : kModeC;
+  launch_ebe(mode, m->view(), x_dev, nullptr, nullptr, y_dev, 0.0, 0, nullptr, nullptr, ctx->stream);
+  CK(cudaGetLastError());
+  return GSW_OK;
+}
+
+gsw_status gsw_read_preconditioner(gsw_ctx* ctx, int32_t model_id, double* out) {
+  if (!ctx || !out) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (!m->time_set) return fail(ctx, GSW_E_STATE, "call gsw_set_time first");
+  CK(cudaMemcpyAsync(out, m->dinv, sizeof(double) * 6 * (size_t)m->N, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return GSW_OK;
+}
+
+gsw_status gsw_read_receivers(gsw_ctx* ctx, int32_t model_id, int32_t* nodes, double* weights) {
+  if (!ctx || !nodes || !weights) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (m->n_rec == 0) return GSW_OK;
+  CK(cudaMemcpyAsync(nodes, m->rec_node, sizeof(int32_t) * 6 * m->n_rec, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(weights, m->rec_w, sizeof(double) * 6 * m->n_rec, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return GSW_OK;
+}
+
+gsw_status gsw_misfit(gsw_ctx* ctx, int32_t n_rec, int32_t n_t, const double* G, const double* obs,
+                      int32_t stride, int32_t n_shifts, double tau, double* err, double* c_out) {
+  if (!ctx || !G || !obs || !err) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  if (n_rec <= 0 || n_t <= 0 || stride <= 0 || n_shifts <= 0 || !(tau >= 0.0))
+    return fail(ctx, GSW_E_INVALID, "need n_rec, n_t, stride, n_shifts > 0 and tau >= 0");
+  if (3 * n_shifts > kMisfitMaxUnknowns)
+    return fail(ctx, GSW_E_INVALID, "3 * n_shifts must be <= %d", kMisfitMaxUnknowns);
+  if (!finite_all(G, (size_t)n_rec * 9 * n_t) || !finite_all(obs, (size_t)n_rec * 3 * n_t))
+    return fail(ctx, GSW_E_INVALID, "non-finite Green's function or observation");
+  char msg[256] = {0};
+  cudaError_t ce = cudaSuccess;
+  int rc = misfit_run(ctx->misfit, ctx->stream, n_rec, n_t, G, obs, stride, n_shifts, tau, err, c_out,
+                      msg, sizeof msg, &ce);
+  if (rc == 1) return fail(ctx, GSW_E_CUDA, "misfit: %s (%s)", msg, cudaGetErrorString(ce));
+  if (rc == 2) return fail(ctx, GSW_E_NOMEM, "misfit: %s", msg);
+  if (rc == 3) return fail(ctx, GSW_E_INVALID, "misfit: %s", msg);
+  return GSW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gsw {
+
+constexpr int kMaxMat = 32;        // materials (layers) per model
+constexpr int kNodeThreads = 256;  // node-wise kernels
+constexpr int kElemThreads = 128;  // element-by-element kernels
+constexpr int kMaxNodeBlocks = 152 * 8;
+
+// Per-material coefficients. lam, mu, rho from (Vp, Vs, rho); alpha, beta the
+// Rayleigh fit; cK = 1 + 2 beta/dt and cM = 4/dt^2 + 2 alpha/dt scale the
+// element stiffness and mass inside A = K + (2/dt) C + (4/dt^2) M.
+struct MatCoef {
+  double lam, mu, rho, alpha, beta, Vp, Vs, h, cK, cM;
+};
+
+// Device-side scalars of one CG solve (one per model and right-hand side).
+struct CgScalars {
+  double bb;      // ||b||^2
+  double rz;      // r . z of the current iterate
+  double pq;      // p . A p
+  double rr;      // r . r
+  double relres;  // ||r|| / ||b||
+  double tol;
+  double beta;    // p <- z + beta p
+  double pad0;
+  int iter;
+  int max_iter;
+  int done;       // 1 once converged or failed
+  int status;     // 0, or a gsw_status error code
+  int zero_rhs;   // b == 0: the solution is exactly 0
+  int pad1;
+  unsigned int counter;  // arrival counter of the last-block reductions
+  unsigned int pad2;
+};
+
+// Element / face / node data of one uploaded model (device pointers).
+struct ModelView {
+  int64_t N;                // nodes
+  int64_t E;                // elements
+  int64_t F;                // boundary faces (all tags)
+  const int32_t* conn;      // [10][E] (structure of arrays)
+  const double* geo;        // [10][E]: grad L1 (3), grad L2 (3), grad L3 (3), V
+  const int32_t* emat;      // [E]
+  const MatCoef* mat;       // [n_mat]
+  const int32_t* fnode;     // [6][F]
+  const double* fgeo;       // [6][F]: A rho Vs, A (rho Vp - rho Vs), n (3), tag
+  double dt;
+};
+
+enum EbeMode { kModeA = 0, kModeK = 1, kModeM = 2, kModeC = 3, kModeRhs = 4 };
+
+// ---- kernels (gsw_kernels.cu) -------------------------------------------------
+void launch_geometry(const ModelView& m, const double* xyz, double px, double py, double* geo,
+                     int* err, cudaStream_t s);
+void launch_face_geometry(const ModelView& m, const double* xyz, double px, double py,
+                          const int32_t* face_elem, const int32_t* face_tag, double* fgeo,
+                          int* err, cudaStream_t s);
+void launch_material(MatCoef* mat, const double* raw, int n_mat, double dt, double f1, double f2,
+                     cudaStream_t s);
+void launch_block_jacobi(const ModelView& m, double* dblk, double* dinv, int* err,
+                         cudaStream_t s);
+void launch_receivers(const ModelView& m, const double* xyz, double px, double py,
+                      const double* rec_xy, int n_rec, int32_t* rec_face, int32_t* rec_node,
+                      double* rec_w, int* err, cudaStream_t s);
+void launch_ebe(int mode, const ModelView& m, const double* x, const double* v, const double* a,
+                double* y, double force, int dir, double* partials, CgScalars* cg,
+                cudaStream_t s);
+void launch_cg_init(const ModelView& m, const double* b, const double* v, const double* a,
+                    double* x, double* q, double* partials, CgScalars* cg, cudaStream_t s);
+void launch_cg_residual(const ModelView& m, const double* b, double* q, double* r, double* z,
+                        double* p, const double* dinv, double* partials, CgScalars* cg,
+                        cudaStream_t s);
+void launch_cg_update(const ModelView& m, double* x, double* r, double* z, const double* p,
+                      double* q, const double* dinv, double* partials, CgScalars* cg,
+                      cudaStream_t s);
+void launch_cg_pupdate(const ModelView& m, const double* z, double* p, const CgScalars* cg,
+                       cudaStream_t s);
+void launch_newmark(const ModelView& m, const double* x, double* u, double* v, double* a,
+                    const CgScalars* cg, cudaStream_t s);
+void launch_record(const double* v, const int32_t* rec_node, const double* rec_w, int n_rec,
+                   double* wave, int n_steps, int step, cudaStream_t s);
+int ebe_blocks(const ModelView& m);
+int node_blocks(int64_t n);
+
+}  // namespace gsw

@@ -1,0 +1,865 @@
+// FP64 kernels of the implicit finite-element wave analysis.
+//
+// Discretisation (Section 2, Eq. (1); Section 3, computational-cost
+// paragraph): second-order (10-node) straight-sided tetrahedra, Newmark
+// average acceleration, block-Jacobi preconditioned CG per step, Lysmer
+// dashpots on base and sides with the input applied as a base force.
+//
+// Element-by-element operator.  For an affine quadratic tetrahedron with
+// barycentric gradients g_m = grad L_m, the displacement gradient is linear:
+// grad u = sum_k L_k H_k, with H_k (the gradient at vertex k)
+//     H_k = 4 [ u_k (x) g_k + sum_{b != k} u_kb (x) g_b ] - sum_a u_a (x) g_a,
+// so the stress is sigma = sum_k L_k S_k with S_k = lam tr(H_k) I + mu (H_k +
+// H_k^T).  Integrating sigma . grad N exactly (int L_i L_j dV = V (1 + d_ij)/20)
+// gives, with T_km = S_k g_m and T_m = sum_k T_km,
+//     vertex a:     f_a  = V/20 (4 T_aa - T_a)
+//     edge (a, b):  f_ab = V/5  (T_a + T_b + T_ab + T_ba).
+// This costs ~520 FP64 operations per element instead of the ~1800 of a dense
+// 30x30 product, which matters because the FP64 pipe is the bound on GB300.
+// The consistent mass uses its closed-form pattern rho V / 420 {vertex diag 6,
+// vertex-vertex 1, vertex-edge -4 (edge contains the vertex) or -6, edge diag
+// 32, adjacent edges 16, opposite edges 8}.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "gsw_internal.cuh"
+
+namespace gsw {
+
+// edge index of the vertex pair (a, b), VTK order 01, 12, 02, 03, 13, 23
+__host__ __device__ constexpr int edge_of(int a, int b) {
+  return (a + b == 1) ? 0 : (a + b == 3 ? (a * b == 2 ? 1 : 3) : (a + b == 2 ? 2 : (a + b == 4 ? 4 : 5)));
+}
+__host__ __device__ constexpr int edge_a(int e) { return e == 0 ? 0 : e == 1 ? 1 : e == 2 ? 0 : e == 3 ? 0 : e == 4 ? 1 : 2; }
+__host__ __device__ constexpr int edge_b(int e) { return e == 0 ? 1 : e == 1 ? 2 : e == 2 ? 2 : e == 3 ? 3 : e == 4 ? 3 : 3; }
+__host__ __device__ constexpr int edge_opp(int e) { return e == 0 ? 5 : e == 1 ? 3 : e == 2 ? 4 : e == 3 ? 1 : e == 4 ? 2 : 0; }
+
+// ------------------------------------------------------------------------------
+// Reductions: warp shuffle, block tree, and a deterministic last-block finish.
+// ------------------------------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block; the result is valid in thread 0.  `sh` holds >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+  if (warp == 0) v = warp_sum(v);
+  return v;
+}
+
+// Each block contributes NQ partial sums; the last block to arrive sums all
+// partials in block order (so the result does not depend on scheduling) and
+// returns true in every thread of that block, with the totals in out[] of
+// thread 0.
+template <int NQ>
+__device__ bool last_block_reduce(const double (&vals)[NQ], double* partials,
+                                  unsigned int* counter, double (&out)[NQ]) {
+  __shared__ double sh[32];
+  __shared__ int am_last;
+  const unsigned int G = gridDim.x;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double s = block_sum(vals[q], sh);
+    if (threadIdx.x == 0) partials[q * G + blockIdx.x] = s;
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned int prev = atomicAdd(counter, 1u);
+    am_last = (prev == G - 1);
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double acc = 0.0;
+    for (unsigned int i = threadIdx.x; i < G; i += blockDim.x)
+      acc += ((volatile double*)partials)[q * G + i];
+    out[q] = block_sum(acc, sh);
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+// ------------------------------------------------------------------------------
+// Setup kernels
+// ------------------------------------------------------------------------------
+
+__device__ __forceinline__ double unwrap(double x, double x0, double P) {
+  return P > 0.0 ? x - P * rint((x - x0) / P) : x;
+}
+
+__global__ void geometry_kernel(ModelView m, const double* __restrict__ xyz, double px, double py,
+                                double* __restrict__ geo, int* err) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.E) return;
+  double X[10][3];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) {
+    const int64_t n = m.conn[k * m.E + e];
+    X[k][0] = xyz[3 * n];
+    X[k][1] = xyz[3 * n + 1];
+    X[k][2] = xyz[3 * n + 2];
+  }
+#pragma unroll
+  for (int k = 1; k < 10; ++k) {
+    X[k][0] = unwrap(X[k][0], X[0][0], px);
+    X[k][1] = unwrap(X[k][1], X[0][1], py);
+  }
+  double c1[3], c2[3], c3[3];
+  for (int i = 0; i < 3; ++i) {
+    c1[i] = X[1][i] - X[0][i];
+    c2[i] = X[2][i] - X[0][i];
+    c3[i] = X[3][i] - X[0][i];
+  }
+  // rows of J^{-1} for J = [c1 c2 c3] are (c2 x c3, c3 x c1, c1 x c2) / det
+  double r1[3] = {c2[1] * c3[2] - c2[2] * c3[1], c2[2] * c3[0] - c2[0] * c3[2], c2[0] * c3[1] - c2[1] * c3[0]};
+  double r2[3] = {c3[1] * c1[2] - c3[2] * c1[1], c3[2] * c1[0] - c3[0] * c1[2], c3[0] * c1[1] - c3[1] * c1[0]};
+  double r3[3] = {c1[1] * c2[2] - c1[2] * c2[1], c1[2] * c2[0] - c1[0] * c2[2], c1[0] * c2[1] - c1[1] * c2[0]};
+  const double det = c1[0] * r1[0] + c1[1] * r1[1] + c1[2] * r1[2];
+  if (!(det > 0.0) || !isfinite(det)) atomicOr(err, 1);
+  // straight sides: mid-edge nodes at the edge midpoints
+  double hmax = 0.0, dev = 0.0;
+#pragma unroll
+  for (int ed = 0; ed < 6; ++ed) {
+    const int a = edge_a(ed), b = edge_b(ed);
+    for (int i = 0; i < 3; ++i) {
+      const double mid = 0.5 * (X[a][i] + X[b][i]);
+      dev = fmax(dev, fabs(X[4 + ed][i] - mid));
+      hmax = fmax(hmax, fabs(X[a][i] - X[b][i]));
+    }
+  }
+  if (!(dev <= 1e-9 * hmax)) atomicOr(err, 2);
+  const double inv = 1.0 / det;
+  for (int i = 0; i < 3; ++i) {
+    geo[(0 + i) * m.E + e] = r1[i] * inv;
+    geo[(3 + i) * m.E + e] = r2[i] * inv;
+    geo[(6 + i) * m.E + e] = r3[i] * inv;
+  }
+  geo[9 * m.E + e] = det / 6.0;
+}
+
+__global__ void face_geometry_kernel(ModelView m, const double* __restrict__ xyz, double px, double py,
+                                     const int32_t* __restrict__ face_elem,
+                                     const int32_t* __restrict__ face_tag, double* __restrict__ fgeo,
+                                     int* err) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= m.F) return;
+  double X[6][3];
+  for (int k = 0; k < 6; ++k) {
+    const int64_t n = m.fnode[k * m.F + f];
+    for (int i = 0; i < 3; ++i) X[k][i] = xyz[3 * n + i];
+    X[k][0] = unwrap(X[k][0], X[0][0], px);
+    X[k][1] = unwrap(X[k][1], X[0][1], py);
+  }
+  double a[3], b[3];
+  for (int i = 0; i < 3; ++i) {
+    a[i] = X[1][i] - X[0][i];
+    b[i] = X[2][i] - X[0][i];
+  }
+  double c[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+  const double nrm = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+  if (!(nrm > 0.0) || !isfinite(nrm)) atomicOr(err, 4);
+  const double area = 0.5 * nrm;
+  const MatCoef mc = m.mat[m.emat[face_elem[f]]];
+  const double zs = mc.rho * mc.Vs, zp = mc.rho * mc.Vp;
+  fgeo[0 * m.F + f] = area * zs;
+  fgeo[1 * m.F + f] = area * (zp - zs);
+  fgeo[2 * m.F + f] = c[0] / nrm;
+  fgeo[3 * m.F + f] = c[1] / nrm;
+  fgeo[4 * m.F + f] = c[2] / nrm;
+  fgeo[5 * m.F + f] = (double)face_tag[f];
+}
+
+// Rayleigh coefficients: least-squares fit of alpha/(4 pi f) + beta pi f to h
+// over [f1, f2], from the closed-form integrals of the normal equations.
+__global__ void material_kernel(MatCoef* mat, const double* raw, int n_mat, double dt, double f1,
+                                double f2) {
+  const int i = threadIdx.x;
+  if (i >= n_mat) return;
+  const double Vp = raw[4 * i], Vs = raw[4 * i + 1], rho = raw[4 * i + 2], h = raw[4 * i + 3];
+  MatCoef c;
+  c.Vp = Vp;
+  c.Vs = Vs;
+  c.rho = rho;
+  c.h = h;
+  c.mu = rho * Vs * Vs;
+  c.lam = rho * Vp * Vp - 2.0 * c.mu;
+  c.alpha = c.beta = 0.0;
+  c.cK = c.cM = 0.0;
+  if (dt > 0.0) {
+    const double pi = 3.14159265358979323846;
+    const double g11 = (1.0 / f1 - 1.0 / f2) / (16.0 * pi * pi);
+    const double g12 = 0.25 * (f2 - f1);
+    const double g22 = pi * pi * (f2 * f2 * f2 - f1 * f1 * f1) / 3.0;
+    const double r1 = h * log(f2 / f1) / (4.0 * pi);
+    const double r2 = h * pi * (f2 * f2 - f1 * f1) / 2.0;
+    const double det = g11 * g22 - g12 * g12;
+    c.alpha = (g22 * r1 - g12 * r2) / det;
+    c.beta = (g11 * r2 - g12 * r1) / det;
+    c.cK = 1.0 + 2.0 * c.beta / dt;
+    c.cM = 4.0 / (dt * dt) + 2.0 * c.alpha / dt;
+  }
+  mat[i] = c;
+}
+
+// Diagonal 3x3 nodal blocks of A: per element, K_aa = (lam + mu) G + mu tr(G) I
+// with G = int grad N_a grad N_a^T dV (vertex: 3V/5 g_a g_a^T; edge (a,b):
+// 8V/5 (g_a g_a^T + g_b g_b^T) + 4V/5 (g_a g_b^T + g_b g_a^T)), M_aa = rho V
+// (6 or 32)/420 I; per absorbing face (2/dt) A (6 or 32)/180 T.
+__global__ void diag_blocks_kernel(ModelView m, double* __restrict__ dblk) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < m.E) {
+    const int64_t e = t;
+    double g[4][3];
+    for (int i = 0; i < 3; ++i) {
+      g[1][i] = m.geo[(0 + i) * m.E + e];
+      g[2][i] = m.geo[(3 + i) * m.E + e];
+      g[3][i] = m.geo[(6 + i) * m.E + e];
+      g[0][i] = -(g[1][i] + g[2][i] + g[3][i]);
+    }
+    const double V = m.geo[9 * m.E + e];
+    const MatCoef mc = m.mat[m.emat[e]];
+    const double kl = mc.cK * (mc.lam + mc.mu), km = mc.cK * mc.mu;
+    for (int k = 0; k < 10; ++k) {
+      double G[3][3];
+      if (k < 4) {
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) G[i][j] = 0.6 * V * g[k][i] * g[k][j];
+      } else {
+        const int a = edge_a(k - 4), b = edge_b(k - 4);
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j)
+            G[i][j] = 1.6 * V * (g[a][i] * g[a][j] + g[b][i] * g[b][j]) +
+                      0.8 * V * (g[a][i] * g[b][j] + g[b][i] * g[a][j]);
+      }
+      const double tr = G[0][0] + G[1][1] + G[2][2];
+      const double md = mc.cM * mc.rho * V * (k < 4 ? 6.0 : 32.0) / 420.0;
+      const int64_t n = m.conn[k * m.E + e];
+      double* d = dblk + 6 * n;
+      atomicAdd(d + 0, kl * G[0][0] + km * tr + md);
+      atomicAdd(d + 1, kl * G[1][1] + km * tr + md);
+      atomicAdd(d + 2, kl * G[2][2] + km * tr + md);
+      atomicAdd(d + 3, kl * G[0][1]);
+      atomicAdd(d + 4, kl * G[0][2]);
+      atomicAdd(d + 5, kl * G[1][2]);
+    }
+  } else if (t < m.E + m.F) {
+    const int64_t f = t - m.E;
+    const double tag = m.fgeo[5 * m.F + f];
+    if (tag < 0.5) return;  // free surface
+    const double As = m.fgeo[f], Ad = m.fgeo[m.F + f];
+    const double n0 = m.fgeo[2 * m.F + f], n1 = m.fgeo[3 * m.F + f], n2 = m.fgeo[4 * m.F + f];
+    const double s = 2.0 / m.dt;
+    for (int k = 0; k < 6; ++k) {
+      const double w = s * (k < 3 ? 6.0 : 32.0) / 180.0;
+      const int64_t n = m.fnode[k * m.F + f];
+      double* d = dblk + 6 * n;
+      atomicAdd(d + 0, w * (As + Ad * n0 * n0));
+      atomicAdd(d + 1, w * (As + Ad * n1 * n1));
+      atomicAdd(d + 2, w * (As + Ad * n2 * n2));
+      atomicAdd(d + 3, w * Ad * n0 * n1);
+      atomicAdd(d + 4, w * Ad * n0 * n2);
+      atomicAdd(d + 5, w * Ad * n1 * n2);
+    }
+  }
+}
+
+__global__ void invert_blocks_kernel(int64_t N, const double* __restrict__ dblk,
+                                     double* __restrict__ dinv, int* err) {
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    const double* d = dblk + 6 * n;
+    const double a = d[0], b = d[1], c = d[2], xy = d[3], xz = d[4], yz = d[5];
+    const double i00 = b * c - yz * yz, i11 = a * c - xz * xz, i22 = a * b - xy * xy;
+    const double i01 = xz * yz - xy * c, i02 = xy * yz - xz * b, i12 = xy * xz - a * yz;
+    const double det = a * i00 + xy * i01 + xz * i02;
+    if (!(det > 0.0) || !isfinite(det)) atomicOr(err, 8);
+    const double s = 1.0 / det;
+    double* o = dinv + 6 * n;
+    o[0] = i00 * s;
+    o[1] = i11 * s;
+    o[2] = i22 * s;
+    o[3] = i01 * s;
+    o[4] = i02 * s;
+    o[5] = i12 * s;
+  }
+}
+
+// Receivers: the lowest-numbered free-surface face whose horizontal projection
+// contains the point (barycentric coordinates >= -1e-10), then the 6-node
+// triangle's shape functions there.
+__global__ void receiver_find_kernel(ModelView m, const double* __restrict__ xyz, double px,
+                                     double py, const double* __restrict__ rec_xy,
+                                     int32_t* rec_face) {
+  const int r = blockIdx.x;
+  const double qx0 = rec_xy[2 * r], qy0 = rec_xy[2 * r + 1];
+  for (int64_t f = threadIdx.x; f < m.F; f += blockDim.x) {
+    if (m.fgeo[5 * m.F + f] != 0.0) continue;
+    double x[3], y[3];
+    for (int k = 0; k < 3; ++k) {
+      const int64_t n = m.fnode[k * m.F + f];
+      x[k] = xyz[3 * n];
+      y[k] = xyz[3 * n + 1];
+    }
+    x[1] = unwrap(x[1], x[0], px);
+    x[2] = unwrap(x[2], x[0], px);
+    y[1] = unwrap(y[1], y[0], py);
+    y[2] = unwrap(y[2], y[0], py);
+    const double qx = unwrap(qx0, x[0], px), qy = unwrap(qy0, y[0], py);
+    const double ax = x[1] - x[0], ay = y[1] - y[0], bx = x[2] - x[0], by = y[2] - y[0];
+    const double det = ax * by - bx * ay;
+    const double dx = qx - x[0], dy = qy - y[0];
+    const double l1 = (dx * by - bx * dy) / det, l2 = (ax * dy - dx * ay) / det;
+    const double l0 = 1.0 - l1 - l2;
+    if (l0 >= -1e-10 && l1 >= -1e-10 && l2 >= -1e-10) atomicMin(rec_face + r, (int32_t)f);
+  }
+}
+
+__global__ void receiver_weights_kernel(ModelView m, const double* __restrict__ xyz, double px,
+                                        double py, const double* __restrict__ rec_xy, int n_rec,
+                                        const int32_t* __restrict__ rec_face, int32_t* rec_node,
+                                        double* rec_w, int* err) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rec) return;
+  const int32_t f = rec_face[r];
+  if (f < 0 || f >= m.F) {
+    atomicOr(err, 16);
+    for (int k = 0; k < 6; ++k) {
+      rec_node[6 * r + k] = 0;
+      rec_w[6 * r + k] = 0.0;
+    }
+    return;
+  }
+  double x[3], y[3];
+  int64_t nd[6];
+  for (int k = 0; k < 6; ++k) nd[k] = m.fnode[k * m.F + f];
+  for (int k = 0; k < 3; ++k) {
+    x[k] = xyz[3 * nd[k]];
+    y[k] = xyz[3 * nd[k] + 1];
+  }
+  x[1] = unwrap(x[1], x[0], px);
+  x[2] = unwrap(x[2], x[0], px);
+  y[1] = unwrap(y[1], y[0], py);
+  y[2] = unwrap(y[2], y[0], py);
+  const double qx = unwrap(rec_xy[2 * r], x[0], px), qy = unwrap(rec_xy[2 * r + 1], y[0], py);
+  const double ax = x[1] - x[0], ay = y[1] - y[0], bx = x[2] - x[0], by = y[2] - y[0];
+  const double det = ax * by - bx * ay;
+  const double dx = qx - x[0], dy = qy - y[0];
+  const double L1 = (dx * by - bx * dy) / det, L2 = (ax * dy - dx * ay) / det;
+  const double L[3] = {1.0 - L1 - L2, L1, L2};
+  double w[6];
+  for (int a = 0; a < 3; ++a) w[a] = L[a] * (2.0 * L[a] - 1.0);
+  w[3] = 4.0 * L[0] * L[1];
+  w[4] = 4.0 * L[1] * L[2];
+  w[5] = 4.0 * L[2] * L[0];
+  for (int k = 0; k < 6; ++k) {
+    rec_node[6 * r + k] = (int32_t)nd[k];
+    rec_w[6 * r + k] = w[k];
+  }
+}
+
+// ------------------------------------------------------------------------------
+// Element-by-element operator
+// ------------------------------------------------------------------------------
+
+// y += K' w, K' = the element stiffness with lam, mu pre-scaled (lamS = s lam
+// V/20, muS = s mu V/20).  g[m] = grad L_{m+1}; grad L_0 = -(g0 + g1 + g2).
+__device__ __forceinline__ void stiffness_apply(const double (&w)[10][3], const double (&g)[3][3],
+                                                double lamS, double muS, double (&y)[10][3]) {
+  double D0[3][3];  // u_m - u_0, m = 1..3
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) D0[m][i] = w[m + 1][i] - w[0][i];
+  double sumT[4][3], diagT[4][3], cross[6][3];
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) sumT[m][i] = 0.0;
+#pragma unroll
+  for (int e = 0; e < 6; ++e)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) cross[e][i] = 0.0;
+  const double mu2S = 2.0 * muS;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    // U(k, b) = u_k if b == k else u_{edge(k, b)}
+    double H[3][3];
+#pragma unroll
+    for (int m = 1; m < 4; ++m) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double ukm = (m == k) ? w[k][i] : w[4 + edge_of(k, m)][i];
+        const double uk0 = (k == 0) ? w[0][i] : w[4 + edge_of(k, 0)][i];
+        const double E = fma(4.0, ukm - uk0, -D0[m - 1][i]);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          if (m == 1)
+            H[i][j] = E * g[0][j];
+          else
+            H[i][j] = fma(E, g[m - 1][j], H[i][j]);
+        }
+      }
+    }
+    const double tr = H[0][0] + H[1][1] + H[2][2];
+    const double lt = lamS * tr;
+    double S[3][3];
+    S[0][0] = fma(mu2S, H[0][0], lt);
+    S[1][1] = fma(mu2S, H[1][1], lt);
+    S[2][2] = fma(mu2S, H[2][2], lt);
+    S[0][1] = S[1][0] = muS * (H[0][1] + H[1][0]);
+    S[0][2] = S[2][0] = muS * (H[0][2] + H[2][0]);
+    S[1][2] = S[2][1] = muS * (H[1][2] + H[2][1]);
+    double T[4][3];
+#pragma unroll
+    for (int m = 1; m < 4; ++m)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        T[m][i] = fma(S[i][0], g[m - 1][0], fma(S[i][1], g[m - 1][1], S[i][2] * g[m - 1][2]));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) T[0][i] = -(T[1][i] + T[2][i] + T[3][i]);
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) sumT[m][i] += T[m][i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) diagT[k][i] = T[k][i];
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+      if (b != k)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) cross[edge_of(k, b)][i] += T[b][i];
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) y[a][i] = fma(4.0, diagT[a][i], -sumT[a][i]);
+#pragma unroll
+  for (int e = 0; e < 6; ++e)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      y[4 + e][i] = 4.0 * (sumT[edge_a(e)][i] + sumT[edge_b(e)][i] + cross[e][i]);
+}
+
+// y += ms * P w with P the consistent-mass pattern (ms = s rho V / 420).
+__device__ __forceinline__ void mass_apply(const double (&w)[10][3], double ms, double (&y)[10][3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const double Xv = (w[0][i] + w[1][i]) + (w[2][i] + w[3][i]);
+    const double Xe = (w[4][i] + w[5][i]) + (w[6][i] + w[7][i]) + (w[8][i] + w[9][i]);
+    const double tv = fma(-6.0, Xe, Xv);
+    const double te = fma(16.0, Xe, -6.0 * Xv);
+    // vertex a: 5 w_a + 2 (edges at a) + Xv - 6 Xe
+    const double P0 = fma(5.0, w[0][i], fma(2.0, w[4][i] + w[6][i] + w[7][i], tv));
+    const double P1 = fma(5.0, w[1][i], fma(2.0, w[4][i] + w[5][i] + w[8][i], tv));
+    const double P2 = fma(5.0, w[2][i], fma(2.0, w[5][i] + w[6][i] + w[9][i], tv));
+    const double P3 = fma(5.0, w[3][i], fma(2.0, w[7][i] + w[8][i] + w[9][i], tv));
+    y[0][i] = fma(ms, P0, y[0][i]);
+    y[1][i] = fma(ms, P1, y[1][i]);
+    y[2][i] = fma(ms, P2, y[2][i]);
+    y[3][i] = fma(ms, P3, y[3][i]);
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      const int a = edge_a(e), b = edge_b(e), o = edge_opp(e);
+      const double P = fma(2.0, w[a][i] + w[b][i], fma(16.0, w[4 + e][i], fma(-8.0, w[4 + o][i], te)));
+      y[4 + e][i] = fma(ms, P, y[4 + e][i]);
+    }
+  }
+}
+
+// One thread per element (t < E) or boundary face (E <= t < E + F).
+//   kModeA   y = A x               (+ partial x.y when partials != nullptr)
+//   kModeK   y = K x,  kModeM y = M x,  kModeC y = C x
+//   kModeRhs y = f - K u + C v + M (a + (4/dt) v)  with x = u
+template <int MODE>
+__global__ void __launch_bounds__(kElemThreads) ebe_kernel(ModelView m, const double* __restrict__ x,
+                                                            const double* __restrict__ vv,
+                                                            const double* __restrict__ aa, double* y,
+                                                            double force, int dir, double* partials,
+                                                            CgScalars* cg) {
+  if (cg != nullptr && ((volatile CgScalars*)cg)->done) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double dot = 0.0;
+  if (t < m.E) {
+    const int64_t e = t;
+    int64_t nd[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) nd[k] = m.conn[k * m.E + e];
+    double g[3][3];
+#pragma unroll
+    for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) g[mm][i] = __ldg(m.geo + (3 * mm + i) * m.E + e);
+    const double V = __ldg(m.geo + 9 * m.E + e);
+    const MatCoef mc = m.mat[m.emat[e]];
+    double ks, ms;  // stiffness and mass scales
+    if (MODE == kModeA) {
+      ks = mc.cK;
+      ms = mc.cM;
+    } else if (MODE == kModeK) {
+      ks = 1.0;
+      ms = 0.0;
+    } else if (MODE == kModeM) {
+      ks = 0.0;
+      ms = 1.0;
+    } else if (MODE == kModeC) {
+      ks = mc.beta;
+      ms = mc.alpha;
+    } else {
+      ks = 1.0;
+      ms = 1.0;
+    }
+    const double lamS = ks * mc.lam * V * (1.0 / 20.0), muS = ks * mc.mu * V * (1.0 / 20.0);
+    const double mS = ms * mc.rho * V * (1.0 / 420.0);
+    double w[10][3], f[10][3];
+    if (MODE == kModeRhs) {
+      // stiffness acts on -u + beta v
+#pragma unroll
+      for (int k = 0; k < 10; ++k)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) w[k][i] = fma(mc.beta, vv[3 * nd[k] + i], -x[3 * nd[k] + i]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 10; ++k)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) w[k][i] = x[3 * nd[k] + i];
+    }
+    if (MODE != kModeM) {
+      stiffness_apply(w, g, lamS, muS, f);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 10; ++k)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) f[k][i] = 0.0;
+    }
+    if (MODE == kModeRhs) {
+      // mass acts on a + (4/dt + alpha) v
+      const double cv = 4.0 / m.dt + mc.alpha;
+#pragma unroll
+      for (int k = 0; k < 10; ++k)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) w[k][i] = fma(cv, vv[3 * nd[k] + i], aa[3 * nd[k] + i]);
+    }
+    if (MODE != kModeK) mass_apply(w, mS, f);
+#pragma unroll
+    for (int k = 0; k < 10; ++k)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        atomicAdd(y + 3 * nd[k] + i, f[k][i]);
+        if (MODE == kModeA) dot = fma(w[k][i], f[k][i], dot);
+      }
+  } else if (t < m.E + m.F && MODE != kModeK && MODE != kModeM) {
+    const int64_t fc = t - m.E;
+    const double tag = m.fgeo[5 * m.F + fc];
+    if (tag > 0.5) {
+      const double sc = (MODE == kModeA) ? 2.0 / m.dt : 1.0;
+      const double As = sc * m.fgeo[fc] / 180.0, Ad = sc * m.fgeo[m.F + fc] / 180.0;
+      const double n[3] = {m.fgeo[2 * m.F + fc], m.fgeo[3 * m.F + fc], m.fgeo[4 * m.F + fc]};
+      int64_t nd[6];
+      double z[6][3], xin[6][3];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        nd[k] = m.fnode[k * m.F + fc];
+        const double* src = (MODE == kModeRhs) ? vv : x;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) xin[k][i] = src[3 * nd[k] + i];
+        const double dn = n[0] * xin[k][0] + n[1] * xin[k][1] + n[2] * xin[k][2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) z[k][i] = fma(As, xin[k][i], Ad * dn * n[i]);
+      }
+      double yf[6][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double Zv = z[0][i] + z[1][i] + z[2][i];
+        const double Ze = z[3][i] + z[4][i] + z[5][i];
+        // vertex a: 7 z_a - Zv - 4 z_(opposite edge); edge e: 16 z_e + 16 Ze - 4 z_(opposite vertex)
+        yf[0][i] = 7.0 * z[0][i] - Zv - 4.0 * z[4][i];
+        yf[1][i] = 7.0 * z[1][i] - Zv - 4.0 * z[5][i];
+        yf[2][i] = 7.0 * z[2][i] - Zv - 4.0 * z[3][i];
+        yf[3][i] = 16.0 * (z[3][i] + Ze) - 4.0 * z[2][i];
+        yf[4][i] = 16.0 * (z[4][i] + Ze) - 4.0 * z[0][i];
+        yf[5][i] = 16.0 * (z[5][i] + Ze) - 4.0 * z[1][i];
+      }
+      if (MODE == kModeRhs && tag < 1.5) {
+        // base force 2 p C_base e_dir: int N_a dA = A/3 at edge nodes, 0 at vertices
+        const double nd_ = dir == 0 ? n[0] : (dir == 1 ? n[1] : n[2]);
+        const double fz[3] = {As * (dir == 0) + Ad * nd_ * n[0], As * (dir == 1) + Ad * nd_ * n[1],
+                              As * (dir == 2) + Ad * nd_ * n[2]};
+#pragma unroll
+        for (int k = 3; k < 6; ++k)
+#pragma unroll
+          for (int i = 0; i < 3; ++i) yf[k][i] += force * 60.0 * fz[i];
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          atomicAdd(y + 3 * nd[k] + i, yf[k][i]);
+          if (MODE == kModeA) dot = fma(xin[k][i], yf[k][i], dot);
+        }
+    }
+  }
+  if (MODE == kModeA && partials != nullptr) {
+    double vals[1] = {dot}, out[1];
+    if (last_block_reduce<1>(vals, partials, &cg->counter, out) && threadIdx.x == 0) cg->pq = out[0];
+  }
+}
+
+// ------------------------------------------------------------------------------
+// CG vector kernels (node-wise, 3 DOF per thread, grid-stride)
+// ------------------------------------------------------------------------------
+
+__device__ __forceinline__ void apply_dinv(const double* __restrict__ d, const double r[3], double z[3]) {
+  z[0] = d[0] * r[0] + d[3] * r[1] + d[4] * r[2];
+  z[1] = d[3] * r[0] + d[1] * r[1] + d[5] * r[2];
+  z[2] = d[4] * r[0] + d[5] * r[1] + d[2] * r[2];
+}
+
+__global__ void cg_init_kernel(int64_t N, const double* __restrict__ b, const double* __restrict__ v,
+                               const double* __restrict__ a, double dt, double* __restrict__ x,
+                               double* __restrict__ q, double* partials, CgScalars* cg) {
+  double bb = 0.0;
+  const double h = 0.5 * dt * dt;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double bi = b[i];
+    bb = fma(bi, bi, bb);
+    x[i] = fma(dt, v[i], h * a[i]);
+    q[i] = 0.0;
+  }
+  double vals[1] = {bb}, out[1];
+  if (last_block_reduce<1>(vals, partials, &cg->counter, out) && threadIdx.x == 0) {
+    cg->bb = out[0];
+    cg->iter = 0;
+    cg->status = 0;
+    cg->relres = 0.0;
+    cg->zero_rhs = (out[0] == 0.0);
+    cg->done = (out[0] == 0.0);
+    if (!isfinite(out[0])) {
+      cg->status = -5;
+      cg->done = 1;
+    }
+  }
+}
+
+__global__ void cg_residual_kernel(int64_t N, const double* __restrict__ b, double* __restrict__ q,
+                                   double* __restrict__ r, double* __restrict__ z,
+                                   double* __restrict__ p, const double* __restrict__ dinv,
+                                   double* partials, CgScalars* cg) {
+  if (((volatile CgScalars*)cg)->done) return;
+  double rr = 0.0, rz = 0.0;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    double rn[3], zn[3];
+    for (int i = 0; i < 3; ++i) {
+      rn[i] = b[3 * n + i] - q[3 * n + i];
+      q[3 * n + i] = 0.0;
+      r[3 * n + i] = rn[i];
+      rr = fma(rn[i], rn[i], rr);
+    }
+    apply_dinv(dinv + 6 * n, rn, zn);
+    for (int i = 0; i < 3; ++i) {
+      z[3 * n + i] = zn[i];
+      p[3 * n + i] = zn[i];
+      rz = fma(rn[i], zn[i], rz);
+    }
+  }
+  double vals[2] = {rr, rz}, out[2];
+  if (last_block_reduce<2>(vals, partials, &cg->counter, out) && threadIdx.x == 0) {
+    cg->rr = out[0];
+    cg->rz = out[1];
+    cg->relres = sqrt(out[0] / cg->bb);
+    if (!isfinite(out[0]) || !isfinite(out[1])) {
+      cg->status = -5;
+      cg->done = 1;
+    } else if (cg->relres <= cg->tol) {
+      cg->done = 1;
+    }
+  }
+}
+
+__global__ void cg_update_kernel(int64_t N, double* __restrict__ x, double* __restrict__ r,
+                                 double* __restrict__ z, const double* __restrict__ p,
+                                 double* __restrict__ q, const double* __restrict__ dinv,
+                                 double* partials, CgScalars* cg) {
+  if (((volatile CgScalars*)cg)->done) return;
+  const double alpha = ((volatile CgScalars*)cg)->rz / ((volatile CgScalars*)cg)->pq;
+  double rr = 0.0, rz = 0.0;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    double rn[3], zn[3];
+    for (int i = 0; i < 3; ++i) {
+      const int64_t k = 3 * n + i;
+      x[k] = fma(alpha, p[k], x[k]);
+      rn[i] = fma(-alpha, q[k], r[k]);
+      q[k] = 0.0;
+      r[k] = rn[i];
+      rr = fma(rn[i], rn[i], rr);
+    }
+    apply_dinv(dinv + 6 * n, rn, zn);
+    for (int i = 0; i < 3; ++i) {
+      z[3 * n + i] = zn[i];
+      rz = fma(rn[i], zn[i], rz);
+    }
+  }
+  double vals[2] = {rr, rz}, out[2];
+  if (last_block_reduce<2>(vals, partials, &cg->counter, out) && threadIdx.x == 0) {
+    cg->iter += 1;
+    cg->rr = out[0];
+    cg->relres = sqrt(out[0] / cg->bb);
+    if (!isfinite(out[0]) || !isfinite(out[1]) || !isfinite(alpha)) {
+      cg->status = -5;
+      cg->done = 1;
+    } else if (cg->relres <= cg->tol) {
+      cg->done = 1;
+    } else if (cg->iter >= cg->max_iter) {
+      cg->status = -4;
+      cg->done = 1;
+    } else {
+      cg->beta = out[1] / cg->rz;
+      cg->rz = out[1];
+    }
+  }
+}
+
+__global__ void cg_pupdate_kernel(int64_t N, const double* __restrict__ z, double* __restrict__ p,
+                                  const CgScalars* cg) {
+  if (((volatile const CgScalars*)cg)->done) return;
+  const double beta = ((volatile const CgScalars*)cg)->beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], z[i]);
+}
+
+__global__ void newmark_kernel(int64_t N, const double* __restrict__ x, double* __restrict__ u,
+                               double* __restrict__ v, double* __restrict__ a, double dt,
+                               const CgScalars* cg) {
+  const bool zero = cg->zero_rhs != 0;
+  const double c1 = 2.0 / dt, c2 = 4.0 / (dt * dt), c3 = 4.0 / dt;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double du = zero ? 0.0 : x[i];
+    const double vi = v[i];
+    u[i] += du;
+    v[i] = fma(c1, du, -vi);
+    a[i] = fma(c2, du, fma(-c3, vi, -a[i]));
+  }
+}
+
+__global__ void record_kernel(const double* __restrict__ v, const int32_t* __restrict__ rec_node,
+                              const double* __restrict__ rec_w, int n_rec, double* wave, int n_steps,
+                              int step) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * n_rec) return;
+  const int r = t / 3, c = t % 3;
+  double s = 0.0;
+  for (int k = 0; k < 6; ++k) s = fma(rec_w[6 * r + k], v[3 * (int64_t)rec_node[6 * r + k] + c], s);
+  wave[(int64_t)(3 * r + c) * n_steps + step] = s;
+}
+
+// ------------------------------------------------------------------------------
+// Launchers
+// ------------------------------------------------------------------------------
+
+int ebe_blocks(const ModelView& m) {
+  return (int)((m.E + m.F + kElemThreads - 1) / kElemThreads);
+}
+int node_blocks(int64_t n) {
+  int64_t b = (n + kNodeThreads - 1) / kNodeThreads;
+  return (int)(b < kMaxNodeBlocks ? (b < 1 ? 1 : b) : kMaxNodeBlocks);
+}
+
+void launch_geometry(const ModelView& m, const double* xyz, double px, double py, double* geo,
+                     int* err, cudaStream_t s) {
+  if (m.E == 0) return;
+  geometry_kernel<<<(unsigned)((m.E + 127) / 128), 128, 0, s>>>(m, xyz, px, py, geo, err);
+}
+void launch_face_geometry(const ModelView& m, const double* xyz, double px, double py,
+                          const int32_t* face_elem, const int32_t* face_tag, double* fgeo, int* err,
+                          cudaStream_t s) {
+  if (m.F == 0) return;
+  face_geometry_kernel<<<(unsigned)((m.F + 127) / 128), 128, 0, s>>>(m, xyz, px, py, face_elem,
+                                                                     face_tag, fgeo, err);
+}
+void launch_material(MatCoef* mat, const double* raw, int n_mat, double dt, double f1, double f2,
+                     cudaStream_t s) {
+  material_kernel<<<1, kMaxMat, 0, s>>>(mat, raw, n_mat, dt, f1, f2);
+}
+void launch_block_jacobi(const ModelView& m, double* dblk, double* dinv, int* err, cudaStream_t s) {
+  cudaMemsetAsync(dblk, 0, sizeof(double) * 6 * m.N, s);
+  if (m.E + m.F > 0)
+    diag_blocks_kernel<<<(unsigned)((m.E + m.F + 127) / 128), 128, 0, s>>>(m, dblk);
+  invert_blocks_kernel<<<node_blocks(m.N), kNodeThreads, 0, s>>>(m.N, dblk, dinv, err);
+}
+void launch_receivers(const ModelView& m, const double* xyz, double px, double py,
+                      const double* rec_xy, int n_rec, int32_t* rec_face, int32_t* rec_node,
+                      double* rec_w, int* err, cudaStream_t s) {
+  if (n_rec == 0) return;
+  cudaMemsetAsync(rec_face, 0x7f, sizeof(int32_t) * n_rec, s);
+  receiver_find_kernel<<<n_rec, 256, 0, s>>>(m, xyz, px, py, rec_xy, rec_face);
+  receiver_weights_kernel<<<(n_rec + 127) / 128, 128, 0, s>>>(m, xyz, px, py, rec_xy, n_rec, rec_face,
+                                                              rec_node, rec_w, err);
+}
+void launch_ebe(int mode, const ModelView& m, const double* x, const double* v, const double* a,
+                double* y, double force, int dir, double* partials, CgScalars* cg, cudaStream_t s) {
+  const int nb = ebe_blocks(m);
+  if (nb == 0) return;
+  switch (mode) {
+    case kModeA:
+      ebe_kernel<kModeA><<<nb, kElemThreads, 0, s>>>(m, x, v, a, y, force, dir, partials, cg);
+      break;
+    case kModeK:
+      ebe_kernel<kModeK><<<nb, kElemThreads, 0, s>>>(m, x, v, a, y, force, dir, nullptr, nullptr);
+      break;
+    case kModeM:
+      ebe_kernel<kModeM><<<nb, kElemThreads, 0, s>>>(m, x, v, a, y, force, dir, nullptr, nullptr);
+      break;
+    case kModeC:
+      ebe_kernel<kModeC><<<nb, kElemThreads, 0, s>>>(m, x, v, a, y, force, dir, nullptr, nullptr);
+      break;
+    default:
+      ebe_kernel<kModeRhs><<<nb, kElemThreads, 0, s>>>(m, x, v, a, y, force, dir, nullptr, nullptr);
+      break;
+  }
+}
+void launch_cg_init(const ModelView& m, const double* b, const double* v, const double* a,
+                    double* x, double* q, double* partials, CgScalars* cg, cudaStream_t s) {
+  cg_init_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, b, v, a, m.dt, x, q, partials, cg);
+}
+void launch_cg_residual(const ModelView& m, const double* b, double* q, double* r, double* z,
+                        double* p, const double* dinv, double* partials, CgScalars* cg,
+                        cudaStream_t s) {
+  cg_residual_kernel<<<node_blocks(m.N), kNodeThreads, 0, s>>>(m.N, b, q, r, z, p, dinv, partials, cg);
+}
+void launch_cg_update(const ModelView& m, double* x, double* r, double* z, const double* p,
+                      double* q, const double* dinv, double* partials, CgScalars* cg,
+                      cudaStream_t s) {
+  cg_update_kernel<<<node_blocks(m.N), kNodeThreads, 0, s>>>(m.N, x, r, z, p, q, dinv, partials, cg);
+}
+void launch_cg_pupdate(const ModelView& m, const double* z, double* p, const CgScalars* cg,
+                       cudaStream_t s) {
+  cg_pupdate_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, z, p, cg);
+}
+void launch_newmark(const ModelView& m, const double* x, double* u, double* v, double* a,
+                    const CgScalars* cg, cudaStream_t s) {
+  newmark_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, x, u, v, a, m.dt, cg);
+}
+void launch_record(const double* v, const int32_t* rec_node, const double* rec_w, int n_rec,
+                   double* wave, int n_steps, int step, cudaStream_t s) {
+  if (n_rec == 0) return;
+  record_kernel<<<(3 * n_rec + 127) / 128, 128, 0, s>>>(v, rec_node, rec_w, n_rec, wave, n_steps, step);
+}
+
+}  // namespace gsw

@@ -1,0 +1,302 @@
+"""Python binding of the GPU library's C ABI (``include/gsw.h``).
+
+Argument marshalling only: every step of the analysis runs in the library's
+CUDA kernels.  PyTorch supplies device memory (its caching allocator backs
+the library's allocations) and the CUDA stream.  The library must be built
+(``paper_2404_17754_gb300.build.build()``); importing this module without it
+raises, and there is no CPU fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgsw.so")
+
+OK, E_INVALID, E_CUDA, E_NOMEM, E_NOCONV, E_NAN, E_TIMEOUT, E_STATE = 0, -1, -2, -3, -4, -5, -6, -7
+PREC_FP64, PREC_FP32, PREC_FP16 = 0, 1, 2
+_STATUS = {E_INVALID: "GSW_E_INVALID", E_CUDA: "GSW_E_CUDA", E_NOMEM: "GSW_E_NOMEM",
+           E_NOCONV: "GSW_E_NOCONV", E_NAN: "GSW_E_NAN", E_TIMEOUT: "GSW_E_TIMEOUT",
+           E_STATE: "GSW_E_STATE"}
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+_lp = C.POINTER(C.c_int64)
+_ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class SolverOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("precision", C.c_int32),
+                ("inner_iters", C.c_int32), ("check_every", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("steps_done", C.c_int64), ("cg_iters_total", C.c_int64), ("cg_iters_last", C.c_int32),
+                ("cg_iters_max", C.c_int32), ("relres_last", C.c_double), ("inner_iters_total", C.c_int64),
+                ("kernel_launches", C.c_int64)]
+
+
+class GswError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, str(status)), msg))
+        self.status = status
+
+
+_lib = None
+
+# entry point -> (restype, argtypes)
+SIGNATURES = {
+    "gsw_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p]),
+    "gsw_destroy": (None, [C.c_void_p]),
+    "gsw_last_error": (C.c_char_p, [C.c_void_p]),
+    "gsw_set_allocator": (C.c_int, [C.c_void_p, _ALLOC, _FREE, C.c_void_p]),
+    "gsw_model_upload": (C.c_int, [C.c_void_p, C.c_int64, _dp, C.c_int64, _ip, _ip, C.c_int32, _dp,
+                                   C.c_int64, _ip, _ip, _ip, _dp, C.c_int32, _dp, _ip]),
+    "gsw_model_free": (C.c_int, [C.c_void_p, C.c_int32]),
+    "gsw_model_info": (C.c_int, [C.c_void_p, C.c_int32, _lp]),
+    "gsw_set_time": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_int32, C.c_double, C.c_double]),
+    "gsw_set_input": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, _dp, C.c_int32]),
+    "gsw_set_solver": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(SolverOpts)]),
+    "gsw_reset": (C.c_int, [C.c_void_p, C.c_int32]),
+    "gsw_step": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "gsw_run": (C.c_int, [C.c_void_p, _ip, C.c_int32]),
+    "gsw_read_waveforms": (C.c_int, [C.c_void_p, C.c_int32, _dp]),
+    "gsw_read_waveform_steps": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, _dp]),
+    "gsw_timing": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, _dp, _lp]),
+    "gsw_stats_get": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Stats)]),
+    "gsw_get_state": (C.c_int, [C.c_void_p, C.c_int32, _dp, _dp, _dp, _lp]),
+    "gsw_set_state": (C.c_int, [C.c_void_p, C.c_int32, _dp, _dp, _dp, C.c_int64]),
+    "gsw_apply": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
+    "gsw_read_preconditioner": (C.c_int, [C.c_void_p, C.c_int32, _dp]),
+    "gsw_read_receivers": (C.c_int, [C.c_void_p, C.c_int32, _ip, _dp]),
+    "gsw_misfit": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, _dp, _dp, C.c_int32, C.c_int32, C.c_double,
+                             _dp, _dp]),
+}
+
+
+def load(path=LIB_PATH):
+    """Load libgsw.so and declare its signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libgsw.so is not built (%s); run paper_2404_17754_gb300.build.build()" % path)
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_dp)
+
+
+def _i(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(_ip)
+
+
+class Context:
+    """A library context bound to one GPU and one CUDA stream.
+
+    ``stream``: a ``torch.cuda.Stream`` (default: torch's current stream on
+    ``device``).  ``torch_alloc``: back device allocations by torch's caching
+    allocator.
+    """
+
+    def __init__(self, device=0, stream=None, torch_alloc=True):
+        import torch
+
+        self.lib = load()
+        self.device = device
+        self._torch = torch
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = C.c_void_p()
+        st = self.lib.gsw_create(C.byref(h), device, C.c_void_p(stream.cuda_stream))
+        if st != OK:
+            raise GswError(st, "gsw_create(device=%d)" % device)
+        self.h = h
+        self._cbs = None
+        if torch_alloc:
+            dev = device
+
+            def _alloc(nbytes, strm, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, strm)
+                except Exception:  # out of memory: report NULL to the library
+                    return None
+
+            def _free(ptr, strm, user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._cbs = (_ALLOC(_alloc), _FREE(_free))
+            self._check(self.lib.gsw_set_allocator(self.h, self._cbs[0], self._cbs[1], None))
+
+    def _check(self, st):
+        if st != OK:
+            raise GswError(st, self.lib.gsw_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gsw_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def upload(self, mesh, mat, rec_xy):
+        """Upload a mesh dict (``synth.mesh.layered_box`` layout); returns a :class:`Model`."""
+        xyz, pxyz = _d(mesh["xyz"])
+        conn, pconn = _i(mesh["conn"])
+        em, pem = _i(mesh["elem_mat"])
+        mt, pmt = _d(mat)
+        fc, pfc = _i(mesh["faces"])
+        fe, pfe = _i(mesh["face_elem"])
+        ft, pft = _i(mesh["face_tag"])
+        per, pper = _d(mesh.get("period", np.zeros(2)))
+        rc, prc = _d(np.asarray(rec_xy, dtype=np.float64).reshape(-1, 2))
+        mid = C.c_int32()
+        self._check(self.lib.gsw_model_upload(self.h, xyz.shape[0], pxyz, conn.shape[0], pconn, pem, mt.shape[0],
+                                              pmt, fc.shape[0], pfc, pfe, pft, pper, rc.shape[0], prc,
+                                              C.byref(mid)))
+        return Model(self, mid.value, xyz.shape[0], rc.shape[0])
+
+    def misfit(self, G, obs, stride, n_shifts, tau=1e-10):
+        """(ERR, c [3, n_shifts]) of Eq. (2) for Green's functions G and observations obs."""
+        G, pG = _d(G)
+        obs, pO = _d(obs)
+        n_rec, n_t = obs.shape[0], obs.shape[2]
+        assert G.shape == (n_rec, 3, 3, n_t)
+        err = C.c_double()
+        c = np.zeros((3, n_shifts))
+        self._check(self.lib.gsw_misfit(self.h, n_rec, n_t, pG, pO, stride, n_shifts, tau, C.byref(err),
+                                        c.ctypes.data_as(_dp)))
+        return err.value, c
+
+
+class Model:
+    """One uploaded ground model (handle into a :class:`Context`)."""
+
+    def __init__(self, ctx, mid, n_nodes, n_rec):
+        self.ctx, self.id, self.n_nodes, self.n_rec = ctx, mid, n_nodes, n_rec
+        self.n_steps = 0
+
+    def _c(self, st):
+        self.ctx._check(st)
+
+    def info(self):
+        out = np.zeros(5, dtype=np.int64)
+        self._c(self.ctx.lib.gsw_model_info(self.ctx.h, self.id, out.ctypes.data_as(_lp)))
+        return dict(n_nodes=int(out[0]), n_elem=int(out[1]), n_faces=int(out[2]), n_rec=int(out[3]),
+                    device_bytes=int(out[4]))
+
+    def set_time(self, dt, n_steps, band):
+        self._c(self.ctx.lib.gsw_set_time(self.ctx.h, self.id, float(dt), int(n_steps), float(band[0]),
+                                          float(band[1])))
+        self.n_steps = int(n_steps)
+
+    def set_input(self, direction, p):
+        p, pp = _d(p)
+        self._c(self.ctx.lib.gsw_set_input(self.ctx.h, self.id, int(direction), pp, p.shape[0]))
+
+    def set_solver(self, tol=1e-8, max_iter=10000, precision=PREC_FP64, inner_iters=20, check_every=8):
+        o = SolverOpts(tol, max_iter, precision, inner_iters, check_every)
+        self._c(self.ctx.lib.gsw_set_solver(self.ctx.h, self.id, C.byref(o)))
+
+    def reset(self):
+        self._c(self.ctx.lib.gsw_reset(self.ctx.h, self.id))
+
+    def step(self, n=1):
+        self._c(self.ctx.lib.gsw_step(self.ctx.h, self.id, int(n)))
+
+    def run(self):
+        ids = np.array([self.id], dtype=np.int32)
+        self._c(self.ctx.lib.gsw_run(self.ctx.h, ids.ctypes.data_as(_ip), 1))
+
+    def waveforms(self):
+        out = np.zeros((self.n_rec, 3, self.n_steps))
+        self._c(self.ctx.lib.gsw_read_waveforms(self.ctx.h, self.id, out.ctypes.data_as(_dp)))
+        return out
+
+    def read_waveforms_into(self, out):
+        """Read the receiver history into a caller-owned float64 host array."""
+        self._c(self.ctx.lib.gsw_read_waveforms(self.ctx.h, self.id, out.ctypes.data_as(_dp)))
+        return out
+
+    def read_steps_into(self, step0, out):
+        """Receiver velocities of steps step0 .. step0 + out.shape[2] - 1 into a host array."""
+        self._c(self.ctx.lib.gsw_read_waveform_steps(self.ctx.h, self.id, int(step0), int(out.shape[2]),
+                                                     out.ctypes.data_as(_dp)))
+        return out
+
+    def timing(self, enable=None):
+        """Start (True) / stop (False) / query (None) EBE launch timing; returns (ms, launches)."""
+        ms = C.c_double()
+        n = C.c_int64()
+        flag = -1 if enable is None else int(bool(enable))
+        self._c(self.ctx.lib.gsw_timing(self.ctx.h, self.id, flag, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def stats(self):
+        s = Stats()
+        self._c(self.ctx.lib.gsw_stats_get(self.ctx.h, self.id, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def get_state(self):
+        u, v, a = (np.zeros((self.n_nodes, 3)) for _ in range(3))
+        step = C.c_int64()
+        self._c(self.ctx.lib.gsw_get_state(self.ctx.h, self.id, u.ctypes.data_as(_dp), v.ctypes.data_as(_dp),
+                                           a.ctypes.data_as(_dp), C.byref(step)))
+        return u, v, a, step.value
+
+    def set_state(self, u, v, a, step):
+        u, pu = _d(u)
+        v, pv = _d(v)
+        a, pa = _d(a)
+        self._c(self.ctx.lib.gsw_set_state(self.ctx.h, self.id, pu, pv, pa, int(step)))
+
+    def apply(self, which, x):
+        """y = A x (0), K x (1), M x (2) or C x (3) for a CUDA float64 tensor x [n_nodes, 3]."""
+        torch = self.ctx._torch
+        assert x.is_cuda and x.dtype == torch.float64 and x.is_contiguous() and x.numel() == 3 * self.n_nodes
+        y = torch.empty_like(x)
+        self._c(self.ctx.lib.gsw_apply(self.ctx.h, self.id, int(which), C.c_void_p(x.data_ptr()),
+                                       C.c_void_p(y.data_ptr())))
+        return y
+
+    def preconditioner(self):
+        out = np.zeros((self.n_nodes, 6))
+        self._c(self.ctx.lib.gsw_read_preconditioner(self.ctx.h, self.id, out.ctypes.data_as(_dp)))
+        return out
+
+    def receivers(self):
+        nodes = np.zeros((self.n_rec, 6), dtype=np.int32)
+        w = np.zeros((self.n_rec, 6))
+        self._c(self.ctx.lib.gsw_read_receivers(self.ctx.h, self.id, nodes.ctypes.data_as(_ip),
+                                                w.ctypes.data_as(_dp)))
+        return nodes, w
+
+    def free(self):
+        self._c(self.ctx.lib.gsw_model_free(self.ctx.h, self.id))
+
+
+def analysis(ctx, cfg, tol=1e-8, n_steps=None, **solver):
+    """Upload a ``synth.configs`` workload, run it, return (waveforms, stats, model)."""
+    n = cfg["n_steps"] if n_steps is None else n_steps
+    m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
+    m.set_time(cfg["dt"], n, cfg["band"])
+    m.set_input(cfg["dir"], np.asarray(cfg["p"][:n]))
+    m.set_solver(tol=tol, **solver)
+    m.run()
+    return m.waveforms(), m.stats(), m
