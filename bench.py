@@ -140,9 +140,30 @@ print(json.dumps(dict(dof=n, steps=steps, seconds=el, iters=iters)))
     return d, None
 
 
-def traffic_from_profile(kernel_file):
+def inner_bytes(n_nodes, n_elem, n_faces, half):
+    """Algorithmic bytes of one inner (reduced-precision) A d launch: d read once,
+    w written once (plus its zeroed read), per element local connectivity (20 B),
+    gradients (9 values), FP32 volume, material id and the block's node-list share (~3 ids)."""
+    sv = 2 if half else 4
+    return n_nodes * 3 * (sv + 4 + 4) + n_elem * (20 + 9 * sv + 4 + 4 + 12) + n_faces * (24 + 24)
+
+
+CSRC = os.path.join(ROOT, "paper_2404_17754_gb300", "csrc")
+FP64_SOURCES = ["gsw_kernels.cu", "gsw_ebe.cuh", "gsw_reduce.cuh", "gsw_internal.cuh"]
+INNER_SOURCES = ["gsw_mixed.cu", "gsw_ebe.cuh", "gsw_reduce.cuh", "gsw_internal.cuh"]
+
+
+def source_hash(files):
+    """sha256 over the kernel's source files (the profile is void once they change)."""
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(CSRC, f), "rb").read())
+    return h.hexdigest()
+
+
+def traffic_from_profile(files, summary):
     """Per-launch DRAM bytes from the committed ncu summary, if the kernel source is unchanged."""
-    path = os.path.join(ROOT, "profiles", "ebe_fp64_realistic.md")
+    path = os.path.join(ROOT, "profiles", summary)
     try:
         text = open(path).read()
     except OSError:
@@ -151,8 +172,7 @@ def traffic_from_profile(kernel_file):
     m2 = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
     if not (m1 and m2):
         return None
-    sha = hashlib.sha256(open(kernel_file, "rb").read()).hexdigest()
-    return float(m1.group(1)) if sha.startswith(m2.group(1)) else None
+    return float(m1.group(1)) if source_hash(files).startswith(m2.group(1)) else None
 
 
 def run_reference(args, rank):
@@ -183,6 +203,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--workload", default="realistic", choices=["realistic", "two-layer"])
+    ap.add_argument("--precision", default="fp16", choices=["fp64", "fp32", "fp16"])
+    ap.add_argument("--inner", type=int, default=20, help="inner preconditioner iterations (mixed modes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -225,7 +247,8 @@ def main():
     m = ctx.upload(mesh, cfg["mat"], cfg["rec_xy"])
     m.set_time(cfg["dt"], n_total + 1, cfg["band"])
     m.set_input(cfg["dir"], cfg["p"])
-    m.set_solver(tol=args.tol)
+    prec = {"fp64": 0, "fp32": 1, "fp16": 2}[args.precision]
+    m.set_solver(tol=args.tol, precision=prec, inner_iters=args.inner)
     n_nodes, n_elem, n_faces = mesh["xyz"].shape[0], mesh["conn"].shape[0], mesh["faces"].shape[0]
     dof = 3 * n_nodes
 
@@ -233,6 +256,7 @@ def main():
     m.step(args.warmup)
     launches0 = m.stats()["kernel_launches"]
     it0 = m.stats()["cg_iters_total"]
+    inner0 = m.stats()["inner_iters_total"]
     m.timing(True)
     clocks = ClockSampler(local)
     clocks.start()
@@ -247,7 +271,9 @@ def main():
     if dist is not None:
         dist.barrier()
     clk = clocks.stop()
-    ebe_ms, ebe_n = m.timing(False)
+    tim = m.timing(False)
+    ebe_ms, ebe_n = tim["fp64"]
+    lo_ms, lo_n = tim["inner"]
     st = m.stats()
     t = e0.elapsed_time(e1) / 1e3
     t_max = t
@@ -289,21 +315,35 @@ def main():
         return
 
     pk = peaks()
+    n_abs = int((mesh["face_tag"] > 0).sum())
     per_launch_s = (ebe_ms / 1e3) / max(1, ebe_n)
-    flops = EBE_FLOPS_PER_ELEM * n_elem + EBE_FLOPS_PER_FACE * int((mesh["face_tag"] > 0).sum())
+    flops = EBE_FLOPS_PER_ELEM * n_elem + EBE_FLOPS_PER_FACE * n_abs
     achieved_tf = flops / per_launch_s / 1e12 if ebe_n else None
     nbytes = ebe_bytes(n_nodes, n_elem, n_faces)
-    kfile = os.path.join(ROOT, "paper_2404_17754_gb300", "csrc", "gsw_kernels.cu")
-    roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": (achieved_tf / FP64_PEAK_TFLOPS) if achieved_tf else None,
-            "traffic": traffic_from_profile(kfile),
-            "kernel": "ebe_kernel<A> (FP64 element-by-element A p)",
-            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FP64 pipe; a DFMA probe "
-                           "measured 1.20 TFLOP/s at 2.0 GHz)",
-            "flops_per_launch": flops, "launch_ms": per_launch_s * 1e3, "launches_timed": ebe_n,
-            "hbm_secondary": {"algorithmic_bytes": nbytes,
-                              "achieved_gbs": nbytes / per_launch_s / 1e9 if ebe_n else None,
-                              "peak_gbs": pk.get("hbm_gbs"), "note": "of measured HBM copy bandwidth"}}
+    fp64_roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                 "frac": (achieved_tf / FP64_PEAK_TFLOPS) if achieved_tf else None,
+                 "traffic": traffic_from_profile(FP64_SOURCES, "ebe_fp64_realistic.md"),
+                 "kernel": "ebe_kernel<0> (FP64 element-by-element A p)",
+                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FP64 pipe; a DFMA probe "
+                                "measured 1.20 TFLOP/s at 2.0 GHz)",
+                 "flops_per_launch": flops, "launch_ms": per_launch_s * 1e3, "launches_timed": ebe_n,
+                 "time_share": ebe_ms / (1e3 * t), "algorithmic_bytes": nbytes}
+    inner_roof = None
+    if lo_n:
+        lo_launch_s = (lo_ms / 1e3) / lo_n
+        lo_bytes = inner_bytes(n_nodes, n_elem, n_faces, args.precision == "fp16")
+        inner_roof = {"bound": "hbm", "achieved": lo_bytes / lo_launch_s / 1e9, "peak": pk.get("hbm_gbs"),
+                      "unit": "GB/s", "frac": lo_bytes / lo_launch_s / 1e9 / pk.get("hbm_gbs"),
+                      "traffic": traffic_from_profile(INNER_SOURCES, "ebe_inner_%s_realistic.md" % args.precision),
+                      "kernel": "ebe_lo_kernel (%s inner element-by-element A d)" % args.precision,
+                      "peak_source": "of measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                      "algorithmic_bytes": lo_bytes, "launch_ms": lo_launch_s * 1e3, "launches_timed": lo_n,
+                      "time_share": lo_ms / (1e3 * t)}
+    roof = fp64_roof
+    if inner_roof is not None and lo_ms > ebe_ms:
+        roof = dict(inner_roof, secondary=fp64_roof)
+    elif inner_roof is not None:
+        roof = dict(fp64_roof, secondary=inner_roof)
     cpu = None
     if not args.no_cpu_baseline:
         d, err = cpu_oracle_sample()
@@ -317,10 +357,14 @@ def main():
     out = {
         "metric": "DOF*steps/s", "value": value, "unit": "DOF*steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+%s" % {"fp32": "f32", "fp16": "f16/f32"}[args.precision],
+        "data": "synthetic",
         "config": {"workload": cfg["name"] if args.workload == "realistic" else "two-layer 100x100x50 m",
-                   "dof": dof, "elements": n_elem, "dt": cfg["dt"], "tol": args.tol, "precision": "fp64",
-                   "solver": "block-Jacobi PCG", "parallelism": "independent directional analyses, 1 per GPU",
+                   "dof": dof, "elements": n_elem, "dt": cfg["dt"], "tol": args.tol, "precision": args.precision,
+                   "solver": "block-Jacobi PCG" if args.precision == "fp64" else
+                             "flexible CG (FP64) + %d-iteration %s block-Jacobi PCG preconditioner" % (
+                                 args.inner, args.precision),
+                   "inner_iters_per_step": (st["inner_iters_total"] - inner0) / args.steps, "parallelism": "independent directional analyses, 1 per GPU",
                    "cg_iters_per_step": iters / args.steps,
                    "l2": "inputs larger than L2 (FP64 working set %.1f GB)" % (
                        (14 * 3 * n_nodes * 8 + n_elem * 124) / 1e9),

@@ -77,7 +77,7 @@ typedef struct {
 /* ---- context ------------------------------------------------------------ */
 
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream`
- * (a cudaStream_t; NULL = the context creates its own non-blocking stream). */
+ * (a cudaStream_t; NULL = the CUDA default stream, as in the runtime API). */
 gsw_status gsw_create(gsw_ctx **out, int device, void *cuda_stream);
 void gsw_destroy(gsw_ctx *ctx);
 const char *gsw_last_error(const gsw_ctx *ctx);
@@ -162,17 +162,22 @@ gsw_status gsw_get_state(gsw_ctx *ctx, int32_t model_id, double *u, double *v, d
 gsw_status gsw_set_state(gsw_ctx *ctx, int32_t model_id, const double *u, const double *v,
                          const double *a, int64_t step);
 
-/* Kernel timing: enable = 1 clears the counters and brackets every CG
- * operator launch (the element-by-element A p product) of subsequent steps
- * with CUDA events on the context's stream; enable = 0 stops.  *ebe_ms and
- * *ebe_launches (either may be NULL) receive the summed device time and the
- * number of timed launches so far. */
-gsw_status gsw_timing(gsw_ctx *ctx, int32_t model_id, int32_t enable, double *ebe_ms,
-                      int64_t *ebe_launches);
+/* Kernel timing: enable = 1 clears the counters and brackets every operator
+ * launch of subsequent steps with CUDA events on the context's stream;
+ * enable = 0 stops; any other value only reads.  ms[2] and launches[2]
+ * (either may be NULL) receive the summed device time and the number of
+ * timed launches of [0] the FP64 element-by-element A p product of the CG
+ * iteration and [1] the reduced-precision element-by-element product of the
+ * inner preconditioner (mixed modes). */
+gsw_status gsw_timing(gsw_ctx *ctx, int32_t model_id, int32_t enable, double *ms,
+                      int64_t *launches);
 
 /* Operator application on device vectors [n_nodes][3] (diagnostics, tests):
  *  which = 0: y = A x, A = K + (2/dt) C + (4/dt^2) M (the CG operator);
- *  which = 1: y = K x;  which = 2: y = M x;  which = 3: y = C x.
+ *  which = 1: y = K x;  which = 2: y = M x;  which = 3: y = C x;
+ *  which = 4: y = A x by the reduced-precision inner operator of the model's
+ *  current mixed precision mode (x rounded to the inner storage type,
+ *  FP32 arithmetic and accumulation); GSW_E_STATE in FP64 mode.
  * x_dev, y_dev device pointers; y is overwritten. */
 gsw_status gsw_apply(gsw_ctx *ctx, int32_t model_id, int32_t which, const double *x_dev,
                      double *y_dev);

@@ -13,6 +13,7 @@
 #include "gsw.h"
 #include "gsw_internal.cuh"
 #include "gsw_misfit.cuh"
+#include <cuda_fp16.h>
 
 using namespace gsw;
 
@@ -57,12 +58,31 @@ struct Model {
   int64_t step = 0;
   bool failed = false;
   gsw_stats stats = {};
+  // reduced-precision inner solve (mixed modes)
+  bool lo_ready = false;
+  int lo_half = 0;  // 1: FP16 geometry and search direction
+  int n_blk = 0, max_local = 0;
+  int32_t* blk_ptr = nullptr;
+  int32_t* blk_nodes = nullptr;
+  uint16_t* lconn = nullptr;
+  void* geo_lo = nullptr;
+  float* fgeo32 = nullptr;
+  float* vol32 = nullptr;
+  float* dinv32 = nullptr;
+  float *y32 = nullptr, *s32 = nullptr, *t32 = nullptr, *w32 = nullptr;
+  void* d_lo = nullptr;
+  InnerScalars* isc = nullptr;
+  LoView<float> lo_f;
+  LoView<__half> lo_h;
   // kernel timing
   bool timing = false;
   std::vector<cudaEvent_t> ev;
   int ev_used = 0;
   double ebe_ms = 0.0;
   int64_t ebe_count = 0;
+  double lo_ms = 0.0;
+  int64_t lo_count = 0;
+  std::vector<cudaEvent_t> ev_lo;
 
   ModelView view() const {
     ModelView m;
@@ -85,7 +105,6 @@ struct Model {
 struct gsw_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
-  bool own_stream = false;
   std::string err;
   void* (*alloc)(size_t, void*, void*) = nullptr;
   void (*free_)(void*, void*, void*) = nullptr;
@@ -166,6 +185,7 @@ gsw_status alloc_into(gsw_ctx* ctx, Model* m, T** out, size_t count) {
 
 void free_model(gsw_ctx* ctx, Model* m) {
   for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : m->ev_lo) cudaEventDestroy(e);
   for (void* p : m->allocs) dev_free(ctx, p);
   m->allocs.clear();
   if (m->cg_host) cudaFreeHost(m->cg_host);
@@ -215,7 +235,7 @@ gsw_status model_state_alloc(gsw_ctx* ctx, Model* m) {
   TRY(alloc_into(ctx, m, &m->dblk, 6 * (size_t)m->N));
   TRY(alloc_into(ctx, m, &m->dinv, 6 * (size_t)m->N));
   ModelView mv = m->view();
-  size_t np = (size_t)ebe_blocks(mv);
+  size_t np = (size_t)ebe_blocks(mv) + 2;
   if (np < 2 * (size_t)kMaxNodeBlocks) np = 2 * (size_t)kMaxNodeBlocks;
   TRY(alloc_into(ctx, m, &m->partials, np));
   TRY(alloc_into(ctx, m, &m->cg, 1));
@@ -314,6 +334,184 @@ gsw_status step_fp64(gsw_ctx* ctx, Model* m) {
   return GSW_OK;
 }
 
+// Element blocks with local numbering and the reduced-precision copies of the
+// operator data and preconditioner (built once per model; the conversion is
+// redone when dt changes).
+gsw_status build_lo(gsw_ctx* ctx, Model* m, int half) {
+  cudaStream_t s = ctx->stream;
+  ModelView mv = m->view();
+  if (!m->lo_ready) {
+    m->n_blk = (int)((m->E + kElemThreads - 1) / kElemThreads);
+    int32_t* counts = nullptr;
+    TRY(alloc_into(ctx, m, &counts, (size_t)m->n_blk));
+    launch_block_count(mv, m->n_blk, counts, s);
+    std::vector<int32_t> h((size_t)m->n_blk), ptr((size_t)m->n_blk + 1);
+    CK(cudaMemcpyAsync(h.data(), counts, sizeof(int32_t) * m->n_blk, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ptr[0] = 0;
+    int mx = 0;
+    for (int b = 0; b < m->n_blk; ++b) {
+      ptr[b + 1] = ptr[b] + h[b];
+      if (h[b] > mx) mx = h[b];
+    }
+    m->max_local = mx;
+    const int total = ptr[m->n_blk];
+    int32_t* refcount = nullptr;
+    TRY(alloc_into(ctx, m, &m->blk_ptr, (size_t)m->n_blk + 1));
+    TRY(alloc_into(ctx, m, &m->blk_nodes, (size_t)total));
+    TRY(alloc_into(ctx, m, &m->lconn, 10 * (size_t)m->E));
+    TRY(alloc_into(ctx, m, &refcount, (size_t)m->N));
+    CK(cudaMemcpyAsync(m->blk_ptr, ptr.data(), sizeof(int32_t) * (m->n_blk + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(refcount, 0, sizeof(int32_t) * m->N, s));
+    BlockView bv = {m->n_blk, m->max_local, m->blk_ptr, m->blk_nodes, m->lconn};
+    launch_block_fill(mv, bv, m->blk_nodes, m->lconn, refcount, s);
+    launch_block_mark(mv, bv, m->blk_nodes, refcount, total, s);
+    CK(cudaGetLastError());
+    const size_t n3 = 3 * (size_t)m->N;
+    TRY(alloc_into(ctx, m, &m->fgeo32, 6 * (size_t)(m->F > 0 ? m->F : 1)));
+    TRY(alloc_into(ctx, m, &m->vol32, (size_t)m->E));
+    TRY(alloc_into(ctx, m, &m->dinv32, 6 * (size_t)m->N));
+    TRY(alloc_into(ctx, m, &m->y32, n3));
+    TRY(alloc_into(ctx, m, &m->s32, n3));
+    TRY(alloc_into(ctx, m, &m->t32, n3));
+    TRY(alloc_into(ctx, m, &m->w32, n3));
+    TRY(alloc_into(ctx, m, &m->isc, 1));
+    CK(cudaMemsetAsync(m->isc, 0, sizeof(InnerScalars), s));
+    m->lo_ready = true;
+    m->geo_lo = nullptr;
+    m->d_lo = nullptr;
+  }
+  if (m->geo_lo == nullptr || m->lo_half != half) {
+    // (re)allocate the precision-dependent buffers; the old ones stay owned by the model
+    m->geo_lo = dev_alloc(ctx, m, (half ? sizeof(__half) : sizeof(float)) * 9 * (size_t)m->E);
+    m->d_lo = dev_alloc(ctx, m, (half ? sizeof(__half) : sizeof(float)) * 3 * (size_t)m->N);
+    if (!m->geo_lo || !m->d_lo) return fail(ctx, GSW_E_NOMEM, "device allocation failed (inner solve)");
+    m->lo_half = half;
+  }
+  launch_lo_convert(mv, half, m->geo_lo, m->vol32, m->fgeo32, m->dinv, m->dinv32, m->partials, m->isc, s);
+  CK(cudaGetLastError());
+  BlockView bv = {m->n_blk, m->max_local, m->blk_ptr, m->blk_nodes, m->lconn};
+  m->lo_f = LoView<float>{m->N, m->E, m->F, bv, (const float*)m->geo_lo, m->vol32, m->emat, m->mat, m->fnode,
+                          m->fgeo32, m->dt};
+  m->lo_h = LoView<__half>{m->N, m->E, m->F, bv, (const __half*)m->geo_lo, m->vol32, m->emat, m->mat, m->fnode,
+                           m->fgeo32, m->dt};
+  return GSW_OK;
+}
+
+// Inner preconditioner: inner_iters block-Jacobi PCG iterations in reduced
+// precision on the scaled outer residual; result in y32 (scaled).
+int64_t inner_solve(Model* m, cudaStream_t s) {
+  const int half = m->lo_half;
+  const void* view = half ? (const void*)&m->lo_h : (const void*)&m->lo_f;
+  launch_inner_init(m->N, m->r, m->dinv32, m->s32, m->y32, m->t32, m->d_lo, half, m->w32, m->partials, m->isc,
+                    m->cg, s);
+  const int it = m->opts.inner_iters > 0 ? m->opts.inner_iters : 1;
+  const bool timed = m->timing && (int)m->ev_lo.size() >= 2 * it;
+  for (int k = 0; k < it; ++k) {
+    if (timed) cudaEventRecord(m->ev_lo[2 * k], s);
+    launch_ebe_lo(half, half, view, m->d_lo, m->w32, m->partials, m->isc, s);
+    if (timed) cudaEventRecord(m->ev_lo[2 * k + 1], s);
+    launch_inner_update(m->N, m->y32, m->s32, m->t32, m->d_lo, half, m->w32, m->dinv32, m->partials, m->isc, s);
+    if (k + 1 < it) launch_inner_dupdate(m->N, m->t32, m->d_lo, half, m->isc, s);
+  }
+  m->stats.inner_iters_total += it;
+  if (timed) {
+    cudaEventSynchronize(m->ev_lo[2 * it - 1]);
+    for (int k = 0; k < it; ++k) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, m->ev_lo[2 * k], m->ev_lo[2 * k + 1]) == cudaSuccess) m->lo_ms += ms;
+    }
+    m->lo_count += it;
+  }
+  return 1 + 3 * (int64_t)it - 1;
+}
+
+// One Newmark step with flexible CG (FP64) preconditioned by the inner solve.
+gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
+  cudaStream_t s = ctx->stream;
+  ModelView mv = m->view();
+  const double force = 2.0 * m->input[(size_t)m->step];
+  CK(cudaMemsetAsync(m->b, 0, sizeof(double) * 3 * (size_t)m->N, s));
+  launch_ebe(kModeRhs, mv, m->u, m->v, m->a, m->b, force, m->dir, nullptr, nullptr, s);
+  CgScalars init = {};
+  init.tol = m->opts.tol;
+  init.max_iter = m->opts.max_iter;
+  CK(cudaMemcpyAsync(m->cg, &init, sizeof(CgScalars), cudaMemcpyHostToDevice, s));
+  launch_cg_init(mv, m->b, m->v, m->a, m->x, m->q, m->partials, m->cg, s);
+  launch_ebe(kModeA, mv, m->x, nullptr, nullptr, m->q, 0.0, 0, nullptr, m->cg, s);
+  launch_fcg_residual(mv, m->b, m->q, m->r, m->partials, m->cg, s);
+  int64_t launches = 5;
+  if (m->timing && (int)m->ev_lo.size() < 2 * m->opts.inner_iters) {
+    for (int i = (int)m->ev_lo.size(); i < 2 * m->opts.inner_iters; ++i) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      m->ev_lo.push_back(e);
+    }
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(m->cg_host, m->cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (!m->cg_host->done) {
+    launches += inner_solve(m, s);
+    launch_fcg_first(mv, m->y32, m->r, m->z, m->p, m->partials, m->cg, m->isc, s);
+    launches += 1;
+    if (m->timing && m->ev.size() < 2) {
+      for (int i = (int)m->ev.size(); i < 2; ++i) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        m->ev.push_back(e);
+      }
+    }
+    if (m->timing && (int)m->ev_lo.size() < 2 * m->opts.inner_iters) {
+      for (int i = (int)m->ev_lo.size(); i < 2 * m->opts.inner_iters; ++i) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        m->ev_lo.push_back(e);
+      }
+    }
+    for (;;) {
+      if (m->timing) CK(cudaEventRecord(m->ev[0], s));
+      launch_ebe(kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, s);
+      if (m->timing) CK(cudaEventRecord(m->ev[1], s));
+      launch_fcg_update(mv, m->x, m->r, m->p, m->q, m->partials, m->cg, s);
+      launches += 2;
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(m->cg_host, m->cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (m->timing) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, m->ev[0], m->ev[1]));
+        m->ebe_ms += ms;
+        m->ebe_count += 1;
+      }
+      if (m->cg_host->done) break;
+      launches += inner_solve(m, s);
+      launch_fcg_zbeta(mv, m->y32, m->r, m->q, m->z, m->partials, m->cg, m->isc, s);
+      launch_fcg_pupdate(mv, m->z, m->p, m->q, m->cg, s);
+      launches += 2;
+    }
+  }
+  const CgScalars& h = *m->cg_host;
+  if (h.status != 0) {
+    m->failed = true;
+    if (h.status == GSW_E_NOCONV)
+      return fail(ctx, GSW_E_NOCONV, "step %lld: flexible CG did not reach %g in %d iterations (at %g)",
+                  (long long)m->step, m->opts.tol, h.iter, h.relres);
+    return fail(ctx, GSW_E_NAN, "step %lld: non-finite CG residual", (long long)m->step);
+  }
+  launch_newmark(mv, m->x, m->u, m->v, m->a, m->cg, s);
+  launch_record(m->v, m->rec_node, m->rec_w, m->n_rec, m->wave, m->n_steps, (int)m->step, s);
+  CK(cudaGetLastError());
+  m->stats.steps_done += 1;
+  m->stats.cg_iters_total += h.iter;
+  m->stats.cg_iters_last = h.iter;
+  if (h.iter > m->stats.cg_iters_max) m->stats.cg_iters_max = h.iter;
+  m->stats.relres_last = h.relres;
+  m->stats.kernel_launches += launches + 2;
+  m->step += 1;
+  return GSW_OK;
+}
+
 bool finite_all(const double* p, size_t n) {
   for (size_t i = 0; i < n; ++i)
     if (!isfinite(p[i])) return false;
@@ -336,15 +534,7 @@ gsw_status gsw_create(gsw_ctx** out, int device, void* cuda_stream) {
   gsw_ctx* ctx = new gsw_ctx();
   ctx->device = device;
   DeviceGuard g(device);
-  if (cuda_stream) {
-    ctx->stream = (cudaStream_t)cuda_stream;
-  } else {
-    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
-      delete ctx;
-      return GSW_E_CUDA;
-    }
-    ctx->own_stream = true;
-  }
+  ctx->stream = (cudaStream_t)cuda_stream;  // NULL: the default stream
   *out = ctx;
   return GSW_OK;
 }
@@ -357,7 +547,6 @@ void gsw_destroy(gsw_ctx* ctx) {
   ctx->models.clear();
   misfit_free(ctx->misfit, ctx->stream);
   cudaStreamSynchronize(ctx->stream);
-  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
 
@@ -546,6 +735,7 @@ gsw_status gsw_set_time(gsw_ctx* ctx, int32_t model_id, double dt, int32_t n_ste
   launch_block_jacobi(m->view(), m->dblk, m->dinv, m->err, s);
   CK(cudaGetLastError());
   TRY(check_device_err(ctx, m, "preconditioner"));
+  if (m->opts.precision != GSW_PREC_FP64) TRY(build_lo(ctx, m, m->opts.precision == GSW_PREC_FP16));
   return model_reset(ctx, m);
 }
 
@@ -569,9 +759,15 @@ gsw_status gsw_set_solver(gsw_ctx* ctx, int32_t model_id, const gsw_solver_opts*
   if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
   if (!(opts->tol > 0.0) || opts->max_iter <= 0)
     return fail(ctx, GSW_E_INVALID, "need tol > 0 and max_iter > 0");
-  if (opts->precision != GSW_PREC_FP64)
-    return fail(ctx, GSW_E_INVALID, "precision mode %d is not available", opts->precision);
+  if (opts->precision < GSW_PREC_FP64 || opts->precision > GSW_PREC_FP16)
+    return fail(ctx, GSW_E_INVALID, "precision mode %d is not one of FP64, FP32, FP16", opts->precision);
+  if (opts->precision != GSW_PREC_FP64 && (opts->inner_iters <= 0 || opts->inner_iters > 10000))
+    return fail(ctx, GSW_E_INVALID, "inner_iters must be 1..10000");
   m->opts = *opts;
+  if (m->opts.precision != GSW_PREC_FP64 && m->time_set) {
+    DeviceGuard g(ctx->device);
+    TRY(build_lo(ctx, m, m->opts.precision == GSW_PREC_FP16));
+  }
   return GSW_OK;
 }
 
@@ -593,7 +789,12 @@ gsw_status gsw_step(gsw_ctx* ctx, int32_t model_id, int32_t n) {
   if (m->failed) return fail(ctx, GSW_E_STATE, "model failed at step %lld; reset it", (long long)m->step);
   if (n < 0 || m->step + n > m->n_steps)
     return fail(ctx, GSW_E_INVALID, "cannot step %d from %lld of %d", n, (long long)m->step, m->n_steps);
-  for (int i = 0; i < n; ++i) TRY(step_fp64(ctx, m));
+  for (int i = 0; i < n; ++i) {
+    if (m->opts.precision == GSW_PREC_FP64)
+      TRY(step_fp64(ctx, m));
+    else
+      TRY(step_mixed(ctx, m));
+  }
   return GSW_OK;
 }
 
@@ -636,19 +837,25 @@ gsw_status gsw_read_waveform_steps(gsw_ctx* ctx, int32_t model_id, int32_t step0
   return GSW_OK;
 }
 
-gsw_status gsw_timing(gsw_ctx* ctx, int32_t model_id, int32_t enable, double* ebe_ms, int64_t* ebe_launches) {
+gsw_status gsw_timing(gsw_ctx* ctx, int32_t model_id, int32_t enable, double* ms, int64_t* launches) {
   if (!ctx) return GSW_E_INVALID;
   Model* m = find(ctx, model_id);
   if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
   if (enable == 1) {
     m->timing = true;
-    m->ebe_ms = 0.0;
-    m->ebe_count = 0;
+    m->ebe_ms = m->lo_ms = 0.0;
+    m->ebe_count = m->lo_count = 0;
   } else if (enable == 0) {
     m->timing = false;
   }
-  if (ebe_ms) *ebe_ms = m->ebe_ms;
-  if (ebe_launches) *ebe_launches = m->ebe_count;
+  if (ms) {
+    ms[0] = m->ebe_ms;
+    ms[1] = m->lo_ms;
+  }
+  if (launches) {
+    launches[0] = m->ebe_count;
+    launches[1] = m->lo_count;
+  }
   return GSW_OK;
 }
 
@@ -702,7 +909,17 @@ gsw_status gsw_apply(gsw_ctx* ctx, int32_t model_id, int32_t which, const double
   Model* m = find(ctx, model_id);
   if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
   if (!m->time_set) return fail(ctx, GSW_E_STATE, "call gsw_set_time first");
-  if (which < 0 || which > 3) return fail(ctx, GSW_E_INVALID, "which must be 0..3");
+  if (which < 0 || which > 4) return fail(ctx, GSW_E_INVALID, "which must be 0..4");
+  if (which == 4) {
+    if (m->opts.precision == GSW_PREC_FP64 || !m->lo_ready)
+      return fail(ctx, GSW_E_STATE, "the reduced-precision operator needs a mixed precision mode");
+    launch_to_lo(m->N, x_dev, m->d_lo, m->lo_half, m->w32, ctx->stream);
+    const void* view = m->lo_half ? (const void*)&m->lo_h : (const void*)&m->lo_f;
+    launch_ebe_lo(m->lo_half, m->lo_half, view, m->d_lo, m->w32, m->partials, m->isc, ctx->stream);
+    launch_from_f32(m->N, m->w32, y_dev, ctx->stream);
+    CK(cudaGetLastError());
+    return GSW_OK;
+  }
   CK(cudaMemsetAsync(y_dev, 0, sizeof(double) * 3 * (size_t)m->N, ctx->stream));
   const int mode = which == 0 ? kModeA : which == 1 ? kModeK : which == 2 ? kModeM : kModeC;
   launch_ebe(mode, m->view(), x_dev, nullptr, nullptr, y_dev, 0.0, 0, nullptr, nullptr, ctx->stream);

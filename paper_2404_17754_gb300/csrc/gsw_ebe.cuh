@@ -1,0 +1,137 @@
+// Element-level operators of the second-order tetrahedron, shared by the
+// FP64 and the reduced-precision kernels (T = double or float).
+//
+// For an affine quadratic tetrahedron with barycentric gradients
+// g_m = grad L_m, the displacement gradient is linear, grad u = sum_k L_k H_k,
+// with H_k (the gradient at vertex k)
+//     H_k = 4 [ u_k (x) g_k + sum_{b != k} u_kb (x) g_b ] - sum_a u_a (x) g_a.
+// The stress is sigma = sum_k L_k S_k, S_k = lam tr(H_k) I + mu (H_k + H_k^T),
+// and exact integration of sigma . grad N (int L_i L_j dV = V (1 + d_ij) / 20)
+// gives, with T_km = S_k g_m and T_m = sum_k T_km,
+//     vertex a:     f_a  = V/20 (4 T_aa - T_a)
+//     edge (a, b):  f_ab = V/5  (T_a + T_b + T_ab + T_ba).
+// The consistent mass is the closed-form pattern rho V / 420 {vertex diag 6,
+// vertex-vertex 1, vertex-edge -4 (edge contains the vertex) or -6, edge diag
+// 32, adjacent edges 16, opposite edges 8}.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace gsw {
+
+// edge index of the vertex pair (a, b), VTK order 01, 12, 02, 03, 13, 23
+__host__ __device__ constexpr int edge_of(int a, int b) {
+  return (a + b == 1) ? 0 : (a + b == 3 ? (a * b == 2 ? 1 : 3) : (a + b == 2 ? 2 : (a + b == 4 ? 4 : 5)));
+}
+__host__ __device__ constexpr int edge_a(int e) { return e == 0 ? 0 : e == 1 ? 1 : e == 2 ? 0 : e == 3 ? 0 : e == 4 ? 1 : 2; }
+__host__ __device__ constexpr int edge_b(int e) { return e == 0 ? 1 : e == 1 ? 2 : e == 2 ? 2 : e == 3 ? 3 : e == 4 ? 3 : 3; }
+__host__ __device__ constexpr int edge_opp(int e) { return e == 0 ? 5 : e == 1 ? 3 : e == 2 ? 4 : e == 3 ? 1 : e == 4 ? 2 : 0; }
+
+// y = K' w, K' = the element stiffness with lam, mu pre-scaled (lamS = s lam
+// V/20, muS = s mu V/20).  g[m] = grad L_{m+1}; grad L_0 = -(g0 + g1 + g2).
+template <typename T>
+__device__ __forceinline__ void stiffness_apply(const T (&w)[10][3], const T (&g)[3][3], T lamS, T muS,
+                                                T (&y)[10][3]) {
+  T D0[3][3];  // u_m - u_0, m = 1..3
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) D0[m][i] = w[m + 1][i] - w[0][i];
+  T sumT[4][3], diagT[4][3], cross[6][3];
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) sumT[m][i] = T(0);
+#pragma unroll
+  for (int e = 0; e < 6; ++e)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) cross[e][i] = T(0);
+  const T mu2S = T(2) * muS;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    // U(k, b) = u_k if b == k else u_{edge(k, b)}
+    T H[3][3];
+#pragma unroll
+    for (int m = 1; m < 4; ++m) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const T ukm = (m == k) ? w[k][i] : w[4 + edge_of(k, m)][i];
+        const T uk0 = (k == 0) ? w[0][i] : w[4 + edge_of(k, 0)][i];
+        const T E = fma(T(4.0), ukm - uk0, -D0[m - 1][i]);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          if (m == 1)
+            H[i][j] = E * g[0][j];
+          else
+            H[i][j] = fma(E, g[m - 1][j], H[i][j]);
+        }
+      }
+    }
+    const T tr = H[0][0] + H[1][1] + H[2][2];
+    const T lt = lamS * tr;
+    T S[3][3];
+    S[0][0] = fma(mu2S, H[0][0], lt);
+    S[1][1] = fma(mu2S, H[1][1], lt);
+    S[2][2] = fma(mu2S, H[2][2], lt);
+    S[0][1] = S[1][0] = muS * (H[0][1] + H[1][0]);
+    S[0][2] = S[2][0] = muS * (H[0][2] + H[2][0]);
+    S[1][2] = S[2][1] = muS * (H[1][2] + H[2][1]);
+    T Tk[4][3];
+#pragma unroll
+    for (int m = 1; m < 4; ++m)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        Tk[m][i] = fma(S[i][0], g[m - 1][0], fma(S[i][1], g[m - 1][1], S[i][2] * g[m - 1][2]));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Tk[0][i] = -(Tk[1][i] + Tk[2][i] + Tk[3][i]);
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) sumT[m][i] += Tk[m][i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) diagT[k][i] = Tk[k][i];
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+      if (b != k)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) cross[edge_of(k, b)][i] += Tk[b][i];
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) y[a][i] = fma(T(4.0), diagT[a][i], -sumT[a][i]);
+#pragma unroll
+  for (int e = 0; e < 6; ++e)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      y[4 + e][i] = T(4) * (sumT[edge_a(e)][i] + sumT[edge_b(e)][i] + cross[e][i]);
+}
+
+// y += ms * P w with P the consistent-mass pattern (ms = s rho V / 420).
+template <typename T>
+__device__ __forceinline__ void mass_apply(const T (&w)[10][3], T ms, T (&y)[10][3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const T Xv = (w[0][i] + w[1][i]) + (w[2][i] + w[3][i]);
+    const T Xe = (w[4][i] + w[5][i]) + (w[6][i] + w[7][i]) + (w[8][i] + w[9][i]);
+    const T tv = fma(T(-6.0), Xe, Xv);
+    const T te = fma(T(16.0), Xe, T(-6.0) * Xv);
+    // vertex a: 5 w_a + 2 (edges at a) + Xv - 6 Xe
+    const T P0 = fma(T(5.0), w[0][i], fma(T(2.0), w[4][i] + w[6][i] + w[7][i], tv));
+    const T P1 = fma(T(5.0), w[1][i], fma(T(2.0), w[4][i] + w[5][i] + w[8][i], tv));
+    const T P2 = fma(T(5.0), w[2][i], fma(T(2.0), w[5][i] + w[6][i] + w[9][i], tv));
+    const T P3 = fma(T(5.0), w[3][i], fma(T(2.0), w[7][i] + w[8][i] + w[9][i], tv));
+    y[0][i] = fma(ms, P0, y[0][i]);
+    y[1][i] = fma(ms, P1, y[1][i]);
+    y[2][i] = fma(ms, P2, y[2][i]);
+    y[3][i] = fma(ms, P3, y[3][i]);
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      const int a = edge_a(e), b = edge_b(e), o = edge_opp(e);
+      const T P = fma(T(2.0), w[a][i] + w[b][i], fma(T(16.0), w[4 + e][i], fma(T(-8.0), w[4 + o][i], te)));
+      y[4 + e][i] = fma(ms, P, y[4 + e][i]);
+    }
+  }
+}
+
+}  // namespace gsw

@@ -26,7 +26,7 @@ struct CgScalars {
   double relres;  // ||r|| / ||b||
   double tol;
   double beta;    // p <- z + beta p
-  double pad0;
+  double alpha;   // step length of the last update
   int iter;
   int max_iter;
   int done;       // 1 once converged or failed
@@ -48,6 +48,44 @@ struct ModelView {
   const MatCoef* mat;       // [n_mat]
   const int32_t* fnode;     // [6][F]
   const double* fgeo;       // [6][F]: A rho Vs, A (rho Vp - rho Vs), n (3), tag
+  double dt;
+};
+
+// Scalars of the reduced-precision inner solve (the variable preconditioner).
+struct InnerScalars {
+  double st;     // s . t  (t = D^-1 s)
+  double dw;     // d . A d
+  double beta;
+  double scale;  // inner right-hand side = scale * outer residual
+  double dinv_mean;  // mean diagonal entry of D^-1 (set once per model)
+  unsigned int counter;
+  unsigned int pad;
+};
+
+// Element blocks with local node numbering: block b holds elements
+// [b * kElemThreads, (b + 1) * kElemThreads); its unique nodes are
+// nodes[ptr[b] .. ptr[b+1]) (bit 31 set: no other block and no absorbing face
+// touches the node), and lconn[k * E + e] is the local index of node k of e.
+struct BlockView {
+  int n_blk;
+  int max_local;
+  const int32_t* ptr;
+  const int32_t* nodes;
+  const uint16_t* lconn;
+};
+
+// Reduced-precision copy of a model for the inner solve.  SG: storage type of
+// the element geometry (float or __half).
+template <typename SG>
+struct LoView {
+  int64_t N, E, F;
+  BlockView blk;
+  const SG* geo;            // [9][E] barycentric gradients
+  const float* vol;         // [E] element volumes
+  const int32_t* emat;
+  const MatCoef* mat;
+  const int32_t* fnode;     // [6][F]
+  const float* fgeo;        // [6][F]
   double dt;
 };
 
@@ -84,6 +122,44 @@ void launch_newmark(const ModelView& m, const double* x, double* u, double* v, d
 void launch_record(const double* v, const int32_t* rec_node, const double* rec_w, int n_rec,
                    double* wave, int n_steps, int step, cudaStream_t s);
 int ebe_blocks(const ModelView& m);
+
+// ---- mixed precision (gsw_mixed.cu) -------------------------------------------
+// Element blocks: counts[b] of unique nodes per block (pass 1), then fill
+// nodes / lconn / refcount given ptr (pass 2), then mark exclusive nodes.
+void launch_block_count(const ModelView& m, int n_blk, int32_t* counts, cudaStream_t s);
+void launch_block_fill(const ModelView& m, BlockView b, int32_t* nodes, uint16_t* lconn,
+                       int32_t* refcount, cudaStream_t s);
+void launch_block_mark(const ModelView& m, BlockView b, int32_t* nodes, int32_t* refcount,
+                       int total, cudaStream_t s);
+void launch_lo_convert(const ModelView& m, int half_geo, void* geo_lo, float* vol32, float* fgeo32,
+                       const double* dinv, float* dinv32, double* partials, InnerScalars* sc,
+                       cudaStream_t s);
+// inner solve: half_vec selects __half storage of the search direction d
+void launch_inner_init(int64_t N, const double* r, const float* dinv32, float* s, float* y,
+                       float* t, void* d, int half_vec, float* w, double* partials,
+                       InnerScalars* sc, const CgScalars* cg, cudaStream_t st);
+void launch_ebe_lo(int half_geo, int half_vec, const void* lo_view, const void* d, float* w,
+                   double* partials, InnerScalars* sc, cudaStream_t st);
+void launch_inner_update(int64_t N, float* y, float* s, float* t, const void* d, int half_vec,
+                         float* w, const float* dinv32, double* partials, InnerScalars* sc,
+                         cudaStream_t st);
+void launch_inner_dupdate(int64_t N, const float* t, void* d, int half_vec, const InnerScalars* sc,
+                          cudaStream_t st);
+// conversions for the standalone reduced-precision operator (tests)
+void launch_to_lo(int64_t N, const double* x, void* d, int half_vec, float* w, cudaStream_t s);
+void launch_from_f32(int64_t N, const float* w, double* y, cudaStream_t s);
+// flexible CG outer iteration (FP64)
+void launch_fcg_residual(const ModelView& m, const double* b, double* q, double* r, double* partials,
+                         CgScalars* cg, cudaStream_t s);
+void launch_fcg_first(const ModelView& m, const float* y, const double* r, double* z, double* p,
+                      double* partials, CgScalars* cg, const InnerScalars* sc, cudaStream_t s);
+void launch_fcg_update(const ModelView& m, double* x, double* r, const double* p, const double* q,
+                       double* partials, CgScalars* cg, cudaStream_t s);
+void launch_fcg_zbeta(const ModelView& m, const float* y, const double* r, const double* q,
+                      double* z, double* partials, CgScalars* cg, const InnerScalars* sc,
+                      cudaStream_t s);
+void launch_fcg_pupdate(const ModelView& m, const double* z, double* p, double* q,
+                        const CgScalars* cg, cudaStream_t s);
 int node_blocks(int64_t n);
 
 }  // namespace gsw

@@ -24,73 +24,10 @@
 #include <stdint.h>
 
 #include "gsw_internal.cuh"
+#include "gsw_ebe.cuh"
+#include "gsw_reduce.cuh"
 
 namespace gsw {
-
-// edge index of the vertex pair (a, b), VTK order 01, 12, 02, 03, 13, 23
-__host__ __device__ constexpr int edge_of(int a, int b) {
-  return (a + b == 1) ? 0 : (a + b == 3 ? (a * b == 2 ? 1 : 3) : (a + b == 2 ? 2 : (a + b == 4 ? 4 : 5)));
-}
-__host__ __device__ constexpr int edge_a(int e) { return e == 0 ? 0 : e == 1 ? 1 : e == 2 ? 0 : e == 3 ? 0 : e == 4 ? 1 : 2; }
-__host__ __device__ constexpr int edge_b(int e) { return e == 0 ? 1 : e == 1 ? 2 : e == 2 ? 2 : e == 3 ? 3 : e == 4 ? 3 : 3; }
-__host__ __device__ constexpr int edge_opp(int e) { return e == 0 ? 5 : e == 1 ? 3 : e == 2 ? 4 : e == 3 ? 1 : e == 4 ? 2 : 0; }
-
-// ------------------------------------------------------------------------------
-// Reductions: warp shuffle, block tree, and a deterministic last-block finish.
-// ------------------------------------------------------------------------------
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Sum over the block; the result is valid in thread 0.  `sh` holds >= 32 doubles.
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = warp_sum(v);
-  __syncthreads();
-  if (lane == 0) sh[warp] = v;
-  __syncthreads();
-  const int nw = (blockDim.x + 31) >> 5;
-  v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
-  if (warp == 0) v = warp_sum(v);
-  return v;
-}
-
-// Each block contributes NQ partial sums; the last block to arrive sums all
-// partials in block order (so the result does not depend on scheduling) and
-// returns true in every thread of that block, with the totals in out[] of
-// thread 0.
-template <int NQ>
-__device__ bool last_block_reduce(const double (&vals)[NQ], double* partials,
-                                  unsigned int* counter, double (&out)[NQ]) {
-  __shared__ double sh[32];
-  __shared__ int am_last;
-  const unsigned int G = gridDim.x;
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    double s = block_sum(vals[q], sh);
-    if (threadIdx.x == 0) partials[q * G + blockIdx.x] = s;
-  }
-  if (threadIdx.x == 0) {
-    __threadfence();
-    unsigned int prev = atomicAdd(counter, 1u);
-    am_last = (prev == G - 1);
-  }
-  __syncthreads();
-  if (!am_last) return false;
-  __threadfence();
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    double acc = 0.0;
-    for (unsigned int i = threadIdx.x; i < G; i += blockDim.x)
-      acc += ((volatile double*)partials)[q * G + i];
-    out[q] = block_sum(acc, sh);
-  }
-  if (threadIdx.x == 0) *counter = 0u;
-  return true;
-}
 
 // ------------------------------------------------------------------------------
 // Setup kernels
@@ -373,111 +310,6 @@ __global__ void receiver_weights_kernel(ModelView m, const double* __restrict__ 
 // ------------------------------------------------------------------------------
 // Element-by-element operator
 // ------------------------------------------------------------------------------
-
-// y += K' w, K' = the element stiffness with lam, mu pre-scaled (lamS = s lam
-// V/20, muS = s mu V/20).  g[m] = grad L_{m+1}; grad L_0 = -(g0 + g1 + g2).
-__device__ __forceinline__ void stiffness_apply(const double (&w)[10][3], const double (&g)[3][3],
-                                                double lamS, double muS, double (&y)[10][3]) {
-  double D0[3][3];  // u_m - u_0, m = 1..3
-#pragma unroll
-  for (int m = 0; m < 3; ++m)
-#pragma unroll
-    for (int i = 0; i < 3; ++i) D0[m][i] = w[m + 1][i] - w[0][i];
-  double sumT[4][3], diagT[4][3], cross[6][3];
-#pragma unroll
-  for (int m = 0; m < 4; ++m)
-#pragma unroll
-    for (int i = 0; i < 3; ++i) sumT[m][i] = 0.0;
-#pragma unroll
-  for (int e = 0; e < 6; ++e)
-#pragma unroll
-    for (int i = 0; i < 3; ++i) cross[e][i] = 0.0;
-  const double mu2S = 2.0 * muS;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    // U(k, b) = u_k if b == k else u_{edge(k, b)}
-    double H[3][3];
-#pragma unroll
-    for (int m = 1; m < 4; ++m) {
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const double ukm = (m == k) ? w[k][i] : w[4 + edge_of(k, m)][i];
-        const double uk0 = (k == 0) ? w[0][i] : w[4 + edge_of(k, 0)][i];
-        const double E = fma(4.0, ukm - uk0, -D0[m - 1][i]);
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          if (m == 1)
-            H[i][j] = E * g[0][j];
-          else
-            H[i][j] = fma(E, g[m - 1][j], H[i][j]);
-        }
-      }
-    }
-    const double tr = H[0][0] + H[1][1] + H[2][2];
-    const double lt = lamS * tr;
-    double S[3][3];
-    S[0][0] = fma(mu2S, H[0][0], lt);
-    S[1][1] = fma(mu2S, H[1][1], lt);
-    S[2][2] = fma(mu2S, H[2][2], lt);
-    S[0][1] = S[1][0] = muS * (H[0][1] + H[1][0]);
-    S[0][2] = S[2][0] = muS * (H[0][2] + H[2][0]);
-    S[1][2] = S[2][1] = muS * (H[1][2] + H[2][1]);
-    double T[4][3];
-#pragma unroll
-    for (int m = 1; m < 4; ++m)
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-        T[m][i] = fma(S[i][0], g[m - 1][0], fma(S[i][1], g[m - 1][1], S[i][2] * g[m - 1][2]));
-#pragma unroll
-    for (int i = 0; i < 3; ++i) T[0][i] = -(T[1][i] + T[2][i] + T[3][i]);
-#pragma unroll
-    for (int m = 0; m < 4; ++m)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) sumT[m][i] += T[m][i];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) diagT[k][i] = T[k][i];
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-      if (b != k)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) cross[edge_of(k, b)][i] += T[b][i];
-  }
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int i = 0; i < 3; ++i) y[a][i] = fma(4.0, diagT[a][i], -sumT[a][i]);
-#pragma unroll
-  for (int e = 0; e < 6; ++e)
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-      y[4 + e][i] = 4.0 * (sumT[edge_a(e)][i] + sumT[edge_b(e)][i] + cross[e][i]);
-}
-
-// y += ms * P w with P the consistent-mass pattern (ms = s rho V / 420).
-__device__ __forceinline__ void mass_apply(const double (&w)[10][3], double ms, double (&y)[10][3]) {
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const double Xv = (w[0][i] + w[1][i]) + (w[2][i] + w[3][i]);
-    const double Xe = (w[4][i] + w[5][i]) + (w[6][i] + w[7][i]) + (w[8][i] + w[9][i]);
-    const double tv = fma(-6.0, Xe, Xv);
-    const double te = fma(16.0, Xe, -6.0 * Xv);
-    // vertex a: 5 w_a + 2 (edges at a) + Xv - 6 Xe
-    const double P0 = fma(5.0, w[0][i], fma(2.0, w[4][i] + w[6][i] + w[7][i], tv));
-    const double P1 = fma(5.0, w[1][i], fma(2.0, w[4][i] + w[5][i] + w[8][i], tv));
-    const double P2 = fma(5.0, w[2][i], fma(2.0, w[5][i] + w[6][i] + w[9][i], tv));
-    const double P3 = fma(5.0, w[3][i], fma(2.0, w[7][i] + w[8][i] + w[9][i], tv));
-    y[0][i] = fma(ms, P0, y[0][i]);
-    y[1][i] = fma(ms, P1, y[1][i]);
-    y[2][i] = fma(ms, P2, y[2][i]);
-    y[3][i] = fma(ms, P3, y[3][i]);
-#pragma unroll
-    for (int e = 0; e < 6; ++e) {
-      const int a = edge_a(e), b = edge_b(e), o = edge_opp(e);
-      const double P = fma(2.0, w[a][i] + w[b][i], fma(16.0, w[4 + e][i], fma(-8.0, w[4 + o][i], te)));
-      y[4 + e][i] = fma(ms, P, y[4 + e][i]);
-    }
-  }
-}
 
 // One thread per element (t < E) or boundary face (E <= t < E + F).
 //   kModeA   y = A x               (+ partial x.y when partials != nullptr)

@@ -1,0 +1,585 @@
+// Mixed-precision solve: flexible CG in FP64 with a reduced-precision inner
+// PCG as the variable preconditioner (Section 3, computational-cost
+// paragraph: conjugate gradients with variable preconditioning).
+//
+// Outer iteration (FP64 residual, dot products and update):
+//   r = b - A x0;  z = P(r);  p = z
+//   repeat: q = A p; alpha = r.z / p.q; x += alpha p; r -= alpha q
+//           z' = P(r); beta = z'.(r' - r) / (r.z) = -alpha z'.q / (r.z); p = z' + beta p
+// (Polak-Ribiere beta keeps CG's short recurrence valid when P varies.)
+//
+// Inner solve P(r): a fixed number of block-Jacobi PCG iterations on A in
+// FP32 arithmetic, with the search direction stored in FP32 or FP16 and the
+// barycentric gradients in FP32 or FP16 (volumes FP32).  The right-hand side
+// is the outer residual scaled so that the preconditioned residual D^-1 s,
+// which seeds the stored search direction, has entries of order one (FP16
+// keeps 3 significant digits between 6e-5 and 6.5e4).  The element-by-element product assembles each block of
+// elements in shared memory over the block's unique nodes (local numbering
+// built on the GPU at setup) and writes every node once per block: a plain
+// store for nodes no other block touches, an atomic add otherwise.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "gsw_ebe.cuh"
+#include "gsw_internal.cuh"
+#include "gsw_reduce.cuh"
+
+namespace gsw {
+
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(__half x) { return __half2float(x); }
+template <typename T>
+__device__ __forceinline__ T from_f(float x);
+template <>
+__device__ __forceinline__ float from_f<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ __half from_f<__half>(float x) { return __float2half_rn(x); }
+
+constexpr int kSortN = 2048;  // >= 10 * kElemThreads, power of two
+
+// ------------------------------------------------------------------------------
+// Element blocks: unique nodes per block via an in-shared-memory bitonic sort
+// ------------------------------------------------------------------------------
+
+__device__ void load_sorted_block(const ModelView& m, int b, int* keys) {
+  const int64_t e0 = (int64_t)b * kElemThreads;
+  const int ne = (int)((m.E - e0) < kElemThreads ? (m.E - e0) : kElemThreads);
+  for (int i = threadIdx.x; i < kSortN; i += blockDim.x) {
+    int v = 0x7fffffff;
+    if (i < 10 * ne) {
+      const int k = i / ne, el = i % ne;
+      v = m.conn[(int64_t)k * m.E + e0 + el];
+    }
+    keys[i] = v;
+  }
+  __syncthreads();
+  for (int size = 2; size <= kSortN; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < kSortN / 2; i += blockDim.x) {
+        const int lo = 2 * i - (i & (stride - 1));
+        const int hi = lo + stride;
+        const bool up = ((lo & size) == 0);
+        const int a = keys[lo], c = keys[hi];
+        if ((a > c) == up) {
+          keys[lo] = c;
+          keys[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void block_count_kernel(ModelView m, int32_t* counts) {
+  __shared__ int keys[kSortN];
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  load_sorted_block(m, blockIdx.x, keys);
+  int c = 0;
+  for (int i = threadIdx.x; i < kSortN; i += blockDim.x)
+    if (keys[i] != 0x7fffffff && (i == 0 || keys[i] != keys[i - 1])) ++c;
+  atomicAdd(&cnt, c);
+  __syncthreads();
+  if (threadIdx.x == 0) counts[blockIdx.x] = cnt;
+}
+
+__global__ void block_fill_kernel(ModelView m, BlockView bv, int32_t* nodes, uint16_t* lconn,
+                                  int32_t* refcount) {
+  __shared__ int keys[kSortN];
+  __shared__ int flag[kSortN];
+  const int b = blockIdx.x;
+  load_sorted_block(m, b, keys);
+  for (int i = threadIdx.x; i < kSortN; i += blockDim.x)
+    flag[i] = (keys[i] != 0x7fffffff && (i == 0 || keys[i] != keys[i - 1])) ? 1 : 0;
+  __syncthreads();
+  // inclusive scan of flags (Hillis-Steele, in place with a temporary)
+  for (int off = 1; off < kSortN; off <<= 1) {
+    int v[kSortN / 256];
+    for (int j = 0; j < kSortN / 256; ++j) {
+      const int i = threadIdx.x + j * 256;
+      v[j] = (i < kSortN && i >= off) ? flag[i - off] : 0;
+    }
+    __syncthreads();
+    for (int j = 0; j < kSortN / 256; ++j) {
+      const int i = threadIdx.x + j * 256;
+      if (i < kSortN) flag[i] += v[j];
+    }
+    __syncthreads();
+  }
+  const int base = bv.ptr[b];
+  const int nu = bv.ptr[b + 1] - base;
+  for (int i = threadIdx.x; i < kSortN; i += blockDim.x) {
+    const bool first = keys[i] != 0x7fffffff && (i == 0 || keys[i] != keys[i - 1]);
+    if (first) {
+      const int slot = flag[i] - 1;
+      nodes[base + slot] = keys[i];
+      atomicAdd(refcount + keys[i], 1);
+    }
+  }
+  __syncthreads();
+  // compact the unique keys to the front of `keys` (reuse flag as storage)
+  for (int i = threadIdx.x; i < nu; i += blockDim.x) flag[i] = nodes[base + i];
+  __syncthreads();
+  const int64_t e0 = (int64_t)b * kElemThreads;
+  const int ne = (int)((m.E - e0) < kElemThreads ? (m.E - e0) : kElemThreads);
+  for (int i = threadIdx.x; i < 10 * ne; i += blockDim.x) {
+    const int k = i / ne, el = i % ne;
+    const int g = m.conn[(int64_t)k * m.E + e0 + el];
+    int lo = 0, hi = nu - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (flag[mid] < g)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    lconn[(int64_t)k * m.E + e0 + el] = (uint16_t)lo;
+  }
+}
+
+__global__ void face_refcount_kernel(ModelView m, int32_t* refcount) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= m.F) return;
+  if (m.fgeo[5 * m.F + f] < 0.5) return;  // free surface faces add nothing
+  for (int k = 0; k < 6; ++k) atomicAdd(refcount + m.fnode[k * m.F + f], 2);
+}
+
+__global__ void block_mark_kernel(int total, int32_t* nodes, const int32_t* refcount) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int g = nodes[i];
+  if (refcount[g] == 1) nodes[i] = (int32_t)((uint32_t)g | 0x80000000u);
+}
+
+template <typename SG>
+__global__ void lo_convert_kernel(ModelView m, SG* geo_lo, float* vol32, float* fgeo32, const double* dinv,
+                                  float* dinv32) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < 9 * m.E) geo_lo[t] = from_f<SG>((float)m.geo[t]);
+  if (t < m.E) vol32[t] = (float)m.geo[9 * m.E + t];
+  if (t < 6 * m.F) fgeo32[t] = (float)m.fgeo[t];
+  if (t < 6 * m.N) dinv32[t] = (float)dinv[t];
+}
+
+// Mean diagonal entry of D^-1 (sets the inner right-hand-side scale).
+__global__ void dinv_mean_kernel(int64_t N, const double* __restrict__ dinv, double* partials, InnerScalars* sc) {
+  double s = 0.0;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+    s += dinv[6 * n] + dinv[6 * n + 1] + dinv[6 * n + 2];
+  double vals[1] = {s}, out[1];
+  if (last_block_reduce<1>(vals, partials, &sc->counter, out) && threadIdx.x == 0) sc->dinv_mean = out[0] / (3.0 * N);
+}
+
+// ------------------------------------------------------------------------------
+// Reduced-precision element-by-element product w = A d (+ partial d . w)
+// ------------------------------------------------------------------------------
+
+template <typename SG, typename SD>
+__global__ void __launch_bounds__(kElemThreads) ebe_lo_kernel(LoView<SG> m, const SD* __restrict__ d,
+                                                               float* __restrict__ w, double* partials,
+                                                               InnerScalars* sc) {
+  extern __shared__ float sm[];
+  float* xs = sm;
+  float* ys = sm + 3 * m.blk.max_local;
+  const int b = blockIdx.x;
+  float dot = 0.f;
+  if (b < m.blk.n_blk) {
+    const int n0 = m.blk.ptr[b], nn = m.blk.ptr[b + 1] - n0;
+    for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+      const int64_t g = m.blk.nodes[n0 + i] & 0x7fffffff;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        xs[3 * i + c] = to_f(d[3 * g + c]);
+        ys[3 * i + c] = 0.f;
+      }
+    }
+    __syncthreads();
+    const int64_t e = (int64_t)b * kElemThreads + threadIdx.x;
+    if (e < m.E) {
+      int lc[10];
+#pragma unroll
+      for (int k = 0; k < 10; ++k) lc[k] = m.blk.lconn[k * m.E + e];
+      float g[3][3];
+#pragma unroll
+      for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) g[mm][i] = to_f(m.geo[(3 * mm + i) * m.E + e]);
+      const float V = m.vol[e];
+      const MatCoef& mc = m.mat[m.emat[e]];
+      const float lamS = (float)(mc.cK * mc.lam * (1.0 / 20.0)) * V;
+      const float muS = (float)(mc.cK * mc.mu * (1.0 / 20.0)) * V;
+      const float mS = (float)(mc.cM * mc.rho * (1.0 / 420.0)) * V;
+      float wv[10][3], f[10][3];
+#pragma unroll
+      for (int k = 0; k < 10; ++k)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) wv[k][i] = xs[3 * lc[k] + i];
+      stiffness_apply<float>(wv, g, lamS, muS, f);
+      mass_apply<float>(wv, mS, f);
+#pragma unroll
+      for (int k = 0; k < 10; ++k)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          atomicAdd(ys + 3 * lc[k] + i, f[k][i]);
+          dot = fmaf(wv[k][i], f[k][i], dot);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+      const int32_t raw = m.blk.nodes[n0 + i];
+      const int64_t g = raw & 0x7fffffff;
+      if (raw < 0) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) w[3 * g + c] = ys[3 * i + c];
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) atomicAdd(w + 3 * g + c, ys[3 * i + c]);
+      }
+    }
+  } else {
+    // absorbing faces: (2/dt) C_abs d
+    const int64_t fc = (int64_t)(b - m.blk.n_blk) * kElemThreads + threadIdx.x;
+    if (fc < m.F && m.fgeo[5 * m.F + fc] > 0.5f) {
+      const float sc2 = (float)(2.0 / m.dt) / 180.f;
+      const float As = sc2 * m.fgeo[fc], Ad = sc2 * m.fgeo[m.F + fc];
+      const float n[3] = {m.fgeo[2 * m.F + fc], m.fgeo[3 * m.F + fc], m.fgeo[4 * m.F + fc]};
+      int64_t nd[6];
+      float z[6][3], xin[6][3];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        nd[k] = m.fnode[k * m.F + fc];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) xin[k][i] = to_f(d[3 * nd[k] + i]);
+        const float dn = n[0] * xin[k][0] + n[1] * xin[k][1] + n[2] * xin[k][2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) z[k][i] = fmaf(As, xin[k][i], Ad * dn * n[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const float Zv = z[0][i] + z[1][i] + z[2][i];
+        const float Ze = z[3][i] + z[4][i] + z[5][i];
+        float yf[6];
+        yf[0] = 7.f * z[0][i] - Zv - 4.f * z[4][i];
+        yf[1] = 7.f * z[1][i] - Zv - 4.f * z[5][i];
+        yf[2] = 7.f * z[2][i] - Zv - 4.f * z[3][i];
+        yf[3] = 16.f * (z[3][i] + Ze) - 4.f * z[2][i];
+        yf[4] = 16.f * (z[4][i] + Ze) - 4.f * z[0][i];
+        yf[5] = 16.f * (z[5][i] + Ze) - 4.f * z[1][i];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          atomicAdd(w + 3 * nd[k] + i, yf[k]);
+          dot = fmaf(xin[k][i], yf[k], dot);
+        }
+      }
+    }
+  }
+  double vals[1] = {(double)dot}, out[1];
+  if (last_block_reduce<1>(vals, partials, &sc->counter, out) && threadIdx.x == 0) sc->dw = out[0];
+}
+
+// ------------------------------------------------------------------------------
+// Inner PCG vector kernels (FP32 arithmetic)
+// ------------------------------------------------------------------------------
+
+__device__ __forceinline__ void dinv_apply_f(const float* __restrict__ D, const float r[3], float z[3]) {
+  z[0] = D[0] * r[0] + D[3] * r[1] + D[4] * r[2];
+  z[1] = D[3] * r[0] + D[1] * r[1] + D[5] * r[2];
+  z[2] = D[4] * r[0] + D[5] * r[1] + D[2] * r[2];
+}
+
+template <typename SD>
+__global__ void inner_init_kernel(int64_t N, const double* __restrict__ r, const float* __restrict__ dinv,
+                                  float* __restrict__ s, float* __restrict__ y, float* __restrict__ t,
+                                  SD* __restrict__ d, float* __restrict__ w, double* partials,
+                                  InnerScalars* sc, const CgScalars* cg) {
+  const double rr = ((volatile const CgScalars*)cg)->rr;
+  const double dm = ((volatile const InnerScalars*)sc)->dinv_mean;
+  const double scale = (rr > 0.0 ? sqrt(3.0 * (double)N / rr) : 1.0) / (dm > 0.0 ? dm : 1.0);
+  float st = 0.f;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+    float sn[3], tn[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      sn[i] = (float)(r[3 * n + i] * scale);
+      s[3 * n + i] = sn[i];
+      y[3 * n + i] = 0.f;
+      w[3 * n + i] = 0.f;
+    }
+    dinv_apply_f(dinv + 6 * n, sn, tn);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      t[3 * n + i] = tn[i];
+      d[3 * n + i] = from_f<SD>(tn[i]);
+      st = fmaf(sn[i], tn[i], st);
+    }
+  }
+  double vals[1] = {(double)st}, out[1];
+  if (last_block_reduce<1>(vals, partials, &sc->counter, out) && threadIdx.x == 0) {
+    sc->st = out[0];
+    sc->scale = scale;
+  }
+}
+
+template <typename SD>
+__global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __restrict__ s, float* __restrict__ t,
+                                    const SD* __restrict__ d, float* __restrict__ w, const float* __restrict__ dinv,
+                                    double* partials, InnerScalars* sc) {
+  const double st_old = ((volatile InnerScalars*)sc)->st, dw = ((volatile InnerScalars*)sc)->dw;
+  const float alpha = (dw != 0.0) ? (float)(st_old / dw) : 0.f;
+  float st = 0.f;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+    float sn[3], tn[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int64_t k = 3 * n + i;
+      y[k] = fmaf(alpha, to_f(d[k]), y[k]);
+      sn[i] = fmaf(-alpha, w[k], s[k]);
+      s[k] = sn[i];
+      w[k] = 0.f;
+    }
+    dinv_apply_f(dinv + 6 * n, sn, tn);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      t[3 * n + i] = tn[i];
+      st = fmaf(sn[i], tn[i], st);
+    }
+  }
+  double vals[1] = {(double)st}, out[1];
+  if (last_block_reduce<1>(vals, partials, &sc->counter, out) && threadIdx.x == 0) {
+    sc->beta = (st_old != 0.0) ? out[0] / st_old : 0.0;
+    sc->st = out[0];
+  }
+}
+
+template <typename SD>
+__global__ void inner_dupdate_kernel(int64_t N, const float* __restrict__ t, SD* __restrict__ d,
+                                     const InnerScalars* sc) {
+  const float beta = (float)((volatile const InnerScalars*)sc)->beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N; i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = from_f<SD>(fmaf(beta, to_f(d[i]), t[i]));
+}
+
+// ------------------------------------------------------------------------------
+// Flexible CG outer kernels (FP64)
+// ------------------------------------------------------------------------------
+
+__global__ void fcg_residual_kernel(int64_t N, const double* __restrict__ b, double* __restrict__ q,
+                                    double* __restrict__ r, double* partials, CgScalars* cg) {
+  if (((volatile CgScalars*)cg)->done) return;
+  double rr = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = b[i] - q[i];
+    r[i] = ri;
+    q[i] = 0.0;
+    rr = fma(ri, ri, rr);
+  }
+  double vals[1] = {rr}, out[1];
+  if (last_block_reduce<1>(vals, partials, &cg->counter, out) && threadIdx.x == 0) {
+    cg->rr = out[0];
+    cg->relres = sqrt(out[0] / cg->bb);
+    if (!isfinite(out[0])) {
+      cg->status = -5;
+      cg->done = 1;
+    } else if (cg->relres <= cg->tol) {
+      cg->done = 1;
+    }
+  }
+}
+
+__global__ void fcg_first_kernel(int64_t N, const float* __restrict__ y, const double* __restrict__ r,
+                                 double* __restrict__ z, double* __restrict__ p, double* partials, CgScalars* cg,
+                                 const InnerScalars* sc) {
+  const double inv = 1.0 / ((volatile const InnerScalars*)sc)->scale;
+  double rz = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double zi = (double)y[i] * inv;
+    z[i] = zi;
+    p[i] = zi;
+    rz = fma(r[i], zi, rz);
+  }
+  double vals[1] = {rz}, out[1];
+  if (last_block_reduce<1>(vals, partials, &cg->counter, out) && threadIdx.x == 0) cg->rz = out[0];
+}
+
+__global__ void fcg_update_kernel(int64_t N, double* __restrict__ x, double* __restrict__ r,
+                                  const double* __restrict__ p, const double* __restrict__ q, double* partials,
+                                  CgScalars* cg) {
+  const double alpha = ((volatile CgScalars*)cg)->rz / ((volatile CgScalars*)cg)->pq;
+  double rr = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = fma(-alpha, q[i], r[i]);
+    r[i] = ri;
+    rr = fma(ri, ri, rr);
+  }
+  double vals[1] = {rr}, out[1];
+  if (last_block_reduce<1>(vals, partials, &cg->counter, out) && threadIdx.x == 0) {
+    cg->iter += 1;
+    cg->alpha = alpha;
+    cg->rr = out[0];
+    cg->relres = sqrt(out[0] / cg->bb);
+    if (!isfinite(out[0]) || !isfinite(alpha)) {
+      cg->status = -5;
+      cg->done = 1;
+    } else if (cg->relres <= cg->tol) {
+      cg->done = 1;
+    } else if (cg->iter >= cg->max_iter) {
+      cg->status = -4;
+      cg->done = 1;
+    }
+  }
+}
+
+__global__ void fcg_zbeta_kernel(int64_t N, const float* __restrict__ y, const double* __restrict__ r,
+                                 const double* __restrict__ q, double* __restrict__ z, double* partials,
+                                 CgScalars* cg, const InnerScalars* sc) {
+  const double inv = 1.0 / ((volatile const InnerScalars*)sc)->scale;
+  double zq = 0.0, rz = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double zi = (double)y[i] * inv;
+    z[i] = zi;
+    zq = fma(zi, q[i], zq);
+    rz = fma(r[i], zi, rz);
+  }
+  double vals[2] = {zq, rz}, out[2];
+  if (last_block_reduce<2>(vals, partials, &cg->counter, out) && threadIdx.x == 0) {
+    cg->beta = -cg->alpha * out[0] / cg->rz;
+    cg->rz = out[1];
+    if (!isfinite(cg->beta) || !isfinite(out[1])) {
+      cg->status = -5;
+      cg->done = 1;
+    }
+  }
+}
+
+__global__ void fcg_pupdate_kernel(int64_t N, const double* __restrict__ z, double* __restrict__ p,
+                                   double* __restrict__ q, const CgScalars* cg) {
+  const double beta = ((volatile const CgScalars*)cg)->beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N; i += (int64_t)gridDim.x * blockDim.x) {
+    p[i] = fma(beta, p[i], z[i]);
+    q[i] = 0.0;
+  }
+}
+
+template <typename SD>
+__global__ void to_lo_kernel(int64_t n, const double* __restrict__ x, SD* __restrict__ d, float* __restrict__ w) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    d[i] = from_f<SD>((float)x[i]);
+    w[i] = 0.f;
+  }
+}
+__global__ void from_f32_kernel(int64_t n, const float* __restrict__ w, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (double)w[i];
+}
+
+// ------------------------------------------------------------------------------
+// Launchers
+// ------------------------------------------------------------------------------
+
+void launch_to_lo(int64_t N, const double* x, void* d, int half_vec, float* w, cudaStream_t s) {
+  if (half_vec)
+    to_lo_kernel<__half><<<node_blocks(3 * N), kNodeThreads, 0, s>>>(3 * N, x, (__half*)d, w);
+  else
+    to_lo_kernel<float><<<node_blocks(3 * N), kNodeThreads, 0, s>>>(3 * N, x, (float*)d, w);
+}
+void launch_from_f32(int64_t N, const float* w, double* y, cudaStream_t s) {
+  from_f32_kernel<<<node_blocks(3 * N), kNodeThreads, 0, s>>>(3 * N, w, y);
+}
+
+void launch_block_count(const ModelView& m, int n_blk, int32_t* counts, cudaStream_t s) {
+  block_count_kernel<<<n_blk, 256, 0, s>>>(m, counts);
+}
+void launch_block_fill(const ModelView& m, BlockView b, int32_t* nodes, uint16_t* lconn, int32_t* refcount,
+                       cudaStream_t s) {
+  block_fill_kernel<<<b.n_blk, 256, 0, s>>>(m, b, nodes, lconn, refcount);
+  if (m.F > 0) face_refcount_kernel<<<(unsigned)((m.F + 255) / 256), 256, 0, s>>>(m, refcount);
+}
+void launch_block_mark(const ModelView& m, BlockView b, int32_t* nodes, int32_t* refcount, int total,
+                       cudaStream_t s) {
+  (void)m;
+  (void)b;
+  block_mark_kernel<<<(total + 255) / 256, 256, 0, s>>>(total, nodes, refcount);
+}
+void launch_lo_convert(const ModelView& m, int half_geo, void* geo_lo, float* vol32, float* fgeo32,
+                       const double* dinv, float* dinv32, double* partials, InnerScalars* sc, cudaStream_t s) {
+  int64_t n = 9 * m.E;
+  if (6 * m.F > n) n = 6 * m.F;
+  if (6 * m.N > n) n = 6 * m.N;
+  const unsigned g = (unsigned)((n + 255) / 256);
+  if (half_geo)
+    lo_convert_kernel<__half><<<g, 256, 0, s>>>(m, (__half*)geo_lo, vol32, fgeo32, dinv, dinv32);
+  else
+    lo_convert_kernel<float><<<g, 256, 0, s>>>(m, (float*)geo_lo, vol32, fgeo32, dinv, dinv32);
+  dinv_mean_kernel<<<node_blocks(m.N), kNodeThreads, 0, s>>>(m.N, dinv, partials, sc);
+}
+void launch_inner_init(int64_t N, const double* r, const float* dinv32, float* s, float* y, float* t, void* d,
+                       int half_vec, float* w, double* partials, InnerScalars* sc, const CgScalars* cg,
+                       cudaStream_t st) {
+  if (half_vec)
+    inner_init_kernel<__half><<<node_blocks(N), kNodeThreads, 0, st>>>(N, r, dinv32, s, y, t, (__half*)d, w,
+                                                                       partials, sc, cg);
+  else
+    inner_init_kernel<float><<<node_blocks(N), kNodeThreads, 0, st>>>(N, r, dinv32, s, y, t, (float*)d, w,
+                                                                      partials, sc, cg);
+}
+void launch_ebe_lo(int half_geo, int half_vec, const void* lo_view, const void* d, float* w, double* partials,
+                   InnerScalars* sc, cudaStream_t st) {
+  if (half_geo) {
+    const LoView<__half>& m = *(const LoView<__half>*)lo_view;
+    const unsigned g = (unsigned)(m.blk.n_blk + (m.F + kElemThreads - 1) / kElemThreads);
+    const size_t smem = sizeof(float) * 6 * (size_t)m.blk.max_local;
+    if (half_vec)
+      ebe_lo_kernel<__half, __half><<<g, kElemThreads, smem, st>>>(m, (const __half*)d, w, partials, sc);
+    else
+      ebe_lo_kernel<__half, float><<<g, kElemThreads, smem, st>>>(m, (const float*)d, w, partials, sc);
+  } else {
+    const LoView<float>& m = *(const LoView<float>*)lo_view;
+    const unsigned g = (unsigned)(m.blk.n_blk + (m.F + kElemThreads - 1) / kElemThreads);
+    const size_t smem = sizeof(float) * 6 * (size_t)m.blk.max_local;
+    if (half_vec)
+      ebe_lo_kernel<float, __half><<<g, kElemThreads, smem, st>>>(m, (const __half*)d, w, partials, sc);
+    else
+      ebe_lo_kernel<float, float><<<g, kElemThreads, smem, st>>>(m, (const float*)d, w, partials, sc);
+  }
+}
+void launch_inner_update(int64_t N, float* y, float* s, float* t, const void* d, int half_vec, float* w,
+                         const float* dinv32, double* partials, InnerScalars* sc, cudaStream_t st) {
+  if (half_vec)
+    inner_update_kernel<__half><<<node_blocks(N), kNodeThreads, 0, st>>>(N, y, s, t, (const __half*)d, w, dinv32,
+                                                                         partials, sc);
+  else
+    inner_update_kernel<float><<<node_blocks(N), kNodeThreads, 0, st>>>(N, y, s, t, (const float*)d, w, dinv32,
+                                                                        partials, sc);
+}
+void launch_inner_dupdate(int64_t N, const float* t, void* d, int half_vec, const InnerScalars* sc,
+                          cudaStream_t st) {
+  if (half_vec)
+    inner_dupdate_kernel<__half><<<node_blocks(3 * N), kNodeThreads, 0, st>>>(N, t, (__half*)d, sc);
+  else
+    inner_dupdate_kernel<float><<<node_blocks(3 * N), kNodeThreads, 0, st>>>(N, t, (float*)d, sc);
+}
+void launch_fcg_residual(const ModelView& m, const double* b, double* q, double* r, double* partials, CgScalars* cg,
+                         cudaStream_t s) {
+  fcg_residual_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, b, q, r, partials, cg);
+}
+void launch_fcg_first(const ModelView& m, const float* y, const double* r, double* z, double* p, double* partials,
+                      CgScalars* cg, const InnerScalars* sc, cudaStream_t s) {
+  fcg_first_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, y, r, z, p, partials, cg, sc);
+}
+void launch_fcg_update(const ModelView& m, double* x, double* r, const double* p, const double* q, double* partials,
+                       CgScalars* cg, cudaStream_t s) {
+  fcg_update_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, x, r, p, q, partials, cg);
+}
+void launch_fcg_zbeta(const ModelView& m, const float* y, const double* r, const double* q, double* z,
+                      double* partials, CgScalars* cg, const InnerScalars* sc, cudaStream_t s) {
+  fcg_zbeta_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, y, r, q, z, partials, cg, sc);
+}
+void launch_fcg_pupdate(const ModelView& m, const double* z, double* p, double* q, const CgScalars* cg,
+                        cudaStream_t s) {
+  fcg_pupdate_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, z, p, q, cg);
+}
+
+}  // namespace gsw

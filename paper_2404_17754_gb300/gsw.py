@@ -241,12 +241,15 @@ class Model:
         return out
 
     def timing(self, enable=None):
-        """Start (True) / stop (False) / query (None) EBE launch timing; returns (ms, launches)."""
-        ms = C.c_double()
-        n = C.c_int64()
+        """Start (True) / stop (False) / query (None) operator launch timing.
+
+        Returns {"fp64": (ms, launches), "inner": (ms, launches)}.
+        """
+        ms = np.zeros(2)
+        n = np.zeros(2, dtype=np.int64)
         flag = -1 if enable is None else int(bool(enable))
-        self._c(self.ctx.lib.gsw_timing(self.ctx.h, self.id, flag, C.byref(ms), C.byref(n)))
-        return ms.value, n.value
+        self._c(self.ctx.lib.gsw_timing(self.ctx.h, self.id, flag, ms.ctypes.data_as(_dp), n.ctypes.data_as(_lp)))
+        return {"fp64": (float(ms[0]), int(n[0])), "inner": (float(ms[1]), int(n[1]))}
 
     def stats(self):
         s = Stats()
@@ -267,7 +270,7 @@ class Model:
         self._c(self.ctx.lib.gsw_set_state(self.ctx.h, self.id, pu, pv, pa, int(step)))
 
     def apply(self, which, x):
-        """y = A x (0), K x (1), M x (2) or C x (3) for a CUDA float64 tensor x [n_nodes, 3]."""
+        """y = A x (0), K x (1), M x (2), C x (3), or A x by the inner reduced-precision operator (4)."""
         torch = self.ctx._torch
         assert x.is_cuda and x.dtype == torch.float64 and x.is_contiguous() and x.numel() == 3 * self.n_nodes
         y = torch.empty_like(x)

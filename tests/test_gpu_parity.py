@@ -136,7 +136,8 @@ def test_checkpoint_restore_continues_identically(ctx):
     m.set_state(u, v, a, step)
     m.step(12)
     w_resumed = m.waveforms()
-    np.testing.assert_allclose(w_resumed[:, :, 12:], w_full[:, :, 12:], rtol=0, atol=1e-12 * np.abs(w_full).max())
+    # atomic scatter order differs run to run: equal up to rounding
+    np.testing.assert_allclose(w_resumed[:, :, 12:], w_full[:, :, 12:], rtol=0, atol=1e-10 * np.abs(w_full).max())
     m.free()
 
 
