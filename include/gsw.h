@@ -205,6 +205,36 @@ gsw_status gsw_misfit(gsw_ctx *ctx, int32_t n_rec, int32_t n_t, const double *G,
                       const double *obs, int32_t stride, int32_t n_shifts, double tau,
                       double *err, double *c_out);
 
+/* ---- misfit without device allocation ------------------------------------ */
+
+/* Same computation as gsw_misfit, for callers that cannot allocate device
+ * memory: for example code whose GPU memory is wholly owned by another
+ * allocator (a framework's caching pool or a fixed arena reserved at start-up),
+ * or a latency-critical loop where cudaMalloc / cudaFree would synchronise the
+ * device.  This paper has no counterpart of this entry point; it is a service
+ * of the library.
+ *
+ * All five array arguments are DEVICE pointers owned by the caller:
+ *  G_dev   [n_rec][3][3][n_t] and obs_dev [n_rec][3][n_t] (inputs, as in
+ *          gsw_misfit);
+ *  err_dev one double (output, Eq. (2));
+ *  c_dev   [3][n_shifts] doubles (output; may be NULL).
+ * The call only launches kernels on the context's stream and returns without
+ * waiting for them.  It calls no cudaMalloc / cudaFree and no allocating
+ * library routine: its working memory is one fixed array of about 0.67 MB
+ * (file-scope __device__ storage) that every GPU loading the library holds
+ * until the process exits.  Limits: n_shifts <= 64 (3 * n_shifts <= 192
+ * unknowns) and n_rec <= 1024; larger sizes return GSW_E_INVALID.
+ * The first call on each device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call on a device shares the one array and leaves its
+ * contents behind; the kernels overwrite every entry they read, so nothing is
+ * cleared between calls.  Calls that overlap on the GPU (other streams or
+ * other contexts on the same device) race on the array: serialise them. */
+gsw_status gsw_misfit_noalloc(gsw_ctx *ctx, int32_t n_rec, int32_t n_t, const double *G_dev,
+                              const double *obs_dev, int32_t stride, int32_t n_shifts,
+                              double tau, double *err_dev, double *c_dev);
+
 #ifdef __cplusplus
 }
 #endif

@@ -970,4 +970,20 @@ gsw_status gsw_misfit(gsw_ctx* ctx, int32_t n_rec, int32_t n_t, const double* G,
   return GSW_OK;
 }
 
+gsw_status gsw_misfit_noalloc(gsw_ctx* ctx, int32_t n_rec, int32_t n_t, const double* G_dev,
+                              const double* obs_dev, int32_t stride, int32_t n_shifts, double tau, double* err_dev,
+                              double* c_dev) {
+  if (!ctx || !G_dev || !obs_dev || !err_dev) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  if (n_rec <= 0 || n_t <= 0 || stride <= 0 || n_shifts <= 0 || !(tau >= 0.0))
+    return fail(ctx, GSW_E_INVALID, "need n_rec, n_t, stride, n_shifts > 0 and tau >= 0");
+  char msg[256] = {0};
+  cudaError_t ce = cudaSuccess;
+  int rc = misfit_run_noalloc(ctx->stream, ctx->device, n_rec, n_t, G_dev, obs_dev, stride, n_shifts, tau,
+                              err_dev, c_dev, msg, sizeof msg, &ce);
+  if (rc == 1) return fail(ctx, GSW_E_CUDA, "misfit (no allocation): %s (%s)", msg, cudaGetErrorString(ce));
+  if (rc == 3) return fail(ctx, GSW_E_INVALID, "misfit (no allocation): %s", msg);
+  return GSW_OK;
+}
+
 }  // extern "C"

@@ -18,6 +18,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "gsw_misfit.cuh"
 
 namespace gsw {
@@ -311,6 +313,77 @@ int misfit_run(MisfitWork& w, cudaStream_t s, int n_rec, int n_t, const double* 
 #undef CKR
   *err = w.host[0];
   if (c_out) memcpy(c_out, w.host + 1, sizeof(double) * P);
+  return 0;
+}
+
+// ---- allocation-free variant ---------------------------------------------------
+//
+// The working memory of gsw_misfit_noalloc lives in this fixed array instead of
+// a cudaMalloc'ed buffer.  Host code cannot pass `g_noalloc_scratch` to a
+// kernel directly (in host code the name denotes a host-side stand-in), so its
+// device address is looked up once per device with cudaGetSymbolAddress.
+namespace {
+constexpr int kNoAllocP = 3 * kNoAllocMaxShifts;
+constexpr int kNoAllocPairs = 3 * kNoAllocMaxRec;
+constexpr size_t kNoAllocDoubles =
+    3 * (size_t)kNoAllocPairs + 2 * (size_t)kNoAllocP * kNoAllocP + 2 * (size_t)kNoAllocP + 4;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+constexpr int kMaxDevices = 64;
+double* g_noalloc_addr[kMaxDevices] = {nullptr};
+std::mutex g_noalloc_mu;
+}  // namespace
+
+int misfit_run_noalloc(cudaStream_t s, int device, int n_rec, int n_t, const double* G_dev, const double* obs_dev,
+                       int stride, int L, double tau, double* err_dev, double* c_dev, char* msg, size_t msg_len,
+                       cudaError_t* ce) {
+  if (L > kNoAllocMaxShifts || n_rec > kNoAllocMaxRec) {
+    snprintf(msg, msg_len, "n_shifts %d / n_rec %d exceed the fixed working memory (max %d / %d)", L, n_rec,
+             kNoAllocMaxShifts, kNoAllocMaxRec);
+    return 3;
+  }
+  if (device < 0 || device >= kMaxDevices) {
+    snprintf(msg, msg_len, "device %d out of range", device);
+    return 3;
+  }
+  double* base;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) {
+        *ce = e;
+        snprintf(msg, msg_len, "cudaGetSymbolAddress of the fixed working memory");
+        return 1;
+      }
+      g_noalloc_addr[device] = (double*)p;
+    }
+    base = g_noalloc_addr[device];
+  }
+  const int P = 3 * L;
+  const int n_pairs = 3 * n_rec;
+  double* energy = base;
+  double* wt = energy + n_pairs;
+  double* ratio = wt + n_pairs;
+  double* A = ratio + n_pairs;
+  double* V = A + (size_t)P * P;
+  double* b = V + (size_t)P * P;
+  double* c = b + P;
+  double* scal = c + P;  // n_kept, err, sweeps
+  energy_kernel<<<n_pairs, kT, 0, s>>>(obs_dev, n_t, energy);
+  weights_kernel<<<1, kT, 0, s>>>(energy, n_pairs, wt, scal);
+  assemble_A_kernel<<<dim3(P, P), kT, 0, s>>>(G_dev, wt, n_rec, n_t, stride, L, A);
+  assemble_b_kernel<<<P, kT, 0, s>>>(G_dev, obs_dev, wt, n_rec, n_t, stride, L, b);
+  jacobi_kernel<<<1, 1024, 0, s>>>(A, V, P, 60, (int*)(scal + 2));
+  pinv_solve_kernel<<<1, kT, 0, s>>>(A, V, b, P, tau, c_dev ? c_dev : c);
+  err_kernel<<<n_pairs, kT, 0, s>>>(G_dev, obs_dev, wt, c_dev ? c_dev : c, n_t, stride, L, ratio);
+  err_final_kernel<<<1, kT, 0, s>>>(ratio, n_pairs, scal, err_dev);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    *ce = e;
+    snprintf(msg, msg_len, "kernel launch");
+    return 1;
+  }
   return 0;
 }
 

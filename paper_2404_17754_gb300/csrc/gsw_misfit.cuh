@@ -20,4 +20,12 @@ int misfit_run(MisfitWork& w, cudaStream_t s, int n_rec, int n_t, const double* 
                size_t msg_len, cudaError_t* ce);
 void misfit_free(MisfitWork& w, cudaStream_t s);
 
+// Allocation-free variant: device inputs and outputs, working memory in a
+// fixed file-scope __device__ array.
+constexpr int kNoAllocMaxShifts = 64;
+constexpr int kNoAllocMaxRec = 1024;
+int misfit_run_noalloc(cudaStream_t s, int device, int n_rec, int n_t, const double* G_dev, const double* obs_dev,
+                       int stride, int n_shifts, double tau, double* err_dev, double* c_dev, char* msg,
+                       size_t msg_len, cudaError_t* ce);
+
 }  // namespace gsw

@@ -73,6 +73,8 @@ SIGNATURES = {
     "gsw_read_receivers": (C.c_int, [C.c_void_p, C.c_int32, _ip, _dp]),
     "gsw_misfit": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, _dp, _dp, C.c_int32, C.c_int32, C.c_double,
                              _dp, _dp]),
+    "gsw_misfit_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
+                                     C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -183,6 +185,24 @@ class Context:
         self._check(self.lib.gsw_misfit(self.h, n_rec, n_t, pG, pO, stride, n_shifts, tau, C.byref(err),
                                         c.ctypes.data_as(_dp)))
         return err.value, c
+
+
+    def misfit_noalloc(self, G_dev, obs_dev, stride, n_shifts, err_dev, c_dev=None, tau=1e-10):
+        """Allocation-free misfit on caller-owned CUDA float64 tensors.
+
+        For callers that cannot allocate device memory: G_dev [n_rec, 3, 3, n_t],
+        obs_dev [n_rec, 3, n_t] are inputs, err_dev (1 element) and c_dev
+        [3, n_shifts] (optional) receive the results.  Nothing is allocated; the
+        work is queued on the context's stream.  Limits: n_shifts <= 64, n_rec <= 1024.
+        """
+        n_rec, n_t = obs_dev.shape[0], obs_dev.shape[2]
+        for t in (G_dev, obs_dev, err_dev) + ((c_dev,) if c_dev is not None else ()):
+            assert t.is_cuda and t.is_contiguous() and t.dtype == self._torch.float64
+        assert tuple(G_dev.shape) == (n_rec, 3, 3, n_t)
+        self._check(self.lib.gsw_misfit_noalloc(self.h, n_rec, n_t, C.c_void_p(G_dev.data_ptr()),
+                                                C.c_void_p(obs_dev.data_ptr()), stride, n_shifts, tau,
+                                                C.c_void_p(err_dev.data_ptr()),
+                                                C.c_void_p(c_dev.data_ptr() if c_dev is not None else 0)))
 
 
 class Model:
