@@ -341,7 +341,7 @@ gsw_status build_lo(gsw_ctx* ctx, Model* m, int half) {
   cudaStream_t s = ctx->stream;
   ModelView mv = m->view();
   if (!m->lo_ready) {
-    m->n_blk = (int)((m->E + kElemThreads - 1) / kElemThreads);
+    m->n_blk = (int)((m->E + kLoBlock - 1) / kLoBlock);
     int32_t* counts = nullptr;
     TRY(alloc_into(ctx, m, &counts, (size_t)m->n_blk));
     launch_block_count(mv, m->n_blk, counts, s);
@@ -384,16 +384,16 @@ gsw_status build_lo(gsw_ctx* ctx, Model* m, int half) {
   if (m->geo_lo == nullptr || m->lo_half != half) {
     // (re)allocate the precision-dependent buffers; the old ones stay owned by the model
     m->geo_lo = dev_alloc(ctx, m, (half ? sizeof(__half) : sizeof(float)) * 9 * (size_t)m->E);
-    m->d_lo = dev_alloc(ctx, m, (half ? sizeof(__half) : sizeof(float)) * 3 * (size_t)m->N);
+    m->d_lo = dev_alloc(ctx, m, (half ? sizeof(__half) : sizeof(float)) * 4 * (size_t)m->N);
     if (!m->geo_lo || !m->d_lo) return fail(ctx, GSW_E_NOMEM, "device allocation failed (inner solve)");
     m->lo_half = half;
   }
   launch_lo_convert(mv, half, m->geo_lo, m->vol32, m->fgeo32, m->dinv, m->dinv32, m->partials, m->isc, s);
   CK(cudaGetLastError());
   BlockView bv = {m->n_blk, m->max_local, m->blk_ptr, m->blk_nodes, m->lconn};
-  m->lo_f = LoView<float>{m->N, m->E, m->F, bv, (const float*)m->geo_lo, m->vol32, m->emat, m->mat, m->fnode,
+  m->lo_f = LoView<float>{m->N, m->E, m->F, m->n_mat, bv, (const float*)m->geo_lo, m->vol32, m->emat, m->mat, m->fnode,
                           m->fgeo32, m->dt};
-  m->lo_h = LoView<__half>{m->N, m->E, m->F, bv, (const __half*)m->geo_lo, m->vol32, m->emat, m->mat, m->fnode,
+  m->lo_h = LoView<__half>{m->N, m->E, m->F, m->n_mat, bv, (const __half*)m->geo_lo, m->vol32, m->emat, m->mat, m->fnode,
                            m->fgeo32, m->dt};
   return GSW_OK;
 }
@@ -431,16 +431,19 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
   cudaStream_t s = ctx->stream;
   ModelView mv = m->view();
   const double force = 2.0 * m->input[(size_t)m->step];
-  CK(cudaMemsetAsync(m->b, 0, sizeof(double) * 3 * (size_t)m->N, s));
-  launch_ebe(kModeRhs, mv, m->u, m->v, m->a, m->b, force, m->dir, nullptr, nullptr, s);
+  // ||b|| from an FP32 right-hand side (w32 is free scratch between solves)
+  CK(cudaMemsetAsync(m->w32, 0, sizeof(float) * 3 * (size_t)m->N, s));
+  launch_rhs_f32(mv, m->u, m->v, m->a, m->w32, force, m->dir, s);
   CgScalars init = {};
   init.tol = m->opts.tol;
   init.max_iter = m->opts.max_iter;
   CK(cudaMemcpyAsync(m->cg, &init, sizeof(CgScalars), cudaMemcpyHostToDevice, s));
-  launch_cg_init(mv, m->b, m->v, m->a, m->x, m->q, m->partials, m->cg, s);
-  launch_ebe(kModeA, mv, m->x, nullptr, nullptr, m->q, 0.0, 0, nullptr, m->cg, s);
-  launch_fcg_residual(mv, m->b, m->q, m->r, m->partials, m->cg, s);
-  int64_t launches = 5;
+  // predictor and predicted state (u~ in p, v~ in z), r = q = 0
+  launch_cg_init_mixed(mv, m->w32, m->u, m->v, m->a, m->x, m->p, m->z, m->r, m->q, m->partials, m->cg, s);
+  // FP64 residual at the predictor in one element-by-element pass
+  launch_ebe(kModeRes, mv, m->p, m->z, m->a, m->r, force, m->dir, nullptr, m->cg, s);
+  launch_cg_rnorm(mv, m->r, m->partials, m->cg, s);
+  int64_t launches = 4;
   if (m->timing && (int)m->ev_lo.size() < 2 * m->opts.inner_iters) {
     for (int i = (int)m->ev_lo.size(); i < 2 * m->opts.inner_iters; ++i) {
       cudaEvent_t e;

@@ -9,6 +9,9 @@ constexpr int kMaxMat = 32;        // materials (layers) per model
 constexpr int kNodeThreads = 256;  // node-wise kernels
 constexpr int kElemThreads = 128;  // element-by-element kernels
 constexpr int kMaxNodeBlocks = 152 * 8;
+constexpr int kLoBlock = 32;   // elements per block of the reduced-precision operator (one warp)
+constexpr int kLoWarps = 4;    // blocks (warps) per CTA
+constexpr int kLoThreads = kLoBlock * kLoWarps;
 
 // Per-material coefficients. lam, mu, rho from (Vp, Vs, rho); alpha, beta the
 // Rayleigh fit; cK = 1 + 2 beta/dt and cM = 4/dt^2 + 2 alpha/dt scale the
@@ -63,7 +66,7 @@ struct InnerScalars {
 };
 
 // Element blocks with local node numbering: block b holds elements
-// [b * kElemThreads, (b + 1) * kElemThreads); its unique nodes are
+// [b * kLoBlock, (b + 1) * kLoBlock); its unique nodes are
 // nodes[ptr[b] .. ptr[b+1]) (bit 31 set: no other block and no absorbing face
 // touches the node), and lconn[k * E + e] is the local index of node k of e.
 struct BlockView {
@@ -79,6 +82,7 @@ struct BlockView {
 template <typename SG>
 struct LoView {
   int64_t N, E, F;
+  int n_mat;
   BlockView blk;
   const SG* geo;            // [9][E] barycentric gradients
   const float* vol;         // [E] element volumes
@@ -89,7 +93,7 @@ struct LoView {
   double dt;
 };
 
-enum EbeMode { kModeA = 0, kModeK = 1, kModeM = 2, kModeC = 3, kModeRhs = 4 };
+enum EbeMode { kModeA = 0, kModeK = 1, kModeM = 2, kModeC = 3, kModeRhs = 4, kModeRes = 5 };
 
 // ---- kernels (gsw_kernels.cu) -------------------------------------------------
 void launch_geometry(const ModelView& m, const double* xyz, double px, double py, double* geo,
@@ -109,6 +113,12 @@ void launch_ebe(int mode, const ModelView& m, const double* x, const double* v, 
                 cudaStream_t s);
 void launch_cg_init(const ModelView& m, const double* b, const double* v, const double* a,
                     double* x, double* q, double* partials, CgScalars* cg, cudaStream_t s);
+void launch_rhs_f32(const ModelView& m, const double* u, const double* v, const double* a, float* b32,
+                    double force, int dir, cudaStream_t s);
+void launch_cg_init_mixed(const ModelView& m, const float* b32, const double* u, const double* v, const double* a,
+                          double* x, double* ut, double* vt, double* r, double* q, double* partials, CgScalars* cg,
+                          cudaStream_t s);
+void launch_cg_rnorm(const ModelView& m, const double* r, double* partials, CgScalars* cg, cudaStream_t s);
 void launch_cg_residual(const ModelView& m, const double* b, double* q, double* r, double* z,
                         double* p, const double* dinv, double* partials, CgScalars* cg,
                         cudaStream_t s);
@@ -135,6 +145,7 @@ void launch_lo_convert(const ModelView& m, int half_geo, void* geo_lo, float* vo
                        const double* dinv, float* dinv32, double* partials, InnerScalars* sc,
                        cudaStream_t s);
 // inner solve: half_vec selects __half storage of the search direction d
+// (padded to 4 entries per node)
 void launch_inner_init(int64_t N, const double* r, const float* dinv32, float* s, float* y,
                        float* t, void* d, int half_vec, float* w, double* partials,
                        InnerScalars* sc, const CgScalars* cg, cudaStream_t st);

@@ -315,6 +315,9 @@ __global__ void receiver_weights_kernel(ModelView m, const double* __restrict__ 
 //   kModeA   y = A x               (+ partial x.y when partials != nullptr)
 //   kModeK   y = K x,  kModeM y = M x,  kModeC y = C x
 //   kModeRhs y = f - K u + C v + M (a + (4/dt) v)  with x = u
+//   kModeRes y = f - K u~ - C v~ - M a  with x = u~ = u + dt v + dt^2/2 a,
+//            vv = v~ = v + dt a: the Newmark residual b - A du0 at the predictor
+//            du0 = dt v + dt^2/2 a, from a single stiffness application
 template <int MODE>
 __global__ void __launch_bounds__(kElemThreads) ebe_kernel(ModelView m, const double* __restrict__ x,
                                                             const double* __restrict__ vv,
@@ -349,6 +352,9 @@ __global__ void __launch_bounds__(kElemThreads) ebe_kernel(ModelView m, const do
     } else if (MODE == kModeC) {
       ks = mc.beta;
       ms = mc.alpha;
+    } else if (MODE == kModeRes) {
+      ks = -1.0;
+      ms = -1.0;
     } else {
       ks = 1.0;
       ms = 1.0;
@@ -362,6 +368,12 @@ __global__ void __launch_bounds__(kElemThreads) ebe_kernel(ModelView m, const do
       for (int k = 0; k < 10; ++k)
 #pragma unroll
         for (int i = 0; i < 3; ++i) w[k][i] = fma(mc.beta, vv[3 * nd[k] + i], -x[3 * nd[k] + i]);
+    } else if (MODE == kModeRes) {
+      // residual at the predictor: stiffness acts on u~ + beta v~ (x = u~, vv = v~)
+#pragma unroll
+      for (int k = 0; k < 10; ++k)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) w[k][i] = fma(mc.beta, vv[3 * nd[k] + i], x[3 * nd[k] + i]);
     } else {
 #pragma unroll
       for (int k = 0; k < 10; ++k)
@@ -376,9 +388,9 @@ __global__ void __launch_bounds__(kElemThreads) ebe_kernel(ModelView m, const do
 #pragma unroll
         for (int i = 0; i < 3; ++i) f[k][i] = 0.0;
     }
-    if (MODE == kModeRhs) {
-      // mass acts on a + (4/dt + alpha) v
-      const double cv = 4.0 / m.dt + mc.alpha;
+    if (MODE == kModeRhs || MODE == kModeRes) {
+      // mass acts on a + (4/dt + alpha) v (right-hand side) or a + alpha v~ (residual)
+      const double cv = (MODE == kModeRhs) ? 4.0 / m.dt + mc.alpha : mc.alpha;
 #pragma unroll
       for (int k = 0; k < 10; ++k)
 #pragma unroll
@@ -396,7 +408,7 @@ __global__ void __launch_bounds__(kElemThreads) ebe_kernel(ModelView m, const do
     const int64_t fc = t - m.E;
     const double tag = m.fgeo[5 * m.F + fc];
     if (tag > 0.5) {
-      const double sc = (MODE == kModeA) ? 2.0 / m.dt : 1.0;
+      const double sc = (MODE == kModeA) ? 2.0 / m.dt : (MODE == kModeRes ? -1.0 : 1.0);
       const double As = sc * m.fgeo[fc] / 180.0, Ad = sc * m.fgeo[m.F + fc] / 180.0;
       const double n[3] = {m.fgeo[2 * m.F + fc], m.fgeo[3 * m.F + fc], m.fgeo[4 * m.F + fc]};
       int64_t nd[6];
@@ -404,7 +416,7 @@ __global__ void __launch_bounds__(kElemThreads) ebe_kernel(ModelView m, const do
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
         nd[k] = m.fnode[k * m.F + fc];
-        const double* src = (MODE == kModeRhs) ? vv : x;
+        const double* src = (MODE == kModeRhs || MODE == kModeRes) ? vv : x;
 #pragma unroll
         for (int i = 0; i < 3; ++i) xin[k][i] = src[3 * nd[k] + i];
         const double dn = n[0] * xin[k][0] + n[1] * xin[k][1] + n[2] * xin[k][2];
@@ -424,11 +436,12 @@ __global__ void __launch_bounds__(kElemThreads) ebe_kernel(ModelView m, const do
         yf[4][i] = 16.0 * (z[4][i] + Ze) - 4.0 * z[0][i];
         yf[5][i] = 16.0 * (z[5][i] + Ze) - 4.0 * z[1][i];
       }
-      if (MODE == kModeRhs && tag < 1.5) {
+      if ((MODE == kModeRhs || MODE == kModeRes) && tag < 1.5) {
         // base force 2 p C_base e_dir: int N_a dA = A/3 at edge nodes, 0 at vertices
         const double nd_ = dir == 0 ? n[0] : (dir == 1 ? n[1] : n[2]);
-        const double fz[3] = {As * (dir == 0) + Ad * nd_ * n[0], As * (dir == 1) + Ad * nd_ * n[1],
-                              As * (dir == 2) + Ad * nd_ * n[2]};
+        const double Af = m.fgeo[fc] / 180.0, Adf = m.fgeo[m.F + fc] / 180.0;
+        const double fz[3] = {Af * (dir == 0) + Adf * nd_ * n[0], Af * (dir == 1) + Adf * nd_ * n[1],
+                              Af * (dir == 2) + Adf * nd_ * n[2]};
 #pragma unroll
         for (int k = 3; k < 6; ++k)
 #pragma unroll
@@ -446,6 +459,83 @@ __global__ void __launch_bounds__(kElemThreads) ebe_kernel(ModelView m, const do
   if (MODE == kModeA && partials != nullptr) {
     double vals[1] = {dot}, out[1];
     if (last_block_reduce<1>(vals, partials, &cg->counter, out) && threadIdx.x == 0) cg->pq = out[0];
+  }
+}
+
+// Right-hand side b = f - K u + C v + M (a + (4/dt) v) in FP32 arithmetic.
+// Only ||b|| is taken from it (the scale of the relative-residual test), so
+// FP32 accuracy suffices; the FP64 solve never uses b itself.
+__global__ void __launch_bounds__(kElemThreads) rhs_f32_kernel(ModelView m, const double* __restrict__ u,
+                                                              const double* __restrict__ vv,
+                                                              const double* __restrict__ aa, float* b,
+                                                              double force, int dir) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < m.E) {
+    const int64_t e = t;
+    int64_t nd[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) nd[k] = m.conn[k * m.E + e];
+    float g[3][3];
+#pragma unroll
+    for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) g[mm][i] = (float)m.geo[(3 * mm + i) * m.E + e];
+    const double V = m.geo[9 * m.E + e];
+    const MatCoef mc = m.mat[m.emat[e]];
+    const float lamS = (float)(mc.lam * V / 20.0), muS = (float)(mc.mu * V / 20.0);
+    const float mS = (float)(mc.rho * V / 420.0);
+    float w[10][3], f[10][3];
+#pragma unroll
+    for (int k = 0; k < 10; ++k)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) w[k][i] = (float)fma(mc.beta, vv[3 * nd[k] + i], -u[3 * nd[k] + i]);
+    stiffness_apply<float>(w, g, lamS, muS, f);
+    const double cv = 4.0 / m.dt + mc.alpha;
+#pragma unroll
+    for (int k = 0; k < 10; ++k)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) w[k][i] = (float)fma(cv, vv[3 * nd[k] + i], aa[3 * nd[k] + i]);
+    mass_apply<float>(w, mS, f);
+#pragma unroll
+    for (int k = 0; k < 10; ++k)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) atomicAdd(b + 3 * nd[k] + i, f[k][i]);
+  } else if (t < m.E + m.F) {
+    const int64_t fc = t - m.E;
+    const double tag = m.fgeo[5 * m.F + fc];
+    if (tag > 0.5) {
+      const double As = m.fgeo[fc] / 180.0, Ad = m.fgeo[m.F + fc] / 180.0;
+      const double n[3] = {m.fgeo[2 * m.F + fc], m.fgeo[3 * m.F + fc], m.fgeo[4 * m.F + fc]};
+      int64_t nd[6];
+      float z[6][3];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        nd[k] = m.fnode[k * m.F + fc];
+        const float x0 = (float)vv[3 * nd[k]], x1 = (float)vv[3 * nd[k] + 1], x2 = (float)vv[3 * nd[k] + 2];
+        const float dn = (float)n[0] * x0 + (float)n[1] * x1 + (float)n[2] * x2;
+        z[k][0] = (float)As * x0 + (float)Ad * dn * (float)n[0];
+        z[k][1] = (float)As * x1 + (float)Ad * dn * (float)n[1];
+        z[k][2] = (float)As * x2 + (float)Ad * dn * (float)n[2];
+      }
+      const double nd_ = dir == 0 ? n[0] : (dir == 1 ? n[1] : n[2]);
+      const float fz[3] = {(float)(force * 60.0 * (As * (dir == 0) + Ad * nd_ * n[0])),
+                           (float)(force * 60.0 * (As * (dir == 1) + Ad * nd_ * n[1])),
+                           (float)(force * 60.0 * (As * (dir == 2) + Ad * nd_ * n[2]))};
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const float Zv = z[0][i] + z[1][i] + z[2][i];
+        const float Ze = z[3][i] + z[4][i] + z[5][i];
+        float yf[6];
+        yf[0] = 7.f * z[0][i] - Zv - 4.f * z[4][i];
+        yf[1] = 7.f * z[1][i] - Zv - 4.f * z[5][i];
+        yf[2] = 7.f * z[2][i] - Zv - 4.f * z[3][i];
+        yf[3] = 16.f * (z[3][i] + Ze) - 4.f * z[2][i] + (tag < 1.5 ? fz[i] : 0.f);
+        yf[4] = 16.f * (z[4][i] + Ze) - 4.f * z[0][i] + (tag < 1.5 ? fz[i] : 0.f);
+        yf[5] = 16.f * (z[5][i] + Ze) - 4.f * z[1][i] + (tag < 1.5 ? fz[i] : 0.f);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) atomicAdd(b + 3 * nd[k] + i, yf[k]);
+      }
+    }
   }
 }
 
@@ -481,6 +571,61 @@ __global__ void cg_init_kernel(int64_t N, const double* __restrict__ b, const do
     cg->done = (out[0] == 0.0);
     if (!isfinite(out[0])) {
       cg->status = -5;
+      cg->done = 1;
+    }
+  }
+}
+
+// Mixed-mode start of a step: ||b||^2 from the FP32 right-hand side,
+// predictor du0 = dt v + dt^2/2 a, predicted state u~ = u + du0 and
+// v~ = v + dt a (inputs of the single-pass residual), r = q = 0.
+__global__ void cg_init_mixed_kernel(int64_t N, const float* __restrict__ b32, const double* __restrict__ u,
+                                     const double* __restrict__ v, const double* __restrict__ a, double dt,
+                                     double* __restrict__ x, double* __restrict__ ut, double* __restrict__ vt,
+                                     double* __restrict__ r, double* __restrict__ q, double* partials,
+                                     CgScalars* cg) {
+  double bb = 0.0;
+  const double h = 0.5 * dt * dt;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double bi = (double)b32[i];
+    bb = fma(bi, bi, bb);
+    const double vi = v[i], ai = a[i];
+    const double x0 = fma(dt, vi, h * ai);
+    x[i] = x0;
+    ut[i] = u[i] + x0;
+    vt[i] = fma(dt, ai, vi);
+    r[i] = 0.0;
+    q[i] = 0.0;
+  }
+  double vals[1] = {bb}, out[1];
+  if (last_block_reduce<1>(vals, partials, &cg->counter, out) && threadIdx.x == 0) {
+    cg->bb = out[0];
+    cg->iter = 0;
+    cg->status = 0;
+    cg->relres = 0.0;
+    cg->zero_rhs = (out[0] == 0.0);
+    cg->done = (out[0] == 0.0);
+    if (!isfinite(out[0])) {
+      cg->status = -5;
+      cg->done = 1;
+    }
+  }
+}
+
+// rr = r . r of the residual produced by the single-pass residual kernel.
+__global__ void cg_rnorm_kernel(int64_t N, const double* __restrict__ r, double* partials, CgScalars* cg) {
+  if (((volatile CgScalars*)cg)->done) return;
+  double rr = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N; i += (int64_t)gridDim.x * blockDim.x)
+    rr = fma(r[i], r[i], rr);
+  double vals[1] = {rr}, out[1];
+  if (last_block_reduce<1>(vals, partials, &cg->counter, out) && threadIdx.x == 0) {
+    cg->rr = out[0];
+    cg->relres = sqrt(out[0] / cg->bb);
+    if (!isfinite(out[0])) {
+      cg->status = -5;
+      cg->done = 1;
+    } else if (cg->relres <= cg->tol) {
       cg->done = 1;
     }
   }
@@ -661,6 +806,9 @@ void launch_ebe(int mode, const ModelView& m, const double* x, const double* v, 
     case kModeC:
       ebe_kernel<kModeC><<<nb, kElemThreads, 0, s>>>(m, x, v, a, y, force, dir, nullptr, nullptr);
       break;
+    case kModeRes:
+      ebe_kernel<kModeRes><<<nb, kElemThreads, 0, s>>>(m, x, v, a, y, force, dir, nullptr, nullptr);
+      break;
     default:
       ebe_kernel<kModeRhs><<<nb, kElemThreads, 0, s>>>(m, x, v, a, y, force, dir, nullptr, nullptr);
       break;
@@ -669,6 +817,20 @@ void launch_ebe(int mode, const ModelView& m, const double* x, const double* v, 
 void launch_cg_init(const ModelView& m, const double* b, const double* v, const double* a,
                     double* x, double* q, double* partials, CgScalars* cg, cudaStream_t s) {
   cg_init_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, b, v, a, m.dt, x, q, partials, cg);
+}
+void launch_rhs_f32(const ModelView& m, const double* u, const double* v, const double* a, float* b32,
+                    double force, int dir, cudaStream_t s) {
+  const int nb = ebe_blocks(m);
+  if (nb > 0) rhs_f32_kernel<<<nb, kElemThreads, 0, s>>>(m, u, v, a, b32, force, dir);
+}
+void launch_cg_init_mixed(const ModelView& m, const float* b32, const double* u, const double* v, const double* a,
+                          double* x, double* ut, double* vt, double* r, double* q, double* partials, CgScalars* cg,
+                          cudaStream_t s) {
+  cg_init_mixed_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, b32, u, v, a, m.dt, x, ut, vt, r, q,
+                                                                       partials, cg);
+}
+void launch_cg_rnorm(const ModelView& m, const double* r, double* partials, CgScalars* cg, cudaStream_t s) {
+  cg_rnorm_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, r, partials, cg);
 }
 void launch_cg_residual(const ModelView& m, const double* b, double* q, double* r, double* z,
                         double* p, const double* dinv, double* partials, CgScalars* cg,

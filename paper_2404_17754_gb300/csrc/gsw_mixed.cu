@@ -37,15 +37,32 @@ __device__ __forceinline__ float from_f<float>(float x) { return x; }
 template <>
 __device__ __forceinline__ __half from_f<__half>(float x) { return __float2half_rn(x); }
 
-constexpr int kSortN = 2048;  // >= 10 * kElemThreads, power of two
+// Search-direction storage is padded to 4 entries per node so that one
+// 8-byte (FP16) or 16-byte (FP32) load fetches a node.
+__device__ __forceinline__ void load3(const float* p, float& a, float& b, float& c) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = v.x;
+  b = v.y;
+  c = v.z;
+}
+__device__ __forceinline__ void load3(const __half* p, float& a, float& b, float& c) {
+  const uint2 v = *reinterpret_cast<const uint2*>(p);
+  const __half2 h0 = *reinterpret_cast<const __half2*>(&v.x);
+  const __half2 h1 = *reinterpret_cast<const __half2*>(&v.y);
+  a = __low2float(h0);
+  b = __high2float(h0);
+  c = __low2float(h1);
+}
+
+constexpr int kSortN = 512;  // >= 10 * kLoBlock, power of two
 
 // ------------------------------------------------------------------------------
 // Element blocks: unique nodes per block via an in-shared-memory bitonic sort
 // ------------------------------------------------------------------------------
 
 __device__ void load_sorted_block(const ModelView& m, int b, int* keys) {
-  const int64_t e0 = (int64_t)b * kElemThreads;
-  const int ne = (int)((m.E - e0) < kElemThreads ? (m.E - e0) : kElemThreads);
+  const int64_t e0 = (int64_t)b * kLoBlock;
+  const int ne = (int)((m.E - e0) < kLoBlock ? (m.E - e0) : kLoBlock);
   for (int i = threadIdx.x; i < kSortN; i += blockDim.x) {
     int v = 0x7fffffff;
     if (i < 10 * ne) {
@@ -97,11 +114,13 @@ __global__ void block_fill_kernel(ModelView m, BlockView bv, int32_t* nodes, uin
   // inclusive scan of flags (Hillis-Steele, in place with a temporary)
   for (int off = 1; off < kSortN; off <<= 1) {
     int v[kSortN / 256];
+#pragma unroll
     for (int j = 0; j < kSortN / 256; ++j) {
       const int i = threadIdx.x + j * 256;
       v[j] = (i < kSortN && i >= off) ? flag[i - off] : 0;
     }
     __syncthreads();
+#pragma unroll
     for (int j = 0; j < kSortN / 256; ++j) {
       const int i = threadIdx.x + j * 256;
       if (i < kSortN) flag[i] += v[j];
@@ -122,8 +141,8 @@ __global__ void block_fill_kernel(ModelView m, BlockView bv, int32_t* nodes, uin
   // compact the unique keys to the front of `keys` (reuse flag as storage)
   for (int i = threadIdx.x; i < nu; i += blockDim.x) flag[i] = nodes[base + i];
   __syncthreads();
-  const int64_t e0 = (int64_t)b * kElemThreads;
-  const int ne = (int)((m.E - e0) < kElemThreads ? (m.E - e0) : kElemThreads);
+  const int64_t e0 = (int64_t)b * kLoBlock;
+  const int ne = (int)((m.E - e0) < kLoBlock ? (m.E - e0) : kLoBlock);
   for (int i = threadIdx.x; i < 10 * ne; i += blockDim.x) {
     const int k = i / ne, el = i % ne;
     const int g = m.conn[(int64_t)k * m.E + e0 + el];
@@ -176,71 +195,92 @@ __global__ void dinv_mean_kernel(int64_t N, const double* __restrict__ dinv, dou
 // Reduced-precision element-by-element product w = A d (+ partial d . w)
 // ------------------------------------------------------------------------------
 
+// Each warp owns one block of kLoBlock consecutive elements: it gathers the
+// block's unique nodes into its own shared-memory slice, applies the elements
+// (one per lane) with shared-memory atomics, and writes the block's nodes
+// back; warps never wait for one another, so gather, compute and write-back
+// phases of different warps overlap.  CTAs after the element CTAs apply the
+// absorbing faces with global atomics.
 template <typename SG, typename SD>
-__global__ void __launch_bounds__(kElemThreads) ebe_lo_kernel(LoView<SG> m, const SD* __restrict__ d,
-                                                               float* __restrict__ w, double* partials,
-                                                               InnerScalars* sc) {
+__global__ void __launch_bounds__(kLoThreads) ebe_lo_kernel(LoView<SG> m, const SD* __restrict__ d,
+                                                             float* __restrict__ w, double* partials,
+                                                             InnerScalars* sc) {
   extern __shared__ float sm[];
-  float* xs = sm;
-  float* ys = sm + 3 * m.blk.max_local;
-  const int b = blockIdx.x;
+  __shared__ float matc[kMaxMat][3];
+  if (threadIdx.x < m.n_mat) {
+    const MatCoef& c = m.mat[threadIdx.x];
+    matc[threadIdx.x][0] = (float)(c.cK * c.lam / 20.0);
+    matc[threadIdx.x][1] = (float)(c.cK * c.mu / 20.0);
+    matc[threadIdx.x][2] = (float)(c.cM * c.rho / 420.0);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_elem_ctas = (m.blk.n_blk + kLoWarps - 1) / kLoWarps;
   float dot = 0.f;
-  if (b < m.blk.n_blk) {
-    const int n0 = m.blk.ptr[b], nn = m.blk.ptr[b + 1] - n0;
-    for (int i = threadIdx.x; i < nn; i += blockDim.x) {
-      const int64_t g = m.blk.nodes[n0 + i] & 0x7fffffff;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        xs[3 * i + c] = to_f(d[3 * g + c]);
-        ys[3 * i + c] = 0.f;
+  if ((int)blockIdx.x < n_elem_ctas) {
+    const int b = blockIdx.x * kLoWarps + warp;
+    if (b < m.blk.n_blk) {
+      float* xs = sm + (size_t)warp * 6 * m.blk.max_local;
+      float* ys = xs + 3 * m.blk.max_local;
+      const int n0 = m.blk.ptr[b], nn = m.blk.ptr[b + 1] - n0;
+      for (int i = lane; i < nn; i += 32) {
+        const int64_t g = m.blk.nodes[n0 + i] & 0x7fffffff;
+        float a0, a1, a2;
+        load3(d + 4 * g, a0, a1, a2);
+        xs[3 * i] = a0;
+        xs[3 * i + 1] = a1;
+        xs[3 * i + 2] = a2;
+        ys[3 * i] = 0.f;
+        ys[3 * i + 1] = 0.f;
+        ys[3 * i + 2] = 0.f;
       }
-    }
-    __syncthreads();
-    const int64_t e = (int64_t)b * kElemThreads + threadIdx.x;
-    if (e < m.E) {
-      int lc[10];
+      __syncwarp();
+      const int64_t e = (int64_t)b * kLoBlock + lane;
+      if (e < m.E) {
+        int lc[10];
 #pragma unroll
-      for (int k = 0; k < 10; ++k) lc[k] = m.blk.lconn[k * m.E + e];
-      float g[3][3];
+        for (int k = 0; k < 10; ++k) lc[k] = m.blk.lconn[k * m.E + e];
+        float g[3][3];
 #pragma unroll
-      for (int mm = 0; mm < 3; ++mm)
+        for (int mm = 0; mm < 3; ++mm)
 #pragma unroll
-        for (int i = 0; i < 3; ++i) g[mm][i] = to_f(m.geo[(3 * mm + i) * m.E + e]);
-      const float V = m.vol[e];
-      const MatCoef& mc = m.mat[m.emat[e]];
-      const float lamS = (float)(mc.cK * mc.lam * (1.0 / 20.0)) * V;
-      const float muS = (float)(mc.cK * mc.mu * (1.0 / 20.0)) * V;
-      const float mS = (float)(mc.cM * mc.rho * (1.0 / 420.0)) * V;
-      float wv[10][3], f[10][3];
+          for (int i = 0; i < 3; ++i) g[mm][i] = to_f(m.geo[(3 * mm + i) * m.E + e]);
+        const float V = m.vol[e];
+        const int mt = m.emat[e];
+        const float lamS = matc[mt][0] * V, muS = matc[mt][1] * V, mS = matc[mt][2] * V;
+        float wv[10][3], f[10][3];
 #pragma unroll
-      for (int k = 0; k < 10; ++k)
+        for (int k = 0; k < 10; ++k)
 #pragma unroll
-        for (int i = 0; i < 3; ++i) wv[k][i] = xs[3 * lc[k] + i];
-      stiffness_apply<float>(wv, g, lamS, muS, f);
-      mass_apply<float>(wv, mS, f);
+          for (int i = 0; i < 3; ++i) wv[k][i] = xs[3 * lc[k] + i];
+        stiffness_apply<float>(wv, g, lamS, muS, f);
+        mass_apply<float>(wv, mS, f);
 #pragma unroll
-      for (int k = 0; k < 10; ++k)
+        for (int k = 0; k < 10; ++k)
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          atomicAdd(ys + 3 * lc[k] + i, f[k][i]);
-          dot = fmaf(wv[k][i], f[k][i], dot);
+          for (int i = 0; i < 3; ++i) {
+            atomicAdd(ys + 3 * lc[k] + i, f[k][i]);
+            dot = fmaf(wv[k][i], f[k][i], dot);
+          }
+      }
+      __syncwarp();
+      for (int i = lane; i < nn; i += 32) {
+        const int32_t raw = m.blk.nodes[n0 + i];
+        const int64_t g = raw & 0x7fffffff;
+        if (raw < 0) {
+          w[3 * g] = ys[3 * i];
+          w[3 * g + 1] = ys[3 * i + 1];
+          w[3 * g + 2] = ys[3 * i + 2];
+        } else {
+          atomicAdd(w + 3 * g, ys[3 * i]);
+          atomicAdd(w + 3 * g + 1, ys[3 * i + 1]);
+          atomicAdd(w + 3 * g + 2, ys[3 * i + 2]);
         }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nn; i += blockDim.x) {
-      const int32_t raw = m.blk.nodes[n0 + i];
-      const int64_t g = raw & 0x7fffffff;
-      if (raw < 0) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) w[3 * g + c] = ys[3 * i + c];
-      } else {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) atomicAdd(w + 3 * g + c, ys[3 * i + c]);
       }
     }
   } else {
     // absorbing faces: (2/dt) C_abs d
-    const int64_t fc = (int64_t)(b - m.blk.n_blk) * kElemThreads + threadIdx.x;
+    const int64_t fc = (int64_t)(blockIdx.x - n_elem_ctas) * kLoThreads + threadIdx.x;
     if (fc < m.F && m.fgeo[5 * m.F + fc] > 0.5f) {
       const float sc2 = (float)(2.0 / m.dt) / 180.f;
       const float As = sc2 * m.fgeo[fc], Ad = sc2 * m.fgeo[m.F + fc];
@@ -250,8 +290,7 @@ __global__ void __launch_bounds__(kElemThreads) ebe_lo_kernel(LoView<SG> m, cons
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
         nd[k] = m.fnode[k * m.F + fc];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) xin[k][i] = to_f(d[3 * nd[k] + i]);
+        load3(d + 4 * nd[k], xin[k][0], xin[k][1], xin[k][2]);
         const float dn = n[0] * xin[k][0] + n[1] * xin[k][1] + n[2] * xin[k][2];
 #pragma unroll
         for (int i = 0; i < 3; ++i) z[k][i] = fmaf(As, xin[k][i], Ad * dn * n[i]);
@@ -311,9 +350,10 @@ __global__ void inner_init_kernel(int64_t N, const double* __restrict__ r, const
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       t[3 * n + i] = tn[i];
-      d[3 * n + i] = from_f<SD>(tn[i]);
+      d[4 * n + i] = from_f<SD>(tn[i]);
       st = fmaf(sn[i], tn[i], st);
     }
+    d[4 * n + 3] = from_f<SD>(0.f);
   }
   double vals[1] = {(double)st}, out[1];
   if (last_block_reduce<1>(vals, partials, &sc->counter, out) && threadIdx.x == 0) {
@@ -334,7 +374,7 @@ __global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __r
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const int64_t k = 3 * n + i;
-      y[k] = fmaf(alpha, to_f(d[k]), y[k]);
+      y[k] = fmaf(alpha, to_f(d[4 * n + i]), y[k]);
       sn[i] = fmaf(-alpha, w[k], s[k]);
       s[k] = sn[i];
       w[k] = 0.f;
@@ -357,8 +397,10 @@ template <typename SD>
 __global__ void inner_dupdate_kernel(int64_t N, const float* __restrict__ t, SD* __restrict__ d,
                                      const InnerScalars* sc) {
   const float beta = (float)((volatile const InnerScalars*)sc)->beta;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N; i += (int64_t)gridDim.x * blockDim.x)
-    d[i] = from_f<SD>(fmaf(beta, to_f(d[i]), t[i]));
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) d[4 * n + i] = from_f<SD>(fmaf(beta, to_f(d[4 * n + i]), t[3 * n + i]));
+  }
 }
 
 // ------------------------------------------------------------------------------
@@ -465,9 +507,13 @@ __global__ void fcg_pupdate_kernel(int64_t N, const double* __restrict__ z, doub
 
 template <typename SD>
 __global__ void to_lo_kernel(int64_t n, const double* __restrict__ x, SD* __restrict__ d, float* __restrict__ w) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    d[i] = from_f<SD>((float)x[i]);
-    w[i] = 0.f;
+  for (int64_t nd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; nd < n / 3; nd += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      d[4 * nd + i] = from_f<SD>((float)x[3 * nd + i]);
+      w[3 * nd + i] = 0.f;
+    }
+    d[4 * nd + 3] = from_f<SD>(0.f);
   }
 }
 __global__ void from_f32_kernel(int64_t n, const float* __restrict__ w, double* __restrict__ y) {
@@ -489,6 +535,7 @@ void launch_from_f32(int64_t N, const float* w, double* y, cudaStream_t s) {
   from_f32_kernel<<<node_blocks(3 * N), kNodeThreads, 0, s>>>(3 * N, w, y);
 }
 
+int lo_block_elems() { return kLoBlock; }
 void launch_block_count(const ModelView& m, int n_blk, int32_t* counts, cudaStream_t s) {
   block_count_kernel<<<n_blk, 256, 0, s>>>(m, counts);
 }
@@ -529,20 +576,20 @@ void launch_ebe_lo(int half_geo, int half_vec, const void* lo_view, const void* 
                    InnerScalars* sc, cudaStream_t st) {
   if (half_geo) {
     const LoView<__half>& m = *(const LoView<__half>*)lo_view;
-    const unsigned g = (unsigned)(m.blk.n_blk + (m.F + kElemThreads - 1) / kElemThreads);
-    const size_t smem = sizeof(float) * 6 * (size_t)m.blk.max_local;
+    const unsigned g = (unsigned)((m.blk.n_blk + kLoWarps - 1) / kLoWarps + (m.F + kLoThreads - 1) / kLoThreads);
+    const size_t smem = sizeof(float) * 6 * (size_t)m.blk.max_local * kLoWarps;
     if (half_vec)
-      ebe_lo_kernel<__half, __half><<<g, kElemThreads, smem, st>>>(m, (const __half*)d, w, partials, sc);
+      ebe_lo_kernel<__half, __half><<<g, kLoThreads, smem, st>>>(m, (const __half*)d, w, partials, sc);
     else
-      ebe_lo_kernel<__half, float><<<g, kElemThreads, smem, st>>>(m, (const float*)d, w, partials, sc);
+      ebe_lo_kernel<__half, float><<<g, kLoThreads, smem, st>>>(m, (const float*)d, w, partials, sc);
   } else {
     const LoView<float>& m = *(const LoView<float>*)lo_view;
-    const unsigned g = (unsigned)(m.blk.n_blk + (m.F + kElemThreads - 1) / kElemThreads);
-    const size_t smem = sizeof(float) * 6 * (size_t)m.blk.max_local;
+    const unsigned g = (unsigned)((m.blk.n_blk + kLoWarps - 1) / kLoWarps + (m.F + kLoThreads - 1) / kLoThreads);
+    const size_t smem = sizeof(float) * 6 * (size_t)m.blk.max_local * kLoWarps;
     if (half_vec)
-      ebe_lo_kernel<float, __half><<<g, kElemThreads, smem, st>>>(m, (const __half*)d, w, partials, sc);
+      ebe_lo_kernel<float, __half><<<g, kLoThreads, smem, st>>>(m, (const __half*)d, w, partials, sc);
     else
-      ebe_lo_kernel<float, float><<<g, kElemThreads, smem, st>>>(m, (const float*)d, w, partials, sc);
+      ebe_lo_kernel<float, float><<<g, kLoThreads, smem, st>>>(m, (const float*)d, w, partials, sc);
   }
 }
 void launch_inner_update(int64_t N, float* y, float* s, float* t, const void* d, int half_vec, float* w,
@@ -557,9 +604,9 @@ void launch_inner_update(int64_t N, float* y, float* s, float* t, const void* d,
 void launch_inner_dupdate(int64_t N, const float* t, void* d, int half_vec, const InnerScalars* sc,
                           cudaStream_t st) {
   if (half_vec)
-    inner_dupdate_kernel<__half><<<node_blocks(3 * N), kNodeThreads, 0, st>>>(N, t, (__half*)d, sc);
+    inner_dupdate_kernel<__half><<<node_blocks(N), kNodeThreads, 0, st>>>(N, t, (__half*)d, sc);
   else
-    inner_dupdate_kernel<float><<<node_blocks(3 * N), kNodeThreads, 0, st>>>(N, t, (float*)d, sc);
+    inner_dupdate_kernel<float><<<node_blocks(N), kNodeThreads, 0, st>>>(N, t, (float*)d, sc);
 }
 void launch_fcg_residual(const ModelView& m, const double* b, double* q, double* r, double* partials, CgScalars* cg,
                          cudaStream_t s) {
