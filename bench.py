@@ -195,6 +195,138 @@ def run_reference(args, rank):
     }))
 
 
+def run_candidates(args, rank, world, dist):
+    """Batched ensemble: `--models` candidate models of the mixed-precision ensemble
+    (120 x 120 x 300 m, 95,817 nodes / 287,451 DOF each, seeded interfaces),
+    one directional analysis each, advanced together by one captured CUDA graph
+    per time step."""
+    import torch
+
+    from paper_2404_17754_gb300 import build, gsw, shard
+    from synth import configs
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    n_total = args.warmup + args.steps
+    prec = {"fp64": 0, "fp32": 1, "fp16": 2}[args.precision]
+    assert prec != 0, "the batched path runs the mixed-precision solver"
+    ctx = gsw.Context(local)
+    models, dof = [], 0
+    for l in range(args.models):
+        cfg = configs.config4_candidate(rank * args.models + l, n_steps=n_total, direction=l % 3)
+        m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
+        m.set_time(cfg["dt"], n_total, cfg["band"])
+        m.set_input(cfg["dir"], cfg["p"])
+        m.set_solver(tol=args.tol, precision=prec, inner_iters=args.inner, batch_outer=8)
+        models.append(m)
+        dof += 3 * cfg["mesh"]["xyz"].shape[0]
+    batch = ctx.batch(models)
+    batch.step(args.warmup)
+    it0 = sum(m.stats()["cg_iters_total"] for m in models)
+    stream = batch_stream = ctx.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    batch.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    t = e0.elapsed_time(e1) / 1e3
+    t_max = shard.max_over_ranks(t, dist)
+    iters = sum(m.stats()["cg_iters_total"] for m in models) - it0
+    lps = batch.launches_per_step()
+    if rank == 0:
+        per_step = t_max / args.steps
+        # one candidate analysis = 3 directional runs of 2000 steps (+ a misfit, negligible)
+        cah = world * args.models / 3.0 * 3600.0 / (2000 * per_step)
+        print(json.dumps({
+            "metric": "candidate analyses/hour", "value": cah, "unit": "candidate analyses/h", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+%s" % {"fp32": "f32", "fp16": "f16/f32"}[args.precision], "data": "synthetic",
+            "config": {"workload": "%d mixed-ensemble candidates (120x120x300 m, 287,451 DOF each), one directional "
+                                   "analysis each, batched" % args.models,
+                       "dof_total": dof, "dof_steps_per_s": world * dof * args.steps / t_max, "tol": args.tol,
+                       "precision": args.precision, "inner_iters": args.inner,
+                       "outer_iters_per_model_step": iters / (args.steps * args.models),
+                       "graph_kernel_nodes_per_step": lps,
+                       "l2": "inputs larger than L2 (%.1f GB resident)" % (sum(m.info()["device_bytes"] for m in models) / 1e9)},
+            "gpu_launches": lps * args.steps, "clocks": clk}))
+    batch.close()
+    ctx.close()
+
+
+def run_learned(args, rank, world, dist):
+    """Learned CG initial guess on the realistic model: train on the first
+    --train-steps steps, then time --steps steps; the same run with the plain
+    predictor is timed over the same steps.  Reports outer CG iterations per
+    step, the mean relative residual of the initial guess and ms per step."""
+    import torch
+
+    from paper_2404_17754_gb300 import build, gsw, shard
+    from synth import configs
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    n_total = args.train_steps + args.steps
+    prec = {"fp64": 0, "fp32": 1, "fp16": 2}[args.precision]
+    cfg = configs.config2(n_steps=n_total, direction=rank % 3)
+    ctx = gsw.Context(local)
+    out = {}
+    for enable in (1, 0):
+        m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
+        m.set_time(cfg["dt"], n_total, cfg["band"])
+        m.set_input(cfg["dir"], cfg["p"])
+        m.set_solver(tol=args.tol, precision=prec, inner_iters=args.inner)
+        if enable:
+            m.set_learning(True, train_steps=args.train_steps, batch=16384, iters_per_step=2, lr=1e-3, seed=7)
+        t0 = time.perf_counter()
+        m.step(args.train_steps)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        s0 = m.stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(ctx.stream)
+        m.step(args.steps)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        t = shard.max_over_ranks(e0.elapsed_time(e1) / 1e3, dist)
+        s1 = m.stats()
+        out[enable] = {"ms_per_step": 1e3 * t / args.steps,
+                       "outer_iters_per_step": (s1["cg_iters_total"] - s0["cg_iters_total"]) / args.steps,
+                       "mean_initial_relres": (s1["init_relres_sum"] - s0["init_relres_sum"]) / args.steps,
+                       "relres_last": s1["relres_last"], "train_phase_s": t_train,
+                       "judge": m.mlp_state() if enable else None}
+        m.free()
+    if rank == 0:
+        dof = 3 * cfg["mesh"]["xyz"].shape[0]
+        print(json.dumps({
+            "metric": "DOF*steps/s", "value": world * dof / (out[1]["ms_per_step"] / 1e3), "unit": "DOF*steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.train_steps, "ms_per_step": out[1]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+%s+bf16" % {"fp32": "f32", "fp16": "f16/f32"}[args.precision], "data": "synthetic",
+            "config": {"workload": "learned CG initial guess on " + cfg["name"], "train_steps": args.train_steps,
+                       "tol": args.tol, "precision": args.precision, "inner_iters": args.inner,
+                       "learned": out[1], "plain": out[0],
+                       "speedup_vs_plain": out[0]["ms_per_step"] / out[1]["ms_per_step"]}}))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -202,9 +334,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tol", type=float, default=1e-8)
-    ap.add_argument("--workload", default="realistic", choices=["realistic", "two-layer"])
-    ap.add_argument("--precision", default="fp16", choices=["fp64", "fp32", "fp16"])
-    ap.add_argument("--inner", type=int, default=20, help="inner preconditioner iterations (mixed modes)")
+    ap.add_argument("--workload", default="realistic", choices=["realistic", "two-layer", "candidates", "learned"])
+    ap.add_argument("--train-steps", type=int, default=500, help="learned workload: training steps")
+    ap.add_argument("--models", type=int, default=128, help="candidates workload: number of models in the batch")
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16"])
+    ap.add_argument("--inner", type=int, default=30, help="inner preconditioner iterations (mixed modes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -224,10 +358,20 @@ def main():
             dist.barrier()
             dist.destroy_process_group()
         return
+    if args.workload == "learned":
+        run_learned(args, rank, world, dist)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    if args.workload == "candidates":
+        run_candidates(args, rank, world, dist)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     import torch
 
-    from paper_2404_17754_gb300 import build, gsw
+    from paper_2404_17754_gb300 import build, gsw, shard
     from synth import configs
 
     torch.cuda.set_device(local)
@@ -276,11 +420,7 @@ def main():
     lo_ms, lo_n = tim["inner"]
     st = m.stats()
     t = e0.elapsed_time(e1) / 1e3
-    t_max = t
-    if dist is not None:
-        tt = torch.tensor([t], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt[0])
+    t_max = shard.max_over_ranks(t, dist)
     value = world * dof * args.steps / t_max
     launches = st["kernel_launches"] - launches0
     iters = st["cg_iters_total"] - it0
@@ -301,11 +441,7 @@ def main():
             m.step(1)
             m.read_steps_into(args.warmup + k, host)
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        if dist is not None:
-            tt = torch.tensor([te], dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt[0])
+        te = shard.max_over_ranks(time.perf_counter() - t0, dist)
         e2e = {"value": world * dof * args.steps / te, "unit": "DOF*steps/s",
                "h2d_bytes_per_step": 8 * len(p_host) / args.steps, "d2h_bytes_per_step": 8 * 3 * m.n_rec}
 
@@ -364,7 +500,8 @@ def main():
                    "solver": "block-Jacobi PCG" if args.precision == "fp64" else
                              "flexible CG (FP64) + %d-iteration %s block-Jacobi PCG preconditioner" % (
                                  args.inner, args.precision),
-                   "inner_iters_per_step": (st["inner_iters_total"] - inner0) / args.steps, "parallelism": "independent directional analyses, 1 per GPU",
+                   "inner_iters_per_step": (st["inner_iters_total"] - inner0) / args.steps,
+                   "inner_operator_variant": m.info()["inner_variant"], "parallelism": "independent directional analyses, 1 per GPU",
                    "cg_iters_per_step": iters / args.steps,
                    "l2": "inputs larger than L2 (FP64 working set %.1f GB)" % (
                        (14 * 3 * n_nodes * 8 + n_elem * 124) / 1e9),

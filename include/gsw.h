@@ -62,6 +62,10 @@ typedef struct {
   int32_t precision;    /* gsw_precision */
   int32_t inner_iters;  /* inner preconditioner iterations (mixed modes) */
   int32_t check_every;  /* CG iterations issued between host convergence checks */
+  int32_t batch_outer;  /* batched stepping: flexible-CG iterations per step in the
+                           captured step graph (0 = 6); a step that needs more
+                           is completed by the host-driven solver (up to
+                           max_iter) and the model then rejoins the graph */
 } gsw_solver_opts;
 
 typedef struct {
@@ -72,6 +76,8 @@ typedef struct {
   double relres_last;     /* final recursive relative residual of the last step */
   int64_t inner_iters_total; /* inner preconditioner iterations (mixed modes) */
   int64_t kernel_launches;   /* library kernels launched by gsw_step since the last reset */
+  double init_relres_sum;    /* sum over host-driven mixed steps of the relative residual
+                                of the initial guess (measures the guess quality) */
 } gsw_stats;
 
 /* ---- context ------------------------------------------------------------ */
@@ -117,7 +123,9 @@ gsw_status gsw_model_upload(gsw_ctx *ctx, int64_t n_nodes, const double *xyz, in
                             int32_t *model_id);
 gsw_status gsw_model_free(gsw_ctx *ctx, int32_t model_id);
 /* Sizes of an uploaded model: out[0]=n_nodes, out[1]=n_elem, out[2]=n_faces,
- * out[3]=n_rec, out[4]=device bytes held. */
+ * out[3]=n_rec, out[4]=device bytes held, out[5]=launch variant of the inner
+ * reduced-precision operator chosen by the set-up autotuner (-1 before a
+ * mixed precision mode is set). */
 gsw_status gsw_model_info(gsw_ctx *ctx, int32_t model_id, int64_t *out);
 
 /* Time integration (Section 3: Newmark-beta, average acceleration
@@ -142,8 +150,31 @@ gsw_status gsw_reset(gsw_ctx *ctx, int32_t model_id);
 gsw_status gsw_step(gsw_ctx *ctx, int32_t model_id, int32_t n);
 
 /* Run every listed model from rest through all its steps (one directional
- * analysis each). */
+ * analysis each).  Models in a mixed precision mode run together as one
+ * batch (see gsw_batch_create); FP64 models run one after the other. */
 gsw_status gsw_run(gsw_ctx *ctx, const int32_t *model_ids, int32_t n_models);
+
+/* ---- batched stepping (mixed precision modes) ----------------------------
+ * A batch advances several models (uneven sizes allowed) together: every
+ * time step of every model runs on the device without host synchronisation
+ * (device-side step counter and input samples; a fixed budget of
+ * solver_opts.batch_outer flexible-CG iterations whose kernels return at
+ * entry once converged), each model on its own stream, all captured into one
+ * CUDA graph that is launched once per time step.  Models that reach their
+ * n_steps stop advancing; a step that needs more outer iterations than the
+ * budget is finished by the host-driven solver; a model that fails stops at
+ * the failing step while the others continue, and gsw_batch_step reports the
+ * first failure.  Member models keep their own state, waveforms and
+ * statistics. */
+gsw_status gsw_batch_create(gsw_ctx *ctx, const int32_t *model_ids, int32_t n_models,
+                            int32_t *batch_id);
+/* Advance every member by n_steps time steps (members already at their end
+ * stay there).  The step graph is (re)captured when a member's solver
+ * options or time set-up changed since the last capture. */
+gsw_status gsw_batch_step(gsw_ctx *ctx, int32_t batch_id, int32_t n_steps);
+gsw_status gsw_batch_destroy(gsw_ctx *ctx, int32_t batch_id);
+/* Kernel launches captured in the batch's step graph (per time step). */
+gsw_status gsw_batch_launches(gsw_ctx *ctx, int32_t batch_id, int64_t *per_step);
 
 /* Receiver velocity history: out [n_rec][3][n_steps] (entries of steps not
  * yet run are zero). */
@@ -189,6 +220,46 @@ gsw_status gsw_read_preconditioner(gsw_ctx *ctx, int32_t model_id, double *out);
 /* Receiver interpolation: nodes [n_rec][6] and weights [n_rec][6] of the
  * 6-node surface triangle containing each receiver. */
 gsw_status gsw_read_receivers(gsw_ctx *ctx, int32_t model_id, int32_t *nodes, double *weights);
+
+/* ---- learned initial guess ------------------------------------------------
+ * A per-node MLP (16 -> 64 -> 64 -> 3, ReLU) corrects the Newmark predictor:
+ * features = the last four displacement increments scaled by the RMS of the
+ * latest one (12 values) and the node's layer properties (Vs/1000, Vp/3000,
+ * rho/2000, h/0.05); du0 = dt v + dt^2/2 a + sigma * MLP(features).  During the
+ * first train_steps steps the CG starts from the plain predictor and, after
+ * each converged step, the network takes iters_per_step Adam steps on a batch
+ * of random nodes (target: the converged increment); afterwards inference
+ * (BF16 tensor cores, FP32 accumulation) supplies the initial guess.  The CG
+ * always iterates to the same relative-residual tolerance; a non-finite guess
+ * falls back to the predictor, and the plain predictor stays the judge (see
+ * gsw_mlp_state).  Host-driven stepping (gsw_step) only. */
+typedef struct {
+  int32_t enable;          /* 0: plain predictor; 1: learned guess */
+  int32_t train_steps;     /* steps used for training (the guess is applied after them) */
+  int32_t batch;           /* training samples per Adam step (<= 65536) */
+  int32_t iters_per_step;  /* Adam steps after each training step */
+  float lr;                /* Adam learning rate */
+  uint32_t seed;           /* weight initialisation and node sampling */
+} gsw_learn_opts;
+gsw_status gsw_set_learning(gsw_ctx *ctx, int32_t model_id, const gsw_learn_opts *opts);
+/* MLP parameters (5443 doubles: W1[16][64], b1[64], W2[64][64], b2[64],
+ * W3[64][3], b3[3], row-major): read into get (if not NULL), then replace
+ * from set (if not NULL). */
+gsw_status gsw_mlp_params(gsw_ctx *ctx, int32_t model_id, double *get, const double *set);
+/* Diagnostics: network outputs out[n][3] for explicit features x[n][16] with
+ * the tensor-core inference kernel; loss and gradient grad[5443] of the mean
+ * squared error against y[n][3] with the training kernels.  Host arrays. */
+gsw_status gsw_mlp_forward(gsw_ctx *ctx, int32_t model_id, int32_t n, const float *x, float *out);
+gsw_status gsw_mlp_grad(gsw_ctx *ctx, int32_t model_id, int32_t n, const float *x, const float *y,
+                        double *loss, double *grad);
+/* State of the learned guess, out[5]: [0] mean training loss of the last
+ * training step, [1] 1 while the guess is applied (0 once the judge has
+ * reverted to the predictor, or when disabled), [2] mean initial relative
+ * residual of the plain predictor over its last (up to 5) steps, [3] the same
+ * for the learned guess, [4] number of steps that used the learned guess.
+ * After training, every 10th step is a probe with the plain predictor; the
+ * judge reverts to the predictor for good when [3] (over 5 steps) exceeds [2]. */
+gsw_status gsw_mlp_state(gsw_ctx *ctx, int32_t model_id, double *out);
 
 /* ---- misfit (Section 2, Eq. (2)) ----------------------------------------- */
 

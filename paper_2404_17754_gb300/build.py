@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgsw.so")
-SOURCES = ["gsw_api.cu", "gsw_kernels.cu", "gsw_mixed.cu", "gsw_misfit.cu"]
+SOURCES = ["gsw_api.cu", "gsw_kernels.cu", "gsw_mixed.cu", "gsw_mlp.cu", "gsw_misfit.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <string>
 #include <vector>
@@ -54,7 +55,7 @@ struct Model {
   std::vector<double> input;
   int dir = 0;
   bool input_set = false;
-  gsw_solver_opts opts = {1e-8, 10000, GSW_PREC_FP64, 20, 8};
+  gsw_solver_opts opts = {1e-8, 10000, GSW_PREC_FP64, 20, 8, 6};
   int64_t step = 0;
   bool failed = false;
   gsw_stats stats = {};
@@ -65,13 +66,33 @@ struct Model {
   int32_t* blk_ptr = nullptr;
   int32_t* blk_nodes = nullptr;
   uint16_t* lconn = nullptr;
-  void* geo_lo = nullptr;
+  void* geo_lo = nullptr;  // packed element records of the inner operator
   float* fgeo32 = nullptr;
-  float* vol32 = nullptr;
   float* dinv32 = nullptr;
   float *y32 = nullptr, *s32 = nullptr, *t32 = nullptr, *w32 = nullptr;
   void* d_lo = nullptr;
   InnerScalars* isc = nullptr;
+  int lo_variant = 0;          // launch variant of the inner operator (autotuned)
+  // learned initial guess
+  gsw_learn_opts learn = {0, 0, 0, 0, 0.f, 0u};
+  bool mlp_ready = false;
+  float *theta = nullptr, *adam_m = nullptr, *adam_v = nullptr, *grad = nullptr;
+  uint32_t* packed = nullptr;
+  float *hist = nullptr, *nodef = nullptr, *trainX = nullptr, *trainY = nullptr;
+  int32_t* node_mat = nullptr;
+  MlpScalars* ms = nullptr;
+  MlpScalars ms_host = {};
+  int hist_head = 3, hist_count = 0, adam_t = 0;
+  // judge of the learned guess: initial residuals of the plain predictor
+  // (training phase) and of the learned guess (application phase)
+  double std_r0_recent[5] = {0, 0, 0, 0, 0}, mlp_r0_recent[5] = {0, 0, 0, 0, 0};
+  int64_t std_r0_n = 0, mlp_r0_n = 0, applied = 0;
+  bool mlp_off = false;
+  // device-driven (batched) stepping
+  double* p_dev = nullptr;     // input samples on the device
+  int batch = 0;               // id of the batch holding the model (0: none)
+  int version = 0;             // bumped when a captured step graph would be stale
+  float lo_variant_ms[kLoVariants] = {0.f, 0.f};
   LoView<float> lo_f;
   LoView<__half> lo_h;
   // kernel timing
@@ -112,6 +133,25 @@ struct gsw_ctx {
   std::map<int, Model*> models;
   int next_id = 1;
   MisfitWork misfit;
+  std::map<int, struct Batch*> batches;
+  int next_batch = 1;
+};
+
+// A set of models advanced together: one CUDA graph per time step holds every
+// model's device-driven step on its own stream branch.
+struct Batch {
+  std::vector<int> ids;
+  std::vector<int> versions;
+  cudaStream_t origin = nullptr;
+  std::vector<cudaStream_t> streams;
+  cudaEvent_t fork = nullptr, done_ev = nullptr;
+  std::vector<cudaEvent_t> joins;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  StepState* ss_dev = nullptr;
+  StepState* ss_host = nullptr;  // pinned
+  int64_t launches_per_step = 0;
+  int outer = 0;
 };
 
 namespace {
@@ -254,6 +294,8 @@ gsw_status model_reset(gsw_ctx* ctx, Model* m) {
   m->step = 0;
   m->failed = false;
   m->stats = gsw_stats{};
+  m->hist_head = 3;
+  m->hist_count = 0;
   return GSW_OK;
 }
 
@@ -334,6 +376,41 @@ gsw_status step_fp64(gsw_ctx* ctx, Model* m) {
   return GSW_OK;
 }
 
+// Set-up autotuner of the inner operator: times every launch variant on this
+// model's own data (search direction = the state u, zero after a reset) and
+// keeps the fastest.
+gsw_status autotune_lo(gsw_ctx* ctx, Model* m) {
+  cudaStream_t s = ctx->stream;
+  const void* view = m->lo_half ? (const void*)&m->lo_h : (const void*)&m->lo_f;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  launch_to_lo(m->N, m->u, m->d_lo, m->lo_half, m->w32, s);
+  float best = 1e30f;
+  for (int v = 0; v < kLoVariants; ++v) {
+    launch_ebe_lo(m->lo_half, m->lo_half, view, m->d_lo, m->w32, m->partials, m->isc, s, v);  // warm-up
+    float tot = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {
+      CK(cudaEventRecord(e0, s));
+      launch_ebe_lo(m->lo_half, m->lo_half, view, m->d_lo, m->w32, m->partials, m->isc, s, v);
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      tot += ms;
+    }
+    m->lo_variant_ms[v] = tot / 3.f;
+    if (tot < best) {
+      best = tot;
+      m->lo_variant = v;
+    }
+  }
+  CK(cudaGetLastError());
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return GSW_OK;
+}
+
 // Element blocks with local numbering and the reduced-precision copies of the
 // operator data and preconditioner (built once per model; the conversion is
 // redone when dt changes).
@@ -355,21 +432,23 @@ gsw_status build_lo(gsw_ctx* ctx, Model* m, int half) {
       if (h[b] > mx) mx = h[b];
     }
     m->max_local = mx;
+    if (mx > kLoBlock * kLoNodesPerThread)
+      return fail(ctx, GSW_E_INVALID, "element block with %d unique nodes exceeds %d (mesh ordering too scattered)", mx,
+                  kLoBlock * kLoNodesPerThread);
     const int total = ptr[m->n_blk];
     int32_t* refcount = nullptr;
     TRY(alloc_into(ctx, m, &m->blk_ptr, (size_t)m->n_blk + 1));
     TRY(alloc_into(ctx, m, &m->blk_nodes, (size_t)total));
-    TRY(alloc_into(ctx, m, &m->lconn, 10 * (size_t)m->E));
+    TRY(alloc_into(ctx, m, &m->lconn, 10 * (size_t)m->n_blk * kLoBlock));
     TRY(alloc_into(ctx, m, &refcount, (size_t)m->N));
     CK(cudaMemcpyAsync(m->blk_ptr, ptr.data(), sizeof(int32_t) * (m->n_blk + 1), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(refcount, 0, sizeof(int32_t) * m->N, s));
-    BlockView bv = {m->n_blk, m->max_local, m->blk_ptr, m->blk_nodes, m->lconn};
+    BlockView bv = {m->n_blk, m->max_local, m->blk_ptr, m->blk_nodes};
     launch_block_fill(mv, bv, m->blk_nodes, m->lconn, refcount, s);
     launch_block_mark(mv, bv, m->blk_nodes, refcount, total, s);
     CK(cudaGetLastError());
     const size_t n3 = 3 * (size_t)m->N;
     TRY(alloc_into(ctx, m, &m->fgeo32, 6 * (size_t)(m->F > 0 ? m->F : 1)));
-    TRY(alloc_into(ctx, m, &m->vol32, (size_t)m->E));
     TRY(alloc_into(ctx, m, &m->dinv32, 6 * (size_t)m->N));
     TRY(alloc_into(ctx, m, &m->y32, n3));
     TRY(alloc_into(ctx, m, &m->s32, n3));
@@ -383,18 +462,118 @@ gsw_status build_lo(gsw_ctx* ctx, Model* m, int half) {
   }
   if (m->geo_lo == nullptr || m->lo_half != half) {
     // (re)allocate the precision-dependent buffers; the old ones stay owned by the model
-    m->geo_lo = dev_alloc(ctx, m, (half ? sizeof(__half) : sizeof(float)) * 9 * (size_t)m->E);
+    m->geo_lo = dev_alloc(ctx, m, lo_record_bytes(half) * (size_t)m->n_blk * kLoBlock);
     m->d_lo = dev_alloc(ctx, m, (half ? sizeof(__half) : sizeof(float)) * 4 * (size_t)m->N);
     if (!m->geo_lo || !m->d_lo) return fail(ctx, GSW_E_NOMEM, "device allocation failed (inner solve)");
     m->lo_half = half;
   }
-  launch_lo_convert(mv, half, m->geo_lo, m->vol32, m->fgeo32, m->dinv, m->dinv32, m->partials, m->isc, s);
+  launch_lo_convert(mv, m->n_blk, m->lconn, half, m->geo_lo, m->fgeo32, m->dinv, m->dinv32, m->partials, m->isc,
+                    s);
   CK(cudaGetLastError());
-  BlockView bv = {m->n_blk, m->max_local, m->blk_ptr, m->blk_nodes, m->lconn};
-  m->lo_f = LoView<float>{m->N, m->E, m->F, m->n_mat, bv, (const float*)m->geo_lo, m->vol32, m->emat, m->mat, m->fnode,
-                          m->fgeo32, m->dt};
-  m->lo_h = LoView<__half>{m->N, m->E, m->F, m->n_mat, bv, (const __half*)m->geo_lo, m->vol32, m->emat, m->mat, m->fnode,
-                           m->fgeo32, m->dt};
+  BlockView bv = {m->n_blk, m->max_local, m->blk_ptr, m->blk_nodes};
+  m->lo_f = LoView<float>{m->N, m->E, m->F, m->n_mat, bv, m->geo_lo, m->mat, m->fnode, m->fgeo32, m->dt};
+  m->lo_h = LoView<__half>{m->N, m->E, m->F, m->n_mat, bv, m->geo_lo, m->mat, m->fnode, m->fgeo32, m->dt};
+  return autotune_lo(ctx, m);
+}
+
+// ---- learned initial guess ----------------------------------------------------
+
+// Reproducible uniform(-1, 1) from a counter (same on every host).
+double hash_uniform(uint32_t seed, uint32_t i) {
+  uint64_t z = ((uint64_t)seed << 32) ^ (uint64_t)i;
+  z += 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  z ^= z >> 31;
+  return 2.0 * ((double)(z >> 11) / 9007199254740992.0) - 1.0;
+}
+
+gsw_status mlp_alloc(gsw_ctx* ctx, Model* m) {
+  if (m->mlp_ready) return GSW_OK;
+  TRY(alloc_into(ctx, m, &m->theta, kMlpParams));
+  TRY(alloc_into(ctx, m, &m->adam_m, kMlpParams));
+  TRY(alloc_into(ctx, m, &m->adam_v, kMlpParams));
+  TRY(alloc_into(ctx, m, &m->grad, kMlpParams));
+  TRY(alloc_into(ctx, m, &m->packed, (size_t)mlp_packed_words()));
+  TRY(alloc_into(ctx, m, &m->hist, 4 * 3 * (size_t)m->N));
+  TRY(alloc_into(ctx, m, &m->nodef, 4 * (size_t)m->N));
+  TRY(alloc_into(ctx, m, &m->node_mat, (size_t)m->N));
+  TRY(alloc_into(ctx, m, &m->trainX, 16 * (size_t)65536));
+  TRY(alloc_into(ctx, m, &m->trainY, 3 * (size_t)65536));
+  TRY(alloc_into(ctx, m, &m->ms, 1));
+  CK(cudaMemsetAsync(m->ms, 0, sizeof(MlpScalars), ctx->stream));
+  launch_node_features(m->view(), m->n_mat, m->node_mat, m->nodef, ctx->stream);
+  m->mlp_ready = true;
+  return GSW_OK;
+}
+
+// He-uniform weights (fan-in) with a 100x smaller last layer, zero biases,
+// Adam moments and gradients cleared, history emptied.
+gsw_status mlp_init(gsw_ctx* ctx, Model* m, uint32_t seed) {
+  std::vector<float> th(kMlpParams, 0.f);
+  const int offs[3] = {0, 1088, 5248}, fan_in[3] = {16, 64, 64}, count[3] = {1024, 4096, 192};
+  for (int l = 0; l < 3; ++l) {
+    const double lim = sqrt(6.0 / fan_in[l]) * (l == 2 ? 0.01 : 1.0);
+    for (int i = 0; i < count[l]; ++i) th[offs[l] + i] = (float)(lim * hash_uniform(seed + 17u * l, (uint32_t)i));
+  }
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemcpyAsync(m->theta, th.data(), sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(m->adam_m, 0, sizeof(float) * kMlpParams, s));
+  CK(cudaMemsetAsync(m->adam_v, 0, sizeof(float) * kMlpParams, s));
+  CK(cudaMemsetAsync(m->grad, 0, sizeof(float) * kMlpParams, s));
+  CK(cudaMemsetAsync(m->hist, 0, sizeof(float) * 12 * (size_t)m->N, s));
+  launch_mlp_pack(m->theta, m->packed, s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  m->hist_head = 3;
+  m->hist_count = 0;
+  m->adam_t = 0;
+  for (int k = 0; k < 5; ++k) m->std_r0_recent[k] = m->mlp_r0_recent[k] = 0.0;
+  m->std_r0_n = m->mlp_r0_n = m->applied = 0;
+  m->mlp_off = false;
+  return GSW_OK;
+}
+
+// Before a step: write the learned guess into x when it applies.
+bool mlp_use_guess(gsw_ctx* ctx, Model* m, cudaStream_t s) {
+  (void)ctx;
+  if (!m->learn.enable || !m->mlp_ready || m->mlp_off || m->hist_count < 4 || m->step < m->learn.train_steps)
+    return false;
+  // every 10th step of the application phase is a probe with the plain
+  // predictor, keeping the judge's baseline current
+  if ((m->applied++ % 10) == 9) return false;
+  launch_mlp_sigma(m->N, m->hist, m->hist_head, m->partials, m->ms, s);
+  launch_mlp_infer(m->N, m->hist, m->hist_head, m->nodef, m->v, m->a, m->dt, m->packed, m->ms, m->x, nullptr,
+                   nullptr, s);
+  m->stats.kernel_launches += 2;
+  return true;
+}
+
+// After a converged step (before the Newmark update overwrites v, a): train on
+// the converged increment, then push it into the history.
+gsw_status mlp_after_step(gsw_ctx* ctx, Model* m, cudaStream_t s) {
+  if (!m->learn.enable || !m->mlp_ready) return GSW_OK;
+  if (m->step < m->learn.train_steps && m->hist_count >= 4 && !m->cg_host->zero_rhs) {
+    launch_mlp_sigma(m->N, m->hist, m->hist_head, m->partials, m->ms, s);
+    CK(cudaMemsetAsync(&m->ms->loss, 0, sizeof(double), s));
+    const int B = m->learn.batch;
+    for (int it = 0; it < m->learn.iters_per_step; ++it) {
+      launch_mlp_sample(m->N, B, m->learn.seed, (int)m->step, it, m->hist, m->hist_head, m->nodef, m->x, m->v, m->a,
+                        m->dt, m->ms, m->trainX, m->trainY, s);
+      if (launch_mlp_fwdbwd(B, m->trainX, m->trainY, m->theta, m->grad, &m->ms->loss, s))
+        return fail(ctx, GSW_E_CUDA, "training kernel configuration failed");
+      m->adam_t += 1;
+      launch_mlp_adam(m->theta, m->grad, m->adam_m, m->adam_v, m->adam_t, m->learn.lr, s);
+    }
+    launch_mlp_pack(m->theta, m->packed, s);
+    m->stats.kernel_launches += 2 + 3 * m->learn.iters_per_step;
+  }
+  const int slot = (m->hist_head + 1) & 3;
+  launch_hist_push(m->N, m->x, m->hist, slot, m->cg, s);
+  m->hist_head = slot;
+  if (m->hist_count < 4) m->hist_count += 1;
+  m->stats.kernel_launches += 1;
+  CK(cudaGetLastError());
   return GSW_OK;
 }
 
@@ -409,10 +588,11 @@ int64_t inner_solve(Model* m, cudaStream_t s) {
   const bool timed = m->timing && (int)m->ev_lo.size() >= 2 * it;
   for (int k = 0; k < it; ++k) {
     if (timed) cudaEventRecord(m->ev_lo[2 * k], s);
-    launch_ebe_lo(half, half, view, m->d_lo, m->w32, m->partials, m->isc, s);
+    launch_ebe_lo(half, half, view, m->d_lo, m->w32, m->partials, m->isc, s, m->lo_variant, m->cg);
     if (timed) cudaEventRecord(m->ev_lo[2 * k + 1], s);
-    launch_inner_update(m->N, m->y32, m->s32, m->t32, m->d_lo, half, m->w32, m->dinv32, m->partials, m->isc, s);
-    if (k + 1 < it) launch_inner_dupdate(m->N, m->t32, m->d_lo, half, m->isc, s);
+    launch_inner_update(m->N, m->y32, m->s32, m->t32, m->d_lo, half, m->w32, m->dinv32, m->partials, m->isc, s,
+                        m->cg);
+    if (k + 1 < it) launch_inner_dupdate(m->N, m->t32, m->d_lo, half, m->isc, s, m->cg);
   }
   m->stats.inner_iters_total += it;
   if (timed) {
@@ -438,10 +618,12 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
   init.tol = m->opts.tol;
   init.max_iter = m->opts.max_iter;
   CK(cudaMemcpyAsync(m->cg, &init, sizeof(CgScalars), cudaMemcpyHostToDevice, s));
-  // predictor and predicted state (u~ in p, v~ in z), r = q = 0
-  launch_cg_init_mixed(mv, m->w32, m->u, m->v, m->a, m->x, m->p, m->z, m->r, m->q, m->partials, m->cg, s);
-  // FP64 residual at the predictor in one element-by-element pass
-  launch_ebe(kModeRes, mv, m->p, m->z, m->a, m->r, force, m->dir, nullptr, m->cg, s);
+  // initial guess (predictor or learned) and the shifted state (u~ in p, v~ in z, a~ in b), r = q = 0
+  const bool learned = mlp_use_guess(ctx, m, s);
+  launch_cg_init_mixed(mv, m->w32, m->u, m->v, m->a, m->x, m->p, m->z, m->b, m->r, m->q, m->partials, m->cg, s,
+                       nullptr, learned ? 1 : 0);
+  // FP64 residual at the initial guess in one element-by-element pass
+  launch_ebe(kModeRes, mv, m->p, m->z, m->b, m->r, force, m->dir, nullptr, m->cg, s);
   launch_cg_rnorm(mv, m->r, m->partials, m->cg, s);
   int64_t launches = 4;
   if (m->timing && (int)m->ev_lo.size() < 2 * m->opts.inner_iters) {
@@ -454,6 +636,23 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(m->cg_host, m->cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  m->stats.init_relres_sum += m->cg_host->relres;
+  if (m->learn.enable && !m->cg_host->zero_rhs) {
+    // judge: the learned guess stays while the mean initial residual of its
+    // last 5 steps beats that of the plain predictor's last 5 steps (the last
+    // training steps, then the probe steps)
+    double* buf = learned ? m->mlp_r0_recent : m->std_r0_recent;
+    int64_t& cnt = learned ? m->mlp_r0_n : m->std_r0_n;
+    buf[cnt % 5] = m->cg_host->relres;
+    cnt += 1;
+    if (learned && m->mlp_r0_n >= 5 && m->std_r0_n >= 1) {
+      const int64_t ks = m->std_r0_n < 5 ? m->std_r0_n : 5;
+      double ml = 0.0, sl = 0.0;
+      for (int k = 0; k < 5; ++k) ml += m->mlp_r0_recent[k] / 5.0;
+      for (int64_t k = 0; k < ks; ++k) sl += m->std_r0_recent[k] / (double)ks;
+      if (ml > sl) m->mlp_off = true;
+    }
+  }
   if (!m->cg_host->done) {
     launches += inner_solve(m, s);
     launch_fcg_first(mv, m->y32, m->r, m->z, m->p, m->partials, m->cg, m->isc, s);
@@ -502,6 +701,7 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
                   (long long)m->step, m->opts.tol, h.iter, h.relres);
     return fail(ctx, GSW_E_NAN, "step %lld: non-finite CG residual", (long long)m->step);
   }
+  TRY(mlp_after_step(ctx, m, s));
   launch_newmark(mv, m->x, m->u, m->v, m->a, m->cg, s);
   launch_record(m->v, m->rec_node, m->rec_w, m->n_rec, m->wave, m->n_steps, (int)m->step, s);
   CK(cudaGetLastError());
@@ -513,6 +713,72 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
   m->stats.kernel_launches += launches + 2;
   m->step += 1;
   return GSW_OK;
+}
+
+// Device-driven inner solve (no timing, no host bookkeeping).
+void inner_solve_dev(Model* m, cudaStream_t s) {
+  const int half = m->lo_half;
+  const void* view = half ? (const void*)&m->lo_h : (const void*)&m->lo_f;
+  launch_inner_init(m->N, m->r, m->dinv32, m->s32, m->y32, m->t32, m->d_lo, half, m->w32, m->partials, m->isc,
+                    m->cg, s);
+  const int it = m->opts.inner_iters > 0 ? m->opts.inner_iters : 1;
+  for (int k = 0; k < it; ++k) {
+    launch_ebe_lo(half, half, view, m->d_lo, m->w32, m->partials, m->isc, s, m->lo_variant, m->cg);
+    launch_inner_update(m->N, m->y32, m->s32, m->t32, m->d_lo, half, m->w32, m->dinv32, m->partials, m->isc, s,
+                        m->cg);
+    if (k + 1 < it) launch_inner_dupdate(m->N, m->t32, m->d_lo, half, m->isc, s, m->cg);
+  }
+}
+
+// One mixed-precision Newmark step driven entirely on the device: the step
+// index and the input sample come from device memory and the flexible CG runs
+// a fixed budget of `outer` iterations whose kernels return at entry once the
+// solve has converged.  Returns the number of kernel launches issued.
+int64_t issue_device_step(Model* m, cudaStream_t s, StepState* ss, int outer) {
+  ModelView mv = m->view();
+  Drive dr{m->p_dev, ss};
+  const int it = m->opts.inner_iters > 0 ? m->opts.inner_iters : 1;
+  const int64_t inner_launches = 1 + 3 * (int64_t)it - 1;
+  int64_t n = 0;
+  launch_step_begin(ss, m->cg, s);
+  cudaMemsetAsync(m->w32, 0, sizeof(float) * 3 * (size_t)m->N, s);
+  launch_rhs_f32(mv, m->u, m->v, m->a, m->w32, 0.0, m->dir, s, dr);
+  launch_cg_init_mixed(mv, m->w32, m->u, m->v, m->a, m->x, m->p, m->z, m->b, m->r, m->q, m->partials, m->cg, s, ss);
+  launch_ebe(kModeRes, mv, m->p, m->z, m->b, m->r, 0.0, m->dir, nullptr, m->cg, s, dr);
+  launch_cg_rnorm(mv, m->r, m->partials, m->cg, s);
+  n += 5;
+  inner_solve_dev(m, s);
+  launch_fcg_first(mv, m->y32, m->r, m->z, m->p, m->partials, m->cg, m->isc, s);
+  n += inner_launches + 1;
+  for (int k = 0; k < outer; ++k) {
+    launch_ebe(kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, s);
+    launch_fcg_update(mv, m->x, m->r, m->p, m->q, m->partials, m->cg, s);
+    n += 2;
+    if (k + 1 < outer) {
+      inner_solve_dev(m, s);
+      launch_fcg_zbeta(mv, m->y32, m->r, m->q, m->z, m->partials, m->cg, m->isc, s);
+      launch_fcg_pupdate(mv, m->z, m->p, m->q, m->cg, s);
+      n += inner_launches + 2;
+    }
+  }
+  launch_step_end(ss, m->cg, s);
+  launch_newmark(mv, m->x, m->u, m->v, m->a, m->cg, s, ss);
+  launch_record(m->v, m->rec_node, m->rec_w, m->n_rec, m->wave, m->n_steps, 0, s, ss);
+  launch_step_advance(ss, s);
+  return n + 4;
+}
+
+void batch_free(Batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->done_ev) cudaEventDestroy(b->done_ev);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  if (b->ss_dev) cudaFree(b->ss_dev);
+  if (b->ss_host) cudaFreeHost(b->ss_host);
+  delete b;
 }
 
 bool finite_all(const double* p, size_t n) {
@@ -546,6 +812,8 @@ void gsw_destroy(gsw_ctx* ctx) {
   if (!ctx) return;
   DeviceGuard g(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  for (auto& kv : ctx->batches) batch_free(kv.second);
+  ctx->batches.clear();
   for (auto& kv : ctx->models) free_model(ctx, kv.second);
   ctx->models.clear();
   misfit_free(ctx->misfit, ctx->stream);
@@ -689,6 +957,7 @@ gsw_status gsw_model_free(gsw_ctx* ctx, int32_t model_id) {
   DeviceGuard g(ctx->device);
   Model* m = find(ctx, model_id);
   if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (m->batch) return fail(ctx, GSW_E_STATE, "model %d belongs to batch %d; destroy the batch first", model_id, m->batch);
   cudaStreamSynchronize(ctx->stream);
   free_model(ctx, m);
   ctx->models.erase(model_id);
@@ -704,6 +973,7 @@ gsw_status gsw_model_info(gsw_ctx* ctx, int32_t model_id, int64_t* out) {
   out[2] = m->F;
   out[3] = m->n_rec;
   out[4] = (int64_t)m->bytes;
+  out[5] = m->lo_ready ? m->lo_variant : -1;
   return GSW_OK;
 }
 
@@ -722,6 +992,7 @@ gsw_status gsw_set_time(gsw_ctx* ctx, int32_t model_id, double dt, int32_t n_ste
       if (p == m->wave) p = nullptr;
     m->n_steps = n_steps;
     TRY(alloc_into(ctx, m, &m->wave, (size_t)m->n_rec * 3 * (size_t)n_steps));
+    m->p_dev = nullptr;  // reallocated at the next batch creation
   }
   m->dt = dt;
   m->f1 = f1;
@@ -732,14 +1003,16 @@ gsw_status gsw_set_time(gsw_ctx* ctx, int32_t model_id, double dt, int32_t n_ste
   }
   m->time_set = true;
   m->input_set = false;
+  m->version += 1;
   cudaStream_t s = ctx->stream;
   CK(cudaMemsetAsync(m->err, 0, sizeof(int), s));
   launch_material(m->mat, m->raw_mat_dev, m->n_mat, dt, f1, f2, s);
   launch_block_jacobi(m->view(), m->dblk, m->dinv, m->err, s);
   CK(cudaGetLastError());
   TRY(check_device_err(ctx, m, "preconditioner"));
+  TRY(model_reset(ctx, m));
   if (m->opts.precision != GSW_PREC_FP64) TRY(build_lo(ctx, m, m->opts.precision == GSW_PREC_FP16));
-  return model_reset(ctx, m);
+  return GSW_OK;
 }
 
 gsw_status gsw_set_input(gsw_ctx* ctx, int32_t model_id, int32_t dir, const double* p, int32_t n) {
@@ -751,8 +1024,14 @@ gsw_status gsw_set_input(gsw_ctx* ctx, int32_t model_id, int32_t dir, const doub
   if (!p || n != m->n_steps) return fail(ctx, GSW_E_INVALID, "input length %d != n_steps %d", n, m->n_steps);
   if (!finite_all(p, (size_t)n)) return fail(ctx, GSW_E_INVALID, "non-finite input sample");
   m->input.assign(p, p + n);
+  if (m->dir != dir) m->version += 1;
   m->dir = dir;
   m->input_set = true;
+  if (m->p_dev) {
+    DeviceGuard g(ctx->device);
+    CK(cudaMemcpyAsync(m->p_dev, p, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
   return GSW_OK;
 }
 
@@ -767,6 +1046,7 @@ gsw_status gsw_set_solver(gsw_ctx* ctx, int32_t model_id, const gsw_solver_opts*
   if (opts->precision != GSW_PREC_FP64 && (opts->inner_iters <= 0 || opts->inner_iters > 10000))
     return fail(ctx, GSW_E_INVALID, "inner_iters must be 1..10000");
   m->opts = *opts;
+  m->version += 1;
   if (m->opts.precision != GSW_PREC_FP64 && m->time_set) {
     DeviceGuard g(ctx->device);
     TRY(build_lo(ctx, m, m->opts.precision == GSW_PREC_FP16));
@@ -803,12 +1083,219 @@ gsw_status gsw_step(gsw_ctx* ctx, int32_t model_id, int32_t n) {
 
 gsw_status gsw_run(gsw_ctx* ctx, const int32_t* model_ids, int32_t n_models) {
   if (!ctx || (!model_ids && n_models > 0)) return GSW_E_INVALID;
+  std::vector<int32_t> mixed;
+  int max_steps = 0;
   for (int i = 0; i < n_models; ++i) {
     Model* m = find(ctx, model_ids[i]);
     if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_ids[i]);
     TRY(gsw_reset(ctx, model_ids[i]));
-    TRY(gsw_step(ctx, model_ids[i], m->n_steps));
+    if (m->opts.precision == GSW_PREC_FP64 || m->batch || m->learn.enable) {
+      TRY(gsw_step(ctx, model_ids[i], m->n_steps));
+    } else {
+      mixed.push_back(model_ids[i]);
+      if (m->n_steps > max_steps) max_steps = m->n_steps;
+    }
   }
+  if (!mixed.empty()) {
+    int32_t bid = 0;
+    TRY(gsw_batch_create(ctx, mixed.data(), (int32_t)mixed.size(), &bid));
+    gsw_status st = gsw_batch_step(ctx, bid, max_steps);
+    std::string msg = ctx->err;
+    gsw_batch_destroy(ctx, bid);
+    if (st != GSW_OK) ctx->err = msg;
+    return st;
+  }
+  return GSW_OK;
+}
+
+gsw_status gsw_batch_create(gsw_ctx* ctx, const int32_t* model_ids, int32_t n_models, int32_t* batch_id) {
+  if (!ctx || !model_ids || n_models <= 0 || !batch_id) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  for (int i = 0; i < n_models; ++i) {
+    Model* m = find(ctx, model_ids[i]);
+    if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_ids[i]);
+    if (!m->time_set || !m->input_set) return fail(ctx, GSW_E_STATE, "model %d: set the time and the input first", model_ids[i]);
+    if (m->opts.precision == GSW_PREC_FP64 || !m->lo_ready)
+      return fail(ctx, GSW_E_STATE, "model %d: batched stepping needs a mixed precision mode", model_ids[i]);
+    if (m->batch) return fail(ctx, GSW_E_STATE, "model %d already belongs to batch %d", model_ids[i], m->batch);
+    if (m->learn.enable)
+      return fail(ctx, GSW_E_STATE, "model %d: the learned guess runs with host-driven stepping only", model_ids[i]);
+    for (int j = 0; j < i; ++j)
+      if (model_ids[j] == model_ids[i]) return fail(ctx, GSW_E_INVALID, "model %d listed twice", model_ids[i]);
+  }
+  Batch* b = new Batch();
+  auto bail = [&](const char* what, cudaError_t e) {
+    batch_free(b);
+    return fail(ctx, GSW_E_CUDA, "batch creation: %s: %s", what, cudaGetErrorString(e));
+  };
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking)) != cudaSuccess) return bail("stream", e);
+  if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess) return bail("event", e);
+  if ((e = cudaEventCreateWithFlags(&b->done_ev, cudaEventDisableTiming)) != cudaSuccess) return bail("event", e);
+  if ((e = cudaMalloc(&b->ss_dev, sizeof(StepState) * n_models)) != cudaSuccess) return bail("state", e);
+  if ((e = cudaMallocHost(&b->ss_host, sizeof(StepState) * n_models)) != cudaSuccess) return bail("state", e);
+  for (int i = 0; i < n_models; ++i) {
+    Model* m = find(ctx, model_ids[i]);
+    cudaStream_t s;
+    cudaEvent_t ev;
+    if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return bail("stream", e);
+    b->streams.push_back(s);
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return bail("event", e);
+    b->joins.push_back(ev);
+    if (!m->p_dev) {
+      m->p_dev = (double*)dev_alloc(ctx, m, sizeof(double) * m->n_steps);
+      if (!m->p_dev) {
+        batch_free(b);
+        return fail(ctx, GSW_E_NOMEM, "device allocation failed (input samples)");
+      }
+    }
+    if ((e = cudaMemcpyAsync(m->p_dev, m->input.data(), sizeof(double) * m->n_steps, cudaMemcpyHostToDevice,
+                             ctx->stream)) != cudaSuccess)
+      return bail("input copy", e);
+    b->ids.push_back(model_ids[i]);
+    b->versions.push_back(-1);
+  }
+  if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return bail("synchronise", e);
+  const int id = ctx->next_batch++;
+  for (int i = 0; i < n_models; ++i) find(ctx, model_ids[i])->batch = id;
+  ctx->batches[id] = b;
+  *batch_id = id;
+  return GSW_OK;
+}
+
+gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
+  if (!ctx) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  auto it = ctx->batches.find(batch_id);
+  if (it == ctx->batches.end()) return fail(ctx, GSW_E_INVALID, "unknown batch %d", batch_id);
+  Batch* b = it->second;
+  if (n_steps < 0) return fail(ctx, GSW_E_INVALID, "n_steps must be >= 0");
+  const int nm = (int)b->ids.size();
+  int outer = 0;
+  bool stale = (b->exec == nullptr);
+  int remaining = 0;
+  for (int i = 0; i < nm; ++i) {
+    Model* m = find(ctx, b->ids[i]);
+    const int o = m->opts.batch_outer > 0 ? m->opts.batch_outer : 6;
+    if (o > outer) outer = o;
+    if (b->versions[i] != m->version) stale = true;
+    StepState& h = b->ss_host[i];
+    memset(&h, 0, sizeof(StepState));
+    h.step = (int)m->step;
+    h.n_steps = m->n_steps;
+    h.stop_at = (int)std::min<int64_t>((int64_t)m->n_steps, m->step + n_steps);
+    h.failed = m->failed ? GSW_E_STATE : 0;
+    h.tol = m->opts.tol;
+    h.max_iter = m->opts.max_iter;
+    h.inner_iters = m->opts.inner_iters > 0 ? m->opts.inner_iters : 1;
+    if (!m->failed) remaining = std::max(remaining, h.stop_at - h.step);
+  }
+  if (outer != b->outer) stale = true;
+  CK(cudaEventRecord(b->fork, ctx->stream));
+  CK(cudaStreamWaitEvent(b->origin, b->fork, 0));
+  CK(cudaMemcpyAsync(b->ss_dev, b->ss_host, sizeof(StepState) * nm, cudaMemcpyHostToDevice, b->origin));
+  if (stale && remaining > 0) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    CK(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+    CK(cudaEventRecord(b->fork, b->origin));
+    int64_t launches = 0;
+    for (int i = 0; i < nm; ++i) {
+      Model* m = find(ctx, b->ids[i]);
+      CK(cudaStreamWaitEvent(b->streams[i], b->fork, 0));
+      launches += issue_device_step(m, b->streams[i], b->ss_dev + i, outer);
+      CK(cudaEventRecord(b->joins[i], b->streams[i]));
+      CK(cudaStreamWaitEvent(b->origin, b->joins[i], 0));
+    }
+    cudaError_t ce = cudaStreamEndCapture(b->origin, &b->graph);
+    if (ce != cudaSuccess) return fail(ctx, GSW_E_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+    CK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    b->launches_per_step = launches;
+    b->outer = outer;
+    for (int i = 0; i < nm; ++i) b->versions[i] = find(ctx, b->ids[i])->version;
+  }
+  gsw_status st = GSW_OK;
+  const int chunk = 8;
+  while (remaining > 0) {
+    const int launch_n = std::min(remaining, chunk);
+    for (int s = 0; s < launch_n; ++s) CK(cudaGraphLaunch(b->exec, b->origin));
+    CK(cudaMemcpyAsync(b->ss_host, b->ss_dev, sizeof(StepState) * nm, cudaMemcpyDeviceToHost, b->origin));
+    CK(cudaStreamSynchronize(b->origin));
+    remaining = 0;
+    bool rewrite = false;
+    for (int i = 0; i < nm; ++i) {
+      Model* m = find(ctx, b->ids[i]);
+      StepState& h = b->ss_host[i];
+      const int advanced = h.step - (int)m->step;
+      m->step = h.step;
+      m->stats.steps_done += advanced;
+      m->stats.cg_iters_total += h.iters_total;
+      m->stats.inner_iters_total += h.inner_total;
+      m->stats.kernel_launches += (int64_t)launch_n * (b->launches_per_step / (nm > 0 ? nm : 1));
+      if (advanced > 0) {
+        m->stats.cg_iters_last = h.iters_last;
+        m->stats.relres_last = h.relres_last;
+      }
+      if (h.iters_max > m->stats.cg_iters_max) m->stats.cg_iters_max = h.iters_max;
+      h.iters_total = h.inner_total = 0;
+      rewrite = true;
+      if (h.failed && !m->failed) {
+        m->failed = true;
+        if (st == GSW_OK) {
+          st = h.failed == GSW_E_NOCONV ? GSW_E_NOCONV : (h.failed == GSW_E_NAN ? GSW_E_NAN : GSW_E_STATE);
+          fail(ctx, st, "model %d failed at step %d (%s)", b->ids[i], h.fail_step,
+               h.failed == GSW_E_NAN ? "non-finite residual" : "no convergence");
+        }
+      }
+      if (h.needs_host && !m->failed) {
+        // more outer iterations than the captured budget: finish this step on
+        // the host-driven path (same algorithm, iteration cap max_iter)
+        CK(cudaEventRecord(b->done_ev, b->origin));
+        CK(cudaStreamWaitEvent(ctx->stream, b->done_ev, 0));
+        gsw_status hs = step_mixed(ctx, m);
+        if (hs != GSW_OK) {
+          h.failed = hs;
+          h.fail_step = h.step;
+          if (st == GSW_OK) st = hs;  // message set by step_mixed
+        } else {
+          h.step = (int)m->step;
+          h.needs_host = 0;
+        }
+        CK(cudaEventRecord(b->fork, ctx->stream));
+        CK(cudaStreamWaitEvent(b->origin, b->fork, 0));
+      }
+      if (!m->failed && !h.failed) remaining = std::max(remaining, h.stop_at - h.step);
+    }
+    if (rewrite) CK(cudaMemcpyAsync(b->ss_dev, b->ss_host, sizeof(StepState) * nm, cudaMemcpyHostToDevice, b->origin));
+  }
+  CK(cudaEventRecord(b->done_ev, b->origin));
+  CK(cudaStreamWaitEvent(ctx->stream, b->done_ev, 0));
+  CK(cudaStreamSynchronize(b->origin));
+  return st;
+}
+
+gsw_status gsw_batch_destroy(gsw_ctx* ctx, int32_t batch_id) {
+  if (!ctx) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  auto it = ctx->batches.find(batch_id);
+  if (it == ctx->batches.end()) return fail(ctx, GSW_E_INVALID, "unknown batch %d", batch_id);
+  cudaStreamSynchronize(it->second->origin);
+  for (int id : it->second->ids) {
+    Model* m = find(ctx, id);
+    if (m) m->batch = 0;
+  }
+  batch_free(it->second);
+  ctx->batches.erase(it);
+  return GSW_OK;
+}
+
+gsw_status gsw_batch_launches(gsw_ctx* ctx, int32_t batch_id, int64_t* per_step) {
+  if (!ctx || !per_step) return GSW_E_INVALID;
+  auto it = ctx->batches.find(batch_id);
+  if (it == ctx->batches.end()) return fail(ctx, GSW_E_INVALID, "unknown batch %d", batch_id);
+  *per_step = it->second->launches_per_step;
   return GSW_OK;
 }
 
@@ -918,7 +1405,7 @@ gsw_status gsw_apply(gsw_ctx* ctx, int32_t model_id, int32_t which, const double
       return fail(ctx, GSW_E_STATE, "the reduced-precision operator needs a mixed precision mode");
     launch_to_lo(m->N, x_dev, m->d_lo, m->lo_half, m->w32, ctx->stream);
     const void* view = m->lo_half ? (const void*)&m->lo_h : (const void*)&m->lo_f;
-    launch_ebe_lo(m->lo_half, m->lo_half, view, m->d_lo, m->w32, m->partials, m->isc, ctx->stream);
+    launch_ebe_lo(m->lo_half, m->lo_half, view, m->d_lo, m->w32, m->partials, m->isc, ctx->stream, m->lo_variant);
     launch_from_f32(m->N, m->w32, y_dev, ctx->stream);
     CK(cudaGetLastError());
     return GSW_OK;
@@ -970,6 +1457,116 @@ gsw_status gsw_misfit(gsw_ctx* ctx, int32_t n_rec, int32_t n_t, const double* G,
   if (rc == 1) return fail(ctx, GSW_E_CUDA, "misfit: %s (%s)", msg, cudaGetErrorString(ce));
   if (rc == 2) return fail(ctx, GSW_E_NOMEM, "misfit: %s", msg);
   if (rc == 3) return fail(ctx, GSW_E_INVALID, "misfit: %s", msg);
+  return GSW_OK;
+}
+
+gsw_status gsw_set_learning(gsw_ctx* ctx, int32_t model_id, const gsw_learn_opts* opts) {
+  if (!ctx || !opts) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (!m->time_set) return fail(ctx, GSW_E_STATE, "call gsw_set_time first");
+  if (m->batch) return fail(ctx, GSW_E_STATE, "model %d belongs to a batch", model_id);
+  if (opts->enable) {
+    if (m->opts.precision == GSW_PREC_FP64)
+      return fail(ctx, GSW_E_STATE, "the learned guess runs with the mixed-precision solver");
+    if (opts->train_steps < 5 || opts->batch < 64 || opts->batch > 65536 || opts->iters_per_step < 0 ||
+        !(opts->lr > 0.f))
+      return fail(ctx, GSW_E_INVALID, "need train_steps >= 5, 64 <= batch <= 65536, iters_per_step >= 0, lr > 0");
+  }
+  m->learn = *opts;
+  if (opts->enable) {
+    TRY(mlp_alloc(ctx, m));
+    TRY(mlp_init(ctx, m, opts->seed));
+  }
+  return GSW_OK;
+}
+
+gsw_status gsw_mlp_params(gsw_ctx* ctx, int32_t model_id, double* get, const double* set) {
+  if (!ctx) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (!m->time_set) return fail(ctx, GSW_E_STATE, "call gsw_set_time first");
+  TRY(mlp_alloc(ctx, m));
+  std::vector<float> th(kMlpParams);
+  if (get) {
+    CK(cudaMemcpyAsync(th.data(), m->theta, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < kMlpParams; ++i) get[i] = th[i];
+  }
+  if (set) {
+    if (!finite_all(set, kMlpParams)) return fail(ctx, GSW_E_INVALID, "non-finite parameter");
+    for (int i = 0; i < kMlpParams; ++i) th[i] = (float)set[i];
+    CK(cudaMemcpyAsync(m->theta, th.data(), sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, ctx->stream));
+    launch_mlp_pack(m->theta, m->packed, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return GSW_OK;
+}
+
+gsw_status gsw_mlp_forward(gsw_ctx* ctx, int32_t model_id, int32_t n, const float* x, float* out) {
+  if (!ctx || !x || !out) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (!m->mlp_ready) return fail(ctx, GSW_E_STATE, "no MLP: call gsw_set_learning or gsw_mlp_params first");
+  if (n <= 0 || n > 65536) return fail(ctx, GSW_E_INVALID, "n must be 1..65536");
+  CK(cudaMemcpyAsync(m->trainX, x, sizeof(float) * 16 * n, cudaMemcpyHostToDevice, ctx->stream));
+  launch_mlp_infer(n, nullptr, 0, nullptr, nullptr, nullptr, 0.0, m->packed, nullptr, nullptr, m->trainX, m->trainY,
+                   ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, m->trainY, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return GSW_OK;
+}
+
+gsw_status gsw_mlp_grad(gsw_ctx* ctx, int32_t model_id, int32_t n, const float* x, const float* y, double* loss,
+                        double* grad) {
+  if (!ctx || !x || !y || !grad || !loss) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (!m->mlp_ready) return fail(ctx, GSW_E_STATE, "no MLP: call gsw_set_learning or gsw_mlp_params first");
+  if (n <= 0 || n > 65536) return fail(ctx, GSW_E_INVALID, "n must be 1..65536");
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemcpyAsync(m->trainX, x, sizeof(float) * 16 * n, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(m->trainY, y, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(m->grad, 0, sizeof(float) * kMlpParams, s));
+  CK(cudaMemsetAsync(&m->ms->loss, 0, sizeof(double), s));
+  if (launch_mlp_fwdbwd(n, m->trainX, m->trainY, m->theta, m->grad, &m->ms->loss, s))
+    return fail(ctx, GSW_E_CUDA, "training kernel configuration failed");
+  CK(cudaGetLastError());
+  std::vector<float> gh(kMlpParams);
+  CK(cudaMemcpyAsync(gh.data(), m->grad, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(loss, &m->ms->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemsetAsync(m->grad, 0, sizeof(float) * kMlpParams, s));
+  CK(cudaStreamSynchronize(s));
+  for (int i = 0; i < kMlpParams; ++i) grad[i] = gh[i];
+  return GSW_OK;
+}
+
+gsw_status gsw_mlp_state(gsw_ctx* ctx, int32_t model_id, double* out) {
+  if (!ctx || !out) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  for (int i = 0; i < 5; ++i) out[i] = 0.0;
+  if (m->mlp_ready) {
+    CK(cudaMemcpyAsync(out, &m->ms->loss, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  out[1] = (m->learn.enable && !m->mlp_off) ? 1.0 : 0.0;
+  double mean = 0.0;
+  const int64_t ks = m->std_r0_n < 5 ? m->std_r0_n : 5;
+  for (int64_t i = 0; i < ks; ++i) mean += m->std_r0_recent[i];
+  out[2] = ks ? mean / (double)ks : 0.0;
+  mean = 0.0;
+  const int64_t k = m->mlp_r0_n < 5 ? m->mlp_r0_n : 5;
+  for (int64_t i = 0; i < k; ++i) mean += m->mlp_r0_recent[i];
+  out[3] = k ? mean / (double)k : 0.0;
+  out[4] = (double)m->mlp_r0_n;
   return GSW_OK;
 }
 

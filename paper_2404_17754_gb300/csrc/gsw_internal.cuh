@@ -9,9 +9,8 @@ constexpr int kMaxMat = 32;        // materials (layers) per model
 constexpr int kNodeThreads = 256;  // node-wise kernels
 constexpr int kElemThreads = 128;  // element-by-element kernels
 constexpr int kMaxNodeBlocks = 152 * 8;
-constexpr int kLoBlock = 32;   // elements per block of the reduced-precision operator (one warp)
-constexpr int kLoWarps = 4;    // blocks (warps) per CTA
-constexpr int kLoThreads = kLoBlock * kLoWarps;
+constexpr int kLoBlock = 192;  // elements (and threads) per CTA of the reduced-precision operator
+constexpr int kLoNodesPerThread = 6;  // unique nodes of a block <= kLoBlock * this (checked at set-up)
 
 // Per-material coefficients. lam, mu, rho from (Vp, Vs, rho); alpha, beta the
 // Rayleigh fit; cK = 1 + 2 beta/dt and cM = 4/dt^2 + 2 alpha/dt scale the
@@ -38,6 +37,41 @@ struct CgScalars {
   int pad1;
   unsigned int counter;  // arrival counter of the last-block reductions
   unsigned int pad2;
+};
+
+// Scalars of the learned initial guess (one set per model).
+constexpr int kMlpParams = 5443;  // 16-64-64-3 MLP
+struct MlpScalars {
+  double sigma;  // RMS of the latest displacement increment
+  double loss;   // training loss accumulator
+  unsigned int counter;
+  unsigned int pad;
+};
+
+// Step counter and status of a model advanced on the device (batched,
+// graph-captured stepping): the host reads it only between steps.
+struct StepState {
+  int step;        // index of the next step to compute
+  int n_steps;
+  int active;      // this step runs (step < n_steps and no earlier failure)
+  int failed;      // sticky: status of the first failure (0 = none)
+  int fail_step;
+  int commit;      // this step converged: apply the Newmark update and record
+  int stop_at;     // the batch call advances the model up to this step
+  int needs_host;  // the outer budget ran out: the host completes this step
+  int iters_last, iters_max;
+  long long iters_total;
+  long long inner_total;
+  double relres_last;
+  double tol;
+  int max_iter;
+  int inner_iters;
+};
+
+// Device-driven inputs of a step (null pointers: the host drives the step).
+struct Drive {
+  const double* p;  // [n_steps] input samples
+  StepState* ss;
 };
 
 // Element / face / node data of one uploaded model (device pointers).
@@ -68,13 +102,12 @@ struct InnerScalars {
 // Element blocks with local node numbering: block b holds elements
 // [b * kLoBlock, (b + 1) * kLoBlock); its unique nodes are
 // nodes[ptr[b] .. ptr[b+1]) (bit 31 set: no other block and no absorbing face
-// touches the node), and lconn[k * E + e] is the local index of node k of e.
+// touches the node).  Local connectivity lives in the packed element records.
 struct BlockView {
   int n_blk;
   int max_local;
   const int32_t* ptr;
   const int32_t* nodes;
-  const uint16_t* lconn;
 };
 
 // Reduced-precision copy of a model for the inner solve.  SG: storage type of
@@ -84,9 +117,7 @@ struct LoView {
   int64_t N, E, F;
   int n_mat;
   BlockView blk;
-  const SG* geo;            // [9][E] barycentric gradients
-  const float* vol;         // [E] element volumes
-  const int32_t* emat;
+  const void* rec;          // [n_blk * kLoBlock] packed element records (operator order)
   const MatCoef* mat;
   const int32_t* fnode;     // [6][F]
   const float* fgeo;        // [6][F]
@@ -110,14 +141,20 @@ void launch_receivers(const ModelView& m, const double* xyz, double px, double p
                       double* rec_w, int* err, cudaStream_t s);
 void launch_ebe(int mode, const ModelView& m, const double* x, const double* v, const double* a,
                 double* y, double force, int dir, double* partials, CgScalars* cg,
-                cudaStream_t s);
+                cudaStream_t s, Drive dr = Drive{nullptr, nullptr});
 void launch_cg_init(const ModelView& m, const double* b, const double* v, const double* a,
                     double* x, double* q, double* partials, CgScalars* cg, cudaStream_t s);
 void launch_rhs_f32(const ModelView& m, const double* u, const double* v, const double* a, float* b32,
-                    double force, int dir, cudaStream_t s);
+                    double force, int dir, cudaStream_t s, Drive dr = Drive{nullptr, nullptr});
+// x0 = x (use_guess) or the predictor dt v + dt^2/2 a; writes u~ = u + x0,
+// v~ = v - (2/dt) x0, a~ = a + (4/dt) v - (4/dt^2) x0 for the one-pass residual
 void launch_cg_init_mixed(const ModelView& m, const float* b32, const double* u, const double* v, const double* a,
-                          double* x, double* ut, double* vt, double* r, double* q, double* partials, CgScalars* cg,
-                          cudaStream_t s);
+                          double* x, double* ut, double* vt, double* at, double* r, double* q, double* partials,
+                          CgScalars* cg, cudaStream_t s, const StepState* ss = nullptr, int use_guess = 0);
+// device-driven step bracket (batched stepping)
+void launch_step_begin(StepState* ss, CgScalars* cg, cudaStream_t s);
+void launch_step_end(StepState* ss, const CgScalars* cg, cudaStream_t s);
+void launch_step_advance(StepState* ss, cudaStream_t s);
 void launch_cg_rnorm(const ModelView& m, const double* r, double* partials, CgScalars* cg, cudaStream_t s);
 void launch_cg_residual(const ModelView& m, const double* b, double* q, double* r, double* z,
                         double* p, const double* dinv, double* partials, CgScalars* cg,
@@ -128,9 +165,9 @@ void launch_cg_update(const ModelView& m, double* x, double* r, double* z, const
 void launch_cg_pupdate(const ModelView& m, const double* z, double* p, const CgScalars* cg,
                        cudaStream_t s);
 void launch_newmark(const ModelView& m, const double* x, double* u, double* v, double* a,
-                    const CgScalars* cg, cudaStream_t s);
+                    const CgScalars* cg, cudaStream_t s, const StepState* ss = nullptr);
 void launch_record(const double* v, const int32_t* rec_node, const double* rec_w, int n_rec,
-                   double* wave, int n_steps, int step, cudaStream_t s);
+                   double* wave, int n_steps, int step, cudaStream_t s, const StepState* ss = nullptr);
 int ebe_blocks(const ModelView& m);
 
 // ---- mixed precision (gsw_mixed.cu) -------------------------------------------
@@ -141,21 +178,24 @@ void launch_block_fill(const ModelView& m, BlockView b, int32_t* nodes, uint16_t
                        int32_t* refcount, cudaStream_t s);
 void launch_block_mark(const ModelView& m, BlockView b, int32_t* nodes, int32_t* refcount,
                        int total, cudaStream_t s);
-void launch_lo_convert(const ModelView& m, int half_geo, void* geo_lo, float* vol32, float* fgeo32,
-                       const double* dinv, float* dinv32, double* partials, InnerScalars* sc,
+void launch_lo_convert(const ModelView& m, int n_blk, const uint16_t* lconn, int half_geo, void* rec,
+                       float* fgeo32, const double* dinv, float* dinv32, double* partials, InnerScalars* sc,
                        cudaStream_t s);
+size_t lo_record_bytes(int half_geo);
 // inner solve: half_vec selects __half storage of the search direction d
 // (padded to 4 entries per node)
 void launch_inner_init(int64_t N, const double* r, const float* dinv32, float* s, float* y,
                        float* t, void* d, int half_vec, float* w, double* partials,
                        InnerScalars* sc, const CgScalars* cg, cudaStream_t st);
 void launch_ebe_lo(int half_geo, int half_vec, const void* lo_view, const void* d, float* w,
-                   double* partials, InnerScalars* sc, cudaStream_t st);
+                   double* partials, InnerScalars* sc, cudaStream_t st, int variant,
+                   const CgScalars* outer = nullptr);
+constexpr int kLoVariants = 2;
 void launch_inner_update(int64_t N, float* y, float* s, float* t, const void* d, int half_vec,
                          float* w, const float* dinv32, double* partials, InnerScalars* sc,
-                         cudaStream_t st);
+                         cudaStream_t st, const CgScalars* outer);
 void launch_inner_dupdate(int64_t N, const float* t, void* d, int half_vec, const InnerScalars* sc,
-                          cudaStream_t st);
+                          cudaStream_t st, const CgScalars* outer);
 // conversions for the standalone reduced-precision operator (tests)
 void launch_to_lo(int64_t N, const double* x, void* d, int half_vec, float* w, cudaStream_t s);
 void launch_from_f32(int64_t N, const float* w, double* y, cudaStream_t s);
@@ -172,5 +212,22 @@ void launch_fcg_zbeta(const ModelView& m, const float* y, const double* r, const
 void launch_fcg_pupdate(const ModelView& m, const double* z, double* p, double* q,
                         const CgScalars* cg, cudaStream_t s);
 int node_blocks(int64_t n);
+
+// ---- learned initial guess (gsw_mlp.cu) ------------------------------------------
+void launch_mlp_pack(const float* theta, uint32_t* packed, cudaStream_t s);
+void launch_node_features(const ModelView& m, int n_mat, int32_t* node_mat, float* nodef, cudaStream_t s);
+void launch_mlp_sigma(int64_t N, const float* hist, int head, double* partials, MlpScalars* ms, cudaStream_t s);
+void launch_mlp_infer(int64_t N, const float* hist, int head, const float* nodef, const double* v, const double* a,
+                      double dt, const uint32_t* packed, const MlpScalars* ms, double* x, const float* xin,
+                      float* yout, cudaStream_t s);
+void launch_mlp_sample(int64_t N, int B, uint32_t seed, int step, int iter, const float* hist, int head,
+                       const float* nodef, const double* du, const double* v, const double* a, double dt,
+                       const MlpScalars* ms, float* X, float* Y, cudaStream_t s);
+int launch_mlp_fwdbwd(int B, const float* X, const float* Y, const float* theta, float* grad, double* loss,
+                      cudaStream_t s);
+void launch_mlp_adam(float* theta, float* grad, float* m, float* v, int t, float lr, cudaStream_t s);
+void launch_hist_push(int64_t N, const double* du, float* hist, int slot, const CgScalars* cg, cudaStream_t s,
+                      const StepState* ss = nullptr);
+int mlp_packed_words();
 
 }  // namespace gsw

@@ -315,16 +315,21 @@ __global__ void receiver_weights_kernel(ModelView m, const double* __restrict__ 
 //   kModeA   y = A x               (+ partial x.y when partials != nullptr)
 //   kModeK   y = K x,  kModeM y = M x,  kModeC y = C x
 //   kModeRhs y = f - K u + C v + M (a + (4/dt) v)  with x = u
-//   kModeRes y = f - K u~ - C v~ - M a  with x = u~ = u + dt v + dt^2/2 a,
-//            vv = v~ = v + dt a: the Newmark residual b - A du0 at the predictor
-//            du0 = dt v + dt^2/2 a, from a single stiffness application
+//   kModeRes y = f - K u~ + C v~ + M a~  with x = u~ = u + du0,
+//            vv = v~ = v - (2/dt) du0, aa = a~ = a + (4/dt) v - (4/dt^2) du0:
+//            the Newmark residual b - A du0 at an initial guess du0 from a
+//            single stiffness application
 template <int MODE>
 __global__ void __launch_bounds__(kElemThreads) ebe_kernel(ModelView m, const double* __restrict__ x,
                                                             const double* __restrict__ vv,
                                                             const double* __restrict__ aa, double* y,
                                                             double force, int dir, double* partials,
-                                                            CgScalars* cg) {
+                                                            CgScalars* cg, Drive dr) {
   if (cg != nullptr && ((volatile CgScalars*)cg)->done) return;
+  if (dr.ss != nullptr) {
+    if (!((volatile StepState*)dr.ss)->active) return;
+    force = 2.0 * dr.p[dr.ss->step];
+  }
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double dot = 0.0;
   if (t < m.E) {
@@ -354,7 +359,7 @@ __global__ void __launch_bounds__(kElemThreads) ebe_kernel(ModelView m, const do
       ms = mc.alpha;
     } else if (MODE == kModeRes) {
       ks = -1.0;
-      ms = -1.0;
+      ms = 1.0;
     } else {
       ks = 1.0;
       ms = 1.0;
@@ -369,11 +374,11 @@ __global__ void __launch_bounds__(kElemThreads) ebe_kernel(ModelView m, const do
 #pragma unroll
         for (int i = 0; i < 3; ++i) w[k][i] = fma(mc.beta, vv[3 * nd[k] + i], -x[3 * nd[k] + i]);
     } else if (MODE == kModeRes) {
-      // residual at the predictor: stiffness acts on u~ + beta v~ (x = u~, vv = v~)
+      // residual at the initial guess: stiffness acts on u~ - beta v~ (x = u~, vv = v~)
 #pragma unroll
       for (int k = 0; k < 10; ++k)
 #pragma unroll
-        for (int i = 0; i < 3; ++i) w[k][i] = fma(mc.beta, vv[3 * nd[k] + i], x[3 * nd[k] + i]);
+        for (int i = 0; i < 3; ++i) w[k][i] = fma(-mc.beta, vv[3 * nd[k] + i], x[3 * nd[k] + i]);
     } else {
 #pragma unroll
       for (int k = 0; k < 10; ++k)
@@ -389,7 +394,7 @@ __global__ void __launch_bounds__(kElemThreads) ebe_kernel(ModelView m, const do
         for (int i = 0; i < 3; ++i) f[k][i] = 0.0;
     }
     if (MODE == kModeRhs || MODE == kModeRes) {
-      // mass acts on a + (4/dt + alpha) v (right-hand side) or a + alpha v~ (residual)
+      // mass acts on a + (4/dt + alpha) v (right-hand side) or a~ + alpha v~ (residual)
       const double cv = (MODE == kModeRhs) ? 4.0 / m.dt + mc.alpha : mc.alpha;
 #pragma unroll
       for (int k = 0; k < 10; ++k)
@@ -408,7 +413,7 @@ __global__ void __launch_bounds__(kElemThreads) ebe_kernel(ModelView m, const do
     const int64_t fc = t - m.E;
     const double tag = m.fgeo[5 * m.F + fc];
     if (tag > 0.5) {
-      const double sc = (MODE == kModeA) ? 2.0 / m.dt : (MODE == kModeRes ? -1.0 : 1.0);
+      const double sc = (MODE == kModeA) ? 2.0 / m.dt : 1.0;
       const double As = sc * m.fgeo[fc] / 180.0, Ad = sc * m.fgeo[m.F + fc] / 180.0;
       const double n[3] = {m.fgeo[2 * m.F + fc], m.fgeo[3 * m.F + fc], m.fgeo[4 * m.F + fc]};
       int64_t nd[6];
@@ -468,7 +473,11 @@ __global__ void __launch_bounds__(kElemThreads) ebe_kernel(ModelView m, const do
 __global__ void __launch_bounds__(kElemThreads) rhs_f32_kernel(ModelView m, const double* __restrict__ u,
                                                               const double* __restrict__ vv,
                                                               const double* __restrict__ aa, float* b,
-                                                              double force, int dir) {
+                                                              double force, int dir, Drive dr) {
+  if (dr.ss != nullptr) {
+    if (!((volatile StepState*)dr.ss)->active) return;
+    force = 2.0 * dr.p[dr.ss->step];
+  }
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t < m.E) {
     const int64_t e = t;
@@ -576,24 +585,31 @@ __global__ void cg_init_kernel(int64_t N, const double* __restrict__ b, const do
   }
 }
 
-// Mixed-mode start of a step: ||b||^2 from the FP32 right-hand side,
-// predictor du0 = dt v + dt^2/2 a, predicted state u~ = u + du0 and
-// v~ = v + dt a (inputs of the single-pass residual), r = q = 0.
+// Mixed-mode start of a step: ||b||^2 from the FP32 right-hand side, the
+// initial guess du0 (the predictor dt v + dt^2/2 a, or the value already in x),
+// and the shifted state u~ = u + du0, v~ = v - (2/dt) du0,
+// a~ = a + (4/dt) v - (4/dt^2) du0 read by the single-pass residual; r = q = 0.
 __global__ void cg_init_mixed_kernel(int64_t N, const float* __restrict__ b32, const double* __restrict__ u,
                                      const double* __restrict__ v, const double* __restrict__ a, double dt,
                                      double* __restrict__ x, double* __restrict__ ut, double* __restrict__ vt,
-                                     double* __restrict__ r, double* __restrict__ q, double* partials,
-                                     CgScalars* cg) {
+                                     double* __restrict__ at, double* __restrict__ r, double* __restrict__ q,
+                                     double* partials, CgScalars* cg, const StepState* ss, int use_guess) {
+  if (ss != nullptr && !((volatile const StepState*)ss)->active) return;
   double bb = 0.0;
-  const double h = 0.5 * dt * dt;
+  const double h = 0.5 * dt * dt, c2 = 2.0 / dt, c4 = 4.0 / dt, c44 = 4.0 / (dt * dt);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N; i += (int64_t)gridDim.x * blockDim.x) {
     const double bi = (double)b32[i];
     bb = fma(bi, bi, bb);
     const double vi = v[i], ai = a[i];
-    const double x0 = fma(dt, vi, h * ai);
+    double x0 = fma(dt, vi, h * ai);
+    if (use_guess) {
+      const double g = x[i];
+      if (isfinite(g)) x0 = g;  // a non-finite guess falls back to the predictor
+    }
     x[i] = x0;
     ut[i] = u[i] + x0;
-    vt[i] = fma(dt, ai, vi);
+    vt[i] = fma(-c2, x0, vi);
+    at[i] = fma(-c44, x0, fma(c4, vi, ai));
     r[i] = 0.0;
     q[i] = 0.0;
   }
@@ -722,7 +738,8 @@ __global__ void cg_pupdate_kernel(int64_t N, const double* __restrict__ z, doubl
 
 __global__ void newmark_kernel(int64_t N, const double* __restrict__ x, double* __restrict__ u,
                                double* __restrict__ v, double* __restrict__ a, double dt,
-                               const CgScalars* cg) {
+                               const CgScalars* cg, const StepState* ss) {
+  if (ss != nullptr && !((volatile const StepState*)ss)->commit) return;
   const bool zero = cg->zero_rhs != 0;
   const double c1 = 2.0 / dt, c2 = 4.0 / (dt * dt), c3 = 4.0 / dt;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N;
@@ -737,7 +754,11 @@ __global__ void newmark_kernel(int64_t N, const double* __restrict__ x, double* 
 
 __global__ void record_kernel(const double* __restrict__ v, const int32_t* __restrict__ rec_node,
                               const double* __restrict__ rec_w, int n_rec, double* wave, int n_steps,
-                              int step) {
+                              int step, const StepState* ss) {
+  if (ss != nullptr) {
+    if (!((volatile const StepState*)ss)->commit) return;
+    step = ss->step;
+  }
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * n_rec) return;
   const int r = t / 3, c = t % 3;
@@ -790,27 +811,27 @@ void launch_receivers(const ModelView& m, const double* xyz, double px, double p
                                                               rec_node, rec_w, err);
 }
 void launch_ebe(int mode, const ModelView& m, const double* x, const double* v, const double* a,
-                double* y, double force, int dir, double* partials, CgScalars* cg, cudaStream_t s) {
+                double* y, double force, int dir, double* partials, CgScalars* cg, cudaStream_t s, Drive dr) {
   const int nb = ebe_blocks(m);
   if (nb == 0) return;
   switch (mode) {
     case kModeA:
-      ebe_kernel<kModeA><<<nb, kElemThreads, 0, s>>>(m, x, v, a, y, force, dir, partials, cg);
+      ebe_kernel<kModeA><<<nb, kElemThreads, 0, s>>>(m, x, v, a, y, force, dir, partials, cg, dr);
       break;
     case kModeK:
-      ebe_kernel<kModeK><<<nb, kElemThreads, 0, s>>>(m, x, v, a, y, force, dir, nullptr, nullptr);
+      ebe_kernel<kModeK><<<nb, kElemThreads, 0, s>>>(m, x, v, a, y, force, dir, nullptr, nullptr, dr);
       break;
     case kModeM:
-      ebe_kernel<kModeM><<<nb, kElemThreads, 0, s>>>(m, x, v, a, y, force, dir, nullptr, nullptr);
+      ebe_kernel<kModeM><<<nb, kElemThreads, 0, s>>>(m, x, v, a, y, force, dir, nullptr, nullptr, dr);
       break;
     case kModeC:
-      ebe_kernel<kModeC><<<nb, kElemThreads, 0, s>>>(m, x, v, a, y, force, dir, nullptr, nullptr);
+      ebe_kernel<kModeC><<<nb, kElemThreads, 0, s>>>(m, x, v, a, y, force, dir, nullptr, nullptr, dr);
       break;
     case kModeRes:
-      ebe_kernel<kModeRes><<<nb, kElemThreads, 0, s>>>(m, x, v, a, y, force, dir, nullptr, nullptr);
+      ebe_kernel<kModeRes><<<nb, kElemThreads, 0, s>>>(m, x, v, a, y, force, dir, nullptr, nullptr, dr);
       break;
     default:
-      ebe_kernel<kModeRhs><<<nb, kElemThreads, 0, s>>>(m, x, v, a, y, force, dir, nullptr, nullptr);
+      ebe_kernel<kModeRhs><<<nb, kElemThreads, 0, s>>>(m, x, v, a, y, force, dir, nullptr, nullptr, dr);
       break;
   }
 }
@@ -819,15 +840,15 @@ void launch_cg_init(const ModelView& m, const double* b, const double* v, const 
   cg_init_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, b, v, a, m.dt, x, q, partials, cg);
 }
 void launch_rhs_f32(const ModelView& m, const double* u, const double* v, const double* a, float* b32,
-                    double force, int dir, cudaStream_t s) {
+                    double force, int dir, cudaStream_t s, Drive dr) {
   const int nb = ebe_blocks(m);
-  if (nb > 0) rhs_f32_kernel<<<nb, kElemThreads, 0, s>>>(m, u, v, a, b32, force, dir);
+  if (nb > 0) rhs_f32_kernel<<<nb, kElemThreads, 0, s>>>(m, u, v, a, b32, force, dir, dr);
 }
 void launch_cg_init_mixed(const ModelView& m, const float* b32, const double* u, const double* v, const double* a,
-                          double* x, double* ut, double* vt, double* r, double* q, double* partials, CgScalars* cg,
-                          cudaStream_t s) {
-  cg_init_mixed_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, b32, u, v, a, m.dt, x, ut, vt, r, q,
-                                                                       partials, cg);
+                          double* x, double* ut, double* vt, double* at, double* r, double* q, double* partials,
+                          CgScalars* cg, cudaStream_t s, const StepState* ss, int use_guess) {
+  cg_init_mixed_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, b32, u, v, a, m.dt, x, ut, vt, at, r, q,
+                                                                       partials, cg, ss, use_guess);
 }
 void launch_cg_rnorm(const ModelView& m, const double* r, double* partials, CgScalars* cg, cudaStream_t s) {
   cg_rnorm_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, r, partials, cg);
@@ -847,13 +868,13 @@ void launch_cg_pupdate(const ModelView& m, const double* z, double* p, const CgS
   cg_pupdate_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, z, p, cg);
 }
 void launch_newmark(const ModelView& m, const double* x, double* u, double* v, double* a,
-                    const CgScalars* cg, cudaStream_t s) {
-  newmark_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, x, u, v, a, m.dt, cg);
+                    const CgScalars* cg, cudaStream_t s, const StepState* ss) {
+  newmark_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, x, u, v, a, m.dt, cg, ss);
 }
 void launch_record(const double* v, const int32_t* rec_node, const double* rec_w, int n_rec,
-                   double* wave, int n_steps, int step, cudaStream_t s) {
+                   double* wave, int n_steps, int step, cudaStream_t s, const StepState* ss) {
   if (n_rec == 0) return;
-  record_kernel<<<(3 * n_rec + 127) / 128, 128, 0, s>>>(v, rec_node, rec_w, n_rec, wave, n_steps, step);
+  record_kernel<<<(3 * n_rec + 127) / 128, 128, 0, s>>>(v, rec_node, rec_w, n_rec, wave, n_steps, step, ss);
 }
 
 }  // namespace gsw

@@ -54,7 +54,34 @@ __device__ __forceinline__ void load3(const __half* p, float& a, float& b, float
   c = __low2float(h1);
 }
 
-constexpr int kSortN = 512;  // >= 10 * kLoBlock, power of two
+// Operator element order inside a block: warp w, lane l processes element
+// 6 l + w of the block.  With the 6 Kuhn tetrahedra of each cell stored
+// consecutively, a warp then holds congruent tetrahedra of 32 different cells,
+// so the 32 lanes of one shared-memory atomic never target the same node.
+__host__ __device__ __forceinline__ int lo_elem_of_pos(int p) { return 6 * (p % 32) + p / 32; }
+
+// Packed per-element record of the reduced-precision operator.
+struct LoRecH {   // 48 bytes: FP16 gradients
+  uint16_t lc[10];
+  __half g[9];
+  uint16_t pad0;
+  float vol;
+  uint16_t mat;
+  uint16_t pad1;
+};
+struct LoRecF {   // 64 bytes: FP32 gradients
+  uint16_t lc[10];
+  float g[9];
+  float vol;
+  uint16_t mat;
+  uint16_t pad1;
+};
+template <typename SG> struct LoRec;
+template <> struct LoRec<__half> { typedef LoRecH type; static constexpr int words = 3; };
+template <> struct LoRec<float> { typedef LoRecF type; static constexpr int words = 4; };
+static_assert(sizeof(LoRecH) == 48 && sizeof(LoRecF) == 64, "record layout");
+
+constexpr int kSortN = 2048;  // >= 10 * kLoBlock, power of two
 
 // ------------------------------------------------------------------------------
 // Element blocks: unique nodes per block via an in-shared-memory bitonic sort
@@ -113,7 +140,7 @@ __global__ void block_fill_kernel(ModelView m, BlockView bv, int32_t* nodes, uin
   __syncthreads();
   // inclusive scan of flags (Hillis-Steele, in place with a temporary)
   for (int off = 1; off < kSortN; off <<= 1) {
-    int v[kSortN / 256];
+    int v[kSortN / 256];  // blockDim.x == 256
 #pragma unroll
     for (int j = 0; j < kSortN / 256; ++j) {
       const int i = threadIdx.x + j * 256;
@@ -141,20 +168,24 @@ __global__ void block_fill_kernel(ModelView m, BlockView bv, int32_t* nodes, uin
   // compact the unique keys to the front of `keys` (reuse flag as storage)
   for (int i = threadIdx.x; i < nu; i += blockDim.x) flag[i] = nodes[base + i];
   __syncthreads();
-  const int64_t e0 = (int64_t)b * kLoBlock;
-  const int ne = (int)((m.E - e0) < kLoBlock ? (m.E - e0) : kLoBlock);
-  for (int i = threadIdx.x; i < 10 * ne; i += blockDim.x) {
-    const int k = i / ne, el = i % ne;
-    const int g = m.conn[(int64_t)k * m.E + e0 + el];
-    int lo = 0, hi = nu - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (flag[mid] < g)
-        lo = mid + 1;
-      else
-        hi = mid;
+  // local indices in the operator's element order: position p = w * 32 + lane
+  // of block b holds element b * kLoBlock + 6 * lane + w
+  for (int i = threadIdx.x; i < 10 * kLoBlock; i += blockDim.x) {
+    const int k = i / kLoBlock, pl = i % kLoBlock;
+    const int64_t e = (int64_t)b * kLoBlock + lo_elem_of_pos(pl);
+    int lo = 0;
+    if (e < m.E) {
+      const int g = m.conn[(int64_t)k * m.E + e];
+      int hi = nu - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (flag[mid] < g)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
     }
-    lconn[(int64_t)k * m.E + e0 + el] = (uint16_t)lo;
+    lconn[(int64_t)k * ((int64_t)bv.n_blk * kLoBlock) + (int64_t)b * kLoBlock + pl] = (uint16_t)lo;
   }
 }
 
@@ -172,12 +203,26 @@ __global__ void block_mark_kernel(int total, int32_t* nodes, const int32_t* refc
   if (refcount[g] == 1) nodes[i] = (int32_t)((uint32_t)g | 0x80000000u);
 }
 
+// Element records in operator order (invalid positions of the last block get
+// zero volume, so they contribute nothing), FP32 face data and D^-1.
 template <typename SG>
-__global__ void lo_convert_kernel(ModelView m, SG* geo_lo, float* vol32, float* fgeo32, const double* dinv,
-                                  float* dinv32) {
+__global__ void lo_convert_kernel(ModelView m, int n_blk, const uint16_t* __restrict__ lconn,
+                                  typename LoRec<SG>::type* rec, float* fgeo32, const double* dinv, float* dinv32) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t < 9 * m.E) geo_lo[t] = from_f<SG>((float)m.geo[t]);
-  if (t < m.E) vol32[t] = (float)m.geo[9 * m.E + t];
+  const int64_t P = (int64_t)n_blk * kLoBlock;
+  if (t < P) {
+    const int64_t b = t / kLoBlock;
+    const int pl = (int)(t % kLoBlock);
+    const int64_t e = b * kLoBlock + lo_elem_of_pos(pl);
+    typename LoRec<SG>::type r;
+    for (int k = 0; k < 10; ++k) r.lc[k] = lconn[(int64_t)k * P + t];
+    const bool ok = e < m.E;
+    for (int k = 0; k < 9; ++k) r.g[k] = from_f<SG>(ok ? (float)m.geo[k * m.E + e] : 0.f);
+    r.vol = ok ? (float)m.geo[9 * m.E + e] : 0.f;
+    r.mat = ok ? (uint16_t)m.emat[e] : 0;
+    r.pad1 = 0;
+    rec[t] = r;
+  }
   if (t < 6 * m.F) fgeo32[t] = (float)m.fgeo[t];
   if (t < 6 * m.N) dinv32[t] = (float)dinv[t];
 }
@@ -195,16 +240,19 @@ __global__ void dinv_mean_kernel(int64_t N, const double* __restrict__ dinv, dou
 // Reduced-precision element-by-element product w = A d (+ partial d . w)
 // ------------------------------------------------------------------------------
 
-// Each warp owns one block of kLoBlock consecutive elements: it gathers the
-// block's unique nodes into its own shared-memory slice, applies the elements
-// (one per lane) with shared-memory atomics, and writes the block's nodes
-// back; warps never wait for one another, so gather, compute and write-back
-// phases of different warps overlap.  CTAs after the element CTAs apply the
-// absorbing faces with global atomics.
-template <typename SG, typename SD>
-__global__ void __launch_bounds__(kLoThreads) ebe_lo_kernel(LoView<SG> m, const SD* __restrict__ d,
-                                                             float* __restrict__ w, double* partials,
-                                                             InnerScalars* sc) {
+// One CTA per block of kLoBlock elements: the CTA gathers the block's unique
+// nodes into shared memory, each thread applies one element (records are
+// loaded as 16-byte vectors before the gather so their latency overlaps it)
+// with shared-memory atomics, and the CTA writes each unique node once (a
+// plain store when no other block or absorbing face touches it).  CTAs after
+// the element blocks apply the absorbing faces with global atomics.
+template <typename SG, typename SD, int MINB>
+__global__ void __launch_bounds__(kLoBlock, MINB) ebe_lo_kernel(LoView<SG> m, const SD* __restrict__ d,
+                                                           float* __restrict__ w, double* partials,
+                                                           InnerScalars* sc, const CgScalars* outer) {
+  if (outer != nullptr && ((volatile const CgScalars*)outer)->done) return;
+  typedef typename LoRec<SG>::type Rec;
+  constexpr int RW = LoRec<SG>::words;
   extern __shared__ float sm[];
   __shared__ float matc[kMaxMat][3];
   if (threadIdx.x < m.n_mat) {
@@ -213,61 +261,77 @@ __global__ void __launch_bounds__(kLoThreads) ebe_lo_kernel(LoView<SG> m, const 
     matc[threadIdx.x][1] = (float)(c.cK * c.mu / 20.0);
     matc[threadIdx.x][2] = (float)(c.cM * c.rho / 420.0);
   }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n_elem_ctas = (m.blk.n_blk + kLoWarps - 1) / kLoWarps;
   float dot = 0.f;
-  if ((int)blockIdx.x < n_elem_ctas) {
-    const int b = blockIdx.x * kLoWarps + warp;
-    if (b < m.blk.n_blk) {
-      float* xs = sm + (size_t)warp * 6 * m.blk.max_local;
-      float* ys = xs + 3 * m.blk.max_local;
-      const int n0 = m.blk.ptr[b], nn = m.blk.ptr[b + 1] - n0;
-      for (int i = lane; i < nn; i += 32) {
-        const int64_t g = m.blk.nodes[n0 + i] & 0x7fffffff;
-        float a0, a1, a2;
-        load3(d + 4 * g, a0, a1, a2);
-        xs[3 * i] = a0;
-        xs[3 * i + 1] = a1;
-        xs[3 * i + 2] = a2;
+  const int b = blockIdx.x;
+  if (b < m.blk.n_blk) {
+    float* xs = sm;
+    float* ys = sm + 3 * m.blk.max_local;
+    union {
+      uint4 v[RW];
+      Rec r;
+    } u;
+    const uint4* rp = reinterpret_cast<const uint4*>(m.rec) + ((int64_t)b * kLoBlock + threadIdx.x) * RW;
+#pragma unroll
+    for (int q = 0; q < RW; ++q) u.v[q] = __ldg(rp + q);
+    const int n0 = m.blk.ptr[b], nn = m.blk.ptr[b + 1] - n0;
+    // each thread owns nodes threadIdx.x + j * kLoBlock (j < kLoNodesPerThread):
+    // all index loads first, then all gathers, so their latencies overlap
+    int32_t raw[kLoNodesPerThread];
+#pragma unroll
+    for (int j = 0; j < kLoNodesPerThread; ++j) {
+      const int i = threadIdx.x + j * kLoBlock;
+      raw[j] = (i < nn) ? m.blk.nodes[n0 + i] : 0;
+    }
+    float xv[kLoNodesPerThread][3];
+#pragma unroll
+    for (int j = 0; j < kLoNodesPerThread; ++j) {
+      const int i = threadIdx.x + j * kLoBlock;
+      if (i < nn) load3(d + 4 * (int64_t)(raw[j] & 0x7fffffff), xv[j][0], xv[j][1], xv[j][2]);
+    }
+#pragma unroll
+    for (int j = 0; j < kLoNodesPerThread; ++j) {
+      const int i = threadIdx.x + j * kLoBlock;
+      if (i < nn) {
+        xs[3 * i] = xv[j][0];
+        xs[3 * i + 1] = xv[j][1];
+        xs[3 * i + 2] = xv[j][2];
         ys[3 * i] = 0.f;
         ys[3 * i + 1] = 0.f;
         ys[3 * i + 2] = 0.f;
       }
-      __syncwarp();
-      const int64_t e = (int64_t)b * kLoBlock + lane;
-      if (e < m.E) {
-        int lc[10];
+    }
+    __syncthreads();
+    {
+      float g[3][3];
 #pragma unroll
-        for (int k = 0; k < 10; ++k) lc[k] = m.blk.lconn[k * m.E + e];
-        float g[3][3];
+      for (int mm = 0; mm < 3; ++mm)
 #pragma unroll
-        for (int mm = 0; mm < 3; ++mm)
+        for (int i = 0; i < 3; ++i) g[mm][i] = to_f(u.r.g[3 * mm + i]);
+      const float V = u.r.vol;
+      const int mt = u.r.mat;
+      const float lamS = matc[mt][0] * V, muS = matc[mt][1] * V, mS = matc[mt][2] * V;
+      float wv[10][3], f[10][3];
 #pragma unroll
-          for (int i = 0; i < 3; ++i) g[mm][i] = to_f(m.geo[(3 * mm + i) * m.E + e]);
-        const float V = m.vol[e];
-        const int mt = m.emat[e];
-        const float lamS = matc[mt][0] * V, muS = matc[mt][1] * V, mS = matc[mt][2] * V;
-        float wv[10][3], f[10][3];
+      for (int k = 0; k < 10; ++k)
 #pragma unroll
-        for (int k = 0; k < 10; ++k)
+        for (int i = 0; i < 3; ++i) wv[k][i] = xs[3 * u.r.lc[k] + i];
+      stiffness_apply<float>(wv, g, lamS, muS, f);
+      mass_apply<float>(wv, mS, f);
 #pragma unroll
-          for (int i = 0; i < 3; ++i) wv[k][i] = xs[3 * lc[k] + i];
-        stiffness_apply<float>(wv, g, lamS, muS, f);
-        mass_apply<float>(wv, mS, f);
+      for (int k = 0; k < 10; ++k)
 #pragma unroll
-        for (int k = 0; k < 10; ++k)
+        for (int i = 0; i < 3; ++i) {
+          atomicAdd(ys + 3 * u.r.lc[k] + i, f[k][i]);
+          dot = fmaf(wv[k][i], f[k][i], dot);
+        }
+    }
+    __syncthreads();
 #pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            atomicAdd(ys + 3 * lc[k] + i, f[k][i]);
-            dot = fmaf(wv[k][i], f[k][i], dot);
-          }
-      }
-      __syncwarp();
-      for (int i = lane; i < nn; i += 32) {
-        const int32_t raw = m.blk.nodes[n0 + i];
-        const int64_t g = raw & 0x7fffffff;
-        if (raw < 0) {
+    for (int j = 0; j < kLoNodesPerThread; ++j) {
+      const int i = threadIdx.x + j * kLoBlock;
+      if (i < nn) {
+        const int64_t g = raw[j] & 0x7fffffff;
+        if (raw[j] < 0) {
           w[3 * g] = ys[3 * i];
           w[3 * g + 1] = ys[3 * i + 1];
           w[3 * g + 2] = ys[3 * i + 2];
@@ -280,7 +344,7 @@ __global__ void __launch_bounds__(kLoThreads) ebe_lo_kernel(LoView<SG> m, const 
     }
   } else {
     // absorbing faces: (2/dt) C_abs d
-    const int64_t fc = (int64_t)(blockIdx.x - n_elem_ctas) * kLoThreads + threadIdx.x;
+    const int64_t fc = (int64_t)(b - m.blk.n_blk) * kLoBlock + threadIdx.x;
     if (fc < m.F && m.fgeo[5 * m.F + fc] > 0.5f) {
       const float sc2 = (float)(2.0 / m.dt) / 180.f;
       const float As = sc2 * m.fgeo[fc], Ad = sc2 * m.fgeo[m.F + fc];
@@ -333,6 +397,7 @@ __global__ void inner_init_kernel(int64_t N, const double* __restrict__ r, const
                                   float* __restrict__ s, float* __restrict__ y, float* __restrict__ t,
                                   SD* __restrict__ d, float* __restrict__ w, double* partials,
                                   InnerScalars* sc, const CgScalars* cg) {
+  if (((volatile const CgScalars*)cg)->done) return;
   const double rr = ((volatile const CgScalars*)cg)->rr;
   const double dm = ((volatile const InnerScalars*)sc)->dinv_mean;
   const double scale = (rr > 0.0 ? sqrt(3.0 * (double)N / rr) : 1.0) / (dm > 0.0 ? dm : 1.0);
@@ -365,7 +430,8 @@ __global__ void inner_init_kernel(int64_t N, const double* __restrict__ r, const
 template <typename SD>
 __global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __restrict__ s, float* __restrict__ t,
                                     const SD* __restrict__ d, float* __restrict__ w, const float* __restrict__ dinv,
-                                    double* partials, InnerScalars* sc) {
+                                    double* partials, InnerScalars* sc, const CgScalars* outer) {
+  if (outer != nullptr && ((volatile const CgScalars*)outer)->done) return;
   const double st_old = ((volatile InnerScalars*)sc)->st, dw = ((volatile InnerScalars*)sc)->dw;
   const float alpha = (dw != 0.0) ? (float)(st_old / dw) : 0.f;
   float st = 0.f;
@@ -395,7 +461,8 @@ __global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __r
 
 template <typename SD>
 __global__ void inner_dupdate_kernel(int64_t N, const float* __restrict__ t, SD* __restrict__ d,
-                                     const InnerScalars* sc) {
+                                     const InnerScalars* sc, const CgScalars* outer) {
+  if (outer != nullptr && ((volatile const CgScalars*)outer)->done) return;
   const float beta = (float)((volatile const InnerScalars*)sc)->beta;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
@@ -433,6 +500,7 @@ __global__ void fcg_residual_kernel(int64_t N, const double* __restrict__ b, dou
 __global__ void fcg_first_kernel(int64_t N, const float* __restrict__ y, const double* __restrict__ r,
                                  double* __restrict__ z, double* __restrict__ p, double* partials, CgScalars* cg,
                                  const InnerScalars* sc) {
+  if (((volatile CgScalars*)cg)->done) return;
   const double inv = 1.0 / ((volatile const InnerScalars*)sc)->scale;
   double rz = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N; i += (int64_t)gridDim.x * blockDim.x) {
@@ -448,6 +516,7 @@ __global__ void fcg_first_kernel(int64_t N, const float* __restrict__ y, const d
 __global__ void fcg_update_kernel(int64_t N, double* __restrict__ x, double* __restrict__ r,
                                   const double* __restrict__ p, const double* __restrict__ q, double* partials,
                                   CgScalars* cg) {
+  if (((volatile CgScalars*)cg)->done) return;
   const double alpha = ((volatile CgScalars*)cg)->rz / ((volatile CgScalars*)cg)->pq;
   double rr = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N; i += (int64_t)gridDim.x * blockDim.x) {
@@ -477,6 +546,7 @@ __global__ void fcg_update_kernel(int64_t N, double* __restrict__ x, double* __r
 __global__ void fcg_zbeta_kernel(int64_t N, const float* __restrict__ y, const double* __restrict__ r,
                                  const double* __restrict__ q, double* __restrict__ z, double* partials,
                                  CgScalars* cg, const InnerScalars* sc) {
+  if (((volatile CgScalars*)cg)->done) return;
   const double inv = 1.0 / ((volatile const InnerScalars*)sc)->scale;
   double zq = 0.0, rz = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N; i += (int64_t)gridDim.x * blockDim.x) {
@@ -498,11 +568,54 @@ __global__ void fcg_zbeta_kernel(int64_t N, const float* __restrict__ y, const d
 
 __global__ void fcg_pupdate_kernel(int64_t N, const double* __restrict__ z, double* __restrict__ p,
                                    double* __restrict__ q, const CgScalars* cg) {
+  if (((volatile const CgScalars*)cg)->done) return;
   const double beta = ((volatile const CgScalars*)cg)->beta;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N; i += (int64_t)gridDim.x * blockDim.x) {
     p[i] = fma(beta, p[i], z[i]);
     q[i] = 0.0;
   }
+}
+
+// ------------------------------------------------------------------------------
+// Device-driven step bracket (batched, graph-captured stepping)
+// ------------------------------------------------------------------------------
+
+__global__ void step_begin_kernel(StepState* ss, CgScalars* cg) {
+  const int active = (ss->step < ss->n_steps) && (ss->step < ss->stop_at) && (ss->failed == 0) &&
+                     (ss->needs_host == 0);
+  ss->active = active;
+  ss->commit = 0;
+  cg->iter = 0;
+  cg->done = active ? 0 : 1;
+  cg->status = 0;
+  cg->zero_rhs = 0;
+  cg->relres = 0.0;
+  cg->tol = ss->tol;
+  cg->max_iter = ss->max_iter;
+}
+
+// After the fixed outer-iteration budget: commit a converged step, record a
+// failure (non-finite value, or the outer-iteration cap), or hand a step that
+// needs more outer iterations than the budget to the host.
+__global__ void step_end_kernel(StepState* ss, const CgScalars* cg) {
+  if (!ss->active) return;
+  if (cg->status != 0) {
+    ss->failed = cg->status;
+    ss->fail_step = ss->step;
+  } else if (!cg->done) {
+    ss->needs_host = 1;
+  } else {
+    ss->commit = 1;
+    ss->iters_last = cg->iter;
+    if (cg->iter > ss->iters_max) ss->iters_max = cg->iter;
+    ss->iters_total += cg->iter;
+    ss->inner_total += (long long)cg->iter * ss->inner_iters;
+    ss->relres_last = cg->relres;
+  }
+}
+
+__global__ void step_advance_kernel(StepState* ss) {
+  if (ss->commit) ss->step += 1;
 }
 
 template <typename SD>
@@ -525,6 +638,9 @@ __global__ void from_f32_kernel(int64_t n, const float* __restrict__ w, double* 
 // Launchers
 // ------------------------------------------------------------------------------
 
+void launch_step_begin(StepState* ss, CgScalars* cg, cudaStream_t s) { step_begin_kernel<<<1, 1, 0, s>>>(ss, cg); }
+void launch_step_end(StepState* ss, const CgScalars* cg, cudaStream_t s) { step_end_kernel<<<1, 1, 0, s>>>(ss, cg); }
+void launch_step_advance(StepState* ss, cudaStream_t s) { step_advance_kernel<<<1, 1, 0, s>>>(ss); }
 void launch_to_lo(int64_t N, const double* x, void* d, int half_vec, float* w, cudaStream_t s) {
   if (half_vec)
     to_lo_kernel<__half><<<node_blocks(3 * N), kNodeThreads, 0, s>>>(3 * N, x, (__half*)d, w);
@@ -541,7 +657,7 @@ void launch_block_count(const ModelView& m, int n_blk, int32_t* counts, cudaStre
 }
 void launch_block_fill(const ModelView& m, BlockView b, int32_t* nodes, uint16_t* lconn, int32_t* refcount,
                        cudaStream_t s) {
-  block_fill_kernel<<<b.n_blk, 256, 0, s>>>(m, b, nodes, lconn, refcount);
+  block_fill_kernel<<<b.n_blk, 256, 0, s>>>(m, b, nodes, lconn, refcount);  // lconn: [10][n_blk * kLoBlock]
   if (m.F > 0) face_refcount_kernel<<<(unsigned)((m.F + 255) / 256), 256, 0, s>>>(m, refcount);
 }
 void launch_block_mark(const ModelView& m, BlockView b, int32_t* nodes, int32_t* refcount, int total,
@@ -550,18 +666,20 @@ void launch_block_mark(const ModelView& m, BlockView b, int32_t* nodes, int32_t*
   (void)b;
   block_mark_kernel<<<(total + 255) / 256, 256, 0, s>>>(total, nodes, refcount);
 }
-void launch_lo_convert(const ModelView& m, int half_geo, void* geo_lo, float* vol32, float* fgeo32,
-                       const double* dinv, float* dinv32, double* partials, InnerScalars* sc, cudaStream_t s) {
-  int64_t n = 9 * m.E;
+void launch_lo_convert(const ModelView& m, int n_blk, const uint16_t* lconn, int half_geo, void* rec,
+                       float* fgeo32, const double* dinv, float* dinv32, double* partials, InnerScalars* sc,
+                       cudaStream_t s) {
+  int64_t n = (int64_t)n_blk * kLoBlock;
   if (6 * m.F > n) n = 6 * m.F;
   if (6 * m.N > n) n = 6 * m.N;
   const unsigned g = (unsigned)((n + 255) / 256);
   if (half_geo)
-    lo_convert_kernel<__half><<<g, 256, 0, s>>>(m, (__half*)geo_lo, vol32, fgeo32, dinv, dinv32);
+    lo_convert_kernel<__half><<<g, 256, 0, s>>>(m, n_blk, lconn, (LoRecH*)rec, fgeo32, dinv, dinv32);
   else
-    lo_convert_kernel<float><<<g, 256, 0, s>>>(m, (float*)geo_lo, vol32, fgeo32, dinv, dinv32);
+    lo_convert_kernel<float><<<g, 256, 0, s>>>(m, n_blk, lconn, (LoRecF*)rec, fgeo32, dinv, dinv32);
   dinv_mean_kernel<<<node_blocks(m.N), kNodeThreads, 0, s>>>(m.N, dinv, partials, sc);
 }
+size_t lo_record_bytes(int half_geo) { return half_geo ? sizeof(LoRecH) : sizeof(LoRecF); }
 void launch_inner_init(int64_t N, const double* r, const float* dinv32, float* s, float* y, float* t, void* d,
                        int half_vec, float* w, double* partials, InnerScalars* sc, const CgScalars* cg,
                        cudaStream_t st) {
@@ -572,41 +690,50 @@ void launch_inner_init(int64_t N, const double* r, const float* dinv32, float* s
     inner_init_kernel<float><<<node_blocks(N), kNodeThreads, 0, st>>>(N, r, dinv32, s, y, t, (float*)d, w,
                                                                       partials, sc, cg);
 }
+// variant: 0 -> up to 3 CTAs per SM (no register cap below 96), 1 -> 4 CTAs
+// per SM (80 registers); picked per model by the set-up autotuner.
+template <typename SG, typename SD>
+static void ebe_lo_launch(int variant, const LoView<SG>& m, const SD* d, float* w, double* partials,
+                          InnerScalars* sc, cudaStream_t st, const CgScalars* outer) {
+  const unsigned g = (unsigned)(m.blk.n_blk + (m.F + kLoBlock - 1) / kLoBlock);
+  const size_t smem = sizeof(float) * 6 * (size_t)m.blk.max_local;
+  if (variant == 1)
+    ebe_lo_kernel<SG, SD, 4><<<g, kLoBlock, smem, st>>>(m, d, w, partials, sc, outer);
+  else
+    ebe_lo_kernel<SG, SD, 1><<<g, kLoBlock, smem, st>>>(m, d, w, partials, sc, outer);
+}
 void launch_ebe_lo(int half_geo, int half_vec, const void* lo_view, const void* d, float* w, double* partials,
-                   InnerScalars* sc, cudaStream_t st) {
+                   InnerScalars* sc, cudaStream_t st, int variant, const CgScalars* outer) {
   if (half_geo) {
     const LoView<__half>& m = *(const LoView<__half>*)lo_view;
-    const unsigned g = (unsigned)((m.blk.n_blk + kLoWarps - 1) / kLoWarps + (m.F + kLoThreads - 1) / kLoThreads);
-    const size_t smem = sizeof(float) * 6 * (size_t)m.blk.max_local * kLoWarps;
     if (half_vec)
-      ebe_lo_kernel<__half, __half><<<g, kLoThreads, smem, st>>>(m, (const __half*)d, w, partials, sc);
+      ebe_lo_launch<__half, __half>(variant, m, (const __half*)d, w, partials, sc, st, outer);
     else
-      ebe_lo_kernel<__half, float><<<g, kLoThreads, smem, st>>>(m, (const float*)d, w, partials, sc);
+      ebe_lo_launch<__half, float>(variant, m, (const float*)d, w, partials, sc, st, outer);
   } else {
     const LoView<float>& m = *(const LoView<float>*)lo_view;
-    const unsigned g = (unsigned)((m.blk.n_blk + kLoWarps - 1) / kLoWarps + (m.F + kLoThreads - 1) / kLoThreads);
-    const size_t smem = sizeof(float) * 6 * (size_t)m.blk.max_local * kLoWarps;
     if (half_vec)
-      ebe_lo_kernel<float, __half><<<g, kLoThreads, smem, st>>>(m, (const __half*)d, w, partials, sc);
+      ebe_lo_launch<float, __half>(variant, m, (const __half*)d, w, partials, sc, st, outer);
     else
-      ebe_lo_kernel<float, float><<<g, kLoThreads, smem, st>>>(m, (const float*)d, w, partials, sc);
+      ebe_lo_launch<float, float>(variant, m, (const float*)d, w, partials, sc, st, outer);
   }
 }
 void launch_inner_update(int64_t N, float* y, float* s, float* t, const void* d, int half_vec, float* w,
-                         const float* dinv32, double* partials, InnerScalars* sc, cudaStream_t st) {
+                         const float* dinv32, double* partials, InnerScalars* sc, cudaStream_t st,
+                         const CgScalars* outer) {
   if (half_vec)
     inner_update_kernel<__half><<<node_blocks(N), kNodeThreads, 0, st>>>(N, y, s, t, (const __half*)d, w, dinv32,
-                                                                         partials, sc);
+                                                                         partials, sc, outer);
   else
     inner_update_kernel<float><<<node_blocks(N), kNodeThreads, 0, st>>>(N, y, s, t, (const float*)d, w, dinv32,
-                                                                        partials, sc);
+                                                                        partials, sc, outer);
 }
 void launch_inner_dupdate(int64_t N, const float* t, void* d, int half_vec, const InnerScalars* sc,
-                          cudaStream_t st) {
+                          cudaStream_t st, const CgScalars* outer) {
   if (half_vec)
-    inner_dupdate_kernel<__half><<<node_blocks(N), kNodeThreads, 0, st>>>(N, t, (__half*)d, sc);
+    inner_dupdate_kernel<__half><<<node_blocks(N), kNodeThreads, 0, st>>>(N, t, (__half*)d, sc, outer);
   else
-    inner_dupdate_kernel<float><<<node_blocks(N), kNodeThreads, 0, st>>>(N, t, (float*)d, sc);
+    inner_dupdate_kernel<float><<<node_blocks(N), kNodeThreads, 0, st>>>(N, t, (float*)d, sc, outer);
 }
 void launch_fcg_residual(const ModelView& m, const double* b, double* q, double* r, double* partials, CgScalars* cg,
                          cudaStream_t s) {

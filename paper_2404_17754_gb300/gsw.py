@@ -29,13 +29,21 @@ _FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
 class SolverOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("precision", C.c_int32),
-                ("inner_iters", C.c_int32), ("check_every", C.c_int32)]
+                ("inner_iters", C.c_int32), ("check_every", C.c_int32), ("batch_outer", C.c_int32)]
 
 
 class Stats(C.Structure):
     _fields_ = [("steps_done", C.c_int64), ("cg_iters_total", C.c_int64), ("cg_iters_last", C.c_int32),
                 ("cg_iters_max", C.c_int32), ("relres_last", C.c_double), ("inner_iters_total", C.c_int64),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("init_relres_sum", C.c_double)]
+
+
+class LearnOpts(C.Structure):
+    _fields_ = [("enable", C.c_int32), ("train_steps", C.c_int32), ("batch", C.c_int32),
+                ("iters_per_step", C.c_int32), ("lr", C.c_float), ("seed", C.c_uint32)]
+
+
+_fp = C.POINTER(C.c_float)
 
 
 class GswError(RuntimeError):
@@ -62,6 +70,10 @@ SIGNATURES = {
     "gsw_reset": (C.c_int, [C.c_void_p, C.c_int32]),
     "gsw_step": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "gsw_run": (C.c_int, [C.c_void_p, _ip, C.c_int32]),
+    "gsw_batch_create": (C.c_int, [C.c_void_p, _ip, C.c_int32, _ip]),
+    "gsw_batch_step": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "gsw_batch_destroy": (C.c_int, [C.c_void_p, C.c_int32]),
+    "gsw_batch_launches": (C.c_int, [C.c_void_p, C.c_int32, _lp]),
     "gsw_read_waveforms": (C.c_int, [C.c_void_p, C.c_int32, _dp]),
     "gsw_read_waveform_steps": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, _dp]),
     "gsw_timing": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, _dp, _lp]),
@@ -73,6 +85,11 @@ SIGNATURES = {
     "gsw_read_receivers": (C.c_int, [C.c_void_p, C.c_int32, _ip, _dp]),
     "gsw_misfit": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, _dp, _dp, C.c_int32, C.c_int32, C.c_double,
                              _dp, _dp]),
+    "gsw_set_learning": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(LearnOpts)]),
+    "gsw_mlp_params": (C.c_int, [C.c_void_p, C.c_int32, _dp, _dp]),
+    "gsw_mlp_forward": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
+    "gsw_mlp_grad": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, _dp, _dp]),
+    "gsw_mlp_state": (C.c_int, [C.c_void_p, C.c_int32, _dp]),
     "gsw_misfit_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
                                      C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),
 }
@@ -205,6 +222,36 @@ class Context:
                                                 C.c_void_p(c_dev.data_ptr() if c_dev is not None else 0)))
 
 
+    def batch(self, models):
+        """Group models (mixed precision) for batched, graph-captured stepping."""
+        return Batch(self, models)
+
+
+class Batch:
+    """Models advanced together, one captured CUDA graph launch per time step."""
+
+    def __init__(self, ctx, models):
+        self.ctx = ctx
+        self.models = list(models)
+        ids = np.array([m.id for m in self.models], dtype=np.int32)
+        bid = C.c_int32()
+        ctx._check(ctx.lib.gsw_batch_create(ctx.h, ids.ctypes.data_as(_ip), len(ids), C.byref(bid)))
+        self.id = bid.value
+
+    def step(self, n=1):
+        self.ctx._check(self.ctx.lib.gsw_batch_step(self.ctx.h, self.id, int(n)))
+
+    def launches_per_step(self):
+        n = C.c_int64()
+        self.ctx._check(self.ctx.lib.gsw_batch_launches(self.ctx.h, self.id, C.byref(n)))
+        return n.value
+
+    def close(self):
+        if self.id:
+            self.ctx._check(self.ctx.lib.gsw_batch_destroy(self.ctx.h, self.id))
+            self.id = 0
+
+
 class Model:
     """One uploaded ground model (handle into a :class:`Context`)."""
 
@@ -216,10 +263,10 @@ class Model:
         self.ctx._check(st)
 
     def info(self):
-        out = np.zeros(5, dtype=np.int64)
+        out = np.zeros(6, dtype=np.int64)
         self._c(self.ctx.lib.gsw_model_info(self.ctx.h, self.id, out.ctypes.data_as(_lp)))
         return dict(n_nodes=int(out[0]), n_elem=int(out[1]), n_faces=int(out[2]), n_rec=int(out[3]),
-                    device_bytes=int(out[4]))
+                    device_bytes=int(out[4]), inner_variant=int(out[5]))
 
     def set_time(self, dt, n_steps, band):
         self._c(self.ctx.lib.gsw_set_time(self.ctx.h, self.id, float(dt), int(n_steps), float(band[0]),
@@ -230,8 +277,9 @@ class Model:
         p, pp = _d(p)
         self._c(self.ctx.lib.gsw_set_input(self.ctx.h, self.id, int(direction), pp, p.shape[0]))
 
-    def set_solver(self, tol=1e-8, max_iter=10000, precision=PREC_FP64, inner_iters=20, check_every=8):
-        o = SolverOpts(tol, max_iter, precision, inner_iters, check_every)
+    def set_solver(self, tol=1e-8, max_iter=10000, precision=PREC_FP64, inner_iters=20, check_every=8,
+                   batch_outer=6):
+        o = SolverOpts(tol, max_iter, precision, inner_iters, check_every, batch_outer)
         self._c(self.ctx.lib.gsw_set_solver(self.ctx.h, self.id, C.byref(o)))
 
     def reset(self):
@@ -309,6 +357,42 @@ class Model:
         self._c(self.ctx.lib.gsw_read_receivers(self.ctx.h, self.id, nodes.ctypes.data_as(_ip),
                                                 w.ctypes.data_as(_dp)))
         return nodes, w
+
+    def set_learning(self, enable=True, train_steps=500, batch=16384, iters_per_step=2, lr=1e-3, seed=1):
+        o = LearnOpts(int(enable), int(train_steps), int(batch), int(iters_per_step), float(lr), int(seed))
+        self._c(self.ctx.lib.gsw_set_learning(self.ctx.h, self.id, C.byref(o)))
+
+    def mlp_params(self, set_to=None):
+        out = np.zeros(5443)
+        src = None
+        if set_to is not None:
+            src = np.ascontiguousarray(set_to, dtype=np.float64)
+        self._c(self.ctx.lib.gsw_mlp_params(self.ctx.h, self.id, out.ctypes.data_as(_dp),
+                                            src.ctypes.data_as(_dp) if src is not None else None))
+        return out
+
+    def mlp_forward(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        out = np.zeros((X.shape[0], 3), dtype=np.float32)
+        self._c(self.ctx.lib.gsw_mlp_forward(self.ctx.h, self.id, X.shape[0], X.ctypes.data, out.ctypes.data))
+        return out
+
+    def mlp_grad(self, X, Y):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.ascontiguousarray(Y, dtype=np.float32)
+        loss = C.c_double()
+        g = np.zeros(5443)
+        self._c(self.ctx.lib.gsw_mlp_grad(self.ctx.h, self.id, X.shape[0], X.ctypes.data, Y.ctypes.data,
+                                          C.byref(loss), g.ctypes.data_as(_dp)))
+        return loss.value, g
+
+    def mlp_state(self):
+        out = np.zeros(5)
+        self._c(self.ctx.lib.gsw_mlp_state(self.ctx.h, self.id, out.ctypes.data_as(_dp)))
+        return dict(loss=out[0], active=bool(out[1]), plain_r0=out[2], learned_r0=out[3], learned_steps=int(out[4]))
+
+    def mlp_loss(self):
+        return self.mlp_state()["loss"]
 
     def free(self):
         self._c(self.ctx.lib.gsw_model_free(self.ctx.h, self.id))

@@ -73,7 +73,7 @@ def test_mixed_small_box_tight_tolerance(ctx):
 
     cfg = configs.small_box(nx=4, ny=3, n_steps=25, direction=2)
     ref = newmark.analysis(cfg, tol=1e-12)
-    wave, stats, m = gsw.analysis(ctx, cfg, tol=1e-12, precision=1, inner_iters=10)
+    wave, stats, m = gsw.analysis(ctx, cfg, tol=1e-12, precision=1, inner_iters=10, batch_outer=40)
     assert _relerr(wave, ref["wave"]) <= 1e-9
     m.free()
 
