@@ -66,6 +66,10 @@ typedef struct {
                            captured step graph (0 = 6); a step that needs more
                            is completed by the host-driven solver (up to
                            max_iter) and the model then rejoins the graph */
+  int32_t inner_variant; /* launch variant of the inner operator: -1 lets the set-up
+                            autotuner time all and keep the fastest; 0, 1 one CTA
+                            per element block (3 or 4 CTAs per SM); 2 persistent,
+                            cp.async-pipelined CTAs */
 } gsw_solver_opts;
 
 typedef struct {

@@ -55,7 +55,7 @@ struct Model {
   std::vector<double> input;
   int dir = 0;
   bool input_set = false;
-  gsw_solver_opts opts = {1e-8, 10000, GSW_PREC_FP64, 20, 8, 6};
+  gsw_solver_opts opts = {1e-8, 10000, GSW_PREC_FP64, 20, 8, 6, -1};
   int64_t step = 0;
   bool failed = false;
   gsw_stats stats = {};
@@ -73,6 +73,7 @@ struct Model {
   void* d_lo = nullptr;
   InnerScalars* isc = nullptr;
   int lo_variant = 0;          // launch variant of the inner operator (autotuned)
+  bool live_tune = false;      // refine the choice inside the next host-driven inner solve
   // learned initial guess
   gsw_learn_opts learn = {0, 0, 0, 0, 0.f, 0u};
   bool mlp_ready = false;
@@ -92,7 +93,7 @@ struct Model {
   double* p_dev = nullptr;     // input samples on the device
   int batch = 0;               // id of the batch holding the model (0: none)
   int version = 0;             // bumped when a captured step graph would be stale
-  float lo_variant_ms[kLoVariants] = {0.f, 0.f};
+  float lo_variant_ms[kLoVariants] = {0.f, 0.f, 0.f};
   LoView<float> lo_f;
   LoView<__half> lo_h;
   // kernel timing
@@ -386,22 +387,29 @@ gsw_status autotune_lo(gsw_ctx* ctx, Model* m) {
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   launch_to_lo(m->N, m->u, m->d_lo, m->lo_half, m->w32, s);
-  float best = 1e30f;
-  for (int v = 0; v < kLoVariants; ++v) {
-    launch_ebe_lo(m->lo_half, m->lo_half, view, m->d_lo, m->w32, m->partials, m->isc, s, v);  // warm-up
-    float tot = 0.f;
-    for (int rep = 0; rep < 3; ++rep) {
+  // rounds interleave the variants so none profits from a cache warmed by
+  // another; each variant keeps the median of its rounds
+  constexpr int kRounds = 5;
+  float t[kLoVariants][kRounds] = {};
+  for (int v = 0; v < kLoVariants; ++v)  // warm-up (and the pipelined kernel's attributes)
+    launch_ebe_lo(m->lo_half, m->lo_half, view, m->d_lo, m->w32, m->partials, m->isc, s, v);
+  for (int rnd = 0; rnd < kRounds; ++rnd) {
+    for (int v = 0; v < kLoVariants; ++v) {
+      if (m->opts.inner_variant >= 0 && v != m->opts.inner_variant) continue;
       CK(cudaEventRecord(e0, s));
       launch_ebe_lo(m->lo_half, m->lo_half, view, m->d_lo, m->w32, m->partials, m->isc, s, v);
       CK(cudaEventRecord(e1, s));
       CK(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, e0, e1));
-      tot += ms;
+      CK(cudaEventElapsedTime(&t[v][rnd], e0, e1));
     }
-    m->lo_variant_ms[v] = tot / 3.f;
-    if (tot < best) {
-      best = tot;
+  }
+  float best = 1e30f;
+  for (int v = 0; v < kLoVariants; ++v) {
+    if (m->opts.inner_variant >= 0 && v != m->opts.inner_variant) continue;
+    std::sort(t[v], t[v] + kRounds);
+    m->lo_variant_ms[v] = t[v][kRounds / 2];
+    if (t[v][kRounds / 2] < best) {
+      best = t[v][kRounds / 2];
       m->lo_variant = v;
     }
   }
@@ -425,11 +433,14 @@ gsw_status build_lo(gsw_ctx* ctx, Model* m, int half) {
     std::vector<int32_t> h((size_t)m->n_blk), ptr((size_t)m->n_blk + 1);
     CK(cudaMemcpyAsync(h.data(), counts, sizeof(int32_t) * m->n_blk, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    // node lists padded to multiples of 4 entries (16-byte aligned starts);
+    // padding entries name the dummy node N (zero contribution)
     ptr[0] = 0;
     int mx = 0;
     for (int b = 0; b < m->n_blk; ++b) {
-      ptr[b + 1] = ptr[b] + h[b];
-      if (h[b] > mx) mx = h[b];
+      const int padded = (h[b] + 3) & ~3;
+      ptr[b + 1] = ptr[b] + padded;
+      if (padded > mx) mx = padded;
     }
     m->max_local = mx;
     if (mx > kLoBlock * kLoNodesPerThread)
@@ -440,11 +451,11 @@ gsw_status build_lo(gsw_ctx* ctx, Model* m, int half) {
     TRY(alloc_into(ctx, m, &m->blk_ptr, (size_t)m->n_blk + 1));
     TRY(alloc_into(ctx, m, &m->blk_nodes, (size_t)total));
     TRY(alloc_into(ctx, m, &m->lconn, 10 * (size_t)m->n_blk * kLoBlock));
-    TRY(alloc_into(ctx, m, &refcount, (size_t)m->N));
+    TRY(alloc_into(ctx, m, &refcount, (size_t)m->N + 1));
     CK(cudaMemcpyAsync(m->blk_ptr, ptr.data(), sizeof(int32_t) * (m->n_blk + 1), cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(refcount, 0, sizeof(int32_t) * m->N, s));
+    CK(cudaMemsetAsync(refcount, 0, sizeof(int32_t) * (m->N + 1), s));
     BlockView bv = {m->n_blk, m->max_local, m->blk_ptr, m->blk_nodes};
-    launch_block_fill(mv, bv, m->blk_nodes, m->lconn, refcount, s);
+    launch_block_fill(mv, bv, m->blk_nodes, m->lconn, refcount, s, counts);
     launch_block_mark(mv, bv, m->blk_nodes, refcount, total, s);
     CK(cudaGetLastError());
     const size_t n3 = 3 * (size_t)m->N;
@@ -453,7 +464,7 @@ gsw_status build_lo(gsw_ctx* ctx, Model* m, int half) {
     TRY(alloc_into(ctx, m, &m->y32, n3));
     TRY(alloc_into(ctx, m, &m->s32, n3));
     TRY(alloc_into(ctx, m, &m->t32, n3));
-    TRY(alloc_into(ctx, m, &m->w32, n3));
+    TRY(alloc_into(ctx, m, &m->w32, n3 + 4));  // + the dummy node's row
     TRY(alloc_into(ctx, m, &m->isc, 1));
     CK(cudaMemsetAsync(m->isc, 0, sizeof(InnerScalars), s));
     m->lo_ready = true;
@@ -463,7 +474,7 @@ gsw_status build_lo(gsw_ctx* ctx, Model* m, int half) {
   if (m->geo_lo == nullptr || m->lo_half != half) {
     // (re)allocate the precision-dependent buffers; the old ones stay owned by the model
     m->geo_lo = dev_alloc(ctx, m, lo_record_bytes(half) * (size_t)m->n_blk * kLoBlock);
-    m->d_lo = dev_alloc(ctx, m, (half ? sizeof(__half) : sizeof(float)) * 4 * (size_t)m->N);
+    m->d_lo = dev_alloc(ctx, m, (half ? sizeof(__half) : sizeof(float)) * 4 * ((size_t)m->N + 1));
     if (!m->geo_lo || !m->d_lo) return fail(ctx, GSW_E_NOMEM, "device allocation failed (inner solve)");
     m->lo_half = half;
   }
@@ -473,6 +484,7 @@ gsw_status build_lo(gsw_ctx* ctx, Model* m, int half) {
   BlockView bv = {m->n_blk, m->max_local, m->blk_ptr, m->blk_nodes};
   m->lo_f = LoView<float>{m->N, m->E, m->F, m->n_mat, bv, m->geo_lo, m->mat, m->fnode, m->fgeo32, m->dt};
   m->lo_h = LoView<__half>{m->N, m->E, m->F, m->n_mat, bv, m->geo_lo, m->mat, m->fnode, m->fgeo32, m->dt};
+  m->live_tune = (m->opts.inner_variant < 0);
   return autotune_lo(ctx, m);
 }
 
@@ -585,10 +597,14 @@ int64_t inner_solve(Model* m, cudaStream_t s) {
   launch_inner_init(m->N, m->r, m->dinv32, m->s32, m->y32, m->t32, m->d_lo, half, m->w32, m->partials, m->isc,
                     m->cg, s);
   const int it = m->opts.inner_iters > 0 ? m->opts.inner_iters : 1;
-  const bool timed = m->timing && (int)m->ev_lo.size() >= 2 * it;
+  // live tuning: inside the first host-driven inner solve the launch variants
+  // take turns (in the cache state of a real solve) and the fastest median wins
+  const bool tune = m->live_tune && it >= 2 * kLoVariants && (int)m->ev_lo.size() >= 2 * it;
+  const bool timed = (m->timing || tune) && (int)m->ev_lo.size() >= 2 * it;
   for (int k = 0; k < it; ++k) {
+    const int variant = tune ? k % kLoVariants : m->lo_variant;
     if (timed) cudaEventRecord(m->ev_lo[2 * k], s);
-    launch_ebe_lo(half, half, view, m->d_lo, m->w32, m->partials, m->isc, s, m->lo_variant, m->cg);
+    launch_ebe_lo(half, half, view, m->d_lo, m->w32, m->partials, m->isc, s, variant, m->cg);
     if (timed) cudaEventRecord(m->ev_lo[2 * k + 1], s);
     launch_inner_update(m->N, m->y32, m->s32, m->t32, m->d_lo, half, m->w32, m->dinv32, m->partials, m->isc, s,
                         m->cg);
@@ -597,11 +613,29 @@ int64_t inner_solve(Model* m, cudaStream_t s) {
   m->stats.inner_iters_total += it;
   if (timed) {
     cudaEventSynchronize(m->ev_lo[2 * it - 1]);
+    std::vector<float> per[kLoVariants];
     for (int k = 0; k < it; ++k) {
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, m->ev_lo[2 * k], m->ev_lo[2 * k + 1]) == cudaSuccess) m->lo_ms += ms;
+      if (cudaEventElapsedTime(&ms, m->ev_lo[2 * k], m->ev_lo[2 * k + 1]) != cudaSuccess) continue;
+      if (m->timing) m->lo_ms += ms;
+      if (tune && k >= kLoVariants) per[k % kLoVariants].push_back(ms);  // the first round warms up
     }
-    m->lo_count += it;
+    if (m->timing) m->lo_count += it;
+    if (tune) {
+      float best = 1e30f;
+      for (int v = 0; v < kLoVariants; ++v) {
+        if (per[v].empty()) continue;
+        std::sort(per[v].begin(), per[v].end());
+        const float med = per[v][per[v].size() / 2];
+        m->lo_variant_ms[v] = med;
+        if (med < best) {
+          best = med;
+          m->lo_variant = v;
+        }
+      }
+      m->live_tune = false;
+      m->version += 1;  // a captured batch graph must pick up the choice
+    }
   }
   return 1 + 3 * (int64_t)it - 1;
 }
@@ -626,7 +660,7 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
   launch_ebe(kModeRes, mv, m->p, m->z, m->b, m->r, force, m->dir, nullptr, m->cg, s);
   launch_cg_rnorm(mv, m->r, m->partials, m->cg, s);
   int64_t launches = 4;
-  if (m->timing && (int)m->ev_lo.size() < 2 * m->opts.inner_iters) {
+  if ((m->timing || m->live_tune) && (int)m->ev_lo.size() < 2 * m->opts.inner_iters) {
     for (int i = (int)m->ev_lo.size(); i < 2 * m->opts.inner_iters; ++i) {
       cudaEvent_t e;
       CK(cudaEventCreate(&e));
@@ -1045,6 +1079,8 @@ gsw_status gsw_set_solver(gsw_ctx* ctx, int32_t model_id, const gsw_solver_opts*
     return fail(ctx, GSW_E_INVALID, "precision mode %d is not one of FP64, FP32, FP16", opts->precision);
   if (opts->precision != GSW_PREC_FP64 && (opts->inner_iters <= 0 || opts->inner_iters > 10000))
     return fail(ctx, GSW_E_INVALID, "inner_iters must be 1..10000");
+  if (opts->inner_variant < -1 || opts->inner_variant >= kLoVariants)
+    return fail(ctx, GSW_E_INVALID, "inner_variant must be -1 (autotune) or 0..%d", kLoVariants - 1);
   m->opts = *opts;
   m->version += 1;
   if (m->opts.precision != GSW_PREC_FP64 && m->time_set) {

@@ -97,6 +97,9 @@ struct InnerScalars {
   double dinv_mean;  // mean diagonal entry of D^-1 (set once per model)
   unsigned int counter;
   unsigned int pad;
+  float alpha_f;  // s . t / d . A d, set by the last block of the operator kernel
+  float beta_f;   // FP32 copy of beta for the direction update
+  float pad_f[2];
 };
 
 // Element blocks with local node numbering: block b holds elements
@@ -175,7 +178,7 @@ int ebe_blocks(const ModelView& m);
 // nodes / lconn / refcount given ptr (pass 2), then mark exclusive nodes.
 void launch_block_count(const ModelView& m, int n_blk, int32_t* counts, cudaStream_t s);
 void launch_block_fill(const ModelView& m, BlockView b, int32_t* nodes, uint16_t* lconn,
-                       int32_t* refcount, cudaStream_t s);
+                       int32_t* refcount, cudaStream_t s, const int32_t* counts);
 void launch_block_mark(const ModelView& m, BlockView b, int32_t* nodes, int32_t* refcount,
                        int total, cudaStream_t s);
 void launch_lo_convert(const ModelView& m, int n_blk, const uint16_t* lconn, int half_geo, void* rec,
@@ -190,7 +193,7 @@ void launch_inner_init(int64_t N, const double* r, const float* dinv32, float* s
 void launch_ebe_lo(int half_geo, int half_vec, const void* lo_view, const void* d, float* w,
                    double* partials, InnerScalars* sc, cudaStream_t st, int variant,
                    const CgScalars* outer = nullptr);
-constexpr int kLoVariants = 2;
+constexpr int kLoVariants = 3;
 void launch_inner_update(int64_t N, float* y, float* s, float* t, const void* d, int half_vec,
                          float* w, const float* dinv32, double* partials, InnerScalars* sc,
                          cudaStream_t st, const CgScalars* outer);

@@ -130,7 +130,7 @@ __global__ void block_count_kernel(ModelView m, int32_t* counts) {
 }
 
 __global__ void block_fill_kernel(ModelView m, BlockView bv, int32_t* nodes, uint16_t* lconn,
-                                  int32_t* refcount) {
+                                  int32_t* refcount, const int32_t* counts) {
   __shared__ int keys[kSortN];
   __shared__ int flag[kSortN];
   const int b = blockIdx.x;
@@ -155,7 +155,8 @@ __global__ void block_fill_kernel(ModelView m, BlockView bv, int32_t* nodes, uin
     __syncthreads();
   }
   const int base = bv.ptr[b];
-  const int nu = bv.ptr[b + 1] - base;
+  const int nu = counts[b];  // unique nodes; entries nu .. ptr[b+1]-base-1 are padding
+  for (int i = nu + threadIdx.x; i < bv.ptr[b + 1] - base; i += blockDim.x) nodes[base + i] = (int32_t)m.N;
   for (int i = threadIdx.x; i < kSortN; i += blockDim.x) {
     const bool first = keys[i] != 0x7fffffff && (i == 0 || keys[i] != keys[i - 1]);
     if (first) {
@@ -200,7 +201,7 @@ __global__ void block_mark_kernel(int total, int32_t* nodes, const int32_t* refc
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
   const int g = nodes[i];
-  if (refcount[g] == 1) nodes[i] = (int32_t)((uint32_t)g | 0x80000000u);
+  if (refcount[g] == 1) nodes[i] = (int32_t)((uint32_t)g | 0x80000000u);  // the dummy node's count stays 0
 }
 
 // Element records in operator order (invalid positions of the last block get
@@ -239,6 +240,17 @@ __global__ void dinv_mean_kernel(int64_t N, const double* __restrict__ dinv, dou
 // ------------------------------------------------------------------------------
 // Reduced-precision element-by-element product w = A d (+ partial d . w)
 // ------------------------------------------------------------------------------
+
+// Grid sum of the per-thread d . A d contributions (FP32); the last block
+// stores d . A d and the step length alpha = s . t / d . A d.
+__device__ __forceinline__ void lo_finish_dw(float dot, double* partials, InnerScalars* sc) {
+  float vals[1] = {dot}, out[1];
+  if (last_block_reduce_f<1>(vals, reinterpret_cast<float*>(partials), &sc->counter, out) && threadIdx.x == 0) {
+    const double st = ((volatile InnerScalars*)sc)->st;
+    sc->dw = out[0];
+    sc->alpha_f = (out[0] != 0.f) ? (float)(st / (double)out[0]) : 0.f;
+  }
+}
 
 // One CTA per block of kLoBlock elements: the CTA gathers the block's unique
 // nodes into shared memory, each thread applies one element (records are
@@ -329,8 +341,8 @@ __global__ void __launch_bounds__(kLoBlock, MINB) ebe_lo_kernel(LoView<SG> m, co
 #pragma unroll
     for (int j = 0; j < kLoNodesPerThread; ++j) {
       const int i = threadIdx.x + j * kLoBlock;
-      if (i < nn) {
-        const int64_t g = raw[j] & 0x7fffffff;
+      const int64_t g = raw[j] & 0x7fffffff;
+      if (i < nn && g != m.N) {  // padding entries name the dummy node N: skip them
         if (raw[j] < 0) {
           w[3 * g] = ys[3 * i];
           w[3 * g + 1] = ys[3 * i + 1];
@@ -378,8 +390,7 @@ __global__ void __launch_bounds__(kLoBlock, MINB) ebe_lo_kernel(LoView<SG> m, co
       }
     }
   }
-  double vals[1] = {(double)dot}, out[1];
-  if (last_block_reduce<1>(vals, partials, &sc->counter, out) && threadIdx.x == 0) sc->dw = out[0];
+  lo_finish_dw(dot, partials, sc);
 }
 
 // ------------------------------------------------------------------------------
@@ -398,9 +409,16 @@ __global__ void inner_init_kernel(int64_t N, const double* __restrict__ r, const
                                   SD* __restrict__ d, float* __restrict__ w, double* partials,
                                   InnerScalars* sc, const CgScalars* cg) {
   if (((volatile const CgScalars*)cg)->done) return;
-  const double rr = ((volatile const CgScalars*)cg)->rr;
-  const double dm = ((volatile const InnerScalars*)sc)->dinv_mean;
-  const double scale = (rr > 0.0 ? sqrt(3.0 * (double)N / rr) : 1.0) / (dm > 0.0 ? dm : 1.0);
+  // the scale is computed once per block (FP64 division and square root are
+  // slow on this GPU) and broadcast through shared memory
+  __shared__ double scale_s;
+  if (threadIdx.x == 0) {
+    const double rr = ((volatile const CgScalars*)cg)->rr;
+    const double dm = ((volatile const InnerScalars*)sc)->dinv_mean;
+    scale_s = (rr > 0.0 ? sqrt(3.0 * (double)N / rr) : 1.0) / (dm > 0.0 ? dm : 1.0);
+  }
+  __syncthreads();
+  const double scale = scale_s;
   float st = 0.f;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
     float sn[3], tn[3];
@@ -420,8 +438,8 @@ __global__ void inner_init_kernel(int64_t N, const double* __restrict__ r, const
     }
     d[4 * n + 3] = from_f<SD>(0.f);
   }
-  double vals[1] = {(double)st}, out[1];
-  if (last_block_reduce<1>(vals, partials, &sc->counter, out) && threadIdx.x == 0) {
+  float vals[1] = {st}, out[1];
+  if (last_block_reduce_f<1>(vals, reinterpret_cast<float*>(partials), &sc->counter, out) && threadIdx.x == 0) {
     sc->st = out[0];
     sc->scale = scale;
   }
@@ -432,8 +450,7 @@ __global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __r
                                     const SD* __restrict__ d, float* __restrict__ w, const float* __restrict__ dinv,
                                     double* partials, InnerScalars* sc, const CgScalars* outer) {
   if (outer != nullptr && ((volatile const CgScalars*)outer)->done) return;
-  const double st_old = ((volatile InnerScalars*)sc)->st, dw = ((volatile InnerScalars*)sc)->dw;
-  const float alpha = (dw != 0.0) ? (float)(st_old / dw) : 0.f;
+  const float alpha = ((volatile InnerScalars*)sc)->alpha_f;
   float st = 0.f;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
     float sn[3], tn[3];
@@ -452,9 +469,12 @@ __global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __r
       st = fmaf(sn[i], tn[i], st);
     }
   }
-  double vals[1] = {(double)st}, out[1];
-  if (last_block_reduce<1>(vals, partials, &sc->counter, out) && threadIdx.x == 0) {
-    sc->beta = (st_old != 0.0) ? out[0] / st_old : 0.0;
+  float vals[1] = {st}, out[1];
+  if (last_block_reduce_f<1>(vals, reinterpret_cast<float*>(partials), &sc->counter, out) && threadIdx.x == 0) {
+    const double st_old = ((volatile InnerScalars*)sc)->st;
+    const double beta = (st_old != 0.0) ? out[0] / st_old : 0.0;
+    sc->beta = beta;
+    sc->beta_f = (float)beta;
     sc->st = out[0];
   }
 }
@@ -463,7 +483,7 @@ template <typename SD>
 __global__ void inner_dupdate_kernel(int64_t N, const float* __restrict__ t, SD* __restrict__ d,
                                      const InnerScalars* sc, const CgScalars* outer) {
   if (outer != nullptr && ((volatile const CgScalars*)outer)->done) return;
-  const float beta = (float)((volatile const InnerScalars*)sc)->beta;
+  const float beta = ((volatile const InnerScalars*)sc)->beta_f;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) d[4 * n + i] = from_f<SD>(fmaf(beta, to_f(d[4 * n + i]), t[3 * n + i]));
@@ -656,8 +676,8 @@ void launch_block_count(const ModelView& m, int n_blk, int32_t* counts, cudaStre
   block_count_kernel<<<n_blk, 256, 0, s>>>(m, counts);
 }
 void launch_block_fill(const ModelView& m, BlockView b, int32_t* nodes, uint16_t* lconn, int32_t* refcount,
-                       cudaStream_t s) {
-  block_fill_kernel<<<b.n_blk, 256, 0, s>>>(m, b, nodes, lconn, refcount);  // lconn: [10][n_blk * kLoBlock]
+                       cudaStream_t s, const int32_t* counts) {
+  block_fill_kernel<<<b.n_blk, 256, 0, s>>>(m, b, nodes, lconn, refcount, counts);  // lconn: [10][n_blk * kLoBlock]
   if (m.F > 0) face_refcount_kernel<<<(unsigned)((m.F + 255) / 256), 256, 0, s>>>(m, refcount);
 }
 void launch_block_mark(const ModelView& m, BlockView b, int32_t* nodes, int32_t* refcount, int total,
@@ -690,11 +710,224 @@ void launch_inner_init(int64_t N, const double* r, const float* dinv32, float* s
     inner_init_kernel<float><<<node_blocks(N), kNodeThreads, 0, st>>>(N, r, dinv32, s, y, t, (float*)d, w,
                                                                       partials, sc, cg);
 }
+
+// ---- software-pipelined variant ----------------------------------------------
+//
+// Persistent CTAs walk their element blocks b_i = blockIdx.x + i * gridDim
+// with cp.async staging: the packed records and the node-index list of b_{i+2}
+// (three stages) and the search-direction gather of b_{i+1} (two stages) are
+// in flight while b_i is applied, so the gather latency overlaps arithmetic.
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+template <typename SD>
+__device__ __forceinline__ void unpack3(const unsigned char* p, float& a, float& b, float& c) {
+  load3(reinterpret_cast<const SD*>(p), a, b, c);
+}
+
+template <typename SG, typename SD>
+size_t lo_pipe_smem(int max_local) {
+  return sizeof(uint4) * 3 * kLoBlock * LoRec<SG>::words + sizeof(int32_t) * 3 * (size_t)max_local +
+         sizeof(SD) * 4 * 2 * (size_t)max_local + sizeof(float) * 3 * (size_t)max_local;
+}
+
+template <typename SG, typename SD>
+__global__ void __launch_bounds__(kLoBlock, 2) ebe_lo_pipe_kernel(LoView<SG> m, const SD* __restrict__ d,
+                                                                   float* __restrict__ w, double* partials,
+                                                                   InnerScalars* sc, const CgScalars* outer,
+                                                                   int n_pipe) {
+  if (outer != nullptr && ((volatile const CgScalars*)outer)->done) return;
+  typedef typename LoRec<SG>::type Rec;
+  constexpr int RW = LoRec<SG>::words;
+  constexpr int NB = (int)sizeof(SD) * 4;  // bytes per node of the padded search direction
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int ML = m.blk.max_local;  // padded, a multiple of 4
+  uint4* recs = reinterpret_cast<uint4*>(smem);
+  int32_t* idx = reinterpret_cast<int32_t*>(recs + 3 * kLoBlock * RW);
+  unsigned char* xr = reinterpret_cast<unsigned char*>(idx + 3 * ML);
+  float* ys = reinterpret_cast<float*>(xr + (size_t)2 * ML * NB);
+  __shared__ float matc[kMaxMat][3];
+  if (threadIdx.x < m.n_mat) {
+    const MatCoef& c = m.mat[threadIdx.x];
+    matc[threadIdx.x][0] = (float)(c.cK * c.lam / 20.0);
+    matc[threadIdx.x][1] = (float)(c.cK * c.mu / 20.0);
+    matc[threadIdx.x][2] = (float)(c.cM * c.rho / 420.0);
+  }
+  for (int q = threadIdx.x; q < 3 * ML; q += kLoBlock) ys[q] = 0.f;
+  float dot = 0.f;
+  const int nb = m.blk.n_blk;
+  if ((int)blockIdx.x < n_pipe) {
+    const int first = blockIdx.x;
+    const int n_my = first < nb ? (nb - first + n_pipe - 1) / n_pipe : 0;
+    auto issue_meta = [&](int i) {
+      if (i < n_my) {
+        const int b = first + i * n_pipe, st = i % 3;
+        const uint4* src = reinterpret_cast<const uint4*>(m.rec) + (int64_t)b * kLoBlock * RW;
+        for (int q = threadIdx.x; q < kLoBlock * RW; q += kLoBlock) cp_async16(recs + st * kLoBlock * RW + q, src + q);
+        const int n0 = m.blk.ptr[b], nn = m.blk.ptr[b + 1] - n0;
+        const int4* isrc = reinterpret_cast<const int4*>(m.blk.nodes + n0);
+        for (int q = threadIdx.x; q < nn / 4; q += kLoBlock) cp_async16(idx + st * ML + 4 * q, isrc + q);
+      }
+      cp_async_commit();
+    };
+    auto issue_gather = [&](int i) {
+      if (i < n_my) {
+        const int b = first + i * n_pipe, st = i % 3, xb = i & 1;
+        const int nn = m.blk.ptr[b + 1] - m.blk.ptr[b];
+        for (int q = threadIdx.x; q < nn; q += kLoBlock) {
+          const int64_t g = idx[st * ML + q] & 0x7fffffff;
+          unsigned char* dst = xr + ((size_t)xb * ML + q) * NB;
+          if (NB == 16)
+            cp_async16(dst, d + 4 * g);
+          else
+            cp_async8(dst, d + 4 * g);
+        }
+      }
+      cp_async_commit();
+    };
+    issue_meta(0);
+    issue_meta(1);
+    cp_async_wait1();
+    __syncthreads();
+    issue_gather(0);
+    for (int i = 0; i < n_my; ++i) {
+      issue_meta(i + 2);
+      cp_async_wait1();  // all but the newest group: gather of b_i, meta of b_{i+1}
+      __syncthreads();
+      issue_gather(i + 1);
+      const int b = first + i * n_pipe, st = i % 3, xb = i & 1;
+      const int nn = m.blk.ptr[b + 1] - m.blk.ptr[b];
+      {
+        union {
+          uint4 v[RW];
+          Rec r;
+        } u;
+#pragma unroll
+        for (int q = 0; q < RW; ++q) u.v[q] = recs[st * kLoBlock * RW + threadIdx.x * RW + q];
+        float g[3][3];
+#pragma unroll
+        for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) g[mm][k] = to_f(u.r.g[3 * mm + k]);
+        const float V = u.r.vol;
+        const int mt = u.r.mat;
+        const float lamS = matc[mt][0] * V, muS = matc[mt][1] * V, mS = matc[mt][2] * V;
+        float wv[10][3], f[10][3];
+#pragma unroll
+        for (int k = 0; k < 10; ++k)
+          unpack3<SD>(xr + ((size_t)xb * ML + u.r.lc[k]) * NB, wv[k][0], wv[k][1], wv[k][2]);
+        stiffness_apply<float>(wv, g, lamS, muS, f);
+        mass_apply<float>(wv, mS, f);
+#pragma unroll
+        for (int k = 0; k < 10; ++k)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            atomicAdd(ys + 3 * u.r.lc[k] + c, f[k][c]);
+            dot = fmaf(wv[k][c], f[k][c], dot);
+          }
+      }
+      __syncthreads();
+      for (int q = threadIdx.x; q < nn; q += kLoBlock) {
+        const int32_t raw = idx[st * ML + q];
+        const int64_t g = raw & 0x7fffffff;
+        const float y0 = ys[3 * q], y1 = ys[3 * q + 1], y2 = ys[3 * q + 2];
+        ys[3 * q] = 0.f;
+        ys[3 * q + 1] = 0.f;
+        ys[3 * q + 2] = 0.f;
+        if (g == m.N) continue;  // padding entry (dummy node N)
+        if (raw < 0) {
+          w[3 * g] = y0;
+          w[3 * g + 1] = y1;
+          w[3 * g + 2] = y2;
+        } else {
+          atomicAdd(w + 3 * g, y0);
+          atomicAdd(w + 3 * g + 1, y1);
+          atomicAdd(w + 3 * g + 2, y2);
+        }
+      }
+      __syncthreads();
+    }
+    cp_async_wait0();
+  } else {
+    __syncthreads();
+    // absorbing faces: (2/dt) C_abs d
+    const int64_t fc = (int64_t)(blockIdx.x - n_pipe) * kLoBlock + threadIdx.x;
+    if (fc < m.F && m.fgeo[5 * m.F + fc] > 0.5f) {
+      const float sc2 = (float)(2.0 / m.dt) / 180.f;
+      const float As = sc2 * m.fgeo[fc], Ad = sc2 * m.fgeo[m.F + fc];
+      const float n[3] = {m.fgeo[2 * m.F + fc], m.fgeo[3 * m.F + fc], m.fgeo[4 * m.F + fc]};
+      int64_t nd[6];
+      float z[6][3], xin[6][3];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        nd[k] = m.fnode[k * m.F + fc];
+        load3(d + 4 * nd[k], xin[k][0], xin[k][1], xin[k][2]);
+        const float dn = n[0] * xin[k][0] + n[1] * xin[k][1] + n[2] * xin[k][2];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) z[k][c] = fmaf(As, xin[k][c], Ad * dn * n[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float Zv = z[0][c] + z[1][c] + z[2][c];
+        const float Ze = z[3][c] + z[4][c] + z[5][c];
+        float yf[6];
+        yf[0] = 7.f * z[0][c] - Zv - 4.f * z[4][c];
+        yf[1] = 7.f * z[1][c] - Zv - 4.f * z[5][c];
+        yf[2] = 7.f * z[2][c] - Zv - 4.f * z[3][c];
+        yf[3] = 16.f * (z[3][c] + Ze) - 4.f * z[2][c];
+        yf[4] = 16.f * (z[4][c] + Ze) - 4.f * z[0][c];
+        yf[5] = 16.f * (z[5][c] + Ze) - 4.f * z[1][c];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          atomicAdd(w + 3 * nd[k] + c, yf[k]);
+          dot = fmaf(xin[k][c], yf[k], dot);
+        }
+      }
+    }
+  }
+  lo_finish_dw(dot, partials, sc);
+}
+
+template <typename SG, typename SD>
+static void ebe_lo_pipe_launch(const LoView<SG>& m, const SD* d, float* w, double* partials, InnerScalars* sc,
+                               cudaStream_t st, const CgScalars* outer) {
+  const size_t smem = lo_pipe_smem<SG, SD>(m.blk.max_local);
+  static size_t attr_set = 0;  // per instantiation
+  if (smem > attr_set) {
+    cudaFuncSetAttribute(ebe_lo_pipe_kernel<SG, SD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = smem;
+  }
+  int dev = 0, sms = 152, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ebe_lo_pipe_kernel<SG, SD>, kLoBlock, smem);
+  if (occ < 1) occ = 1;
+  int n_pipe = sms * occ;
+  if (n_pipe > m.blk.n_blk) n_pipe = m.blk.n_blk > 0 ? m.blk.n_blk : 1;
+  const unsigned g = (unsigned)(n_pipe + (m.F + kLoBlock - 1) / kLoBlock);
+  ebe_lo_pipe_kernel<SG, SD><<<g, kLoBlock, smem, st>>>(m, d, w, partials, sc, outer, n_pipe);
+}
+
 // variant: 0 -> up to 3 CTAs per SM (no register cap below 96), 1 -> 4 CTAs
-// per SM (80 registers); picked per model by the set-up autotuner.
+// per SM (80 registers), 2 -> the persistent software-pipelined kernel;
+// picked per model by the set-up autotuner.
 template <typename SG, typename SD>
 static void ebe_lo_launch(int variant, const LoView<SG>& m, const SD* d, float* w, double* partials,
                           InnerScalars* sc, cudaStream_t st, const CgScalars* outer) {
+  if (variant == 2) {
+    ebe_lo_pipe_launch<SG, SD>(m, d, w, partials, sc, st, outer);
+    return;
+  }
   const unsigned g = (unsigned)(m.blk.n_blk + (m.F + kLoBlock - 1) / kLoBlock);
   const size_t smem = sizeof(float) * 6 * (size_t)m.blk.max_local;
   if (variant == 1)

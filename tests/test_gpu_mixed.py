@@ -33,9 +33,10 @@ def _relerr(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("prec,bound", [("fp32", 2e-6), ("fp16", 5e-3)])
-@pytest.mark.parametrize("nx,ny", [(3, 2), (6, 5)])
-def test_inner_operator_matches_csr(ctx, prec, bound, nx, ny):
+@pytest.mark.parametrize("nx,ny", [(3, 2), (6, 5), (14, 9)])
+def test_inner_operator_matches_csr(ctx, prec, bound, nx, ny, variant):
     """Block-local shared-memory assembly in reduced precision vs the assembled FP64 operator."""
     import torch
 
@@ -43,7 +44,8 @@ def test_inner_operator_matches_csr(ctx, prec, bound, nx, ny):
     ops = fem.assemble(cfg["mesh"], cfg["mat"], cfg["band"])
     m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
     m.set_time(cfg["dt"], 4, cfg["band"])
-    m.set_solver(tol=1e-8, precision=PREC[prec], inner_iters=4)
+    m.set_solver(tol=1e-8, precision=PREC[prec], inner_iters=4, inner_variant=variant)
+    assert m.info()["inner_variant"] == variant
     dt = cfg["dt"]
     A = ops["K"] + (2 / dt) * (ops["CR"] + ops["Cabs"]) + (4 / dt ** 2) * ops["M"]
     x = np.random.default_rng(1).standard_normal((m.n_nodes, 3))

@@ -1,0 +1,70 @@
+"""End-to-end model selection on the GPU (Section 2 method, Section 3 workflow).
+
+Candidates are seeded interface realisations of the two-layer box; one of
+them is the hidden truth.  Each candidate's Green's functions (unit sin^2
+pulse in x1, x2, x3; Section 3: three analyses per model) are computed by the
+batched GPU solver, observations of three events are the truth's responses to
+seeded input-coefficient sets, and the GPU misfit estimates each candidate's
+input and ERR (Eq. (2)).  The truth must reproduce the observations and be
+selected, per event and by the historical maximum.
+"""
+import numpy as np
+import pytest
+
+from oracle import misfit
+from synth import configs
+from synth.waves import sin2_pulse
+
+pytestmark = pytest.mark.gpu
+
+
+def test_truth_is_selected_from_candidates():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_17754_gb300 import build, gsw
+
+    build.build()
+    ctx = gsw.Context(0)
+    n_steps, s, L = 90, 10, 5
+    seeds = [11, 12, 13, 14]
+    truth = 2
+    cfgs = [configs.config3_candidate(l, n_steps=n_steps, n_lateral=6) for l in seeds]
+    t = cfgs[0]["dt"] * np.arange(1, n_steps + 1)
+    pulse = sin2_pulse(t, 2 * s * cfgs[0]["dt"])
+    models = []
+    for cfg in cfgs:
+        for j in range(3):
+            m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
+            m.set_time(cfg["dt"], n_steps, cfg["band"])
+            m.set_input(j, pulse)
+            m.set_solver(tol=1e-10, precision=1, inner_iters=15, batch_outer=12)
+            models.append(m)
+    batch = ctx.batch(models)
+    batch.step(n_steps)
+    batch.close()
+    G = []
+    for c in range(len(cfgs)):
+        g = np.stack([models[3 * c + j].waveforms() for j in range(3)], axis=2)  # [rec, i, j, t]
+        G.append(g)
+    rng = np.random.default_rng(8)
+    ERR = np.zeros((len(cfgs), 3))
+    for e in range(3):
+        c_true = rng.standard_normal((3, L)) * np.hanning(L + 2)[1:-1]
+        obs = misfit.superpose(G[truth], c_true, s)
+        for c in range(len(cfgs)):
+            err, c_est = ctx.misfit(G[c], obs, s, L, tau=1e-10)
+            ERR[c, e] = err
+            err_o, _ = misfit.estimate(G[c], obs, s, L, tau=1e-10)
+            assert abs(err - err_o) <= 1e-9 * max(err_o, 1e-6)
+            if c == truth:
+                np.testing.assert_allclose(c_est, c_true, atol=1e-6 * np.abs(c_true).max())
+    best, hist = misfit.select(ERR)
+    assert ERR[truth].max() < 1e-6
+    assert np.all(best == truth) and np.all(hist == truth)
+    others = np.delete(ERR, truth, axis=0)
+    assert others.min() > 100 * ERR[truth].max()
+    for m in models:
+        m.free()
+    ctx.close()
