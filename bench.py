@@ -149,6 +149,8 @@ def inner_bytes(n_nodes, n_elem, n_faces, half):
 
 
 CSRC = os.path.join(ROOT, "paper_2404_17754_gb300", "csrc")
+LO_KERNELS = {0: "ebe_lo_kernel<., ., 1>", 1: "ebe_lo_kernel<., ., 4>", 2: "ebe_lo_pipe_kernel",
+              3: "ebe_lo_ws_kernel"}
 FP64_SOURCES = ["gsw_kernels.cu", "gsw_ebe.cuh", "gsw_reduce.cuh", "gsw_internal.cuh"]
 INNER_SOURCES = ["gsw_mixed.cu", "gsw_ebe.cuh", "gsw_reduce.cuh", "gsw_internal.cuh"]
 
@@ -471,7 +473,7 @@ def main():
         inner_roof = {"bound": "hbm", "achieved": lo_bytes / lo_launch_s / 1e9, "peak": pk.get("hbm_gbs"),
                       "unit": "GB/s", "frac": lo_bytes / lo_launch_s / 1e9 / pk.get("hbm_gbs"),
                       "traffic": traffic_from_profile(INNER_SOURCES, "ebe_inner_%s_realistic.md" % args.precision),
-                      "kernel": "ebe_lo_kernel (%s inner element-by-element A d)" % args.precision,
+                      "kernel": "%s (%s inner element-by-element A d)" % (LO_KERNELS.get(m.info()["inner_variant"], "ebe_lo"), args.precision),
                       "peak_source": "of measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                       "algorithmic_bytes": lo_bytes, "launch_ms": lo_launch_s * 1e3, "launches_timed": lo_n,
                       "time_share": lo_ms / (1e3 * t)}

@@ -69,7 +69,9 @@ typedef struct {
   int32_t inner_variant; /* launch variant of the inner operator: -1 lets the set-up
                             autotuner time all and keep the fastest; 0, 1 one CTA
                             per element block (3 or 4 CTAs per SM); 2 persistent,
-                            cp.async-pipelined CTAs */
+                            cp.async-pipelined CTAs; 3 persistent warp-specialised
+                            CTAs (a producer warp stages element blocks with bulk
+                            asynchronous copies and mbarriers) */
 } gsw_solver_opts;
 
 typedef struct {

@@ -14,6 +14,8 @@
 #include "gsw.h"
 #include "gsw_internal.cuh"
 #include "gsw_misfit.cuh"
+
+static_assert(gsw::kStatusTimeout == GSW_E_TIMEOUT, "device timeout status");
 #include <cuda_fp16.h>
 
 using namespace gsw;
@@ -416,6 +418,10 @@ gsw_status autotune_lo(gsw_ctx* ctx, Model* m) {
   CK(cudaGetLastError());
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  unsigned int err = 0;
+  CK(cudaMemcpyAsync(&err, &m->isc->err, sizeof(err), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (err) return fail(ctx, GSW_E_TIMEOUT, "inner operator: a bounded device-side wait ran out");
   return GSW_OK;
 }
 
@@ -733,6 +739,8 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
     if (h.status == GSW_E_NOCONV)
       return fail(ctx, GSW_E_NOCONV, "step %lld: flexible CG did not reach %g in %d iterations (at %g)",
                   (long long)m->step, m->opts.tol, h.iter, h.relres);
+    if (h.status == GSW_E_TIMEOUT)
+      return fail(ctx, GSW_E_TIMEOUT, "step %lld: a bounded wait of the inner operator ran out", (long long)m->step);
     return fail(ctx, GSW_E_NAN, "step %lld: non-finite CG residual", (long long)m->step);
   }
   TRY(mlp_after_step(ctx, m, s));

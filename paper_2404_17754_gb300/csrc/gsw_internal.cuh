@@ -6,6 +6,7 @@
 namespace gsw {
 
 constexpr int kMaxMat = 32;        // materials (layers) per model
+constexpr int kStatusTimeout = -6;  // GSW_E_TIMEOUT: a bounded device-side wait ran out
 constexpr int kNodeThreads = 256;  // node-wise kernels
 constexpr int kElemThreads = 128;  // element-by-element kernels
 constexpr int kMaxNodeBlocks = 152 * 8;
@@ -99,7 +100,8 @@ struct InnerScalars {
   unsigned int pad;
   float alpha_f;  // s . t / d . A d, set by the last block of the operator kernel
   float beta_f;   // FP32 copy of beta for the direction update
-  float pad_f[2];
+  unsigned int err;  // nonzero: a bounded wait of the operator kernel ran out
+  unsigned int pad2;
 };
 
 // Element blocks with local node numbering: block b holds elements
@@ -193,7 +195,7 @@ void launch_inner_init(int64_t N, const double* r, const float* dinv32, float* s
 void launch_ebe_lo(int half_geo, int half_vec, const void* lo_view, const void* d, float* w,
                    double* partials, InnerScalars* sc, cudaStream_t st, int variant,
                    const CgScalars* outer = nullptr);
-constexpr int kLoVariants = 3;
+constexpr int kLoVariants = 4;
 void launch_inner_update(int64_t N, float* y, float* s, float* t, const void* d, int half_vec,
                          float* w, const float* dinv32, double* partials, InnerScalars* sc,
                          cudaStream_t st, const CgScalars* outer);

@@ -222,7 +222,17 @@ __global__ void lo_convert_kernel(ModelView m, int n_blk, const uint16_t* __rest
     r.vol = ok ? (float)m.geo[9 * m.E + e] : 0.f;
     r.mat = ok ? (uint16_t)m.emat[e] : 0;
     r.pad1 = 0;
-    rec[t] = r;
+    // block b's records are stored as RW planes of kLoBlock 16-byte words, so
+    // that consecutive threads read consecutive words
+    constexpr int RW = LoRec<SG>::words;
+    union {
+      typename LoRec<SG>::type r;
+      uint4 v[RW];
+    } u;
+    u.r = r;
+    uint4* out = reinterpret_cast<uint4*>(rec) + b * RW * kLoBlock + pl;
+#pragma unroll
+    for (int q = 0; q < RW; ++q) out[q * kLoBlock] = u.v[q];
   }
   if (t < 6 * m.F) fgeo32[t] = (float)m.fgeo[t];
   if (t < 6 * m.N) dinv32[t] = (float)dinv[t];
@@ -282,9 +292,9 @@ __global__ void __launch_bounds__(kLoBlock, MINB) ebe_lo_kernel(LoView<SG> m, co
       uint4 v[RW];
       Rec r;
     } u;
-    const uint4* rp = reinterpret_cast<const uint4*>(m.rec) + ((int64_t)b * kLoBlock + threadIdx.x) * RW;
+    const uint4* rp = reinterpret_cast<const uint4*>(m.rec) + (int64_t)b * kLoBlock * RW + threadIdx.x;
 #pragma unroll
-    for (int q = 0; q < RW; ++q) u.v[q] = __ldg(rp + q);
+    for (int q = 0; q < RW; ++q) u.v[q] = __ldg(rp + q * kLoBlock);
     const int n0 = m.blk.ptr[b], nn = m.blk.ptr[b + 1] - n0;
     // each thread owns nodes threadIdx.x + j * kLoBlock (j < kLoNodesPerThread):
     // all index loads first, then all gathers, so their latencies overlap
@@ -813,7 +823,7 @@ __global__ void __launch_bounds__(kLoBlock, 2) ebe_lo_pipe_kernel(LoView<SG> m, 
           Rec r;
         } u;
 #pragma unroll
-        for (int q = 0; q < RW; ++q) u.v[q] = recs[st * kLoBlock * RW + threadIdx.x * RW + q];
+        for (int q = 0; q < RW; ++q) u.v[q] = recs[st * kLoBlock * RW + q * kLoBlock + threadIdx.x];
         float g[3][3];
 #pragma unroll
         for (int mm = 0; mm < 3; ++mm)
@@ -918,14 +928,322 @@ static void ebe_lo_pipe_launch(const LoView<SG>& m, const SD* d, float* w, doubl
   ebe_lo_pipe_kernel<SG, SD><<<g, kLoBlock, smem, st>>>(m, d, w, partials, sc, outer, n_pipe);
 }
 
+// ---- warp-specialised variant -------------------------------------------------
+//
+// Persistent CTAs of 6 consumer warps (one element per thread, as above) and
+// one producer warp.  The producer stages element block b_i in a ring of
+// kWsStages shared-memory stages: lane 0 issues two bulk asynchronous copies
+// (the block's packed records and its node list) that complete on the
+// stage's "meta" mbarrier; once they have landed, the 32 lanes gather the
+// block's search-direction entries with cp.async, completing on the stage's
+// "x" mbarrier.  Metadata runs one block ahead of the gathers, so the
+// producer keeps two blocks in flight while the consumers apply a third;
+// the consumers release a stage through its "empty" mbarrier.  Every wait is
+// bounded: a wait that runs out sets InnerScalars::err (and fails the outer
+// solve), and the CTA stops after its copies in flight have landed.
+
+constexpr int kWsStages = 3;
+constexpr int kWsThreads = kLoBlock + 32;
+constexpr long long kWsSpin = 1ll << 22;  // try_wait attempts (each may suspend briefly)
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(b)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for the phase of the given parity; false if it ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
+  for (long long it = 0; it < kWsSpin; ++it)
+    if (mbar_try(b, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive(uint64_t* b) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;\n" ::"n"(kLoBlock) : "memory"); }
+
+template <typename SG, typename SD>
+size_t lo_ws_smem(int max_local) {
+  return (sizeof(uint4) * kLoBlock * LoRec<SG>::words + sizeof(int32_t) * (size_t)max_local +
+          sizeof(SD) * 4 * (size_t)max_local) *
+             kWsStages +
+         sizeof(float) * 3 * (size_t)max_local;
+}
+
+template <typename SG, typename SD>
+__global__ void __launch_bounds__(kWsThreads, 2) ebe_lo_ws_kernel(LoView<SG> m, const SD* __restrict__ d,
+                                                                 float* __restrict__ w, double* partials,
+                                                                 InnerScalars* sc, const CgScalars* outer,
+                                                                 int n_ws) {
+  if (outer != nullptr && ((volatile const CgScalars*)outer)->done) return;
+  typedef typename LoRec<SG>::type Rec;
+  constexpr int RW = LoRec<SG>::words;
+  constexpr int NB = (int)sizeof(SD) * 4;  // bytes per node of the padded search direction
+  constexpr unsigned kRecBytes = sizeof(uint4) * kLoBlock * RW;
+  extern __shared__ __align__(16) unsigned char ws_smem[];
+  const int ML = m.blk.max_local;  // a multiple of 4
+  uint4* recs = reinterpret_cast<uint4*>(ws_smem);
+  int32_t* idx = reinterpret_cast<int32_t*>(ws_smem + (size_t)kRecBytes * kWsStages);
+  unsigned char* xr = reinterpret_cast<unsigned char*>(idx + (size_t)kWsStages * ML);
+  float* ys = reinterpret_cast<float*>(xr + (size_t)kWsStages * ML * NB);
+  __shared__ __align__(8) uint64_t bar_meta[kWsStages], bar_x[kWsStages], bar_empty[kWsStages];
+  __shared__ int nn_stage[kWsStages];
+  __shared__ int abort_flag;
+  __shared__ float matc[kMaxMat][3];
+  const int tid = threadIdx.x;
+  if (tid < m.n_mat) {
+    const MatCoef& c = m.mat[tid];
+    matc[tid][0] = (float)(c.cK * c.lam / 20.0);
+    matc[tid][1] = (float)(c.cK * c.mu / 20.0);
+    matc[tid][2] = (float)(c.cM * c.rho / 420.0);
+  }
+  if (tid == 0) {
+    for (int st = 0; st < kWsStages; ++st) {
+      mbar_init(&bar_meta[st], 1);
+      mbar_init(&bar_x[st], 32);
+      mbar_init(&bar_empty[st], kLoBlock / 32);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  }
+  for (int q = tid; q < 3 * ML; q += kWsThreads) ys[q] = 0.f;
+  __syncthreads();
+  float dot = 0.f;
+  const int nb = m.blk.n_blk;
+  const int b0 = blockIdx.x;
+  if (b0 < n_ws) {
+    const int n_my = b0 < nb ? (nb - b0 + n_ws - 1) / n_ws : 0;
+    if (tid >= kLoBlock) {
+      // ---------------- producer warp ----------------
+      const int lane = tid - kLoBlock;
+      int issued = 0;  // blocks whose metadata copies were issued
+      bool ok = true;
+      for (int i = 0; i <= n_my && ok; ++i) {
+        if (i < n_my) {
+          const int st = i % kWsStages;
+          if (i >= kWsStages) ok = mbar_wait(&bar_empty[st], ((i / kWsStages) - 1) & 1);
+          if (ok && lane == 0) {
+            const int b = b0 + i * n_ws;
+            const int n0 = m.blk.ptr[b], nn = m.blk.ptr[b + 1] - n0;
+            nn_stage[st] = nn;
+            mbar_expect_tx(&bar_meta[st], kRecBytes + 4u * (unsigned)nn);
+            bulk_g2s(recs + (size_t)st * kLoBlock * RW,
+                     reinterpret_cast<const uint4*>(m.rec) + (int64_t)b * kLoBlock * RW, kRecBytes,
+                     &bar_meta[st]);
+            if (nn > 0) bulk_g2s(idx + (size_t)st * ML, m.blk.nodes + n0, 4u * (unsigned)nn, &bar_meta[st]);
+          }
+          if (ok) issued = i + 1;
+          ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        }
+        if (ok && i >= 1) {
+          const int j = i - 1, st = j % kWsStages;
+          ok = mbar_wait(&bar_meta[st], (j / kWsStages) & 1);
+          ok = __all_sync(0xffffffffu, ok);
+          if (ok) {
+            const int nn = nn_stage[st];
+            const int32_t* ix = idx + (size_t)st * ML;
+            unsigned char* dst = xr + (size_t)st * ML * NB;
+            for (int q = lane; q < nn; q += 32) {
+              const int64_t g = ix[q] & 0x7fffffff;
+              if (NB == 16)
+                cp_async16(dst + (size_t)q * NB, d + 4 * g);
+              else
+                cp_async8(dst + (size_t)q * NB, d + 4 * g);
+            }
+            cp_async_arrive(&bar_x[st]);
+          }
+        }
+      }
+      if (!ok) {
+        abort_flag = 1;
+        sc->err = 1u;
+        if (outer != nullptr) {
+          ((CgScalars*)outer)->status = kStatusTimeout;
+          ((CgScalars*)outer)->done = 1;
+        }
+      }
+      // every copy issued by this warp lands before the CTA may exit
+      cp_async_wait0();
+      if (lane == 0)
+        for (int i = (issued > kWsStages ? issued - kWsStages : 0); i < issued; ++i)
+          mbar_wait(&bar_meta[i % kWsStages], (i / kWsStages) & 1);
+      __syncwarp();
+    } else {
+      // ---------------- consumer warps ----------------
+      for (int i = 0; i < n_my; ++i) {
+        const int st = i % kWsStages;
+        const unsigned ph = (i / kWsStages) & 1;
+        bool ok = mbar_wait(&bar_meta[st], ph);
+        if (ok) ok = mbar_wait(&bar_x[st], ph);
+        if (!ok) {
+          atomicExch(&abort_flag, 1);
+          sc->err = 1u;
+          if (outer != nullptr) {
+            ((CgScalars*)outer)->status = kStatusTimeout;
+            ((CgScalars*)outer)->done = 1;
+          }
+        }
+        consumer_sync();
+        if (((volatile int*)&abort_flag)[0]) break;
+        const uint4* rs = recs + (size_t)st * kLoBlock * RW;
+        const unsigned char* xs = xr + (size_t)st * ML * NB;
+        {
+          union {
+            uint4 v[RW];
+            Rec r;
+          } u;
+#pragma unroll
+          for (int q = 0; q < RW; ++q) u.v[q] = rs[q * kLoBlock + tid];
+          float g[3][3];
+#pragma unroll
+          for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) g[mm][k] = to_f(u.r.g[3 * mm + k]);
+          const float V = u.r.vol;
+          const int mt = u.r.mat;
+          const float lamS = matc[mt][0] * V, muS = matc[mt][1] * V, mS = matc[mt][2] * V;
+          float wv[10][3], f[10][3];
+#pragma unroll
+          for (int k = 0; k < 10; ++k) unpack3<SD>(xs + (size_t)u.r.lc[k] * NB, wv[k][0], wv[k][1], wv[k][2]);
+          stiffness_apply<float>(wv, g, lamS, muS, f);
+          mass_apply<float>(wv, mS, f);
+#pragma unroll
+          for (int k = 0; k < 10; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              atomicAdd(ys + 3 * u.r.lc[k] + c, f[k][c]);
+              dot = fmaf(wv[k][c], f[k][c], dot);
+            }
+        }
+        consumer_sync();
+        const int nn = nn_stage[st];
+        const int32_t* ix = idx + (size_t)st * ML;
+        for (int q = tid; q < nn; q += kLoBlock) {
+          const int32_t raw = ix[q];
+          const int64_t g = raw & 0x7fffffff;
+          const float y0 = ys[3 * q], y1 = ys[3 * q + 1], y2 = ys[3 * q + 2];
+          ys[3 * q] = 0.f;
+          ys[3 * q + 1] = 0.f;
+          ys[3 * q + 2] = 0.f;
+          if (g == m.N) continue;  // padding entry (dummy node N)
+          if (raw < 0) {
+            w[3 * g] = y0;
+            w[3 * g + 1] = y1;
+            w[3 * g + 2] = y2;
+          } else {
+            atomicAdd(w + 3 * g, y0);
+            atomicAdd(w + 3 * g + 1, y1);
+            atomicAdd(w + 3 * g + 2, y2);
+          }
+        }
+        consumer_sync();
+        if ((tid & 31) == 0) mbar_arrive(&bar_empty[st]);
+      }
+    }
+  } else {
+    // absorbing faces: (2/dt) C_abs d
+    const int64_t fc = (int64_t)(b0 - n_ws) * kWsThreads + tid;
+    if (fc < m.F && m.fgeo[5 * m.F + fc] > 0.5f) {
+      const float sc2 = (float)(2.0 / m.dt) / 180.f;
+      const float As = sc2 * m.fgeo[fc], Ad = sc2 * m.fgeo[m.F + fc];
+      const float n[3] = {m.fgeo[2 * m.F + fc], m.fgeo[3 * m.F + fc], m.fgeo[4 * m.F + fc]};
+      int64_t nd[6];
+      float z[6][3], xin[6][3];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        nd[k] = m.fnode[k * m.F + fc];
+        load3(d + 4 * nd[k], xin[k][0], xin[k][1], xin[k][2]);
+        const float dn = n[0] * xin[k][0] + n[1] * xin[k][1] + n[2] * xin[k][2];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) z[k][c] = fmaf(As, xin[k][c], Ad * dn * n[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float Zv = z[0][c] + z[1][c] + z[2][c];
+        const float Ze = z[3][c] + z[4][c] + z[5][c];
+        float yf[6];
+        yf[0] = 7.f * z[0][c] - Zv - 4.f * z[4][c];
+        yf[1] = 7.f * z[1][c] - Zv - 4.f * z[5][c];
+        yf[2] = 7.f * z[2][c] - Zv - 4.f * z[3][c];
+        yf[3] = 16.f * (z[3][c] + Ze) - 4.f * z[2][c];
+        yf[4] = 16.f * (z[4][c] + Ze) - 4.f * z[0][c];
+        yf[5] = 16.f * (z[5][c] + Ze) - 4.f * z[1][c];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          atomicAdd(w + 3 * nd[k] + c, yf[k]);
+          dot = fmaf(xin[k][c], yf[k], dot);
+        }
+      }
+    }
+  }
+  lo_finish_dw(dot, partials, sc);
+}
+
+template <typename SG, typename SD>
+static void ebe_lo_ws_launch(const LoView<SG>& m, const SD* d, float* w, double* partials, InnerScalars* sc,
+                             cudaStream_t st, const CgScalars* outer) {
+  const size_t smem = lo_ws_smem<SG, SD>(m.blk.max_local);
+  static size_t attr_set = 0;  // per instantiation
+  static int sms = 0, occ = 0;
+  static size_t occ_smem = 0;
+  if (smem > attr_set) {
+    cudaFuncSetAttribute(ebe_lo_ws_kernel<SG, SD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = smem;
+  }
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  if (occ_smem != smem) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ebe_lo_ws_kernel<SG, SD>, kWsThreads, smem);
+    if (occ < 1) occ = 1;
+    occ_smem = smem;
+  }
+  int n_ws = sms * occ;
+  if (n_ws > m.blk.n_blk) n_ws = m.blk.n_blk > 0 ? m.blk.n_blk : 1;
+  const unsigned g = (unsigned)(n_ws + (m.F + kWsThreads - 1) / kWsThreads);
+  ebe_lo_ws_kernel<SG, SD><<<g, kWsThreads, smem, st>>>(m, d, w, partials, sc, outer, n_ws);
+}
+
 // variant: 0 -> up to 3 CTAs per SM (no register cap below 96), 1 -> 4 CTAs
-// per SM (80 registers), 2 -> the persistent software-pipelined kernel;
+// per SM (80 registers), 2 -> the persistent software-pipelined kernel,
+// 3 -> the persistent warp-specialised kernel (bulk copies, mbarriers);
 // picked per model by the set-up autotuner.
 template <typename SG, typename SD>
 static void ebe_lo_launch(int variant, const LoView<SG>& m, const SD* d, float* w, double* partials,
                           InnerScalars* sc, cudaStream_t st, const CgScalars* outer) {
   if (variant == 2) {
     ebe_lo_pipe_launch<SG, SD>(m, d, w, partials, sc, st, outer);
+    return;
+  }
+  // bulk copies need 16-byte aligned sources (device allocations are)
+  if (variant == 3 && ((reinterpret_cast<uintptr_t>(m.rec) | reinterpret_cast<uintptr_t>(m.blk.nodes)) & 15) == 0) {
+    ebe_lo_ws_launch<SG, SD>(m, d, w, partials, sc, st, outer);
     return;
   }
   const unsigned g = (unsigned)(m.blk.n_blk + (m.F + kLoBlock - 1) / kLoBlock);

@@ -33,7 +33,7 @@ def _relerr(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("prec,bound", [("fp32", 2e-6), ("fp16", 5e-3)])
 @pytest.mark.parametrize("nx,ny", [(3, 2), (6, 5), (14, 9)])
 def test_inner_operator_matches_csr(ctx, prec, bound, nx, ny, variant):
@@ -108,4 +108,33 @@ def test_mixed_full_size_true_residual(ctx):
     assert np.linalg.norm(res) / np.linalg.norm(b) <= 2e-8
     st = m.stats()
     assert st["cg_iters_last"] < 20
+    m.free()
+
+
+def test_inner_variants_agree_mid_size(ctx):
+    """Every launch variant of the inner operator gives the same product on a mesh with many
+    element blocks per persistent CTA (stage rings wrap several times), and the warp-specialised
+    variant drives the mixed solve to the same states as the one-CTA-per-block variant."""
+    import torch
+
+    cfg = configs.config2(n_steps=4, crop=60)
+    m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
+    m.set_time(cfg["dt"], 4, cfg["band"])
+    m.set_input(cfg["dir"], cfg["p"])
+    x = torch.tensor(np.random.default_rng(5).standard_normal((m.n_nodes, 3)), device="cuda")
+    ref = m.apply(0, x).cpu().numpy().ravel()
+    ys = {}
+    for v in range(4):
+        m.set_solver(tol=1e-8, precision=1, inner_iters=20, inner_variant=v)
+        ys[v] = m.apply(4, x).cpu().numpy().ravel()
+        assert _relerr(ys[v], ref) <= 2e-6, v
+    for v in range(4):
+        assert _relerr(ys[v], ys[1]) <= 1e-6, v
+    states = {}
+    for v in (1, 3):
+        m.set_solver(tol=1e-8, precision=1, inner_iters=20, inner_variant=v)
+        m.reset()
+        m.step(3)
+        states[v] = m.get_state()[0]
+    assert _relerr(states[3], states[1]) <= 1e-6
     m.free()
