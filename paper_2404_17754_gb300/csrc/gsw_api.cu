@@ -74,6 +74,7 @@ struct Model {
   float *y32 = nullptr, *s32 = nullptr, *t32 = nullptr, *w32 = nullptr;
   void* d_lo = nullptr;
   InnerScalars* isc = nullptr;
+  float* dw_part = nullptr;    // per-CTA partial sums of the inner operator's d . A d
   int lo_variant = 0;          // launch variant of the inner operator (autotuned)
   bool live_tune = false;      // refine the choice inside the next host-driven inner solve
   // learned initial guess
@@ -439,16 +440,15 @@ gsw_status build_lo(gsw_ctx* ctx, Model* m, int half) {
     std::vector<int32_t> h((size_t)m->n_blk), ptr((size_t)m->n_blk + 1);
     CK(cudaMemcpyAsync(h.data(), counts, sizeof(int32_t) * m->n_blk, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    // node lists padded to multiples of 4 entries (16-byte aligned starts);
-    // padding entries name the dummy node N (zero contribution)
-    ptr[0] = 0;
-    int mx = 0;
-    for (int b = 0; b < m->n_blk; ++b) {
-      const int padded = (h[b] + 3) & ~3;
-      ptr[b + 1] = ptr[b] + padded;
-      if (padded > mx) mx = padded;
-    }
+    // node lists at the fixed stride max_local (a multiple of 4 entries, so
+    // 16-byte aligned starts); padding entries name the dummy node N (zero
+    // contribution)
+    int mx = 4;
+    for (int b = 0; b < m->n_blk; ++b) mx = std::max(mx, (h[b] + 3) & ~3);
+    for (int b = 0; b <= m->n_blk; ++b) ptr[b] = b * mx;
     m->max_local = mx;
+    if ((int64_t)m->n_blk * mx > (int64_t)INT32_MAX)
+      return fail(ctx, GSW_E_INVALID, "mesh too large for 32-bit element-block node lists");
     if (mx > kLoBlock * kLoNodesPerThread)
       return fail(ctx, GSW_E_INVALID, "element block with %d unique nodes exceeds %d (mesh ordering too scattered)", mx,
                   kLoBlock * kLoNodesPerThread);
@@ -472,6 +472,7 @@ gsw_status build_lo(gsw_ctx* ctx, Model* m, int half) {
     TRY(alloc_into(ctx, m, &m->t32, n3));
     TRY(alloc_into(ctx, m, &m->w32, n3 + 4));  // + the dummy node's row
     TRY(alloc_into(ctx, m, &m->isc, 1));
+    TRY(alloc_into(ctx, m, &m->dw_part, (size_t)m->n_blk + (size_t)((m->F + kLoBlock - 1) / kLoBlock) + 1));
     CK(cudaMemsetAsync(m->isc, 0, sizeof(InnerScalars), s));
     m->lo_ready = true;
     m->geo_lo = nullptr;
@@ -488,8 +489,8 @@ gsw_status build_lo(gsw_ctx* ctx, Model* m, int half) {
                     s);
   CK(cudaGetLastError());
   BlockView bv = {m->n_blk, m->max_local, m->blk_ptr, m->blk_nodes};
-  m->lo_f = LoView<float>{m->N, m->E, m->F, m->n_mat, bv, m->geo_lo, m->mat, m->fnode, m->fgeo32, m->dt};
-  m->lo_h = LoView<__half>{m->N, m->E, m->F, m->n_mat, bv, m->geo_lo, m->mat, m->fnode, m->fgeo32, m->dt};
+  m->lo_f = LoView<float>{m->N, m->E, m->F, m->n_mat, bv, m->geo_lo, m->mat, m->fnode, m->fgeo32, m->dt, m->dw_part};
+  m->lo_h = LoView<__half>{m->N, m->E, m->F, m->n_mat, bv, m->geo_lo, m->mat, m->fnode, m->fgeo32, m->dt, m->dw_part};
   m->live_tune = (m->opts.inner_variant < 0);
   return autotune_lo(ctx, m);
 }
@@ -612,7 +613,7 @@ int64_t inner_solve(Model* m, cudaStream_t s) {
     if (timed) cudaEventRecord(m->ev_lo[2 * k], s);
     launch_ebe_lo(half, half, view, m->d_lo, m->w32, m->partials, m->isc, s, variant, m->cg);
     if (timed) cudaEventRecord(m->ev_lo[2 * k + 1], s);
-    launch_inner_update(m->N, m->y32, m->s32, m->t32, m->d_lo, half, m->w32, m->dinv32, m->partials, m->isc, s,
+    launch_inner_update(m->N, m->y32, m->s32, m->t32, m->d_lo, half, m->w32, m->dinv32, m->dw_part, m->partials, m->isc, s,
                         m->cg);
     if (k + 1 < it) launch_inner_dupdate(m->N, m->t32, m->d_lo, half, m->isc, s, m->cg);
   }
@@ -766,7 +767,7 @@ void inner_solve_dev(Model* m, cudaStream_t s) {
   const int it = m->opts.inner_iters > 0 ? m->opts.inner_iters : 1;
   for (int k = 0; k < it; ++k) {
     launch_ebe_lo(half, half, view, m->d_lo, m->w32, m->partials, m->isc, s, m->lo_variant, m->cg);
-    launch_inner_update(m->N, m->y32, m->s32, m->t32, m->d_lo, half, m->w32, m->dinv32, m->partials, m->isc, s,
+    launch_inner_update(m->N, m->y32, m->s32, m->t32, m->d_lo, half, m->w32, m->dinv32, m->dw_part, m->partials, m->isc, s,
                         m->cg);
     if (k + 1 < it) launch_inner_dupdate(m->N, m->t32, m->d_lo, half, m->isc, s, m->cg);
   }

@@ -100,8 +100,8 @@ struct InnerScalars {
   unsigned int pad;
   float alpha_f;  // s . t / d . A d, set by the last block of the operator kernel
   float beta_f;   // FP32 copy of beta for the direction update
-  unsigned int err;  // nonzero: a bounded wait of the operator kernel ran out
-  unsigned int pad2;
+  unsigned int err;   // nonzero: a bounded wait of the operator kernel ran out
+  unsigned int n_dw;  // grid size of the last operator launch (entries of LoView::dw_part)
 };
 
 // Element blocks with local node numbering: block b holds elements
@@ -127,6 +127,7 @@ struct LoView {
   const int32_t* fnode;     // [6][F]
   const float* fgeo;        // [6][F]
   double dt;
+  float* dw_part;           // [operator grid] per-CTA partial sums of d . A d
 };
 
 enum EbeMode { kModeA = 0, kModeK = 1, kModeM = 2, kModeC = 3, kModeRhs = 4, kModeRes = 5 };
@@ -197,8 +198,8 @@ void launch_ebe_lo(int half_geo, int half_vec, const void* lo_view, const void* 
                    const CgScalars* outer = nullptr);
 constexpr int kLoVariants = 4;
 void launch_inner_update(int64_t N, float* y, float* s, float* t, const void* d, int half_vec,
-                         float* w, const float* dinv32, double* partials, InnerScalars* sc,
-                         cudaStream_t st, const CgScalars* outer);
+                         float* w, const float* dinv32, const float* dw_part, double* partials,
+                         InnerScalars* sc, cudaStream_t st, const CgScalars* outer);
 void launch_inner_dupdate(int64_t N, const float* t, void* d, int half_vec, const InnerScalars* sc,
                           cudaStream_t st, const CgScalars* outer);
 // conversions for the standalone reduced-precision operator (tests)

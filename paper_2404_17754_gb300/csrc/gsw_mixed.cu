@@ -251,14 +251,15 @@ __global__ void dinv_mean_kernel(int64_t N, const double* __restrict__ dinv, dou
 // Reduced-precision element-by-element product w = A d (+ partial d . w)
 // ------------------------------------------------------------------------------
 
-// Grid sum of the per-thread d . A d contributions (FP32); the last block
-// stores d . A d and the step length alpha = s . t / d . A d.
-__device__ __forceinline__ void lo_finish_dw(float dot, double* partials, InnerScalars* sc) {
-  float vals[1] = {dot}, out[1];
-  if (last_block_reduce_f<1>(vals, reinterpret_cast<float*>(partials), &sc->counter, out) && threadIdx.x == 0) {
-    const double st = ((volatile InnerScalars*)sc)->st;
-    sc->dw = out[0];
-    sc->alpha_f = (out[0] != 0.f) ? (float)(st / (double)out[0]) : 0.f;
+// Per-CTA partial sum of the per-thread d . A d contributions (FP32), stored
+// in dw_part[blockIdx.x]; the direction update sums the partials in a fixed
+// order (so the operator kernel carries no grid-wide reduction tail).
+__device__ __forceinline__ void lo_store_dw(float dot, float* dw_part, InnerScalars* sc) {
+  __shared__ float shd[32];
+  const float s = block_sum_f(dot, shd);
+  if (threadIdx.x == 0) {
+    dw_part[blockIdx.x] = s;
+    if (blockIdx.x == 0) sc->n_dw = gridDim.x;
   }
 }
 
@@ -295,7 +296,10 @@ __global__ void __launch_bounds__(kLoBlock, MINB) ebe_lo_kernel(LoView<SG> m, co
     const uint4* rp = reinterpret_cast<const uint4*>(m.rec) + (int64_t)b * kLoBlock * RW + threadIdx.x;
 #pragma unroll
     for (int q = 0; q < RW; ++q) u.v[q] = __ldg(rp + q * kLoBlock);
-    const int n0 = m.blk.ptr[b], nn = m.blk.ptr[b + 1] - n0;
+    // node lists have the fixed stride max_local (padding names the dummy
+    // node N), so no offset load precedes the index loads
+    const int64_t n0 = (int64_t)b * m.blk.max_local;
+    const int nn = m.blk.max_local;
     // each thread owns nodes threadIdx.x + j * kLoBlock (j < kLoNodesPerThread):
     // all index loads first, then all gathers, so their latencies overlap
     int32_t raw[kLoNodesPerThread];
@@ -400,7 +404,7 @@ __global__ void __launch_bounds__(kLoBlock, MINB) ebe_lo_kernel(LoView<SG> m, co
       }
     }
   }
-  lo_finish_dw(dot, partials, sc);
+  lo_store_dw(dot, m.dw_part, sc);
 }
 
 // ------------------------------------------------------------------------------
@@ -458,9 +462,41 @@ __global__ void inner_init_kernel(int64_t N, const double* __restrict__ r, const
 template <typename SD>
 __global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __restrict__ s, float* __restrict__ t,
                                     const SD* __restrict__ d, float* __restrict__ w, const float* __restrict__ dinv,
-                                    double* partials, InnerScalars* sc, const CgScalars* outer) {
+                                    const float* __restrict__ dw_part, double* partials, InnerScalars* sc,
+                                    const CgScalars* outer) {
   if (outer != nullptr && ((volatile const CgScalars*)outer)->done) return;
-  const float alpha = ((volatile InnerScalars*)sc)->alpha_f;
+  // d . A d from the operator's per-CTA partials, summed in the same fixed
+  // order by every CTA; alpha = s . t / d . A d
+  __shared__ float sh_red[32];
+  __shared__ float alpha_s;
+  {
+    const unsigned int G = ((volatile const InnerScalars*)sc)->n_dw, B = blockDim.x;
+    float a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = 0.f;
+    unsigned int i = threadIdx.x;
+    for (; i + 7 * B < G; i += 8 * B) {
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = __ldcg(dw_part + i + j * B);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) a[j] += v[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (i + j * B < G) a[j] += __ldcg(dw_part + i + j * B);
+    const float dw = block_sum_f(((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])), sh_red);
+    if (threadIdx.x == 0) {
+      const double st_old = ((volatile InnerScalars*)sc)->st;
+      alpha_s = (dw != 0.f) ? (float)(st_old / (double)dw) : 0.f;
+      if (blockIdx.x == 0) {
+        sc->dw = dw;
+        sc->alpha_f = alpha_s;
+      }
+    }
+    __syncthreads();
+  }
+  const float alpha = alpha_s;
   float st = 0.f;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
     float sn[3], tn[3];
@@ -905,7 +941,7 @@ __global__ void __launch_bounds__(kLoBlock, 2) ebe_lo_pipe_kernel(LoView<SG> m, 
       }
     }
   }
-  lo_finish_dw(dot, partials, sc);
+  lo_store_dw(dot, m.dw_part, sc);
 }
 
 template <typename SG, typename SD>
@@ -1200,7 +1236,7 @@ __global__ void __launch_bounds__(kWsThreads, 2) ebe_lo_ws_kernel(LoView<SG> m, 
       }
     }
   }
-  lo_finish_dw(dot, partials, sc);
+  lo_store_dw(dot, m.dw_part, sc);
 }
 
 template <typename SG, typename SD>
@@ -1270,14 +1306,14 @@ void launch_ebe_lo(int half_geo, int half_vec, const void* lo_view, const void* 
   }
 }
 void launch_inner_update(int64_t N, float* y, float* s, float* t, const void* d, int half_vec, float* w,
-                         const float* dinv32, double* partials, InnerScalars* sc, cudaStream_t st,
-                         const CgScalars* outer) {
+                         const float* dinv32, const float* dw_part, double* partials, InnerScalars* sc,
+                         cudaStream_t st, const CgScalars* outer) {
   if (half_vec)
     inner_update_kernel<__half><<<node_blocks(N), kNodeThreads, 0, st>>>(N, y, s, t, (const __half*)d, w, dinv32,
-                                                                         partials, sc, outer);
+                                                                         dw_part, partials, sc, outer);
   else
     inner_update_kernel<float><<<node_blocks(N), kNodeThreads, 0, st>>>(N, y, s, t, (const float*)d, w, dinv32,
-                                                                        partials, sc, outer);
+                                                                        dw_part, partials, sc, outer);
 }
 void launch_inner_dupdate(int64_t N, const float* t, void* d, int half_vec, const InnerScalars* sc,
                           cudaStream_t st, const CgScalars* outer) {
