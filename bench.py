@@ -223,7 +223,7 @@ def run_candidates(args, rank, world, dist):
         m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
         m.set_time(cfg["dt"], n_total, cfg["band"])
         m.set_input(cfg["dir"], cfg["p"])
-        m.set_solver(tol=args.tol, precision=prec, inner_iters=args.inner, batch_outer=8)
+        m.set_solver(tol=args.tol, precision=prec, inner_iters=args.inner, batch_outer=8, inner_rtol=args.inner_rtol)
         models.append(m)
         dof += 3 * cfg["mesh"]["xyz"].shape[0]
     batch = ctx.batch(models)
@@ -293,7 +293,7 @@ def run_learned(args, rank, world, dist):
         m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
         m.set_time(cfg["dt"], n_total, cfg["band"])
         m.set_input(cfg["dir"], cfg["p"])
-        m.set_solver(tol=args.tol, precision=prec, inner_iters=args.inner)
+        m.set_solver(tol=args.tol, precision=prec, inner_iters=args.inner, inner_rtol=args.inner_rtol)
         if enable:
             m.set_learning(True, train_steps=args.train_steps, batch=16384, iters_per_step=2, lr=1e-3, seed=7)
         t0 = time.perf_counter()
@@ -340,7 +340,10 @@ def main():
     ap.add_argument("--train-steps", type=int, default=500, help="learned workload: training steps")
     ap.add_argument("--models", type=int, default=128, help="candidates workload: number of models in the batch")
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16"])
-    ap.add_argument("--inner", type=int, default=30, help="inner preconditioner iterations (mixed modes)")
+    ap.add_argument("--inner", type=int, default=30, help="inner preconditioner iterations (mixed modes; the cap "
+                    "when --inner-rtol > 0)")
+    ap.add_argument("--inner-rtol", type=float, default=0.0,
+                    help="inner PCG relative stopping factor (0 = always --inner iterations)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -394,7 +397,7 @@ def main():
     m.set_time(cfg["dt"], n_total + 1, cfg["band"])
     m.set_input(cfg["dir"], cfg["p"])
     prec = {"fp64": 0, "fp32": 1, "fp16": 2}[args.precision]
-    m.set_solver(tol=args.tol, precision=prec, inner_iters=args.inner)
+    m.set_solver(tol=args.tol, precision=prec, inner_iters=args.inner, inner_rtol=args.inner_rtol)
     n_nodes, n_elem, n_faces = mesh["xyz"].shape[0], mesh["conn"].shape[0], mesh["faces"].shape[0]
     dof = 3 * n_nodes
 
@@ -500,8 +503,10 @@ def main():
         "config": {"workload": cfg["name"] if args.workload == "realistic" else "two-layer 100x100x50 m",
                    "dof": dof, "elements": n_elem, "dt": cfg["dt"], "tol": args.tol, "precision": args.precision,
                    "solver": "block-Jacobi PCG" if args.precision == "fp64" else
-                             "flexible CG (FP64) + %d-iteration %s block-Jacobi PCG preconditioner" % (
-                                 args.inner, args.precision),
+                             ("flexible CG (FP64) + %s block-Jacobi PCG preconditioner, %d iterations" % (
+                                 args.precision, args.inner) if args.inner_rtol <= 0 else
+                              "flexible CG (FP64) + %s block-Jacobi PCG preconditioner to relative %g (at most %d "
+                              "iterations)" % (args.precision, args.inner_rtol, args.inner)),
                    "inner_iters_per_step": (st["inner_iters_total"] - inner0) / args.steps,
                    "inner_operator_variant": m.info()["inner_variant"], "parallelism": "independent directional analyses, 1 per GPU",
                    "cg_iters_per_step": iters / args.steps,

@@ -72,6 +72,9 @@ typedef struct {
                             cp.async-pipelined CTAs; 3 persistent warp-specialised
                             CTAs (a producer warp stages element blocks with bulk
                             asynchronous copies and mbarriers) */
+  double inner_rtol;     /* mixed modes: the inner PCG stops once its preconditioned
+                            residual norm has dropped by this factor (0 = always run
+                            inner_iters iterations, which stay the cap); must be in [0, 1) */
 } gsw_solver_opts;
 
 typedef struct {

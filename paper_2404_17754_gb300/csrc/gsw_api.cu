@@ -57,7 +57,7 @@ struct Model {
   std::vector<double> input;
   int dir = 0;
   bool input_set = false;
-  gsw_solver_opts opts = {1e-8, 10000, GSW_PREC_FP64, 20, 8, 6, -1};
+  gsw_solver_opts opts = {1e-8, 10000, GSW_PREC_FP64, 20, 8, 6, -1, 0.0};
   int64_t step = 0;
   bool failed = false;
   gsw_stats stats = {};
@@ -75,6 +75,8 @@ struct Model {
   void* d_lo = nullptr;
   InnerScalars* isc = nullptr;
   float* dw_part = nullptr;    // per-CTA partial sums of the inner operator's d . A d
+  unsigned long long iters_mark = 0;   // device inner-iteration counter when timing started
+  unsigned long long iters_reset = 0;  // device inner-iteration counter at the last reset
   int lo_variant = 0;          // launch variant of the inner operator (autotuned)
   bool live_tune = false;      // refine the choice inside the next host-driven inner solve
   // learned initial guess
@@ -298,6 +300,11 @@ gsw_status model_reset(gsw_ctx* ctx, Model* m) {
   m->step = 0;
   m->failed = false;
   m->stats = gsw_stats{};
+  if (m->lo_ready) {
+    CK(cudaMemcpyAsync(&m->iters_reset, &m->isc->iters, sizeof(m->iters_reset), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
   m->hist_head = 3;
   m->hist_count = 0;
   return GSW_OK;
@@ -601,12 +608,13 @@ gsw_status mlp_after_step(gsw_ctx* ctx, Model* m, cudaStream_t s) {
 int64_t inner_solve(Model* m, cudaStream_t s) {
   const int half = m->lo_half;
   const void* view = half ? (const void*)&m->lo_h : (const void*)&m->lo_f;
-  launch_inner_init(m->N, m->r, m->dinv32, m->s32, m->y32, m->t32, m->d_lo, half, m->w32, m->partials, m->isc,
-                    m->cg, s);
   const int it = m->opts.inner_iters > 0 ? m->opts.inner_iters : 1;
   // live tuning: inside the first host-driven inner solve the launch variants
-  // take turns (in the cache state of a real solve) and the fastest median wins
+  // take turns (in the cache state of a real solve) and the fastest median
+  // wins; that solve runs all inner_iters iterations
   const bool tune = m->live_tune && it >= 2 * kLoVariants && (int)m->ev_lo.size() >= 2 * it;
+  launch_inner_init(m->N, m->r, m->dinv32, m->s32, m->y32, m->t32, m->d_lo, half, m->w32, m->partials, m->isc,
+                    m->cg, s, tune ? 0.f : (float)m->opts.inner_rtol);
   const bool timed = (m->timing || tune) && (int)m->ev_lo.size() >= 2 * it;
   for (int k = 0; k < it; ++k) {
     const int variant = tune ? k % kLoVariants : m->lo_variant;
@@ -627,7 +635,15 @@ int64_t inner_solve(Model* m, cudaStream_t s) {
       if (m->timing) m->lo_ms += ms;
       if (tune && k >= kLoVariants) per[k % kLoVariants].push_back(ms);  // the first round warms up
     }
-    if (m->timing) m->lo_count += it;
+    if (m->timing) {
+      // executed iterations (a solve that met inner_rtol skips the rest)
+      unsigned long long n = 0;
+      if (cudaMemcpyAsync(&n, &m->isc->iters, sizeof(n), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+          cudaStreamSynchronize(s) == cudaSuccess) {
+        m->lo_count += (int64_t)(n - m->iters_mark);
+        m->iters_mark = n;
+      }
+    }
     if (tune) {
       float best = 1e30f;
       for (int v = 0; v < kLoVariants; ++v) {
@@ -763,7 +779,7 @@ void inner_solve_dev(Model* m, cudaStream_t s) {
   const int half = m->lo_half;
   const void* view = half ? (const void*)&m->lo_h : (const void*)&m->lo_f;
   launch_inner_init(m->N, m->r, m->dinv32, m->s32, m->y32, m->t32, m->d_lo, half, m->w32, m->partials, m->isc,
-                    m->cg, s);
+                    m->cg, s, (float)m->opts.inner_rtol);
   const int it = m->opts.inner_iters > 0 ? m->opts.inner_iters : 1;
   for (int k = 0; k < it; ++k) {
     launch_ebe_lo(half, half, view, m->d_lo, m->w32, m->partials, m->isc, s, m->lo_variant, m->cg);
@@ -1088,6 +1104,8 @@ gsw_status gsw_set_solver(gsw_ctx* ctx, int32_t model_id, const gsw_solver_opts*
     return fail(ctx, GSW_E_INVALID, "precision mode %d is not one of FP64, FP32, FP16", opts->precision);
   if (opts->precision != GSW_PREC_FP64 && (opts->inner_iters <= 0 || opts->inner_iters > 10000))
     return fail(ctx, GSW_E_INVALID, "inner_iters must be 1..10000");
+  if (!(opts->inner_rtol >= 0.0 && opts->inner_rtol < 1.0))
+    return fail(ctx, GSW_E_INVALID, "inner_rtol must be in [0, 1)");
   if (opts->inner_variant < -1 || opts->inner_variant >= kLoVariants)
     return fail(ctx, GSW_E_INVALID, "inner_variant must be -1 (autotune) or 0..%d", kLoVariants - 1);
   m->opts = *opts;
@@ -1380,6 +1398,13 @@ gsw_status gsw_timing(gsw_ctx* ctx, int32_t model_id, int32_t enable, double* ms
     m->timing = true;
     m->ebe_ms = m->lo_ms = 0.0;
     m->ebe_count = m->lo_count = 0;
+    m->iters_mark = 0;
+    if (m->lo_ready) {
+      DeviceGuard g(ctx->device);
+      CK(cudaMemcpyAsync(&m->iters_mark, &m->isc->iters, sizeof(m->iters_mark), cudaMemcpyDeviceToHost,
+                         ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+    }
   } else if (enable == 0) {
     m->timing = false;
   }
@@ -1399,6 +1424,14 @@ gsw_status gsw_stats_get(gsw_ctx* ctx, int32_t model_id, gsw_stats* out) {
   Model* m = find(ctx, model_id);
   if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
   *out = m->stats;
+  if (m->lo_ready && m->opts.precision != GSW_PREC_FP64) {
+    // inner iterations actually executed since the last reset (device counter)
+    DeviceGuard g(ctx->device);
+    unsigned long long n = 0;
+    CK(cudaMemcpyAsync(&n, &m->isc->iters, sizeof(n), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    out->inner_iters_total = (int64_t)(n - m->iters_reset);
+  }
   return GSW_OK;
 }
 

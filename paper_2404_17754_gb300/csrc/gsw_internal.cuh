@@ -102,6 +102,10 @@ struct InnerScalars {
   float beta_f;   // FP32 copy of beta for the direction update
   unsigned int err;   // nonzero: a bounded wait of the operator kernel ran out
   unsigned int n_dw;  // grid size of the last operator launch (entries of LoView::dw_part)
+  double st0;         // s . t at the start of the current inner solve
+  float rtol2;        // squared relative stopping factor (0: fixed iteration count)
+  unsigned int idone; // 1 once the current inner solve has met rtol
+  unsigned long long iters;  // inner iterations executed (all solves)
 };
 
 // Element blocks with local node numbering: block b holds elements
@@ -192,7 +196,7 @@ size_t lo_record_bytes(int half_geo);
 // (padded to 4 entries per node)
 void launch_inner_init(int64_t N, const double* r, const float* dinv32, float* s, float* y,
                        float* t, void* d, int half_vec, float* w, double* partials,
-                       InnerScalars* sc, const CgScalars* cg, cudaStream_t st);
+                       InnerScalars* sc, const CgScalars* cg, cudaStream_t st, float rtol);
 void launch_ebe_lo(int half_geo, int half_vec, const void* lo_view, const void* d, float* w,
                    double* partials, InnerScalars* sc, cudaStream_t st, int variant,
                    const CgScalars* outer = nullptr);

@@ -251,6 +251,14 @@ __global__ void dinv_mean_kernel(int64_t N, const double* __restrict__ dinv, dou
 // Reduced-precision element-by-element product w = A d (+ partial d . w)
 // ------------------------------------------------------------------------------
 
+// Inside a solve (outer != nullptr) the inner kernels return at entry once the
+// outer iteration has converged or the current inner solve has met its
+// relative tolerance.
+__device__ __forceinline__ bool inner_stopped(const CgScalars* outer, const InnerScalars* sc) {
+  return outer != nullptr &&
+         (((volatile const CgScalars*)outer)->done || ((volatile const InnerScalars*)sc)->idone);
+}
+
 // Per-CTA partial sum of the per-thread d . A d contributions (FP32), stored
 // in dw_part[blockIdx.x]; the direction update sums the partials in a fixed
 // order (so the operator kernel carries no grid-wide reduction tail).
@@ -273,7 +281,7 @@ template <typename SG, typename SD, int MINB>
 __global__ void __launch_bounds__(kLoBlock, MINB) ebe_lo_kernel(LoView<SG> m, const SD* __restrict__ d,
                                                            float* __restrict__ w, double* partials,
                                                            InnerScalars* sc, const CgScalars* outer) {
-  if (outer != nullptr && ((volatile const CgScalars*)outer)->done) return;
+  if (inner_stopped(outer, sc)) return;
   typedef typename LoRec<SG>::type Rec;
   constexpr int RW = LoRec<SG>::words;
   extern __shared__ float sm[];
@@ -421,7 +429,7 @@ template <typename SD>
 __global__ void inner_init_kernel(int64_t N, const double* __restrict__ r, const float* __restrict__ dinv,
                                   float* __restrict__ s, float* __restrict__ y, float* __restrict__ t,
                                   SD* __restrict__ d, float* __restrict__ w, double* partials,
-                                  InnerScalars* sc, const CgScalars* cg) {
+                                  InnerScalars* sc, const CgScalars* cg, float rtol) {
   if (((volatile const CgScalars*)cg)->done) return;
   // the scale is computed once per block (FP64 division and square root are
   // slow on this GPU) and broadcast through shared memory
@@ -455,7 +463,10 @@ __global__ void inner_init_kernel(int64_t N, const double* __restrict__ r, const
   float vals[1] = {st}, out[1];
   if (last_block_reduce_f<1>(vals, reinterpret_cast<float*>(partials), &sc->counter, out) && threadIdx.x == 0) {
     sc->st = out[0];
+    sc->st0 = out[0];
     sc->scale = scale;
+    sc->rtol2 = rtol * rtol;
+    sc->idone = (rtol > 0.f && !(out[0] > 0.f)) ? 1u : 0u;
   }
 }
 
@@ -464,7 +475,7 @@ __global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __r
                                     const SD* __restrict__ d, float* __restrict__ w, const float* __restrict__ dinv,
                                     const float* __restrict__ dw_part, double* partials, InnerScalars* sc,
                                     const CgScalars* outer) {
-  if (outer != nullptr && ((volatile const CgScalars*)outer)->done) return;
+  if (inner_stopped(outer, sc)) return;
   // d . A d from the operator's per-CTA partials, summed in the same fixed
   // order by every CTA; alpha = s . t / d . A d
   __shared__ float sh_red[32];
@@ -522,13 +533,16 @@ __global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __r
     sc->beta = beta;
     sc->beta_f = (float)beta;
     sc->st = out[0];
+    sc->iters += 1ull;
+    const float r2 = ((volatile InnerScalars*)sc)->rtol2;
+    if (r2 > 0.f && (double)out[0] <= (double)r2 * ((volatile InnerScalars*)sc)->st0) sc->idone = 1u;
   }
 }
 
 template <typename SD>
 __global__ void inner_dupdate_kernel(int64_t N, const float* __restrict__ t, SD* __restrict__ d,
                                      const InnerScalars* sc, const CgScalars* outer) {
-  if (outer != nullptr && ((volatile const CgScalars*)outer)->done) return;
+  if (inner_stopped(outer, sc)) return;
   const float beta = ((volatile const InnerScalars*)sc)->beta_f;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
@@ -748,13 +762,13 @@ void launch_lo_convert(const ModelView& m, int n_blk, const uint16_t* lconn, int
 size_t lo_record_bytes(int half_geo) { return half_geo ? sizeof(LoRecH) : sizeof(LoRecF); }
 void launch_inner_init(int64_t N, const double* r, const float* dinv32, float* s, float* y, float* t, void* d,
                        int half_vec, float* w, double* partials, InnerScalars* sc, const CgScalars* cg,
-                       cudaStream_t st) {
+                       cudaStream_t st, float rtol) {
   if (half_vec)
     inner_init_kernel<__half><<<node_blocks(N), kNodeThreads, 0, st>>>(N, r, dinv32, s, y, t, (__half*)d, w,
-                                                                       partials, sc, cg);
+                                                                       partials, sc, cg, rtol);
   else
     inner_init_kernel<float><<<node_blocks(N), kNodeThreads, 0, st>>>(N, r, dinv32, s, y, t, (float*)d, w,
-                                                                      partials, sc, cg);
+                                                                      partials, sc, cg, rtol);
 }
 
 // ---- software-pipelined variant ----------------------------------------------
@@ -792,7 +806,7 @@ __global__ void __launch_bounds__(kLoBlock, 2) ebe_lo_pipe_kernel(LoView<SG> m, 
                                                                    float* __restrict__ w, double* partials,
                                                                    InnerScalars* sc, const CgScalars* outer,
                                                                    int n_pipe) {
-  if (outer != nullptr && ((volatile const CgScalars*)outer)->done) return;
+  if (inner_stopped(outer, sc)) return;
   typedef typename LoRec<SG>::type Rec;
   constexpr int RW = LoRec<SG>::words;
   constexpr int NB = (int)sizeof(SD) * 4;  // bytes per node of the padded search direction
@@ -1034,7 +1048,7 @@ __global__ void __launch_bounds__(kWsThreads, 2) ebe_lo_ws_kernel(LoView<SG> m, 
                                                                  float* __restrict__ w, double* partials,
                                                                  InnerScalars* sc, const CgScalars* outer,
                                                                  int n_ws) {
-  if (outer != nullptr && ((volatile const CgScalars*)outer)->done) return;
+  if (inner_stopped(outer, sc)) return;
   typedef typename LoRec<SG>::type Rec;
   constexpr int RW = LoRec<SG>::words;
   constexpr int NB = (int)sizeof(SD) * 4;  // bytes per node of the padded search direction

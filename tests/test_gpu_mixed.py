@@ -138,3 +138,18 @@ def test_inner_variants_agree_mid_size(ctx):
         states[v] = m.get_state()[0]
     assert _relerr(states[3], states[1]) <= 1e-6
     m.free()
+
+
+def test_inner_relative_tolerance(ctx):
+    """An inner solve that stops at a relative tolerance still drives the FP64 outer iteration to
+    1e-8 (same waveforms as the oracle), and stops early: fewer executed inner iterations than the
+    cap allows."""
+    from paper_2404_17754_gb300 import gsw
+
+    cfg = configs.config1(n_steps=40)
+    ref = newmark.analysis(cfg, tol=1e-8)
+    wave, stats, m = gsw.analysis(ctx, cfg, tol=1e-8, precision=1, inner_iters=60, inner_rtol=1e-2)
+    assert _relerr(wave, ref["wave"]) <= 1e-6
+    assert stats["relres_last"] <= 1e-8
+    assert 0 < stats["inner_iters_total"] < 60 * stats["cg_iters_total"]
+    m.free()
