@@ -75,6 +75,7 @@ struct Model {
   void* d_lo = nullptr;
   InnerScalars* isc = nullptr;
   float* dw_part = nullptr;    // per-CTA partial sums of the inner operator's d . A d
+  float4* matf = nullptr;      // FP32 material coefficients of the inner operator
   unsigned long long iters_mark = 0;   // device inner-iteration counter when timing started
   unsigned long long iters_reset = 0;  // device inner-iteration counter at the last reset
   int lo_variant = 0;          // launch variant of the inner operator (autotuned)
@@ -480,6 +481,7 @@ gsw_status build_lo(gsw_ctx* ctx, Model* m, int half) {
     TRY(alloc_into(ctx, m, &m->w32, n3 + 4));  // + the dummy node's row
     TRY(alloc_into(ctx, m, &m->isc, 1));
     TRY(alloc_into(ctx, m, &m->dw_part, (size_t)m->n_blk + (size_t)((m->F + kLoBlock - 1) / kLoBlock) + 1));
+    TRY(alloc_into(ctx, m, &m->matf, (size_t)kMaxMat));
     CK(cudaMemsetAsync(m->isc, 0, sizeof(InnerScalars), s));
     m->lo_ready = true;
     m->geo_lo = nullptr;
@@ -493,11 +495,14 @@ gsw_status build_lo(gsw_ctx* ctx, Model* m, int half) {
     m->lo_half = half;
   }
   launch_lo_convert(mv, m->n_blk, m->lconn, half, m->geo_lo, m->fgeo32, m->dinv, m->dinv32, m->partials, m->isc,
-                    s);
+                    m->matf, m->n_mat, s);
   CK(cudaGetLastError());
   BlockView bv = {m->n_blk, m->max_local, m->blk_ptr, m->blk_nodes};
-  m->lo_f = LoView<float>{m->N, m->E, m->F, m->n_mat, bv, m->geo_lo, m->mat, m->fnode, m->fgeo32, m->dt, m->dw_part};
-  m->lo_h = LoView<__half>{m->N, m->E, m->F, m->n_mat, bv, m->geo_lo, m->mat, m->fnode, m->fgeo32, m->dt, m->dw_part};
+  const float face_c = (float)(2.0 / m->dt / 180.0);
+  m->lo_f = LoView<float>{m->N, m->E, m->F, m->n_mat, bv, m->geo_lo, m->matf, m->fnode, m->fgeo32, m->dt,
+                          m->dw_part, face_c};
+  m->lo_h = LoView<__half>{m->N, m->E, m->F, m->n_mat, bv, m->geo_lo, m->matf, m->fnode, m->fgeo32, m->dt,
+                           m->dw_part, face_c};
   m->live_tune = (m->opts.inner_variant < 0);
   return autotune_lo(ctx, m);
 }

@@ -127,11 +127,12 @@ struct LoView {
   int n_mat;
   BlockView blk;
   const void* rec;          // [n_blk * kLoBlock] packed element records (operator order)
-  const MatCoef* mat;
+  const float4* matf;       // [n_mat] (cK lam / 20, cK mu / 20, cM rho / 420, 0) in FP32
   const int32_t* fnode;     // [6][F]
   const float* fgeo;        // [6][F]
   double dt;
   float* dw_part;           // [operator grid] per-CTA partial sums of d . A d
+  float face_c;             // (2 / dt) / 180: dashpot face-mass scale
 };
 
 enum EbeMode { kModeA = 0, kModeK = 1, kModeM = 2, kModeC = 3, kModeRhs = 4, kModeRes = 5 };
@@ -190,7 +191,7 @@ void launch_block_mark(const ModelView& m, BlockView b, int32_t* nodes, int32_t*
                        int total, cudaStream_t s);
 void launch_lo_convert(const ModelView& m, int n_blk, const uint16_t* lconn, int half_geo, void* rec,
                        float* fgeo32, const double* dinv, float* dinv32, double* partials, InnerScalars* sc,
-                       cudaStream_t s);
+                       float4* matf, int n_mat, cudaStream_t s);
 size_t lo_record_bytes(int half_geo);
 // inner solve: half_vec selects __half storage of the search direction d
 // (padded to 4 entries per node)

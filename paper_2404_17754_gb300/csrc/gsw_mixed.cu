@@ -287,10 +287,10 @@ __global__ void __launch_bounds__(kLoBlock, MINB) ebe_lo_kernel(LoView<SG> m, co
   extern __shared__ float sm[];
   __shared__ float matc[kMaxMat][3];
   if (threadIdx.x < m.n_mat) {
-    const MatCoef& c = m.mat[threadIdx.x];
-    matc[threadIdx.x][0] = (float)(c.cK * c.lam / 20.0);
-    matc[threadIdx.x][1] = (float)(c.cK * c.mu / 20.0);
-    matc[threadIdx.x][2] = (float)(c.cM * c.rho / 420.0);
+    const float4 c = m.matf[threadIdx.x];
+    matc[threadIdx.x][0] = c.x;
+    matc[threadIdx.x][1] = c.y;
+    matc[threadIdx.x][2] = c.z;
   }
   float dot = 0.f;
   const int b = blockIdx.x;
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(kLoBlock, MINB) ebe_lo_kernel(LoView<SG> m, co
     // absorbing faces: (2/dt) C_abs d
     const int64_t fc = (int64_t)(b - m.blk.n_blk) * kLoBlock + threadIdx.x;
     if (fc < m.F && m.fgeo[5 * m.F + fc] > 0.5f) {
-      const float sc2 = (float)(2.0 / m.dt) / 180.f;
+      const float sc2 = m.face_c;
       const float As = sc2 * m.fgeo[fc], Ad = sc2 * m.fgeo[m.F + fc];
       const float n[3] = {m.fgeo[2 * m.F + fc], m.fgeo[3 * m.F + fc], m.fgeo[4 * m.F + fc]};
       int64_t nd[6];
@@ -746,9 +746,21 @@ void launch_block_mark(const ModelView& m, BlockView b, int32_t* nodes, int32_t*
   (void)b;
   block_mark_kernel<<<(total + 255) / 256, 256, 0, s>>>(total, nodes, refcount);
 }
+// FP32 material coefficients of the reduced-precision operator (computed once
+// per model so that the operator kernels do no FP64 arithmetic).
+__global__ void lo_material_kernel(const MatCoef* mat, int n_mat, float4* matf) {
+  const int i = threadIdx.x;
+  if (i < n_mat) {
+    const MatCoef& c = mat[i];
+    matf[i] = make_float4((float)(c.cK * c.lam / 20.0), (float)(c.cK * c.mu / 20.0), (float)(c.cM * c.rho / 420.0),
+                          0.f);
+  }
+}
+
 void launch_lo_convert(const ModelView& m, int n_blk, const uint16_t* lconn, int half_geo, void* rec,
                        float* fgeo32, const double* dinv, float* dinv32, double* partials, InnerScalars* sc,
-                       cudaStream_t s) {
+                       float4* matf, int n_mat, cudaStream_t s) {
+  lo_material_kernel<<<1, kMaxMat, 0, s>>>(m.mat, n_mat, matf);
   int64_t n = (int64_t)n_blk * kLoBlock;
   if (6 * m.F > n) n = 6 * m.F;
   if (6 * m.N > n) n = 6 * m.N;
@@ -818,10 +830,10 @@ __global__ void __launch_bounds__(kLoBlock, 2) ebe_lo_pipe_kernel(LoView<SG> m, 
   float* ys = reinterpret_cast<float*>(xr + (size_t)2 * ML * NB);
   __shared__ float matc[kMaxMat][3];
   if (threadIdx.x < m.n_mat) {
-    const MatCoef& c = m.mat[threadIdx.x];
-    matc[threadIdx.x][0] = (float)(c.cK * c.lam / 20.0);
-    matc[threadIdx.x][1] = (float)(c.cK * c.mu / 20.0);
-    matc[threadIdx.x][2] = (float)(c.cM * c.rho / 420.0);
+    const float4 c = m.matf[threadIdx.x];
+    matc[threadIdx.x][0] = c.x;
+    matc[threadIdx.x][1] = c.y;
+    matc[threadIdx.x][2] = c.z;
   }
   for (int q = threadIdx.x; q < 3 * ML; q += kLoBlock) ys[q] = 0.f;
   float dot = 0.f;
@@ -923,7 +935,7 @@ __global__ void __launch_bounds__(kLoBlock, 2) ebe_lo_pipe_kernel(LoView<SG> m, 
     // absorbing faces: (2/dt) C_abs d
     const int64_t fc = (int64_t)(blockIdx.x - n_pipe) * kLoBlock + threadIdx.x;
     if (fc < m.F && m.fgeo[5 * m.F + fc] > 0.5f) {
-      const float sc2 = (float)(2.0 / m.dt) / 180.f;
+      const float sc2 = m.face_c;
       const float As = sc2 * m.fgeo[fc], Ad = sc2 * m.fgeo[m.F + fc];
       const float n[3] = {m.fgeo[2 * m.F + fc], m.fgeo[3 * m.F + fc], m.fgeo[4 * m.F + fc]};
       int64_t nd[6];
@@ -1065,10 +1077,10 @@ __global__ void __launch_bounds__(kWsThreads, 2) ebe_lo_ws_kernel(LoView<SG> m, 
   __shared__ float matc[kMaxMat][3];
   const int tid = threadIdx.x;
   if (tid < m.n_mat) {
-    const MatCoef& c = m.mat[tid];
-    matc[tid][0] = (float)(c.cK * c.lam / 20.0);
-    matc[tid][1] = (float)(c.cK * c.mu / 20.0);
-    matc[tid][2] = (float)(c.cM * c.rho / 420.0);
+    const float4 c = m.matf[tid];
+    matc[tid][0] = c.x;
+    matc[tid][1] = c.y;
+    matc[tid][2] = c.z;
   }
   if (tid == 0) {
     for (int st = 0; st < kWsStages; ++st) {
@@ -1218,7 +1230,7 @@ __global__ void __launch_bounds__(kWsThreads, 2) ebe_lo_ws_kernel(LoView<SG> m, 
     // absorbing faces: (2/dt) C_abs d
     const int64_t fc = (int64_t)(b0 - n_ws) * kWsThreads + tid;
     if (fc < m.F && m.fgeo[5 * m.F + fc] > 0.5f) {
-      const float sc2 = (float)(2.0 / m.dt) / 180.f;
+      const float sc2 = m.face_c;
       const float As = sc2 * m.fgeo[fc], Ad = sc2 * m.fgeo[m.F + fc];
       const float n[3] = {m.fgeo[2 * m.F + fc], m.fgeo[3 * m.F + fc], m.fgeo[4 * m.F + fc]};
       int64_t nd[6];
