@@ -215,7 +215,6 @@ def run_candidates(args, rank, world, dist):
         dist.barrier()
     n_total = args.warmup + args.steps
     prec = {"fp64": 0, "fp32": 1, "fp16": 2}[args.precision]
-    assert prec != 0, "the batched path runs the mixed-precision solver"
     ctx = gsw.Context(local)
     models, dof = [], 0
     for l in range(args.models):
@@ -226,10 +225,20 @@ def run_candidates(args, rank, world, dist):
         m.set_solver(tol=args.tol, precision=prec, inner_iters=args.inner, batch_outer=8, inner_rtol=args.inner_rtol)
         models.append(m)
         dof += 3 * cfg["mesh"]["xyz"].shape[0]
-    batch = ctx.batch(models)
-    batch.step(args.warmup)
+    # the plain FP64 form advances the candidates one after another (host-driven
+    # block-Jacobi PCG); the mixed form advances them together in one graph per step
+    batch = ctx.batch(models) if prec != 0 else None
+
+    def advance(n):
+        if batch is not None:
+            batch.step(n)
+        else:
+            for m in models:
+                m.step(n)
+
+    advance(args.warmup)
     it0 = sum(m.stats()["cg_iters_total"] for m in models)
-    stream = batch_stream = ctx.stream
+    stream = ctx.stream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     clocks.start()
@@ -237,7 +246,7 @@ def run_candidates(args, rank, world, dist):
         dist.barrier()
     torch.cuda.synchronize()
     e0.record(stream)
-    batch.step(args.steps)
+    advance(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
     if dist is not None:
@@ -246,7 +255,8 @@ def run_candidates(args, rank, world, dist):
     t = e0.elapsed_time(e1) / 1e3
     t_max = shard.max_over_ranks(t, dist)
     iters = sum(m.stats()["cg_iters_total"] for m in models) - it0
-    lps = batch.launches_per_step()
+    lps = batch.launches_per_step() if batch is not None else sum(m.stats()["kernel_launches"] for m in models) // max(
+        1, n_total)
     if rank == 0:
         per_step = t_max / args.steps
         # one candidate analysis = 3 directional runs of 2000 steps (+ a misfit, negligible)
@@ -255,16 +265,19 @@ def run_candidates(args, rank, world, dist):
             "metric": "candidate analyses/hour", "value": cah, "unit": "candidate analyses/h", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64+%s" % {"fp32": "f32", "fp16": "f16/f32"}[args.precision], "data": "synthetic",
+            "dtype": "f64" if prec == 0 else "f64+%s" % {"fp32": "f32", "fp16": "f16/f32"}[args.precision],
+            "data": "synthetic",
             "config": {"workload": "%d mixed-ensemble candidates (120x120x300 m, 287,451 DOF each), one directional "
-                                   "analysis each, batched" % args.models,
+                                   "analysis each, %s" % (args.models, "batched" if batch is not None else
+                                                          "one after another (plain FP64 form)"),
                        "dof_total": dof, "dof_steps_per_s": world * dof * args.steps / t_max, "tol": args.tol,
                        "precision": args.precision, "inner_iters": args.inner,
                        "outer_iters_per_model_step": iters / (args.steps * args.models),
                        "graph_kernel_nodes_per_step": lps,
                        "l2": "inputs larger than L2 (%.1f GB resident)" % (sum(m.info()["device_bytes"] for m in models) / 1e9)},
             "gpu_launches": lps * args.steps, "clocks": clk}))
-    batch.close()
+    if batch is not None:
+        batch.close()
     ctx.close()
 
 

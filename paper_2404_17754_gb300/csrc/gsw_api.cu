@@ -665,7 +665,7 @@ int64_t inner_solve(Model* m, cudaStream_t s) {
       m->version += 1;  // a captured batch graph must pick up the choice
     }
   }
-  return 1 + 3 * (int64_t)it - 1;
+  return 1 + 4 * (int64_t)it - 1;
 }
 
 // One Newmark step with flexible CG (FP64) preconditioned by the inner solve.
@@ -802,7 +802,7 @@ int64_t issue_device_step(Model* m, cudaStream_t s, StepState* ss, int outer) {
   ModelView mv = m->view();
   Drive dr{m->p_dev, ss};
   const int it = m->opts.inner_iters > 0 ? m->opts.inner_iters : 1;
-  const int64_t inner_launches = 1 + 3 * (int64_t)it - 1;
+  const int64_t inner_launches = 1 + 4 * (int64_t)it - 1;
   int64_t n = 0;
   launch_step_begin(ss, m->cg, s);
   cudaMemsetAsync(m->w32, 0, sizeof(float) * 3 * (size_t)m->N, s);

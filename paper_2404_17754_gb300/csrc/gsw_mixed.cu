@@ -470,60 +470,136 @@ __global__ void inner_init_kernel(int64_t N, const double* __restrict__ r, const
   }
 }
 
+// Node quads: thread g owns nodes 4g .. 4g+3, whose 3-vectors (12 floats),
+// D^-1 blocks (24 floats) and padded direction entries (16 values) are whole
+// 16-byte words; the N mod 4 trailing nodes go to thread N/4.
+template <int K>
+__device__ __forceinline__ void ldq(const float* p, float (&v)[4 * K]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float4 a = q[k];
+    v[4 * k] = a.x;
+    v[4 * k + 1] = a.y;
+    v[4 * k + 2] = a.z;
+    v[4 * k + 3] = a.w;
+  }
+}
+template <int K>
+__device__ __forceinline__ void stq(float* p, const float (&v)[4 * K]) {
+  float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+  for (int k = 0; k < K; ++k) q[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+}
+__device__ __forceinline__ void ld_dir(const float* p, float (&v)[16]) { ldq<4>(p, v); }
+__device__ __forceinline__ void ld_dir(const __half* p, float (&v)[16]) {
+  const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const uint4 a = q[k];
+    const unsigned u[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const __half2 x = *reinterpret_cast<const __half2*>(&u[h]);
+      v[8 * k + 2 * h] = __low2float(x);
+      v[8 * k + 2 * h + 1] = __high2float(x);
+    }
+  }
+}
+__device__ __forceinline__ void st_dir(float* p, const float (&v)[16]) { stq<4>(p, v); }
+__device__ __forceinline__ void st_dir(__half* p, const float (&v)[16]) {
+  uint4* q = reinterpret_cast<uint4*>(p);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    unsigned u[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const __half2 x = __floats2half2_rn(v[8 * k + 2 * h], v[8 * k + 2 * h + 1]);
+      u[h] = *reinterpret_cast<const unsigned*>(&x);
+    }
+    q[k] = make_uint4(u[0], u[1], u[2], u[3]);
+  }
+}
+
+// alpha = s . t / d . A d from the operator's per-CTA partials (one CTA,
+// fixed summation order).
+__global__ void inner_alpha_kernel(const float* __restrict__ dw_part, InnerScalars* sc, const CgScalars* outer) {
+  if (inner_stopped(outer, sc)) return;
+  __shared__ float sh_red[32];
+  const unsigned int G = ((volatile const InnerScalars*)sc)->n_dw, B = blockDim.x;
+  float a[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a[j] = 0.f;
+  unsigned int i = threadIdx.x;
+  for (; i + 7 * B < G; i += 8 * B) {
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __ldcg(dw_part + i + j * B);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] += v[j];
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    if (i + j * B < G) a[j] += __ldcg(dw_part + i + j * B);
+  const float dw = block_sum_f(((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])), sh_red);
+  if (threadIdx.x == 0) {
+    const double st = ((volatile InnerScalars*)sc)->st;
+    sc->dw = dw;
+    sc->alpha_f = (dw != 0.f) ? (float)(st / (double)dw) : 0.f;
+  }
+}
+
+// y += alpha d, s -= alpha w, t = D^-1 s, w = 0, partial s . t; the last
+// block forms beta and tests the relative stopping factor.
 template <typename SD>
 __global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __restrict__ s, float* __restrict__ t,
                                     const SD* __restrict__ d, float* __restrict__ w, const float* __restrict__ dinv,
-                                    const float* __restrict__ dw_part, double* partials, InnerScalars* sc,
-                                    const CgScalars* outer) {
+                                    double* partials, InnerScalars* sc, const CgScalars* outer) {
   if (inner_stopped(outer, sc)) return;
-  // d . A d from the operator's per-CTA partials, summed in the same fixed
-  // order by every CTA; alpha = s . t / d . A d
-  __shared__ float sh_red[32];
-  __shared__ float alpha_s;
-  {
-    const unsigned int G = ((volatile const InnerScalars*)sc)->n_dw, B = blockDim.x;
-    float a[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) a[j] = 0.f;
-    unsigned int i = threadIdx.x;
-    for (; i + 7 * B < G; i += 8 * B) {
-      float v[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = __ldcg(dw_part + i + j * B);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) a[j] += v[j];
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-      if (i + j * B < G) a[j] += __ldcg(dw_part + i + j * B);
-    const float dw = block_sum_f(((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])), sh_red);
-    if (threadIdx.x == 0) {
-      const double st_old = ((volatile InnerScalars*)sc)->st;
-      alpha_s = (dw != 0.f) ? (float)(st_old / (double)dw) : 0.f;
-      if (blockIdx.x == 0) {
-        sc->dw = dw;
-        sc->alpha_f = alpha_s;
-      }
-    }
-    __syncthreads();
-  }
-  const float alpha = alpha_s;
+  const float alpha = ((volatile const InnerScalars*)sc)->alpha_f;
   float st = 0.f;
-  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
-    float sn[3], tn[3];
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t G4 = N >> 2;
+  if (g < G4) {
+    float yv[12], sv[12], wv[12], tv[12], dv[16], Dv[24];
+    ldq<3>(y + 12 * g, yv);
+    ldq<3>(s + 12 * g, sv);
+    ldq<3>(w + 12 * g, wv);
+    ld_dir(d + 16 * g, dv);
+    ldq<6>(dinv + 24 * g, Dv);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const int64_t k = 3 * n + i;
-      y[k] = fmaf(alpha, to_f(d[4 * n + i]), y[k]);
-      sn[i] = fmaf(-alpha, w[k], s[k]);
-      s[k] = sn[i];
-      w[k] = 0.f;
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        yv[3 * q + i] = fmaf(alpha, dv[4 * q + i], yv[3 * q + i]);
+        sv[3 * q + i] = fmaf(-alpha, wv[3 * q + i], sv[3 * q + i]);
+      }
+      dinv_apply_f(Dv + 6 * q, sv + 3 * q, tv + 3 * q);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) st = fmaf(sv[3 * q + i], tv[3 * q + i], st);
     }
-    dinv_apply_f(dinv + 6 * n, sn, tn);
+    const float zero[12] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    stq<3>(y + 12 * g, yv);
+    stq<3>(s + 12 * g, sv);
+    stq<3>(t + 12 * g, tv);
+    stq<3>(w + 12 * g, zero);
+  } else if (g == G4) {
+    for (int64_t n = 4 * G4; n < N; ++n) {
+      float sn[3], tn[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      t[3 * n + i] = tn[i];
-      st = fmaf(sn[i], tn[i], st);
+      for (int i = 0; i < 3; ++i) {
+        const int64_t k = 3 * n + i;
+        y[k] = fmaf(alpha, to_f(d[4 * n + i]), y[k]);
+        sn[i] = fmaf(-alpha, w[k], s[k]);
+        s[k] = sn[i];
+        w[k] = 0.f;
+      }
+      dinv_apply_f(dinv + 6 * n, sn, tn);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        t[3 * n + i] = tn[i];
+        st = fmaf(sn[i], tn[i], st);
+      }
     }
   }
   float vals[1] = {st}, out[1];
@@ -539,14 +615,27 @@ __global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __r
   }
 }
 
+// d = t + beta d (the padding entry of each node stays 0).
 template <typename SD>
 __global__ void inner_dupdate_kernel(int64_t N, const float* __restrict__ t, SD* __restrict__ d,
                                      const InnerScalars* sc, const CgScalars* outer) {
   if (inner_stopped(outer, sc)) return;
   const float beta = ((volatile const InnerScalars*)sc)->beta_f;
-  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t G4 = N >> 2;
+  if (g < G4) {
+    float tv[12], dv[16];
+    ldq<3>(t + 12 * g, tv);
+    ld_dir(d + 16 * g, dv);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) d[4 * n + i] = from_f<SD>(fmaf(beta, to_f(d[4 * n + i]), t[3 * n + i]));
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) dv[4 * q + i] = fmaf(beta, dv[4 * q + i], tv[3 * q + i]);
+    st_dir(d + 16 * g, dv);
+  } else if (g == G4) {
+    for (int64_t n = 4 * G4; n < N; ++n)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) d[4 * n + i] = from_f<SD>(fmaf(beta, to_f(d[4 * n + i]), t[3 * n + i]));
   }
 }
 
@@ -1331,22 +1420,24 @@ void launch_ebe_lo(int half_geo, int half_vec, const void* lo_view, const void* 
       ebe_lo_launch<float, float>(variant, m, (const float*)d, w, partials, sc, st, outer);
   }
 }
+static unsigned quad_blocks(int64_t N) { return (unsigned)(((N >> 2) + 1 + kNodeThreads - 1) / kNodeThreads); }
 void launch_inner_update(int64_t N, float* y, float* s, float* t, const void* d, int half_vec, float* w,
                          const float* dinv32, const float* dw_part, double* partials, InnerScalars* sc,
                          cudaStream_t st, const CgScalars* outer) {
+  inner_alpha_kernel<<<1, 1024, 0, st>>>(dw_part, sc, outer);
   if (half_vec)
-    inner_update_kernel<__half><<<node_blocks(N), kNodeThreads, 0, st>>>(N, y, s, t, (const __half*)d, w, dinv32,
-                                                                         dw_part, partials, sc, outer);
+    inner_update_kernel<__half><<<quad_blocks(N), kNodeThreads, 0, st>>>(N, y, s, t, (const __half*)d, w, dinv32,
+                                                                         partials, sc, outer);
   else
-    inner_update_kernel<float><<<node_blocks(N), kNodeThreads, 0, st>>>(N, y, s, t, (const float*)d, w, dinv32,
-                                                                        dw_part, partials, sc, outer);
+    inner_update_kernel<float><<<quad_blocks(N), kNodeThreads, 0, st>>>(N, y, s, t, (const float*)d, w, dinv32,
+                                                                        partials, sc, outer);
 }
 void launch_inner_dupdate(int64_t N, const float* t, void* d, int half_vec, const InnerScalars* sc,
                           cudaStream_t st, const CgScalars* outer) {
   if (half_vec)
-    inner_dupdate_kernel<__half><<<node_blocks(N), kNodeThreads, 0, st>>>(N, t, (__half*)d, sc, outer);
+    inner_dupdate_kernel<__half><<<quad_blocks(N), kNodeThreads, 0, st>>>(N, t, (__half*)d, sc, outer);
   else
-    inner_dupdate_kernel<float><<<node_blocks(N), kNodeThreads, 0, st>>>(N, t, (float*)d, sc, outer);
+    inner_dupdate_kernel<float><<<quad_blocks(N), kNodeThreads, 0, st>>>(N, t, (float*)d, sc, outer);
 }
 void launch_fcg_residual(const ModelView& m, const double* b, double* q, double* r, double* partials, CgScalars* cg,
                          cudaStream_t s) {
