@@ -75,7 +75,8 @@ struct Model {
   void* d_lo = nullptr;
   InnerScalars* isc = nullptr;
   float* dw_part = nullptr;    // per-CTA partial sums of the inner operator's d . A d
-  float4* matf = nullptr;      // FP32 material coefficients of the inner operator
+  float4* matf = nullptr;      // FP32 material coefficients of the inner operator and the FP32 RHS
+  float4* uva = nullptr;       // FP32 copy of u, v, a ([N + 1][3] words) for the FP32 RHS
   unsigned long long iters_mark = 0;   // device inner-iteration counter when timing started
   unsigned long long iters_reset = 0;  // device inner-iteration counter at the last reset
   int lo_variant = 0;          // launch variant of the inner operator (autotuned)
@@ -481,7 +482,9 @@ gsw_status build_lo(gsw_ctx* ctx, Model* m, int half) {
     TRY(alloc_into(ctx, m, &m->w32, n3 + 4));  // + the dummy node's row
     TRY(alloc_into(ctx, m, &m->isc, 1));
     TRY(alloc_into(ctx, m, &m->dw_part, (size_t)m->n_blk + (size_t)((m->F + kLoBlock - 1) / kLoBlock) + 1));
-    TRY(alloc_into(ctx, m, &m->matf, (size_t)kMaxMat));
+    TRY(alloc_into(ctx, m, &m->matf, (size_t)3 * kMaxMat));
+    TRY(alloc_into(ctx, m, &m->uva, 3 * ((size_t)m->N + 1)));
+    CK(cudaMemsetAsync(m->uva, 0, sizeof(float4) * 3 * ((size_t)m->N + 1), s));
     CK(cudaMemsetAsync(m->isc, 0, sizeof(InnerScalars), s));
     m->lo_ready = true;
     m->geo_lo = nullptr;
@@ -675,7 +678,8 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
   const double force = 2.0 * m->input[(size_t)m->step];
   // ||b|| from an FP32 right-hand side (w32 is free scratch between solves)
   CK(cudaMemsetAsync(m->w32, 0, sizeof(float) * 3 * (size_t)m->N, s));
-  launch_rhs_f32(mv, m->u, m->v, m->a, m->w32, force, m->dir, s);
+  launch_rhs_lo(m->lo_half, m->lo_half ? (const void*)&m->lo_h : (const void*)&m->lo_f, m->N, m->u, m->v, m->a,
+                m->uva, m->w32, force, m->dir, s);
   CgScalars init = {};
   init.tol = m->opts.tol;
   init.max_iter = m->opts.max_iter;
@@ -806,7 +810,8 @@ int64_t issue_device_step(Model* m, cudaStream_t s, StepState* ss, int outer) {
   int64_t n = 0;
   launch_step_begin(ss, m->cg, s);
   cudaMemsetAsync(m->w32, 0, sizeof(float) * 3 * (size_t)m->N, s);
-  launch_rhs_f32(mv, m->u, m->v, m->a, m->w32, 0.0, m->dir, s, dr);
+  launch_rhs_lo(m->lo_half, m->lo_half ? (const void*)&m->lo_h : (const void*)&m->lo_f, m->N, m->u, m->v, m->a,
+                m->uva, m->w32, 0.0, m->dir, s, dr);
   launch_cg_init_mixed(mv, m->w32, m->u, m->v, m->a, m->x, m->p, m->z, m->b, m->r, m->q, m->partials, m->cg, s, ss);
   launch_ebe(kModeRes, mv, m->p, m->z, m->b, m->r, 0.0, m->dir, nullptr, m->cg, s, dr);
   launch_cg_rnorm(mv, m->r, m->partials, m->cg, s);

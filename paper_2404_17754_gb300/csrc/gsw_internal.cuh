@@ -155,8 +155,10 @@ void launch_ebe(int mode, const ModelView& m, const double* x, const double* v, 
                 cudaStream_t s, Drive dr = Drive{nullptr, nullptr});
 void launch_cg_init(const ModelView& m, const double* b, const double* v, const double* a,
                     double* x, double* q, double* partials, CgScalars* cg, cudaStream_t s);
-void launch_rhs_f32(const ModelView& m, const double* u, const double* v, const double* a, float* b32,
-                    double force, int dir, cudaStream_t s, Drive dr = Drive{nullptr, nullptr});
+// FP32 right-hand side on the reduced-precision operator's element blocks
+// (uva: [N + 1][3] float4 scratch for the FP32 state; b32 zero on entry).
+void launch_rhs_lo(int half_geo, const void* lo_view, int64_t N, const double* u, const double* v, const double* a,
+                   float4* uva, float* b32, double force, int dir, cudaStream_t st, Drive dr = Drive{nullptr, nullptr});
 // x0 = x (use_guess) or the predictor dt v + dt^2/2 a; writes u~ = u + x0,
 // v~ = v - (2/dt) x0, a~ = a + (4/dt) v - (4/dt^2) x0 for the one-pass residual
 void launch_cg_init_mixed(const ModelView& m, const float* b32, const double* u, const double* v, const double* a,

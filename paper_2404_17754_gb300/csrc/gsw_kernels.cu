@@ -467,87 +467,6 @@ __global__ void __launch_bounds__(kElemThreads) ebe_kernel(ModelView m, const do
   }
 }
 
-// Right-hand side b = f - K u + C v + M (a + (4/dt) v) in FP32 arithmetic.
-// Only ||b|| is taken from it (the scale of the relative-residual test), so
-// FP32 accuracy suffices; the FP64 solve never uses b itself.
-__global__ void __launch_bounds__(kElemThreads) rhs_f32_kernel(ModelView m, const double* __restrict__ u,
-                                                              const double* __restrict__ vv,
-                                                              const double* __restrict__ aa, float* b,
-                                                              double force, int dir, Drive dr) {
-  if (dr.ss != nullptr) {
-    if (!((volatile StepState*)dr.ss)->active) return;
-    force = 2.0 * dr.p[dr.ss->step];
-  }
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t < m.E) {
-    const int64_t e = t;
-    int64_t nd[10];
-#pragma unroll
-    for (int k = 0; k < 10; ++k) nd[k] = m.conn[k * m.E + e];
-    float g[3][3];
-#pragma unroll
-    for (int mm = 0; mm < 3; ++mm)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) g[mm][i] = (float)m.geo[(3 * mm + i) * m.E + e];
-    const double V = m.geo[9 * m.E + e];
-    const MatCoef mc = m.mat[m.emat[e]];
-    const float lamS = (float)(mc.lam * V / 20.0), muS = (float)(mc.mu * V / 20.0);
-    const float mS = (float)(mc.rho * V / 420.0);
-    float w[10][3], f[10][3];
-#pragma unroll
-    for (int k = 0; k < 10; ++k)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) w[k][i] = (float)fma(mc.beta, vv[3 * nd[k] + i], -u[3 * nd[k] + i]);
-    stiffness_apply<float>(w, g, lamS, muS, f);
-    const double cv = 4.0 / m.dt + mc.alpha;
-#pragma unroll
-    for (int k = 0; k < 10; ++k)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) w[k][i] = (float)fma(cv, vv[3 * nd[k] + i], aa[3 * nd[k] + i]);
-    mass_apply<float>(w, mS, f);
-#pragma unroll
-    for (int k = 0; k < 10; ++k)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) atomicAdd(b + 3 * nd[k] + i, f[k][i]);
-  } else if (t < m.E + m.F) {
-    const int64_t fc = t - m.E;
-    const double tag = m.fgeo[5 * m.F + fc];
-    if (tag > 0.5) {
-      const double As = m.fgeo[fc] / 180.0, Ad = m.fgeo[m.F + fc] / 180.0;
-      const double n[3] = {m.fgeo[2 * m.F + fc], m.fgeo[3 * m.F + fc], m.fgeo[4 * m.F + fc]};
-      int64_t nd[6];
-      float z[6][3];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        nd[k] = m.fnode[k * m.F + fc];
-        const float x0 = (float)vv[3 * nd[k]], x1 = (float)vv[3 * nd[k] + 1], x2 = (float)vv[3 * nd[k] + 2];
-        const float dn = (float)n[0] * x0 + (float)n[1] * x1 + (float)n[2] * x2;
-        z[k][0] = (float)As * x0 + (float)Ad * dn * (float)n[0];
-        z[k][1] = (float)As * x1 + (float)Ad * dn * (float)n[1];
-        z[k][2] = (float)As * x2 + (float)Ad * dn * (float)n[2];
-      }
-      const double nd_ = dir == 0 ? n[0] : (dir == 1 ? n[1] : n[2]);
-      const float fz[3] = {(float)(force * 60.0 * (As * (dir == 0) + Ad * nd_ * n[0])),
-                           (float)(force * 60.0 * (As * (dir == 1) + Ad * nd_ * n[1])),
-                           (float)(force * 60.0 * (As * (dir == 2) + Ad * nd_ * n[2]))};
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const float Zv = z[0][i] + z[1][i] + z[2][i];
-        const float Ze = z[3][i] + z[4][i] + z[5][i];
-        float yf[6];
-        yf[0] = 7.f * z[0][i] - Zv - 4.f * z[4][i];
-        yf[1] = 7.f * z[1][i] - Zv - 4.f * z[5][i];
-        yf[2] = 7.f * z[2][i] - Zv - 4.f * z[3][i];
-        yf[3] = 16.f * (z[3][i] + Ze) - 4.f * z[2][i] + (tag < 1.5 ? fz[i] : 0.f);
-        yf[4] = 16.f * (z[4][i] + Ze) - 4.f * z[0][i] + (tag < 1.5 ? fz[i] : 0.f);
-        yf[5] = 16.f * (z[5][i] + Ze) - 4.f * z[1][i] + (tag < 1.5 ? fz[i] : 0.f);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) atomicAdd(b + 3 * nd[k] + i, yf[k]);
-      }
-    }
-  }
-}
-
 // ------------------------------------------------------------------------------
 // CG vector kernels (node-wise, 3 DOF per thread, grid-stride)
 // ------------------------------------------------------------------------------
@@ -838,11 +757,6 @@ void launch_ebe(int mode, const ModelView& m, const double* x, const double* v, 
 void launch_cg_init(const ModelView& m, const double* b, const double* v, const double* a,
                     double* x, double* q, double* partials, CgScalars* cg, cudaStream_t s) {
   cg_init_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, b, v, a, m.dt, x, q, partials, cg);
-}
-void launch_rhs_f32(const ModelView& m, const double* u, const double* v, const double* a, float* b32,
-                    double force, int dir, cudaStream_t s, Drive dr) {
-  const int nb = ebe_blocks(m);
-  if (nb > 0) rhs_f32_kernel<<<nb, kElemThreads, 0, s>>>(m, u, v, a, b32, force, dir, dr);
 }
 void launch_cg_init_mixed(const ModelView& m, const float* b32, const double* u, const double* v, const double* a,
                           double* x, double* ut, double* vt, double* at, double* r, double* q, double* partials,

@@ -837,19 +837,25 @@ void launch_block_mark(const ModelView& m, BlockView b, int32_t* nodes, int32_t*
 }
 // FP32 material coefficients of the reduced-precision operator (computed once
 // per model so that the operator kernels do no FP64 arithmetic).
-__global__ void lo_material_kernel(const MatCoef* mat, int n_mat, float4* matf) {
+// matf[i]: operator A (cK lam/20, cK mu/20, cM rho/420, 0); matf[kMaxMat + 2i]:
+// right-hand side (lam/20, mu/20, rho/420, beta); matf[kMaxMat + 2i + 1]:
+// (4/dt + alpha, 0, 0, 0).
+__global__ void lo_material_kernel(const MatCoef* mat, int n_mat, double dt, float4* matf) {
   const int i = threadIdx.x;
   if (i < n_mat) {
     const MatCoef& c = mat[i];
     matf[i] = make_float4((float)(c.cK * c.lam / 20.0), (float)(c.cK * c.mu / 20.0), (float)(c.cM * c.rho / 420.0),
                           0.f);
+    matf[kMaxMat + 2 * i] = make_float4((float)(c.lam / 20.0), (float)(c.mu / 20.0), (float)(c.rho / 420.0),
+                                        (float)c.beta);
+    matf[kMaxMat + 2 * i + 1] = make_float4((float)(4.0 / dt + c.alpha), 0.f, 0.f, 0.f);
   }
 }
 
 void launch_lo_convert(const ModelView& m, int n_blk, const uint16_t* lconn, int half_geo, void* rec,
                        float* fgeo32, const double* dinv, float* dinv32, double* partials, InnerScalars* sc,
                        float4* matf, int n_mat, cudaStream_t s) {
-  lo_material_kernel<<<1, kMaxMat, 0, s>>>(m.mat, n_mat, matf);
+  lo_material_kernel<<<1, kMaxMat, 0, s>>>(m.mat, n_mat, m.dt, matf);
   int64_t n = (int64_t)n_blk * kLoBlock;
   if (6 * m.F > n) n = 6 * m.F;
   if (6 * m.N > n) n = 6 * m.N;
@@ -1420,6 +1426,168 @@ void launch_ebe_lo(int half_geo, int half_vec, const void* lo_view, const void* 
       ebe_lo_launch<float, float>(variant, m, (const float*)d, w, partials, sc, st, outer);
   }
 }
+// ------------------------------------------------------------------------------
+// FP32 right-hand side (its norm sets the relative-residual scale)
+// ------------------------------------------------------------------------------
+
+// u, v, a in FP32, one padded 16-byte word each per node: uva[3n + {0, 1, 2}].
+__global__ void uva_f32_kernel(int64_t N, const double* __restrict__ u, const double* __restrict__ v,
+                               const double* __restrict__ a, float4* __restrict__ uva, const StepState* ss) {
+  if (ss != nullptr && !((volatile const StepState*)ss)->active) return;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+    uva[3 * n] = make_float4((float)u[3 * n], (float)u[3 * n + 1], (float)u[3 * n + 2], 0.f);
+    uva[3 * n + 1] = make_float4((float)v[3 * n], (float)v[3 * n + 1], (float)v[3 * n + 2], 0.f);
+    uva[3 * n + 2] = make_float4((float)a[3 * n], (float)a[3 * n + 1], (float)a[3 * n + 2], 0.f);
+  }
+}
+
+// b = f - K u + C v + M (a + 4/dt v) in FP32 on the reduced-precision
+// operator's element blocks (Newmark, the right-hand side of A du = b):
+// element stiffness on beta_e v - u, element mass on a + (4/dt + alpha_e) v,
+// dashpot faces on v plus the base force 2 p C_base e_dir.  Same block
+// assembly as the operator (shared-memory gather and atomics, one write per
+// unique node).  b must be zero on entry.  Only ||b|| is taken from it (the
+// scale of the relative-residual test), so FP32 accuracy suffices; the FP64
+// solve never uses b itself.
+template <typename SG>
+__global__ void __launch_bounds__(kLoBlock, 3) ebe_lo_rhs_kernel(LoView<SG> m, const float4* __restrict__ uva,
+                                                                float* __restrict__ b, float force, int dir,
+                                                                Drive dr) {
+  if (dr.ss != nullptr) {
+    if (!((volatile const StepState*)dr.ss)->active) return;
+    force = 2.f * (float)dr.p[dr.ss->step];
+  }
+  typedef typename LoRec<SG>::type Rec;
+  constexpr int RW = LoRec<SG>::words;
+  extern __shared__ __align__(16) float rhs_sm[];
+  __shared__ float4 mr[2 * kMaxMat];
+  if (threadIdx.x < 2 * m.n_mat) mr[threadIdx.x] = m.matf[kMaxMat + threadIdx.x];
+  const int b0 = blockIdx.x;
+  const int ML = m.blk.max_local;
+  if (b0 < m.blk.n_blk) {
+    float4* xs = reinterpret_cast<float4*>(rhs_sm);  // [ML][3]: u, v, a
+    float* ys = rhs_sm + 12 * ML;
+    union {
+      uint4 v[RW];
+      Rec r;
+    } u;
+    const uint4* rp = reinterpret_cast<const uint4*>(m.rec) + (int64_t)b0 * kLoBlock * RW + threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < RW; ++q) u.v[q] = __ldg(rp + q * kLoBlock);
+    const int64_t n0 = (int64_t)b0 * ML;
+    for (int i = threadIdx.x; i < ML; i += kLoBlock) {
+      const int64_t g = m.blk.nodes[n0 + i] & 0x7fffffff;
+      xs[3 * i] = uva[3 * g];
+      xs[3 * i + 1] = uva[3 * g + 1];
+      xs[3 * i + 2] = uva[3 * g + 2];
+      ys[3 * i] = 0.f;
+      ys[3 * i + 1] = 0.f;
+      ys[3 * i + 2] = 0.f;
+    }
+    __syncthreads();
+    {
+      float g[3][3];
+#pragma unroll
+      for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) g[mm][i] = to_f(u.r.g[3 * mm + i]);
+      const float V = u.r.vol;
+      const float4 c0 = mr[2 * u.r.mat], c1 = mr[2 * u.r.mat + 1];
+      float w[10][3], f[10][3];
+#pragma unroll
+      for (int k = 0; k < 10; ++k) {
+        const float4 uu = xs[3 * u.r.lc[k]], vv = xs[3 * u.r.lc[k] + 1];
+        w[k][0] = fmaf(c0.w, vv.x, -uu.x);
+        w[k][1] = fmaf(c0.w, vv.y, -uu.y);
+        w[k][2] = fmaf(c0.w, vv.z, -uu.z);
+      }
+      stiffness_apply<float>(w, g, c0.x * V, c0.y * V, f);
+#pragma unroll
+      for (int k = 0; k < 10; ++k) {
+        const float4 vv = xs[3 * u.r.lc[k] + 1], aa = xs[3 * u.r.lc[k] + 2];
+        w[k][0] = fmaf(c1.x, vv.x, aa.x);
+        w[k][1] = fmaf(c1.x, vv.y, aa.y);
+        w[k][2] = fmaf(c1.x, vv.z, aa.z);
+      }
+      mass_apply<float>(w, c0.z * V, f);
+#pragma unroll
+      for (int k = 0; k < 10; ++k)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) atomicAdd(ys + 3 * u.r.lc[k] + i, f[k][i]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ML; i += kLoBlock) {
+      const int32_t raw = m.blk.nodes[n0 + i];
+      const int64_t g = raw & 0x7fffffff;
+      if (g == m.N) continue;  // padding entry (dummy node N)
+      if (raw < 0) {
+        b[3 * g] = ys[3 * i];
+        b[3 * g + 1] = ys[3 * i + 1];
+        b[3 * g + 2] = ys[3 * i + 2];
+      } else {
+        atomicAdd(b + 3 * g, ys[3 * i]);
+        atomicAdd(b + 3 * g + 1, ys[3 * i + 1]);
+        atomicAdd(b + 3 * g + 2, ys[3 * i + 2]);
+      }
+    }
+  } else {
+    // dashpot faces: C_abs v (face mass pattern A/180 on rho Vs / rho Vp) and,
+    // on the base, the input force 2 p C_base e_dir (int N_a dA = A/3 at edge
+    // nodes, 0 at vertices)
+    const int64_t fc = (int64_t)(b0 - m.blk.n_blk) * kLoBlock + threadIdx.x;
+    if (fc < m.F && m.fgeo[5 * m.F + fc] > 0.5f) {
+      const float tag = m.fgeo[5 * m.F + fc];
+      const float As = m.fgeo[fc] / 180.f, Ad = m.fgeo[m.F + fc] / 180.f;
+      const float n[3] = {m.fgeo[2 * m.F + fc], m.fgeo[3 * m.F + fc], m.fgeo[4 * m.F + fc]};
+      int64_t nd[6];
+      float z[6][3];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        nd[k] = m.fnode[k * m.F + fc];
+        const float4 vv = uva[3 * nd[k] + 1];
+        const float dn = n[0] * vv.x + n[1] * vv.y + n[2] * vv.z;
+        z[k][0] = fmaf(As, vv.x, Ad * dn * n[0]);
+        z[k][1] = fmaf(As, vv.y, Ad * dn * n[1]);
+        z[k][2] = fmaf(As, vv.z, Ad * dn * n[2]);
+      }
+      const float ndir = dir == 0 ? n[0] : (dir == 1 ? n[1] : n[2]);
+      float fz[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) fz[i] = (tag < 1.5f) ? force * 60.f * (As * (dir == i) + Ad * ndir * n[i]) : 0.f;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const float Zv = z[0][i] + z[1][i] + z[2][i];
+        const float Ze = z[3][i] + z[4][i] + z[5][i];
+        float yf[6];
+        yf[0] = 7.f * z[0][i] - Zv - 4.f * z[4][i];
+        yf[1] = 7.f * z[1][i] - Zv - 4.f * z[5][i];
+        yf[2] = 7.f * z[2][i] - Zv - 4.f * z[3][i];
+        yf[3] = 16.f * (z[3][i] + Ze) - 4.f * z[2][i] + fz[i];
+        yf[4] = 16.f * (z[4][i] + Ze) - 4.f * z[0][i] + fz[i];
+        yf[5] = 16.f * (z[5][i] + Ze) - 4.f * z[1][i] + fz[i];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) atomicAdd(b + 3 * nd[k] + i, yf[k]);
+      }
+    }
+  }
+}
+
+void launch_rhs_lo(int half_geo, const void* lo_view, int64_t N, const double* u, const double* v, const double* a,
+                   float4* uva, float* b32, double force, int dir, cudaStream_t st, Drive dr) {
+  uva_f32_kernel<<<node_blocks(N), kNodeThreads, 0, st>>>(N, u, v, a, uva, dr.ss);
+  if (half_geo) {
+    const LoView<__half>& m = *(const LoView<__half>*)lo_view;
+    const unsigned g = (unsigned)(m.blk.n_blk + (m.F + kLoBlock - 1) / kLoBlock);
+    ebe_lo_rhs_kernel<__half><<<g, kLoBlock, sizeof(float) * 15 * (size_t)m.blk.max_local, st>>>(m, uva, b32,
+                                                                                                 (float)force, dir, dr);
+  } else {
+    const LoView<float>& m = *(const LoView<float>*)lo_view;
+    const unsigned g = (unsigned)(m.blk.n_blk + (m.F + kLoBlock - 1) / kLoBlock);
+    ebe_lo_rhs_kernel<float><<<g, kLoBlock, sizeof(float) * 15 * (size_t)m.blk.max_local, st>>>(m, uva, b32,
+                                                                                                (float)force, dir, dr);
+  }
+}
+
 static unsigned quad_blocks(int64_t N) { return (unsigned)(((N >> 2) + 1 + kNodeThreads - 1) / kNodeThreads); }
 void launch_inner_update(int64_t N, float* y, float* s, float* t, const void* d, int half_vec, float* w,
                          const float* dinv32, const float* dw_part, double* partials, InnerScalars* sc,
