@@ -222,7 +222,8 @@ def run_candidates(args, rank, world, dist):
         m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
         m.set_time(cfg["dt"], n_total, cfg["band"])
         m.set_input(cfg["dir"], cfg["p"])
-        m.set_solver(tol=args.tol, precision=prec, inner_iters=args.inner, batch_outer=8, inner_rtol=args.inner_rtol)
+        m.set_solver(tol=args.tol, precision=prec, inner_iters=args.inner, batch_outer=args.batch_outer,
+                     inner_rtol=args.inner_rtol)
         models.append(m)
         dof += 3 * cfg["mesh"]["xyz"].shape[0]
     # the plain FP64 form advances the candidates one after another (host-driven
@@ -271,7 +272,7 @@ def run_candidates(args, rank, world, dist):
                                    "analysis each, %s" % (args.models, "batched" if batch is not None else
                                                           "one after another (plain FP64 form)"),
                        "dof_total": dof, "dof_steps_per_s": world * dof * args.steps / t_max, "tol": args.tol,
-                       "precision": args.precision, "inner_iters": args.inner,
+                       "precision": args.precision, "inner_iters": args.inner, "batch_outer": args.batch_outer,
                        "outer_iters_per_model_step": iters / (args.steps * args.models),
                        "graph_kernel_nodes_per_step": lps,
                        "l2": "inputs larger than L2 (%.1f GB resident)" % (sum(m.info()["device_bytes"] for m in models) / 1e9)},
@@ -355,6 +356,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16"])
     ap.add_argument("--inner", type=int, default=30, help="inner preconditioner iterations (mixed modes; the cap "
                     "when --inner-rtol > 0)")
+    ap.add_argument("--batch-outer", type=int, default=8,
+                    help="candidates workload: flexible-CG iterations per step in the captured step graph")
     ap.add_argument("--inner-rtol", type=float, default=0.0,
                     help="inner PCG relative stopping factor (0 = always --inner iterations)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -57,7 +57,7 @@ def test_truth_is_selected_from_candidates():
             err, c_est = ctx.misfit(G[c], obs, s, L, tau=1e-10)
             ERR[c, e] = err
             err_o, _ = misfit.estimate(G[c], obs, s, L, tau=1e-10)
-            assert abs(err - err_o) <= 1e-9 * max(err_o, 1e-6)
+            assert abs(err - err_o) <= 1e-9 * max(err_o, 1e-3)  # an exact fit leaves rounding noise (~1e-15)
             if c == truth:
                 np.testing.assert_allclose(c_est, c_true, atol=1e-6 * np.abs(c_true).max())
     best, hist = misfit.select(ERR)
