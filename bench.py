@@ -356,8 +356,9 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16"])
     ap.add_argument("--inner", type=int, default=30, help="inner preconditioner iterations (mixed modes; the cap "
                     "when --inner-rtol > 0)")
-    ap.add_argument("--batch-outer", type=int, default=8,
-                    help="candidates workload: flexible-CG iterations per step in the captured step graph")
+    ap.add_argument("--batch-outer", type=int, default=0,
+                    help="candidates workload: flexible-CG iterations per step in the captured step graph "
+                    "(0 = adaptive)")
     ap.add_argument("--inner-rtol", type=float, default=0.0,
                     help="inner PCG relative stopping factor (0 = always --inner iterations)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

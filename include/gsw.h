@@ -63,9 +63,13 @@ typedef struct {
   int32_t inner_iters;  /* inner preconditioner iterations (mixed modes) */
   int32_t check_every;  /* CG iterations issued between host convergence checks */
   int32_t batch_outer;  /* batched stepping: flexible-CG iterations per step in the
-                           captured step graph (0 = 6); a step that needs more
-                           is completed by the host-driven solver (up to
-                           max_iter) and the model then rejoins the graph */
+                           captured step graph; a step that needs more is
+                           completed by the host-driven solver (up to max_iter)
+                           and the model then rejoins the graph.  0 = adaptive:
+                           the budget starts at 6 and follows the steps (one
+                           more than the most iterations a step of the last
+                           8-step chunk needed; raised at once, lowered after
+                           two lower chunks; the graph is re-captured) */
   int32_t inner_variant; /* launch variant of the inner operator: -1 lets the set-up
                             autotuner time all and keep the fastest; 0, 1 one CTA
                             per element block (3 or 4 CTAs per SM); 2 persistent,

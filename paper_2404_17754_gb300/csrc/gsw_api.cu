@@ -160,6 +160,10 @@ struct Batch {
   StepState* ss_host = nullptr;  // pinned
   int64_t launches_per_step = 0;
   int outer = 0;
+  // adaptive budget (members with batch_outer == 0): outer iterations captured
+  // per step, and the chunks in a row whose steps needed fewer
+  int adapt_outer = 6;
+  int lower_streak = 0, lower_max = 0;
 };
 
 namespace {
@@ -1246,10 +1250,12 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
   const int nm = (int)b->ids.size();
   int outer = 0;
   bool stale = (b->exec == nullptr);
+  bool adaptive = false;
   int remaining = 0;
   for (int i = 0; i < nm; ++i) {
     Model* m = find(ctx, b->ids[i]);
-    const int o = m->opts.batch_outer > 0 ? m->opts.batch_outer : 6;
+    const int o = m->opts.batch_outer > 0 ? m->opts.batch_outer : b->adapt_outer;
+    if (m->opts.batch_outer <= 0) adaptive = true;
     if (o > outer) outer = o;
     if (b->versions[i] != m->version) stale = true;
     StepState& h = b->ss_host[i];
@@ -1267,7 +1273,8 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
   CK(cudaEventRecord(b->fork, ctx->stream));
   CK(cudaStreamWaitEvent(b->origin, b->fork, 0));
   CK(cudaMemcpyAsync(b->ss_dev, b->ss_host, sizeof(StepState) * nm, cudaMemcpyHostToDevice, b->origin));
-  if (stale && remaining > 0) {
+  // (re)capture the step graph with `outer` flexible-CG iterations per member
+  auto capture = [&]() -> gsw_status {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     b->exec = nullptr;
@@ -1288,7 +1295,9 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
     b->launches_per_step = launches;
     b->outer = outer;
     for (int i = 0; i < nm; ++i) b->versions[i] = find(ctx, b->ids[i])->version;
-  }
+    return GSW_OK;
+  };
+  if (stale && remaining > 0) TRY(capture());
   gsw_status st = GSW_OK;
   const int chunk = 8;
   while (remaining > 0) {
@@ -1298,6 +1307,7 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
     CK(cudaStreamSynchronize(b->origin));
     remaining = 0;
     bool rewrite = false;
+    int need = 0;  // most outer iterations a step of this chunk needed
     for (int i = 0; i < nm; ++i) {
       Model* m = find(ctx, b->ids[i]);
       StepState& h = b->ss_host[i];
@@ -1312,7 +1322,8 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
         m->stats.relres_last = h.relres_last;
       }
       if (h.iters_max > m->stats.cg_iters_max) m->stats.cg_iters_max = h.iters_max;
-      h.iters_total = h.inner_total = 0;
+      need = std::max(need, h.iters_max);
+      h.iters_total = h.inner_total = h.iters_max = 0;
       rewrite = true;
       if (h.failed && !m->failed) {
         m->failed = true;
@@ -1335,6 +1346,7 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
         } else {
           h.step = (int)m->step;
           h.needs_host = 0;
+          need = std::max(need, m->stats.cg_iters_last);
         }
         CK(cudaEventRecord(b->fork, ctx->stream));
         CK(cudaStreamWaitEvent(b->origin, b->fork, 0));
@@ -1342,6 +1354,35 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
       if (!m->failed && !h.failed) remaining = std::max(remaining, h.stop_at - h.step);
     }
     if (rewrite) CK(cudaMemcpyAsync(b->ss_dev, b->ss_host, sizeof(StepState) * nm, cudaMemcpyHostToDevice, b->origin));
+    if (adaptive && need > 0 && st == GSW_OK) {
+      // the captured budget follows the steps: one more than the most outer
+      // iterations a step of the chunk needed (2..16); raised at once (steps
+      // beyond it were finished by the host), lowered after two chunks in a
+      // row that needed less
+      const int target = std::min(16, std::max(2, need + 1));
+      int next = b->adapt_outer;
+      if (target > b->adapt_outer) {
+        next = target;
+        b->lower_streak = b->lower_max = 0;
+      } else if (target < b->adapt_outer) {
+        b->lower_max = std::max(b->lower_max, target);
+        if (++b->lower_streak >= 2) {
+          next = b->lower_max;
+          b->lower_streak = b->lower_max = 0;
+        }
+      } else {
+        b->lower_streak = b->lower_max = 0;
+      }
+      if (next != b->adapt_outer) {
+        b->adapt_outer = next;
+        outer = 0;
+        for (int i = 0; i < nm; ++i) {
+          Model* m = find(ctx, b->ids[i]);
+          outer = std::max(outer, m->opts.batch_outer > 0 ? m->opts.batch_outer : b->adapt_outer);
+        }
+        if (outer != b->outer && remaining > 0) TRY(capture());
+      }
+    }
   }
   CK(cudaEventRecord(b->done_ev, b->origin));
   CK(cudaStreamWaitEvent(ctx->stream, b->done_ev, 0));
