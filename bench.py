@@ -239,6 +239,7 @@ def run_candidates(args, rank, world, dist):
 
     advance(args.warmup)
     it0 = sum(m.stats()["cg_iters_total"] for m in models)
+    kl0 = sum(m.stats()["kernel_launches"] for m in models)
     stream = ctx.stream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
@@ -256,8 +257,8 @@ def run_candidates(args, rank, world, dist):
     t = e0.elapsed_time(e1) / 1e3
     t_max = shard.max_over_ranks(t, dist)
     iters = sum(m.stats()["cg_iters_total"] for m in models) - it0
-    lps = batch.launches_per_step() if batch is not None else sum(m.stats()["kernel_launches"] for m in models) // max(
-        1, n_total)
+    kernels = sum(m.stats()["kernel_launches"] for m in models) - kl0  # launched in the timed steps
+    lps = batch.launches_per_step() if batch is not None else kernels // max(1, args.steps)
     if rank == 0:
         per_step = t_max / args.steps
         # one candidate analysis = 3 directional runs of 2000 steps (+ a misfit, negligible)
@@ -274,9 +275,9 @@ def run_candidates(args, rank, world, dist):
                        "dof_total": dof, "dof_steps_per_s": world * dof * args.steps / t_max, "tol": args.tol,
                        "precision": args.precision, "inner_iters": args.inner, "batch_outer": args.batch_outer,
                        "outer_iters_per_model_step": iters / (args.steps * args.models),
-                       "graph_kernel_nodes_per_step": lps,
+                       "graph_kernel_nodes_captured": lps,
                        "l2": "inputs larger than L2 (%.1f GB resident)" % (sum(m.info()["device_bytes"] for m in models) / 1e9)},
-            "gpu_launches": lps * args.steps, "clocks": clk}))
+            "gpu_launches": kernels, "clocks": clk}))
     if batch is not None:
         batch.close()
     ctx.close()

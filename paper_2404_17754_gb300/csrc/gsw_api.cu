@@ -147,6 +147,12 @@ struct gsw_ctx {
 
 // A set of models advanced together: one CUDA graph per time step holds every
 // model's device-driven step on its own stream branch.
+// Kernel launches of one captured step, split into the part issued once per
+// step and the device-side loop body (issued once per further outer iteration).
+struct StepLaunches {
+  int64_t fixed = 0, body = 0;
+};
+
 struct Batch {
   std::vector<int> ids;
   std::vector<int> versions;
@@ -164,6 +170,10 @@ struct Batch {
   // per step, and the chunks in a row whose steps needed fewer
   int adapt_outer = 6;
   int lower_streak = 0, lower_max = 0;
+  // device-side outer loop (WHILE conditional nodes); off after a failed build
+  bool use_while = true;
+  cudaStream_t body_stream = nullptr;
+  std::vector<StepLaunches> launches;  // per member, of the captured step
 };
 
 namespace {
@@ -806,12 +816,68 @@ void inner_solve_dev(Model* m, cudaStream_t s) {
 // index and the input sample come from device memory and the flexible CG runs
 // a fixed budget of `outer` iterations whose kernels return at entry once the
 // solve has converged.  Returns the number of kernel launches issued.
-int64_t issue_device_step(Model* m, cudaStream_t s, StepState* ss, int outer) {
+// Outer iterations 2.. of a captured step.  With a body stream, they run in a
+// WHILE conditional node of the graph (device-side loop: the body runs while
+// the step has not converged, at most outer - 1 times); otherwise they are
+// unrolled `outer` - 1 times (kernels of a converged step return at entry).
+// Returns false if the conditional node could not be built.
+bool issue_outer_loop(Model* m, cudaStream_t s, StepState* ss, int outer, cudaStream_t bs, StepLaunches* n) {
+  ModelView mv = m->view();
+  const int it = m->opts.inner_iters > 0 ? m->opts.inner_iters : 1;
+  const int64_t per_iter = (1 + 4 * (int64_t)it - 1) + 4;  // inner solve, zbeta, pupdate, A p, update
+  auto body = [&](cudaStream_t st) {
+    inner_solve_dev(m, st);
+    launch_fcg_zbeta(mv, m->y32, m->r, m->q, m->z, m->partials, m->cg, m->isc, st);
+    launch_fcg_pupdate(mv, m->z, m->p, m->q, m->cg, st);
+    launch_ebe(kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, st);
+    launch_fcg_update(mv, m->x, m->r, m->p, m->q, m->partials, m->cg, st);
+  };
+  if (bs == nullptr) {
+    for (int k = 1; k < outer; ++k) body(s);
+    n->fixed += per_iter * (outer - 1);
+    return true;
+  }
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g) != cudaSuccess || cs != cudaStreamCaptureStatusActive) return false;
+  cudaGraphConditionalHandle h;
+  if (cudaGraphConditionalHandleCreate(&h, g, 0, 0) != cudaSuccess) return false;
+  launch_loop_open(h, ss, m->cg, outer - 1, s);
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edges = nullptr;
+  size_t nd = 0;
+  if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edges, &nd) != cudaSuccess) return false;
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (cudaGraphAddNode(&node, g, deps, edges, nd, &p) != cudaSuccess) return false;
+  if (cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+    return false;
+  cudaGraph_t bg = p.conditional.phGraph_out[0];
+  if (cudaStreamBeginCaptureToGraph(bs, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return false;
+  body(bs);
+  launch_loop_next(h, ss, m->cg, outer - 1, bs);
+  if (cudaStreamEndCapture(bs, &bg) != cudaSuccess) return false;
+  n->fixed += 1;
+  n->body += per_iter + 1;
+  return true;
+}
+
+// Issues one mixed time step of model m on stream s with no host
+// synchronisation (device-side step counter, input samples and stopping):
+// step_begin, FP32 right-hand side, shifted state and FP64 residual, the
+// first outer iteration, the remaining ones (see issue_outer_loop), and
+// step_end (commit or pause for the host), Newmark update, receivers and
+// step advance.  Kernels return at entry once the solve has converged.
+bool issue_device_step(Model* m, cudaStream_t s, StepState* ss, int outer, cudaStream_t bs, StepLaunches* n) {
   ModelView mv = m->view();
   Drive dr{m->p_dev, ss};
   const int it = m->opts.inner_iters > 0 ? m->opts.inner_iters : 1;
   const int64_t inner_launches = 1 + 4 * (int64_t)it - 1;
-  int64_t n = 0;
   launch_step_begin(ss, m->cg, s);
   cudaMemsetAsync(m->w32, 0, sizeof(float) * 3 * (size_t)m->N, s);
   launch_rhs_lo(m->lo_half, m->lo_half ? (const void*)&m->lo_h : (const void*)&m->lo_f, m->N, m->u, m->v, m->a,
@@ -819,26 +885,18 @@ int64_t issue_device_step(Model* m, cudaStream_t s, StepState* ss, int outer) {
   launch_cg_init_mixed(mv, m->w32, m->u, m->v, m->a, m->x, m->p, m->z, m->b, m->r, m->q, m->partials, m->cg, s, ss);
   launch_ebe(kModeRes, mv, m->p, m->z, m->b, m->r, 0.0, m->dir, nullptr, m->cg, s, dr);
   launch_cg_rnorm(mv, m->r, m->partials, m->cg, s);
-  n += 5;
   inner_solve_dev(m, s);
   launch_fcg_first(mv, m->y32, m->r, m->z, m->p, m->partials, m->cg, m->isc, s);
-  n += inner_launches + 1;
-  for (int k = 0; k < outer; ++k) {
-    launch_ebe(kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, s);
-    launch_fcg_update(mv, m->x, m->r, m->p, m->q, m->partials, m->cg, s);
-    n += 2;
-    if (k + 1 < outer) {
-      inner_solve_dev(m, s);
-      launch_fcg_zbeta(mv, m->y32, m->r, m->q, m->z, m->partials, m->cg, m->isc, s);
-      launch_fcg_pupdate(mv, m->z, m->p, m->q, m->cg, s);
-      n += inner_launches + 2;
-    }
-  }
+  launch_ebe(kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, s);
+  launch_fcg_update(mv, m->x, m->r, m->p, m->q, m->partials, m->cg, s);
+  n->fixed += 6 + inner_launches + 3;
+  if (!issue_outer_loop(m, s, ss, outer, bs, n)) return false;
   launch_step_end(ss, m->cg, s);
   launch_newmark(mv, m->x, m->u, m->v, m->a, m->cg, s, ss);
   launch_record(m->v, m->rec_node, m->rec_w, m->n_rec, m->wave, m->n_steps, 0, s, ss);
   launch_step_advance(ss, s);
-  return n + 4;
+  n->fixed += 4;
+  return true;
 }
 
 void batch_free(Batch* b) {
@@ -849,6 +907,7 @@ void batch_free(Batch* b) {
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->done_ev) cudaEventDestroy(b->done_ev);
   if (b->origin) cudaStreamDestroy(b->origin);
+  if (b->body_stream) cudaStreamDestroy(b->body_stream);
   if (b->ss_dev) cudaFree(b->ss_dev);
   if (b->ss_host) cudaFreeHost(b->ss_host);
   delete b;
@@ -1207,6 +1266,7 @@ gsw_status gsw_batch_create(gsw_ctx* ctx, const int32_t* model_ids, int32_t n_mo
   };
   cudaError_t e;
   if ((e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking)) != cudaSuccess) return bail("stream", e);
+  if ((e = cudaStreamCreateWithFlags(&b->body_stream, cudaStreamNonBlocking)) != cudaSuccess) return bail("stream", e);
   if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess) return bail("event", e);
   if ((e = cudaEventCreateWithFlags(&b->done_ev, cudaEventDisableTiming)) != cudaSuccess) return bail("event", e);
   if ((e = cudaMalloc(&b->ss_dev, sizeof(StepState) * n_models)) != cudaSuccess) return bail("state", e);
@@ -1251,12 +1311,14 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
   int outer = 0;
   bool stale = (b->exec == nullptr);
   bool adaptive = false;
+  int outer_loop = 0;  // budget of the device-side loop (adaptive members: 32)
   int remaining = 0;
   for (int i = 0; i < nm; ++i) {
     Model* m = find(ctx, b->ids[i]);
     const int o = m->opts.batch_outer > 0 ? m->opts.batch_outer : b->adapt_outer;
     if (m->opts.batch_outer <= 0) adaptive = true;
     if (o > outer) outer = o;
+    outer_loop = std::max(outer_loop, m->opts.batch_outer > 0 ? m->opts.batch_outer : 32);
     if (b->versions[i] != m->version) stale = true;
     StepState& h = b->ss_host[i];
     memset(&h, 0, sizeof(StepState));
@@ -1269,31 +1331,46 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
     h.inner_iters = m->opts.inner_iters > 0 ? m->opts.inner_iters : 1;
     if (!m->failed) remaining = std::max(remaining, h.stop_at - h.step);
   }
-  if (outer != b->outer) stale = true;
+  if ((b->use_while ? outer_loop : outer) != b->outer) stale = true;
   CK(cudaEventRecord(b->fork, ctx->stream));
   CK(cudaStreamWaitEvent(b->origin, b->fork, 0));
   CK(cudaMemcpyAsync(b->ss_dev, b->ss_host, sizeof(StepState) * nm, cudaMemcpyHostToDevice, b->origin));
-  // (re)capture the step graph with `outer` flexible-CG iterations per member
+  // (re)capture the step graph: the outer iterations after the first run in a
+  // device-side WHILE loop per member (budget outer_loop), or, if that cannot
+  // be built, unrolled (budget outer)
   auto capture = [&]() -> gsw_status {
-    if (b->exec) cudaGraphExecDestroy(b->exec);
-    if (b->graph) cudaGraphDestroy(b->graph);
-    b->exec = nullptr;
-    b->graph = nullptr;
-    CK(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
-    CK(cudaEventRecord(b->fork, b->origin));
-    int64_t launches = 0;
-    for (int i = 0; i < nm; ++i) {
-      Model* m = find(ctx, b->ids[i]);
-      CK(cudaStreamWaitEvent(b->streams[i], b->fork, 0));
-      launches += issue_device_step(m, b->streams[i], b->ss_dev + i, outer);
-      CK(cudaEventRecord(b->joins[i], b->streams[i]));
-      CK(cudaStreamWaitEvent(b->origin, b->joins[i], 0));
+    for (;;) {
+      const bool wl = b->use_while;
+      if (b->exec) cudaGraphExecDestroy(b->exec);
+      if (b->graph) cudaGraphDestroy(b->graph);
+      b->exec = nullptr;
+      b->graph = nullptr;
+      CK(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+      CK(cudaEventRecord(b->fork, b->origin));
+      bool ok = true;
+      b->launches.assign(nm, StepLaunches());
+      for (int i = 0; i < nm && ok; ++i) {
+        Model* m = find(ctx, b->ids[i]);
+        ok = cudaStreamWaitEvent(b->streams[i], b->fork, 0) == cudaSuccess &&
+             issue_device_step(m, b->streams[i], b->ss_dev + i, wl ? outer_loop : outer,
+                               wl ? b->body_stream : nullptr, &b->launches[i]) &&
+             cudaEventRecord(b->joins[i], b->streams[i]) == cudaSuccess &&
+             cudaStreamWaitEvent(b->origin, b->joins[i], 0) == cudaSuccess;
+      }
+      cudaError_t ce = cudaStreamEndCapture(b->origin, &b->graph);
+      if (ok && ce == cudaSuccess && cudaGraphInstantiate(&b->exec, b->graph, 0) == cudaSuccess) break;
+      cudaGetLastError();
+      if (b->exec) cudaGraphExecDestroy(b->exec);
+      if (b->graph) cudaGraphDestroy(b->graph);
+      b->exec = nullptr;
+      b->graph = nullptr;
+      if (!wl) return fail(ctx, GSW_E_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+      b->use_while = false;  // retry with the unrolled loop
     }
-    cudaError_t ce = cudaStreamEndCapture(b->origin, &b->graph);
-    if (ce != cudaSuccess) return fail(ctx, GSW_E_CUDA, "graph capture: %s", cudaGetErrorString(ce));
-    CK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    int64_t launches = 0;
+    for (const StepLaunches& l : b->launches) launches += l.fixed + l.body;
     b->launches_per_step = launches;
-    b->outer = outer;
+    b->outer = b->use_while ? outer_loop : outer;
     for (int i = 0; i < nm; ++i) b->versions[i] = find(ctx, b->ids[i])->version;
     return GSW_OK;
   };
@@ -1316,7 +1393,13 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
       m->stats.steps_done += advanced;
       m->stats.cg_iters_total += h.iters_total;
       m->stats.inner_iters_total += h.inner_total;
-      m->stats.kernel_launches += (int64_t)launch_n * (b->launches_per_step / (nm > 0 ? nm : 1));
+      {
+        // launches issued for this member: the fixed part of every graph
+        // launch, plus one loop body per outer iteration after a step's first
+        const StepLaunches& l = b->launches[i];
+        const int64_t extra = std::max<int64_t>(0, h.iters_total - advanced);
+        m->stats.kernel_launches += (int64_t)launch_n * l.fixed + (b->use_while ? extra * l.body : 0);
+      }
       if (advanced > 0) {
         m->stats.cg_iters_last = h.iters_last;
         m->stats.relres_last = h.relres_last;
@@ -1354,7 +1437,7 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
       if (!m->failed && !h.failed) remaining = std::max(remaining, h.stop_at - h.step);
     }
     if (rewrite) CK(cudaMemcpyAsync(b->ss_dev, b->ss_host, sizeof(StepState) * nm, cudaMemcpyHostToDevice, b->origin));
-    if (adaptive && need > 0 && st == GSW_OK) {
+    if (adaptive && !b->use_while && need > 0 && st == GSW_OK) {
       // the captured budget follows the steps: one more than the most outer
       // iterations a step of the chunk needed (2..16); raised at once (steps
       // beyond it were finished by the host), lowered after two chunks in a

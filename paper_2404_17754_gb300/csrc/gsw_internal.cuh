@@ -67,6 +67,8 @@ struct StepState {
   double tol;
   int max_iter;
   int inner_iters;
+  int loops;       // body runs of the device-side outer-iteration loop in this step
+  int pad_;
 };
 
 // Device-driven inputs of a step (null pointers: the host drives the step).
@@ -168,6 +170,13 @@ void launch_cg_init_mixed(const ModelView& m, const float* b32, const double* u,
 void launch_step_begin(StepState* ss, CgScalars* cg, cudaStream_t s);
 void launch_step_end(StepState* ss, const CgScalars* cg, cudaStream_t s);
 void launch_step_advance(StepState* ss, cudaStream_t s);
+// Device-side outer-iteration loop of a captured step (a WHILE conditional
+// node): `open` sets the loop condition before the node (run the body unless
+// the step is inactive or already converged); `next`, the body's last kernel,
+// keeps it set while the step has not converged and the body has run fewer
+// than `cap` times, so the loop always ends.
+void launch_loop_open(cudaGraphConditionalHandle h, StepState* ss, const CgScalars* cg, int cap, cudaStream_t s);
+void launch_loop_next(cudaGraphConditionalHandle h, StepState* ss, const CgScalars* cg, int cap, cudaStream_t s);
 void launch_cg_rnorm(const ModelView& m, const double* r, double* partials, CgScalars* cg, cudaStream_t s);
 void launch_cg_residual(const ModelView& m, const double* b, double* q, double* r, double* z,
                         double* p, const double* dinv, double* partials, CgScalars* cg,

@@ -810,6 +810,21 @@ __global__ void from_f32_kernel(int64_t n, const float* __restrict__ w, double* 
 void launch_step_begin(StepState* ss, CgScalars* cg, cudaStream_t s) { step_begin_kernel<<<1, 1, 0, s>>>(ss, cg); }
 void launch_step_end(StepState* ss, const CgScalars* cg, cudaStream_t s) { step_end_kernel<<<1, 1, 0, s>>>(ss, cg); }
 void launch_step_advance(StepState* ss, cudaStream_t s) { step_advance_kernel<<<1, 1, 0, s>>>(ss); }
+
+__global__ void loop_open_kernel(cudaGraphConditionalHandle h, StepState* ss, const CgScalars* cg, int cap) {
+  ss->loops = 0;
+  cudaGraphSetConditional(h, (cap > 0 && ss->active && !((volatile const CgScalars*)cg)->done) ? 1u : 0u);
+}
+__global__ void loop_next_kernel(cudaGraphConditionalHandle h, StepState* ss, const CgScalars* cg, int cap) {
+  const int n = ++ss->loops;
+  cudaGraphSetConditional(h, (!((volatile const CgScalars*)cg)->done && n < cap) ? 1u : 0u);
+}
+void launch_loop_open(cudaGraphConditionalHandle h, StepState* ss, const CgScalars* cg, int cap, cudaStream_t s) {
+  loop_open_kernel<<<1, 1, 0, s>>>(h, ss, cg, cap);
+}
+void launch_loop_next(cudaGraphConditionalHandle h, StepState* ss, const CgScalars* cg, int cap, cudaStream_t s) {
+  loop_next_kernel<<<1, 1, 0, s>>>(h, ss, cg, cap);
+}
 void launch_to_lo(int64_t N, const double* x, void* d, int half_vec, float* w, cudaStream_t s) {
   if (half_vec)
     to_lo_kernel<__half><<<node_blocks(3 * N), kNodeThreads, 0, s>>>(3 * N, x, (__half*)d, w);
