@@ -62,11 +62,12 @@ typedef struct {
   int32_t precision;    /* gsw_precision */
   int32_t inner_iters;  /* inner preconditioner iterations (mixed modes) */
   int32_t check_every;  /* CG iterations issued between host convergence checks */
-  int32_t batch_outer;  /* batched stepping: flexible-CG iterations per step in the
-                           captured step graph; a step that needs more is
+  int32_t batch_outer;  /* batched stepping: flexible-CG iterations a step may use
+                           inside the step graph; a step that needs more is
                            completed by the host-driven solver (up to max_iter)
-                           and the model then rejoins the graph.  0 = adaptive:
-                           the budget starts at 6 and follows the steps (one
+                           and the model then rejoins the graph.  0 = 32 in the
+                           device-side loop; with the unrolled fallback, 0 =
+                           a budget that starts at 6 and follows the steps (one
                            more than the most iterations a step of the last
                            8-step chunk needed; raised at once, lowered after
                            two lower chunks; the graph is re-captured) */
@@ -170,10 +171,13 @@ gsw_status gsw_run(gsw_ctx *ctx, const int32_t *model_ids, int32_t n_models);
 /* ---- batched stepping (mixed precision modes) ----------------------------
  * A batch advances several models (uneven sizes allowed) together: every
  * time step of every model runs on the device without host synchronisation
- * (device-side step counter and input samples; a fixed budget of
- * solver_opts.batch_outer flexible-CG iterations whose kernels return at
- * entry once converged), each model on its own stream, all captured into one
- * CUDA graph that is launched once per time step.  Models that reach their
+ * (device-side step counter and input samples; after a step's first
+ * flexible-CG iteration the others run in a device-side loop of the graph,
+ * a WHILE conditional node, until the step converges or the budget
+ * solver_opts.batch_outer is used up), each model on its own stream, all
+ * captured into one CUDA graph that is launched once per time step.  Where
+ * the conditional node cannot be built, the budget is unrolled into the
+ * graph (kernels of a converged step return at entry).  Models that reach their
  * n_steps stop advancing; a step that needs more outer iterations than the
  * budget is finished by the host-driven solver; a model that fails stops at
  * the failing step while the others continue, and gsw_batch_step reports the
