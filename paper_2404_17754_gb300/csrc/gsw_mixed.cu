@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kLoBlock, MINB) ebe_lo_kernel(LoView<SG> m, co
     } u;
     const uint4* rp = reinterpret_cast<const uint4*>(m.rec) + (int64_t)b * kLoBlock * RW + threadIdx.x;
 #pragma unroll
-    for (int q = 0; q < RW; ++q) u.v[q] = __ldg(rp + q * kLoBlock);
+    for (int q = 0; q < RW; ++q) u.v[q] = __ldcs(rp + q * kLoBlock);  // streamed: read once per launch
     // node lists have the fixed stride max_local (padding names the dummy
     // node N), so no offset load precedes the index loads
     const int64_t n0 = (int64_t)b * m.blk.max_local;
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(kLoBlock, MINB) ebe_lo_kernel(LoView<SG> m, co
 #pragma unroll
     for (int j = 0; j < kLoNodesPerThread; ++j) {
       const int i = threadIdx.x + j * kLoBlock;
-      raw[j] = (i < nn) ? m.blk.nodes[n0 + i] : 0;
+      raw[j] = (i < nn) ? __ldcs(m.blk.nodes + n0 + i) : 0;
     }
     float xv[kLoNodesPerThread][3];
 #pragma unroll
