@@ -140,12 +140,14 @@ print(json.dumps(dict(dof=n, steps=steps, seconds=el, iters=iters)))
     return d, None
 
 
-def inner_bytes(n_nodes, n_elem, n_faces, half):
+def inner_bytes(n_nodes, n_elem, n_faces, half, fused=False):
     """Algorithmic bytes of one inner (reduced-precision) A d launch: d read once,
     w written once (plus its zeroed read), per element local connectivity (20 B),
-    gradients (9 values), FP32 volume, material id and the block's node-list share (~3 ids)."""
+    gradients (9 values), FP32 volume, material id and the block's node-list share (~3 ids).
+    A launch that fuses the direction recurrence also reads t (FP32) and writes the new d."""
     sv = 2 if half else 4
-    return n_nodes * 3 * (sv + 4 + 4) + n_elem * (20 + 9 * sv + 4 + 4 + 12) + n_faces * (24 + 24)
+    per_node = 3 * (sv + 4 + 4) + (3 * (4 + sv) if fused else 0)
+    return n_nodes * per_node + n_elem * (20 + 9 * sv + 4 + 4 + 12) + n_faces * (24 + 24)
 
 
 CSRC = os.path.join(ROOT, "paper_2404_17754_gb300", "csrc")
@@ -490,11 +492,15 @@ def main():
     inner_roof = None
     if lo_n:
         lo_launch_s = (lo_ms / 1e3) / lo_n
-        lo_bytes = inner_bytes(n_nodes, n_elem, n_faces, args.precision == "fp16")
+        # variants 0 and 1 fuse the direction recurrence on small models only (grid <= 2048 CTAs)
+        lo_fused = m.info()["inner_variant"] in (0, 1) and (n_elem + 191) // 192 + (n_faces + 191) // 192 <= 2048
+        lo_bytes = inner_bytes(n_nodes, n_elem, n_faces, args.precision == "fp16", lo_fused)
         inner_roof = {"bound": "hbm", "achieved": lo_bytes / lo_launch_s / 1e9, "peak": pk.get("hbm_gbs"),
                       "unit": "GB/s", "frac": lo_bytes / lo_launch_s / 1e9 / pk.get("hbm_gbs"),
                       "traffic": traffic_from_profile(INNER_SOURCES, "ebe_inner_%s_realistic.md" % args.precision),
-                      "kernel": "%s (%s inner element-by-element A d)" % (LO_KERNELS.get(m.info()["inner_variant"], "ebe_lo"), args.precision),
+                      "kernel": "%s (%s inner element-by-element A d%s)" % (
+                          LO_KERNELS.get(m.info()["inner_variant"], "ebe_lo"), args.precision,
+                          ", with the fused direction recurrence d = t + beta d" if lo_fused else ""),
                       "peak_source": "of measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                       "algorithmic_bytes": lo_bytes, "launch_ms": lo_launch_s * 1e3, "launches_timed": lo_n,
                       "time_share": lo_ms / (1e3 * t)}

@@ -73,6 +73,7 @@ struct Model {
   float* dinv32 = nullptr;
   float *y32 = nullptr, *s32 = nullptr, *t32 = nullptr, *w32 = nullptr;
   void* d_lo = nullptr;
+  void* d_lo2 = nullptr;  // second inner direction buffer (the fused recurrence alternates the two)
   InnerScalars* isc = nullptr;
   float* dw_part = nullptr;    // per-CTA partial sums of the inner operator's d . A d
   float4* matf = nullptr;      // FP32 material coefficients of the inner operator and the FP32 RHS
@@ -492,7 +493,8 @@ gsw_status build_lo(gsw_ctx* ctx, Model* m, int half) {
     TRY(alloc_into(ctx, m, &m->dinv32, 6 * (size_t)m->N));
     TRY(alloc_into(ctx, m, &m->y32, n3));
     TRY(alloc_into(ctx, m, &m->s32, n3));
-    TRY(alloc_into(ctx, m, &m->t32, n3));
+    TRY(alloc_into(ctx, m, &m->t32, 4 * ((size_t)m->N + 1)));  // padded: 4 entries per node
+    CK(cudaMemsetAsync(m->t32, 0, sizeof(float) * 4 * ((size_t)m->N + 1), s));  // the dummy node's row stays 0
     TRY(alloc_into(ctx, m, &m->w32, n3 + 4));  // + the dummy node's row
     TRY(alloc_into(ctx, m, &m->isc, 1));
     TRY(alloc_into(ctx, m, &m->dw_part, (size_t)m->n_blk + (size_t)((m->F + kLoBlock - 1) / kLoBlock) + 1));
@@ -503,12 +505,17 @@ gsw_status build_lo(gsw_ctx* ctx, Model* m, int half) {
     m->lo_ready = true;
     m->geo_lo = nullptr;
     m->d_lo = nullptr;
+    m->d_lo2 = nullptr;
   }
   if (m->geo_lo == nullptr || m->lo_half != half) {
     // (re)allocate the precision-dependent buffers; the old ones stay owned by the model
     m->geo_lo = dev_alloc(ctx, m, lo_record_bytes(half) * (size_t)m->n_blk * kLoBlock);
-    m->d_lo = dev_alloc(ctx, m, (half ? sizeof(__half) : sizeof(float)) * 4 * ((size_t)m->N + 1));
-    if (!m->geo_lo || !m->d_lo) return fail(ctx, GSW_E_NOMEM, "device allocation failed (inner solve)");
+    const size_t dbytes = (half ? sizeof(__half) : sizeof(float)) * 4 * ((size_t)m->N + 1);
+    m->d_lo = dev_alloc(ctx, m, dbytes);
+    m->d_lo2 = dev_alloc(ctx, m, dbytes);
+    if (!m->geo_lo || !m->d_lo || !m->d_lo2) return fail(ctx, GSW_E_NOMEM, "device allocation failed (inner solve)");
+    CK(cudaMemsetAsync(m->d_lo, 0, dbytes, s));
+    CK(cudaMemsetAsync(m->d_lo2, 0, dbytes, s));
     m->lo_half = half;
   }
   launch_lo_convert(mv, m->n_blk, m->lconn, half, m->geo_lo, m->fgeo32, m->dinv, m->dinv32, m->partials, m->isc,
@@ -625,6 +632,38 @@ gsw_status mlp_after_step(gsw_ctx* ctx, Model* m, cudaStream_t s) {
   return GSW_OK;
 }
 
+// Upper bound of the inner operator's grid (element blocks + face CTAs).
+int lo_grid_max(const Model* m) { return m->n_blk + (int)((m->F + kLoBlock - 1) / kLoBlock); }
+// The direction recurrence is fused into the operator (variants 0, 1) only on
+// small models, where launches dominate: on the 2.42 M-element model the fused
+// operator costs more than the recurrence kernel it replaces.
+bool inner_fuses(const Model* m, int variant) {
+  return lo_variant_fuses(variant) && lo_grid_max(m) <= kAlphaPrologueMax;
+}
+// Kernel launches of one inner solve: initialisation, then per iteration the
+// operator, the update (+ a one-CTA alpha kernel for large models) and,
+// unless the operator fuses it, the direction recurrence (not after the last).
+int64_t inner_solve_launches(const Model* m, bool fuse) {
+  const int64_t it = m->opts.inner_iters > 0 ? m->opts.inner_iters : 1;
+  const int64_t per = (lo_grid_max(m) <= kAlphaPrologueMax ? 2 : 3);
+  return 1 + per * it + (fuse ? 0 : it - 1);
+}
+// Operator product of inner iteration k; returns the direction buffer that
+// holds d_k.  With a fusing variant, iteration k > 0 forms d_k = t + beta
+// d_{k-1} in its gather and writes it to the other of the two direction
+// buffers (no separate recurrence kernel).
+void* inner_operator_step(Model* m, cudaStream_t s, const void* view, int k, int variant, bool fuse) {
+  const int half = m->lo_half;
+  void* dk = (fuse && (k & 1)) ? m->d_lo2 : m->d_lo;
+  if (fuse && k > 0) {
+    void* dprev = (k & 1) ? m->d_lo : m->d_lo2;
+    launch_ebe_lo_fused(half, half, view, dprev, m->t32, dk, m->w32, m->partials, m->isc, s, variant, m->cg);
+  } else {
+    launch_ebe_lo(half, half, view, dk, m->w32, m->partials, m->isc, s, variant, m->cg);
+  }
+  return dk;
+}
+
 // Inner preconditioner: inner_iters block-Jacobi PCG iterations in reduced
 // precision on the scaled outer residual; result in y32 (scaled).
 int64_t inner_solve(Model* m, cudaStream_t s) {
@@ -638,14 +677,15 @@ int64_t inner_solve(Model* m, cudaStream_t s) {
   launch_inner_init(m->N, m->r, m->dinv32, m->s32, m->y32, m->t32, m->d_lo, half, m->w32, m->partials, m->isc,
                     m->cg, s, tune ? 0.f : (float)m->opts.inner_rtol);
   const bool timed = (m->timing || tune) && (int)m->ev_lo.size() >= 2 * it;
+  const bool fuse = !tune && inner_fuses(m, m->lo_variant);
   for (int k = 0; k < it; ++k) {
     const int variant = tune ? k % kLoVariants : m->lo_variant;
     if (timed) cudaEventRecord(m->ev_lo[2 * k], s);
-    launch_ebe_lo(half, half, view, m->d_lo, m->w32, m->partials, m->isc, s, variant, m->cg);
+    void* dk = inner_operator_step(m, s, view, k, variant, fuse);
     if (timed) cudaEventRecord(m->ev_lo[2 * k + 1], s);
-    launch_inner_update(m->N, m->y32, m->s32, m->t32, m->d_lo, half, m->w32, m->dinv32, m->dw_part, m->partials, m->isc, s,
-                        m->cg);
-    if (k + 1 < it) launch_inner_dupdate(m->N, m->t32, m->d_lo, half, m->isc, s, m->cg);
+    launch_inner_update(m->N, m->y32, m->s32, m->t32, dk, half, m->w32, m->dinv32, m->dw_part, m->partials, m->isc, s,
+                        m->cg, lo_grid_max(m));
+    if (!fuse && k + 1 < it) launch_inner_dupdate(m->N, m->t32, m->d_lo, half, m->isc, s, m->cg);
   }
   m->stats.inner_iters_total += it;
   if (timed) {
@@ -682,7 +722,7 @@ int64_t inner_solve(Model* m, cudaStream_t s) {
       m->version += 1;  // a captured batch graph must pick up the choice
     }
   }
-  return 1 + 4 * (int64_t)it - 1;
+  return inner_solve_launches(m, fuse);
 }
 
 // One Newmark step with flexible CG (FP64) preconditioned by the inner solve.
@@ -804,18 +844,15 @@ void inner_solve_dev(Model* m, cudaStream_t s) {
   launch_inner_init(m->N, m->r, m->dinv32, m->s32, m->y32, m->t32, m->d_lo, half, m->w32, m->partials, m->isc,
                     m->cg, s, (float)m->opts.inner_rtol);
   const int it = m->opts.inner_iters > 0 ? m->opts.inner_iters : 1;
+  const bool fuse = inner_fuses(m, m->lo_variant);
   for (int k = 0; k < it; ++k) {
-    launch_ebe_lo(half, half, view, m->d_lo, m->w32, m->partials, m->isc, s, m->lo_variant, m->cg);
-    launch_inner_update(m->N, m->y32, m->s32, m->t32, m->d_lo, half, m->w32, m->dinv32, m->dw_part, m->partials, m->isc, s,
-                        m->cg);
-    if (k + 1 < it) launch_inner_dupdate(m->N, m->t32, m->d_lo, half, m->isc, s, m->cg);
+    void* dk = inner_operator_step(m, s, view, k, m->lo_variant, fuse);
+    launch_inner_update(m->N, m->y32, m->s32, m->t32, dk, half, m->w32, m->dinv32, m->dw_part, m->partials, m->isc, s,
+                        m->cg, lo_grid_max(m));
+    if (!fuse && k + 1 < it) launch_inner_dupdate(m->N, m->t32, m->d_lo, half, m->isc, s, m->cg);
   }
 }
 
-// One mixed-precision Newmark step driven entirely on the device: the step
-// index and the input sample come from device memory and the flexible CG runs
-// a fixed budget of `outer` iterations whose kernels return at entry once the
-// solve has converged.  Returns the number of kernel launches issued.
 // Outer iterations 2.. of a captured step.  With a body stream, they run in a
 // WHILE conditional node of the graph (device-side loop: the body runs while
 // the step has not converged, at most outer - 1 times); otherwise they are
@@ -824,7 +861,7 @@ void inner_solve_dev(Model* m, cudaStream_t s) {
 bool issue_outer_loop(Model* m, cudaStream_t s, StepState* ss, int outer, cudaStream_t bs, StepLaunches* n) {
   ModelView mv = m->view();
   const int it = m->opts.inner_iters > 0 ? m->opts.inner_iters : 1;
-  const int64_t per_iter = (1 + 4 * (int64_t)it - 1) + 4;  // inner solve, zbeta, pupdate, A p, update
+  const int64_t per_iter = inner_solve_launches(m, inner_fuses(m, m->lo_variant)) + 4;  // + zbeta, pupdate, A p, update
   auto body = [&](cudaStream_t st) {
     inner_solve_dev(m, st);
     launch_fcg_zbeta(mv, m->y32, m->r, m->q, m->z, m->partials, m->cg, m->isc, st);
@@ -877,7 +914,7 @@ bool issue_device_step(Model* m, cudaStream_t s, StepState* ss, int outer, cudaS
   ModelView mv = m->view();
   Drive dr{m->p_dev, ss};
   const int it = m->opts.inner_iters > 0 ? m->opts.inner_iters : 1;
-  const int64_t inner_launches = 1 + 4 * (int64_t)it - 1;
+  const int64_t inner_launches = inner_solve_launches(m, inner_fuses(m, m->lo_variant));
   launch_step_begin(ss, m->cg, s);
   cudaMemsetAsync(m->w32, 0, sizeof(float) * 3 * (size_t)m->N, s);
   launch_rhs_lo(m->lo_half, m->lo_half ? (const void*)&m->lo_h : (const void*)&m->lo_f, m->N, m->u, m->v, m->a,

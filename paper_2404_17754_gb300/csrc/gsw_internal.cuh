@@ -213,9 +213,19 @@ void launch_ebe_lo(int half_geo, int half_vec, const void* lo_view, const void* 
                    double* partials, InnerScalars* sc, cudaStream_t st, int variant,
                    const CgScalars* outer = nullptr);
 constexpr int kLoVariants = 4;
+// Variants 0 and 1 can fuse the previous inner iteration's direction
+// recurrence d' = t + beta d into their gather (t padded to 4 entries per
+// node; d' goes to the other direction buffer).
+bool lo_variant_fuses(int variant);
+void launch_ebe_lo_fused(int half_geo, int half_vec, const void* lo_view, const void* dprev, const float* t4,
+                         void* dnew, float* w, double* partials, InnerScalars* sc, cudaStream_t st, int variant,
+                         const CgScalars* outer);
+// n_dw_max: an upper bound of the operator's grid size; up to
+// kAlphaPrologueMax partials the update forms alpha itself (one launch less).
+constexpr int kAlphaPrologueMax = 2048;
 void launch_inner_update(int64_t N, float* y, float* s, float* t, const void* d, int half_vec,
                          float* w, const float* dinv32, const float* dw_part, double* partials,
-                         InnerScalars* sc, cudaStream_t st, const CgScalars* outer);
+                         InnerScalars* sc, cudaStream_t st, const CgScalars* outer, int n_dw_max);
 void launch_inner_dupdate(int64_t N, const float* t, void* d, int half_vec, const InnerScalars* sc,
                           cudaStream_t st, const CgScalars* outer);
 // conversions for the standalone reduced-precision operator (tests)

@@ -54,6 +54,14 @@ __device__ __forceinline__ void load3(const __half* p, float& a, float& b, float
   c = __low2float(h1);
 }
 
+__device__ __forceinline__ void store4(float* p, const float (&q)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(q[0], q[1], q[2], q[3]);
+}
+__device__ __forceinline__ void store4(__half* p, const __half (&q)[4]) {
+  const __half2 a = __halves2half2(q[0], q[1]), b = __halves2half2(q[2], q[3]);
+  *reinterpret_cast<uint2*>(p) = make_uint2(*reinterpret_cast<const unsigned*>(&a), *reinterpret_cast<const unsigned*>(&b));
+}
+
 // Operator element order inside a block: warp w, lane l processes element
 // 6 l + w of the block.  With the 6 Kuhn tetrahedra of each cell stored
 // consecutively, a warp then holds congruent tetrahedra of 32 different cells,
@@ -277,10 +285,12 @@ __device__ __forceinline__ void lo_store_dw(float dot, float* dw_part, InnerScal
 // with shared-memory atomics, and the CTA writes each unique node once (a
 // plain store when no other block or absorbing face touches it).  CTAs after
 // the element blocks apply the absorbing faces with global atomics.
-template <typename SG, typename SD, int MINB>
+template <typename SG, typename SD, int MINB, bool FUSE = false>
 __global__ void __launch_bounds__(kLoBlock, MINB) ebe_lo_kernel(LoView<SG> m, const SD* __restrict__ d,
                                                            float* __restrict__ w, double* partials,
-                                                           InnerScalars* sc, const CgScalars* outer) {
+                                                           InnerScalars* sc, const CgScalars* outer,
+                                                           const float* __restrict__ t4 = nullptr,
+                                                           SD* __restrict__ dnew = nullptr) {
   if (inner_stopped(outer, sc)) return;
   typedef typename LoRec<SG>::type Rec;
   constexpr int RW = LoRec<SG>::words;
@@ -317,10 +327,43 @@ __global__ void __launch_bounds__(kLoBlock, MINB) ebe_lo_kernel(LoView<SG> m, co
       raw[j] = (i < nn) ? __ldcs(m.blk.nodes + n0 + i) : 0;
     }
     float xv[kLoNodesPerThread][3];
+    if (FUSE) {
+      // the direction recurrence of the previous inner iteration, fused into
+      // the gather: d' = t + beta d (rounded to the storage precision), written
+      // to the other direction buffer (every block touching a node writes the
+      // same value; the buffer read here is not written in this launch)
+      const float beta = ((volatile const InnerScalars*)sc)->beta_f;
+      float tv[kLoNodesPerThread][3];
 #pragma unroll
-    for (int j = 0; j < kLoNodesPerThread; ++j) {
-      const int i = threadIdx.x + j * kLoBlock;
-      if (i < nn) load3(d + 4 * (int64_t)(raw[j] & 0x7fffffff), xv[j][0], xv[j][1], xv[j][2]);
+      for (int j = 0; j < kLoNodesPerThread; ++j) {
+        const int i = threadIdx.x + j * kLoBlock;
+        if (i < nn) {
+          const int64_t g = raw[j] & 0x7fffffff;
+          load3(d + 4 * g, xv[j][0], xv[j][1], xv[j][2]);
+          load3(t4 + 4 * g, tv[j][0], tv[j][1], tv[j][2]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kLoNodesPerThread; ++j) {
+        const int i = threadIdx.x + j * kLoBlock;
+        if (i < nn) {
+          const int64_t g = raw[j] & 0x7fffffff;
+          SD q[4];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            q[c] = from_f<SD>(fmaf(beta, xv[j][c], tv[j][c]));
+            xv[j][c] = to_f(q[c]);
+          }
+          q[3] = from_f<SD>(0.f);
+          store4(dnew + 4 * g, q);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < kLoNodesPerThread; ++j) {
+        const int i = threadIdx.x + j * kLoBlock;
+        if (i < nn) load3(d + 4 * (int64_t)(raw[j] & 0x7fffffff), xv[j][0], xv[j][1], xv[j][2]);
+      }
     }
 #pragma unroll
     for (int j = 0; j < kLoNodesPerThread; ++j) {
@@ -389,6 +432,14 @@ __global__ void __launch_bounds__(kLoBlock, MINB) ebe_lo_kernel(LoView<SG> m, co
       for (int k = 0; k < 6; ++k) {
         nd[k] = m.fnode[k * m.F + fc];
         load3(d + 4 * nd[k], xin[k][0], xin[k][1], xin[k][2]);
+        if (FUSE) {
+          // the same fused direction the element blocks use (rounded alike)
+          const float beta = ((volatile const InnerScalars*)sc)->beta_f;
+          float tv[3];
+          load3(t4 + 4 * nd[k], tv[0], tv[1], tv[2]);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) xin[k][c] = to_f(from_f<SD>(fmaf(beta, xin[k][c], tv[c])));
+        }
         const float dn = n[0] * xin[k][0] + n[1] * xin[k][1] + n[2] * xin[k][2];
 #pragma unroll
         for (int i = 0; i < 3; ++i) z[k][i] = fmaf(As, xin[k][i], Ad * dn * n[i]);
@@ -454,10 +505,11 @@ __global__ void inner_init_kernel(int64_t N, const double* __restrict__ r, const
     dinv_apply_f(dinv + 6 * n, sn, tn);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      t[3 * n + i] = tn[i];
+      t[4 * n + i] = tn[i];
       d[4 * n + i] = from_f<SD>(tn[i]);
       st = fmaf(sn[i], tn[i], st);
     }
+    t[4 * n + 3] = 0.f;
     d[4 * n + 3] = from_f<SD>(0.f);
   }
   float vals[1] = {st}, out[1];
@@ -471,8 +523,9 @@ __global__ void inner_init_kernel(int64_t N, const double* __restrict__ r, const
 }
 
 // Node quads: thread g owns nodes 4g .. 4g+3, whose 3-vectors (12 floats),
-// D^-1 blocks (24 floats) and padded direction entries (16 values) are whole
-// 16-byte words; the N mod 4 trailing nodes go to thread N/4.
+// D^-1 blocks (24 floats) and padded 4-entry vectors (the direction d and the
+// preconditioned residual t: 16 values) are whole 16-byte words; the N mod 4
+// trailing nodes go to thread N/4.
 template <int K>
 __device__ __forceinline__ void ldq(const float* p, float (&v)[4 * K]) {
   const float4* q = reinterpret_cast<const float4*>(p);
@@ -521,11 +574,10 @@ __device__ __forceinline__ void st_dir(__half* p, const float (&v)[16]) {
   }
 }
 
-// alpha = s . t / d . A d from the operator's per-CTA partials (one CTA,
-// fixed summation order).
-__global__ void inner_alpha_kernel(const float* __restrict__ dw_part, InnerScalars* sc, const CgScalars* outer) {
-  if (inner_stopped(outer, sc)) return;
-  __shared__ float sh_red[32];
+// d . A d from the operator's per-CTA partials, summed by the calling CTA in
+// a fixed order (the result is valid in thread 0).
+__device__ __forceinline__ float sum_dw_partials(const float* __restrict__ dw_part, const InnerScalars* sc,
+                                                 float* sh_red) {
   const unsigned int G = ((volatile const InnerScalars*)sc)->n_dw, B = blockDim.x;
   float a[8];
 #pragma unroll
@@ -541,7 +593,15 @@ __global__ void inner_alpha_kernel(const float* __restrict__ dw_part, InnerScala
 #pragma unroll
   for (int j = 0; j < 8; ++j)
     if (i + j * B < G) a[j] += __ldcg(dw_part + i + j * B);
-  const float dw = block_sum_f(((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])), sh_red);
+  return block_sum_f(((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])), sh_red);
+}
+
+// alpha = s . t / d . A d from the operator's per-CTA partials (one CTA,
+// fixed summation order).
+__global__ void inner_alpha_kernel(const float* __restrict__ dw_part, InnerScalars* sc, const CgScalars* outer) {
+  if (inner_stopped(outer, sc)) return;
+  __shared__ float sh_red[32];
+  const float dw = sum_dw_partials(dw_part, sc, sh_red);
   if (threadIdx.x == 0) {
     const double st = ((volatile InnerScalars*)sc)->st;
     sc->dw = dw;
@@ -550,18 +610,38 @@ __global__ void inner_alpha_kernel(const float* __restrict__ dw_part, InnerScala
 }
 
 // y += alpha d, s -= alpha w, t = D^-1 s, w = 0, partial s . t; the last
-// block forms beta and tests the relative stopping factor.
-template <typename SD>
+// block forms beta and tests the relative stopping factor.  With PRO (few
+// operator partials, i.e. a small model) every CTA forms alpha itself in a
+// prologue and no separate alpha kernel is launched.
+template <typename SD, bool PRO = false>
 __global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __restrict__ s, float* __restrict__ t,
                                     const SD* __restrict__ d, float* __restrict__ w, const float* __restrict__ dinv,
-                                    double* partials, InnerScalars* sc, const CgScalars* outer) {
+                                    double* partials, InnerScalars* sc, const CgScalars* outer,
+                                    const float* __restrict__ dw_part = nullptr) {
   if (inner_stopped(outer, sc)) return;
-  const float alpha = ((volatile const InnerScalars*)sc)->alpha_f;
+  float alpha;
+  if (PRO) {
+    __shared__ float sh_red[32];
+    __shared__ float alpha_s;
+    const float dw = sum_dw_partials(dw_part, sc, sh_red);
+    if (threadIdx.x == 0) {
+      const double st_old = ((volatile const InnerScalars*)sc)->st;
+      alpha_s = (dw != 0.f) ? (float)(st_old / (double)dw) : 0.f;
+      if (blockIdx.x == 0) {
+        sc->dw = dw;
+        sc->alpha_f = alpha_s;
+      }
+    }
+    __syncthreads();
+    alpha = alpha_s;
+  } else {
+    alpha = ((volatile const InnerScalars*)sc)->alpha_f;
+  }
   float st = 0.f;
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t G4 = N >> 2;
   if (g < G4) {
-    float yv[12], sv[12], wv[12], tv[12], dv[16], Dv[24];
+    float yv[12], sv[12], wv[12], tv[16], dv[16], Dv[24];
     ldq<3>(y + 12 * g, yv);
     ldq<3>(s + 12 * g, sv);
     ldq<3>(w + 12 * g, wv);
@@ -574,14 +654,15 @@ __global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __r
         yv[3 * q + i] = fmaf(alpha, dv[4 * q + i], yv[3 * q + i]);
         sv[3 * q + i] = fmaf(-alpha, wv[3 * q + i], sv[3 * q + i]);
       }
-      dinv_apply_f(Dv + 6 * q, sv + 3 * q, tv + 3 * q);
+      dinv_apply_f(Dv + 6 * q, sv + 3 * q, tv + 4 * q);
+      tv[4 * q + 3] = 0.f;
 #pragma unroll
-      for (int i = 0; i < 3; ++i) st = fmaf(sv[3 * q + i], tv[3 * q + i], st);
+      for (int i = 0; i < 3; ++i) st = fmaf(sv[3 * q + i], tv[4 * q + i], st);
     }
     const float zero[12] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     stq<3>(y + 12 * g, yv);
     stq<3>(s + 12 * g, sv);
-    stq<3>(t + 12 * g, tv);
+    stq<4>(t + 16 * g, tv);
     stq<3>(w + 12 * g, zero);
   } else if (g == G4) {
     for (int64_t n = 4 * G4; n < N; ++n) {
@@ -597,9 +678,10 @@ __global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __r
       dinv_apply_f(dinv + 6 * n, sn, tn);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        t[3 * n + i] = tn[i];
+        t[4 * n + i] = tn[i];
         st = fmaf(sn[i], tn[i], st);
       }
+      t[4 * n + 3] = 0.f;
     }
   }
   float vals[1] = {st}, out[1];
@@ -624,18 +706,18 @@ __global__ void inner_dupdate_kernel(int64_t N, const float* __restrict__ t, SD*
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t G4 = N >> 2;
   if (g < G4) {
-    float tv[12], dv[16];
-    ldq<3>(t + 12 * g, tv);
+    float tv[16], dv[16];
+    ldq<4>(t + 16 * g, tv);
     ld_dir(d + 16 * g, dv);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-      for (int i = 0; i < 3; ++i) dv[4 * q + i] = fmaf(beta, dv[4 * q + i], tv[3 * q + i]);
+      for (int i = 0; i < 3; ++i) dv[4 * q + i] = fmaf(beta, dv[4 * q + i], tv[4 * q + i]);
     st_dir(d + 16 * g, dv);
   } else if (g == G4) {
     for (int64_t n = 4 * G4; n < N; ++n)
 #pragma unroll
-      for (int i = 0; i < 3; ++i) d[4 * n + i] = from_f<SD>(fmaf(beta, to_f(d[4 * n + i]), t[3 * n + i]));
+      for (int i = 0; i < 3; ++i) d[4 * n + i] = from_f<SD>(fmaf(beta, to_f(d[4 * n + i]), t[4 * n + i]));
   }
 }
 
@@ -1425,6 +1507,39 @@ static void ebe_lo_launch(int variant, const LoView<SG>& m, const SD* d, float* 
   else
     ebe_lo_kernel<SG, SD, 1><<<g, kLoBlock, smem, st>>>(m, d, w, partials, sc, outer);
 }
+template <typename SG, typename SD>
+static void ebe_lo_fused_launch(int variant, const LoView<SG>& m, const SD* dprev, const float* t4, SD* dnew,
+                                float* w, double* partials, InnerScalars* sc, cudaStream_t st,
+                                const CgScalars* outer) {
+  const unsigned g = (unsigned)(m.blk.n_blk + (m.F + kLoBlock - 1) / kLoBlock);
+  const size_t smem = sizeof(float) * 6 * (size_t)m.blk.max_local;
+  if (variant == 1)
+    ebe_lo_kernel<SG, SD, 4, true><<<g, kLoBlock, smem, st>>>(m, dprev, w, partials, sc, outer, t4, dnew);
+  else
+    ebe_lo_kernel<SG, SD, 1, true><<<g, kLoBlock, smem, st>>>(m, dprev, w, partials, sc, outer, t4, dnew);
+}
+bool lo_variant_fuses(int variant) { return variant == 0 || variant == 1; }
+void launch_ebe_lo_fused(int half_geo, int half_vec, const void* lo_view, const void* dprev, const float* t4,
+                         void* dnew, float* w, double* partials, InnerScalars* sc, cudaStream_t st, int variant,
+                         const CgScalars* outer) {
+  if (half_geo) {
+    const LoView<__half>& m = *(const LoView<__half>*)lo_view;
+    if (half_vec)
+      ebe_lo_fused_launch<__half, __half>(variant, m, (const __half*)dprev, t4, (__half*)dnew, w, partials, sc, st,
+                                          outer);
+    else
+      ebe_lo_fused_launch<__half, float>(variant, m, (const float*)dprev, t4, (float*)dnew, w, partials, sc, st,
+                                         outer);
+  } else {
+    const LoView<float>& m = *(const LoView<float>*)lo_view;
+    if (half_vec)
+      ebe_lo_fused_launch<float, __half>(variant, m, (const __half*)dprev, t4, (__half*)dnew, w, partials, sc, st,
+                                         outer);
+    else
+      ebe_lo_fused_launch<float, float>(variant, m, (const float*)dprev, t4, (float*)dnew, w, partials, sc, st,
+                                        outer);
+  }
+}
 void launch_ebe_lo(int half_geo, int half_vec, const void* lo_view, const void* d, float* w, double* partials,
                    InnerScalars* sc, cudaStream_t st, int variant, const CgScalars* outer) {
   if (half_geo) {
@@ -1606,7 +1721,16 @@ void launch_rhs_lo(int half_geo, const void* lo_view, int64_t N, const double* u
 static unsigned quad_blocks(int64_t N) { return (unsigned)(((N >> 2) + 1 + kNodeThreads - 1) / kNodeThreads); }
 void launch_inner_update(int64_t N, float* y, float* s, float* t, const void* d, int half_vec, float* w,
                          const float* dinv32, const float* dw_part, double* partials, InnerScalars* sc,
-                         cudaStream_t st, const CgScalars* outer) {
+                         cudaStream_t st, const CgScalars* outer, int n_dw_max) {
+  if (n_dw_max <= kAlphaPrologueMax) {
+    if (half_vec)
+      inner_update_kernel<__half, true><<<quad_blocks(N), kNodeThreads, 0, st>>>(
+          N, y, s, t, (const __half*)d, w, dinv32, partials, sc, outer, dw_part);
+    else
+      inner_update_kernel<float, true><<<quad_blocks(N), kNodeThreads, 0, st>>>(
+          N, y, s, t, (const float*)d, w, dinv32, partials, sc, outer, dw_part);
+    return;
+  }
   inner_alpha_kernel<<<1, 1024, 0, st>>>(dw_part, sc, outer);
   if (half_vec)
     inner_update_kernel<__half><<<quad_blocks(N), kNodeThreads, 0, st>>>(N, y, s, t, (const __half*)d, w, dinv32,

@@ -162,3 +162,23 @@ def test_inner_relative_tolerance(ctx):
     assert stats["relres_last"] <= 1e-8
     assert 0 < stats["inner_iters_total"] < 60 * stats["cg_iters_total"]
     m.free()
+
+
+def test_fused_recurrence_small_model(ctx):
+    """On small models the one-CTA-per-block variants fold the inner direction
+    recurrence into the operator launch: same outer iteration counts and states as
+    the warp-specialised variant, which keeps the separate recurrence kernel."""
+    cfg = configs.config1(n_steps=20)
+    m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
+    m.set_time(cfg["dt"], 20, cfg["band"])
+    m.set_input(cfg["dir"], cfg["p"])
+    states, outer = {}, {}
+    for v in (1, 3):
+        m.set_solver(tol=1e-8, precision=1, inner_iters=15, inner_variant=v)
+        m.reset()
+        m.step(20)
+        states[v] = m.get_state()[0]
+        outer[v] = m.stats()["cg_iters_total"]
+    assert _relerr(states[1], states[3]) <= 1e-6
+    assert abs(outer[1] - outer[3]) <= 2, outer
+    m.free()
