@@ -349,8 +349,10 @@ def run_learned(args, rank, world, dist):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    # default window: steps 200..219, past the start-up transient (the first steps
+    # of a run from rest converge in fewer iterations than the rest of the run)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--workload", default="realistic", choices=["realistic", "two-layer", "candidates", "learned"])
