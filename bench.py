@@ -225,7 +225,7 @@ def run_candidates(args, rank, world, dist):
         m.set_time(cfg["dt"], n_total, cfg["band"])
         m.set_input(cfg["dir"], cfg["p"])
         m.set_solver(tol=args.tol, precision=prec, inner_iters=args.inner, batch_outer=args.batch_outer,
-                     inner_rtol=args.inner_rtol)
+                     inner_rtol=args.inner_rtol, guess_order=args.guess_order)
         models.append(m)
         dof += 3 * cfg["mesh"]["xyz"].shape[0]
     # the plain FP64 form advances the candidates one after another (host-driven
@@ -276,6 +276,7 @@ def run_candidates(args, rank, world, dist):
                                                           "one after another (plain FP64 form)"),
                        "dof_total": dof, "dof_steps_per_s": world * dof * args.steps / t_max, "tol": args.tol,
                        "precision": args.precision, "inner_iters": args.inner, "batch_outer": args.batch_outer,
+                       "guess_order": args.guess_order,
                        "outer_iters_per_model_step": iters / (args.steps * args.models),
                        "graph_kernel_nodes_captured": lps,
                        "l2": "inputs larger than L2 (%.1f GB resident)" % (sum(m.info()["device_bytes"] for m in models) / 1e9)},
@@ -310,7 +311,8 @@ def run_learned(args, rank, world, dist):
         m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
         m.set_time(cfg["dt"], n_total, cfg["band"])
         m.set_input(cfg["dir"], cfg["p"])
-        m.set_solver(tol=args.tol, precision=prec, inner_iters=args.inner, inner_rtol=args.inner_rtol)
+        m.set_solver(tol=args.tol, precision=prec, inner_iters=args.inner, inner_rtol=args.inner_rtol,
+                     guess_order=args.guess_order)
         if enable:
             m.set_learning(True, train_steps=args.train_steps, batch=16384, iters_per_step=2, lr=1e-3, seed=7)
         t0 = time.perf_counter()
@@ -361,6 +363,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16"])
     ap.add_argument("--inner", type=int, default=30, help="inner preconditioner iterations (mixed modes; the cap "
                     "when --inner-rtol > 0)")
+    ap.add_argument("--guess-order", type=int, default=4,
+                    help="initial guess: 0 = Newmark predictor, k = degree-k extrapolation of the last k+1 increments")
     ap.add_argument("--batch-outer", type=int, default=0,
                     help="candidates workload: flexible-CG iterations per step in the captured step graph "
                     "(0 = adaptive)")
@@ -419,7 +423,8 @@ def main():
     m.set_time(cfg["dt"], n_total + 1, cfg["band"])
     m.set_input(cfg["dir"], cfg["p"])
     prec = {"fp64": 0, "fp32": 1, "fp16": 2}[args.precision]
-    m.set_solver(tol=args.tol, precision=prec, inner_iters=args.inner, inner_rtol=args.inner_rtol)
+    m.set_solver(tol=args.tol, precision=prec, inner_iters=args.inner, inner_rtol=args.inner_rtol,
+                     guess_order=args.guess_order)
     n_nodes, n_elem, n_faces = mesh["xyz"].shape[0], mesh["conn"].shape[0], mesh["faces"].shape[0]
     dof = 3 * n_nodes
 
@@ -528,6 +533,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": cfg["name"] if args.workload == "realistic" else "two-layer 100x100x50 m",
                    "dof": dof, "elements": n_elem, "dt": cfg["dt"], "tol": args.tol, "precision": args.precision,
+                   "guess_order": args.guess_order,
                    "solver": "block-Jacobi PCG" if args.precision == "fp64" else
                              ("flexible CG (FP64) + %s block-Jacobi PCG preconditioner, %d iterations" % (
                                  args.precision, args.inner) if args.inner_rtol <= 0 else

@@ -80,6 +80,13 @@ typedef struct {
   double inner_rtol;     /* mixed modes: the inner PCG stops once its preconditioned
                             residual norm has dropped by this factor (0 = always run
                             inner_iters iterations, which stay the cap); must be in [0, 1) */
+  int32_t guess_order;   /* initial guess of each step's solve: 0 = the Newmark
+                            predictor dt v + dt^2/2 a; k = 1..6 = the degree-k
+                            polynomial through the last k+1 converged increments,
+                            one step ahead (the predictor until k+1 exist; the
+                            history restarts at gsw_reset / gsw_set_state).  Any
+                            guess converges to the same tolerance. */
+  int32_t reserved;      /* must be 0 */
 } gsw_solver_opts;
 
 typedef struct {

@@ -57,7 +57,7 @@ struct Model {
   std::vector<double> input;
   int dir = 0;
   bool input_set = false;
-  gsw_solver_opts opts = {1e-8, 10000, GSW_PREC_FP64, 20, 8, 6, -1, 0.0};
+  gsw_solver_opts opts = {1e-8, 10000, GSW_PREC_FP64, 20, 8, 6, -1, 0.0, 0, 0};
   int64_t step = 0;
   bool failed = false;
   gsw_stats stats = {};
@@ -76,6 +76,9 @@ struct Model {
   void* d_lo2 = nullptr;  // second inner direction buffer (the fused recurrence alternates the two)
   InnerScalars* isc = nullptr;
   float* dw_part = nullptr;    // per-CTA partial sums of the inner operator's d . A d
+  double* guess_ring = nullptr;  // [k+1][3N] converged increments (extrapolated initial guess)
+  int guess_ring_k = 0;           // degree the ring was sized for
+  int* guess_ext = nullptr;       // {count, head} of the ring, on the device
   float4* matf = nullptr;      // FP32 material coefficients of the inner operator and the FP32 RHS
   float4* uva = nullptr;       // FP32 copy of u, v, a ([N + 1][3] words) for the FP32 RHS
   unsigned long long iters_mark = 0;   // device inner-iteration counter when timing started
@@ -317,6 +320,7 @@ gsw_status model_reset(gsw_ctx* ctx, Model* m) {
   m->step = 0;
   m->failed = false;
   m->stats = gsw_stats{};
+  if (m->guess_ext) CK(cudaMemsetAsync(m->guess_ext, 0, 2 * sizeof(int), ctx->stream));  // no increment history
   if (m->lo_ready) {
     CK(cudaMemcpyAsync(&m->iters_reset, &m->isc->iters, sizeof(m->iters_reset), cudaMemcpyDeviceToHost,
                        ctx->stream));
@@ -339,7 +343,9 @@ gsw_status step_fp64(gsw_ctx* ctx, Model* m) {
   init.tol = m->opts.tol;
   init.max_iter = m->opts.max_iter;
   CK(cudaMemcpyAsync(m->cg, &init, sizeof(CgScalars), cudaMemcpyHostToDevice, s));
-  launch_cg_init(mv, m->b, m->v, m->a, m->x, m->q, m->partials, m->cg, s);
+  const int k_guess = m->opts.guess_order;
+  if (k_guess > 0) launch_guess_extrap(m->N, m->guess_ring, k_guess, m->guess_ext, m->v, m->a, m->dt, m->x, s);
+  launch_cg_init(mv, m->b, m->v, m->a, m->x, m->q, m->partials, m->cg, s, k_guess > 0 ? 1 : 0);
   launch_ebe(kModeA, mv, m->x, nullptr, nullptr, m->q, 0.0, 0, nullptr, m->cg, s);
   launch_cg_residual(mv, m->b, m->q, m->r, m->z, m->p, m->dinv, m->partials, m->cg, s);
   const int chunk = m->opts.check_every > 0 ? m->opts.check_every : 8;
@@ -390,6 +396,7 @@ gsw_status step_fp64(gsw_ctx* ctx, Model* m) {
                   (long long)m->step, m->opts.tol, h.iter, h.relres);
     return fail(ctx, GSW_E_NAN, "step %lld: non-finite CG residual", (long long)m->step);
   }
+  if (m->opts.guess_order > 0) launch_guess_push(m->N, m->x, m->guess_ring, m->opts.guess_order, m->guess_ext, s);
   launch_newmark(mv, m->x, m->u, m->v, m->a, m->cg, s);
   launch_record(m->v, m->rec_node, m->rec_w, m->n_rec, m->wave, m->n_steps, (int)m->step, s);
   CK(cudaGetLastError());
@@ -740,8 +747,11 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
   CK(cudaMemcpyAsync(m->cg, &init, sizeof(CgScalars), cudaMemcpyHostToDevice, s));
   // initial guess (predictor or learned) and the shifted state (u~ in p, v~ in z, a~ in b), r = q = 0
   const bool learned = mlp_use_guess(ctx, m, s);
+  const bool extrap = !learned && m->opts.guess_order > 0;
+  if (extrap)
+    launch_guess_extrap(m->N, m->guess_ring, m->opts.guess_order, m->guess_ext, m->v, m->a, m->dt, m->x, s);
   launch_cg_init_mixed(mv, m->w32, m->u, m->v, m->a, m->x, m->p, m->z, m->b, m->r, m->q, m->partials, m->cg, s,
-                       nullptr, learned ? 1 : 0);
+                       nullptr, (learned || extrap) ? 1 : 0);
   // FP64 residual at the initial guess in one element-by-element pass
   launch_ebe(kModeRes, mv, m->p, m->z, m->b, m->r, force, m->dir, nullptr, m->cg, s);
   launch_cg_rnorm(mv, m->r, m->partials, m->cg, s);
@@ -824,6 +834,7 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
     return fail(ctx, GSW_E_NAN, "step %lld: non-finite CG residual", (long long)m->step);
   }
   TRY(mlp_after_step(ctx, m, s));
+  if (m->opts.guess_order > 0) launch_guess_push(m->N, m->x, m->guess_ring, m->opts.guess_order, m->guess_ext, s);
   launch_newmark(mv, m->x, m->u, m->v, m->a, m->cg, s);
   launch_record(m->v, m->rec_node, m->rec_w, m->n_rec, m->wave, m->n_steps, (int)m->step, s);
   CK(cudaGetLastError());
@@ -919,16 +930,20 @@ bool issue_device_step(Model* m, cudaStream_t s, StepState* ss, int outer, cudaS
   cudaMemsetAsync(m->w32, 0, sizeof(float) * 3 * (size_t)m->N, s);
   launch_rhs_lo(m->lo_half, m->lo_half ? (const void*)&m->lo_h : (const void*)&m->lo_f, m->N, m->u, m->v, m->a,
                 m->uva, m->w32, 0.0, m->dir, s, dr);
-  launch_cg_init_mixed(mv, m->w32, m->u, m->v, m->a, m->x, m->p, m->z, m->b, m->r, m->q, m->partials, m->cg, s, ss);
+  const int k_guess = m->opts.guess_order;
+  if (k_guess > 0) launch_guess_extrap(m->N, m->guess_ring, k_guess, m->guess_ext, m->v, m->a, m->dt, m->x, s, ss);
+  launch_cg_init_mixed(mv, m->w32, m->u, m->v, m->a, m->x, m->p, m->z, m->b, m->r, m->q, m->partials, m->cg, s, ss,
+                       k_guess > 0 ? 1 : 0);
   launch_ebe(kModeRes, mv, m->p, m->z, m->b, m->r, 0.0, m->dir, nullptr, m->cg, s, dr);
   launch_cg_rnorm(mv, m->r, m->partials, m->cg, s);
   inner_solve_dev(m, s);
   launch_fcg_first(mv, m->y32, m->r, m->z, m->p, m->partials, m->cg, m->isc, s);
   launch_ebe(kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, s);
   launch_fcg_update(mv, m->x, m->r, m->p, m->q, m->partials, m->cg, s);
-  n->fixed += 6 + inner_launches + 3;
+  n->fixed += 6 + inner_launches + 3 + (k_guess > 0 ? 3 : 0);
   if (!issue_outer_loop(m, s, ss, outer, bs, n)) return false;
   launch_step_end(ss, m->cg, s);
+  if (k_guess > 0) launch_guess_push(m->N, m->x, m->guess_ring, k_guess, m->guess_ext, s, ss);  // on commit
   launch_newmark(mv, m->x, m->u, m->v, m->a, m->cg, s, ss);
   launch_record(m->v, m->rec_node, m->rec_w, m->n_rec, m->wave, m->n_steps, 0, s, ss);
   launch_step_advance(ss, s);
@@ -1218,6 +1233,18 @@ gsw_status gsw_set_solver(gsw_ctx* ctx, int32_t model_id, const gsw_solver_opts*
     return fail(ctx, GSW_E_INVALID, "inner_rtol must be in [0, 1)");
   if (opts->inner_variant < -1 || opts->inner_variant >= kLoVariants)
     return fail(ctx, GSW_E_INVALID, "inner_variant must be -1 (autotune) or 0..%d", kLoVariants - 1);
+  if (opts->guess_order < 0 || opts->guess_order > kMaxGuessOrder || opts->reserved != 0)
+    return fail(ctx, GSW_E_INVALID, "guess_order must be 0..%d (and reserved 0)", kMaxGuessOrder);
+  if (opts->guess_order > 0) {
+    DeviceGuard g(ctx->device);
+    if (!m->guess_ext) TRY(alloc_into(ctx, m, &m->guess_ext, 2));
+    if (!m->guess_ring || m->guess_ring_k < opts->guess_order) {
+      TRY(alloc_into(ctx, m, &m->guess_ring, (size_t)(opts->guess_order + 1) * 3 * (size_t)m->N));
+      m->guess_ring_k = opts->guess_order;
+    }
+    if (opts->guess_order != m->opts.guess_order || m->opts.guess_order == 0)
+      CK(cudaMemsetAsync(m->guess_ext, 0, 2 * sizeof(int), ctx->stream));  // the history restarts
+  }
   m->opts = *opts;
   m->version += 1;
   if (m->opts.precision != GSW_PREC_FP64 && m->time_set) {
@@ -1636,6 +1663,7 @@ gsw_status gsw_set_state(gsw_ctx* ctx, int32_t model_id, const double* u, const 
   CK(cudaMemcpyAsync(m->u, u, bytes, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(m->v, v, bytes, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(m->a, a, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  if (m->guess_ext) CK(cudaMemsetAsync(m->guess_ext, 0, 2 * sizeof(int), ctx->stream));  // no increment history
   CK(cudaStreamSynchronize(ctx->stream));
   m->step = step;
   m->failed = false;

@@ -155,8 +155,15 @@ void launch_receivers(const ModelView& m, const double* xyz, double px, double p
 void launch_ebe(int mode, const ModelView& m, const double* x, const double* v, const double* a,
                 double* y, double force, int dir, double* partials, CgScalars* cg,
                 cudaStream_t s, Drive dr = Drive{nullptr, nullptr});
+// Initial guess from the last k+1 increments (degree-k extrapolation), k <=
+// kMaxGuessOrder; ring: [k+1][3N] doubles, ext: {count, head} on the device.
+constexpr int kMaxGuessOrder = 6;
+void launch_guess_extrap(int64_t N, const double* ring, int k, const int* ext, const double* v, const double* a,
+                         double dt, double* x, cudaStream_t s, const StepState* ss = nullptr);
+void launch_guess_push(int64_t N, const double* du, double* ring, int k, int* ext, cudaStream_t s,
+                       const StepState* ss = nullptr);
 void launch_cg_init(const ModelView& m, const double* b, const double* v, const double* a,
-                    double* x, double* q, double* partials, CgScalars* cg, cudaStream_t s);
+                    double* x, double* q, double* partials, CgScalars* cg, cudaStream_t s, int use_guess = 0);
 // FP32 right-hand side on the reduced-precision operator's element blocks
 // (uva: [N + 1][3] float4 scratch for the FP32 state; b32 zero on entry).
 void launch_rhs_lo(int half_geo, const void* lo_view, int64_t N, const double* u, const double* v, const double* a,

@@ -479,14 +479,19 @@ __device__ __forceinline__ void apply_dinv(const double* __restrict__ d, const d
 
 __global__ void cg_init_kernel(int64_t N, const double* __restrict__ b, const double* __restrict__ v,
                                const double* __restrict__ a, double dt, double* __restrict__ x,
-                               double* __restrict__ q, double* partials, CgScalars* cg) {
+                               double* __restrict__ q, double* partials, CgScalars* cg, int use_guess) {
   double bb = 0.0;
   const double h = 0.5 * dt * dt;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double bi = b[i];
     bb = fma(bi, bi, bb);
-    x[i] = fma(dt, v[i], h * a[i]);
+    double x0 = fma(dt, v[i], h * a[i]);
+    if (use_guess) {
+      const double g = x[i];
+      if (isfinite(g)) x0 = g;  // a non-finite guess falls back to the predictor
+    }
+    x[i] = x0;
     q[i] = 0.0;
   }
   double vals[1] = {bb}, out[1];
@@ -755,8 +760,65 @@ void launch_ebe(int mode, const ModelView& m, const double* x, const double* v, 
   }
 }
 void launch_cg_init(const ModelView& m, const double* b, const double* v, const double* a,
-                    double* x, double* q, double* partials, CgScalars* cg, cudaStream_t s) {
-  cg_init_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, b, v, a, m.dt, x, q, partials, cg);
+                    double* x, double* q, double* partials, CgScalars* cg, cudaStream_t s, int use_guess) {
+  cg_init_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, b, v, a, m.dt, x, q, partials, cg, use_guess);
+}
+
+// ------------------------------------------------------------------------------
+// Initial guess from the increment history
+// ------------------------------------------------------------------------------
+
+// du0 = sum_j c_j du_{n-j}, j = 0..k, c_j = (-1)^j C(k+1, j+1): the degree-k
+// polynomial through the last k+1 increments, evaluated one step ahead.  ring
+// holds S = k+1 increments ([S][3N]); ext = {count, head} (head: next slot).
+// Until k+1 increments exist the Newmark predictor dt v + dt^2/2 a is used.
+__global__ void guess_extrap_kernel(int64_t n3, const double* __restrict__ ring, int S, const int* ext, int k,
+                                    const double* __restrict__ v, const double* __restrict__ a, double dt,
+                                    double* __restrict__ x, const StepState* ss) {
+  if (ss != nullptr && !((volatile const StepState*)ss)->active) return;
+  const int count = ((volatile const int*)ext)[0], head = ((volatile const int*)ext)[1];
+  const bool ok = count >= k + 1;
+  double c[kMaxGuessOrder + 1];
+  int slot[kMaxGuessOrder + 1];
+  double binom = 1.0;  // C(k+1, j+1), built up term by term
+  for (int j = 0; j <= k; ++j) {
+    binom = binom * (double)(k + 1 - j) / (double)(j + 1);
+    c[j] = (j & 1) ? -binom : binom;
+    slot[j] = ((head - 1 - j) % S + S) % S;
+  }
+  const double h = 0.5 * dt * dt;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    double g;
+    if (ok) {
+      g = 0.0;
+      for (int j = 0; j <= k; ++j) g = fma(c[j], ring[(int64_t)slot[j] * n3 + i], g);
+    } else {
+      g = fma(dt, v[i], h * a[i]);
+    }
+    x[i] = g;
+  }
+}
+// After a committed step: ring[head] = du, then (one thread) head, count advance.
+__global__ void guess_push_kernel(int64_t n3, const double* __restrict__ du, double* __restrict__ ring, int S,
+                                  const int* ext, const StepState* ss) {
+  if (ss != nullptr && !((volatile const StepState*)ss)->commit) return;
+  const int head = ((volatile const int*)ext)[1];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
+    ring[(int64_t)head * n3 + i] = du[i];
+}
+__global__ void guess_advance_kernel(int* ext, int S, const StepState* ss) {
+  if (ss != nullptr && !((volatile const StepState*)ss)->commit) return;
+  ext[1] = (ext[1] + 1) % S;
+  ext[0] = ext[0] < S ? ext[0] + 1 : S;
+}
+void launch_guess_extrap(int64_t N, const double* ring, int k, const int* ext, const double* v, const double* a,
+                         double dt, double* x, cudaStream_t s, const StepState* ss) {
+  guess_extrap_kernel<<<node_blocks(3 * N), kNodeThreads, 0, s>>>(3 * N, ring, k + 1, ext, k, v, a, dt, x, ss);
+}
+void launch_guess_push(int64_t N, const double* du, double* ring, int k, int* ext, cudaStream_t s,
+                       const StepState* ss) {
+  guess_push_kernel<<<node_blocks(3 * N), kNodeThreads, 0, s>>>(3 * N, du, ring, k + 1, ext, ss);
+  guess_advance_kernel<<<1, 1, 0, s>>>(ext, k + 1, ss);
 }
 void launch_cg_init_mixed(const ModelView& m, const float* b32, const double* u, const double* v, const double* a,
                           double* x, double* ut, double* vt, double* at, double* r, double* q, double* partials,

@@ -152,3 +152,26 @@ def test_batch_adaptive_budget(ctx):
     b.close()
     for m in models:
         m.free()
+
+
+def test_batch_extrapolated_guess(ctx):
+    """The increment history of the extrapolated initial guess is kept on the device, so
+    batched steps (which only push a step's increment once it commits) match the same
+    models stepped alone."""
+    cfgs = _cfgs(n_steps=30)
+    alone = []
+    for cfg in cfgs:
+        m = _upload(ctx, cfg, guess_order=3)
+        m.step(cfg["n_steps"])
+        alone.append(m.waveforms())
+        m.free()
+    models = [_upload(ctx, cfg, guess_order=3) for cfg in cfgs]
+    b = ctx.batch(models)
+    b.step(30)
+    for cfg, m, w_alone in zip(cfgs, models, alone):
+        assert m.stats()["steps_done"] == cfg["n_steps"]
+        assert _relerr(m.waveforms(), w_alone) <= 1e-7
+        assert _relerr(m.waveforms(), newmark.analysis(cfg, tol=1e-8)["wave"]) <= 1e-6
+    b.close()
+    for m in models:
+        m.free()

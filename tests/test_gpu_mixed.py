@@ -182,3 +182,28 @@ def test_fused_recurrence_small_model(ctx):
     assert _relerr(states[1], states[3]) <= 1e-6
     assert abs(outer[1] - outer[3]) <= 2, outer
     m.free()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_extrapolated_initial_guess(ctx, prec):
+    """guess_order = 4: each step starts from the quartic through the last five converged
+    increments.  The steps still converge to the same tolerance (oracle parity), the
+    initial residual is smaller than from the Newmark predictor, and the solves need
+    fewer iterations."""
+    cfg = configs.config1(n_steps=80)
+    ref = newmark.analysis(cfg, tol=1e-8)
+    out = {}
+    for order in (0, 4):
+        m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
+        m.set_time(cfg["dt"], 80, cfg["band"])
+        m.set_input(cfg["dir"], cfg["p"])
+        m.set_solver(tol=1e-8, precision=prec, inner_iters=15, guess_order=order)
+        m.step(80)
+        st = m.stats()
+        assert _relerr(m.waveforms(), ref["wave"]) <= 1e-6
+        out[order] = (st["init_relres_sum"] / 80, st["cg_iters_total"])
+        m.free()
+    if prec != 0:  # the initial residual is recorded by the mixed steps (its mean includes
+        # the start-up steps, where both runs use the predictor)
+        assert out[4][0] < out[0][0], out
+    assert out[4][1] < out[0][1], out
