@@ -79,6 +79,7 @@ struct Model {
   double* guess_ring = nullptr;  // [k+1][3N] converged increments (extrapolated initial guess)
   int guess_ring_k = 0;           // degree the ring was sized for
   int* guess_ext = nullptr;       // {count, head} of the ring, on the device
+  double* guess_base = nullptr;   // this step's extrapolated guess (base of the learned correction)
   float4* matf = nullptr;      // FP32 material coefficients of the inner operator and the FP32 RHS
   float4* uva = nullptr;       // FP32 copy of u, v, a ([N + 1][3] words) for the FP32 RHS
   unsigned long long iters_mark = 0;   // device inner-iteration counter when timing started
@@ -597,7 +598,7 @@ gsw_status mlp_init(gsw_ctx* ctx, Model* m, uint32_t seed) {
 }
 
 // Before a step: write the learned guess into x when it applies.
-bool mlp_use_guess(gsw_ctx* ctx, Model* m, cudaStream_t s) {
+bool mlp_use_guess(gsw_ctx* ctx, Model* m, cudaStream_t s, const double* base) {
   (void)ctx;
   if (!m->learn.enable || !m->mlp_ready || m->mlp_off || m->hist_count < 4 || m->step < m->learn.train_steps)
     return false;
@@ -606,22 +607,25 @@ bool mlp_use_guess(gsw_ctx* ctx, Model* m, cudaStream_t s) {
   if ((m->applied++ % 10) == 9) return false;
   launch_mlp_sigma(m->N, m->hist, m->hist_head, m->partials, m->ms, s);
   launch_mlp_infer(m->N, m->hist, m->hist_head, m->nodef, m->v, m->a, m->dt, m->packed, m->ms, m->x, nullptr,
-                   nullptr, s);
+                   nullptr, s, base);
   m->stats.kernel_launches += 2;
   return true;
 }
 
 // After a converged step (before the Newmark update overwrites v, a): train on
 // the converged increment, then push it into the history.
-gsw_status mlp_after_step(gsw_ctx* ctx, Model* m, cudaStream_t s) {
+gsw_status mlp_after_step(gsw_ctx* ctx, Model* m, cudaStream_t s, const double* base) {
   if (!m->learn.enable || !m->mlp_ready) return GSW_OK;
+  // the scale of the correction to an extrapolated base: this step's targets
+  // and the next step's output use it
+  if (base) launch_mlp_sigma_e(m->N, m->x, base, m->partials, m->ms, s);
   if (m->step < m->learn.train_steps && m->hist_count >= 4 && !m->cg_host->zero_rhs) {
     launch_mlp_sigma(m->N, m->hist, m->hist_head, m->partials, m->ms, s);
     CK(cudaMemsetAsync(&m->ms->loss, 0, sizeof(double), s));
     const int B = m->learn.batch;
     for (int it = 0; it < m->learn.iters_per_step; ++it) {
       launch_mlp_sample(m->N, B, m->learn.seed, (int)m->step, it, m->hist, m->hist_head, m->nodef, m->x, m->v, m->a,
-                        m->dt, m->ms, m->trainX, m->trainY, s);
+                        m->dt, m->ms, m->trainX, m->trainY, s, base);
       if (launch_mlp_fwdbwd(B, m->trainX, m->trainY, m->theta, m->grad, &m->ms->loss, s))
         return fail(ctx, GSW_E_CUDA, "training kernel configuration failed");
       m->adam_t += 1;
@@ -746,9 +750,19 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
   init.max_iter = m->opts.max_iter;
   CK(cudaMemcpyAsync(m->cg, &init, sizeof(CgScalars), cudaMemcpyHostToDevice, s));
   // initial guess (predictor or learned) and the shifted state (u~ in p, v~ in z, a~ in b), r = q = 0
-  const bool learned = mlp_use_guess(ctx, m, s);
+  // with learning and an extrapolated guess, the network corrects the
+  // extrapolation: keep this step's extrapolated guess as its base
+  double* base = nullptr;
+  if (m->learn.enable && m->opts.guess_order > 0) {
+    if (!m->guess_base) TRY(alloc_into(ctx, m, &m->guess_base, 3 * (size_t)m->N));
+    base = m->guess_base;
+    launch_guess_extrap(m->N, m->guess_ring, m->opts.guess_order, m->guess_ext, m->v, m->a, m->dt, base, s);
+  }
+  const bool learned = mlp_use_guess(ctx, m, s, base);
   const bool extrap = !learned && m->opts.guess_order > 0;
-  if (extrap)
+  if (extrap && base)
+    CK(cudaMemcpyAsync(m->x, base, sizeof(double) * 3 * (size_t)m->N, cudaMemcpyDeviceToDevice, s));
+  else if (extrap)
     launch_guess_extrap(m->N, m->guess_ring, m->opts.guess_order, m->guess_ext, m->v, m->a, m->dt, m->x, s);
   launch_cg_init_mixed(mv, m->w32, m->u, m->v, m->a, m->x, m->p, m->z, m->b, m->r, m->q, m->partials, m->cg, s,
                        nullptr, (learned || extrap) ? 1 : 0);
@@ -833,7 +847,7 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
       return fail(ctx, GSW_E_TIMEOUT, "step %lld: a bounded wait of the inner operator ran out", (long long)m->step);
     return fail(ctx, GSW_E_NAN, "step %lld: non-finite CG residual", (long long)m->step);
   }
-  TRY(mlp_after_step(ctx, m, s));
+  TRY(mlp_after_step(ctx, m, s, base));
   if (m->opts.guess_order > 0) launch_guess_push(m->N, m->x, m->guess_ring, m->opts.guess_order, m->guess_ext, s);
   launch_newmark(mv, m->x, m->u, m->v, m->a, m->cg, s);
   launch_record(m->v, m->rec_node, m->rec_w, m->n_rec, m->wave, m->n_steps, (int)m->step, s);

@@ -43,11 +43,14 @@ struct CgScalars {
 // Scalars of the learned initial guess (one set per model).
 constexpr int kMlpParams = 5443;  // 16-64-64-3 MLP
 struct MlpScalars {
-  double sigma;  // RMS of the latest displacement increment
-  double loss;   // training loss accumulator
+  double sigma;    // RMS of the latest displacement increment
+  double loss;     // training loss accumulator
   unsigned int counter;
   unsigned int pad;
+  double sigma_e;  // RMS of the last step's correction to the extrapolated guess (its output scale)
 };
+void launch_mlp_sigma_e(int64_t N, const double* du, const double* base, double* partials, MlpScalars* ms,
+                        cudaStream_t s);
 
 // Step counter and status of a model advanced on the device (batched,
 // graph-captured stepping): the host reads it only between steps.
@@ -258,10 +261,10 @@ void launch_node_features(const ModelView& m, int n_mat, int32_t* node_mat, floa
 void launch_mlp_sigma(int64_t N, const float* hist, int head, double* partials, MlpScalars* ms, cudaStream_t s);
 void launch_mlp_infer(int64_t N, const float* hist, int head, const float* nodef, const double* v, const double* a,
                       double dt, const uint32_t* packed, const MlpScalars* ms, double* x, const float* xin,
-                      float* yout, cudaStream_t s);
+                      float* yout, cudaStream_t s, const double* x_base = nullptr);
 void launch_mlp_sample(int64_t N, int B, uint32_t seed, int step, int iter, const float* hist, int head,
                        const float* nodef, const double* du, const double* v, const double* a, double dt,
-                       const MlpScalars* ms, float* X, float* Y, cudaStream_t s);
+                       const MlpScalars* ms, float* X, float* Y, cudaStream_t s, const double* x_base = nullptr);
 int launch_mlp_fwdbwd(int B, const float* X, const float* Y, const float* theta, float* grad, double* loss,
                       cudaStream_t s);
 void launch_mlp_adam(float* theta, float* grad, float* m, float* v, int t, float lr, cudaStream_t s);

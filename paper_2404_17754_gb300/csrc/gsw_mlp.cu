@@ -118,6 +118,27 @@ __global__ void mlp_sigma_kernel(int64_t N, const float* __restrict__ hist, int 
   }
 }
 
+// RMS of du - base (the correction the network should have made to the
+// extrapolated guess of the step just converged): the output scale of the
+// correction to an extrapolated base, far smaller than the increment itself.
+__global__ void mlp_sigma_e_kernel(int64_t N, const double* __restrict__ du, const double* __restrict__ base,
+                                   double* partials, MlpScalars* ms) {
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double e = du[i] - base[i];
+    s = fma(e, e, s);
+  }
+  double vals[1] = {s}, out[1];
+  if (last_block_reduce<1>(vals, partials, &ms->counter, out) && threadIdx.x == 0) {
+    const double sg = sqrt(out[0] / (3.0 * N));
+    ms->sigma_e = sg > 0.0 ? sg : ms->sigma;
+  }
+}
+void launch_mlp_sigma_e(int64_t N, const double* du, const double* base, double* partials, MlpScalars* ms,
+                        cudaStream_t s) {
+  mlp_sigma_e_kernel<<<node_blocks(3 * N), kNodeThreads, 0, s>>>(N, du, base, partials, ms);
+}
+
 __device__ __forceinline__ float node_feature(const float* __restrict__ hist, const float* __restrict__ nodef,
                                               int64_t N, int head, int64_t n, int f, float inv_sigma) {
   if (f < 12) {
@@ -134,7 +155,8 @@ __global__ void __launch_bounds__(128) mlp_infer_kernel(int64_t N, const float* 
                                                         const double* __restrict__ v, const double* __restrict__ a,
                                                         double dt, const uint32_t* __restrict__ packed,
                                                         const MlpScalars* ms, double* __restrict__ x,
-                                                        const float* __restrict__ xin, float* __restrict__ yout) {
+                                                        const float* __restrict__ xin, float* __restrict__ yout,
+                                                        const double* __restrict__ x_base) {
   __shared__ uint32_t wf[kFrag];
   __shared__ float bias[136];
   __shared__ __nv_bfloat16 feat[4][16][16];
@@ -143,6 +165,7 @@ __global__ void __launch_bounds__(128) mlp_infer_kernel(int64_t N, const float* 
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const double sigma = ms ? ms->sigma : 1.0;
+  const double sigma_e = ms ? ms->sigma_e : 1.0;
   const float inv_sigma = (float)(1.0 / sigma);
   const int64_t n_tiles = (N + 15) / 16;
   for (int64_t tile = (int64_t)blockIdx.x * 4 + warp; tile < n_tiles; tile += (int64_t)gridDim.x * 4) {
@@ -234,7 +257,10 @@ __global__ void __launch_bounds__(128) mlp_infer_kernel(int64_t N, const float* 
           yout[n * 3 + c] = o;
         } else {
           const int64_t k = 3 * n + c;
-          x[k] = fma(dt, v[k], 0.5 * dt * dt * a[k]) + sigma * (double)o;
+          // the network corrects a base guess: the extrapolated one when given,
+          // else the Newmark predictor
+          const double b0 = x_base ? x_base[k] : fma(dt, v[k], 0.5 * dt * dt * a[k]);
+          x[k] = b0 + (x_base ? sigma_e : sigma) * (double)o;
         }
       }
     }
@@ -242,7 +268,8 @@ __global__ void __launch_bounds__(128) mlp_infer_kernel(int64_t N, const float* 
 }
 
 // Training samples: node = hash(seed, step, iter, i) mod N; features as in
-// inference (FP32), target = (du_s - predictor) / sigma.
+// inference (FP32), target = (du_s - base guess) / sigma (base: the extrapolated
+// guess when given, else the Newmark predictor).
 __device__ __forceinline__ uint32_t mix32(uint32_t x) {
   x ^= x >> 16;
   x *= 0x7feb352dU;
@@ -256,17 +283,19 @@ __global__ void mlp_sample_kernel(int64_t N, int B, uint32_t seed, int step, int
                                   const float* __restrict__ hist, int head, const float* __restrict__ nodef,
                                   const double* __restrict__ du, const double* __restrict__ v,
                                   const double* __restrict__ a, double dt, const MlpScalars* ms, float* X,
-                                  float* Y) {
+                                  float* Y, const double* __restrict__ x_base) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B) return;
   const uint32_t h = mix32(seed ^ mix32((uint32_t)step * 0x9E3779B9U ^ mix32((uint32_t)iter * 0x85EBCA6BU ^ (uint32_t)i)));
   const int64_t n = (int64_t)(h % (uint32_t)N);
   const double sigma = ms->sigma;
+  const double out_scale = x_base ? ms->sigma_e : sigma;
   const float inv_sigma = (float)(1.0 / sigma);
   for (int f = 0; f < 16; ++f) X[(int64_t)i * 16 + f] = node_feature(hist, nodef, N, head, n, f, inv_sigma);
   for (int c = 0; c < 3; ++c) {
     const int64_t k = 3 * n + c;
-    Y[(int64_t)i * 3 + c] = (float)((du[k] - fma(dt, v[k], 0.5 * dt * dt * a[k])) / sigma);
+    const double b0 = x_base ? x_base[k] : fma(dt, v[k], 0.5 * dt * dt * a[k]);
+    Y[(int64_t)i * 3 + c] = (float)((du[k] - b0) / out_scale);
   }
 }
 
@@ -394,17 +423,18 @@ void launch_mlp_sigma(int64_t N, const float* hist, int head, double* partials, 
 }
 void launch_mlp_infer(int64_t N, const float* hist, int head, const float* nodef, const double* v, const double* a,
                       double dt, const uint32_t* packed, const MlpScalars* ms, double* x, const float* xin,
-                      float* yout, cudaStream_t s) {
+                      float* yout, cudaStream_t s, const double* x_base) {
   const int64_t tiles = (N + 15) / 16;
   int64_t blocks = (tiles + 3) / 4;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
-  mlp_infer_kernel<<<(unsigned)blocks, 128, 0, s>>>(N, hist, head, nodef, v, a, dt, packed, ms, x, xin, yout);
+  mlp_infer_kernel<<<(unsigned)blocks, 128, 0, s>>>(N, hist, head, nodef, v, a, dt, packed, ms, x, xin, yout, x_base);
 }
 void launch_mlp_sample(int64_t N, int B, uint32_t seed, int step, int iter, const float* hist, int head,
                        const float* nodef, const double* du, const double* v, const double* a, double dt,
-                       const MlpScalars* ms, float* X, float* Y, cudaStream_t s) {
-  mlp_sample_kernel<<<(B + 255) / 256, 256, 0, s>>>(N, B, seed, step, iter, hist, head, nodef, du, v, a, dt, ms, X, Y);
+                       const MlpScalars* ms, float* X, float* Y, cudaStream_t s, const double* x_base) {
+  mlp_sample_kernel<<<(B + 255) / 256, 256, 0, s>>>(N, B, seed, step, iter, hist, head, nodef, du, v, a, dt, ms, X, Y,
+                                                    x_base);
 }
 size_t mlp_fwdbwd_smem() { return sizeof(float) * (kMlpParams + kMlpChunk * (16 + 4 * 64 + 3)); }
 int launch_mlp_fwdbwd(int B, const float* X, const float* Y, const float* theta, float* grad, double* loss,
