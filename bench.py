@@ -224,7 +224,7 @@ def run_candidates(args, rank, world, dist):
         m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
         m.set_time(cfg["dt"], n_total, cfg["band"])
         m.set_input(cfg["dir"], cfg["p"])
-        m.set_solver(tol=args.tol, precision=prec, inner_iters=args.inner, batch_outer=args.batch_outer,
+        m.set_solver(tol=args.tol, outer_op=OUTER_OPS[args.outer_op], precision=prec, inner_iters=args.inner, batch_outer=args.batch_outer,
                      inner_rtol=args.inner_rtol, guess_order=args.guess_order)
         models.append(m)
         dof += 3 * cfg["mesh"]["xyz"].shape[0]
@@ -311,7 +311,7 @@ def run_learned(args, rank, world, dist):
         m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
         m.set_time(cfg["dt"], n_total, cfg["band"])
         m.set_input(cfg["dir"], cfg["p"])
-        m.set_solver(tol=args.tol, precision=prec, inner_iters=args.inner, inner_rtol=args.inner_rtol,
+        m.set_solver(tol=args.tol, outer_op=OUTER_OPS[args.outer_op], precision=prec, inner_iters=args.inner, inner_rtol=args.inner_rtol,
                      guess_order=args.guess_order)
         if enable:
             m.set_learning(True, train_steps=args.train_steps, batch=16384, iters_per_step=2, lr=1e-3, seed=7)
@@ -348,6 +348,9 @@ def run_learned(args, rank, world, dist):
     ctx.close()
 
 
+OUTER_OPS = {"auto": 0, "fp64": 1, "dword": 2}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -370,6 +373,9 @@ def main():
                     "(0 = adaptive)")
     ap.add_argument("--inner-rtol", type=float, default=0.0,
                     help="inner PCG relative stopping factor (0 = always --inner iterations)")
+    ap.add_argument("--outer-op", default="auto", choices=["auto", "fp64", "dword"],
+                    help="arithmetic of the CG's element-by-element operator: auto = double-word (paired FP32) in "
+                         "the mixed modes, FP64 in the FP64 mode")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -429,7 +435,7 @@ def main():
     m.set_time(cfg["dt"], n_total + 1, cfg["band"])
     m.set_input(cfg["dir"], cfg["p"])
     prec = {"fp64": 0, "fp32": 1, "fp16": 2}[args.precision]
-    m.set_solver(tol=args.tol, precision=prec, inner_iters=args.inner, inner_rtol=args.inner_rtol,
+    m.set_solver(tol=args.tol, outer_op=OUTER_OPS[args.outer_op], precision=prec, inner_iters=args.inner, inner_rtol=args.inner_rtol,
                      guess_order=args.guess_order)
     n_nodes, n_elem, n_faces = mesh["xyz"].shape[0], mesh["conn"].shape[0], mesh["faces"].shape[0]
     dof = 3 * n_nodes

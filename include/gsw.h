@@ -49,12 +49,28 @@ typedef enum {
 } gsw_status;
 
 /* Solver precision of the preconditioner's inner products (the outer CG
- * residual, its dot products and the Newmark update are FP64 in every mode). */
+ * vectors, its dot products and the Newmark update are FP64 in every mode;
+ * the arithmetic of the outer operator is set by gsw_outer_op). */
 typedef enum {
   GSW_PREC_FP64 = 0,   /* plain block-Jacobi PCG, everything FP64 */
   GSW_PREC_FP32 = 1,   /* flexible CG; inner preconditioner EBE in FP32 */
   GSW_PREC_FP16 = 2    /* flexible CG; inner vectors FP16, FP32 EBE arithmetic */
 } gsw_precision;
+
+/* Arithmetic of the CG's (outer) operator A = K + (2/dt) C + (4/dt^2) M.
+ * Double-word: each FP64 value is carried as an unevaluated sum of two floats
+ * (about 48 significant bits) and every operation is an error-free
+ * transformation on the FP32 pipe (TwoSum, Fast2Sum, TwoProd with a fused
+ * multiply-add); element data, vectors and the accumulation of A x stay FP64
+ * in memory.  Relative error of A x about 2^-46 times the cancellation of the
+ * element sums, far below the 1e-8 residual target; on GB300, whose FP64 pipe
+ * retires 2 fused multiply-adds per clock per SM against 128 in FP32, the
+ * double-word operator is the faster one. */
+typedef enum {
+  GSW_OUTER_AUTO = 0,   /* double-word in the mixed modes, FP64 in GSW_PREC_FP64 */
+  GSW_OUTER_FP64 = 1,   /* hardware FP64 */
+  GSW_OUTER_DWORD = 2   /* double-word arithmetic */
+} gsw_outer_op;
 
 typedef struct {
   double tol;           /* relative residual ||b - A x|| / ||b|| target (1e-8) */
@@ -86,7 +102,8 @@ typedef struct {
                             one step ahead (the predictor until k+1 exist; the
                             history restarts at gsw_reset / gsw_set_state).  Any
                             guess converges to the same tolerance. */
-  int32_t reserved;      /* must be 0 */
+  int32_t outer_op;      /* arithmetic of the CG's element-by-element operator (the
+                            FP64 residual at the initial guess and A p): gsw_outer_op */
 } gsw_solver_opts;
 
 typedef struct {
@@ -232,7 +249,8 @@ gsw_status gsw_timing(gsw_ctx *ctx, int32_t model_id, int32_t enable, double *ms
  *  which = 1: y = K x;  which = 2: y = M x;  which = 3: y = C x;
  *  which = 4: y = A x by the reduced-precision inner operator of the model's
  *  current mixed precision mode (x rounded to the inner storage type,
- *  FP32 arithmetic and accumulation); GSW_E_STATE in FP64 mode.
+ *  FP32 arithmetic and accumulation); GSW_E_STATE in FP64 mode;
+ *  which = 5: y = A x in double-word arithmetic (GSW_OUTER_DWORD).
  * x_dev, y_dev device pointers; y is overwritten. */
 gsw_status gsw_apply(gsw_ctx *ctx, int32_t model_id, int32_t which, const double *x_dev,
                      double *y_dev);

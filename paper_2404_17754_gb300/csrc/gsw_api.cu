@@ -333,6 +333,21 @@ gsw_status model_reset(gsw_ctx* ctx, Model* m) {
 }
 
 // One Newmark step: RHS (one EBE pass), PCG from the predictor, update, record.
+// The CG's (outer) element-by-element operator: hardware FP64, or double-word
+// arithmetic on the FP32 pipe (gsw_solver_opts.outer_op; by default the mixed
+// modes use double-word, the FP64 mode FP64).
+bool outer_dword(const Model* m) {
+  return m->opts.outer_op == GSW_OUTER_DWORD || (m->opts.outer_op == GSW_OUTER_AUTO && m->opts.precision != GSW_PREC_FP64);
+}
+void launch_outer(const Model* m, int mode, const ModelView& mv, const double* x, const double* v, const double* a,
+                  double* y, double force, int dir, double* partials, CgScalars* cg, cudaStream_t s,
+                  Drive dr = Drive{nullptr, nullptr}) {
+  if (outer_dword(m))
+    launch_ebe_dw(mode, mv, x, v, a, y, force, dir, partials, cg, s, dr);
+  else
+    launch_ebe(mode, mv, x, v, a, y, force, dir, partials, cg, s, dr);
+}
+
 gsw_status step_fp64(gsw_ctx* ctx, Model* m) {
   cudaStream_t s = ctx->stream;
   ModelView mv = m->view();
@@ -347,7 +362,7 @@ gsw_status step_fp64(gsw_ctx* ctx, Model* m) {
   const int k_guess = m->opts.guess_order;
   if (k_guess > 0) launch_guess_extrap(m->N, m->guess_ring, k_guess, m->guess_ext, m->v, m->a, m->dt, m->x, s);
   launch_cg_init(mv, m->b, m->v, m->a, m->x, m->q, m->partials, m->cg, s, k_guess > 0 ? 1 : 0);
-  launch_ebe(kModeA, mv, m->x, nullptr, nullptr, m->q, 0.0, 0, nullptr, m->cg, s);
+  launch_outer(m, kModeA, mv, m->x, nullptr, nullptr, m->q, 0.0, 0, nullptr, m->cg, s);
   launch_cg_residual(mv, m->b, m->q, m->r, m->z, m->p, m->dinv, m->partials, m->cg, s);
   const int chunk = m->opts.check_every > 0 ? m->opts.check_every : 8;
   int64_t launches = 5;  // rhs, init, A x0, residual (+ newmark and record below)
@@ -363,7 +378,7 @@ gsw_status step_fp64(gsw_ctx* ctx, Model* m) {
     m->ev_used = 0;
     for (int k = 0; k < chunk; ++k) {
       if (m->timing) CK(cudaEventRecord(m->ev[2 * k], s));
-      launch_ebe(kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, s);
+      launch_outer(m, kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, s);
       if (m->timing) {
         CK(cudaEventRecord(m->ev[2 * k + 1], s));
         m->ev_used = k + 1;
@@ -767,7 +782,7 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
   launch_cg_init_mixed(mv, m->w32, m->u, m->v, m->a, m->x, m->p, m->z, m->b, m->r, m->q, m->partials, m->cg, s,
                        nullptr, (learned || extrap) ? 1 : 0);
   // FP64 residual at the initial guess in one element-by-element pass
-  launch_ebe(kModeRes, mv, m->p, m->z, m->b, m->r, force, m->dir, nullptr, m->cg, s);
+  launch_outer(m, kModeRes, mv, m->p, m->z, m->b, m->r, force, m->dir, nullptr, m->cg, s);
   launch_cg_rnorm(mv, m->r, m->partials, m->cg, s);
   int64_t launches = 4;
   if ((m->timing || m->live_tune) && (int)m->ev_lo.size() < 2 * m->opts.inner_iters) {
@@ -817,7 +832,7 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
     }
     for (;;) {
       if (m->timing) CK(cudaEventRecord(m->ev[0], s));
-      launch_ebe(kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, s);
+      launch_outer(m, kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, s);
       if (m->timing) CK(cudaEventRecord(m->ev[1], s));
       launch_fcg_update(mv, m->x, m->r, m->p, m->q, m->partials, m->cg, s);
       launches += 2;
@@ -891,7 +906,7 @@ bool issue_outer_loop(Model* m, cudaStream_t s, StepState* ss, int outer, cudaSt
     inner_solve_dev(m, st);
     launch_fcg_zbeta(mv, m->y32, m->r, m->q, m->z, m->partials, m->cg, m->isc, st);
     launch_fcg_pupdate(mv, m->z, m->p, m->q, m->cg, st);
-    launch_ebe(kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, st);
+    launch_outer(m, kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, st);
     launch_fcg_update(mv, m->x, m->r, m->p, m->q, m->partials, m->cg, st);
   };
   if (bs == nullptr) {
@@ -948,11 +963,11 @@ bool issue_device_step(Model* m, cudaStream_t s, StepState* ss, int outer, cudaS
   if (k_guess > 0) launch_guess_extrap(m->N, m->guess_ring, k_guess, m->guess_ext, m->v, m->a, m->dt, m->x, s, ss);
   launch_cg_init_mixed(mv, m->w32, m->u, m->v, m->a, m->x, m->p, m->z, m->b, m->r, m->q, m->partials, m->cg, s, ss,
                        k_guess > 0 ? 1 : 0);
-  launch_ebe(kModeRes, mv, m->p, m->z, m->b, m->r, 0.0, m->dir, nullptr, m->cg, s, dr);
+  launch_outer(m, kModeRes, mv, m->p, m->z, m->b, m->r, 0.0, m->dir, nullptr, m->cg, s, dr);
   launch_cg_rnorm(mv, m->r, m->partials, m->cg, s);
   inner_solve_dev(m, s);
   launch_fcg_first(mv, m->y32, m->r, m->z, m->p, m->partials, m->cg, m->isc, s);
-  launch_ebe(kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, s);
+  launch_outer(m, kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, s);
   launch_fcg_update(mv, m->x, m->r, m->p, m->q, m->partials, m->cg, s);
   n->fixed += 6 + inner_launches + 3 + (k_guess > 0 ? 3 : 0);
   if (!issue_outer_loop(m, s, ss, outer, bs, n)) return false;
@@ -1247,8 +1262,10 @@ gsw_status gsw_set_solver(gsw_ctx* ctx, int32_t model_id, const gsw_solver_opts*
     return fail(ctx, GSW_E_INVALID, "inner_rtol must be in [0, 1)");
   if (opts->inner_variant < -1 || opts->inner_variant >= kLoVariants)
     return fail(ctx, GSW_E_INVALID, "inner_variant must be -1 (autotune) or 0..%d", kLoVariants - 1);
-  if (opts->guess_order < 0 || opts->guess_order > kMaxGuessOrder || opts->reserved != 0)
-    return fail(ctx, GSW_E_INVALID, "guess_order must be 0..%d (and reserved 0)", kMaxGuessOrder);
+  if (opts->guess_order < 0 || opts->guess_order > kMaxGuessOrder)
+    return fail(ctx, GSW_E_INVALID, "guess_order must be 0..%d", kMaxGuessOrder);
+  if (opts->outer_op < GSW_OUTER_AUTO || opts->outer_op > GSW_OUTER_DWORD)
+    return fail(ctx, GSW_E_INVALID, "outer_op must be 0 (auto), 1 (FP64) or 2 (double-word)");
   if (opts->guess_order > 0) {
     DeviceGuard g(ctx->device);
     if (!m->guess_ext) TRY(alloc_into(ctx, m, &m->guess_ext, 2));
@@ -1690,7 +1707,7 @@ gsw_status gsw_apply(gsw_ctx* ctx, int32_t model_id, int32_t which, const double
   Model* m = find(ctx, model_id);
   if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
   if (!m->time_set) return fail(ctx, GSW_E_STATE, "call gsw_set_time first");
-  if (which < 0 || which > 4) return fail(ctx, GSW_E_INVALID, "which must be 0..4");
+  if (which < 0 || which > 5) return fail(ctx, GSW_E_INVALID, "which must be 0..5");
   if (which == 4) {
     if (m->opts.precision == GSW_PREC_FP64 || !m->lo_ready)
       return fail(ctx, GSW_E_STATE, "the reduced-precision operator needs a mixed precision mode");
@@ -1702,6 +1719,11 @@ gsw_status gsw_apply(gsw_ctx* ctx, int32_t model_id, int32_t which, const double
     return GSW_OK;
   }
   CK(cudaMemsetAsync(y_dev, 0, sizeof(double) * 3 * (size_t)m->N, ctx->stream));
+  if (which == 5) {
+    launch_ebe_dw(kModeA, m->view(), x_dev, nullptr, nullptr, y_dev, 0.0, 0, nullptr, nullptr, ctx->stream);
+    CK(cudaGetLastError());
+    return GSW_OK;
+  }
   const int mode = which == 0 ? kModeA : which == 1 ? kModeK : which == 2 ? kModeM : kModeC;
   launch_ebe(mode, m->view(), x_dev, nullptr, nullptr, y_dev, 0.0, 0, nullptr, nullptr, ctx->stream);
   CK(cudaGetLastError());

@@ -19,6 +19,16 @@
 
 namespace gsw {
 
+// products with an exact float constant (overloaded for double-word values)
+template <typename T>
+__device__ __forceinline__ T kmul(float c, T x) {
+  return T(c) * x;
+}
+template <typename T>
+__device__ __forceinline__ T kfma(float c, T x, T y) {
+  return fma(T(c), x, y);
+}
+
 // edge index of the vertex pair (a, b), VTK order 01, 12, 02, 03, 13, 23
 __host__ __device__ constexpr int edge_of(int a, int b) {
   return (a + b == 1) ? 0 : (a + b == 3 ? (a * b == 2 ? 1 : 3) : (a + b == 2 ? 2 : (a + b == 4 ? 4 : 5)));
@@ -26,6 +36,45 @@ __host__ __device__ constexpr int edge_of(int a, int b) {
 __host__ __device__ constexpr int edge_a(int e) { return e == 0 ? 0 : e == 1 ? 1 : e == 2 ? 0 : e == 3 ? 0 : e == 4 ? 1 : 2; }
 __host__ __device__ constexpr int edge_b(int e) { return e == 0 ? 1 : e == 1 ? 2 : e == 2 ? 2 : e == 3 ? 3 : e == 4 ? 3 : 3; }
 __host__ __device__ constexpr int edge_opp(int e) { return e == 0 ? 5 : e == 1 ? 3 : e == 2 ? 4 : e == 3 ? 1 : e == 4 ? 2 : 0; }
+
+// T_km = S_k g_m (m = 0..3, g_0 = -(g_1 + g_2 + g_3)) at vertex k, from
+// U[b] = u_k (b == k) or u_edge(k, b) and D0[m] = u_{m+1} - u_0:
+// H_k = sum_{m=1..3} (4 (U[m] - U[0]) - D0[m-1]) (x) g_m, S_k its stress.
+template <typename T>
+__device__ __forceinline__ void vertex_traction(const T (&U)[4][3], const T (&D0)[3][3], const T (&g)[3][3],
+                                                T lamS, T muS, T mu2S, T (&Tk)[4][3]) {
+  T H[3][3];
+#pragma unroll
+  for (int m = 1; m < 4; ++m) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const T E = kfma(4.0f, U[m][i] - U[0][i], -D0[m - 1][i]);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        if (m == 1)
+          H[i][j] = E * g[0][j];
+        else
+          H[i][j] = fma(E, g[m - 1][j], H[i][j]);
+      }
+    }
+  }
+  const T tr = H[0][0] + H[1][1] + H[2][2];
+  const T lt = lamS * tr;
+  T S[3][3];
+  S[0][0] = fma(mu2S, H[0][0], lt);
+  S[1][1] = fma(mu2S, H[1][1], lt);
+  S[2][2] = fma(mu2S, H[2][2], lt);
+  S[0][1] = S[1][0] = muS * (H[0][1] + H[1][0]);
+  S[0][2] = S[2][0] = muS * (H[0][2] + H[2][0]);
+  S[1][2] = S[2][1] = muS * (H[1][2] + H[2][1]);
+#pragma unroll
+  for (int m = 1; m < 4; ++m)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      Tk[m][i] = fma(S[i][0], g[m - 1][0], fma(S[i][1], g[m - 1][1], S[i][2] * g[m - 1][2]));
+#pragma unroll
+  for (int i = 0; i < 3; ++i) Tk[0][i] = -(Tk[1][i] + Tk[2][i] + Tk[3][i]);
+}
 
 // y = K' w, K' = the element stiffness with lam, mu pre-scaled (lamS = s lam
 // V/20, muS = s mu V/20).  g[m] = grad L_{m+1}; grad L_0 = -(g0 + g1 + g2).
@@ -46,44 +95,15 @@ __device__ __forceinline__ void stiffness_apply(const T (&w)[10][3], const T (&g
   for (int e = 0; e < 6; ++e)
 #pragma unroll
     for (int i = 0; i < 3; ++i) cross[e][i] = T(0);
-  const T mu2S = T(2) * muS;
+  const T mu2S = kmul(2.0f, muS);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    // U(k, b) = u_k if b == k else u_{edge(k, b)}
-    T H[3][3];
+    T U[4][3], Tk[4][3];
 #pragma unroll
-    for (int m = 1; m < 4; ++m) {
+    for (int b = 0; b < 4; ++b)
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const T ukm = (m == k) ? w[k][i] : w[4 + edge_of(k, m)][i];
-        const T uk0 = (k == 0) ? w[0][i] : w[4 + edge_of(k, 0)][i];
-        const T E = fma(T(4.0), ukm - uk0, -D0[m - 1][i]);
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          if (m == 1)
-            H[i][j] = E * g[0][j];
-          else
-            H[i][j] = fma(E, g[m - 1][j], H[i][j]);
-        }
-      }
-    }
-    const T tr = H[0][0] + H[1][1] + H[2][2];
-    const T lt = lamS * tr;
-    T S[3][3];
-    S[0][0] = fma(mu2S, H[0][0], lt);
-    S[1][1] = fma(mu2S, H[1][1], lt);
-    S[2][2] = fma(mu2S, H[2][2], lt);
-    S[0][1] = S[1][0] = muS * (H[0][1] + H[1][0]);
-    S[0][2] = S[2][0] = muS * (H[0][2] + H[2][0]);
-    S[1][2] = S[2][1] = muS * (H[1][2] + H[2][1]);
-    T Tk[4][3];
-#pragma unroll
-    for (int m = 1; m < 4; ++m)
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-        Tk[m][i] = fma(S[i][0], g[m - 1][0], fma(S[i][1], g[m - 1][1], S[i][2] * g[m - 1][2]));
-#pragma unroll
-    for (int i = 0; i < 3; ++i) Tk[0][i] = -(Tk[1][i] + Tk[2][i] + Tk[3][i]);
+      for (int i = 0; i < 3; ++i) U[b][i] = (b == k) ? w[k][i] : w[4 + edge_of(k, b)][i];
+    vertex_traction(U, D0, g, lamS, muS, mu2S, Tk);
 #pragma unroll
     for (int m = 0; m < 4; ++m)
 #pragma unroll
@@ -99,12 +119,36 @@ __device__ __forceinline__ void stiffness_apply(const T (&w)[10][3], const T (&g
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int i = 0; i < 3; ++i) y[a][i] = fma(T(4.0), diagT[a][i], -sumT[a][i]);
+    for (int i = 0; i < 3; ++i) y[a][i] = kfma(4.0f, diagT[a][i], -sumT[a][i]);
 #pragma unroll
   for (int e = 0; e < 6; ++e)
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-      y[4 + e][i] = T(4) * (sumT[edge_a(e)][i] + sumT[edge_b(e)][i] + cross[e][i]);
+      y[4 + e][i] = kmul(4.0f, sumT[edge_a(e)][i] + sumT[edge_b(e)][i] + cross[e][i]);
+}
+
+// One displacement component: y += ms * P w (w, y: the 10 nodes' entries).
+template <typename T>
+__device__ __forceinline__ void mass_comp(const T (&w)[10], T ms, T (&y)[10]) {
+  const T Xv = (w[0] + w[1]) + (w[2] + w[3]);
+  const T Xe = (w[4] + w[5]) + (w[6] + w[7]) + (w[8] + w[9]);
+  const T tv = kfma(-6.0f, Xe, Xv);
+  const T te = kfma(16.0f, Xe, kmul(-6.0f, Xv));
+  // vertex a: 5 w_a + 2 (edges at a) + Xv - 6 Xe
+  const T P0 = kfma(5.0f, w[0], kfma(2.0f, w[4] + w[6] + w[7], tv));
+  const T P1 = kfma(5.0f, w[1], kfma(2.0f, w[4] + w[5] + w[8], tv));
+  const T P2 = kfma(5.0f, w[2], kfma(2.0f, w[5] + w[6] + w[9], tv));
+  const T P3 = kfma(5.0f, w[3], kfma(2.0f, w[7] + w[8] + w[9], tv));
+  y[0] = fma(ms, P0, y[0]);
+  y[1] = fma(ms, P1, y[1]);
+  y[2] = fma(ms, P2, y[2]);
+  y[3] = fma(ms, P3, y[3]);
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    const int a = edge_a(e), b = edge_b(e), o = edge_opp(e);
+    const T P = kfma(2.0f, w[a] + w[b], kfma(16.0f, w[4 + e], kfma(-8.0f, w[4 + o], te)));
+    y[4 + e] = fma(ms, P, y[4 + e]);
+  }
 }
 
 // y += ms * P w with P the consistent-mass pattern (ms = s rho V / 420).
@@ -112,25 +156,15 @@ template <typename T>
 __device__ __forceinline__ void mass_apply(const T (&w)[10][3], T ms, T (&y)[10][3]) {
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const T Xv = (w[0][i] + w[1][i]) + (w[2][i] + w[3][i]);
-    const T Xe = (w[4][i] + w[5][i]) + (w[6][i] + w[7][i]) + (w[8][i] + w[9][i]);
-    const T tv = fma(T(-6.0), Xe, Xv);
-    const T te = fma(T(16.0), Xe, T(-6.0) * Xv);
-    // vertex a: 5 w_a + 2 (edges at a) + Xv - 6 Xe
-    const T P0 = fma(T(5.0), w[0][i], fma(T(2.0), w[4][i] + w[6][i] + w[7][i], tv));
-    const T P1 = fma(T(5.0), w[1][i], fma(T(2.0), w[4][i] + w[5][i] + w[8][i], tv));
-    const T P2 = fma(T(5.0), w[2][i], fma(T(2.0), w[5][i] + w[6][i] + w[9][i], tv));
-    const T P3 = fma(T(5.0), w[3][i], fma(T(2.0), w[7][i] + w[8][i] + w[9][i], tv));
-    y[0][i] = fma(ms, P0, y[0][i]);
-    y[1][i] = fma(ms, P1, y[1][i]);
-    y[2][i] = fma(ms, P2, y[2][i]);
-    y[3][i] = fma(ms, P3, y[3][i]);
+    T wi[10], yi[10];
 #pragma unroll
-    for (int e = 0; e < 6; ++e) {
-      const int a = edge_a(e), b = edge_b(e), o = edge_opp(e);
-      const T P = fma(T(2.0), w[a][i] + w[b][i], fma(T(16.0), w[4 + e][i], fma(T(-8.0), w[4 + o][i], te)));
-      y[4 + e][i] = fma(ms, P, y[4 + e][i]);
+    for (int k = 0; k < 10; ++k) {
+      wi[k] = w[k][i];
+      yi[k] = y[k][i];
     }
+    mass_comp(wi, ms, yi);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) y[k][i] = yi[k];
   }
 }
 

@@ -158,6 +158,11 @@ void launch_receivers(const ModelView& m, const double* xyz, double px, double p
 void launch_ebe(int mode, const ModelView& m, const double* x, const double* v, const double* a,
                 double* y, double force, int dir, double* partials, CgScalars* cg,
                 cudaStream_t s, Drive dr = Drive{nullptr, nullptr});
+// The flexible CG's outer operator in double-word (paired FP32) arithmetic:
+// mode kModeA (with partials / cg as launch_ebe) or kModeRes.
+void launch_ebe_dw(int mode, const ModelView& m, const double* x, const double* v, const double* a,
+                   double* y, double force, int dir, double* partials, CgScalars* cg,
+                   cudaStream_t s, Drive dr = Drive{nullptr, nullptr});
 // Initial guess from the last k+1 increments (degree-k extrapolation), k <=
 // kMaxGuessOrder; ring: [k+1][3N] doubles, ext: {count, head} on the device.
 constexpr int kMaxGuessOrder = 6;

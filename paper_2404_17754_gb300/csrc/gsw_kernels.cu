@@ -24,6 +24,7 @@
 #include <stdint.h>
 
 #include "gsw_internal.cuh"
+#include "gsw_dword.cuh"
 #include "gsw_ebe.cuh"
 #include "gsw_reduce.cuh"
 
@@ -311,6 +312,64 @@ __global__ void receiver_weights_kernel(ModelView m, const double* __restrict__ 
 // Element-by-element operator
 // ------------------------------------------------------------------------------
 
+// Dashpot faces (threads E <= t < E + F) of the element-by-element operator,
+// FP64: the face term of A (scaled by 2/dt) in kModeA, the damping force of
+// the velocity plus the base force in kModeRhs / kModeRes.
+template <int MODE>
+__device__ __forceinline__ void face_apply(const ModelView& m, int64_t fc, const double* __restrict__ x,
+                                           const double* __restrict__ vv, double force, int dir, double* y,
+                                           double& dot) {
+  const double tag = m.fgeo[5 * m.F + fc];
+  if (tag > 0.5) {
+    const double sc = (MODE == kModeA) ? 2.0 / m.dt : 1.0;
+    const double As = sc * m.fgeo[fc] / 180.0, Ad = sc * m.fgeo[m.F + fc] / 180.0;
+    const double n[3] = {m.fgeo[2 * m.F + fc], m.fgeo[3 * m.F + fc], m.fgeo[4 * m.F + fc]};
+    int64_t nd[6];
+    double z[6][3], xin[6][3];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      nd[k] = m.fnode[k * m.F + fc];
+      const double* src = (MODE == kModeRhs || MODE == kModeRes) ? vv : x;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) xin[k][i] = src[3 * nd[k] + i];
+      const double dn = n[0] * xin[k][0] + n[1] * xin[k][1] + n[2] * xin[k][2];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) z[k][i] = fma(As, xin[k][i], Ad * dn * n[i]);
+    }
+    double yf[6][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const double Zv = z[0][i] + z[1][i] + z[2][i];
+      const double Ze = z[3][i] + z[4][i] + z[5][i];
+      // vertex a: 7 z_a - Zv - 4 z_(opposite edge); edge e: 16 z_e + 16 Ze - 4 z_(opposite vertex)
+      yf[0][i] = 7.0 * z[0][i] - Zv - 4.0 * z[4][i];
+      yf[1][i] = 7.0 * z[1][i] - Zv - 4.0 * z[5][i];
+      yf[2][i] = 7.0 * z[2][i] - Zv - 4.0 * z[3][i];
+      yf[3][i] = 16.0 * (z[3][i] + Ze) - 4.0 * z[2][i];
+      yf[4][i] = 16.0 * (z[4][i] + Ze) - 4.0 * z[0][i];
+      yf[5][i] = 16.0 * (z[5][i] + Ze) - 4.0 * z[1][i];
+    }
+    if ((MODE == kModeRhs || MODE == kModeRes) && tag < 1.5) {
+      // base force 2 p C_base e_dir: int N_a dA = A/3 at edge nodes, 0 at vertices
+      const double nd_ = dir == 0 ? n[0] : (dir == 1 ? n[1] : n[2]);
+      const double Af = m.fgeo[fc] / 180.0, Adf = m.fgeo[m.F + fc] / 180.0;
+      const double fz[3] = {Af * (dir == 0) + Adf * nd_ * n[0], Af * (dir == 1) + Adf * nd_ * n[1],
+                            Af * (dir == 2) + Adf * nd_ * n[2]};
+#pragma unroll
+      for (int k = 3; k < 6; ++k)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) yf[k][i] += force * 60.0 * fz[i];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        atomicAdd(y + 3 * nd[k] + i, yf[k][i]);
+        if (MODE == kModeA) dot = fma(xin[k][i], yf[k][i], dot);
+      }
+  }
+}
+
 // One thread per element (t < E) or boundary face (E <= t < E + F).
 //   kModeA   y = A x               (+ partial x.y when partials != nullptr)
 //   kModeK   y = K x,  kModeM y = M x,  kModeC y = C x
@@ -410,56 +469,160 @@ __global__ void __launch_bounds__(kElemThreads) ebe_kernel(ModelView m, const do
         if (MODE == kModeA) dot = fma(w[k][i], f[k][i], dot);
       }
   } else if (t < m.E + m.F && MODE != kModeK && MODE != kModeM) {
-    const int64_t fc = t - m.E;
-    const double tag = m.fgeo[5 * m.F + fc];
-    if (tag > 0.5) {
-      const double sc = (MODE == kModeA) ? 2.0 / m.dt : 1.0;
-      const double As = sc * m.fgeo[fc] / 180.0, Ad = sc * m.fgeo[m.F + fc] / 180.0;
-      const double n[3] = {m.fgeo[2 * m.F + fc], m.fgeo[3 * m.F + fc], m.fgeo[4 * m.F + fc]};
-      int64_t nd[6];
-      double z[6][3], xin[6][3];
+    face_apply<MODE>(m, t - m.E, x, vv, force, dir, y, dot);
+  }
+  if (MODE == kModeA && partials != nullptr) {
+    double vals[1] = {dot}, out[1];
+    if (last_block_reduce<1>(vals, partials, &cg->counter, out) && threadIdx.x == 0) cg->pq = out[0];
+  }
+}
+
+// The same operator for the flexible CG's outer iteration in double-word
+// arithmetic (gsw_dword.cuh): y = A x with the partial x . A x (kModeA), or
+// the residual at the initial guess (kModeRes).  Element data and state are
+// FP64 in memory; each element converts its inputs to double-word values
+// (bit operations), applies the same stiffness and mass formulas on the FP32
+// pipe and adds its 30 results to y as doubles.  Dashpot faces stay FP64.
+//
+// Double-word code is about ten FP32 instructions per FP64 operation, so the
+// element is laid out to keep the kernel's code and registers small: the
+// element's inputs and its per-vertex sums live in shared memory (one slot
+// column per thread), the four vertices run through one loop body (the
+// vertex's nodes are picked by index) and so do the three displacement
+// components of the output and mass stage.
+constexpr int kDwSlotW = 0;      // [30] stiffness input w, node k component i at 3k + i
+constexpr int kDwSlotDiag = 30;  // [12] 4 T_aa, vertex a
+constexpr int kDwSlotCross = 42; // [18] T_ab + T_ba, edge (a, b)
+constexpr int kDwSlots = 60;
+constexpr int kDwMinBlocks = 3;
+constexpr size_t kDwSmem = sizeof(float2) * kDwSlots * kElemThreads;
+
+template <int MODE>
+__global__ void __launch_bounds__(kElemThreads, kDwMinBlocks)
+    ebe_dw_kernel(ModelView m, const double* __restrict__ x, const double* __restrict__ vv,
+                  const double* __restrict__ aa, double* y, double force, int dir, double* partials,
+                  CgScalars* cg, Drive dr) {
+  static_assert(MODE == kModeA || MODE == kModeRes, "double-word operator: kModeA or kModeRes");
+  extern __shared__ float2 dsm[];  // [kDwSlots][kElemThreads]
+  if (cg != nullptr && ((volatile CgScalars*)cg)->done) return;
+  if (dr.ss != nullptr) {
+    if (!((volatile StepState*)dr.ss)->active) return;
+    force = 2.0 * dr.p[dr.ss->step];
+  }
+  float2* sl = dsm + threadIdx.x;
+  auto ld = [&](int q) {
+    const float2 v = sl[q * kElemThreads];
+    return dw(v.x, v.y);
+  };
+  auto st = [&](int q, dw v) { sl[q * kElemThreads] = make_float2(v.hi, v.lo); };
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double dot = 0.0;
+  if (t < m.E) {
+    const int64_t e = t;
+    int32_t nd[10];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        nd[k] = m.fnode[k * m.F + fc];
-        const double* src = (MODE == kModeRhs || MODE == kModeRes) ? vv : x;
+    for (int k = 0; k < 10; ++k) nd[k] = m.conn[k * m.E + e];
+    const MatCoef mc = m.mat[m.emat[e]];
+    // stiffness input: x (kModeA) or u~ - beta v~ (kModeRes)
+    const dw nbeta = to_dw(-mc.beta);
+    // two halves of five nodes: each half's gathers are issued together
+#pragma unroll 1
+    for (int h = 0; h < 10; h += 5) {
+      double xs[5][3], vs[5][3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) xin[k][i] = src[3 * nd[k] + i];
-        const double dn = n[0] * xin[k][0] + n[1] * xin[k][1] + n[2] * xin[k][2];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) z[k][i] = fma(As, xin[k][i], Ad * dn * n[i]);
-      }
-      double yf[6][3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const double Zv = z[0][i] + z[1][i] + z[2][i];
-        const double Ze = z[3][i] + z[4][i] + z[5][i];
-        // vertex a: 7 z_a - Zv - 4 z_(opposite edge); edge e: 16 z_e + 16 Ze - 4 z_(opposite vertex)
-        yf[0][i] = 7.0 * z[0][i] - Zv - 4.0 * z[4][i];
-        yf[1][i] = 7.0 * z[1][i] - Zv - 4.0 * z[5][i];
-        yf[2][i] = 7.0 * z[2][i] - Zv - 4.0 * z[3][i];
-        yf[3][i] = 16.0 * (z[3][i] + Ze) - 4.0 * z[2][i];
-        yf[4][i] = 16.0 * (z[4][i] + Ze) - 4.0 * z[0][i];
-        yf[5][i] = 16.0 * (z[5][i] + Ze) - 4.0 * z[1][i];
-      }
-      if ((MODE == kModeRhs || MODE == kModeRes) && tag < 1.5) {
-        // base force 2 p C_base e_dir: int N_a dA = A/3 at edge nodes, 0 at vertices
-        const double nd_ = dir == 0 ? n[0] : (dir == 1 ? n[1] : n[2]);
-        const double Af = m.fgeo[fc] / 180.0, Adf = m.fgeo[m.F + fc] / 180.0;
-        const double fz[3] = {Af * (dir == 0) + Adf * nd_ * n[0], Af * (dir == 1) + Adf * nd_ * n[1],
-                              Af * (dir == 2) + Adf * nd_ * n[2]};
-#pragma unroll
-        for (int k = 3; k < 6; ++k)
-#pragma unroll
-          for (int i = 0; i < 3; ++i) yf[k][i] += force * 60.0 * fz[i];
-      }
-#pragma unroll
-      for (int k = 0; k < 6; ++k)
+      for (int k = 0; k < 5; ++k) {
+        const int64_t n3 = 3 * (int64_t)m.conn[(h + k) * m.E + e];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-          atomicAdd(y + 3 * nd[k] + i, yf[k][i]);
-          if (MODE == kModeA) dot = fma(xin[k][i], yf[k][i], dot);
+          xs[k][i] = x[n3 + i];
+          if (MODE == kModeRes) vs[k][i] = vv[n3 + i];
         }
+      }
+#pragma unroll
+      for (int k = 0; k < 5; ++k)
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          st(kDwSlotW + 3 * (h + k) + i,
+             MODE == kModeRes ? fma(nbeta, to_dw(vs[k][i]), to_dw(xs[k][i])) : to_dw(xs[k][i]));
     }
+#pragma unroll
+    for (int q = 0; q < 18; ++q) st(kDwSlotCross + q, dw(0));
+    dw g[3][3];
+#pragma unroll
+    for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) g[mm][i] = to_dw(__ldg(m.geo + (3 * mm + i) * m.E + e));
+    const double V = __ldg(m.geo + 9 * m.E + e);
+    const double ks = (MODE == kModeA) ? mc.cK : -1.0;
+    const double ms = (MODE == kModeA) ? mc.cM : 1.0;
+    const dw lamS = to_dw(ks * mc.lam * V * (1.0 / 20.0)), muS = to_dw(ks * mc.mu * V * (1.0 / 20.0));
+    const dw mu2S = kmul(2.0f, muS);
+    const dw mS = to_dw(ms * mc.rho * V * (1.0 / 420.0));
+    dw D0[3][3];
+#pragma unroll
+    for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) D0[mm][i] = ld(kDwSlotW + 3 * (mm + 1) + i) - ld(kDwSlotW + i);
+    dw sumT[4][3];
+#pragma unroll
+    for (int mm = 0; mm < 4; ++mm)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) sumT[mm][i] = dw(0);
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+      dw U[4][3], Tk[4][3];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int nb = (b == k) ? k : 4 + edge_of(k, b);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) U[b][i] = ld(kDwSlotW + 3 * nb + i);
+      }
+      vertex_traction(U, D0, g, lamS, muS, mu2S, Tk);
+#pragma unroll
+      for (int mm = 0; mm < 4; ++mm)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) sumT[mm][i] += Tk[mm][i];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        if (b == k) {
+#pragma unroll
+          for (int i = 0; i < 3; ++i) st(kDwSlotDiag + 3 * b + i, kmul(4.0f, Tk[b][i]));
+        } else {
+          const int q = kDwSlotCross + 3 * edge_of(k, b);
+#pragma unroll
+          for (int i = 0; i < 3; ++i) st(q + i, ld(q + i) + Tk[b][i]);
+        }
+      }
+    }
+    // per component: vertex a 4 T_aa - T_a, edge (a, b) 4 (T_a + T_b + T_ab + T_ba), plus the mass
+    const dw ca = to_dw(mc.alpha);
+    dw dd(0);
+#pragma unroll 1
+    for (int i = 0; i < 3; ++i) {
+      dw sT[4], yi[10], wi[10];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) sT[a] = i == 0 ? sumT[a][0] : (i == 1 ? sumT[a][1] : sumT[a][2]);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) yi[a] = ld(kDwSlotDiag + 3 * a + i) - sT[a];
+#pragma unroll
+      for (int q = 0; q < 6; ++q)
+        yi[4 + q] = kmul(4.0f, sT[edge_a(q)] + sT[edge_b(q)] + ld(kDwSlotCross + 3 * q + i));
+#pragma unroll
+      for (int k = 0; k < 10; ++k) {
+        // mass input: x (kModeA) or a~ + alpha v~ (kModeRes)
+        const int64_t q = 3 * (int64_t)nd[k] + i;
+        wi[k] = MODE == kModeRes ? fma(ca, to_dw(vv[q]), to_dw(aa[q])) : ld(kDwSlotW + 3 * k + i);
+      }
+      mass_comp(wi, mS, yi);
+#pragma unroll
+      for (int k = 0; k < 10; ++k) {
+        atomicAdd(y + 3 * (int64_t)nd[k] + i, to_double(yi[k]));
+        if (MODE == kModeA) dd = fma(wi[k], yi[k], dd);
+      }
+    }
+    if (MODE == kModeA) dot = to_double(dd);
+  } else if (t < m.E + m.F) {
+    face_apply<MODE>(m, t - m.E, x, vv, force, dir, y, dot);
   }
   if (MODE == kModeA && partials != nullptr) {
     double vals[1] = {dot}, out[1];
@@ -758,6 +921,21 @@ void launch_ebe(int mode, const ModelView& m, const double* x, const double* v, 
       ebe_kernel<kModeRhs><<<nb, kElemThreads, 0, s>>>(m, x, v, a, y, force, dir, nullptr, nullptr, dr);
       break;
   }
+}
+void launch_ebe_dw(int mode, const ModelView& m, const double* x, const double* v, const double* a,
+                   double* y, double force, int dir, double* partials, CgScalars* cg, cudaStream_t s, Drive dr) {
+  const int nb = ebe_blocks(m);
+  if (nb == 0) return;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(ebe_dw_kernel<kModeA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDwSmem);
+    cudaFuncSetAttribute(ebe_dw_kernel<kModeRes>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDwSmem);
+    attr_set = true;
+  }
+  if (mode == kModeA)
+    ebe_dw_kernel<kModeA><<<nb, kElemThreads, kDwSmem, s>>>(m, x, v, a, y, force, dir, partials, cg, dr);
+  else
+    ebe_dw_kernel<kModeRes><<<nb, kElemThreads, kDwSmem, s>>>(m, x, v, a, y, force, dir, nullptr, nullptr, dr);
 }
 void launch_cg_init(const ModelView& m, const double* b, const double* v, const double* a,
                     double* x, double* q, double* partials, CgScalars* cg, cudaStream_t s, int use_guess) {

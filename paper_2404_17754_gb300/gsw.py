@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libgsw.so")
 
 OK, E_INVALID, E_CUDA, E_NOMEM, E_NOCONV, E_NAN, E_TIMEOUT, E_STATE = 0, -1, -2, -3, -4, -5, -6, -7
 PREC_FP64, PREC_FP32, PREC_FP16 = 0, 1, 2
+OUTER_AUTO, OUTER_FP64, OUTER_DWORD = 0, 1, 2
 _STATUS = {E_INVALID: "GSW_E_INVALID", E_CUDA: "GSW_E_CUDA", E_NOMEM: "GSW_E_NOMEM",
            E_NOCONV: "GSW_E_NOCONV", E_NAN: "GSW_E_NAN", E_TIMEOUT: "GSW_E_TIMEOUT",
            E_STATE: "GSW_E_STATE"}
@@ -31,7 +32,7 @@ class SolverOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("precision", C.c_int32),
                 ("inner_iters", C.c_int32), ("check_every", C.c_int32), ("batch_outer", C.c_int32),
                 ("inner_variant", C.c_int32), ("inner_rtol", C.c_double), ("guess_order", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("outer_op", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -280,9 +281,9 @@ class Model:
         self._c(self.ctx.lib.gsw_set_input(self.ctx.h, self.id, int(direction), pp, p.shape[0]))
 
     def set_solver(self, tol=1e-8, max_iter=10000, precision=PREC_FP64, inner_iters=20, check_every=8,
-                   batch_outer=6, inner_variant=-1, inner_rtol=0.0, guess_order=0):
+                   batch_outer=6, inner_variant=-1, inner_rtol=0.0, guess_order=0, outer_op=OUTER_AUTO):
         o = SolverOpts(tol, max_iter, precision, inner_iters, check_every, batch_outer, inner_variant, inner_rtol,
-                       guess_order, 0)
+                       guess_order, outer_op)
         self._c(self.ctx.lib.gsw_set_solver(self.ctx.h, self.id, C.byref(o)))
 
     def reset(self):
@@ -341,7 +342,8 @@ class Model:
         self._c(self.ctx.lib.gsw_set_state(self.ctx.h, self.id, pu, pv, pa, int(step)))
 
     def apply(self, which, x):
-        """y = A x (0), K x (1), M x (2), C x (3), or A x by the inner reduced-precision operator (4)."""
+        """y = A x (0), K x (1), M x (2), C x (3), A x by the inner reduced-precision operator (4), or A x
+        in double-word arithmetic (5)."""
         torch = self.ctx._torch
         assert x.is_cuda and x.dtype == torch.float64 and x.is_contiguous() and x.numel() == 3 * self.n_nodes
         y = torch.empty_like(x)
