@@ -92,6 +92,36 @@ __device__ __forceinline__ dw fma(dw a, dw b, dw c) {
   return fast_two_sum(s, t);
 }
 
+// Unnormalised variants for intermediate results that feed another
+// double-word operation at once: the final Fast2Sum is skipped, so lo may
+// exceed half an ulp of hi (it stays below about 2^-22 |hi| unless the sum
+// cancels, and then its error is still bounded by the operands' magnitudes).
+// Every operation above accepts such a pair as input.
+__device__ __forceinline__ dw add_u(dw a, dw b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return dw(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ dw sub_u(dw a, dw b) { return add_u(a, -b); }
+
+__device__ __forceinline__ dw mul_u(dw a, dw b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  return dw(p, __fmaf_rn(a.lo, b.hi, e));
+}
+
+__device__ __forceinline__ dw fma_u(dw a, dw b, dw c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  float s, t;
+  two_sum(p, c.hi, s, t);
+  return dw(s, __fadd_rn(t, __fadd_rn(e, c.lo)));
+}
+
 // ---- products with an exact float constant ----------------------------------------
 
 __host__ __device__ constexpr bool pow2_const(float c) {
@@ -123,6 +153,22 @@ __device__ __forceinline__ dw kfma(float c, dw x, dw y) {
   two_sum(p, y.hi, s, t);
   t = __fadd_rn(t, __fadd_rn(e, y.lo));
   return fast_two_sum(s, t);
+}
+
+// c x + y, unnormalised
+__device__ __forceinline__ dw kfma_u(float c, dw x, dw y) {
+  float p, e;
+  if (pow2_const(c)) {
+    p = __fmul_rn(c, x.hi);
+    e = __fmul_rn(c, x.lo);
+  } else {
+    p = __fmul_rn(c, x.hi);
+    e = __fmaf_rn(c, x.hi, -p);
+    e = __fmaf_rn(c, x.lo, e);
+  }
+  float s, t;
+  two_sum(p, y.hi, s, t);
+  return dw(s, __fadd_rn(t, __fadd_rn(e, y.lo)));
 }
 
 // ---- conversions ------------------------------------------------------------------
