@@ -31,7 +31,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
-EBE_FLOPS_PER_ELEM = 1088      # A-mode EBE with the p.Ap partial
+ISSUE_PEAK = 152 * 4 * 32 * 2.07e9  # thread instructions/s: 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz
+EBE_FLOPS_PER_ELEM = 1088      # A-mode element: vertex-gradient stiffness, consistent mass, p.Ap partial
 EBE_FLOPS_PER_FACE = 150
 # algorithmic bytes of one FP64 A p launch: x, y (read + write) once per DOF,
 # connectivity + material id + geometry once per element
@@ -155,6 +156,7 @@ LO_KERNELS = {0: "ebe_lo_kernel<., ., 1>", 1: "ebe_lo_kernel<., ., 4>", 2: "ebe_
               3: "ebe_lo_ws_kernel"}
 FP64_SOURCES = ["gsw_kernels.cu", "gsw_ebe.cuh", "gsw_reduce.cuh", "gsw_internal.cuh"]
 INNER_SOURCES = ["gsw_mixed.cu", "gsw_ebe.cuh", "gsw_reduce.cuh", "gsw_internal.cuh"]
+DW_SOURCES = ["gsw_kernels.cu", "gsw_ebe.cuh", "gsw_dword.cuh", "gsw_reduce.cuh", "gsw_internal.cuh"]
 
 
 def source_hash(files):
@@ -165,18 +167,23 @@ def source_hash(files):
     return h.hexdigest()
 
 
-def traffic_from_profile(files, summary):
-    """Per-launch DRAM bytes from the committed ncu summary, if the kernel source is unchanged."""
+def profile_value(files, summary, key):
+    """A figure of a committed ncu summary, if the kernel source is unchanged since the capture."""
     path = os.path.join(ROOT, "profiles", summary)
     try:
         text = open(path).read()
     except OSError:
         return None
-    m1 = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m1 = re.search(key + r":\s*([0-9.eE+]+)", text)
     m2 = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
     if not (m1 and m2):
         return None
     return float(m1.group(1)) if source_hash(files).startswith(m2.group(1)) else None
+
+
+def traffic_from_profile(files, summary):
+    """Per-launch DRAM bytes from the committed ncu summary, if the kernel source is unchanged."""
+    return profile_value(files, summary, "traffic_bytes_per_launch")
 
 
 def run_reference(args, rank):
@@ -277,6 +284,7 @@ def run_candidates(args, rank, world, dist):
                        "dof_total": dof, "dof_steps_per_s": world * dof * args.steps / t_max, "tol": args.tol,
                        "precision": args.precision, "inner_iters": args.inner, "batch_outer": args.batch_outer,
                        "guess_order": args.guess_order,
+                       "outer_operator": "FP64" if args.outer_op == "fp64" or (args.outer_op == "auto" and args.precision == "fp64") else "double-word",
                        "outer_iters_per_model_step": iters / (args.steps * args.models),
                        "graph_kernel_nodes_captured": lps,
                        "l2": "inputs larger than L2 (%.1f GB resident)" % (sum(m.info()["device_bytes"] for m in models) / 1e9)},
@@ -507,14 +515,30 @@ def main():
     flops = EBE_FLOPS_PER_ELEM * n_elem + EBE_FLOPS_PER_FACE * n_abs
     achieved_tf = flops / per_launch_s / 1e12 if ebe_n else None
     nbytes = ebe_bytes(n_nodes, n_elem, n_faces)
-    fp64_roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                 "frac": (achieved_tf / FP64_PEAK_TFLOPS) if achieved_tf else None,
-                 "traffic": traffic_from_profile(FP64_SOURCES, "ebe_fp64_realistic.md"),
-                 "kernel": "ebe_kernel<0> (FP64 element-by-element A p)",
-                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FP64 pipe; a DFMA probe "
-                                "measured 1.20 TFLOP/s at 2.0 GHz)",
-                 "flops_per_launch": flops, "launch_ms": per_launch_s * 1e3, "launches_timed": ebe_n,
-                 "time_share": ebe_ms / (1e3 * t_roof), "algorithmic_bytes": nbytes}
+    dword = args.outer_op == "dword" or (args.outer_op == "auto" and args.precision != "fp64")
+    if dword:
+        # issue-bound on the FP32 pipe: the peak is the instruction issue rate divided by the
+        # instructions the double-word element needs per algorithmic flop (ncu count, same source)
+        ipe = profile_value(DW_SOURCES, "ebe_dw_realistic.md", "thread_instructions_per_element")
+        peak_tf = ISSUE_PEAK * EBE_FLOPS_PER_ELEM / ipe / 1e12 if ipe else None
+        fp64_roof = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                     "frac": (achieved_tf / peak_tf) if (achieved_tf and peak_tf) else None,
+                     "traffic": traffic_from_profile(DW_SOURCES, "ebe_dw_realistic.md"),
+                     "kernel": "ebe_dw_kernel<0> (double-word element-by-element A p, FP32 pipe)",
+                     "peak_source": "derived: instruction issue 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz / "
+                                    "%s thread instructions per element (ncu) x %d flop per element" % (
+                                        "%.0f" % ipe if ipe else "?", EBE_FLOPS_PER_ELEM),
+                     "flops_per_launch": flops, "launch_ms": per_launch_s * 1e3, "launches_timed": ebe_n,
+                     "time_share": ebe_ms / (1e3 * t_roof), "algorithmic_bytes": nbytes}
+    else:
+        fp64_roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": (achieved_tf / FP64_PEAK_TFLOPS) if achieved_tf else None,
+                     "traffic": traffic_from_profile(FP64_SOURCES, "ebe_fp64_realistic.md"),
+                     "kernel": "ebe_kernel<0> (FP64 element-by-element A p)",
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FP64 pipe; a DFMA probe "
+                                    "measured 1.20 TFLOP/s at 2.0 GHz)",
+                     "flops_per_launch": flops, "launch_ms": per_launch_s * 1e3, "launches_timed": ebe_n,
+                     "time_share": ebe_ms / (1e3 * t_roof), "algorithmic_bytes": nbytes}
     inner_roof = None
     if lo_n:
         lo_launch_s = (lo_ms / 1e3) / lo_n
@@ -553,6 +577,7 @@ def main():
         "config": {"workload": cfg["name"] if args.workload == "realistic" else "two-layer 100x100x50 m",
                    "dof": dof, "elements": n_elem, "dt": cfg["dt"], "tol": args.tol, "precision": args.precision,
                    "guess_order": args.guess_order,
+                   "outer_operator": "FP64" if args.outer_op == "fp64" or (args.outer_op == "auto" and args.precision == "fp64") else "double-word",
                    "solver": "block-Jacobi PCG" if args.precision == "fp64" else
                              ("flexible CG (FP64) + %s block-Jacobi PCG preconditioner, %d iterations" % (
                                  args.precision, args.inner) if args.inner_rtol <= 0 else

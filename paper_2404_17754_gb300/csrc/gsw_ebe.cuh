@@ -71,7 +71,7 @@ __device__ __forceinline__ void vertex_traction(const T (&U)[4][3], const T (&D0
   for (int m = 1; m < 4; ++m) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      const T E = kfma(4.0f, sub_u(U[m][i], U[0][i]), -D0[m - 1][i]);
+      const T E = kfma_u(4.0f, sub_u(U[m][i], U[0][i]), -D0[m - 1][i]);
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         if (m == 1)
@@ -79,26 +79,26 @@ __device__ __forceinline__ void vertex_traction(const T (&U)[4][3], const T (&D0
         else if (m == 2)
           H[i][j] = fma_u(E, g[m - 1][j], H[i][j]);
         else
-          H[i][j] = fma(E, g[m - 1][j], H[i][j]);
+          H[i][j] = fma_u(E, g[m - 1][j], H[i][j]);
       }
     }
   }
-  const T tr = add_u(H[0][0], H[1][1]) + H[2][2];
-  const T lt = lamS * tr;
+  const T tr = add_u(add_u(H[0][0], H[1][1]), H[2][2]);
+  const T lt = mul_u(lamS, tr);
   T S[3][3];
-  S[0][0] = fma(mu2S, H[0][0], lt);
-  S[1][1] = fma(mu2S, H[1][1], lt);
-  S[2][2] = fma(mu2S, H[2][2], lt);
-  S[0][1] = S[1][0] = muS * add_u(H[0][1], H[1][0]);
-  S[0][2] = S[2][0] = muS * add_u(H[0][2], H[2][0]);
-  S[1][2] = S[2][1] = muS * add_u(H[1][2], H[2][1]);
+  S[0][0] = fma_u(mu2S, H[0][0], lt);
+  S[1][1] = fma_u(mu2S, H[1][1], lt);
+  S[2][2] = fma_u(mu2S, H[2][2], lt);
+  S[0][1] = S[1][0] = mul_u(muS, add_u(H[0][1], H[1][0]));
+  S[0][2] = S[2][0] = mul_u(muS, add_u(H[0][2], H[2][0]));
+  S[1][2] = S[2][1] = mul_u(muS, add_u(H[1][2], H[2][1]));
 #pragma unroll
   for (int m = 1; m < 4; ++m)
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-      Tk[m][i] = fma(S[i][0], g[m - 1][0], fma_u(S[i][1], g[m - 1][1], mul_u(S[i][2], g[m - 1][2])));
+      Tk[m][i] = fma_u(S[i][0], g[m - 1][0], fma_u(S[i][1], g[m - 1][1], mul_u(S[i][2], g[m - 1][2])));
 #pragma unroll
-  for (int i = 0; i < 3; ++i) Tk[0][i] = -(add_u(Tk[1][i], Tk[2][i]) + Tk[3][i]);
+  for (int i = 0; i < 3; ++i) Tk[0][i] = -add_u(add_u(Tk[1][i], Tk[2][i]), Tk[3][i]);
 }
 
 // y = K' w, K' = the element stiffness with lam, mu pre-scaled (lamS = s lam
@@ -155,24 +155,24 @@ __device__ __forceinline__ void stiffness_apply(const T (&w)[10][3], const T (&g
 // One displacement component: y += ms * P w (w, y: the 10 nodes' entries).
 template <typename T>
 __device__ __forceinline__ void mass_comp(const T (&w)[10], T ms, T (&y)[10]) {
-  const T Xv = add_u(w[0], w[1]) + add_u(w[2], w[3]);
-  const T Xe = add_u(add_u(w[4], w[5]), add_u(w[6], w[7])) + add_u(w[8], w[9]);
-  const T tv = kfma(-6.0f, Xe, Xv);
-  const T te = kfma(16.0f, Xe, kmul(-6.0f, Xv));
+  const T Xv = add_u(add_u(w[0], w[1]), add_u(w[2], w[3]));
+  const T Xe = add_u(add_u(add_u(w[4], w[5]), add_u(w[6], w[7])), add_u(w[8], w[9]));
+  const T tv = kfma_u(-6.0f, Xe, Xv);
+  const T te = kfma_u(16.0f, Xe, kmul(-6.0f, Xv));
   // vertex a: 5 w_a + 2 (edges at a) + Xv - 6 Xe
-  const T P0 = kfma(5.0f, w[0], kfma_u(2.0f, add_u(add_u(w[4], w[6]), w[7]), tv));
-  const T P1 = kfma(5.0f, w[1], kfma_u(2.0f, add_u(add_u(w[4], w[5]), w[8]), tv));
-  const T P2 = kfma(5.0f, w[2], kfma_u(2.0f, add_u(add_u(w[5], w[6]), w[9]), tv));
-  const T P3 = kfma(5.0f, w[3], kfma_u(2.0f, add_u(add_u(w[7], w[8]), w[9]), tv));
-  y[0] = fma(ms, P0, y[0]);
-  y[1] = fma(ms, P1, y[1]);
-  y[2] = fma(ms, P2, y[2]);
-  y[3] = fma(ms, P3, y[3]);
+  const T P0 = kfma_u(5.0f, w[0], kfma_u(2.0f, add_u(add_u(w[4], w[6]), w[7]), tv));
+  const T P1 = kfma_u(5.0f, w[1], kfma_u(2.0f, add_u(add_u(w[4], w[5]), w[8]), tv));
+  const T P2 = kfma_u(5.0f, w[2], kfma_u(2.0f, add_u(add_u(w[5], w[6]), w[9]), tv));
+  const T P3 = kfma_u(5.0f, w[3], kfma_u(2.0f, add_u(add_u(w[7], w[8]), w[9]), tv));
+  y[0] = fma_u(ms, P0, y[0]);
+  y[1] = fma_u(ms, P1, y[1]);
+  y[2] = fma_u(ms, P2, y[2]);
+  y[3] = fma_u(ms, P3, y[3]);
 #pragma unroll
   for (int e = 0; e < 6; ++e) {
     const int a = edge_a(e), b = edge_b(e), o = edge_opp(e);
-    const T P = kfma(2.0f, add_u(w[a], w[b]), kfma_u(16.0f, w[4 + e], kfma_u(-8.0f, w[4 + o], te)));
-    y[4 + e] = fma(ms, P, y[4 + e]);
+    const T P = kfma_u(2.0f, add_u(w[a], w[b]), kfma_u(16.0f, w[4 + e], kfma_u(-8.0f, w[4 + o], te)));
+    y[4 + e] = fma_u(ms, P, y[4 + e]);
   }
 }
 

@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(kElemThreads, kDwMinBlocks)
 #pragma unroll
         for (int i = 0; i < 3; ++i)
           st(kDwSlotW + 3 * (h + k) + i,
-             MODE == kModeRes ? fma(nbeta, to_dw(vs[k][i]), to_dw(xs[k][i])) : to_dw(xs[k][i]));
+             MODE == kModeRes ? fma_u(nbeta, to_dw(vs[k][i]), to_dw(xs[k][i])) : to_dw(xs[k][i]));
     }
 #pragma unroll
     for (int q = 0; q < 18; ++q) st(kDwSlotCross + q, dw(0));
@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(kElemThreads, kDwMinBlocks)
 #pragma unroll
     for (int mm = 0; mm < 3; ++mm)
 #pragma unroll
-      for (int i = 0; i < 3; ++i) D0[mm][i] = ld(kDwSlotW + 3 * (mm + 1) + i) - ld(kDwSlotW + i);
+      for (int i = 0; i < 3; ++i) D0[mm][i] = sub_u(ld(kDwSlotW + 3 * (mm + 1) + i), ld(kDwSlotW + i));
     dw sumT[4][3];
 #pragma unroll
     for (int mm = 0; mm < 4; ++mm)
@@ -581,7 +581,7 @@ __global__ void __launch_bounds__(kElemThreads, kDwMinBlocks)
 #pragma unroll
       for (int mm = 0; mm < 4; ++mm)
 #pragma unroll
-        for (int i = 0; i < 3; ++i) sumT[mm][i] += Tk[mm][i];
+        for (int i = 0; i < 3; ++i) sumT[mm][i] = add_u(sumT[mm][i], Tk[mm][i]);
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         if (b == k) {
@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(kElemThreads, kDwMinBlocks)
         } else {
           const int q = kDwSlotCross + 3 * edge_of(k, b);
 #pragma unroll
-          for (int i = 0; i < 3; ++i) st(q + i, ld(q + i) + Tk[b][i]);
+          for (int i = 0; i < 3; ++i) st(q + i, add_u(ld(q + i), Tk[b][i]));
         }
       }
     }
@@ -603,21 +603,21 @@ __global__ void __launch_bounds__(kElemThreads, kDwMinBlocks)
 #pragma unroll
       for (int a = 0; a < 4; ++a) sT[a] = i == 0 ? sumT[a][0] : (i == 1 ? sumT[a][1] : sumT[a][2]);
 #pragma unroll
-      for (int a = 0; a < 4; ++a) yi[a] = ld(kDwSlotDiag + 3 * a + i) - sT[a];
+      for (int a = 0; a < 4; ++a) yi[a] = sub_u(ld(kDwSlotDiag + 3 * a + i), sT[a]);
 #pragma unroll
       for (int q = 0; q < 6; ++q)
-        yi[4 + q] = kmul(4.0f, sT[edge_a(q)] + sT[edge_b(q)] + ld(kDwSlotCross + 3 * q + i));
+        yi[4 + q] = kmul(4.0f, add_u(add_u(sT[edge_a(q)], sT[edge_b(q)]), ld(kDwSlotCross + 3 * q + i)));
 #pragma unroll
       for (int k = 0; k < 10; ++k) {
         // mass input: x (kModeA) or a~ + alpha v~ (kModeRes)
         const int64_t q = 3 * (int64_t)nd[k] + i;
-        wi[k] = MODE == kModeRes ? fma(ca, to_dw(vv[q]), to_dw(aa[q])) : ld(kDwSlotW + 3 * k + i);
+        wi[k] = MODE == kModeRes ? fma_u(ca, to_dw(vv[q]), to_dw(aa[q])) : ld(kDwSlotW + 3 * k + i);
       }
       mass_comp(wi, mS, yi);
 #pragma unroll
       for (int k = 0; k < 10; ++k) {
         atomicAdd(y + 3 * (int64_t)nd[k] + i, to_double(yi[k]));
-        if (MODE == kModeA) dd = fma(wi[k], yi[k], dd);
+        if (MODE == kModeA) dd = fma_u(wi[k], yi[k], dd);
       }
     }
     if (MODE == kModeA) dot = to_double(dd);
