@@ -638,9 +638,9 @@ __global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __r
     alpha = ((volatile const InnerScalars*)sc)->alpha_f;
   }
   float st = 0.f;
-  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t g0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t G4 = N >> 2;
-  if (g < G4) {
+  for (int64_t g = g0; g < G4; g += (int64_t)gridDim.x * blockDim.x) {
     float yv[12], sv[12], wv[12], tv[16], dv[16], Dv[24];
     ldq<3>(y + 12 * g, yv);
     ldq<3>(s + 12 * g, sv);
@@ -664,7 +664,8 @@ __global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __r
     stq<3>(s + 12 * g, sv);
     stq<4>(t + 16 * g, tv);
     stq<3>(w + 12 * g, zero);
-  } else if (g == G4) {
+  }
+  if (g0 == 0) {  // the last N mod 4 nodes
     for (int64_t n = 4 * G4; n < N; ++n) {
       float sn[3], tn[3];
 #pragma unroll
@@ -703,9 +704,9 @@ __global__ void inner_dupdate_kernel(int64_t N, const float* __restrict__ t, SD*
                                      const InnerScalars* sc, const CgScalars* outer) {
   if (inner_stopped(outer, sc)) return;
   const float beta = ((volatile const InnerScalars*)sc)->beta_f;
-  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t g0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t G4 = N >> 2;
-  if (g < G4) {
+  for (int64_t g = g0; g < G4; g += (int64_t)gridDim.x * blockDim.x) {
     float tv[16], dv[16];
     ldq<4>(t + 16 * g, tv);
     ld_dir(d + 16 * g, dv);
@@ -714,7 +715,8 @@ __global__ void inner_dupdate_kernel(int64_t N, const float* __restrict__ t, SD*
 #pragma unroll
       for (int i = 0; i < 3; ++i) dv[4 * q + i] = fmaf(beta, dv[4 * q + i], tv[4 * q + i]);
     st_dir(d + 16 * g, dv);
-  } else if (g == G4) {
+  }
+  if (g0 == 0) {
     for (int64_t n = 4 * G4; n < N; ++n)
 #pragma unroll
       for (int i = 0; i < 3; ++i) d[4 * n + i] = from_f<SD>(fmaf(beta, to_f(d[4 * n + i]), t[4 * n + i]));
@@ -1719,32 +1721,54 @@ void launch_rhs_lo(int half_geo, const void* lo_view, int64_t N, const double* u
 }
 
 static unsigned quad_blocks(int64_t N) { return (unsigned)(((N >> 2) + 1 + kNodeThreads - 1) / kNodeThreads); }
+// Persistent grid of the node-quad kernels: the SMs times the CTAs that fit on
+// one, so a CTA walks many quads and forms its reduction partial once.
+static unsigned persistent_cap(const void* kernel) {
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kNodeThreads, 0);
+  return (unsigned)((sms > 0 ? sms : 1) * (occ > 0 ? occ : 1));
+}
+static unsigned quad_grid(int64_t N, unsigned cap) {
+  const unsigned b = quad_blocks(N);
+  return b < cap ? b : cap;
+}
 void launch_inner_update(int64_t N, float* y, float* s, float* t, const void* d, int half_vec, float* w,
                          const float* dinv32, const float* dw_part, double* partials, InnerScalars* sc,
                          cudaStream_t st, const CgScalars* outer, int n_dw_max) {
   if (n_dw_max <= kAlphaPrologueMax) {
-    if (half_vec)
-      inner_update_kernel<__half, true><<<quad_blocks(N), kNodeThreads, 0, st>>>(
+    if (half_vec) {
+      static const unsigned cap = persistent_cap((const void*)inner_update_kernel<__half, true>);
+      inner_update_kernel<__half, true><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(
           N, y, s, t, (const __half*)d, w, dinv32, partials, sc, outer, dw_part);
-    else
-      inner_update_kernel<float, true><<<quad_blocks(N), kNodeThreads, 0, st>>>(
+    } else {
+      static const unsigned cap = persistent_cap((const void*)inner_update_kernel<float, true>);
+      inner_update_kernel<float, true><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(
           N, y, s, t, (const float*)d, w, dinv32, partials, sc, outer, dw_part);
+    }
     return;
   }
   inner_alpha_kernel<<<1, 1024, 0, st>>>(dw_part, sc, outer);
-  if (half_vec)
-    inner_update_kernel<__half><<<quad_blocks(N), kNodeThreads, 0, st>>>(N, y, s, t, (const __half*)d, w, dinv32,
-                                                                         partials, sc, outer);
-  else
-    inner_update_kernel<float><<<quad_blocks(N), kNodeThreads, 0, st>>>(N, y, s, t, (const float*)d, w, dinv32,
-                                                                        partials, sc, outer);
+  if (half_vec) {
+    static const unsigned cap = persistent_cap((const void*)inner_update_kernel<__half>);
+    inner_update_kernel<__half><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(N, y, s, t, (const __half*)d, w, dinv32,
+                                                                            partials, sc, outer);
+  } else {
+    static const unsigned cap = persistent_cap((const void*)inner_update_kernel<float>);
+    inner_update_kernel<float><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(N, y, s, t, (const float*)d, w, dinv32,
+                                                                           partials, sc, outer);
+  }
 }
 void launch_inner_dupdate(int64_t N, const float* t, void* d, int half_vec, const InnerScalars* sc,
                           cudaStream_t st, const CgScalars* outer) {
-  if (half_vec)
-    inner_dupdate_kernel<__half><<<quad_blocks(N), kNodeThreads, 0, st>>>(N, t, (__half*)d, sc, outer);
-  else
-    inner_dupdate_kernel<float><<<quad_blocks(N), kNodeThreads, 0, st>>>(N, t, (float*)d, sc, outer);
+  if (half_vec) {
+    static const unsigned cap = persistent_cap((const void*)inner_dupdate_kernel<__half>);
+    inner_dupdate_kernel<__half><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(N, t, (__half*)d, sc, outer);
+  } else {
+    static const unsigned cap = persistent_cap((const void*)inner_dupdate_kernel<float>);
+    inner_dupdate_kernel<float><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(N, t, (float*)d, sc, outer);
+  }
 }
 void launch_fcg_residual(const ModelView& m, const double* b, double* q, double* r, double* partials, CgScalars* cg,
                          cudaStream_t s) {
