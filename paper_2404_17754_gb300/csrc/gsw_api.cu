@@ -342,8 +342,9 @@ bool outer_dword(const Model* m) {
 void launch_outer(const Model* m, int mode, const ModelView& mv, const double* x, const double* v, const double* a,
                   double* y, double force, int dir, double* partials, CgScalars* cg, cudaStream_t s,
                   Drive dr = Drive{nullptr, nullptr}) {
+  // the mixed modes keep the search direction and the shifted state as double-word pairs
   if (outer_dword(m))
-    launch_ebe_dw(mode, mv, x, v, a, y, force, dir, partials, cg, s, dr);
+    launch_ebe_dw(mode, m->opts.precision != GSW_PREC_FP64 ? 1 : 0, mv, x, v, a, y, force, dir, partials, cg, s, dr);
   else
     launch_ebe(mode, mv, x, v, a, y, force, dir, partials, cg, s, dr);
 }
@@ -780,7 +781,7 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
   else if (extrap)
     launch_guess_extrap(m->N, m->guess_ring, m->opts.guess_order, m->guess_ext, m->v, m->a, m->dt, m->x, s);
   launch_cg_init_mixed(mv, m->w32, m->u, m->v, m->a, m->x, m->p, m->z, m->b, m->r, m->q, m->partials, m->cg, s,
-                       nullptr, (learned || extrap) ? 1 : 0);
+                       nullptr, (learned || extrap) ? 1 : 0, outer_dword(m) ? 1 : 0);
   // FP64 residual at the initial guess in one element-by-element pass
   launch_outer(m, kModeRes, mv, m->p, m->z, m->b, m->r, force, m->dir, nullptr, m->cg, s);
   launch_cg_rnorm(mv, m->r, m->partials, m->cg, s);
@@ -814,7 +815,7 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
   }
   if (!m->cg_host->done) {
     launches += inner_solve(m, s);
-    launch_fcg_first(mv, m->y32, m->r, m->z, m->p, m->partials, m->cg, m->isc, s);
+    launch_fcg_first(mv, m->y32, m->r, m->z, m->p, m->partials, m->cg, m->isc, s, outer_dword(m) ? 1 : 0);
     launches += 1;
     if (m->timing && m->ev.size() < 2) {
       for (int i = (int)m->ev.size(); i < 2; ++i) {
@@ -834,7 +835,7 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
       if (m->timing) CK(cudaEventRecord(m->ev[0], s));
       launch_outer(m, kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, s);
       if (m->timing) CK(cudaEventRecord(m->ev[1], s));
-      launch_fcg_update(mv, m->x, m->r, m->p, m->q, m->partials, m->cg, s);
+      launch_fcg_update(mv, m->x, m->r, m->p, m->q, m->partials, m->cg, s, outer_dword(m) ? 1 : 0);
       launches += 2;
       CK(cudaGetLastError());
       CK(cudaMemcpyAsync(m->cg_host, m->cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
@@ -848,7 +849,7 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
       if (m->cg_host->done) break;
       launches += inner_solve(m, s);
       launch_fcg_zbeta(mv, m->y32, m->r, m->q, m->z, m->partials, m->cg, m->isc, s);
-      launch_fcg_pupdate(mv, m->z, m->p, m->q, m->cg, s);
+      launch_fcg_pupdate(mv, m->z, m->p, m->q, m->cg, s, outer_dword(m) ? 1 : 0);
       launches += 2;
     }
   }
@@ -905,9 +906,9 @@ bool issue_outer_loop(Model* m, cudaStream_t s, StepState* ss, int outer, cudaSt
   auto body = [&](cudaStream_t st) {
     inner_solve_dev(m, st);
     launch_fcg_zbeta(mv, m->y32, m->r, m->q, m->z, m->partials, m->cg, m->isc, st);
-    launch_fcg_pupdate(mv, m->z, m->p, m->q, m->cg, st);
+    launch_fcg_pupdate(mv, m->z, m->p, m->q, m->cg, st, outer_dword(m) ? 1 : 0);
     launch_outer(m, kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, st);
-    launch_fcg_update(mv, m->x, m->r, m->p, m->q, m->partials, m->cg, st);
+    launch_fcg_update(mv, m->x, m->r, m->p, m->q, m->partials, m->cg, st, outer_dword(m) ? 1 : 0);
   };
   if (bs == nullptr) {
     for (int k = 1; k < outer; ++k) body(s);
@@ -962,13 +963,13 @@ bool issue_device_step(Model* m, cudaStream_t s, StepState* ss, int outer, cudaS
   const int k_guess = m->opts.guess_order;
   if (k_guess > 0) launch_guess_extrap(m->N, m->guess_ring, k_guess, m->guess_ext, m->v, m->a, m->dt, m->x, s, ss);
   launch_cg_init_mixed(mv, m->w32, m->u, m->v, m->a, m->x, m->p, m->z, m->b, m->r, m->q, m->partials, m->cg, s, ss,
-                       k_guess > 0 ? 1 : 0);
+                       k_guess > 0 ? 1 : 0, outer_dword(m) ? 1 : 0);
   launch_outer(m, kModeRes, mv, m->p, m->z, m->b, m->r, 0.0, m->dir, nullptr, m->cg, s, dr);
   launch_cg_rnorm(mv, m->r, m->partials, m->cg, s);
   inner_solve_dev(m, s);
-  launch_fcg_first(mv, m->y32, m->r, m->z, m->p, m->partials, m->cg, m->isc, s);
+  launch_fcg_first(mv, m->y32, m->r, m->z, m->p, m->partials, m->cg, m->isc, s, outer_dword(m) ? 1 : 0);
   launch_outer(m, kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, s);
-  launch_fcg_update(mv, m->x, m->r, m->p, m->q, m->partials, m->cg, s);
+  launch_fcg_update(mv, m->x, m->r, m->p, m->q, m->partials, m->cg, s, outer_dword(m) ? 1 : 0);
   n->fixed += 6 + inner_launches + 3 + (k_guess > 0 ? 3 : 0);
   if (!issue_outer_loop(m, s, ss, outer, bs, n)) return false;
   launch_step_end(ss, m->cg, s);
@@ -1720,7 +1721,7 @@ gsw_status gsw_apply(gsw_ctx* ctx, int32_t model_id, int32_t which, const double
   }
   CK(cudaMemsetAsync(y_dev, 0, sizeof(double) * 3 * (size_t)m->N, ctx->stream));
   if (which == 5) {
-    launch_ebe_dw(kModeA, m->view(), x_dev, nullptr, nullptr, y_dev, 0.0, 0, nullptr, nullptr, ctx->stream);
+    launch_ebe_dw(kModeA, 0, m->view(), x_dev, nullptr, nullptr, y_dev, 0.0, 0, nullptr, nullptr, ctx->stream);
     CK(cudaGetLastError());
     return GSW_OK;
   }

@@ -159,8 +159,9 @@ void launch_ebe(int mode, const ModelView& m, const double* x, const double* v, 
                 double* y, double force, int dir, double* partials, CgScalars* cg,
                 cudaStream_t s, Drive dr = Drive{nullptr, nullptr});
 // The flexible CG's outer operator in double-word (paired FP32) arithmetic:
-// mode kModeA (with partials / cg as launch_ebe) or kModeRes.
-void launch_ebe_dw(int mode, const ModelView& m, const double* x, const double* v, const double* a,
+// mode kModeA (with partials / cg as launch_ebe) or kModeRes.  dw_in: the
+// input vectors are stored as double-word pairs (always so for kModeRes).
+void launch_ebe_dw(int mode, int dw_in, const ModelView& m, const double* x, const double* v, const double* a,
                    double* y, double force, int dir, double* partials, CgScalars* cg,
                    cudaStream_t s, Drive dr = Drive{nullptr, nullptr});
 // Initial guess from the last k+1 increments (degree-k extrapolation), k <=
@@ -180,7 +181,8 @@ void launch_rhs_lo(int half_geo, const void* lo_view, int64_t N, const double* u
 // v~ = v - (2/dt) x0, a~ = a + (4/dt) v - (4/dt^2) x0 for the one-pass residual
 void launch_cg_init_mixed(const ModelView& m, const float* b32, const double* u, const double* v, const double* a,
                           double* x, double* ut, double* vt, double* at, double* r, double* q, double* partials,
-                          CgScalars* cg, cudaStream_t s, const StepState* ss = nullptr, int use_guess = 0);
+                          CgScalars* cg, cudaStream_t s, const StepState* ss = nullptr, int use_guess = 0,
+                          int dw_out = 0);
 // device-driven step bracket (batched stepping)
 void launch_step_begin(StepState* ss, CgScalars* cg, cudaStream_t s);
 void launch_step_end(StepState* ss, const CgScalars* cg, cudaStream_t s);
@@ -250,14 +252,14 @@ void launch_from_f32(int64_t N, const float* w, double* y, cudaStream_t s);
 void launch_fcg_residual(const ModelView& m, const double* b, double* q, double* r, double* partials,
                          CgScalars* cg, cudaStream_t s);
 void launch_fcg_first(const ModelView& m, const float* y, const double* r, double* z, double* p,
-                      double* partials, CgScalars* cg, const InnerScalars* sc, cudaStream_t s);
+                      double* partials, CgScalars* cg, const InnerScalars* sc, cudaStream_t s, int dwp = 0);
 void launch_fcg_update(const ModelView& m, double* x, double* r, const double* p, const double* q,
-                       double* partials, CgScalars* cg, cudaStream_t s);
+                       double* partials, CgScalars* cg, cudaStream_t s, int dwp = 0);
 void launch_fcg_zbeta(const ModelView& m, const float* y, const double* r, const double* q,
                       double* z, double* partials, CgScalars* cg, const InnerScalars* sc,
                       cudaStream_t s);
 void launch_fcg_pupdate(const ModelView& m, const double* z, double* p, double* q,
-                        const CgScalars* cg, cudaStream_t s);
+                        const CgScalars* cg, cudaStream_t s, int dwp = 0);
 int node_blocks(int64_t n);
 
 // ---- learned initial guess (gsw_mlp.cu) ------------------------------------------

@@ -315,7 +315,7 @@ __global__ void receiver_weights_kernel(ModelView m, const double* __restrict__ 
 // Dashpot faces (threads E <= t < E + F) of the element-by-element operator,
 // FP64: the face term of A (scaled by 2/dt) in kModeA, the damping force of
 // the velocity plus the base force in kModeRhs / kModeRes.
-template <int MODE>
+template <int MODE, bool DWIN = false>
 __device__ __forceinline__ void face_apply(const ModelView& m, int64_t fc, const double* __restrict__ x,
                                            const double* __restrict__ vv, double force, int dir, double* y,
                                            double& dot) {
@@ -331,7 +331,14 @@ __device__ __forceinline__ void face_apply(const ModelView& m, int64_t fc, const
       nd[k] = m.fnode[k * m.F + fc];
       const double* src = (MODE == kModeRhs || MODE == kModeRes) ? vv : x;
 #pragma unroll
-      for (int i = 0; i < 3; ++i) xin[k][i] = src[3 * nd[k] + i];
+      for (int i = 0; i < 3; ++i) {
+        if (DWIN) {  // v~ stored as double-word pairs
+          const float2 c = reinterpret_cast<const float2*>(src)[3 * nd[k] + i];
+          xin[k][i] = to_double(dw(c.x, c.y));
+        } else {
+          xin[k][i] = src[3 * nd[k] + i];
+        }
+      }
       const double dn = n[0] * xin[k][0] + n[1] * xin[k][1] + n[2] * xin[k][2];
 #pragma unroll
       for (int i = 0; i < 3; ++i) z[k][i] = fma(As, xin[k][i], Ad * dn * n[i]);
@@ -497,13 +504,19 @@ constexpr int kDwSlots = 60;
 constexpr int kDwMinBlocks = 3;
 constexpr size_t kDwSmem = sizeof(float2) * kDwSlots * kElemThreads;
 
-template <int MODE>
+template <int MODE, bool DWIN>
 __global__ void __launch_bounds__(kElemThreads, kDwMinBlocks)
     ebe_dw_kernel(ModelView m, const double* __restrict__ x, const double* __restrict__ vv,
                   const double* __restrict__ aa, double* y, double force, int dir, double* partials,
                   CgScalars* cg, Drive dr) {
   static_assert(MODE == kModeA || MODE == kModeRes, "double-word operator: kModeA or kModeRes");
+  static_assert(MODE == kModeA || DWIN, "the residual pass reads double-word inputs");
   extern __shared__ float2 dsm[];  // [kDwSlots][kElemThreads]
+  // DWIN: the inputs arrive as double-word pairs (float2): the search
+  // direction (fcg kernels) or u~, v~, a~ (cg_init_mixed_kernel)
+  const float2* __restrict__ x2 = reinterpret_cast<const float2*>(x);
+  const float2* __restrict__ v2 = reinterpret_cast<const float2*>(vv);
+  const float2* __restrict__ a2 = reinterpret_cast<const float2*>(aa);
   if (cg != nullptr && ((volatile CgScalars*)cg)->done) return;
   if (dr.ss != nullptr) {
     if (!((volatile StepState*)dr.ss)->active) return;
@@ -528,22 +541,38 @@ __global__ void __launch_bounds__(kElemThreads, kDwMinBlocks)
     // two halves of five nodes: each half's gathers are issued together
 #pragma unroll 1
     for (int h = 0; h < 10; h += 5) {
-      double xs[5][3], vs[5][3];
+      if (DWIN) {
+        float2 xs[5][3], vs[5][3];
 #pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        const int64_t n3 = 3 * (int64_t)m.conn[(h + k) * m.E + e];
+        for (int k = 0; k < 5; ++k) {
+          const int64_t n3 = 3 * (int64_t)m.conn[(h + k) * m.E + e];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          xs[k][i] = x[n3 + i];
-          if (MODE == kModeRes) vs[k][i] = vv[n3 + i];
+          for (int i = 0; i < 3; ++i) {
+            xs[k][i] = x2[n3 + i];
+            if (MODE == kModeRes) vs[k][i] = v2[n3 + i];
+          }
         }
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            const dw xd(xs[k][i].x, xs[k][i].y);
+            st(kDwSlotW + 3 * (h + k) + i,
+               MODE == kModeRes ? fma_u(nbeta, dw(vs[k][i].x, vs[k][i].y), xd) : xd);
+          }
+      } else {
+        double xs[5][3];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+          const int64_t n3 = 3 * (int64_t)m.conn[(h + k) * m.E + e];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) xs[k][i] = x[n3 + i];
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+#pragma unroll
+          for (int i = 0; i < 3; ++i) st(kDwSlotW + 3 * (h + k) + i, to_dw(xs[k][i]));
       }
-#pragma unroll
-      for (int k = 0; k < 5; ++k)
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-          st(kDwSlotW + 3 * (h + k) + i,
-             MODE == kModeRes ? fma_u(nbeta, to_dw(vs[k][i]), to_dw(xs[k][i])) : to_dw(xs[k][i]));
     }
 #pragma unroll
     for (int q = 0; q < 18; ++q) st(kDwSlotCross + q, dw(0));
@@ -611,7 +640,12 @@ __global__ void __launch_bounds__(kElemThreads, kDwMinBlocks)
       for (int k = 0; k < 10; ++k) {
         // mass input: x (kModeA) or a~ + alpha v~ (kModeRes)
         const int64_t q = 3 * (int64_t)nd[k] + i;
-        wi[k] = MODE == kModeRes ? fma_u(ca, to_dw(vv[q]), to_dw(aa[q])) : ld(kDwSlotW + 3 * k + i);
+        if (MODE == kModeRes) {
+          const float2 vq = v2[q], aq = a2[q];
+          wi[k] = fma_u(ca, dw(vq.x, vq.y), dw(aq.x, aq.y));
+        } else {
+          wi[k] = ld(kDwSlotW + 3 * k + i);
+        }
       }
       mass_comp(wi, mS, yi);
 #pragma unroll
@@ -622,7 +656,7 @@ __global__ void __launch_bounds__(kElemThreads, kDwMinBlocks)
     }
     if (MODE == kModeA) dot = to_double(dd);
   } else if (t < m.E + m.F) {
-    face_apply<MODE>(m, t - m.E, x, vv, force, dir, y, dot);
+    face_apply<MODE, DWIN>(m, t - m.E, x, vv, force, dir, y, dot);
   }
   if (MODE == kModeA && partials != nullptr) {
     double vals[1] = {dot}, out[1];
@@ -676,11 +710,14 @@ __global__ void cg_init_kernel(int64_t N, const double* __restrict__ b, const do
 // initial guess du0 (the predictor dt v + dt^2/2 a, or the value already in x),
 // and the shifted state u~ = u + du0, v~ = v - (2/dt) du0,
 // a~ = a + (4/dt) v - (4/dt^2) du0 read by the single-pass residual; r = q = 0.
+// With dw_out the shifted state is stored as double-word pairs (float2, the
+// same 8 bytes) for the double-word residual kernel.
 __global__ void cg_init_mixed_kernel(int64_t N, const float* __restrict__ b32, const double* __restrict__ u,
                                      const double* __restrict__ v, const double* __restrict__ a, double dt,
                                      double* __restrict__ x, double* __restrict__ ut, double* __restrict__ vt,
                                      double* __restrict__ at, double* __restrict__ r, double* __restrict__ q,
-                                     double* partials, CgScalars* cg, const StepState* ss, int use_guess) {
+                                     double* partials, CgScalars* cg, const StepState* ss, int use_guess,
+                                     int dw_out) {
   if (ss != nullptr && !((volatile const StepState*)ss)->active) return;
   double bb = 0.0;
   const double h = 0.5 * dt * dt, c2 = 2.0 / dt, c4 = 4.0 / dt, c44 = 4.0 / (dt * dt);
@@ -694,9 +731,17 @@ __global__ void cg_init_mixed_kernel(int64_t N, const float* __restrict__ b32, c
       if (isfinite(g)) x0 = g;  // a non-finite guess falls back to the predictor
     }
     x[i] = x0;
-    ut[i] = u[i] + x0;
-    vt[i] = fma(-c2, x0, vi);
-    at[i] = fma(-c44, x0, fma(c4, vi, ai));
+    const double uti = u[i] + x0, vti = fma(-c2, x0, vi), ati = fma(-c44, x0, fma(c4, vi, ai));
+    if (dw_out) {
+      const dw a2 = to_dw(uti), b2 = to_dw(vti), c3 = to_dw(ati);
+      reinterpret_cast<float2*>(ut)[i] = make_float2(a2.hi, a2.lo);
+      reinterpret_cast<float2*>(vt)[i] = make_float2(b2.hi, b2.lo);
+      reinterpret_cast<float2*>(at)[i] = make_float2(c3.hi, c3.lo);
+    } else {
+      ut[i] = uti;
+      vt[i] = vti;
+      at[i] = ati;
+    }
     r[i] = 0.0;
     q[i] = 0.0;
   }
@@ -922,20 +967,24 @@ void launch_ebe(int mode, const ModelView& m, const double* x, const double* v, 
       break;
   }
 }
-void launch_ebe_dw(int mode, const ModelView& m, const double* x, const double* v, const double* a,
+void launch_ebe_dw(int mode, int dw_in, const ModelView& m, const double* x, const double* v, const double* a,
                    double* y, double force, int dir, double* partials, CgScalars* cg, cudaStream_t s, Drive dr) {
   const int nb = ebe_blocks(m);
   if (nb == 0) return;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(ebe_dw_kernel<kModeA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDwSmem);
-    cudaFuncSetAttribute(ebe_dw_kernel<kModeRes>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDwSmem);
+    cudaFuncSetAttribute(ebe_dw_kernel<kModeA, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDwSmem);
+    cudaFuncSetAttribute(ebe_dw_kernel<kModeA, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDwSmem);
+    cudaFuncSetAttribute(ebe_dw_kernel<kModeRes, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDwSmem);
     attr_set = true;
   }
-  if (mode == kModeA)
-    ebe_dw_kernel<kModeA><<<nb, kElemThreads, kDwSmem, s>>>(m, x, v, a, y, force, dir, partials, cg, dr);
+  if (mode == kModeA && dw_in)
+    ebe_dw_kernel<kModeA, true><<<nb, kElemThreads, kDwSmem, s>>>(m, x, v, a, y, force, dir, partials, cg, dr);
+  else if (mode == kModeA)
+    ebe_dw_kernel<kModeA, false><<<nb, kElemThreads, kDwSmem, s>>>(m, x, v, a, y, force, dir, partials, cg, dr);
   else
-    ebe_dw_kernel<kModeRes><<<nb, kElemThreads, kDwSmem, s>>>(m, x, v, a, y, force, dir, nullptr, nullptr, dr);
+    ebe_dw_kernel<kModeRes, true><<<nb, kElemThreads, kDwSmem, s>>>(m, x, v, a, y, force, dir, nullptr, nullptr,
+                                                                     dr);
 }
 void launch_cg_init(const ModelView& m, const double* b, const double* v, const double* a,
                     double* x, double* q, double* partials, CgScalars* cg, cudaStream_t s, int use_guess) {
@@ -1000,9 +1049,9 @@ void launch_guess_push(int64_t N, const double* du, double* ring, int k, int* ex
 }
 void launch_cg_init_mixed(const ModelView& m, const float* b32, const double* u, const double* v, const double* a,
                           double* x, double* ut, double* vt, double* at, double* r, double* q, double* partials,
-                          CgScalars* cg, cudaStream_t s, const StepState* ss, int use_guess) {
+                          CgScalars* cg, cudaStream_t s, const StepState* ss, int use_guess, int dw_out) {
   cg_init_mixed_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, b32, u, v, a, m.dt, x, ut, vt, at, r, q,
-                                                                       partials, cg, ss, use_guess);
+                                                                       partials, cg, ss, use_guess, dw_out);
 }
 void launch_cg_rnorm(const ModelView& m, const double* r, double* partials, CgScalars* cg, cudaStream_t s) {
   cg_rnorm_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, r, partials, cg);

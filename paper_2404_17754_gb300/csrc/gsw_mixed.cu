@@ -22,6 +22,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "gsw_dword.cuh"
 #include "gsw_ebe.cuh"
 #include "gsw_internal.cuh"
 #include "gsw_reduce.cuh"
@@ -750,16 +751,35 @@ __global__ void fcg_residual_kernel(int64_t N, const double* __restrict__ b, dou
   }
 }
 
+// The flexible CG's search direction p: FP64, or (dwp, double-word outer
+// operator) stored as double-word pairs in the same 8 bytes, so that the
+// operator reads it without conversion; every reader sees the same value.
+__device__ __forceinline__ double ld_p(const double* __restrict__ p, int64_t i, int dwp) {
+  if (dwp) {
+    const float2 c = reinterpret_cast<const float2*>(p)[i];
+    return to_double(dw(c.x, c.y));
+  }
+  return p[i];
+}
+__device__ __forceinline__ void st_p(double* __restrict__ p, int64_t i, double v, int dwp) {
+  if (dwp) {
+    const dw d = to_dw(v);
+    reinterpret_cast<float2*>(p)[i] = make_float2(d.hi, d.lo);
+  } else {
+    p[i] = v;
+  }
+}
+
 __global__ void fcg_first_kernel(int64_t N, const float* __restrict__ y, const double* __restrict__ r,
                                  double* __restrict__ z, double* __restrict__ p, double* partials, CgScalars* cg,
-                                 const InnerScalars* sc) {
+                                 const InnerScalars* sc, int dwp) {
   if (((volatile CgScalars*)cg)->done) return;
   const double inv = 1.0 / ((volatile const InnerScalars*)sc)->scale;
   double rz = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N; i += (int64_t)gridDim.x * blockDim.x) {
     const double zi = (double)y[i] * inv;
     z[i] = zi;
-    p[i] = zi;
+    st_p(p, i, zi, dwp);
     rz = fma(r[i], zi, rz);
   }
   double vals[1] = {rz}, out[1];
@@ -768,12 +788,12 @@ __global__ void fcg_first_kernel(int64_t N, const float* __restrict__ y, const d
 
 __global__ void fcg_update_kernel(int64_t N, double* __restrict__ x, double* __restrict__ r,
                                   const double* __restrict__ p, const double* __restrict__ q, double* partials,
-                                  CgScalars* cg) {
+                                  CgScalars* cg, int dwp) {
   if (((volatile CgScalars*)cg)->done) return;
   const double alpha = ((volatile CgScalars*)cg)->rz / ((volatile CgScalars*)cg)->pq;
   double rr = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N; i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] = fma(alpha, p[i], x[i]);
+    x[i] = fma(alpha, ld_p(p, i, dwp), x[i]);
     const double ri = fma(-alpha, q[i], r[i]);
     r[i] = ri;
     rr = fma(ri, ri, rr);
@@ -820,11 +840,11 @@ __global__ void fcg_zbeta_kernel(int64_t N, const float* __restrict__ y, const d
 }
 
 __global__ void fcg_pupdate_kernel(int64_t N, const double* __restrict__ z, double* __restrict__ p,
-                                   double* __restrict__ q, const CgScalars* cg) {
+                                   double* __restrict__ q, const CgScalars* cg, int dwp) {
   if (((volatile const CgScalars*)cg)->done) return;
   const double beta = ((volatile const CgScalars*)cg)->beta;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N; i += (int64_t)gridDim.x * blockDim.x) {
-    p[i] = fma(beta, p[i], z[i]);
+    st_p(p, i, fma(beta, ld_p(p, i, dwp), z[i]), dwp);
     q[i] = 0.0;
   }
 }
@@ -1775,20 +1795,20 @@ void launch_fcg_residual(const ModelView& m, const double* b, double* q, double*
   fcg_residual_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, b, q, r, partials, cg);
 }
 void launch_fcg_first(const ModelView& m, const float* y, const double* r, double* z, double* p, double* partials,
-                      CgScalars* cg, const InnerScalars* sc, cudaStream_t s) {
-  fcg_first_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, y, r, z, p, partials, cg, sc);
+                      CgScalars* cg, const InnerScalars* sc, cudaStream_t s, int dwp) {
+  fcg_first_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, y, r, z, p, partials, cg, sc, dwp);
 }
 void launch_fcg_update(const ModelView& m, double* x, double* r, const double* p, const double* q, double* partials,
-                       CgScalars* cg, cudaStream_t s) {
-  fcg_update_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, x, r, p, q, partials, cg);
+                       CgScalars* cg, cudaStream_t s, int dwp) {
+  fcg_update_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, x, r, p, q, partials, cg, dwp);
 }
 void launch_fcg_zbeta(const ModelView& m, const float* y, const double* r, const double* q, double* z,
                       double* partials, CgScalars* cg, const InnerScalars* sc, cudaStream_t s) {
   fcg_zbeta_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, y, r, q, z, partials, cg, sc);
 }
 void launch_fcg_pupdate(const ModelView& m, const double* z, double* p, double* q, const CgScalars* cg,
-                        cudaStream_t s) {
-  fcg_pupdate_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, z, p, q, cg);
+                        cudaStream_t s, int dwp) {
+  fcg_pupdate_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, z, p, q, cg, dwp);
 }
 
 }  // namespace gsw
