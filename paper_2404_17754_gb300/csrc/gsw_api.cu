@@ -542,7 +542,7 @@ gsw_status build_lo(gsw_ctx* ctx, Model* m, int half) {
     CK(cudaMemsetAsync(m->d_lo2, 0, dbytes, s));
     m->lo_half = half;
   }
-  launch_lo_convert(mv, m->n_blk, m->lconn, half, m->geo_lo, m->fgeo32, m->dinv, m->dinv32, m->partials, m->isc,
+  launch_lo_convert(mv, m->n_blk, m->lconn, half, half, m->geo_lo, m->fgeo32, m->dinv, m->dinv32, m->partials, m->isc,
                     m->matf, m->n_mat, s);
   CK(cudaGetLastError());
   BlockView bv = {m->n_blk, m->max_local, m->blk_ptr, m->blk_nodes};

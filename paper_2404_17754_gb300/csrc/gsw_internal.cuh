@@ -217,14 +217,15 @@ void launch_block_fill(const ModelView& m, BlockView b, int32_t* nodes, uint16_t
                        int32_t* refcount, cudaStream_t s, const int32_t* counts);
 void launch_block_mark(const ModelView& m, BlockView b, int32_t* nodes, int32_t* refcount,
                        int total, cudaStream_t s);
-void launch_lo_convert(const ModelView& m, int n_blk, const uint16_t* lconn, int half_geo, void* rec,
-                       float* fgeo32, const double* dinv, float* dinv32, double* partials, InnerScalars* sc,
+// dinv_lo: D^-1 divided by its mean diagonal entry, in the inner storage type (half_vec)
+void launch_lo_convert(const ModelView& m, int n_blk, const uint16_t* lconn, int half_geo, int half_vec, void* rec,
+                       float* fgeo32, const double* dinv, void* dinv_lo, double* partials, InnerScalars* sc,
                        float4* matf, int n_mat, cudaStream_t s);
 size_t lo_record_bytes(int half_geo);
-// inner solve: half_vec selects __half storage of the search direction d
-// (padded to 4 entries per node)
-void launch_inner_init(int64_t N, const double* r, const float* dinv32, float* s, float* y,
-                       float* t, void* d, int half_vec, float* w, double* partials,
+// inner solve: half_vec selects __half storage of the search direction d, of
+// t = D^-1 s (both padded to 4 entries per node) and of the scaled D^-1
+void launch_inner_init(int64_t N, const double* r, const void* dinv_lo, float* s, float* y,
+                       void* t, void* d, int half_vec, float* w, double* partials,
                        InnerScalars* sc, const CgScalars* cg, cudaStream_t st, float rtol);
 void launch_ebe_lo(int half_geo, int half_vec, const void* lo_view, const void* d, float* w,
                    double* partials, InnerScalars* sc, cudaStream_t st, int variant,
@@ -234,16 +235,16 @@ constexpr int kLoVariants = 4;
 // recurrence d' = t + beta d into their gather (t padded to 4 entries per
 // node; d' goes to the other direction buffer).
 bool lo_variant_fuses(int variant);
-void launch_ebe_lo_fused(int half_geo, int half_vec, const void* lo_view, const void* dprev, const float* t4,
+void launch_ebe_lo_fused(int half_geo, int half_vec, const void* lo_view, const void* dprev, const void* t4,
                          void* dnew, float* w, double* partials, InnerScalars* sc, cudaStream_t st, int variant,
                          const CgScalars* outer);
 // n_dw_max: an upper bound of the operator's grid size; up to
 // kAlphaPrologueMax partials the update forms alpha itself (one launch less).
 constexpr int kAlphaPrologueMax = 2048;
-void launch_inner_update(int64_t N, float* y, float* s, float* t, const void* d, int half_vec,
-                         float* w, const float* dinv32, const float* dw_part, double* partials,
+void launch_inner_update(int64_t N, float* y, float* s, void* t, const void* d, int half_vec,
+                         float* w, const void* dinv_lo, const float* dw_part, double* partials,
                          InnerScalars* sc, cudaStream_t st, const CgScalars* outer, int n_dw_max);
-void launch_inner_dupdate(int64_t N, const float* t, void* d, int half_vec, const InnerScalars* sc,
+void launch_inner_dupdate(int64_t N, const void* t, void* d, int half_vec, const InnerScalars* sc,
                           cudaStream_t st, const CgScalars* outer);
 // conversions for the standalone reduced-precision operator (tests)
 void launch_to_lo(int64_t N, const double* x, void* d, int half_vec, float* w, cudaStream_t s);

@@ -214,10 +214,10 @@ __global__ void block_mark_kernel(int total, int32_t* nodes, const int32_t* refc
 }
 
 // Element records in operator order (invalid positions of the last block get
-// zero volume, so they contribute nothing), FP32 face data and D^-1.
+// zero volume, so they contribute nothing) and FP32 face data.
 template <typename SG>
 __global__ void lo_convert_kernel(ModelView m, int n_blk, const uint16_t* __restrict__ lconn,
-                                  typename LoRec<SG>::type* rec, float* fgeo32, const double* dinv, float* dinv32) {
+                                  typename LoRec<SG>::type* rec, float* fgeo32) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t P = (int64_t)n_blk * kLoBlock;
   if (t < P) {
@@ -244,7 +244,6 @@ __global__ void lo_convert_kernel(ModelView m, int n_blk, const uint16_t* __rest
     for (int q = 0; q < RW; ++q) out[q * kLoBlock] = u.v[q];
   }
   if (t < 6 * m.F) fgeo32[t] = (float)m.fgeo[t];
-  if (t < 6 * m.N) dinv32[t] = (float)dinv[t];
 }
 
 // Mean diagonal entry of D^-1 (sets the inner right-hand-side scale).
@@ -254,6 +253,19 @@ __global__ void dinv_mean_kernel(int64_t N, const double* __restrict__ dinv, dou
     s += dinv[6 * n] + dinv[6 * n + 1] + dinv[6 * n + 2];
   double vals[1] = {s}, out[1];
   if (last_block_reduce<1>(vals, partials, &sc->counter, out) && threadIdx.x == 0) sc->dinv_mean = out[0] / (3.0 * N);
+}
+
+// D^-1 in the inner storage type, divided by its mean diagonal entry: entries
+// of order one (FP16 keeps them), and the inner PCG iterates do not change
+// when the preconditioner is scaled by a constant (the inner right-hand side
+// is scaled to match, see inner_init_kernel).
+template <typename SD>
+__global__ void dinv_lo_kernel(int64_t n6, const double* __restrict__ dinv, const InnerScalars* sc,
+                               SD* __restrict__ out) {
+  const double dm = ((volatile const InnerScalars*)sc)->dinv_mean;
+  const double inv = dm > 0.0 ? 1.0 / dm : 1.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n6; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = from_f<SD>((float)(dinv[i] * inv));
 }
 
 // ------------------------------------------------------------------------------
@@ -290,7 +302,7 @@ template <typename SG, typename SD, int MINB, bool FUSE = false>
 __global__ void __launch_bounds__(kLoBlock, MINB) ebe_lo_kernel(LoView<SG> m, const SD* __restrict__ d,
                                                            float* __restrict__ w, double* partials,
                                                            InnerScalars* sc, const CgScalars* outer,
-                                                           const float* __restrict__ t4 = nullptr,
+                                                           const SD* __restrict__ t4 = nullptr,
                                                            SD* __restrict__ dnew = nullptr) {
   if (inner_stopped(outer, sc)) return;
   typedef typename LoRec<SG>::type Rec;
@@ -478,8 +490,8 @@ __device__ __forceinline__ void dinv_apply_f(const float* __restrict__ D, const 
 }
 
 template <typename SD>
-__global__ void inner_init_kernel(int64_t N, const double* __restrict__ r, const float* __restrict__ dinv,
-                                  float* __restrict__ s, float* __restrict__ y, float* __restrict__ t,
+__global__ void inner_init_kernel(int64_t N, const double* __restrict__ r, const SD* __restrict__ dinv,
+                                  float* __restrict__ s, float* __restrict__ y, SD* __restrict__ t,
                                   SD* __restrict__ d, float* __restrict__ w, double* partials,
                                   InnerScalars* sc, const CgScalars* cg, float rtol) {
   if (((volatile const CgScalars*)cg)->done) return;
@@ -487,9 +499,9 @@ __global__ void inner_init_kernel(int64_t N, const double* __restrict__ r, const
   // slow on this GPU) and broadcast through shared memory
   __shared__ double scale_s;
   if (threadIdx.x == 0) {
+    // s of RMS one; with D^-1 stored divided by its mean (dinv_lo_kernel), t and d are of order one
     const double rr = ((volatile const CgScalars*)cg)->rr;
-    const double dm = ((volatile const InnerScalars*)sc)->dinv_mean;
-    scale_s = (rr > 0.0 ? sqrt(3.0 * (double)N / rr) : 1.0) / (dm > 0.0 ? dm : 1.0);
+    scale_s = rr > 0.0 ? sqrt(3.0 * (double)N / rr) : 1.0;
   }
   __syncthreads();
   const double scale = scale_s;
@@ -503,14 +515,17 @@ __global__ void inner_init_kernel(int64_t N, const double* __restrict__ r, const
       y[3 * n + i] = 0.f;
       w[3 * n + i] = 0.f;
     }
-    dinv_apply_f(dinv + 6 * n, sn, tn);
+    float Dn[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) Dn[k] = to_f(dinv[6 * n + k]);
+    dinv_apply_f(Dn, sn, tn);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      t[4 * n + i] = tn[i];
+      t[4 * n + i] = from_f<SD>(tn[i]);
       d[4 * n + i] = from_f<SD>(tn[i]);
       st = fmaf(sn[i], tn[i], st);
     }
-    t[4 * n + 3] = 0.f;
+    t[4 * n + 3] = from_f<SD>(0.f);
     d[4 * n + 3] = from_f<SD>(0.f);
   }
   float vals[1] = {st}, out[1];
@@ -561,6 +576,22 @@ __device__ __forceinline__ void ld_dir(const __half* p, float (&v)[16]) {
   }
 }
 __device__ __forceinline__ void st_dir(float* p, const float (&v)[16]) { stq<4>(p, v); }
+// the four D^-1 blocks of a node quad (24 entries)
+__device__ __forceinline__ void ld_dinv(const float* p, float (&v)[24]) { ldq<6>(p, v); }
+__device__ __forceinline__ void ld_dinv(const __half* p, float (&v)[24]) {
+  const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const uint4 a = q[k];
+    const unsigned u[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const __half2 x = *reinterpret_cast<const __half2*>(&u[h]);
+      v[8 * k + 2 * h] = __low2float(x);
+      v[8 * k + 2 * h + 1] = __high2float(x);
+    }
+  }
+}
 __device__ __forceinline__ void st_dir(__half* p, const float (&v)[16]) {
   uint4* q = reinterpret_cast<uint4*>(p);
 #pragma unroll
@@ -615,8 +646,8 @@ __global__ void inner_alpha_kernel(const float* __restrict__ dw_part, InnerScala
 // operator partials, i.e. a small model) every CTA forms alpha itself in a
 // prologue and no separate alpha kernel is launched.
 template <typename SD, bool PRO = false>
-__global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __restrict__ s, float* __restrict__ t,
-                                    const SD* __restrict__ d, float* __restrict__ w, const float* __restrict__ dinv,
+__global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __restrict__ s, SD* __restrict__ t,
+                                    const SD* __restrict__ d, float* __restrict__ w, const SD* __restrict__ dinv,
                                     double* partials, InnerScalars* sc, const CgScalars* outer,
                                     const float* __restrict__ dw_part = nullptr) {
   if (inner_stopped(outer, sc)) return;
@@ -647,7 +678,7 @@ __global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __r
     ldq<3>(s + 12 * g, sv);
     ldq<3>(w + 12 * g, wv);
     ld_dir(d + 16 * g, dv);
-    ldq<6>(dinv + 24 * g, Dv);
+    ld_dinv(dinv + 24 * g, Dv);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
 #pragma unroll
@@ -663,7 +694,7 @@ __global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __r
     const float zero[12] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     stq<3>(y + 12 * g, yv);
     stq<3>(s + 12 * g, sv);
-    stq<4>(t + 16 * g, tv);
+    st_dir(t + 16 * g, tv);
     stq<3>(w + 12 * g, zero);
   }
   if (g0 == 0) {  // the last N mod 4 nodes
@@ -677,13 +708,16 @@ __global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __r
         s[k] = sn[i];
         w[k] = 0.f;
       }
-      dinv_apply_f(dinv + 6 * n, sn, tn);
+      float Dn[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) Dn[k] = to_f(dinv[6 * n + k]);
+      dinv_apply_f(Dn, sn, tn);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        t[4 * n + i] = tn[i];
+        t[4 * n + i] = from_f<SD>(tn[i]);
         st = fmaf(sn[i], tn[i], st);
       }
-      t[4 * n + 3] = 0.f;
+      t[4 * n + 3] = from_f<SD>(0.f);
     }
   }
   float vals[1] = {st}, out[1];
@@ -701,7 +735,7 @@ __global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __r
 
 // d = t + beta d (the padding entry of each node stays 0).
 template <typename SD>
-__global__ void inner_dupdate_kernel(int64_t N, const float* __restrict__ t, SD* __restrict__ d,
+__global__ void inner_dupdate_kernel(int64_t N, const SD* __restrict__ t, SD* __restrict__ d,
                                      const InnerScalars* sc, const CgScalars* outer) {
   if (inner_stopped(outer, sc)) return;
   const float beta = ((volatile const InnerScalars*)sc)->beta_f;
@@ -709,7 +743,7 @@ __global__ void inner_dupdate_kernel(int64_t N, const float* __restrict__ t, SD*
   const int64_t G4 = N >> 2;
   for (int64_t g = g0; g < G4; g += (int64_t)gridDim.x * blockDim.x) {
     float tv[16], dv[16];
-    ldq<4>(t + 16 * g, tv);
+    ld_dir(t + 16 * g, tv);
     ld_dir(d + 16 * g, dv);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
@@ -720,7 +754,7 @@ __global__ void inner_dupdate_kernel(int64_t N, const float* __restrict__ t, SD*
   if (g0 == 0) {
     for (int64_t n = 4 * G4; n < N; ++n)
 #pragma unroll
-      for (int i = 0; i < 3; ++i) d[4 * n + i] = from_f<SD>(fmaf(beta, to_f(d[4 * n + i]), t[4 * n + i]));
+      for (int i = 0; i < 3; ++i) d[4 * n + i] = from_f<SD>(fmaf(beta, to_f(d[4 * n + i]), to_f(t[4 * n + i])));
   }
 }
 
@@ -971,8 +1005,8 @@ __global__ void lo_material_kernel(const MatCoef* mat, int n_mat, double dt, flo
   }
 }
 
-void launch_lo_convert(const ModelView& m, int n_blk, const uint16_t* lconn, int half_geo, void* rec,
-                       float* fgeo32, const double* dinv, float* dinv32, double* partials, InnerScalars* sc,
+void launch_lo_convert(const ModelView& m, int n_blk, const uint16_t* lconn, int half_geo, int half_vec, void* rec,
+                       float* fgeo32, const double* dinv, void* dinv_lo, double* partials, InnerScalars* sc,
                        float4* matf, int n_mat, cudaStream_t s) {
   lo_material_kernel<<<1, kMaxMat, 0, s>>>(m.mat, n_mat, m.dt, matf);
   int64_t n = (int64_t)n_blk * kLoBlock;
@@ -980,21 +1014,25 @@ void launch_lo_convert(const ModelView& m, int n_blk, const uint16_t* lconn, int
   if (6 * m.N > n) n = 6 * m.N;
   const unsigned g = (unsigned)((n + 255) / 256);
   if (half_geo)
-    lo_convert_kernel<__half><<<g, 256, 0, s>>>(m, n_blk, lconn, (LoRecH*)rec, fgeo32, dinv, dinv32);
+    lo_convert_kernel<__half><<<g, 256, 0, s>>>(m, n_blk, lconn, (LoRecH*)rec, fgeo32);
   else
-    lo_convert_kernel<float><<<g, 256, 0, s>>>(m, n_blk, lconn, (LoRecF*)rec, fgeo32, dinv, dinv32);
+    lo_convert_kernel<float><<<g, 256, 0, s>>>(m, n_blk, lconn, (LoRecF*)rec, fgeo32);
   dinv_mean_kernel<<<node_blocks(m.N), kNodeThreads, 0, s>>>(m.N, dinv, partials, sc);
+  if (half_vec)
+    dinv_lo_kernel<__half><<<node_blocks(6 * m.N), kNodeThreads, 0, s>>>(6 * m.N, dinv, sc, (__half*)dinv_lo);
+  else
+    dinv_lo_kernel<float><<<node_blocks(6 * m.N), kNodeThreads, 0, s>>>(6 * m.N, dinv, sc, (float*)dinv_lo);
 }
 size_t lo_record_bytes(int half_geo) { return half_geo ? sizeof(LoRecH) : sizeof(LoRecF); }
-void launch_inner_init(int64_t N, const double* r, const float* dinv32, float* s, float* y, float* t, void* d,
+void launch_inner_init(int64_t N, const double* r, const void* dinv_lo, float* s, float* y, void* t, void* d,
                        int half_vec, float* w, double* partials, InnerScalars* sc, const CgScalars* cg,
                        cudaStream_t st, float rtol) {
   if (half_vec)
-    inner_init_kernel<__half><<<node_blocks(N), kNodeThreads, 0, st>>>(N, r, dinv32, s, y, t, (__half*)d, w,
-                                                                       partials, sc, cg, rtol);
+    inner_init_kernel<__half><<<node_blocks(N), kNodeThreads, 0, st>>>(
+        N, r, (const __half*)dinv_lo, s, y, (__half*)t, (__half*)d, w, partials, sc, cg, rtol);
   else
-    inner_init_kernel<float><<<node_blocks(N), kNodeThreads, 0, st>>>(N, r, dinv32, s, y, t, (float*)d, w,
-                                                                      partials, sc, cg, rtol);
+    inner_init_kernel<float><<<node_blocks(N), kNodeThreads, 0, st>>>(
+        N, r, (const float*)dinv_lo, s, y, (float*)t, (float*)d, w, partials, sc, cg, rtol);
 }
 
 // ---- software-pipelined variant ----------------------------------------------
@@ -1530,7 +1568,7 @@ static void ebe_lo_launch(int variant, const LoView<SG>& m, const SD* d, float* 
     ebe_lo_kernel<SG, SD, 1><<<g, kLoBlock, smem, st>>>(m, d, w, partials, sc, outer);
 }
 template <typename SG, typename SD>
-static void ebe_lo_fused_launch(int variant, const LoView<SG>& m, const SD* dprev, const float* t4, SD* dnew,
+static void ebe_lo_fused_launch(int variant, const LoView<SG>& m, const SD* dprev, const SD* t4, SD* dnew,
                                 float* w, double* partials, InnerScalars* sc, cudaStream_t st,
                                 const CgScalars* outer) {
   const unsigned g = (unsigned)(m.blk.n_blk + (m.F + kLoBlock - 1) / kLoBlock);
@@ -1541,24 +1579,24 @@ static void ebe_lo_fused_launch(int variant, const LoView<SG>& m, const SD* dpre
     ebe_lo_kernel<SG, SD, 1, true><<<g, kLoBlock, smem, st>>>(m, dprev, w, partials, sc, outer, t4, dnew);
 }
 bool lo_variant_fuses(int variant) { return variant == 0 || variant == 1; }
-void launch_ebe_lo_fused(int half_geo, int half_vec, const void* lo_view, const void* dprev, const float* t4,
+void launch_ebe_lo_fused(int half_geo, int half_vec, const void* lo_view, const void* dprev, const void* t4,
                          void* dnew, float* w, double* partials, InnerScalars* sc, cudaStream_t st, int variant,
                          const CgScalars* outer) {
   if (half_geo) {
     const LoView<__half>& m = *(const LoView<__half>*)lo_view;
     if (half_vec)
-      ebe_lo_fused_launch<__half, __half>(variant, m, (const __half*)dprev, t4, (__half*)dnew, w, partials, sc, st,
+      ebe_lo_fused_launch<__half, __half>(variant, m, (const __half*)dprev, (const __half*)t4, (__half*)dnew, w, partials, sc, st,
                                           outer);
     else
-      ebe_lo_fused_launch<__half, float>(variant, m, (const float*)dprev, t4, (float*)dnew, w, partials, sc, st,
+      ebe_lo_fused_launch<__half, float>(variant, m, (const float*)dprev, (const float*)t4, (float*)dnew, w, partials, sc, st,
                                          outer);
   } else {
     const LoView<float>& m = *(const LoView<float>*)lo_view;
     if (half_vec)
-      ebe_lo_fused_launch<float, __half>(variant, m, (const __half*)dprev, t4, (__half*)dnew, w, partials, sc, st,
+      ebe_lo_fused_launch<float, __half>(variant, m, (const __half*)dprev, (const __half*)t4, (__half*)dnew, w, partials, sc, st,
                                          outer);
     else
-      ebe_lo_fused_launch<float, float>(variant, m, (const float*)dprev, t4, (float*)dnew, w, partials, sc, st,
+      ebe_lo_fused_launch<float, float>(variant, m, (const float*)dprev, (const float*)t4, (float*)dnew, w, partials, sc, st,
                                         outer);
   }
 }
@@ -1754,40 +1792,42 @@ static unsigned quad_grid(int64_t N, unsigned cap) {
   const unsigned b = quad_blocks(N);
   return b < cap ? b : cap;
 }
-void launch_inner_update(int64_t N, float* y, float* s, float* t, const void* d, int half_vec, float* w,
-                         const float* dinv32, const float* dw_part, double* partials, InnerScalars* sc,
+void launch_inner_update(int64_t N, float* y, float* s, void* t, const void* d, int half_vec, float* w,
+                         const void* dinv_lo, const float* dw_part, double* partials, InnerScalars* sc,
                          cudaStream_t st, const CgScalars* outer, int n_dw_max) {
   if (n_dw_max <= kAlphaPrologueMax) {
     if (half_vec) {
       static const unsigned cap = persistent_cap((const void*)inner_update_kernel<__half, true>);
       inner_update_kernel<__half, true><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(
-          N, y, s, t, (const __half*)d, w, dinv32, partials, sc, outer, dw_part);
+          N, y, s, (__half*)t, (const __half*)d, w, (const __half*)dinv_lo, partials, sc, outer, dw_part);
     } else {
       static const unsigned cap = persistent_cap((const void*)inner_update_kernel<float, true>);
       inner_update_kernel<float, true><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(
-          N, y, s, t, (const float*)d, w, dinv32, partials, sc, outer, dw_part);
+          N, y, s, (float*)t, (const float*)d, w, (const float*)dinv_lo, partials, sc, outer, dw_part);
     }
     return;
   }
   inner_alpha_kernel<<<1, 1024, 0, st>>>(dw_part, sc, outer);
   if (half_vec) {
     static const unsigned cap = persistent_cap((const void*)inner_update_kernel<__half>);
-    inner_update_kernel<__half><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(N, y, s, t, (const __half*)d, w, dinv32,
-                                                                            partials, sc, outer);
+    inner_update_kernel<__half><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(
+        N, y, s, (__half*)t, (const __half*)d, w, (const __half*)dinv_lo, partials, sc, outer);
   } else {
     static const unsigned cap = persistent_cap((const void*)inner_update_kernel<float>);
-    inner_update_kernel<float><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(N, y, s, t, (const float*)d, w, dinv32,
-                                                                           partials, sc, outer);
+    inner_update_kernel<float><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(
+        N, y, s, (float*)t, (const float*)d, w, (const float*)dinv_lo, partials, sc, outer);
   }
 }
-void launch_inner_dupdate(int64_t N, const float* t, void* d, int half_vec, const InnerScalars* sc,
+void launch_inner_dupdate(int64_t N, const void* t, void* d, int half_vec, const InnerScalars* sc,
                           cudaStream_t st, const CgScalars* outer) {
   if (half_vec) {
     static const unsigned cap = persistent_cap((const void*)inner_dupdate_kernel<__half>);
-    inner_dupdate_kernel<__half><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(N, t, (__half*)d, sc, outer);
+    inner_dupdate_kernel<__half><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(N, (const __half*)t, (__half*)d, sc,
+                                                                             outer);
   } else {
     static const unsigned cap = persistent_cap((const void*)inner_dupdate_kernel<float>);
-    inner_dupdate_kernel<float><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(N, t, (float*)d, sc, outer);
+    inner_dupdate_kernel<float><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(N, (const float*)t, (float*)d, sc,
+                                                                            outer);
   }
 }
 void launch_fcg_residual(const ModelView& m, const double* b, double* q, double* r, double* partials, CgScalars* cg,
