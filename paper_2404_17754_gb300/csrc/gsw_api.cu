@@ -105,6 +105,9 @@ struct Model {
   double* p_dev = nullptr;     // input samples on the device
   int batch = 0;               // id of the batch holding the model (0: none)
   int version = 0;             // bumped when a captured step graph would be stale
+  // host-driven steps: the inner solve captured once as a CUDA graph
+  cudaGraphExec_t ig_exec = nullptr;
+  int ig_version = -1;
   float lo_variant_ms[kLoVariants] = {0.f, 0.f, 0.f};
   LoView<float> lo_f;
   LoView<__half> lo_h;
@@ -251,6 +254,7 @@ gsw_status alloc_into(gsw_ctx* ctx, Model* m, T** out, size_t count) {
   } while (0)
 
 void free_model(gsw_ctx* ctx, Model* m) {
+  if (m->ig_exec) cudaGraphExecDestroy(m->ig_exec);
   for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
   for (cudaEvent_t e : m->ev_lo) cudaEventDestroy(e);
   for (void* p : m->allocs) dev_free(ctx, p);
@@ -752,6 +756,33 @@ int64_t inner_solve(Model* m, cudaStream_t s) {
   return inner_solve_launches(m, fuse);
 }
 
+// Host-driven steps after the live tuning: the inner solve's launches (about
+// four per inner iteration) are captured once into a CUDA graph, re-captured
+// when the model's version changes (solver options, time step, tuning
+// choice), and launched as one graph per outer iteration.  With kernel timing
+// on, or where the stream cannot be captured, the launches are issued directly.
+void inner_solve_dev(Model* m, cudaStream_t s);
+int64_t inner_solve_step(Model* m, cudaStream_t s) {
+  if (m->timing || m->live_tune) return inner_solve(m, s);
+  if (m->ig_version != m->version) {
+    if (m->ig_exec) cudaGraphExecDestroy(m->ig_exec);
+    m->ig_exec = nullptr;
+    m->ig_version = m->version;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      inner_solve_dev(m, s);
+      if (cudaStreamEndCapture(s, &g) == cudaSuccess && g != nullptr) {
+        if (cudaGraphInstantiate(&m->ig_exec, g, 0) != cudaSuccess) m->ig_exec = nullptr;
+        cudaGraphDestroy(g);
+      }
+    }
+    cudaGetLastError();  // a failed capture leaves the direct launches
+  }
+  if (!m->ig_exec || cudaGraphLaunch(m->ig_exec, s) != cudaSuccess) return inner_solve(m, s);
+  m->stats.inner_iters_total += m->opts.inner_iters > 0 ? m->opts.inner_iters : 1;
+  return inner_solve_launches(m, inner_fuses(m, m->lo_variant));
+}
+
 // One Newmark step with flexible CG (FP64) preconditioned by the inner solve.
 gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
   cudaStream_t s = ctx->stream;
@@ -814,7 +845,7 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
     }
   }
   if (!m->cg_host->done) {
-    launches += inner_solve(m, s);
+    launches += inner_solve_step(m, s);
     launch_fcg_first(mv, m->y32, m->r, m->z, m->p, m->partials, m->cg, m->isc, s, outer_dword(m) ? 1 : 0);
     launches += 1;
     if (m->timing && m->ev.size() < 2) {
@@ -847,7 +878,7 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
         m->ebe_count += 1;
       }
       if (m->cg_host->done) break;
-      launches += inner_solve(m, s);
+      launches += inner_solve_step(m, s);
       launch_fcg_zbeta(mv, m->y32, m->r, m->q, m->z, m->partials, m->cg, m->isc, s);
       launch_fcg_pupdate(mv, m->z, m->p, m->q, m->cg, s, outer_dword(m) ? 1 : 0);
       launches += 2;
