@@ -238,9 +238,11 @@ gsw_status gsw_set_state(gsw_ctx *ctx, int32_t model_id, const double *u, const 
  * launch of subsequent steps with CUDA events on the context's stream;
  * enable = 0 stops; any other value only reads.  ms[2] and launches[2]
  * (either may be NULL) receive the summed device time and the number of
- * timed launches of [0] the FP64 element-by-element A p product of the CG
- * iteration and [1] the reduced-precision element-by-element product of the
- * inner preconditioner (mixed modes). */
+ * timed launches of [0] the element-by-element A p product of the CG
+ * iteration (FP64 or double-word, gsw_outer_op) and [1] the reduced-precision
+ * element-by-element product of the inner preconditioner (mixed modes; an
+ * inner solve that met inner_rtol returns at entry from its remaining
+ * launches, which are not counted). */
 gsw_status gsw_timing(gsw_ctx *ctx, int32_t model_id, int32_t enable, double *ms,
                       int64_t *launches);
 

@@ -721,19 +721,22 @@ int64_t inner_solve(Model* m, cudaStream_t s) {
   m->stats.inner_iters_total += it;
   if (timed) {
     cudaEventSynchronize(m->ev_lo[2 * it - 1]);
-    std::vector<float> per[kLoVariants];
+    std::vector<float> per[kLoVariants], msv((size_t)it, 0.f);
     for (int k = 0; k < it; ++k) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, m->ev_lo[2 * k], m->ev_lo[2 * k + 1]) != cudaSuccess) continue;
-      if (m->timing) m->lo_ms += ms;
+      msv[(size_t)k] = ms;
       if (tune && k >= kLoVariants) per[k % kLoVariants].push_back(ms);  // the first round warms up
     }
     if (m->timing) {
-      // executed iterations (a solve that met inner_rtol skips the rest)
+      // executed iterations: a solve that met inner_rtol returns at entry from the
+      // remaining launches, which are not operator applications and are not counted
       unsigned long long n = 0;
       if (cudaMemcpyAsync(&n, &m->isc->iters, sizeof(n), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
           cudaStreamSynchronize(s) == cudaSuccess) {
-        m->lo_count += (int64_t)(n - m->iters_mark);
+        const int64_t done = (int64_t)(n - m->iters_mark);
+        for (int64_t k = 0; k < done && k < it; ++k) m->lo_ms += msv[(size_t)k];
+        m->lo_count += done;
         m->iters_mark = n;
       }
     }
