@@ -44,3 +44,34 @@ def test_binding_declares_signatures_for_every_symbol(lib_path):
 
     assert set(gsw.SIGNATURES) == set(declared_symbols())
     gsw.load(lib_path)
+
+
+def test_binding_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the option and statistics structs have the header's size and field offsets."""
+    import shutil
+
+    from paper_2404_17754_gb300 import gsw
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"gsw_solver_opts": gsw.SolverOpts, "gsw_stats": gsw.Stats, "gsw_learn_opts": gsw.LearnOpts}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "gsw.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append('  printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for fname, _ in py._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, fname, cname, fname))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = {}
+    for line in filter(None, out):
+        cname, field, value = line.split()
+        seen[(cname, field)] = int(value)
+    for cname, py in mirrors.items():
+        assert seen[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert seen[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
