@@ -374,7 +374,7 @@ def main():
     ap.add_argument("--precision", default="fp16", choices=["fp64", "fp32", "fp16"])
     ap.add_argument("--inner", type=int, default=0, help="inner preconditioner iterations (mixed modes; the cap "
                     "when --inner-rtol > 0); 0 = the workload's tuned count (realistic: cap 45 with --inner-rtol "
-                    "0.0125 unless given; others: 30)")
+                    "0.0125 unless given; candidates: 25; others: 30)")
     ap.add_argument("--guess-order", type=int, default=4,
                     help="initial guess: 0 = Newmark predictor, k = degree-k extrapolation of the last k+1 increments")
     ap.add_argument("--batch-outer", type=int, default=0,
@@ -392,11 +392,13 @@ def main():
     if args.inner <= 0:
         # tuned on GB300 with the quartic initial guess: fewest ms per step (the realistic model
         # stops each inner solve once its preconditioned residual fell 80-fold, at most 45
-        # iterations; the batched candidates run a fixed 30)
+        # iterations; the batched candidates run a fixed 25)
         if args.workload == "realistic":
             args.inner = 45
             if args.inner_rtol < 0:
                 args.inner_rtol = 0.0125
+        elif args.workload == "candidates":
+            args.inner = 25
         else:
             args.inner = 30
     if args.inner_rtol < 0:
