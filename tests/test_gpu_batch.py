@@ -175,3 +175,27 @@ def test_batch_extrapolated_guess(ctx):
     b.close()
     for m in models:
         m.free()
+
+
+def test_batch_with_fp64_outer_operator(ctx):
+    """The batched graph with the outer operator in hardware FP64 (search direction and
+    shifted state stored as doubles) matches the same models stepped alone and the oracle."""
+    from paper_2404_17754_gb300 import gsw
+
+    cfgs = _cfgs(n_steps=20)
+    alone = []
+    for cfg in cfgs:
+        m = _upload(ctx, cfg, outer_op=gsw.OUTER_FP64, guess_order=2)
+        m.step(cfg["n_steps"])
+        alone.append(m.waveforms())
+        m.free()
+    models = [_upload(ctx, cfg, outer_op=gsw.OUTER_FP64, guess_order=2) for cfg in cfgs]
+    b = ctx.batch(models)
+    b.step(20)
+    for cfg, m, w_alone in zip(cfgs, models, alone):
+        assert m.stats()["steps_done"] == cfg["n_steps"]
+        assert _relerr(m.waveforms(), w_alone) <= 1e-7
+        assert _relerr(m.waveforms(), newmark.analysis(cfg, tol=1e-8)["wave"]) <= 1e-6
+    b.close()
+    for m in models:
+        m.free()
