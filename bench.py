@@ -31,13 +31,20 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
-ISSUE_PEAK = 152 * 4 * 32 * 2.07e9  # thread instructions/s: 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz
 EBE_FLOPS_PER_ELEM = 1088      # A-mode element: vertex-gradient stiffness, consistent mass, p.Ap partial
 EBE_FLOPS_PER_FACE = 150
 # algorithmic bytes of one FP64 A p launch: x, y (read + write) once per DOF,
 # connectivity + material id + geometry once per element
 def ebe_bytes(n_nodes, n_elem, n_faces):
     return n_nodes * 3 * (8 + 8 + 8) + n_elem * (40 + 4 + 80) + n_faces * (24 + 48)
+
+
+def unique_node_bytes(n_nodes, n_elem, n_vert, s_x, s_y):
+    """Algorithmic bytes of one element-by-element product with unique data only
+    (every shared node read and written once): x and y once per DOF (s_x, s_y
+    bytes per value), 10 int32 node ids and an int32 material id per element,
+    three FP64 coordinates per vertex node."""
+    return n_nodes * 3 * (s_x + s_y) + n_elem * 44 + n_vert * 24
 
 
 def peaks():
@@ -100,18 +107,49 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_sample(budget_s=15.0, crop=12, tol=1e-8):
-    """Time the FP64 CPU oracle on a bounded sample of the same workload.
+def host_cpu():
+    """(logical cores, CPU model name) of this host."""
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                name = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return os.cpu_count() or 1, name
 
-    Runs in a child process with one BLAS/OpenMP thread: the oracle's CSR
-    product and vector updates are single-threaded, so cores = 1.
-    """
-    code = r"""
+
+def cpu_oracle_all_cores(budget_s=12.0, crop=12, tol=1e-8):
+    """The oracle on every host core: one single-threaded oracle process per core,
+    each timing its own directional analysis of the same crop (directions cycle
+    x1, x2, x3); the throughput is the sum over the processes."""
+    n = os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    procs = [subprocess.Popen([sys.executable, "-c", _oracle_code(budget_s, crop, tol, k % 3)], stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True, env=env) for k in range(n)]
+    total, dof, steps, fails = 0.0, None, 0, 0
+    for pr in procs:
+        try:
+            out, _ = pr.communicate(timeout=900)
+            d = json.loads(out.strip().splitlines()[-1])
+            total += d["dof"] * d["steps"] / d["seconds"]
+            dof, steps = d["dof"], steps + d["steps"]
+        except Exception:
+            fails += 1
+    if fails == n:
+        return None
+    return dict(value=total, cores=n - fails, dof=dof, steps=steps)
+
+
+def _oracle_code(budget_s, crop, tol, direction=0):
+    return r"""
 import json, sys, time
 sys.path.insert(0, %r)
 from synth import configs
 from oracle import fem, newmark
-cfg = configs.config2(n_steps=200, crop=%d)
+cfg = configs.config2(n_steps=200, crop=%d, direction=%d)
 ops = fem.assemble(cfg["mesh"], cfg["mat"], cfg["band"])
 dt = cfg["dt"]
 C = (ops["CR"] + ops["Cabs"]).tocsr()
@@ -132,7 +170,16 @@ while True:
     if el > %g or steps >= 200:
         break
 print(json.dumps(dict(dof=n, steps=steps, seconds=el, iters=iters)))
-""" % (ROOT, crop, tol, budget_s)
+""" % (ROOT, crop, direction, tol, budget_s)
+
+
+def cpu_oracle_sample(budget_s=15.0, crop=12, tol=1e-8):
+    """Time the FP64 CPU oracle on a bounded sample of the same workload.
+
+    Runs in a child process with one BLAS/OpenMP thread: the oracle's CSR
+    product and vector updates are single-threaded, so cores = 1.
+    """
+    code = _oracle_code(budget_s, crop, tol)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
     if r.returncode != 0:
@@ -235,9 +282,8 @@ def run_candidates(args, rank, world, dist):
                      inner_rtol=args.inner_rtol, guess_order=args.guess_order)
         models.append(m)
         dof += 3 * cfg["mesh"]["xyz"].shape[0]
-    # the plain FP64 form advances the candidates one after another (host-driven
-    # block-Jacobi PCG); the mixed form advances them together in one graph per step
-    batch = ctx.batch(models) if prec != 0 else None
+    # every form advances the candidates together, one captured graph launch per step
+    batch = ctx.batch(models)
 
     def advance(n):
         if batch is not None:
@@ -279,8 +325,7 @@ def run_candidates(args, rank, world, dist):
             "dtype": "f64" if prec == 0 else "f64+%s" % {"fp32": "f32", "fp16": "f16/f32"}[args.precision],
             "data": "synthetic",
             "config": {"workload": "%d mixed-ensemble candidates (120x120x300 m, 287,451 DOF each), one directional "
-                                   "analysis each, %s" % (args.models, "batched" if batch is not None else
-                                                          "one after another (plain FP64 form)"),
+                                   "analysis each, batched" % args.models,
                        "dof_total": dof, "dof_steps_per_s": world * dof * args.steps / t_max, "tol": args.tol,
                        "precision": args.precision, "inner_iters": args.inner, "batch_outer": args.batch_outer,
                        "guess_order": args.guess_order,
@@ -292,6 +337,94 @@ def run_candidates(args, rank, world, dist):
     if batch is not None:
         batch.close()
     ctx.close()
+
+
+def candidates_block(ctx, n_models, warmup, steps, tol, inner, guess_order, seq_models=16):
+    """Candidate analyses/h of the mixed-ensemble candidates (120 x 120 x 300 m,
+    287,451 DOF each, seeded interfaces, one directional analysis each, directions
+    cycling x1, x2, x3) in three forms, each timed over `steps` steps after
+    `warmup` steps from rest (CUDA events on the library's stream):
+    the batched mixed form (one captured graph launch per time step), the batched
+    plain FP64 form (block-Jacobi PCG from the Newmark predictor, every PCG
+    iteration in the graph's device-side loop) and the plain FP64 form run one
+    model after another with host-driven steps (timed on `seq_models` of the
+    models; all candidates have the same size, so the time scales linearly)."""
+    import torch
+
+    from synth import configs
+
+    n_total = warmup + steps
+    models, dof = [], 0
+    for l in range(n_models):
+        cfg = configs.config4_candidate(l, n_steps=n_total, direction=l % 3)
+        m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
+        m.set_time(cfg["dt"], n_total, cfg["band"])
+        m.set_input(cfg["dir"], cfg["p"])
+        m.set_solver(tol=tol, precision=2, inner_iters=inner, guess_order=guess_order)
+        models.append(m)
+        dof += 3 * cfg["mesh"]["xyz"].shape[0]
+    stream = ctx.stream
+
+    def timed(advance, group):
+        advance(warmup)
+        it0 = sum(m.stats()["cg_iters_total"] for m in group)
+        kl0 = sum(m.stats()["kernel_launches"] for m in group)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        advance(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / steps
+        it = (sum(m.stats()["cg_iters_total"] for m in group) - it0) / (steps * len(group))
+        kl = sum(m.stats()["kernel_launches"] for m in group) - kl0
+        return t, it, kl
+
+    def cah(per_step_s):
+        # one candidate analysis = 3 directional runs of 2000 steps (+ a misfit, negligible)
+        return n_models / 3.0 * 3600.0 / (2000 * per_step_s)
+
+    out = {"workload": "%d mixed-ensemble candidates (120x120x300 m, 287,451 DOF each, seeded interfaces), "
+                       "one directional analysis each" % n_models, "dof_total": dof, "steps": steps,
+           "warmup": warmup, "tol": tol}
+    b = ctx.batch(models)
+    t, it, kl = timed(b.step, models)
+    lps = b.launches_per_step()
+    b.close()
+    out["batched_mixed"] = {"candidate_analyses_per_hour": cah(t), "ms_per_step": 1e3 * t,
+                            "outer_iters_per_model_step": it, "dof_steps_per_s": dof / t, "gpu_launches": kl,
+                            "graph_kernel_nodes_captured": lps,
+                            "solver": "flexible CG (FP64, double-word outer operator) + fp16 block-Jacobi PCG "
+                                      "preconditioner, %d iterations; initial guess order %d" % (inner, guess_order)}
+    for m in models:
+        m.set_solver(tol=tol, precision=0, guess_order=0)
+        m.reset()
+    b = ctx.batch(models)
+    t, it, kl = timed(b.step, models)
+    b.close()
+    out["batched_fp64"] = {"candidate_analyses_per_hour": cah(t), "ms_per_step": 1e3 * t,
+                           "pcg_iters_per_model_step": it, "dof_steps_per_s": dof / t, "gpu_launches": kl,
+                           "solver": "block-Jacobi PCG (FP64) from the Newmark predictor"}
+    sub = models[:seq_models]
+    for m in sub:
+        m.reset()
+
+    def seq(n):
+        for m in sub:
+            m.step(n)
+
+    t, it, kl = timed(seq, sub)
+    t *= n_models / len(sub)
+    out["plain_fp64_one_after_another"] = {
+        "candidate_analyses_per_hour": cah(t), "ms_per_step": 1e3 * t, "pcg_iters_per_model_step": it,
+        "timed_models": len(sub), "solver": "block-Jacobi PCG (FP64) from the Newmark predictor, host-driven"}
+    base = out["plain_fp64_one_after_another"]["candidate_analyses_per_hour"]
+    out["speedup_batched_mixed_vs_plain_fp64"] = out["batched_mixed"]["candidate_analyses_per_hour"] / base
+    out["speedup_batched_fp64_vs_plain_fp64"] = out["batched_fp64"]["candidate_analyses_per_hour"] / base
+    out["l2"] = "inputs larger than L2 (%.1f GB resident)" % (sum(m.info()["device_bytes"] for m in models) / 1e9)
+    for m in models:
+        m.free()
+    return out
 
 
 def run_learned(args, rank, world, dist):
@@ -388,6 +521,8 @@ def main():
                          "the mixed modes, FP64 in the FP64 mode")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the plain FP64 form and the candidates block of the default line")
     args = ap.parse_args()
     if args.inner <= 0:
         # tuned on GB300 with the quartic initial guess: fewest ms per step (the realistic model
@@ -492,6 +627,7 @@ def main():
     tim = m.timing(False)
     ebe_ms, ebe_n = tim["fp64"]
     lo_ms, lo_n = tim["inner"]
+    m_info = m.info()
     t_max = shard.max_over_ranks(t, dist)
     value = world * dof * args.steps / t_max
     launches = st["kernel_launches"] - launches0
@@ -522,51 +658,74 @@ def main():
             dist.destroy_process_group()
         return
 
+    # ---- the plain FP64 form over the same window ---------------------------------------
+    plain = None
+    if not args.no_extras and args.precision != "fp64":
+        m.set_solver(tol=args.tol, precision=0, guess_order=0)
+        m.reset()
+        m.step(args.warmup)
+        s0 = m.stats()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        m.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tp = e0.elapsed_time(e1) / 1e3
+        s1 = m.stats()
+        plain = {"ms_per_step": 1e3 * tp / args.steps, "value": dof * args.steps / tp, "unit": "DOF*steps/s",
+                 "pcg_iters_per_step": (s1["cg_iters_total"] - s0["cg_iters_total"]) / args.steps,
+                 "solver": "block-Jacobi PCG (FP64 operator, FP64 vectors) from the Newmark predictor",
+                 "window": "steps %d-%d (the timed window above)" % (args.warmup, args.warmup + args.steps - 1)}
+    m.free()
+
     pk = peaks()
     n_abs = int((mesh["face_tag"] > 0).sum())
+    n_vert = int(np.unique(mesh["conn"][:, :4]).size)
     per_launch_s = (ebe_ms / 1e3) / max(1, ebe_n)
     flops = EBE_FLOPS_PER_ELEM * n_elem + EBE_FLOPS_PER_FACE * n_abs
     achieved_tf = flops / per_launch_s / 1e12 if ebe_n else None
-    nbytes = ebe_bytes(n_nodes, n_elem, n_faces)
+    fp64_bytes = unique_node_bytes(n_nodes, n_elem, n_vert, 8, 8)
+    bytes_note = ("algorithmic bytes N*3*(s_x+s_y) + E*44 + N_v*24: unique node vectors x (s_x bytes per value) and "
+                  "y (s_y), 10 node ids and a material id per element, vertex coordinates")
     dword = args.outer_op == "dword" or (args.outer_op == "auto" and args.precision != "fp64")
+    fp64_roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                 "frac": (achieved_tf / FP64_PEAK_TFLOPS) if achieved_tf else None,
+                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (the FP64 pipe; a DFMA probe "
+                                "measured 1.20 TFLOP/s at 2.0 GHz)",
+                 "flops_per_launch": flops, "launch_ms": per_launch_s * 1e3, "launches_timed": ebe_n,
+                 "time_share": ebe_ms / (1e3 * t_roof),
+                 "hbm": {"algorithmic_bytes": fp64_bytes, "achieved": fp64_bytes / per_launch_s / 1e9 if ebe_n else None,
+                         "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                         "frac": fp64_bytes / per_launch_s / 1e9 / pk.get("hbm_gbs") if ebe_n else None,
+                         "basis": bytes_note + " (s_x = s_y = 8)"}}
     if dword:
-        # issue-bound on the FP32 pipe: the peak is the instruction issue rate divided by the
-        # instructions the double-word element needs per algorithmic flop (ncu count, same source)
-        ipe = profile_value(DW_SOURCES, "ebe_dw_realistic.md", "thread_instructions_per_element")
-        peak_tf = ISSUE_PEAK * EBE_FLOPS_PER_ELEM / ipe / 1e12 if ipe else None
-        fp64_roof = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                     "frac": (achieved_tf / peak_tf) if (achieved_tf and peak_tf) else None,
-                     "traffic": traffic_from_profile(DW_SOURCES, "ebe_dw_realistic.md"),
-                     "kernel": "ebe_dw_kernel<0> (double-word element-by-element A p, FP32 pipe)",
-                     "peak_source": "derived: instruction issue 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz / "
-                                    "%s thread instructions per element (ncu) x %d flop per element" % (
-                                        "%.0f" % ipe if ipe else "?", EBE_FLOPS_PER_ELEM),
-                     "flops_per_launch": flops, "launch_ms": per_launch_s * 1e3, "launches_timed": ebe_n,
-                     "time_share": ebe_ms / (1e3 * t_roof), "algorithmic_bytes": nbytes}
+        fp64_roof.update({
+            "traffic": traffic_from_profile(DW_SOURCES, "ebe_dw_realistic.md"),
+            "kernel": "ebe_dw_kernel<0> (double-word element-by-element A p on the FP32 pipe)",
+            "note": "FP64-accurate arithmetic (paired FP32, about 48 significant bits) measured against the FP64 "
+                    "pipe's peak: a fraction above 1 is the gain of running it on the FP32 pipe"})
     else:
-        fp64_roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": (achieved_tf / FP64_PEAK_TFLOPS) if achieved_tf else None,
-                     "traffic": traffic_from_profile(FP64_SOURCES, "ebe_fp64_realistic.md"),
-                     "kernel": "ebe_kernel<0> (FP64 element-by-element A p)",
-                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FP64 pipe; a DFMA probe "
-                                    "measured 1.20 TFLOP/s at 2.0 GHz)",
-                     "flops_per_launch": flops, "launch_ms": per_launch_s * 1e3, "launches_timed": ebe_n,
-                     "time_share": ebe_ms / (1e3 * t_roof), "algorithmic_bytes": nbytes}
+        fp64_roof.update({"traffic": traffic_from_profile(FP64_SOURCES, "ebe_fp64_realistic.md"),
+                          "kernel": "ebe_kernel<0> (FP64 element-by-element A p)"})
     inner_roof = None
     if lo_n:
         lo_launch_s = (lo_ms / 1e3) / lo_n
         # variants 0 and 1 fuse the direction recurrence on small models only (grid <= 2048 CTAs)
-        lo_fused = m.info()["inner_variant"] in (0, 1) and (n_elem + 191) // 192 + (n_faces + 191) // 192 <= 2048
-        lo_bytes = inner_bytes(n_nodes, n_elem, n_faces, args.precision == "fp16", lo_fused)
+        lo_fused = m_info["inner_variant"] in (0, 1) and (n_elem + 191) // 192 + (n_faces + 191) // 192 <= 2048
+        s_x = 2 if args.precision == "fp16" else 4
+        lo_bytes = unique_node_bytes(n_nodes, n_elem, n_vert, s_x, 4)
         inner_roof = {"bound": "hbm", "achieved": lo_bytes / lo_launch_s / 1e9, "peak": pk.get("hbm_gbs"),
                       "unit": "GB/s", "frac": lo_bytes / lo_launch_s / 1e9 / pk.get("hbm_gbs"),
                       "traffic": traffic_from_profile(INNER_SOURCES, "ebe_inner_%s_realistic.md" % args.precision),
                       "kernel": "%s (%s inner element-by-element A d%s)" % (
-                          LO_KERNELS.get(m.info()["inner_variant"], "ebe_lo"), args.precision,
+                          LO_KERNELS.get(m_info["inner_variant"], "ebe_lo"), args.precision,
                           ", with the fused direction recurrence d = t + beta d" if lo_fused else ""),
                       "peak_source": "of measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                      "algorithmic_bytes": lo_bytes, "launch_ms": lo_launch_s * 1e3, "launches_timed": lo_n,
-                      "time_share": lo_ms / (1e3 * t_roof)}
+                      "algorithmic_bytes": lo_bytes, "basis": bytes_note + " (s_x = %d, s_y = 4)" % s_x,
+                      "layout_bytes": inner_bytes(n_nodes, n_elem, n_faces, args.precision == "fp16", lo_fused),
+                      "layout_bytes_note": "bytes the kernel's own layout must move (y zeroed and re-read, the "
+                                           "block node lists, 9 stored gradients and a volume per element)",
+                      "launch_ms": lo_launch_s * 1e3, "launches_timed": lo_n, "time_share": lo_ms / (1e3 * t_roof)}
     roof = fp64_roof
     if inner_roof is not None and lo_ms > ebe_ms:
         roof = dict(inner_roof, secondary=fp64_roof)
@@ -574,14 +733,24 @@ def main():
         roof = dict(fp64_roof, secondary=inner_roof)
     cpu = None
     if not args.no_cpu_baseline:
+        cores, cpu_name = host_cpu()
         d, err = cpu_oracle_sample()
         if d is not None:
             cpu = {"value": d["dof"] * d["steps"] / d["seconds"], "unit": "DOF*steps/s", "cores": 1,
-                   "kind": "oracle",
+                   "kind": "oracle", "host_cores": cores, "cpu": cpu_name,
                    "sample": "FP64 CPU oracle on a 120 x 120 m lateral crop of the same model (%d DOF), %d steps "
-                             "from rest, %.1f s" % (d["dof"], d["steps"], d["seconds"])}
+                             "from rest, %.1f s, one thread" % (d["dof"], d["steps"], d["seconds"])}
+            allc = cpu_oracle_all_cores()
+            if allc is not None:
+                cpu["all_cores"] = {"value": allc["value"], "unit": "DOF*steps/s", "cores": allc["cores"],
+                                    "sample": "%d single-threaded oracle processes at once, one directional analysis "
+                                              "of the same crop each, %d steps in all" % (allc["cores"],
+                                                                                          allc["steps"])}
         else:
             cpu = {"value": None, "unit": "DOF*steps/s", "cores": 1, "kind": "oracle", "sample": "failed: " + err}
+    cand = None
+    if not args.no_extras and args.workload == "realistic":
+        cand = candidates_block(ctx, args.models, args.warmup, args.steps, args.tol, 25, args.guess_order)
     out = {
         "metric": "DOF*steps/s", "value": value, "unit": "DOF*steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
@@ -597,11 +766,14 @@ def main():
                               "flexible CG (FP64) + %s block-Jacobi PCG preconditioner to relative %g (at most %d "
                               "iterations)" % (args.precision, args.inner_rtol, args.inner)),
                    "inner_iters_per_step": (st["inner_iters_total"] - inner0) / args.steps,
-                   "inner_operator_variant": m.info()["inner_variant"], "parallelism": "independent directional analyses, 1 per GPU",
+                   "inner_operator_variant": m_info["inner_variant"], "parallelism": "independent directional analyses, 1 per GPU",
                    "cg_iters_per_step": iters / args.steps,
                    "l2": "inputs larger than L2 (FP64 working set %.1f GB)" % (
                        (14 * 3 * n_nodes * 8 + n_elem * 124) / 1e9),
-                   "candidate_analyses_per_hour_extrapolated": 3600.0 / (3 * 4000 * t_max / args.steps)},
+                   "candidate_analyses_per_hour_extrapolated": 3600.0 / (3 * 4000 * t_max / args.steps),
+                   "plain_fp64": plain,
+                   "speedup_vs_plain_fp64": (plain["ms_per_step"] / (1e3 * t_max / args.steps)) if plain else None,
+                   "candidates": cand},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
     }
     print(json.dumps(out))

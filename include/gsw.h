@@ -19,8 +19,10 @@
  *    (device memory on the context's GPU).  The library copies what it needs
  *    from host arrays during the call; the caller keeps ownership.
  *  - Arrays are C-contiguous.  Node-major vectors are [n_nodes][3] float64.
- *  - Device memory is allocated through the allocator set by
- *    gsw_set_allocator (default: cudaMallocAsync on the context's stream).
+ *  - Device memory (model data, batch step states, misfit scratch) is
+ *    allocated through the allocator set by gsw_set_allocator (default:
+ *    cudaMallocAsync on the context's stream); gsw_misfit_noalloc allocates
+ *    none.
  *  - All GPU work is issued on the stream given to gsw_create.  Calls that
  *    return host data synchronise that stream.
  *  - A context is not thread-safe; use one per host thread.
@@ -188,18 +190,22 @@ gsw_status gsw_reset(gsw_ctx *ctx, int32_t model_id);
 gsw_status gsw_step(gsw_ctx *ctx, int32_t model_id, int32_t n);
 
 /* Run every listed model from rest through all its steps (one directional
- * analysis each).  Models in a mixed precision mode run together as one
- * batch (see gsw_batch_create); FP64 models run one after the other. */
+ * analysis each).  The models run together as one batch (see
+ * gsw_batch_create), except those with the learned guess enabled, which run
+ * one after the other with host-driven steps. */
 gsw_status gsw_run(gsw_ctx *ctx, const int32_t *model_ids, int32_t n_models);
 
-/* ---- batched stepping (mixed precision modes) ----------------------------
- * A batch advances several models (uneven sizes allowed) together: every
- * time step of every model runs on the device without host synchronisation
- * (device-side step counter and input samples; after a step's first
- * flexible-CG iteration the others run in a device-side loop of the graph,
- * a WHILE conditional node, until the step converges or the budget
- * solver_opts.batch_outer is used up), each model on its own stream, all
- * captured into one CUDA graph that is launched once per time step.  Where
+/* ---- batched stepping ------------------------------------------------------
+ * A batch advances several models (uneven sizes and any mix of precision
+ * modes allowed) together: every time step of every model runs on the device
+ * without host synchronisation (device-side step counter and input samples;
+ * the CG iterations run in a device-side loop of the graph, a WHILE
+ * conditional node, until the step converges or the budget is used up: in the
+ * mixed modes the flexible-CG iterations after a step's first, at most
+ * solver_opts.batch_outer; in GSW_PREC_FP64 every block-Jacobi PCG iteration,
+ * at most batch_outer, or 1000 when batch_outer = 0), each model on its own
+ * stream, all captured into one CUDA graph that is launched once per time
+ * step.  Where
  * the conditional node cannot be built, the budget is unrolled into the
  * graph (kernels of a converged step return at entry).  Models that reach their
  * n_steps stop advancing; a step that needs more outer iterations than the
@@ -304,6 +310,22 @@ gsw_status gsw_mlp_grad(gsw_ctx *ctx, int32_t model_id, int32_t n, const float *
  * After training, every 10th step is a probe with the plain predictor; the
  * judge reverts to the predictor for good when [3] (over 5 steps) exceeds [2]. */
 gsw_status gsw_mlp_state(gsw_ctx *ctx, int32_t model_id, double *out);
+
+/* Diagnostics of the learned guess's data path (tests), between steps of a
+ * model with learning enabled.
+ *  x_train [batch][16], y_train [batch][3] (either may be NULL): the last
+ *    training batch -- features and targets of the last Adam step of the last
+ *    training step.  Sample j of Adam step i of step s is node
+ *    H(seed ^ H(s * 0x9E3779B9 ^ H(i * 0x85EBCA6B ^ j))) mod n_nodes, with H
+ *    Wellons' "lowbias32" 32-bit hash and products modulo 2^32.
+ *  nodes [n]: for these nodes, x [n][16] receives the features and base [n][3]
+ *    the base guess (predictor, or the guess_order extrapolation) that the
+ *    next step's inference would use.
+ *  scale [2] (may be NULL): sigma (RMS of the latest increment) and the output
+ *    scale of the next step's correction.
+ * Host arrays.  GSW_E_STATE before the first converged step or without learning. */
+gsw_status gsw_mlp_inputs(gsw_ctx *ctx, int32_t model_id, float *x_train, float *y_train, int32_t n,
+                          const int32_t *nodes, float *x, double *base, double *scale);
 
 /* ---- misfit (Section 2, Eq. (2)) ----------------------------------------- */
 

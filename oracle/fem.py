@@ -272,7 +272,12 @@ def dashpot_faces(xyz, faces, face_elem, elem_mat, mat, period=(0.0, 0.0)):
 
 
 def _assemble(blocks, nodes, n_dof):
-    """Sum element blocks [E, n*3, n*3] into a CSR matrix over node lists [E, n]."""
+    """Sum element blocks [E, n*3, n*3] into a CSR matrix over node lists [E, n].
+
+    An empty block list (E = 0, e.g. a mesh with no absorbing faces) sums to
+    the zero matrix."""
+    if nodes.shape[0] == 0:
+        return sp.csr_matrix((n_dof, n_dof))
     dofs = (3 * nodes[:, :, None] + np.arange(3)[None, None, :]).reshape(nodes.shape[0], -1)
     k = dofs.shape[1]
     rows = np.repeat(dofs, k, axis=1).ravel()

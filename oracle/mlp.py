@@ -1,16 +1,29 @@
-"""Learned CG initial guess: the per-node MLP (oracle).
+"""Learned CG initial guess: the per-node MLP and its data path (oracle).
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-The network maps 16 per-node features to a 3-component correction of the
-standard Newmark predictor (dt v + dt^2/2 a):
+The network maps 16 per-node features to a 3-component correction of a base
+initial guess for step s (the method's spec form (4): the network
+predicts each step's CG initial guess from the previous steps' increments):
 
     features  x = [du_{s-1}, du_{s-2}, du_{s-3}, du_{s-4}] / sigma  (12 values)
                   ++ [Vs / 1000, Vp / 3000, rho / 2000, h / 0.05] of the node's layer
-    sigma     = RMS over all DOF of du_{s-1}
+                  (the lowest layer index among the elements touching the node)
+    sigma     = RMS over all DOF of du_{s-1} (1 if that is zero)
     network   h1 = relu(x W1 + b1) (64), h2 = relu(h1 W2 + b2) (64), o = h2 W3 + b3 (3)
-    guess     du0 = dt v + dt^2/2 a + sigma * o
-    target    (du_s - dt v - dt^2/2 a) / sigma, loss = mean over the batch of |o - target|^2
+    base      the Newmark predictor dt v + dt^2/2 a (guess order 0), or the
+              degree-k polynomial through the last k+1 increments evaluated one
+              step ahead (guess order k, once k+1 increments exist)
+    scale     sigma for the predictor base; for a polynomial base, the RMS of
+              the previous step's correction du_{s-1} - base_{s-1}
+    guess     du0 = base + scale * o
+    target    of training step s: (du_s - base_s) / scale_s, where scale_s is
+              sigma for the predictor base and RMS(du_s - base_s) for a
+              polynomial base; loss = mean over the batch of |o - target|^2
+
+Training samples of step s, Adam iteration i, batch slot j are nodes
+hash(seed, s, i, j) mod N, with the counter-based hash built from Wellons'
+"lowbias32" integer mixer (see :func:`sample_nodes`).
 
 Parameters are packed in one vector: W1 [16,64], b1 [64], W2 [64,64], b2 [64],
 W3 [64,3], b3 [3] (row-major), 5,443 values.  Training uses Adam
@@ -101,3 +114,107 @@ def forward_bf16(theta, X):
     h = bf16(np.maximum(h @ bf16(p["W1"]) + p["b1"], 0.0))
     h = bf16(np.maximum(h @ bf16(p["W2"]) + p["b2"], 0.0))
     return h @ bf16(p["W3"]) + p["b3"]
+
+
+# ----------------------------------------------------------------------------
+# Data path of the learned guess: features, base guess, scale, targets
+# ----------------------------------------------------------------------------
+
+
+def layer_features(mesh, mat):
+    """[N, 4] layer features of each node: (Vs/1000, Vp/3000, rho/2000, h/0.05)
+    of the lowest layer index among the elements touching it (layer 0 for a
+    node in no element)."""
+    n = mesh["xyz"].shape[0]
+    conn = np.asarray(mesh["conn"], dtype=np.int64)
+    em = np.asarray(mesh["elem_mat"], dtype=np.int64)
+    big = np.iinfo(np.int64).max
+    lay = np.full(n, big, dtype=np.int64)
+    for k in range(conn.shape[1]):
+        np.minimum.at(lay, conn[:, k], em)
+    lay[lay == big] = 0
+    m = np.asarray(mat, dtype=np.float64)[lay]
+    return np.stack([m[:, 1] / 1000.0, m[:, 0] / 3000.0, m[:, 2] / 2000.0, m[:, 3] / 0.05], axis=1)
+
+
+def rms(x):
+    x = np.asarray(x, dtype=np.float64).ravel()
+    return float(np.sqrt(np.mean(x * x)))
+
+
+def features(history, nodef):
+    """Features [N, 16] and sigma from ``history`` = [du_{s-1}, du_{s-2},
+    du_{s-3}, du_{s-4}] (each [N, 3], latest first) and layer features [N, 4]."""
+    sigma = rms(history[0])
+    if sigma == 0.0:
+        sigma = 1.0
+    X = np.concatenate([np.asarray(h, dtype=np.float64).reshape(-1, 3) / sigma for h in history[:4]]
+                       + [np.asarray(nodef, dtype=np.float64)], axis=1)
+    return X, sigma
+
+
+def extrapolate(increments, k):
+    """Degree-k polynomial through the last k+1 increments, one step ahead.
+
+    ``increments[j]`` is the increment j steps back (j = 0 the latest, at
+    t = 0; increment j sits at t = -j).  The polynomial is written in
+    Lagrange form and evaluated at t = 1."""
+    t = -np.arange(k + 1, dtype=np.float64)
+    out = np.zeros_like(np.asarray(increments[0], dtype=np.float64))
+    for j in range(k + 1):
+        L = 1.0
+        for m in range(k + 1):
+            if m != j:
+                L *= (1.0 - t[m]) / (t[j] - t[m])
+        out = out + L * np.asarray(increments[j], dtype=np.float64)
+    return out
+
+
+def base_guess(v, a, dt, increments, k):
+    """Base initial guess of a step: the polynomial extrapolation of order k
+    when k > 0 and k+1 increments exist, else the Newmark predictor."""
+    if k > 0 and len(increments) >= k + 1:
+        return extrapolate(increments, k)
+    return dt * np.asarray(v, dtype=np.float64) + 0.5 * dt * dt * np.asarray(a, dtype=np.float64)
+
+
+def correction_scale(du, base, sigma):
+    """RMS of the correction du - base, or sigma when the correction is zero."""
+    r = rms(np.asarray(du) - np.asarray(base))
+    return r if r > 0.0 else sigma
+
+
+def targets(du, base, scale):
+    """Training targets (du - base) / scale, [N, 3]."""
+    return ((np.asarray(du, dtype=np.float64) - np.asarray(base, dtype=np.float64)) / scale).reshape(-1, 3)
+
+
+def learned_guess(theta, X, base, scale):
+    """du0 = base + scale * o, o from the BF16 inference (:func:`forward_bf16`)."""
+    return np.asarray(base, dtype=np.float64).reshape(-1, 3) + scale * forward_bf16(theta, X)
+
+
+_M32 = np.uint64(0xFFFFFFFF)
+
+
+def lowbias32(x):
+    """Wellons' "lowbias32" 32-bit integer hash (xorshift-multiply, constants
+    0x7feb352d and 0x846ca68b), on uint64 arrays holding 32-bit values."""
+    x = np.asarray(x, dtype=np.uint64) & _M32
+    x = x ^ (x >> np.uint64(16))
+    x = (x * np.uint64(0x7FEB352D)) & _M32
+    x = x ^ (x >> np.uint64(15))
+    x = (x * np.uint64(0x846CA68B)) & _M32
+    x = x ^ (x >> np.uint64(16))
+    return x
+
+
+def sample_nodes(n_nodes, batch, seed, step, it):
+    """Node index of each training sample: h mod N with
+    h = H(seed ^ H(step * 0x9E3779B9 ^ H(it * 0x85EBCA6B ^ j))), H = lowbias32,
+    products taken modulo 2^32."""
+    j = np.arange(batch, dtype=np.uint64)
+    inner = lowbias32(((np.uint64(it) * np.uint64(0x85EBCA6B)) & _M32) ^ j)
+    mid = lowbias32(((np.uint64(step) * np.uint64(0x9E3779B9)) & _M32) ^ inner)
+    h = lowbias32(np.uint64(seed) ^ mid)
+    return (h % np.uint64(n_nodes)).astype(np.int64)

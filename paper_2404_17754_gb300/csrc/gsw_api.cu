@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -157,6 +158,11 @@ struct gsw_ctx {
 // model's device-driven step on its own stream branch.
 // Kernel launches of one captured step, split into the part issued once per
 // step and the device-side loop body (issued once per further outer iteration).
+// PCG iterations an FP64 member's step may run inside the step graph's
+// device-side loop (batch_outer = 0); a step that needs more is finished by
+// the host-driven solver.
+constexpr int kFp64LoopCap = 1000;
+
 struct StepLaunches {
   int64_t fixed = 0, body = 0;
 };
@@ -174,6 +180,7 @@ struct Batch {
   StepState* ss_host = nullptr;  // pinned
   int64_t launches_per_step = 0;
   int outer = 0;
+  int fp64_loop = 0;  // device-side loop budget of the FP64 members when captured
   // adaptive budget (members with batch_outer == 0): outer iterations captured
   // per step, and the chunks in a row whose steps needed fewer
   int adapt_outer = 6;
@@ -928,22 +935,13 @@ void inner_solve_dev(Model* m, cudaStream_t s) {
   }
 }
 
-// Outer iterations 2.. of a captured step.  With a body stream, they run in a
-// WHILE conditional node of the graph (device-side loop: the body runs while
+// Iterations 2.. of a captured step's solve.  With a body stream, they run in
+// a WHILE conditional node of the graph (device-side loop: the body runs while
 // the step has not converged, at most outer - 1 times); otherwise they are
 // unrolled `outer` - 1 times (kernels of a converged step return at entry).
 // Returns false if the conditional node could not be built.
-bool issue_outer_loop(Model* m, cudaStream_t s, StepState* ss, int outer, cudaStream_t bs, StepLaunches* n) {
-  ModelView mv = m->view();
-  const int it = m->opts.inner_iters > 0 ? m->opts.inner_iters : 1;
-  const int64_t per_iter = inner_solve_launches(m, inner_fuses(m, m->lo_variant)) + 4;  // + zbeta, pupdate, A p, update
-  auto body = [&](cudaStream_t st) {
-    inner_solve_dev(m, st);
-    launch_fcg_zbeta(mv, m->y32, m->r, m->q, m->z, m->partials, m->cg, m->isc, st);
-    launch_fcg_pupdate(mv, m->z, m->p, m->q, m->cg, st, outer_dword(m) ? 1 : 0);
-    launch_outer(m, kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, st);
-    launch_fcg_update(mv, m->x, m->r, m->p, m->q, m->partials, m->cg, st, outer_dword(m) ? 1 : 0);
-  };
+bool issue_loop(cudaStream_t s, StepState* ss, CgScalars* cg, int outer, cudaStream_t bs, StepLaunches* n,
+                int64_t per_iter, const std::function<void(cudaStream_t)>& body) {
   if (bs == nullptr) {
     for (int k = 1; k < outer; ++k) body(s);
     n->fixed += per_iter * (outer - 1);
@@ -954,7 +952,7 @@ bool issue_outer_loop(Model* m, cudaStream_t s, StepState* ss, int outer, cudaSt
   if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g) != cudaSuccess || cs != cudaStreamCaptureStatusActive) return false;
   cudaGraphConditionalHandle h;
   if (cudaGraphConditionalHandleCreate(&h, g, 0, 0) != cudaSuccess) return false;
-  launch_loop_open(h, ss, m->cg, outer - 1, s);
+  launch_loop_open(h, ss, cg, outer - 1, s);
   const cudaGraphNode_t* deps = nullptr;
   const cudaGraphEdgeData* edges = nullptr;
   size_t nd = 0;
@@ -972,10 +970,56 @@ bool issue_outer_loop(Model* m, cudaStream_t s, StepState* ss, int outer, cudaSt
   if (cudaStreamBeginCaptureToGraph(bs, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     return false;
   body(bs);
-  launch_loop_next(h, ss, m->cg, outer - 1, bs);
+  launch_loop_next(h, ss, cg, outer - 1, bs);
   if (cudaStreamEndCapture(bs, &bg) != cudaSuccess) return false;
   n->fixed += 1;
   n->body += per_iter + 1;
+  return true;
+}
+
+// Outer (flexible-CG) iterations 2.. of a captured mixed step.
+bool issue_outer_loop(Model* m, cudaStream_t s, StepState* ss, int outer, cudaStream_t bs, StepLaunches* n) {
+  ModelView mv = m->view();
+  const int64_t per_iter = inner_solve_launches(m, inner_fuses(m, m->lo_variant)) + 4;  // + zbeta, pupdate, A p, update
+  return issue_loop(s, ss, m->cg, outer, bs, n, per_iter, [&](cudaStream_t st) {
+    inner_solve_dev(m, st);
+    launch_fcg_zbeta(mv, m->y32, m->r, m->q, m->z, m->partials, m->cg, m->isc, st);
+    launch_fcg_pupdate(mv, m->z, m->p, m->q, m->cg, st, outer_dword(m) ? 1 : 0);
+    launch_outer(m, kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, st);
+    launch_fcg_update(mv, m->x, m->r, m->p, m->q, m->partials, m->cg, st, outer_dword(m) ? 1 : 0);
+  });
+}
+
+// Issues one plain FP64 time step (block-Jacobi PCG) of model m on stream s
+// with no host synchronisation: step_begin, right-hand side, initial guess,
+// A x0 and the first residual, the PCG iterations in a device-side loop (at
+// most `outer` - 1 body runs of one iteration each: A p, update, direction),
+// step_end, Newmark update, receivers and step advance.
+bool issue_device_step_fp64(Model* m, cudaStream_t s, StepState* ss, int outer, cudaStream_t bs, StepLaunches* n) {
+  ModelView mv = m->view();
+  Drive dr{m->p_dev, ss};
+  launch_step_begin(ss, m->cg, s);
+  cudaMemsetAsync(m->b, 0, sizeof(double) * 3 * (size_t)m->N, s);
+  launch_ebe(kModeRhs, mv, m->u, m->v, m->a, m->b, 0.0, m->dir, nullptr, nullptr, s, dr);
+  const int k_guess = m->opts.guess_order;
+  if (k_guess > 0) launch_guess_extrap(m->N, m->guess_ring, k_guess, m->guess_ext, m->v, m->a, m->dt, m->x, s, ss);
+  launch_cg_init(mv, m->b, m->v, m->a, m->x, m->q, m->partials, m->cg, s, k_guess > 0 ? 1 : 0, ss);
+  launch_outer(m, kModeA, mv, m->x, nullptr, nullptr, m->q, 0.0, 0, nullptr, m->cg, s);
+  launch_cg_residual(mv, m->b, m->q, m->r, m->z, m->p, m->dinv, m->partials, m->cg, s);
+  n->fixed += 6 + (k_guess > 0 ? 1 : 0);
+  // the first residual may already meet the tolerance; every PCG iteration is a loop body
+  if (!issue_loop(s, ss, m->cg, outer + 1, bs, n, 3, [&](cudaStream_t st) {
+        launch_outer(m, kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, st);
+        launch_cg_update(mv, m->x, m->r, m->z, m->p, m->q, m->dinv, m->partials, m->cg, st);
+        launch_cg_pupdate(mv, m->z, m->p, m->cg, st);
+      }))
+    return false;
+  launch_step_end(ss, m->cg, s);
+  if (k_guess > 0) launch_guess_push(m->N, m->x, m->guess_ring, k_guess, m->guess_ext, s, ss);
+  launch_newmark(mv, m->x, m->u, m->v, m->a, m->cg, s, ss);
+  launch_record(m->v, m->rec_node, m->rec_w, m->n_rec, m->wave, m->n_steps, 0, s, ss);
+  launch_step_advance(ss, s);
+  n->fixed += 5;
   return true;
 }
 
@@ -1015,7 +1059,7 @@ bool issue_device_step(Model* m, cudaStream_t s, StepState* ss, int outer, cudaS
   return true;
 }
 
-void batch_free(Batch* b) {
+void batch_free(gsw_ctx* ctx, Batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
@@ -1024,7 +1068,10 @@ void batch_free(Batch* b) {
   if (b->done_ev) cudaEventDestroy(b->done_ev);
   if (b->origin) cudaStreamDestroy(b->origin);
   if (b->body_stream) cudaStreamDestroy(b->body_stream);
-  if (b->ss_dev) cudaFree(b->ss_dev);
+  if (b->ss_dev) {
+    cudaStreamSynchronize(ctx->stream);
+    dev_free(ctx, b->ss_dev);
+  }
   if (b->ss_host) cudaFreeHost(b->ss_host);
   delete b;
 }
@@ -1060,7 +1107,7 @@ void gsw_destroy(gsw_ctx* ctx) {
   if (!ctx) return;
   DeviceGuard g(ctx->device);
   cudaStreamSynchronize(ctx->stream);
-  for (auto& kv : ctx->batches) batch_free(kv.second);
+  for (auto& kv : ctx->batches) batch_free(ctx, kv.second);
   ctx->batches.clear();
   for (auto& kv : ctx->models) free_model(ctx, kv.second);
   ctx->models.clear();
@@ -1077,9 +1124,16 @@ gsw_status gsw_set_allocator(gsw_ctx* ctx, void* (*alloc)(size_t, void*, void*),
   if (!ctx->models.empty()) return fail(ctx, GSW_E_STATE, "set the allocator before uploading models");
   if ((alloc == nullptr) != (free_ == nullptr))
     return fail(ctx, GSW_E_INVALID, "alloc and free must both be set or both be NULL");
+  if (ctx->misfit.buf) {
+    misfit_free(ctx->misfit, ctx->stream);  // scratch of the previous allocator
+    cudaStreamSynchronize(ctx->stream);
+  }
   ctx->alloc = alloc;
   ctx->free_ = free_;
   ctx->user = user;
+  ctx->misfit.alloc = alloc;
+  ctx->misfit.free_ = free_;
+  ctx->misfit.user = user;
   return GSW_OK;
 }
 
@@ -1355,7 +1409,7 @@ gsw_status gsw_run(gsw_ctx* ctx, const int32_t* model_ids, int32_t n_models) {
     Model* m = find(ctx, model_ids[i]);
     if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_ids[i]);
     TRY(gsw_reset(ctx, model_ids[i]));
-    if (m->opts.precision == GSW_PREC_FP64 || m->batch || m->learn.enable) {
+    if (m->batch || m->learn.enable) {
       TRY(gsw_step(ctx, model_ids[i], m->n_steps));
     } else {
       mixed.push_back(model_ids[i]);
@@ -1381,8 +1435,8 @@ gsw_status gsw_batch_create(gsw_ctx* ctx, const int32_t* model_ids, int32_t n_mo
     Model* m = find(ctx, model_ids[i]);
     if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_ids[i]);
     if (!m->time_set || !m->input_set) return fail(ctx, GSW_E_STATE, "model %d: set the time and the input first", model_ids[i]);
-    if (m->opts.precision == GSW_PREC_FP64 || !m->lo_ready)
-      return fail(ctx, GSW_E_STATE, "model %d: batched stepping needs a mixed precision mode", model_ids[i]);
+    if (m->opts.precision != GSW_PREC_FP64 && !m->lo_ready)
+      return fail(ctx, GSW_E_STATE, "model %d: the inner solve of the mixed mode is not set up", model_ids[i]);
     if (m->batch) return fail(ctx, GSW_E_STATE, "model %d already belongs to batch %d", model_ids[i], m->batch);
     if (m->learn.enable)
       return fail(ctx, GSW_E_STATE, "model %d: the learned guess runs with host-driven stepping only", model_ids[i]);
@@ -1391,7 +1445,7 @@ gsw_status gsw_batch_create(gsw_ctx* ctx, const int32_t* model_ids, int32_t n_mo
   }
   Batch* b = new Batch();
   auto bail = [&](const char* what, cudaError_t e) {
-    batch_free(b);
+    batch_free(ctx, b);
     return fail(ctx, GSW_E_CUDA, "batch creation: %s: %s", what, cudaGetErrorString(e));
   };
   cudaError_t e;
@@ -1399,7 +1453,11 @@ gsw_status gsw_batch_create(gsw_ctx* ctx, const int32_t* model_ids, int32_t n_mo
   if ((e = cudaStreamCreateWithFlags(&b->body_stream, cudaStreamNonBlocking)) != cudaSuccess) return bail("stream", e);
   if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess) return bail("event", e);
   if ((e = cudaEventCreateWithFlags(&b->done_ev, cudaEventDisableTiming)) != cudaSuccess) return bail("event", e);
-  if ((e = cudaMalloc(&b->ss_dev, sizeof(StepState) * n_models)) != cudaSuccess) return bail("state", e);
+  b->ss_dev = (StepState*)dev_alloc(ctx, nullptr, sizeof(StepState) * n_models);
+  if (!b->ss_dev) {
+    batch_free(ctx, b);
+    return fail(ctx, GSW_E_NOMEM, "device allocation failed (batch step states)");
+  }
   if ((e = cudaMallocHost(&b->ss_host, sizeof(StepState) * n_models)) != cudaSuccess) return bail("state", e);
   for (int i = 0; i < n_models; ++i) {
     Model* m = find(ctx, model_ids[i]);
@@ -1412,7 +1470,7 @@ gsw_status gsw_batch_create(gsw_ctx* ctx, const int32_t* model_ids, int32_t n_mo
     if (!m->p_dev) {
       m->p_dev = (double*)dev_alloc(ctx, m, sizeof(double) * m->n_steps);
       if (!m->p_dev) {
-        batch_free(b);
+        batch_free(ctx, b);
         return fail(ctx, GSW_E_NOMEM, "device allocation failed (input samples)");
       }
     }
@@ -1443,12 +1501,17 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
   bool adaptive = false;
   int outer_loop = 0;  // budget of the device-side loop (adaptive members: 32)
   int remaining = 0;
+  int fp64_loop = 0;  // budget of the device-side loop of FP64 members (PCG iterations)
   for (int i = 0; i < nm; ++i) {
     Model* m = find(ctx, b->ids[i]);
-    const int o = m->opts.batch_outer > 0 ? m->opts.batch_outer : b->adapt_outer;
-    if (m->opts.batch_outer <= 0) adaptive = true;
-    if (o > outer) outer = o;
-    outer_loop = std::max(outer_loop, m->opts.batch_outer > 0 ? m->opts.batch_outer : 32);
+    if (m->opts.precision == GSW_PREC_FP64) {
+      fp64_loop = std::max(fp64_loop, m->opts.batch_outer > 0 ? m->opts.batch_outer : kFp64LoopCap);
+    } else {
+      const int o = m->opts.batch_outer > 0 ? m->opts.batch_outer : b->adapt_outer;
+      if (m->opts.batch_outer <= 0) adaptive = true;
+      if (o > outer) outer = o;
+      outer_loop = std::max(outer_loop, m->opts.batch_outer > 0 ? m->opts.batch_outer : 32);
+    }
     if (b->versions[i] != m->version) stale = true;
     StepState& h = b->ss_host[i];
     memset(&h, 0, sizeof(StepState));
@@ -1458,10 +1521,10 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
     h.failed = m->failed ? GSW_E_STATE : 0;
     h.tol = m->opts.tol;
     h.max_iter = m->opts.max_iter;
-    h.inner_iters = m->opts.inner_iters > 0 ? m->opts.inner_iters : 1;
+    h.inner_iters = m->opts.precision == GSW_PREC_FP64 ? 0 : (m->opts.inner_iters > 0 ? m->opts.inner_iters : 1);
     if (!m->failed) remaining = std::max(remaining, h.stop_at - h.step);
   }
-  if ((b->use_while ? outer_loop : outer) != b->outer) stale = true;
+  if ((b->use_while ? outer_loop : outer) != b->outer || fp64_loop != b->fp64_loop) stale = true;
   CK(cudaEventRecord(b->fork, ctx->stream));
   CK(cudaStreamWaitEvent(b->origin, b->fork, 0));
   CK(cudaMemcpyAsync(b->ss_dev, b->ss_host, sizeof(StepState) * nm, cudaMemcpyHostToDevice, b->origin));
@@ -1481,9 +1544,12 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
       b->launches.assign(nm, StepLaunches());
       for (int i = 0; i < nm && ok; ++i) {
         Model* m = find(ctx, b->ids[i]);
+        const bool fp64 = m->opts.precision == GSW_PREC_FP64;
         ok = cudaStreamWaitEvent(b->streams[i], b->fork, 0) == cudaSuccess &&
-             issue_device_step(m, b->streams[i], b->ss_dev + i, wl ? outer_loop : outer,
-                               wl ? b->body_stream : nullptr, &b->launches[i]) &&
+             (fp64 ? issue_device_step_fp64(m, b->streams[i], b->ss_dev + i, wl ? fp64_loop : outer,
+                                            wl ? b->body_stream : nullptr, &b->launches[i])
+                   : issue_device_step(m, b->streams[i], b->ss_dev + i, wl ? outer_loop : outer,
+                                       wl ? b->body_stream : nullptr, &b->launches[i])) &&
              cudaEventRecord(b->joins[i], b->streams[i]) == cudaSuccess &&
              cudaStreamWaitEvent(b->origin, b->joins[i], 0) == cudaSuccess;
       }
@@ -1501,6 +1567,7 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
     for (const StepLaunches& l : b->launches) launches += l.fixed + l.body;
     b->launches_per_step = launches;
     b->outer = b->use_while ? outer_loop : outer;
+    b->fp64_loop = fp64_loop;
     for (int i = 0; i < nm; ++i) b->versions[i] = find(ctx, b->ids[i])->version;
     return GSW_OK;
   };
@@ -1526,8 +1593,10 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
       {
         // launches issued for this member: the fixed part of every graph
         // launch, plus one loop body per outer iteration after a step's first
+        // (an FP64 member runs every PCG iteration in the loop)
         const StepLaunches& l = b->launches[i];
-        const int64_t extra = std::max<int64_t>(0, h.iters_total - advanced);
+        const bool fp64 = m->opts.precision == GSW_PREC_FP64;
+        const int64_t extra = fp64 ? h.iters_total : std::max<int64_t>(0, h.iters_total - advanced);
         m->stats.kernel_launches += (int64_t)launch_n * l.fixed + (b->use_while ? extra * l.body : 0);
       }
       if (advanced > 0) {
@@ -1535,7 +1604,7 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
         m->stats.relres_last = h.relres_last;
       }
       if (h.iters_max > m->stats.cg_iters_max) m->stats.cg_iters_max = h.iters_max;
-      need = std::max(need, h.iters_max);
+      if (m->opts.precision != GSW_PREC_FP64) need = std::max(need, h.iters_max);
       h.iters_total = h.inner_total = h.iters_max = 0;
       rewrite = true;
       if (h.failed && !m->failed) {
@@ -1551,7 +1620,7 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
         // the host-driven path (same algorithm, iteration cap max_iter)
         CK(cudaEventRecord(b->done_ev, b->origin));
         CK(cudaStreamWaitEvent(ctx->stream, b->done_ev, 0));
-        gsw_status hs = step_mixed(ctx, m);
+        gsw_status hs = m->opts.precision == GSW_PREC_FP64 ? step_fp64(ctx, m) : step_mixed(ctx, m);
         if (hs != GSW_OK) {
           h.failed = hs;
           h.fail_step = h.step;
@@ -1559,7 +1628,7 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
         } else {
           h.step = (int)m->step;
           h.needs_host = 0;
-          need = std::max(need, m->stats.cg_iters_last);
+          if (m->opts.precision != GSW_PREC_FP64) need = std::max(need, m->stats.cg_iters_last);
         }
         CK(cudaEventRecord(b->fork, ctx->stream));
         CK(cudaStreamWaitEvent(b->origin, b->fork, 0));
@@ -1613,7 +1682,7 @@ gsw_status gsw_batch_destroy(gsw_ctx* ctx, int32_t batch_id) {
     Model* m = find(ctx, id);
     if (m) m->batch = 0;
   }
-  batch_free(it->second);
+  batch_free(ctx, it->second);
   ctx->batches.erase(it);
   return GSW_OK;
 }
@@ -1915,6 +1984,65 @@ gsw_status gsw_mlp_state(gsw_ctx* ctx, int32_t model_id, double* out) {
   for (int64_t i = 0; i < k; ++i) mean += m->mlp_r0_recent[i];
   out[3] = k ? mean / (double)k : 0.0;
   out[4] = (double)m->mlp_r0_n;
+  return GSW_OK;
+}
+
+gsw_status gsw_mlp_inputs(gsw_ctx* ctx, int32_t model_id, float* x_train, float* y_train, int32_t n,
+                          const int32_t* nodes, float* x, double* base, double* scale) {
+  if (!ctx) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (!m->learn.enable || !m->mlp_ready) return fail(ctx, GSW_E_STATE, "the learned guess is not enabled");
+  if (n < 0 || n > 65536 || (n > 0 && (!nodes || !x || !base)))
+    return fail(ctx, GSW_E_INVALID, "need 0 <= n <= 65536 and node, feature and base arrays");
+  for (int i = 0; i < n; ++i)
+    if (nodes[i] < 0 || nodes[i] >= m->N) return fail(ctx, GSW_E_INVALID, "node %d out of range", nodes[i]);
+  if ((n > 0 || scale) && m->hist_count < 1) return fail(ctx, GSW_E_STATE, "no converged step yet");
+  cudaStream_t s = ctx->stream;
+  const int B = m->learn.batch;
+  if (x_train) CK(cudaMemcpyAsync(x_train, m->trainX, sizeof(float) * 16 * (size_t)B, cudaMemcpyDeviceToHost, s));
+  if (y_train) CK(cudaMemcpyAsync(y_train, m->trainY, sizeof(float) * 3 * (size_t)B, cudaMemcpyDeviceToHost, s));
+  if (n > 0 || scale) {
+    // the next step's inputs: sigma of the latest increment, the base guess
+    launch_mlp_sigma(m->N, m->hist, m->hist_head, m->partials, m->ms, s);
+    const double* xb = nullptr;
+    if (m->opts.guess_order > 0) {
+      if (!m->guess_base) TRY(alloc_into(ctx, m, &m->guess_base, 3 * (size_t)m->N));
+      launch_guess_extrap(m->N, m->guess_ring, m->opts.guess_order, m->guess_ext, m->v, m->a, m->dt, m->guess_base, s);
+      xb = m->guess_base;
+    }
+    if (n > 0) {
+      int32_t* nd = (int32_t*)dev_alloc(ctx, nullptr, sizeof(int32_t) * n);
+      float* xd = (float*)dev_alloc(ctx, nullptr, sizeof(float) * 16 * (size_t)n);
+      double* bd = (double*)dev_alloc(ctx, nullptr, sizeof(double) * 3 * (size_t)n);
+      gsw_status st = GSW_OK;
+      if (!nd || !xd || !bd) {
+        st = fail(ctx, GSW_E_NOMEM, "device allocation failed (diagnostics)");
+      } else if (cudaMemcpyAsync(nd, nodes, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        st = fail(ctx, GSW_E_CUDA, "node list copy failed");
+      } else {
+        launch_mlp_inputs(n, nd, m->N, m->hist, m->hist_head, m->nodef, m->ms, m->v, m->a, m->dt, xb, xd, bd, s);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(x, xd, sizeof(float) * 16 * (size_t)n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(base, bd, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+          st = fail(ctx, GSW_E_CUDA, "diagnostic read-back failed");
+      }
+      cudaStreamSynchronize(s);
+      dev_free(ctx, nd);
+      dev_free(ctx, xd);
+      dev_free(ctx, bd);
+      TRY(st);
+    }
+    if (scale) {
+      MlpScalars h = {};
+      CK(cudaMemcpyAsync(&h, m->ms, sizeof(MlpScalars), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      scale[0] = h.sigma;
+      scale[1] = xb ? h.sigma_e : h.sigma;
+    }
+  }
+  CK(cudaStreamSynchronize(s));
   return GSW_OK;
 }
 

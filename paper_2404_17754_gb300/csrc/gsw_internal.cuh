@@ -172,7 +172,8 @@ void launch_guess_extrap(int64_t N, const double* ring, int k, const int* ext, c
 void launch_guess_push(int64_t N, const double* du, double* ring, int k, int* ext, cudaStream_t s,
                        const StepState* ss = nullptr);
 void launch_cg_init(const ModelView& m, const double* b, const double* v, const double* a,
-                    double* x, double* q, double* partials, CgScalars* cg, cudaStream_t s, int use_guess = 0);
+                    double* x, double* q, double* partials, CgScalars* cg, cudaStream_t s, int use_guess = 0,
+                    const StepState* ss = nullptr);
 // FP32 right-hand side on the reduced-precision operator's element blocks
 // (uva: [N + 1][3] float4 scratch for the FP32 state; b32 zero on entry).
 void launch_rhs_lo(int half_geo, const void* lo_view, int64_t N, const double* u, const double* v, const double* a,
@@ -278,6 +279,9 @@ int launch_mlp_fwdbwd(int B, const float* X, const float* Y, const float* theta,
 void launch_mlp_adam(float* theta, float* grad, float* m, float* v, int t, float lr, cudaStream_t s);
 void launch_hist_push(int64_t N, const double* du, float* hist, int slot, const CgScalars* cg, cudaStream_t s,
                       const StepState* ss = nullptr);
+void launch_mlp_inputs(int n, const int32_t* nodes, int64_t N, const float* hist, int head, const float* nodef,
+                       const MlpScalars* ms, const double* v, const double* a, double dt, const double* x_base, float* X,
+                       double* base, cudaStream_t s);
 int mlp_packed_words();
 
 }  // namespace gsw

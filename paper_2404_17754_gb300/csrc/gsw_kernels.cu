@@ -676,7 +676,9 @@ __device__ __forceinline__ void apply_dinv(const double* __restrict__ d, const d
 
 __global__ void cg_init_kernel(int64_t N, const double* __restrict__ b, const double* __restrict__ v,
                                const double* __restrict__ a, double dt, double* __restrict__ x,
-                               double* __restrict__ q, double* partials, CgScalars* cg, int use_guess) {
+                               double* __restrict__ q, double* partials, CgScalars* cg, int use_guess,
+                               const StepState* ss) {
+  if (ss != nullptr && !((volatile const StepState*)ss)->active) return;
   double bb = 0.0;
   const double h = 0.5 * dt * dt;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N;
@@ -987,8 +989,9 @@ void launch_ebe_dw(int mode, int dw_in, const ModelView& m, const double* x, con
                                                                      dr);
 }
 void launch_cg_init(const ModelView& m, const double* b, const double* v, const double* a,
-                    double* x, double* q, double* partials, CgScalars* cg, cudaStream_t s, int use_guess) {
-  cg_init_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, b, v, a, m.dt, x, q, partials, cg, use_guess);
+                    double* x, double* q, double* partials, CgScalars* cg, cudaStream_t s, int use_guess,
+                    const StepState* ss) {
+  cg_init_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, b, v, a, m.dt, x, q, partials, cg, use_guess, ss);
 }
 
 // ------------------------------------------------------------------------------

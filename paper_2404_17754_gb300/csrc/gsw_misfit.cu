@@ -258,27 +258,60 @@ __global__ void err_final_kernel(const double* __restrict__ ratio, int n_pairs, 
 
 }  // namespace
 
-int misfit_run(MisfitWork& w, cudaStream_t s, int n_rec, int n_t, const double* G, const double* obs,
-               int stride, int L, double tau, double* err, double* c_out, char* msg, size_t msg_len,
-               cudaError_t* ce) {
-  const int P = 3 * L;
-  const int n_pairs = 3 * n_rec;
-  const size_t nG = (size_t)n_rec * 9 * n_t, nO = (size_t)n_rec * 3 * n_t;
-  const size_t need = nG + nO + 3 * (size_t)n_pairs + 2 * (size_t)P * P + 2 * (size_t)P + 4;
+// Green's functions from the three directions' receiver histories:
+// G[k][i][j][n] = wave_j[k][i][n], n < n_t.
+__global__ void gather_green_kernel(int n_rec, int n_t, int n_steps, const double* __restrict__ w0,
+                                    const double* __restrict__ w1, const double* __restrict__ w2,
+                                    double* __restrict__ G) {
+  const int64_t total = (int64_t)n_rec * 9 * n_t;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int n = (int)(t % n_t);
+    const int64_t kij = t / n_t;
+    const int j = (int)(kij % 3);
+    const int64_t ki = kij / 3;
+    const double* w = j == 0 ? w0 : (j == 1 ? w1 : w2);
+    G[t] = w[ki * n_steps + n];
+  }
+}
+
+namespace {
+
+int misfit_scratch(MisfitWork& w, cudaStream_t s, size_t need, char* msg, size_t msg_len) {
   if (need * sizeof(double) > w.bytes) {
-    if (w.buf) cudaFreeAsync(w.buf, s);
+    if (w.buf) {
+      if (w.free_)
+        w.free_(w.buf, (void*)s, w.user);
+      else
+        cudaFreeAsync(w.buf, s);
+    }
     w.buf = nullptr;
     w.bytes = 0;
-    if (cudaMallocAsync(&w.buf, need * sizeof(double), s) != cudaSuccess) {
+    void* p = nullptr;
+    if (w.alloc)
+      p = w.alloc(need * sizeof(double), (void*)s, w.user);
+    else if (cudaMallocAsync(&p, need * sizeof(double), s) != cudaSuccess)
+      p = nullptr;
+    if (!p) {
       snprintf(msg, msg_len, "scratch allocation of %zu bytes failed", need * sizeof(double));
       return 2;
     }
+    w.buf = (double*)p;
     w.bytes = need * sizeof(double);
   }
   if (!w.host && cudaMallocHost(&w.host, sizeof(double) * (kMisfitMaxUnknowns + 4)) != cudaSuccess) {
     snprintf(msg, msg_len, "pinned allocation failed");
     return 2;
   }
+  return 0;
+}
+
+// The misfit on device-resident G and obs (inside w.buf): weights, normal
+// equations, Jacobi eigen pseudo-inverse, ERR; results to the host.
+int misfit_core(MisfitWork& w, cudaStream_t s, int n_rec, int n_t, int stride, int L, double tau, double* err,
+                double* c_out, char* msg, size_t msg_len, cudaError_t* ce) {
+  const int P = 3 * L;
+  const int n_pairs = 3 * n_rec;
+  const size_t nG = (size_t)n_rec * 9 * n_t, nO = (size_t)n_rec * 3 * n_t;
   double* dG = w.buf;
   double* dO = dG + nG;
   double* energy = dO + nO;
@@ -296,8 +329,6 @@ int misfit_run(MisfitWork& w, cudaStream_t s, int n_rec, int n_t, const double* 
     snprintf(msg, msg_len, "%s", #call); \
     return 1;            \
   }
-  CKR(cudaMemcpyAsync(dG, G, nG * sizeof(double), cudaMemcpyHostToDevice, s));
-  CKR(cudaMemcpyAsync(dO, obs, nO * sizeof(double), cudaMemcpyHostToDevice, s));
   energy_kernel<<<n_pairs, kT, 0, s>>>(dO, n_t, energy);
   weights_kernel<<<1, kT, 0, s>>>(energy, n_pairs, wt, scal);
   assemble_A_kernel<<<dim3(P, P), kT, 0, s>>>(dG, wt, n_rec, n_t, stride, L, A);
@@ -314,6 +345,49 @@ int misfit_run(MisfitWork& w, cudaStream_t s, int n_rec, int n_t, const double* 
   *err = w.host[0];
   if (c_out) memcpy(c_out, w.host + 1, sizeof(double) * P);
   return 0;
+}
+
+size_t misfit_need(int n_rec, int n_t, int L) {
+  const int P = 3 * L;
+  const size_t n_pairs = 3 * (size_t)n_rec;
+  return (size_t)n_rec * 9 * n_t + (size_t)n_rec * 3 * n_t + 3 * n_pairs + 2 * (size_t)P * P + 2 * (size_t)P + 4;
+}
+
+}  // namespace
+
+int misfit_run(MisfitWork& w, cudaStream_t s, int n_rec, int n_t, const double* G, const double* obs,
+               int stride, int L, double tau, double* err, double* c_out, char* msg, size_t msg_len,
+               cudaError_t* ce) {
+  int rc = misfit_scratch(w, s, misfit_need(n_rec, n_t, L), msg, msg_len);
+  if (rc) return rc;
+  const size_t nG = (size_t)n_rec * 9 * n_t, nO = (size_t)n_rec * 3 * n_t;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(w.buf, G, nG * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(w.buf + nG, obs, nO * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+    *ce = e;
+    snprintf(msg, msg_len, "input copy");
+    return 1;
+  }
+  return misfit_core(w, s, n_rec, n_t, stride, L, tau, err, c_out, msg, msg_len, ce);
+}
+
+int misfit_run_waves(MisfitWork& w, cudaStream_t s, int n_rec, int n_t, int n_steps, const double* const wave[3],
+                     const double* obs, int stride, int L, double tau, double* err, double* c_out, char* msg,
+                     size_t msg_len, cudaError_t* ce) {
+  int rc = misfit_scratch(w, s, misfit_need(n_rec, n_t, L), msg, msg_len);
+  if (rc) return rc;
+  const size_t nG = (size_t)n_rec * 9 * n_t, nO = (size_t)n_rec * 3 * n_t;
+  int64_t blocks = ((int64_t)nG + kT - 1) / kT;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  gather_green_kernel<<<(unsigned)blocks, kT, 0, s>>>(n_rec, n_t, n_steps, wave[0], wave[1], wave[2], w.buf);
+  cudaError_t e;
+  if ((e = cudaGetLastError()) != cudaSuccess ||
+      (e = cudaMemcpyAsync(w.buf + nG, obs, nO * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+    *ce = e;
+    snprintf(msg, msg_len, "Green's function gather");
+    return 1;
+  }
+  return misfit_core(w, s, n_rec, n_t, stride, L, tau, err, c_out, msg, msg_len, ce);
 }
 
 // ---- allocation-free variant ---------------------------------------------------
@@ -388,7 +462,12 @@ int misfit_run_noalloc(cudaStream_t s, int device, int n_rec, int n_t, const dou
 }
 
 void misfit_free(MisfitWork& w, cudaStream_t s) {
-  if (w.buf) cudaFreeAsync(w.buf, s);
+  if (w.buf) {
+    if (w.free_)
+      w.free_(w.buf, (void*)s, w.user);
+    else
+      cudaFreeAsync(w.buf, s);
+  }
   w.buf = nullptr;
   w.bytes = 0;
   if (w.host) cudaFreeHost(w.host);

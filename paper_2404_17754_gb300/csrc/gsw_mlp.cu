@@ -267,6 +267,23 @@ __global__ void __launch_bounds__(128) mlp_infer_kernel(int64_t N, const float* 
   }
 }
 
+// Diagnostics: the features and the base guess that the next step's inference
+// would use, for the listed nodes only (X [n][16], base [n][3]).
+__global__ void mlp_inputs_kernel(int n, const int32_t* __restrict__ nodes, int64_t N, const float* __restrict__ hist,
+                                  int head, const float* __restrict__ nodef, const MlpScalars* ms,
+                                  const double* __restrict__ v, const double* __restrict__ a, double dt,
+                                  const double* __restrict__ x_base, float* X, double* base) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t nd = nodes[i];
+  const float inv_sigma = (float)(1.0 / ms->sigma);
+  for (int f = 0; f < 16; ++f) X[(int64_t)i * 16 + f] = node_feature(hist, nodef, N, head, nd, f, inv_sigma);
+  for (int c = 0; c < 3; ++c) {
+    const int64_t k = 3 * nd + c;
+    base[(int64_t)i * 3 + c] = x_base ? x_base[k] : fma(dt, v[k], 0.5 * dt * dt * a[k]);
+  }
+}
+
 // Training samples: node = hash(seed, step, iter, i) mod N; features as in
 // inference (FP32), target = (du_s - base guess) / sigma (base: the extrapolated
 // guess when given, else the Newmark predictor).
@@ -455,6 +472,11 @@ void launch_mlp_adam(float* theta, float* grad, float* m, float* v, int t, float
 void launch_hist_push(int64_t N, const double* du, float* hist, int slot, const CgScalars* cg, cudaStream_t s,
                       const StepState* ss) {
   hist_push_kernel<<<node_blocks(3 * N), kNodeThreads, 0, s>>>(N, du, hist, slot, cg, ss);
+}
+void launch_mlp_inputs(int n, const int32_t* nodes, int64_t N, const float* hist, int head, const float* nodef,
+                       const MlpScalars* ms, const double* v, const double* a, double dt, const double* x_base, float* X,
+                       double* base, cudaStream_t s) {
+  mlp_inputs_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, nodes, N, hist, head, nodef, ms, v, a, dt, x_base, X, base);
 }
 int mlp_packed_words() { return kPacked; }
 

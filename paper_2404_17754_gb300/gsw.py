@@ -93,6 +93,8 @@ SIGNATURES = {
     "gsw_mlp_forward": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     "gsw_mlp_grad": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, _dp, _dp]),
     "gsw_mlp_state": (C.c_int, [C.c_void_p, C.c_int32, _dp]),
+    "gsw_mlp_inputs": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, _ip, C.c_void_p, _dp,
+                                 _dp]),
     "gsw_misfit_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
                                      C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),
 }
@@ -215,10 +217,18 @@ class Context:
         [3, n_shifts] (optional) receive the results.  Nothing is allocated; the
         work is queued on the context's stream.  Limits: n_shifts <= 64, n_rec <= 1024.
         """
-        n_rec, n_t = obs_dev.shape[0], obs_dev.shape[2]
         for t in (G_dev, obs_dev, err_dev) + ((c_dev,) if c_dev is not None else ()):
-            assert t.is_cuda and t.is_contiguous() and t.dtype == self._torch.float64
-        assert tuple(G_dev.shape) == (n_rec, 3, 3, n_t)
+            if not (t.is_cuda and t.is_contiguous() and t.dtype == self._torch.float64):
+                raise ValueError("device arguments must be contiguous CUDA float64 tensors")
+        if obs_dev.dim() != 3 or obs_dev.shape[1] != 3:
+            raise ValueError("obs_dev must have shape (n_rec, 3, n_t)")
+        n_rec, n_t = obs_dev.shape[0], obs_dev.shape[2]
+        if tuple(G_dev.shape) != (n_rec, 3, 3, n_t):
+            raise ValueError("G_dev must have shape (n_rec, 3, 3, n_t) = (%d, 3, 3, %d)" % (n_rec, n_t))
+        if err_dev.numel() < 1:
+            raise ValueError("err_dev must hold at least one element")
+        if c_dev is not None and c_dev.numel() != 3 * n_shifts:
+            raise ValueError("c_dev must hold 3 * n_shifts = %d elements" % (3 * n_shifts))
         self._check(self.lib.gsw_misfit_noalloc(self.h, n_rec, n_t, C.c_void_p(G_dev.data_ptr()),
                                                 C.c_void_p(obs_dev.data_ptr()), stride, n_shifts, tau,
                                                 C.c_void_p(err_dev.data_ptr()),
@@ -395,6 +405,20 @@ class Model:
         out = np.zeros(5)
         self._c(self.ctx.lib.gsw_mlp_state(self.ctx.h, self.id, out.ctypes.data_as(_dp)))
         return dict(loss=out[0], active=bool(out[1]), plain_r0=out[2], learned_r0=out[3], learned_steps=int(out[4]))
+
+    def mlp_inputs(self, nodes, batch):
+        """The last training batch (X [batch, 16], Y [batch, 3]) and, for ``nodes``, the
+        features [n, 16], base guess [n, 3] and (sigma, output scale) of the next step."""
+        nodes, pn = _i(nodes)
+        n = nodes.shape[0]
+        Xt = np.zeros((batch, 16), dtype=np.float32)
+        Yt = np.zeros((batch, 3), dtype=np.float32)
+        X = np.zeros((max(n, 1), 16), dtype=np.float32)
+        base = np.zeros((max(n, 1), 3))
+        scale = np.zeros(2)
+        self._c(self.ctx.lib.gsw_mlp_inputs(self.ctx.h, self.id, Xt.ctypes.data, Yt.ctypes.data, n, pn,
+                                            X.ctypes.data, base.ctypes.data_as(_dp), scale.ctypes.data_as(_dp)))
+        return dict(x_train=Xt, y_train=Yt, x=X[:n], base=base[:n], sigma=scale[0], scale=scale[1])
 
     def mlp_loss(self):
         return self.mlp_state()["loss"]

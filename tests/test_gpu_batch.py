@@ -199,3 +199,54 @@ def test_batch_with_fp64_outer_operator(ctx):
     b.close()
     for m in models:
         m.free()
+
+
+@pytest.mark.parametrize("guess_order", [0, 3])
+def test_fp64_batch_matches_oracle_and_host_driven_steps(ctx, guess_order):
+    """Plain FP64 members (block-Jacobi PCG with every iteration in the step graph's
+    device-side loop) batched with uneven sizes, together with a mixed member: the
+    FP64 members agree with the oracle to 1e-9 at tolerance 1e-12 on both sides, with
+    the same PCG iteration count as host-driven steps (+-1 per step)."""
+    cfgs = _cfgs(n_steps=20)
+    alone = []
+    for cfg in cfgs:
+        m = _upload(ctx, cfg, 0, guess_order=guess_order)
+        m.set_solver(tol=1e-12, precision=0, guess_order=guess_order)
+        m.step(cfg["n_steps"])
+        alone.append((m.waveforms(), m.stats()["cg_iters_total"]))
+        m.free()
+    models = []
+    for cfg in cfgs:
+        m = _upload(ctx, cfg, 0)
+        m.set_solver(tol=1e-12, precision=0, guess_order=guess_order)
+        models.append(m)
+    mixed = _upload(ctx, cfgs[0], 2, guess_order=guess_order)
+    b = ctx.batch(models + [mixed])
+    b.step(7)
+    b.step(20)
+    for cfg, m, (w_alone, it_alone) in zip(cfgs, models, alone):
+        st = m.stats()
+        assert st["steps_done"] == cfg["n_steps"] and st["relres_last"] <= 1e-12
+        assert abs(st["cg_iters_total"] - it_alone) <= cfg["n_steps"]
+        w = m.waveforms()
+        assert _relerr(w, w_alone) <= 1e-10
+        assert _relerr(w, newmark.analysis(cfg, tol=1e-12)["wave"]) <= 1e-9
+    assert mixed.stats()["steps_done"] == cfgs[0]["n_steps"]
+    assert _relerr(mixed.waveforms(), newmark.analysis(cfgs[0], tol=1e-8)["wave"]) <= 1e-6
+    b.close()
+    for m in models + [mixed]:
+        m.free()
+
+
+def test_fp64_batch_budget_overflow_finishes_on_the_host(ctx):
+    """A device-side loop budget smaller than the PCG needs: every step is handed to the
+    host-driven solver and the result is unchanged."""
+    cfg = _cfgs(n_steps=8)[1]
+    m = _upload(ctx, cfg, 0)
+    m.set_solver(tol=1e-12, precision=0, batch_outer=3)
+    b = ctx.batch([m])
+    b.step(cfg["n_steps"])
+    assert m.stats()["steps_done"] == cfg["n_steps"]
+    assert _relerr(m.waveforms(), newmark.analysis(cfg, tol=1e-12)["wave"]) <= 1e-9
+    b.close()
+    m.free()

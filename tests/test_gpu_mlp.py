@@ -110,3 +110,60 @@ def test_learned_guess_run_converges_and_matches_plain(ctx):
         assert st["learned_steps"] < 60
     # and the run as a whole is not made much worse than the plain one
     assert runs[1]["iters"] <= 1.2 * runs[0]["iters"]
+
+
+@pytest.mark.parametrize("order", [0, 2])
+def test_learned_guess_data_path_matches_oracle(ctx, order):
+    """Features, layer features, sampled training nodes, targets, base guess and output
+    scale of the GPU's learned guess against the oracle's data path, both sides solving
+    the same small box to relative residual 1e-11.  order 0: the network corrects the
+    Newmark predictor (output scale sigma); order 2: it corrects the quadratic
+    extrapolation of the last three increments (output scale: RMS of the previous
+    step's correction)."""
+    from oracle import fem
+    from paper_2404_17754_gb300 import gsw
+
+    cfg = configs.small_box(nx=4, ny=3, n_steps=12)
+    n_run, B, seed, ips = 9, 256, 5, 2
+    m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
+    m.set_time(cfg["dt"], cfg["n_steps"], cfg["band"])
+    m.set_input(cfg["dir"], cfg["p"])
+    m.set_solver(tol=1e-11, precision=1, inner_iters=15, outer_op=gsw.OUTER_FP64, guess_order=order)
+    m.set_learning(True, train_steps=100, batch=B, iters_per_step=ips, lr=1e-3, seed=seed)
+    m.step(n_run)
+    N = m.n_nodes
+    nodes = np.arange(0, N, 7)
+    got = m.mlp_inputs(nodes, B)
+    m.free()
+
+    ops = fem.assemble(cfg["mesh"], cfg["mat"], cfg["band"])
+    C = (ops["CR"] + ops["Cabs"]).tocsr()
+    w, dt = ops["w"][cfg["dir"]], cfg["dt"]
+    z = np.zeros(3 * N)
+    states = [(z, z, z)]
+    newmark.newmark_run(ops["K"], ops["M"], C, lambda n: 2.0 * cfg["p"][n] * w, dt, n_run, tol=1e-11,
+                        observe=lambda n, u, v, a: states.append((u.copy(), v.copy(), a.copy())))
+    du = [states[k + 1][0] - states[k][0] for k in range(n_run)]
+    nodef = mlp.layer_features(cfg["mesh"], cfg["mat"])
+
+    def base_of(step):
+        incs = [du[step - 1 - j] for j in range(step)]
+        return mlp.base_guess(states[step][1], states[step][2], dt, incs, order).reshape(-1, 3)
+
+    s = n_run - 1  # the last training step
+    X_tr, sig = mlp.features([du[s - 1 - j] for j in range(4)], nodef)
+    b_s = base_of(s)
+    scale_s = mlp.correction_scale(du[s], b_s, sig) if order > 0 else sig
+    Y_tr = mlp.targets(du[s], b_s, scale_s)
+    idx = mlp.sample_nodes(N, B, seed, s, ips - 1)
+    assert np.abs(got["x_train"] - X_tr[idx]).max() <= 2e-5 * max(1.0, np.abs(X_tr[idx]).max())
+    yr = np.sqrt(np.mean(Y_tr[idx] ** 2))
+    assert np.abs(got["y_train"] - Y_tr[idx]).max() <= 1e-3 * yr
+    # inputs of the next step's inference
+    X_n, sig_n = mlp.features([du[s - j] for j in range(4)], nodef)
+    b_n = base_of(s + 1)
+    scale_n = mlp.correction_scale(du[s], b_s, sig_n) if order > 0 else sig_n
+    assert np.abs(got["x"] - X_n[nodes]).max() <= 2e-5 * max(1.0, np.abs(X_n[nodes]).max())
+    assert np.abs(got["base"] - b_n[nodes]).max() <= 1e-8 * np.abs(b_n).max()
+    assert abs(got["sigma"] - sig_n) <= 1e-6 * sig_n
+    assert abs(got["scale"] - scale_n) <= 1e-4 * scale_n

@@ -207,3 +207,28 @@ def test_mass_total_and_receiver_interpolation():
     fq = lambda X, Y: 1.0 + 0.3 * X - 0.2 * Y + 0.01 * X * X - 0.02 * X * Y + 0.03 * Y * Y
     vals = (w * fq(x[nodes, 0], x[nodes, 1])).sum(axis=1)
     np.testing.assert_allclose(vals, fq(pts[:, 0], pts[:, 1]), rtol=1e-12)
+
+
+def test_assemble_without_absorbing_faces():
+    """A mesh whose only boundary faces are free surface (tag 0): no dashpots, no
+    base load, and K, M, C_R identical to those of the same mesh with its
+    absorbing faces."""
+    cfg = configs.small_box(nx=3, ny=2, distort=True)
+    mesh = dict(cfg["mesh"])
+    full = fem.assemble(mesh, cfg["mat"], cfg["band"])
+    keep = mesh["face_tag"] == 0
+    for key in ("faces", "face_elem", "face_tag"):
+        mesh[key] = mesh[key][keep]
+    assert mesh["faces"].shape[0] > 0 and (mesh["face_tag"] == 0).all()
+    ops = fem.assemble(mesh, cfg["mat"], cfg["band"])
+    n = 3 * mesh["xyz"].shape[0]
+    for key in ("Cabs", "Cbase"):
+        assert ops[key].shape == (n, n) and ops[key].nnz == 0
+    assert np.abs(ops["w"]).max() == 0.0
+    for key in ("K", "M", "CR"):
+        assert abs(ops[key] - full[key]).max() == 0.0
+    # and with no boundary faces at all
+    for key in ("faces", "face_elem", "face_tag"):
+        mesh[key] = mesh[key][:0]
+    ops0 = fem.assemble(mesh, cfg["mat"], cfg["band"])
+    assert ops0["Cabs"].nnz == 0 and abs(ops0["K"] - full["K"]).max() == 0.0

@@ -59,5 +59,20 @@ def test_noalloc_misfit_matches_allocating_entry_point():
         with pytest.raises(gsw.GswError) as ei:
             ctx.misfit_noalloc(G_dev, obs_dev, 1, 65, err_dev)
         assert ei.value.status == gsw.E_INVALID
+        G, obs, s, L = _problem(24, n_rec=1025, n_t=16, L=2)
+        with pytest.raises(gsw.GswError) as ei:
+            ctx.misfit_noalloc(torch.tensor(G, device="cuda"), torch.tensor(obs, device="cuda"), s, L, err_dev)
+        assert ei.value.status == gsw.E_INVALID
+        # the input-wave coefficients are optional
+        G, obs, s, L = _problem(25)
+        e_ref, _ = ctx.misfit(G, obs, s, L, tau=1e-10)
+        err_dev = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+        ctx.misfit_noalloc(torch.tensor(G, device="cuda"), torch.tensor(obs, device="cuda"), s, L, err_dev, None)
+        torch.cuda.synchronize()
+        assert abs(float(err_dev.cpu()[0]) - e_ref) <= 1e-9 * e_ref
+        # outputs smaller than the result are refused before any launch
+        with pytest.raises(ValueError):
+            ctx.misfit_noalloc(torch.tensor(G, device="cuda"), torch.tensor(obs, device="cuda"), s, L, err_dev,
+                               torch.zeros(3 * L - 1, dtype=torch.float64, device="cuda"))
     finally:
         ctx.close()
