@@ -177,7 +177,10 @@ gsw_status gsw_set_time(gsw_ctx *ctx, int32_t model_id, double dt, int32_t n_ste
 
 /* Input velocity (Section 2: force at the base): p[n] is the incident
  * velocity at t_{n+1} = (n+1) dt in direction dir (0 = x1, 1 = x2, 2 = x3);
- * the base load is 2 C_base (p e_dir).  n must equal the model's n_steps. */
+ * the base load is 2 C_base (p e_dir).  n must equal the model's n_steps.
+ * The model keeps the input of each direction (for gsw_run's direction mask);
+ * its own analysis, advanced by gsw_step, follows the direction of the last
+ * call. */
 gsw_status gsw_set_input(gsw_ctx *ctx, int32_t model_id, int32_t dir, const double *p, int32_t n);
 
 gsw_status gsw_set_solver(gsw_ctx *ctx, int32_t model_id, const gsw_solver_opts *opts);
@@ -189,11 +192,21 @@ gsw_status gsw_reset(gsw_ctx *ctx, int32_t model_id);
  * last completed step and further steps return GSW_E_STATE until reset. */
 gsw_status gsw_step(gsw_ctx *ctx, int32_t model_id, int32_t n);
 
-/* Run every listed model from rest through all its steps (one directional
- * analysis each).  The models run together as one batch (see
- * gsw_batch_create), except those with the learned guess enabled, which run
- * one after the other with host-driven steps. */
-gsw_status gsw_run(gsw_ctx *ctx, const int32_t *model_ids, int32_t n_models);
+/* Run analyses from rest through all their steps (Section 2: the Green's
+ * functions of a candidate are three analyses, one per input direction; one
+ * candidate analysis in the sense of Section 3's cost paragraph is all three).
+ *  dirs_mask = 0: each listed model's own analysis (its last gsw_set_input
+ *    direction);
+ *  dirs_mask bits 0..2 (x1, x2, x3): for every listed model, the analysis of
+ *    each direction whose bit is set, from the input last set for that
+ *    direction (GSW_E_STATE if none).  These analyses share the model's mesh,
+ *    element, preconditioner and inner-operator data and hold their own state
+ *    and receiver history (read with gsw_read_waveforms(..., dir, ...)); they
+ *    are re-made after gsw_set_time or gsw_set_solver.
+ * All analyses run together as one batch (see gsw_batch_create), except a
+ * model's own analysis with the learned guess enabled, which runs first with
+ * host-driven steps. */
+gsw_status gsw_run(gsw_ctx *ctx, const int32_t *model_ids, int32_t n_models, int32_t dirs_mask);
 
 /* ---- batched stepping ------------------------------------------------------
  * A batch advances several models (uneven sizes and any mix of precision
@@ -224,13 +237,17 @@ gsw_status gsw_batch_destroy(gsw_ctx *ctx, int32_t batch_id);
 gsw_status gsw_batch_launches(gsw_ctx *ctx, int32_t batch_id, int64_t *per_step);
 
 /* Receiver velocity history: out [n_rec][3][n_steps] (entries of steps not
- * yet run are zero). */
-gsw_status gsw_read_waveforms(gsw_ctx *ctx, int32_t model_id, double *out);
+ * yet run are zero) of the model's own analysis (dir = -1) or of the
+ * analysis of input direction dir = 0..2 run by gsw_run (GSW_E_STATE if it
+ * has not been run). */
+gsw_status gsw_read_waveforms(gsw_ctx *ctx, int32_t model_id, int32_t dir, double *out);
 /* Receiver velocities of steps step0 .. step0+count-1 only:
  * out [n_rec][3][count] (host; pinned memory gives an asynchronous copy). */
 gsw_status gsw_read_waveform_steps(gsw_ctx *ctx, int32_t model_id, int32_t step0, int32_t count,
                                    double *out);
-gsw_status gsw_stats_get(gsw_ctx *ctx, int32_t model_id, gsw_stats *out);
+/* Statistics of the model's own analysis (dir = -1) or of the analysis of
+ * input direction dir = 0..2 run by gsw_run. */
+gsw_status gsw_stats_get(gsw_ctx *ctx, int32_t model_id, int32_t dir, gsw_stats *out);
 
 /* Checkpoint / restore of the time-stepping state: u, v, a [n_nodes][3] and
  * the step counter (receiver history up to that step is kept by the caller
@@ -239,6 +256,19 @@ gsw_status gsw_get_state(gsw_ctx *ctx, int32_t model_id, double *u, double *v, d
                          int64_t *step);
 gsw_status gsw_set_state(gsw_ctx *ctx, int32_t model_id, const double *u, const double *v,
                          const double *a, int64_t step);
+
+/* Full checkpoint of the model's own analysis, for resuming a run exactly:
+ * u, v, a, the step counter and statistics, the receiver history, the
+ * increment history of the extrapolated initial guess (guess_order > 0) and,
+ * with the learned guess enabled, the network's parameters, its Adam moments
+ * and step count, its increment history, its training schedule and the
+ * judge's state.  buf is a
+ * host buffer of *bytes bytes; buf = NULL returns the size needed in *bytes.
+ * gsw_restore needs the same model sizes, n_steps, input direction and
+ * guess_order (and learning enabled when the checkpoint holds a network);
+ * otherwise GSW_E_INVALID / GSW_E_STATE and the model is unchanged. */
+gsw_status gsw_checkpoint(gsw_ctx *ctx, int32_t model_id, void *buf, size_t *bytes);
+gsw_status gsw_restore(gsw_ctx *ctx, int32_t model_id, const void *buf, size_t bytes);
 
 /* Kernel timing: enable = 1 clears the counters and brackets every operator
  * launch of subsequent steps with CUDA events on the context's stream;
@@ -272,17 +302,21 @@ gsw_status gsw_read_preconditioner(gsw_ctx *ctx, int32_t model_id, double *out);
 gsw_status gsw_read_receivers(gsw_ctx *ctx, int32_t model_id, int32_t *nodes, double *weights);
 
 /* ---- learned initial guess ------------------------------------------------
- * A per-node MLP (16 -> 64 -> 64 -> 3, ReLU) corrects the Newmark predictor:
- * features = the last four displacement increments scaled by the RMS of the
- * latest one (12 values) and the node's layer properties (Vs/1000, Vp/3000,
- * rho/2000, h/0.05); du0 = dt v + dt^2/2 a + sigma * MLP(features).  During the
- * first train_steps steps the CG starts from the plain predictor and, after
- * each converged step, the network takes iters_per_step Adam steps on a batch
- * of random nodes (target: the converged increment); afterwards inference
- * (BF16 tensor cores, FP32 accumulation) supplies the initial guess.  The CG
- * always iterates to the same relative-residual tolerance; a non-finite guess
- * falls back to the predictor, and the plain predictor stays the judge (see
- * gsw_mlp_state).  Host-driven stepping (gsw_step) only. */
+ * A per-node MLP (16 -> 64 -> 64 -> 3, ReLU) corrects the step's base guess
+ * (the Newmark predictor dt v + dt^2/2 a, or the guess_order extrapolation):
+ * features = the backward differences D_0..D_3 of the last four displacement
+ * increments (D_k = sum_j (-1)^j C(k, j) du_{s-1-j}), each divided by its RMS
+ * over all DOF (12 values), and the node's layer properties (Vs/1000, Vp/3000,
+ * rho/2000, h/0.05); du0 = base + sigma_e * MLP(features), sigma_e the RMS of
+ * the previous step's correction du - base.  During the first train_steps
+ * steps the CG starts from the base guess and, after each converged step, the
+ * network takes iters_per_step Adam steps on a batch of random nodes (target:
+ * (du - base) / RMS(du - base)); the training's products run on the tensor
+ * cores (BF16 operands, FP32 accumulation), as does the inference that
+ * supplies the initial guess afterwards.  The CG always iterates to the same
+ * relative-residual tolerance; a non-finite guess falls back to the
+ * predictor, and the plain base guess stays the judge (see gsw_mlp_state).
+ * Host-driven stepping (gsw_step) only. */
 typedef struct {
   int32_t enable;          /* 0: plain predictor; 1: learned guess */
   int32_t train_steps;     /* steps used for training (the guess is applied after them) */
@@ -292,6 +326,14 @@ typedef struct {
   uint32_t seed;           /* weight initialisation and node sampling */
 } gsw_learn_opts;
 gsw_status gsw_set_learning(gsw_ctx *ctx, int32_t model_id, const gsw_learn_opts *opts);
+/* Train the learned guess on the model's next n_train_steps steps and advance
+ * them (host-driven): each converged step's solution trains the network
+ * (opts->iters_per_step Adam steps on opts->batch random nodes); afterwards
+ * gsw_step applies the learned guess.  opts->train_steps is ignored (training
+ * ends n_train_steps from the current step).  A network already enabled on
+ * the model keeps training; otherwise it is initialised from opts->seed.
+ * GSW_E_STATE in GSW_PREC_FP64 or for a batch member. */
+gsw_status gsw_mlp_train(gsw_ctx *ctx, int32_t model_id, int32_t n_train_steps, const gsw_learn_opts *opts);
 /* MLP parameters (5443 doubles: W1[16][64], b1[64], W2[64][64], b2[64],
  * W3[64][3], b3[3], row-major): read into get (if not NULL), then replace
  * from set (if not NULL). */
@@ -321,30 +363,41 @@ gsw_status gsw_mlp_state(gsw_ctx *ctx, int32_t model_id, double *out);
  *  nodes [n]: for these nodes, x [n][16] receives the features and base [n][3]
  *    the base guess (predictor, or the guess_order extrapolation) that the
  *    next step's inference would use.
- *  scale [2] (may be NULL): sigma (RMS of the latest increment) and the output
- *    scale of the next step's correction.
+ *  scale [2] (may be NULL): the RMS of the latest increment and the output
+ *    scale of the next step's correction (the RMS of the last correction).
  * Host arrays.  GSW_E_STATE before the first converged step or without learning. */
 gsw_status gsw_mlp_inputs(gsw_ctx *ctx, int32_t model_id, float *x_train, float *y_train, int32_t n,
                           const int32_t *nodes, float *x, double *base, double *scale);
 
 /* ---- misfit (Section 2, Eq. (2)) ----------------------------------------- */
 
-/* Input-wave estimate and ERR for one candidate and one event.
- *  G    [n_rec][3 (i)][3 (j)][n_t] Green's functions: velocity in direction i
- *       at receiver k for the unit pulse input in direction j.
- *  obs  [n_rec][3][n_t] observed surface velocity.
- *  stride, n_shifts: pulse shifts l * stride samples, l = 0..n_shifts-1.
+/* Input-wave estimate and ERR for one candidate model and one event, from
+ * the model's device-resident Green's functions: the receiver histories of
+ * its three input-direction analyses (gsw_run with dirs_mask 7, run to the
+ * end since the last set-up; GSW_E_STATE otherwise), each driven by the unit
+ * pulse p(t) of the basis.
+ *  obs  [n_rec][3][n_steps] observed surface velocity (host).
+ *  stride, n_shifts: pulse shifts l * stride steps, l = 0..n_shifts-1
+ *       (3 * n_shifts <= 384).
  *  tau  relative eigenvalue cut of the truncated pseudo-inverse.
- * Outputs: *err (Eq. (2)) and c_out [3][n_shifts] (may be NULL).
+ * Outputs: *err (Eq. (2)) and c_out [3][n_shifts] (may be NULL), host.
  * Pairs (k, i) whose observed energy is below 1e-12 of the largest are
- * dropped from the weights and from n_obs. Host arrays; computed on the GPU. */
-gsw_status gsw_misfit(gsw_ctx *ctx, int32_t n_rec, int32_t n_t, const double *G,
-                      const double *obs, int32_t stride, int32_t n_shifts, double tau,
-                      double *err, double *c_out);
+ * dropped from the weights and from n_obs.  Model selection is the caller's
+ * argmin over the candidates' err (ties: lowest index). */
+gsw_status gsw_misfit(gsw_ctx *ctx, int32_t model_id, const double *obs, int32_t stride, int32_t n_shifts,
+                      double tau, double *err, double *c_out);
+
+/* The same for Green's functions given by the caller (host arrays):
+ *  G    [n_rec][3 (i)][3 (j)][n_t]: velocity in direction i at receiver k for
+ *       the unit pulse input in direction j;
+ *  obs  [n_rec][3][n_t]. */
+gsw_status gsw_misfit_green(gsw_ctx *ctx, int32_t n_rec, int32_t n_t, const double *G,
+                            const double *obs, int32_t stride, int32_t n_shifts, double tau,
+                            double *err, double *c_out);
 
 /* ---- misfit without device allocation ------------------------------------ */
 
-/* Same computation as gsw_misfit, for callers that cannot allocate device
+/* Same computation as gsw_misfit_green, for callers that cannot allocate device
  * memory: for example code whose GPU memory is wholly owned by another
  * allocator (a framework's caching pool or a fixed arena reserved at start-up),
  * or a latency-critical loop where cudaMalloc / cudaFree would synchronise the

@@ -6,20 +6,26 @@ The network maps 16 per-node features to a 3-component correction of a base
 initial guess for step s (the method's spec form (4): the network
 predicts each step's CG initial guess from the previous steps' increments):
 
-    features  x = [du_{s-1}, du_{s-2}, du_{s-3}, du_{s-4}] / sigma  (12 values)
+    differences  D_k = k-th backward difference of the increments at s-1:
+                 D_k = sum_j (-1)^j C(k, j) du_{s-1-j},  k = 0..3
+    features  x = [D_0 / s_0, D_1 / s_1, D_2 / s_2, D_3 / s_3]  (12 values)
                   ++ [Vs / 1000, Vp / 3000, rho / 2000, h / 0.05] of the node's layer
                   (the lowest layer index among the elements touching the node)
-    sigma     = RMS over all DOF of du_{s-1} (1 if that is zero)
+    s_k       = RMS over all DOF of D_k (1 if that is zero)
     network   h1 = relu(x W1 + b1) (64), h2 = relu(h1 W2 + b2) (64), o = h2 W3 + b3 (3)
     base      the Newmark predictor dt v + dt^2/2 a (guess order 0), or the
               degree-k polynomial through the last k+1 increments evaluated one
               step ahead (guess order k, once k+1 increments exist)
-    scale     sigma for the predictor base; for a polynomial base, the RMS of
-              the previous step's correction du_{s-1} - base_{s-1}
+    scale     the RMS of the previous step's correction du_{s-1} - base_{s-1}
+              (s_0 if that is zero)
     guess     du0 = base + scale * o
-    target    of training step s: (du_s - base_s) / scale_s, where scale_s is
-              sigma for the predictor base and RMS(du_s - base_s) for a
-              polynomial base; loss = mean over the batch of |o - target|^2
+    target    of training step s: (du_s - base_s) / RMS(du_s - base_s);
+              loss = mean over the batch of |o - target|^2
+
+Differences rather than the increments themselves: the correction is a
+nearly cancelling combination of nearly equal increments, which features
+rounded to bfloat16 (8 significant bits) could not resolve; each difference
+normalised by its own RMS keeps its leading digits.
 
 Training samples of step s, Adam iteration i, batch slot j are nodes
 hash(seed, s, i, j) mod N, with the counter-based hash built from Wellons'
@@ -142,15 +148,24 @@ def rms(x):
     return float(np.sqrt(np.mean(x * x)))
 
 
+def backward_differences(history):
+    """D_k = sum_j (-1)^j C(k, j) history[j], k = 0..3 (history[0] the latest)."""
+    from math import comb
+
+    return [sum((-1) ** j * comb(k, j) * np.asarray(history[j], dtype=np.float64) for j in range(k + 1))
+            for k in range(4)]
+
+
 def features(history, nodef):
-    """Features [N, 16] and sigma from ``history`` = [du_{s-1}, du_{s-2},
-    du_{s-3}, du_{s-4}] (each [N, 3], latest first) and layer features [N, 4]."""
-    sigma = rms(history[0])
-    if sigma == 0.0:
-        sigma = 1.0
-    X = np.concatenate([np.asarray(h, dtype=np.float64).reshape(-1, 3) / sigma for h in history[:4]]
+    """Features [N, 16] and the scales s_k [4] from ``history`` = [du_{s-1},
+    du_{s-2}, du_{s-3}, du_{s-4}] (each [N, 3], latest first) and layer
+    features [N, 4]."""
+    D = backward_differences(history)
+    sig = np.array([rms(d) for d in D])
+    sig[sig == 0.0] = 1.0
+    X = np.concatenate([d.reshape(-1, 3) / sg for d, sg in zip(D, sig)]
                        + [np.asarray(nodef, dtype=np.float64)], axis=1)
-    return X, sigma
+    return X, sig
 
 
 def extrapolate(increments, k):
@@ -178,15 +193,16 @@ def base_guess(v, a, dt, increments, k):
     return dt * np.asarray(v, dtype=np.float64) + 0.5 * dt * dt * np.asarray(a, dtype=np.float64)
 
 
-def correction_scale(du, base, sigma):
-    """RMS of the correction du - base, or sigma when the correction is zero."""
-    r = rms(np.asarray(du) - np.asarray(base))
-    return r if r > 0.0 else sigma
+def correction_scale(du, base, fallback):
+    """RMS of the correction du - base, or ``fallback`` when it is zero."""
+    r = rms(np.asarray(du, dtype=np.float64).ravel() - np.asarray(base, dtype=np.float64).ravel())
+    return r if r > 0.0 else fallback
 
 
 def targets(du, base, scale):
     """Training targets (du - base) / scale, [N, 3]."""
-    return ((np.asarray(du, dtype=np.float64) - np.asarray(base, dtype=np.float64)) / scale).reshape(-1, 3)
+    return ((np.asarray(du, dtype=np.float64).ravel() - np.asarray(base, dtype=np.float64).ravel())
+            / scale).reshape(-1, 3)
 
 
 def learned_guess(theta, X, base, scale):
@@ -218,3 +234,40 @@ def sample_nodes(n_nodes, batch, seed, step, it):
     mid = lowbias32(((np.uint64(step) * np.uint64(0x9E3779B9)) & _M32) ^ inner)
     h = lowbias32(np.uint64(seed) ^ mid)
     return (h % np.uint64(n_nodes)).astype(np.int64)
+
+
+def loss_grad_bf16(theta, X, Y, rnd=None):
+    """Loss and gradient as the tensor-core training kernel computes them.
+
+    Every matrix product takes its operands rounded by ``rnd`` (bfloat16,
+    :func:`bf16`, by default) and sums exactly (the kernel accumulates in
+    FP32): features, weights and the stored activations h1, h2 of the
+    forward pass; the output error 2 (o - y) / B; the back-propagated
+    dz2 = (d3 W3^T) * [z2 > 0] and dz1 = (dz2 W2^T) * [z1 > 0].  Biases and
+    bias gradients are not rounded.  With ``rnd`` the identity this is
+    :func:`loss_grad`."""
+    r = bf16 if rnd is None else rnd
+    p = unpack(theta)
+    W1, W2, W3 = r(p["W1"]), r(p["W2"]), r(p["W3"])
+    x = r(X)
+    z1 = x @ W1 + p["b1"]
+    h1 = r(np.maximum(z1, 0.0))
+    z2 = h1 @ W2 + p["b2"]
+    h2 = r(np.maximum(z2, 0.0))
+    o = h2 @ W3 + p["b3"]
+    B = X.shape[0]
+    diff = o - Y
+    loss = float((diff ** 2).sum() / B)
+    d3 = 2.0 * diff / B
+    g = {"b3": d3.sum(axis=0)}
+    d3r = r(d3)
+    g["W3"] = h2.T @ d3r
+    dz2 = (d3r @ W3.T) * (z2 > 0)
+    g["b2"] = dz2.sum(axis=0)
+    dz2r = r(dz2)
+    g["W2"] = h1.T @ dz2r
+    dz1 = (dz2r @ W2.T) * (z1 > 0)
+    g["b1"] = dz1.sum(axis=0)
+    g["W1"] = x.T @ r(dz1)
+    grad = np.concatenate([g[name].ravel() for name, _ in SHAPES])
+    return loss, grad

@@ -92,7 +92,8 @@ struct Model {
   bool mlp_ready = false;
   float *theta = nullptr, *adam_m = nullptr, *adam_v = nullptr, *grad = nullptr;
   uint32_t* packed = nullptr;
-  float *hist = nullptr, *nodef = nullptr, *trainX = nullptr, *trainY = nullptr;
+  double* hist = nullptr;  // [4][3N] backward differences of the last four increments
+  float *nodef = nullptr, *trainX = nullptr, *trainY = nullptr;
   int32_t* node_mat = nullptr;
   MlpScalars* ms = nullptr;
   MlpScalars ms_host = {};
@@ -112,6 +113,14 @@ struct Model {
   float lo_variant_ms[kLoVariants] = {0.f, 0.f, 0.f};
   LoView<float> lo_f;
   LoView<__half> lo_h;
+  // directional analyses of gsw_run's direction mask: one instance per input
+  // direction, sharing this model's mesh, element, preconditioner and
+  // inner-operator data (read-only, owned here) and holding its own state,
+  // solver vectors and receiver history
+  Model* parent = nullptr;                      // set on an instance
+  Model* inst[3] = {nullptr, nullptr, nullptr};  // instances (parent only)
+  int inst_version[3] = {-1, -1, -1};           // parent version each was made for
+  std::vector<double> dir_input[3];             // input of each direction (parent only)
   // kernel timing
   bool timing = false;
   std::vector<cudaEvent_t> ev;
@@ -168,7 +177,9 @@ struct StepLaunches {
 };
 
 struct Batch {
-  std::vector<int> ids;
+  std::vector<Model*> members;  // models or direction instances
+  std::vector<int> ids;         // model id of each member (for messages)
+  std::vector<int> dirs;        // input direction of an instance member, -1 for a model
   std::vector<int> versions;
   cudaStream_t origin = nullptr;
   std::vector<cudaStream_t> streams;
@@ -261,6 +272,11 @@ gsw_status alloc_into(gsw_ctx* ctx, Model* m, T** out, size_t count) {
   } while (0)
 
 void free_model(gsw_ctx* ctx, Model* m) {
+  for (int d = 0; d < 3; ++d)
+    if (m->inst[d]) {
+      free_model(ctx, m->inst[d]);
+      m->inst[d] = nullptr;
+    }
   if (m->ig_exec) cudaGraphExecDestroy(m->ig_exec);
   for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
   for (cudaEvent_t e : m->ev_lo) cudaEventDestroy(e);
@@ -299,7 +315,9 @@ std::vector<int32_t> soa(const int32_t* src, int64_t n, int k) {
   return out;
 }
 
-gsw_status model_state_alloc(gsw_ctx* ctx, Model* m) {
+// Step-dependent state of an analysis; own_precond: also the block-Jacobi
+// blocks (an instance shares its parent's).
+gsw_status model_state_alloc(gsw_ctx* ctx, Model* m, bool own_precond = true) {
   const size_t n3 = 3 * (size_t)m->N;
   TRY(alloc_into(ctx, m, &m->u, n3));
   TRY(alloc_into(ctx, m, &m->v, n3));
@@ -310,8 +328,10 @@ gsw_status model_state_alloc(gsw_ctx* ctx, Model* m) {
   TRY(alloc_into(ctx, m, &m->z, n3));
   TRY(alloc_into(ctx, m, &m->p, n3));
   TRY(alloc_into(ctx, m, &m->q, n3));
-  TRY(alloc_into(ctx, m, &m->dblk, 6 * (size_t)m->N));
-  TRY(alloc_into(ctx, m, &m->dinv, 6 * (size_t)m->N));
+  if (own_precond) {
+    TRY(alloc_into(ctx, m, &m->dblk, 6 * (size_t)m->N));
+    TRY(alloc_into(ctx, m, &m->dinv, 6 * (size_t)m->N));
+  }
   ModelView mv = m->view();
   size_t np = (size_t)ebe_blocks(mv) + 2;
   if (np < 2 * (size_t)kMaxNodeBlocks) np = 2 * (size_t)kMaxNodeBlocks;
@@ -566,6 +586,127 @@ gsw_status build_lo(gsw_ctx* ctx, Model* m, int half) {
   return autotune_lo(ctx, m);
 }
 
+// The analysis of input direction d of model m, sharing m's mesh, element,
+// preconditioner and inner-operator data; its own state, CG and inner
+// vectors, increment history and receiver history; at rest.
+gsw_status make_instance(gsw_ctx* ctx, Model* m, int d, Model** out) {
+  Model* c = new Model();
+  c->parent = m;
+  c->N = m->N;
+  c->E = m->E;
+  c->F = m->F;
+  c->n_mat = m->n_mat;
+  c->n_rec = m->n_rec;
+  c->period[0] = m->period[0];
+  c->period[1] = m->period[1];
+  c->raw_mat = m->raw_mat;
+  c->xyz = m->xyz;
+  c->conn = m->conn;
+  c->geo = m->geo;
+  c->emat = m->emat;
+  c->raw_mat_dev = m->raw_mat_dev;
+  c->mat = m->mat;
+  c->fnode = m->fnode;
+  c->face_elem = m->face_elem;
+  c->face_tag = m->face_tag;
+  c->fgeo = m->fgeo;
+  c->rec_xy = m->rec_xy;
+  c->rec_face = m->rec_face;
+  c->rec_node = m->rec_node;
+  c->rec_w = m->rec_w;
+  c->err = m->err;
+  c->time_set = true;
+  c->dt = m->dt;
+  c->f1 = m->f1;
+  c->f2 = m->f2;
+  c->n_steps = m->n_steps;
+  c->dblk = m->dblk;
+  c->dinv = m->dinv;
+  c->opts = m->opts;
+  c->dir = d;
+  c->input = m->dir_input[d];
+  c->input_set = true;
+  cudaStream_t s = ctx->stream;
+  auto bail = [&](gsw_status st) {
+    cudaStreamSynchronize(s);
+    free_model(ctx, c);
+    return st;
+  };
+#define TRYI(expr)                   \
+  do {                               \
+    gsw_status s_ = (expr);          \
+    if (s_ != GSW_OK) return bail(s_); \
+  } while (0)
+  TRYI(model_state_alloc(ctx, c, false));
+  if (c->opts.guess_order > 0) {
+    TRYI(alloc_into(ctx, c, &c->guess_ext, 2));
+    TRYI(alloc_into(ctx, c, &c->guess_ring, (size_t)(c->opts.guess_order + 1) * 3 * (size_t)c->N));
+    c->guess_ring_k = c->opts.guess_order;
+  }
+  if (m->lo_ready && m->opts.precision != GSW_PREC_FP64) {
+    c->lo_half = m->lo_half;
+    c->n_blk = m->n_blk;
+    c->max_local = m->max_local;
+    c->blk_ptr = m->blk_ptr;
+    c->blk_nodes = m->blk_nodes;
+    c->lconn = m->lconn;
+    c->geo_lo = m->geo_lo;
+    c->fgeo32 = m->fgeo32;
+    c->dinv32 = m->dinv32;
+    c->matf = m->matf;
+    c->lo_variant = m->lo_variant;
+    for (int v = 0; v < kLoVariants; ++v) c->lo_variant_ms[v] = m->lo_variant_ms[v];
+    const size_t n3 = 3 * (size_t)c->N;
+    TRYI(alloc_into(ctx, c, &c->y32, n3));
+    TRYI(alloc_into(ctx, c, &c->s32, n3));
+    TRYI(alloc_into(ctx, c, &c->t32, 4 * ((size_t)c->N + 1)));
+    TRYI(alloc_into(ctx, c, &c->w32, n3 + 4));
+    TRYI(alloc_into(ctx, c, &c->isc, 1));
+    TRYI(alloc_into(ctx, c, &c->dw_part, (size_t)c->n_blk + (size_t)((c->F + kLoBlock - 1) / kLoBlock) + 1));
+    TRYI(alloc_into(ctx, c, &c->uva, 3 * ((size_t)c->N + 1)));
+    const size_t dbytes = (c->lo_half ? sizeof(__half) : sizeof(float)) * 4 * ((size_t)c->N + 1);
+    c->d_lo = dev_alloc(ctx, c, dbytes);
+    c->d_lo2 = dev_alloc(ctx, c, dbytes);
+    if (!c->d_lo || !c->d_lo2) return bail(fail(ctx, GSW_E_NOMEM, "device allocation failed (inner solve)"));
+    if (cudaMemsetAsync(c->t32, 0, sizeof(float) * 4 * ((size_t)c->N + 1), s) != cudaSuccess ||
+        cudaMemsetAsync(c->uva, 0, sizeof(float4) * 3 * ((size_t)c->N + 1), s) != cudaSuccess ||
+        cudaMemsetAsync(c->d_lo, 0, dbytes, s) != cudaSuccess || cudaMemsetAsync(c->d_lo2, 0, dbytes, s) != cudaSuccess ||
+        cudaMemcpyAsync(c->isc, m->isc, sizeof(InnerScalars), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return bail(fail(ctx, GSW_E_CUDA, "instance set-up copies failed"));
+    BlockView bv = {c->n_blk, c->max_local, c->blk_ptr, c->blk_nodes};
+    const float face_c = (float)(2.0 / c->dt / 180.0);
+    c->lo_f = LoView<float>{c->N, c->E, c->F, c->n_mat, bv, c->geo_lo, c->matf, c->fnode, c->fgeo32, c->dt,
+                            c->dw_part, face_c};
+    c->lo_h = LoView<__half>{c->N, c->E, c->F, c->n_mat, bv, c->geo_lo, c->matf, c->fnode, c->fgeo32, c->dt,
+                             c->dw_part, face_c};
+    c->lo_ready = true;
+    c->live_tune = false;
+  }
+  TRYI(model_reset(ctx, c));
+#undef TRYI
+  *out = c;
+  return GSW_OK;
+}
+
+// The up-to-date instance of direction d (made, or re-made after the parent's
+// time, input or solver set-up changed).
+gsw_status get_instance(gsw_ctx* ctx, Model* m, int d, Model** out) {
+  if (m->dir_input[d].empty()) return fail(ctx, GSW_E_STATE, "no input set for direction %d", d);
+  if (m->inst[d] && m->inst_version[d] == m->version && m->inst[d]->input == m->dir_input[d]) {
+    *out = m->inst[d];
+    return GSW_OK;
+  }
+  if (m->inst[d]) {
+    cudaStreamSynchronize(ctx->stream);
+    free_model(ctx, m->inst[d]);
+    m->inst[d] = nullptr;
+  }
+  TRY(make_instance(ctx, m, d, &m->inst[d]));
+  m->inst_version[d] = m->version;
+  *out = m->inst[d];
+  return GSW_OK;
+}
+
 // ---- learned initial guess ----------------------------------------------------
 
 // Reproducible uniform(-1, 1) from a counter (same on every host).
@@ -611,7 +752,7 @@ gsw_status mlp_init(gsw_ctx* ctx, Model* m, uint32_t seed) {
   CK(cudaMemsetAsync(m->adam_m, 0, sizeof(float) * kMlpParams, s));
   CK(cudaMemsetAsync(m->adam_v, 0, sizeof(float) * kMlpParams, s));
   CK(cudaMemsetAsync(m->grad, 0, sizeof(float) * kMlpParams, s));
-  CK(cudaMemsetAsync(m->hist, 0, sizeof(float) * 12 * (size_t)m->N, s));
+  CK(cudaMemsetAsync(m->hist, 0, sizeof(double) * 12 * (size_t)m->N, s));
   launch_mlp_pack(m->theta, m->packed, s);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
@@ -632,9 +773,8 @@ bool mlp_use_guess(gsw_ctx* ctx, Model* m, cudaStream_t s, const double* base) {
   // every 10th step of the application phase is a probe with the plain
   // predictor, keeping the judge's baseline current
   if ((m->applied++ % 10) == 9) return false;
-  launch_mlp_sigma(m->N, m->hist, m->hist_head, m->partials, m->ms, s);
-  launch_mlp_infer(m->N, m->hist, m->hist_head, m->nodef, m->v, m->a, m->dt, m->packed, m->ms, m->x, nullptr,
-                   nullptr, s, base);
+  launch_mlp_sigma(m->N, m->hist, m->partials, m->ms, s);
+  launch_mlp_infer(m->N, m->hist, m->nodef, m->packed, m->ms, m->x, nullptr, nullptr, s, base);
   m->stats.kernel_launches += 2;
   return true;
 }
@@ -643,16 +783,16 @@ bool mlp_use_guess(gsw_ctx* ctx, Model* m, cudaStream_t s, const double* base) {
 // the converged increment, then push it into the history.
 gsw_status mlp_after_step(gsw_ctx* ctx, Model* m, cudaStream_t s, const double* base) {
   if (!m->learn.enable || !m->mlp_ready) return GSW_OK;
-  // the scale of the correction to an extrapolated base: this step's targets
-  // and the next step's output use it
-  if (base) launch_mlp_sigma_e(m->N, m->x, base, m->partials, m->ms, s);
+  // the scale of the correction to the base guess: this step's targets and
+  // the next step's output use it
+  launch_mlp_sigma_e(m->N, m->x, base, m->partials, m->ms, s);
   if (m->step < m->learn.train_steps && m->hist_count >= 4 && !m->cg_host->zero_rhs) {
-    launch_mlp_sigma(m->N, m->hist, m->hist_head, m->partials, m->ms, s);
+    launch_mlp_sigma(m->N, m->hist, m->partials, m->ms, s);
     CK(cudaMemsetAsync(&m->ms->loss, 0, sizeof(double), s));
     const int B = m->learn.batch;
     for (int it = 0; it < m->learn.iters_per_step; ++it) {
-      launch_mlp_sample(m->N, B, m->learn.seed, (int)m->step, it, m->hist, m->hist_head, m->nodef, m->x, m->v, m->a,
-                        m->dt, m->ms, m->trainX, m->trainY, s, base);
+      launch_mlp_sample(m->N, B, m->learn.seed, (int)m->step, it, m->hist, m->nodef, m->x, base, m->ms, m->trainX,
+                        m->trainY, s);
       if (launch_mlp_fwdbwd(B, m->trainX, m->trainY, m->theta, m->grad, &m->ms->loss, s))
         return fail(ctx, GSW_E_CUDA, "training kernel configuration failed");
       m->adam_t += 1;
@@ -661,9 +801,7 @@ gsw_status mlp_after_step(gsw_ctx* ctx, Model* m, cudaStream_t s, const double* 
     launch_mlp_pack(m->theta, m->packed, s);
     m->stats.kernel_launches += 2 + 3 * m->learn.iters_per_step;
   }
-  const int slot = (m->hist_head + 1) & 3;
-  launch_hist_push(m->N, m->x, m->hist, slot, m->cg, s);
-  m->hist_head = slot;
+  launch_hist_push(m->N, m->x, m->hist, m->cg, s);
   if (m->hist_count < 4) m->hist_count += 1;
   m->stats.kernel_launches += 1;
   CK(cudaGetLastError());
@@ -806,14 +944,17 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
   init.tol = m->opts.tol;
   init.max_iter = m->opts.max_iter;
   CK(cudaMemcpyAsync(m->cg, &init, sizeof(CgScalars), cudaMemcpyHostToDevice, s));
-  // initial guess (predictor or learned) and the shifted state (u~ in p, v~ in z, a~ in b), r = q = 0
-  // with learning and an extrapolated guess, the network corrects the
-  // extrapolation: keep this step's extrapolated guess as its base
+  // initial guess (predictor, extrapolation or learned) and the shifted state (u~ in p, v~ in z, a~ in b),
+  // r = q = 0; with learning the network corrects the step's base guess (the
+  // extrapolation at guess order > 0, else the predictor), kept in guess_base
   double* base = nullptr;
-  if (m->learn.enable && m->opts.guess_order > 0) {
+  if (m->learn.enable) {
     if (!m->guess_base) TRY(alloc_into(ctx, m, &m->guess_base, 3 * (size_t)m->N));
     base = m->guess_base;
-    launch_guess_extrap(m->N, m->guess_ring, m->opts.guess_order, m->guess_ext, m->v, m->a, m->dt, base, s);
+    if (m->opts.guess_order > 0)
+      launch_guess_extrap(m->N, m->guess_ring, m->opts.guess_order, m->guess_ext, m->v, m->a, m->dt, base, s);
+    else
+      launch_predictor(m->N, m->v, m->a, m->dt, base, s);
   }
   const bool learned = mlp_use_guess(ctx, m, s, base);
   const bool extrap = !learned && m->opts.guess_order > 0;
@@ -1274,7 +1415,10 @@ gsw_status gsw_model_info(gsw_ctx* ctx, int32_t model_id, int64_t* out) {
   out[1] = m->E;
   out[2] = m->F;
   out[3] = m->n_rec;
-  out[4] = (int64_t)m->bytes;
+  size_t bytes = m->bytes;
+  for (int d = 0; d < 3; ++d)
+    if (m->inst[d]) bytes += m->inst[d]->bytes;
+  out[4] = (int64_t)bytes;
   out[5] = m->lo_ready ? m->lo_variant : -1;
   return GSW_OK;
 }
@@ -1326,6 +1470,7 @@ gsw_status gsw_set_input(gsw_ctx* ctx, int32_t model_id, int32_t dir, const doub
   if (!p || n != m->n_steps) return fail(ctx, GSW_E_INVALID, "input length %d != n_steps %d", n, m->n_steps);
   if (!finite_all(p, (size_t)n)) return fail(ctx, GSW_E_INVALID, "non-finite input sample");
   m->input.assign(p, p + n);
+  m->dir_input[dir].assign(p, p + n);
   if (m->dir != dir) m->version += 1;
   m->dir = dir;
   m->input_set = true;
@@ -1401,47 +1546,69 @@ gsw_status gsw_step(gsw_ctx* ctx, int32_t model_id, int32_t n) {
   return GSW_OK;
 }
 
-gsw_status gsw_run(gsw_ctx* ctx, const int32_t* model_ids, int32_t n_models) {
+static gsw_status batch_make(gsw_ctx* ctx, const std::vector<Model*>& ms, const std::vector<int>& model_ids,
+                             const std::vector<int>& dirs, int32_t* batch_id);
+
+gsw_status gsw_run(gsw_ctx* ctx, const int32_t* model_ids, int32_t n_models, int32_t dirs_mask) {
   if (!ctx || (!model_ids && n_models > 0)) return GSW_E_INVALID;
-  std::vector<int32_t> mixed;
+  if (dirs_mask < 0 || dirs_mask > 7) return fail(ctx, GSW_E_INVALID, "dirs_mask must be 0..7");
+  DeviceGuard g(ctx->device);
+  std::vector<Model*> members;
+  std::vector<int> ids, dirs;
   int max_steps = 0;
   for (int i = 0; i < n_models; ++i) {
     Model* m = find(ctx, model_ids[i]);
     if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_ids[i]);
-    TRY(gsw_reset(ctx, model_ids[i]));
-    if (m->batch || m->learn.enable) {
-      TRY(gsw_step(ctx, model_ids[i], m->n_steps));
+    for (int j = 0; j < i; ++j)
+      if (model_ids[j] == model_ids[i]) return fail(ctx, GSW_E_INVALID, "model %d listed twice", model_ids[i]);
+    if (!m->time_set) return fail(ctx, GSW_E_STATE, "model %d: call gsw_set_time first", model_ids[i]);
+    if (m->batch) return fail(ctx, GSW_E_STATE, "model %d belongs to batch %d", model_ids[i], m->batch);
+    if (dirs_mask == 0) {
+      TRY(gsw_reset(ctx, model_ids[i]));
+      if (m->learn.enable) {
+        TRY(gsw_step(ctx, model_ids[i], m->n_steps));
+        continue;
+      }
+      if (!m->input_set) return fail(ctx, GSW_E_STATE, "model %d: set the input first", model_ids[i]);
+      members.push_back(m);
+      ids.push_back(model_ids[i]);
+      dirs.push_back(-1);
     } else {
-      mixed.push_back(model_ids[i]);
-      if (m->n_steps > max_steps) max_steps = m->n_steps;
+      for (int d = 0; d < 3; ++d) {
+        if (!(dirs_mask & (1 << d))) continue;
+        Model* c = nullptr;
+        TRY(get_instance(ctx, m, d, &c));
+        TRY(model_reset(ctx, c));
+        members.push_back(c);
+        ids.push_back(model_ids[i]);
+        dirs.push_back(d);
+      }
     }
+    max_steps = std::max(max_steps, m->n_steps);
   }
-  if (!mixed.empty()) {
-    int32_t bid = 0;
-    TRY(gsw_batch_create(ctx, mixed.data(), (int32_t)mixed.size(), &bid));
-    gsw_status st = gsw_batch_step(ctx, bid, max_steps);
-    std::string msg = ctx->err;
-    gsw_batch_destroy(ctx, bid);
-    if (st != GSW_OK) ctx->err = msg;
-    return st;
-  }
-  return GSW_OK;
+  if (members.empty()) return GSW_OK;
+  int32_t bid = 0;
+  TRY(batch_make(ctx, members, ids, dirs, &bid));
+  gsw_status st = gsw_batch_step(ctx, bid, max_steps);
+  std::string msg = ctx->err;
+  gsw_batch_destroy(ctx, bid);
+  if (st != GSW_OK) ctx->err = msg;
+  return st;
 }
 
-gsw_status gsw_batch_create(gsw_ctx* ctx, const int32_t* model_ids, int32_t n_models, int32_t* batch_id) {
-  if (!ctx || !model_ids || n_models <= 0 || !batch_id) return GSW_E_INVALID;
+// A batch over models or direction instances (the members).
+static gsw_status batch_make(gsw_ctx* ctx, const std::vector<Model*>& ms, const std::vector<int>& model_ids,
+                      const std::vector<int>& dirs, int32_t* batch_id) {
   DeviceGuard g(ctx->device);
+  const int n_models = (int)ms.size();
   for (int i = 0; i < n_models; ++i) {
-    Model* m = find(ctx, model_ids[i]);
-    if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_ids[i]);
+    Model* m = ms[i];
     if (!m->time_set || !m->input_set) return fail(ctx, GSW_E_STATE, "model %d: set the time and the input first", model_ids[i]);
     if (m->opts.precision != GSW_PREC_FP64 && !m->lo_ready)
       return fail(ctx, GSW_E_STATE, "model %d: the inner solve of the mixed mode is not set up", model_ids[i]);
     if (m->batch) return fail(ctx, GSW_E_STATE, "model %d already belongs to batch %d", model_ids[i], m->batch);
     if (m->learn.enable)
       return fail(ctx, GSW_E_STATE, "model %d: the learned guess runs with host-driven stepping only", model_ids[i]);
-    for (int j = 0; j < i; ++j)
-      if (model_ids[j] == model_ids[i]) return fail(ctx, GSW_E_INVALID, "model %d listed twice", model_ids[i]);
   }
   Batch* b = new Batch();
   auto bail = [&](const char* what, cudaError_t e) {
@@ -1460,7 +1627,7 @@ gsw_status gsw_batch_create(gsw_ctx* ctx, const int32_t* model_ids, int32_t n_mo
   }
   if ((e = cudaMallocHost(&b->ss_host, sizeof(StepState) * n_models)) != cudaSuccess) return bail("state", e);
   for (int i = 0; i < n_models; ++i) {
-    Model* m = find(ctx, model_ids[i]);
+    Model* m = ms[i];
     cudaStream_t s;
     cudaEvent_t ev;
     if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return bail("stream", e);
@@ -1477,15 +1644,33 @@ gsw_status gsw_batch_create(gsw_ctx* ctx, const int32_t* model_ids, int32_t n_mo
     if ((e = cudaMemcpyAsync(m->p_dev, m->input.data(), sizeof(double) * m->n_steps, cudaMemcpyHostToDevice,
                              ctx->stream)) != cudaSuccess)
       return bail("input copy", e);
+    b->members.push_back(m);
     b->ids.push_back(model_ids[i]);
+    b->dirs.push_back(dirs[i]);
     b->versions.push_back(-1);
   }
   if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return bail("synchronise", e);
   const int id = ctx->next_batch++;
-  for (int i = 0; i < n_models; ++i) find(ctx, model_ids[i])->batch = id;
+  for (int i = 0; i < n_models; ++i) ms[i]->batch = id;
   ctx->batches[id] = b;
   *batch_id = id;
   return GSW_OK;
+}
+
+gsw_status gsw_batch_create(gsw_ctx* ctx, const int32_t* model_ids, int32_t n_models, int32_t* batch_id) {
+  if (!ctx || !model_ids || n_models <= 0 || !batch_id) return GSW_E_INVALID;
+  std::vector<Model*> ms;
+  std::vector<int> ids, dirs;
+  for (int i = 0; i < n_models; ++i) {
+    Model* m = find(ctx, model_ids[i]);
+    if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_ids[i]);
+    for (int j = 0; j < i; ++j)
+      if (model_ids[j] == model_ids[i]) return fail(ctx, GSW_E_INVALID, "model %d listed twice", model_ids[i]);
+    ms.push_back(m);
+    ids.push_back(model_ids[i]);
+    dirs.push_back(-1);
+  }
+  return batch_make(ctx, ms, ids, dirs, batch_id);
 }
 
 gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
@@ -1503,7 +1688,7 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
   int remaining = 0;
   int fp64_loop = 0;  // budget of the device-side loop of FP64 members (PCG iterations)
   for (int i = 0; i < nm; ++i) {
-    Model* m = find(ctx, b->ids[i]);
+    Model* m = b->members[i];
     if (m->opts.precision == GSW_PREC_FP64) {
       fp64_loop = std::max(fp64_loop, m->opts.batch_outer > 0 ? m->opts.batch_outer : kFp64LoopCap);
     } else {
@@ -1543,7 +1728,7 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
       bool ok = true;
       b->launches.assign(nm, StepLaunches());
       for (int i = 0; i < nm && ok; ++i) {
-        Model* m = find(ctx, b->ids[i]);
+        Model* m = b->members[i];
         const bool fp64 = m->opts.precision == GSW_PREC_FP64;
         ok = cudaStreamWaitEvent(b->streams[i], b->fork, 0) == cudaSuccess &&
              (fp64 ? issue_device_step_fp64(m, b->streams[i], b->ss_dev + i, wl ? fp64_loop : outer,
@@ -1568,7 +1753,7 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
     b->launches_per_step = launches;
     b->outer = b->use_while ? outer_loop : outer;
     b->fp64_loop = fp64_loop;
-    for (int i = 0; i < nm; ++i) b->versions[i] = find(ctx, b->ids[i])->version;
+    for (int i = 0; i < nm; ++i) b->versions[i] = b->members[i]->version;
     return GSW_OK;
   };
   if (stale && remaining > 0) TRY(capture());
@@ -1583,7 +1768,7 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
     bool rewrite = false;
     int need = 0;  // most outer iterations a step of this chunk needed
     for (int i = 0; i < nm; ++i) {
-      Model* m = find(ctx, b->ids[i]);
+      Model* m = b->members[i];
       StepState& h = b->ss_host[i];
       const int advanced = h.step - (int)m->step;
       m->step = h.step;
@@ -1611,8 +1796,10 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
         m->failed = true;
         if (st == GSW_OK) {
           st = h.failed == GSW_E_NOCONV ? GSW_E_NOCONV : (h.failed == GSW_E_NAN ? GSW_E_NAN : GSW_E_STATE);
-          fail(ctx, st, "model %d failed at step %d (%s)", b->ids[i], h.fail_step,
-               h.failed == GSW_E_NAN ? "non-finite residual" : "no convergence");
+          fail(ctx, st, "model %d%s failed at step %d (%s)", b->ids[i],
+               b->dirs[i] == 0 ? " (direction x1)" : (b->dirs[i] == 1 ? " (direction x2)" :
+                                                      (b->dirs[i] == 2 ? " (direction x3)" : "")),
+               h.fail_step, h.failed == GSW_E_NAN ? "non-finite residual" : "no convergence");
         }
       }
       if (h.needs_host && !m->failed) {
@@ -1659,7 +1846,7 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
         b->adapt_outer = next;
         outer = 0;
         for (int i = 0; i < nm; ++i) {
-          Model* m = find(ctx, b->ids[i]);
+          Model* m = b->members[i];
           outer = std::max(outer, m->opts.batch_outer > 0 ? m->opts.batch_outer : b->adapt_outer);
         }
         if (outer != b->outer && remaining > 0) TRY(capture());
@@ -1678,10 +1865,7 @@ gsw_status gsw_batch_destroy(gsw_ctx* ctx, int32_t batch_id) {
   auto it = ctx->batches.find(batch_id);
   if (it == ctx->batches.end()) return fail(ctx, GSW_E_INVALID, "unknown batch %d", batch_id);
   cudaStreamSynchronize(it->second->origin);
-  for (int id : it->second->ids) {
-    Model* m = find(ctx, id);
-    if (m) m->batch = 0;
-  }
+  for (Model* m : it->second->members) m->batch = 0;
   batch_free(ctx, it->second);
   ctx->batches.erase(it);
   return GSW_OK;
@@ -1695,12 +1879,28 @@ gsw_status gsw_batch_launches(gsw_ctx* ctx, int32_t batch_id, int64_t* per_step)
   return GSW_OK;
 }
 
-gsw_status gsw_read_waveforms(gsw_ctx* ctx, int32_t model_id, double* out) {
-  if (!ctx || !out) return GSW_E_INVALID;
-  DeviceGuard g(ctx->device);
+// The analysis selected by dir: -1 the model's own (the direction of its last
+// gsw_set_input), 0..2 the instance of that input direction run by gsw_run.
+gsw_status analysis_of(gsw_ctx* ctx, int32_t model_id, int32_t dir, Model** out, bool need_time = true) {
   Model* m = find(ctx, model_id);
   if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
-  if (!m->time_set) return fail(ctx, GSW_E_STATE, "call gsw_set_time first");
+  if (dir < -1 || dir > 2) return fail(ctx, GSW_E_INVALID, "dir must be -1, 0, 1 or 2");
+  if (need_time && !m->time_set) return fail(ctx, GSW_E_STATE, "call gsw_set_time first");
+  if (dir >= 0) {
+    m = m->inst[dir];
+    if (!m)
+      return fail(ctx, GSW_E_STATE, "direction %d of model %d has not been run (gsw_run with its bit in dirs_mask)",
+                  dir, model_id);
+  }
+  *out = m;
+  return GSW_OK;
+}
+
+gsw_status gsw_read_waveforms(gsw_ctx* ctx, int32_t model_id, int32_t dir, double* out) {
+  if (!ctx || !out) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  Model* m = nullptr;
+  TRY(analysis_of(ctx, model_id, dir, &m));
   CK(cudaMemcpyAsync(out, m->wave, sizeof(double) * (size_t)m->n_rec * 3 * m->n_steps,
                      cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -1752,10 +1952,10 @@ gsw_status gsw_timing(gsw_ctx* ctx, int32_t model_id, int32_t enable, double* ms
   return GSW_OK;
 }
 
-gsw_status gsw_stats_get(gsw_ctx* ctx, int32_t model_id, gsw_stats* out) {
+gsw_status gsw_stats_get(gsw_ctx* ctx, int32_t model_id, int32_t dir, gsw_stats* out) {
   if (!ctx || !out) return GSW_E_INVALID;
-  Model* m = find(ctx, model_id);
-  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  Model* m = nullptr;
+  TRY(analysis_of(ctx, model_id, dir, &m, false));
   *out = m->stats;
   if (m->lo_ready && m->opts.precision != GSW_PREC_FP64) {
     // inner iterations actually executed since the last reset (device counter)
@@ -1802,6 +2002,185 @@ gsw_status gsw_set_state(gsw_ctx* ctx, int32_t model_id, const double* u, const 
   CK(cudaStreamSynchronize(ctx->stream));
   m->step = step;
   m->failed = false;
+  return GSW_OK;
+}
+
+// Checkpoint layout: a fixed header, then u, v, a [3N] doubles, the receiver
+// history [n_rec][3][n_steps] doubles, the increment ring [(k+1)][3N] doubles
+// (guess order k > 0), and with the learned guess its parameters, Adam
+// moments ([5443] floats each) and increment history ([4][3N] floats).
+namespace {
+constexpr uint64_t kCkptMagic = 0x31544b5057534737ULL;  // "7GSWPKT1"
+struct CkptHeader {
+  uint64_t magic;
+  int64_t n_nodes, n_steps, n_rec, step;
+  int32_t dir, guess_order, ring_count, ring_head;
+  int32_t has_mlp, hist_head, hist_count, adam_t;
+  int32_t mlp_off, failed;
+  int64_t std_r0_n, mlp_r0_n, applied, inner_done;
+  double std_r0[5], mlp_r0[5];
+  gsw_stats stats;
+  MlpScalars ms;
+  gsw_learn_opts learn;
+  uint64_t bytes;
+};
+size_t ckpt_bytes(const Model* m, bool mlp) {
+  const size_t n3 = 3 * (size_t)m->N;
+  size_t b = sizeof(CkptHeader) + 3 * n3 * sizeof(double) + (size_t)m->n_rec * 3 * m->n_steps * sizeof(double);
+  if (m->opts.guess_order > 0) b += (size_t)(m->opts.guess_order + 1) * n3 * sizeof(double);
+  if (mlp) b += 3 * (size_t)kMlpParams * sizeof(float) + 4 * n3 * sizeof(double);
+  return b;
+}
+}  // namespace
+
+gsw_status gsw_checkpoint(gsw_ctx* ctx, int32_t model_id, void* buf, size_t* bytes) {
+  if (!ctx || !bytes) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (!m->time_set) return fail(ctx, GSW_E_STATE, "call gsw_set_time first");
+  const bool mlp = m->mlp_ready && m->learn.enable;
+  const size_t need = ckpt_bytes(m, mlp);
+  if (!buf) {
+    *bytes = need;
+    return GSW_OK;
+  }
+  if (*bytes < need) {
+    *bytes = need;
+    return fail(ctx, GSW_E_INVALID, "checkpoint buffer of %zu bytes is smaller than %zu", *bytes, need);
+  }
+  cudaStream_t s = ctx->stream;
+  CkptHeader h = {};
+  h.magic = kCkptMagic;
+  h.n_nodes = m->N;
+  h.n_steps = m->n_steps;
+  h.n_rec = m->n_rec;
+  h.step = m->step;
+  h.dir = m->dir;
+  h.guess_order = m->opts.guess_order;
+  h.has_mlp = mlp ? 1 : 0;
+  h.hist_head = m->hist_head;
+  h.hist_count = m->hist_count;
+  h.adam_t = m->adam_t;
+  h.mlp_off = m->mlp_off ? 1 : 0;
+  h.failed = m->failed ? 1 : 0;
+  h.std_r0_n = m->std_r0_n;
+  h.mlp_r0_n = m->mlp_r0_n;
+  h.applied = m->applied;
+  for (int k = 0; k < 5; ++k) {
+    h.std_r0[k] = m->std_r0_recent[k];
+    h.mlp_r0[k] = m->mlp_r0_recent[k];
+  }
+  TRY(gsw_stats_get(ctx, model_id, -1, &h.stats));
+  h.bytes = need;
+  if (m->guess_ext) {
+    int ext[2] = {0, 0};
+    CK(cudaMemcpyAsync(ext, m->guess_ext, sizeof(ext), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    h.ring_count = ext[0];
+    h.ring_head = ext[1];
+  }
+  if (mlp) {
+    h.learn = m->learn;
+    CK(cudaMemcpyAsync(&h.ms, m->ms, sizeof(MlpScalars), cudaMemcpyDeviceToHost, s));
+  }
+  char* p = (char*)buf + sizeof(CkptHeader);
+  const size_t n3 = 3 * (size_t)m->N;
+  auto d2h = [&](const void* src, size_t nb) {
+    cudaError_t e = cudaMemcpyAsync(p, src, nb, cudaMemcpyDeviceToHost, s);
+    p += nb;
+    return e;
+  };
+  CK(d2h(m->u, n3 * sizeof(double)));
+  CK(d2h(m->v, n3 * sizeof(double)));
+  CK(d2h(m->a, n3 * sizeof(double)));
+  CK(d2h(m->wave, (size_t)m->n_rec * 3 * m->n_steps * sizeof(double)));
+  if (m->opts.guess_order > 0) CK(d2h(m->guess_ring, (size_t)(m->opts.guess_order + 1) * n3 * sizeof(double)));
+  if (mlp) {
+    CK(d2h(m->theta, kMlpParams * sizeof(float)));
+    CK(d2h(m->adam_m, kMlpParams * sizeof(float)));
+    CK(d2h(m->adam_v, kMlpParams * sizeof(float)));
+    CK(d2h(m->hist, 4 * n3 * sizeof(double)));
+  }
+  CK(cudaStreamSynchronize(s));
+  memcpy(buf, &h, sizeof(h));
+  *bytes = need;
+  return GSW_OK;
+}
+
+gsw_status gsw_restore(gsw_ctx* ctx, int32_t model_id, const void* buf, size_t bytes) {
+  if (!ctx || !buf) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (!m->time_set) return fail(ctx, GSW_E_STATE, "call gsw_set_time first");
+  if (m->batch) return fail(ctx, GSW_E_STATE, "model %d belongs to a batch", model_id);
+  CkptHeader h;
+  if (bytes < sizeof(h)) return fail(ctx, GSW_E_INVALID, "checkpoint too short");
+  memcpy(&h, buf, sizeof(h));
+  if (h.magic != kCkptMagic) return fail(ctx, GSW_E_INVALID, "not a checkpoint of this library");
+  if (h.n_nodes != m->N || h.n_steps != m->n_steps || h.n_rec != m->n_rec)
+    return fail(ctx, GSW_E_INVALID, "checkpoint of a different model or time set-up");
+  if (h.dir != m->dir)
+    return fail(ctx, GSW_E_INVALID, "checkpoint of input direction %d, model set to direction %d", h.dir, m->dir);
+  if (h.guess_order != m->opts.guess_order)
+    return fail(ctx, GSW_E_INVALID, "checkpoint taken with guess_order %d, model set to %d", h.guess_order,
+                m->opts.guess_order);
+  if (h.has_mlp && !(m->learn.enable && m->mlp_ready))
+    return fail(ctx, GSW_E_STATE, "checkpoint holds a learned guess: enable learning on the model first");
+  if (h.step < 0 || h.step > m->n_steps || h.bytes != bytes || bytes != ckpt_bytes(m, h.has_mlp != 0))
+    return fail(ctx, GSW_E_INVALID, "checkpoint size or step inconsistent");
+  cudaStream_t s = ctx->stream;
+  const char* p = (const char*)buf + sizeof(CkptHeader);
+  const size_t n3 = 3 * (size_t)m->N;
+  if (!finite_all((const double*)p, 3 * n3)) return fail(ctx, GSW_E_INVALID, "non-finite state in checkpoint");
+  auto h2d = [&](void* dst, size_t nb) {
+    cudaError_t e = cudaMemcpyAsync(dst, p, nb, cudaMemcpyHostToDevice, s);
+    p += nb;
+    return e;
+  };
+  CK(h2d(m->u, n3 * sizeof(double)));
+  CK(h2d(m->v, n3 * sizeof(double)));
+  CK(h2d(m->a, n3 * sizeof(double)));
+  CK(h2d(m->wave, (size_t)m->n_rec * 3 * m->n_steps * sizeof(double)));
+  if (m->opts.guess_order > 0) {
+    CK(h2d(m->guess_ring, (size_t)(m->opts.guess_order + 1) * n3 * sizeof(double)));
+    const int ext[2] = {h.ring_count, h.ring_head};
+    CK(cudaMemcpyAsync(m->guess_ext, ext, sizeof(ext), cudaMemcpyHostToDevice, s));
+  }
+  if (h.has_mlp) {
+    CK(h2d(m->theta, kMlpParams * sizeof(float)));
+    CK(h2d(m->adam_m, kMlpParams * sizeof(float)));
+    CK(h2d(m->adam_v, kMlpParams * sizeof(float)));
+    CK(h2d(m->hist, 4 * n3 * sizeof(double)));
+    CK(cudaMemcpyAsync(m->ms, &h.ms, sizeof(MlpScalars), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(m->grad, 0, sizeof(float) * kMlpParams, s));
+    launch_mlp_pack(m->theta, m->packed, s);
+    CK(cudaGetLastError());
+    m->learn = h.learn;
+    m->hist_head = h.hist_head;
+    m->hist_count = h.hist_count;
+    m->adam_t = h.adam_t;
+    m->mlp_off = h.mlp_off != 0;
+    m->std_r0_n = h.std_r0_n;
+    m->mlp_r0_n = h.mlp_r0_n;
+    m->applied = h.applied;
+    for (int k = 0; k < 5; ++k) {
+      m->std_r0_recent[k] = h.std_r0[k];
+      m->mlp_r0_recent[k] = h.mlp_r0[k];
+    }
+  }
+  if (m->lo_ready) {
+    // inner iterations since the reset continue from the checkpoint's count
+    unsigned long long n = 0;
+    CK(cudaMemcpyAsync(&n, &m->isc->iters, sizeof(n), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    m->iters_reset = n - (unsigned long long)h.stats.inner_iters_total;
+  }
+  CK(cudaStreamSynchronize(s));
+  m->stats = h.stats;
+  m->step = h.step;
+  m->failed = h.failed != 0;
   return GSW_OK;
 }
 
@@ -1857,8 +2236,39 @@ gsw_status gsw_read_receivers(gsw_ctx* ctx, int32_t model_id, int32_t* nodes, do
   return GSW_OK;
 }
 
-gsw_status gsw_misfit(gsw_ctx* ctx, int32_t n_rec, int32_t n_t, const double* G, const double* obs,
-                      int32_t stride, int32_t n_shifts, double tau, double* err, double* c_out) {
+gsw_status gsw_misfit(gsw_ctx* ctx, int32_t model_id, const double* obs, int32_t stride, int32_t n_shifts,
+                      double tau, double* err, double* c_out) {
+  if (!ctx || !obs || !err) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (stride <= 0 || n_shifts <= 0 || !(tau >= 0.0))
+    return fail(ctx, GSW_E_INVALID, "need stride, n_shifts > 0 and tau >= 0");
+  if (3 * n_shifts > kMisfitMaxUnknowns)
+    return fail(ctx, GSW_E_INVALID, "3 * n_shifts must be <= %d", kMisfitMaxUnknowns);
+  if (m->n_rec <= 0) return fail(ctx, GSW_E_STATE, "model %d has no receivers", model_id);
+  const double* waves[3];
+  for (int d = 0; d < 3; ++d) {
+    Model* c = m->inst[d];
+    if (!c || c->failed || c->step != c->n_steps || m->inst_version[d] != m->version || c->input != m->dir_input[d])
+      return fail(ctx, GSW_E_STATE, "model %d: run all three input directions to the end first (gsw_run with "
+                  "dirs_mask 7)", model_id);
+    waves[d] = c->wave;
+  }
+  if (!finite_all(obs, (size_t)m->n_rec * 3 * m->n_steps))
+    return fail(ctx, GSW_E_INVALID, "non-finite observation");
+  char msg[256] = {0};
+  cudaError_t ce = cudaSuccess;
+  int rc = misfit_run_waves(ctx->misfit, ctx->stream, m->n_rec, m->n_steps, m->n_steps, waves, obs, stride,
+                            n_shifts, tau, err, c_out, msg, sizeof msg, &ce);
+  if (rc == 1) return fail(ctx, GSW_E_CUDA, "misfit: %s (%s)", msg, cudaGetErrorString(ce));
+  if (rc == 2) return fail(ctx, GSW_E_NOMEM, "misfit: %s", msg);
+  if (rc == 3) return fail(ctx, GSW_E_INVALID, "misfit: %s", msg);
+  return GSW_OK;
+}
+
+gsw_status gsw_misfit_green(gsw_ctx* ctx, int32_t n_rec, int32_t n_t, const double* G, const double* obs,
+                            int32_t stride, int32_t n_shifts, double tau, double* err, double* c_out) {
   if (!ctx || !G || !obs || !err) return GSW_E_INVALID;
   DeviceGuard g(ctx->device);
   if (n_rec <= 0 || n_t <= 0 || stride <= 0 || n_shifts <= 0 || !(tau >= 0.0))
@@ -1899,6 +2309,31 @@ gsw_status gsw_set_learning(gsw_ctx* ctx, int32_t model_id, const gsw_learn_opts
   return GSW_OK;
 }
 
+gsw_status gsw_mlp_train(gsw_ctx* ctx, int32_t model_id, int32_t n_train_steps, const gsw_learn_opts* opts) {
+  if (!ctx || !opts) return GSW_E_INVALID;
+  DeviceGuard g(ctx->device);
+  Model* m = find(ctx, model_id);
+  if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
+  if (!m->time_set || !m->input_set) return fail(ctx, GSW_E_STATE, "set the time and the input first");
+  if (m->batch) return fail(ctx, GSW_E_STATE, "model %d belongs to a batch", model_id);
+  if (m->opts.precision == GSW_PREC_FP64)
+    return fail(ctx, GSW_E_STATE, "the learned guess runs with the mixed-precision solver");
+  if (!opts->enable) return fail(ctx, GSW_E_INVALID, "opts->enable must be 1");
+  if (n_train_steps < 5 || m->step + n_train_steps > m->n_steps)
+    return fail(ctx, GSW_E_INVALID, "need 5 <= n_train_steps <= the steps left (%lld)",
+                (long long)(m->n_steps - m->step));
+  if (opts->batch < 64 || opts->batch > 65536 || opts->iters_per_step < 0 || !(opts->lr > 0.f))
+    return fail(ctx, GSW_E_INVALID, "need 64 <= batch <= 65536, iters_per_step >= 0, lr > 0");
+  const bool fresh = !(m->learn.enable && m->mlp_ready);
+  m->learn = *opts;
+  m->learn.train_steps = (int32_t)(m->step + n_train_steps);
+  if (fresh) {
+    TRY(mlp_alloc(ctx, m));
+    TRY(mlp_init(ctx, m, opts->seed));
+  }
+  return gsw_step(ctx, model_id, n_train_steps);
+}
+
 gsw_status gsw_mlp_params(gsw_ctx* ctx, int32_t model_id, double* get, const double* set) {
   if (!ctx) return GSW_E_INVALID;
   DeviceGuard g(ctx->device);
@@ -1931,8 +2366,7 @@ gsw_status gsw_mlp_forward(gsw_ctx* ctx, int32_t model_id, int32_t n, const floa
   if (!m->mlp_ready) return fail(ctx, GSW_E_STATE, "no MLP: call gsw_set_learning or gsw_mlp_params first");
   if (n <= 0 || n > 65536) return fail(ctx, GSW_E_INVALID, "n must be 1..65536");
   CK(cudaMemcpyAsync(m->trainX, x, sizeof(float) * 16 * n, cudaMemcpyHostToDevice, ctx->stream));
-  launch_mlp_infer(n, nullptr, 0, nullptr, nullptr, nullptr, 0.0, m->packed, nullptr, nullptr, m->trainX, m->trainY,
-                   ctx->stream);
+  launch_mlp_infer(n, nullptr, nullptr, m->packed, nullptr, nullptr, m->trainX, m->trainY, ctx->stream, nullptr);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(out, m->trainY, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -2004,14 +2438,14 @@ gsw_status gsw_mlp_inputs(gsw_ctx* ctx, int32_t model_id, float* x_train, float*
   if (x_train) CK(cudaMemcpyAsync(x_train, m->trainX, sizeof(float) * 16 * (size_t)B, cudaMemcpyDeviceToHost, s));
   if (y_train) CK(cudaMemcpyAsync(y_train, m->trainY, sizeof(float) * 3 * (size_t)B, cudaMemcpyDeviceToHost, s));
   if (n > 0 || scale) {
-    // the next step's inputs: sigma of the latest increment, the base guess
-    launch_mlp_sigma(m->N, m->hist, m->hist_head, m->partials, m->ms, s);
-    const double* xb = nullptr;
-    if (m->opts.guess_order > 0) {
-      if (!m->guess_base) TRY(alloc_into(ctx, m, &m->guess_base, 3 * (size_t)m->N));
+    // the next step's inputs: the difference scales, the base guess
+    launch_mlp_sigma(m->N, m->hist, m->partials, m->ms, s);
+    if (!m->guess_base) TRY(alloc_into(ctx, m, &m->guess_base, 3 * (size_t)m->N));
+    const double* xb = m->guess_base;
+    if (m->opts.guess_order > 0)
       launch_guess_extrap(m->N, m->guess_ring, m->opts.guess_order, m->guess_ext, m->v, m->a, m->dt, m->guess_base, s);
-      xb = m->guess_base;
-    }
+    else
+      launch_predictor(m->N, m->v, m->a, m->dt, m->guess_base, s);
     if (n > 0) {
       int32_t* nd = (int32_t*)dev_alloc(ctx, nullptr, sizeof(int32_t) * n);
       float* xd = (float*)dev_alloc(ctx, nullptr, sizeof(float) * 16 * (size_t)n);
@@ -2022,7 +2456,7 @@ gsw_status gsw_mlp_inputs(gsw_ctx* ctx, int32_t model_id, float* x_train, float*
       } else if (cudaMemcpyAsync(nd, nodes, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s) != cudaSuccess) {
         st = fail(ctx, GSW_E_CUDA, "node list copy failed");
       } else {
-        launch_mlp_inputs(n, nd, m->N, m->hist, m->hist_head, m->nodef, m->ms, m->v, m->a, m->dt, xb, xd, bd, s);
+        launch_mlp_inputs(n, nd, m->N, m->hist, m->nodef, m->ms, xb, xd, bd, s);
         if (cudaGetLastError() != cudaSuccess ||
             cudaMemcpyAsync(x, xd, sizeof(float) * 16 * (size_t)n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaMemcpyAsync(base, bd, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -2038,8 +2472,8 @@ gsw_status gsw_mlp_inputs(gsw_ctx* ctx, int32_t model_id, float* x_train, float*
       MlpScalars h = {};
       CK(cudaMemcpyAsync(&h, m->ms, sizeof(MlpScalars), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
-      scale[0] = h.sigma;
-      scale[1] = xb ? h.sigma_e : h.sigma;
+      scale[0] = h.sigma[0];
+      scale[1] = h.sigma_e;
     }
   }
   CK(cudaStreamSynchronize(s));

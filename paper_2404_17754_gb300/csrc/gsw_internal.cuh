@@ -43,11 +43,11 @@ struct CgScalars {
 // Scalars of the learned initial guess (one set per model).
 constexpr int kMlpParams = 5443;  // 16-64-64-3 MLP
 struct MlpScalars {
-  double sigma;    // RMS of the latest displacement increment
-  double loss;     // training loss accumulator
+  double sigma[4];  // RMS of the backward differences D_0..D_3 of the latest increments
+  double loss;      // training loss accumulator
   unsigned int counter;
   unsigned int pad;
-  double sigma_e;  // RMS of the last step's correction to the extrapolated guess (its output scale)
+  double sigma_e;   // RMS of the last step's correction du - base (the output scale)
 };
 void launch_mlp_sigma_e(int64_t N, const double* du, const double* base, double* partials, MlpScalars* ms,
                         cudaStream_t s);
@@ -267,21 +267,23 @@ int node_blocks(int64_t n);
 // ---- learned initial guess (gsw_mlp.cu) ------------------------------------------
 void launch_mlp_pack(const float* theta, uint32_t* packed, cudaStream_t s);
 void launch_node_features(const ModelView& m, int n_mat, int32_t* node_mat, float* nodef, cudaStream_t s);
-void launch_mlp_sigma(int64_t N, const float* hist, int head, double* partials, MlpScalars* ms, cudaStream_t s);
-void launch_mlp_infer(int64_t N, const float* hist, int head, const float* nodef, const double* v, const double* a,
-                      double dt, const uint32_t* packed, const MlpScalars* ms, double* x, const float* xin,
-                      float* yout, cudaStream_t s, const double* x_base = nullptr);
-void launch_mlp_sample(int64_t N, int B, uint32_t seed, int step, int iter, const float* hist, int head,
-                       const float* nodef, const double* du, const double* v, const double* a, double dt,
-                       const MlpScalars* ms, float* X, float* Y, cudaStream_t s, const double* x_base = nullptr);
+// hist: [4][3N] doubles, the backward differences D_0..D_3 of the last four
+// converged increments (D_k = sum_j (-1)^j C(k, j) du_{s-1-j}).
+void launch_mlp_sigma(int64_t N, const double* hist, double* partials, MlpScalars* ms, cudaStream_t s);
+// x <- base + sigma_e * MLP(features) over all nodes (xin / yout: explicit
+// features and raw outputs, diagnostics)
+void launch_mlp_infer(int64_t N, const double* hist, const float* nodef, const uint32_t* packed, const MlpScalars* ms,
+                      double* x, const float* xin, float* yout, cudaStream_t s, const double* x_base);
+void launch_mlp_sample(int64_t N, int B, uint32_t seed, int step, int iter, const double* hist, const float* nodef,
+                       const double* du, const double* base, const MlpScalars* ms, float* X, float* Y, cudaStream_t s);
 int launch_mlp_fwdbwd(int B, const float* X, const float* Y, const float* theta, float* grad, double* loss,
                       cudaStream_t s);
 void launch_mlp_adam(float* theta, float* grad, float* m, float* v, int t, float lr, cudaStream_t s);
-void launch_hist_push(int64_t N, const double* du, float* hist, int slot, const CgScalars* cg, cudaStream_t s,
+void launch_hist_push(int64_t N, const double* du, double* hist, const CgScalars* cg, cudaStream_t s,
                       const StepState* ss = nullptr);
-void launch_mlp_inputs(int n, const int32_t* nodes, int64_t N, const float* hist, int head, const float* nodef,
-                       const MlpScalars* ms, const double* v, const double* a, double dt, const double* x_base, float* X,
-                       double* base, cudaStream_t s);
+void launch_predictor(int64_t N, const double* v, const double* a, double dt, double* x, cudaStream_t s);
+void launch_mlp_inputs(int n, const int32_t* nodes, int64_t N, const double* hist, const float* nodef,
+                       const MlpScalars* ms, const double* base, float* X, double* base_out, cudaStream_t s);
 int mlp_packed_words();
 
 }  // namespace gsw

@@ -1,17 +1,20 @@
 // Learned initial guess for the per-step CG solve: a per-node MLP that maps
-// the last four displacement increments (scaled by the RMS of the latest one)
-// and the node's layer properties to a correction of the Newmark predictor.
+// the backward differences of the last four displacement increments (each
+// scaled by its RMS) and the node's layer properties to a correction of the
+// step's base guess (the Newmark predictor, or the polynomial extrapolation).
 //
-//   x (16)  = [du_{s-1}, du_{s-2}, du_{s-3}, du_{s-4}] / sigma ++ [Vs/1000, Vp/3000, rho/2000, h/0.05]
+//   x (16)  = [D_0 / s_0, D_1 / s_1, D_2 / s_2, D_3 / s_3] ++ [Vs/1000, Vp/3000, rho/2000, h/0.05],
+//             D_k = sum_j (-1)^j C(k, j) du_{s-1-j}, s_k = RMS(D_k)
 //   h1 = relu(x W1 + b1) (64), h2 = relu(h1 W2 + b2) (64), o = h2 W3 + b3 (3)
-//   du0 = dt v + dt^2/2 a + sigma * o
+//   du0 = base + sigma_e * o, sigma_e = RMS of the previous step's correction
 //
 // Inference runs on the tensor cores: BF16 operands, FP32 accumulation, with
 // mma.m16n8k16; the accumulator fragment of one layer is exactly the operand
 // fragment of the next (after bias, ReLU and BF16 rounding), so a warp carries
 // 16 nodes through all three layers in registers.  Training (on the solutions
-// of the first steps) runs in FP32: a fused forward/backward kernel per batch
-// chunk with the weight gradients reduced in shared memory, then Adam.
+// of the first steps) runs on the tensor cores too: forward, back-propagated
+// errors and weight gradients as BF16 products with FP32 accumulation, then
+// Adam on FP32 master weights.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -46,42 +49,47 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
 
 // Operand fragment of B (K x N, "col") for lane (g = lane/4, t = lane%4):
 // reg0 = (B[2t][g], B[2t+1][g]), reg1 = (B[2t+8][g], B[2t+9][g]).
+// The forward weights as BF16 B fragments (layer 1: 8 n-tiles; layer 2: 4
+// k-tiles x 8 n-tiles; layer 3: 4 k-tiles, N padded 3 -> 8) and the FP32
+// biases (64 + 64 + 8), written by threads tid0, tid0 + stride, ...
+__device__ void build_fwd_frags(const float* __restrict__ theta, uint32_t* frag, float* bias, int tid0, int stride) {
+  for (int tid = tid0; tid < 32 * 32; tid += stride) {
+    const int lane = tid % 32, g = lane / 4, t = lane % 4;
+    if (tid < 8 * 32) {  // layer 1: K = 16, N = 64
+      const int n = 8 * (tid / 32) + g;
+      auto W = [&](int k) { return theta[kW1 + k * 64 + n]; };
+      frag[kF1 + 2 * tid] = pack_bf16(W(2 * t), W(2 * t + 1));
+      frag[kF1 + 2 * tid + 1] = pack_bf16(W(2 * t + 8), W(2 * t + 9));
+    }
+    {  // layer 2: K = 64 (4 k-tiles), N = 64
+      const int kt = tid / 256, nt = (tid / 32) % 8;
+      const int n = 8 * nt + g, k0 = 16 * kt;
+      auto W = [&](int k) { return theta[kW2 + (k0 + k) * 64 + n]; };
+      frag[kF2 + 2 * tid] = pack_bf16(W(2 * t), W(2 * t + 1));
+      frag[kF2 + 2 * tid + 1] = pack_bf16(W(2 * t + 8), W(2 * t + 9));
+    }
+    if (tid < 4 * 32) {  // layer 3: K = 64, N = 3 padded to 8
+      const int k0 = 16 * (tid / 32);
+      auto W = [&](int k) { return g < 3 ? theta[kW3 + (k0 + k) * 3 + g] : 0.f; };
+      frag[kF3 + 2 * tid] = pack_bf16(W(2 * t), W(2 * t + 1));
+      frag[kF3 + 2 * tid + 1] = pack_bf16(W(2 * t + 8), W(2 * t + 9));
+    }
+    if (tid < 136) {
+      float b = 0.f;
+      if (tid < 64)
+        b = theta[kB1 + tid];
+      else if (tid < 128)
+        b = theta[kB2 + tid - 64];
+      else if (tid < 131)
+        b = theta[kB3 + tid - 128];
+      bias[tid] = b;
+    }
+  }
+}
+
 __global__ void mlp_pack_kernel(const float* __restrict__ theta, uint32_t* packed) {
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  // layer 1: K = 16, N = 64
-  if (tid < 8 * 32) {
-    const int nt = tid / 32, lane = tid % 32, g = lane / 4, t = lane % 4;
-    const int n = 8 * nt + g;
-    auto W = [&](int k) { return theta[kW1 + k * 64 + n]; };
-    packed[kF1 + 2 * tid] = pack_bf16(W(2 * t), W(2 * t + 1));
-    packed[kF1 + 2 * tid + 1] = pack_bf16(W(2 * t + 8), W(2 * t + 9));
-  }
-  // layer 2: K = 64 (4 k-tiles), N = 64
-  if (tid < 32 * 32) {
-    const int kt = tid / 256, nt = (tid / 32) % 8, lane = tid % 32, g = lane / 4, t = lane % 4;
-    const int n = 8 * nt + g, k0 = 16 * kt;
-    auto W = [&](int k) { return theta[kW2 + (k0 + k) * 64 + n]; };
-    packed[kF2 + 2 * tid] = pack_bf16(W(2 * t), W(2 * t + 1));
-    packed[kF2 + 2 * tid + 1] = pack_bf16(W(2 * t + 8), W(2 * t + 9));
-  }
-  // layer 3: K = 64, N = 3 padded to 8
-  if (tid < 4 * 32) {
-    const int kt = tid / 32, lane = tid % 32, g = lane / 4, t = lane % 4;
-    const int k0 = 16 * kt;
-    auto W = [&](int k) { return g < 3 ? theta[kW3 + (k0 + k) * 3 + g] : 0.f; };
-    packed[kF3 + 2 * tid] = pack_bf16(W(2 * t), W(2 * t + 1));
-    packed[kF3 + 2 * tid + 1] = pack_bf16(W(2 * t + 8), W(2 * t + 9));
-  }
-  if (tid < 136) {
-    float b = 0.f;
-    if (tid < 64)
-      b = theta[kB1 + tid];
-    else if (tid < 128)
-      b = theta[kB2 + tid - 64];
-    else if (tid < 131)
-      b = theta[kB3 + tid - 128];
-    reinterpret_cast<float*>(packed)[kBias + tid] = b;
-  }
+  build_fwd_frags(theta, packed, reinterpret_cast<float*>(packed) + kBias, blockIdx.x * blockDim.x + threadIdx.x,
+                  gridDim.x * blockDim.x);
 }
 
 // Per-node layer features (Vs/1000, Vp/3000, rho/2000, h/0.05) of the lowest
@@ -104,23 +112,26 @@ __global__ void node_features_kernel(int64_t N, const int32_t* node_mat, const M
   nodef[4 * n + 3] = (float)(c.h / 0.05);
 }
 
-// sigma = RMS over all DOF of the latest increment (history slot `head`).
-__global__ void mlp_sigma_kernel(int64_t N, const float* __restrict__ hist, int head, double* partials,
-                                 MlpScalars* ms) {
-  const float* h = hist + (int64_t)head * 3 * N;
-  double s = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N; i += (int64_t)gridDim.x * blockDim.x)
-    s += (double)h[i] * h[i];
-  double vals[1] = {s}, out[1];
-  if (last_block_reduce<1>(vals, partials, &ms->counter, out) && threadIdx.x == 0) {
-    const double sg = sqrt(out[0] / (3.0 * N));
-    ms->sigma = sg > 0.0 ? sg : 1.0;
+// sigma_k = RMS over all DOF of the backward difference D_k (1 if zero).
+__global__ void mlp_sigma_kernel(int64_t N, const double* __restrict__ hist, double* partials, MlpScalars* ms) {
+  double sq[4] = {0.0, 0.0, 0.0, 0.0};
+  const int64_t n3 = 3 * N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sq[k] = fma(hist[k * n3 + i], hist[k * n3 + i], sq[k]);
+  double out[4];
+  if (last_block_reduce<4>(sq, partials, &ms->counter, out) && threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double sg = sqrt(out[k] / (double)n3);
+      ms->sigma[k] = sg > 0.0 ? sg : 1.0;
+    }
   }
 }
 
-// RMS of du - base (the correction the network should have made to the
-// extrapolated guess of the step just converged): the output scale of the
-// correction to an extrapolated base, far smaller than the increment itself.
+// RMS of du - base (the correction the network should have made to the base
+// guess of the step just converged): the output scale of the next step's
+// correction, far smaller than the increment itself.
 __global__ void mlp_sigma_e_kernel(int64_t N, const double* __restrict__ du, const double* __restrict__ base,
                                    double* partials, MlpScalars* ms) {
   double s = 0.0;
@@ -131,7 +142,7 @@ __global__ void mlp_sigma_e_kernel(int64_t N, const double* __restrict__ du, con
   double vals[1] = {s}, out[1];
   if (last_block_reduce<1>(vals, partials, &ms->counter, out) && threadIdx.x == 0) {
     const double sg = sqrt(out[0] / (3.0 * N));
-    ms->sigma_e = sg > 0.0 ? sg : ms->sigma;
+    ms->sigma_e = sg > 0.0 ? sg : ms->sigma[0];
   }
 }
 void launch_mlp_sigma_e(int64_t N, const double* du, const double* base, double* partials, MlpScalars* ms,
@@ -139,21 +150,19 @@ void launch_mlp_sigma_e(int64_t N, const double* du, const double* base, double*
   mlp_sigma_e_kernel<<<node_blocks(3 * N), kNodeThreads, 0, s>>>(N, du, base, partials, ms);
 }
 
-__device__ __forceinline__ float node_feature(const float* __restrict__ hist, const float* __restrict__ nodef,
-                                              int64_t N, int head, int64_t n, int f, float inv_sigma) {
+__device__ __forceinline__ float node_feature(const double* __restrict__ hist, const float* __restrict__ nodef,
+                                              int64_t N, int64_t n, int f, const float (&inv_sigma)[4]) {
   if (f < 12) {
     const int k = f / 3, c = f % 3;
-    const int slot = (head - k + 4) & 3;
-    return hist[((int64_t)slot * N + n) * 3 + c] * inv_sigma;
+    return (float)hist[((int64_t)k * N + n) * 3 + c] * inv_sigma[k];
   }
   return nodef[4 * n + (f - 12)];
 }
 
-// Tensor-core inference over all nodes: x <- dt v + dt^2/2 a + sigma * MLP(features).
-__global__ void __launch_bounds__(128) mlp_infer_kernel(int64_t N, const float* __restrict__ hist, int head,
+// Tensor-core inference over all nodes: x <- base + sigma_e * MLP(features).
+__global__ void __launch_bounds__(128) mlp_infer_kernel(int64_t N, const double* __restrict__ hist,
                                                         const float* __restrict__ nodef,
-                                                        const double* __restrict__ v, const double* __restrict__ a,
-                                                        double dt, const uint32_t* __restrict__ packed,
+                                                        const uint32_t* __restrict__ packed,
                                                         const MlpScalars* ms, double* __restrict__ x,
                                                         const float* __restrict__ xin, float* __restrict__ yout,
                                                         const double* __restrict__ x_base) {
@@ -164,9 +173,10 @@ __global__ void __launch_bounds__(128) mlp_infer_kernel(int64_t N, const float* 
   for (int i = threadIdx.x; i < 136; i += blockDim.x) bias[i] = reinterpret_cast<const float*>(packed)[kBias + i];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const double sigma = ms ? ms->sigma : 1.0;
   const double sigma_e = ms ? ms->sigma_e : 1.0;
-  const float inv_sigma = (float)(1.0 / sigma);
+  float inv_sigma[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) inv_sigma[k] = ms ? (float)(1.0 / ms->sigma[k]) : 1.f;
   const int64_t n_tiles = (N + 15) / 16;
   for (int64_t tile = (int64_t)blockIdx.x * 4 + warp; tile < n_tiles; tile += (int64_t)gridDim.x * 4) {
     const int64_t base = tile * 16;
@@ -175,7 +185,7 @@ __global__ void __launch_bounds__(128) mlp_infer_kernel(int64_t N, const float* 
       const int64_t n = base + lane;
       for (int f = 0; f < 16; ++f) {
         float val = 0.f;
-        if (n < N) val = xin ? xin[n * 16 + f] : node_feature(hist, nodef, N, head, n, f, inv_sigma);
+        if (n < N) val = xin ? xin[n * 16 + f] : node_feature(hist, nodef, N, n, f, inv_sigma);
         feat[warp][lane][f] = __float2bfloat16_rn(val);
       }
     }
@@ -256,11 +266,9 @@ __global__ void __launch_bounds__(128) mlp_infer_kernel(int64_t N, const float* 
         if (yout) {
           yout[n * 3 + c] = o;
         } else {
+          // the network corrects the step's base guess (predictor or extrapolation)
           const int64_t k = 3 * n + c;
-          // the network corrects a base guess: the extrapolated one when given,
-          // else the Newmark predictor
-          const double b0 = x_base ? x_base[k] : fma(dt, v[k], 0.5 * dt * dt * a[k]);
-          x[k] = b0 + (x_base ? sigma_e : sigma) * (double)o;
+          x[k] = x_base[k] + sigma_e * (double)o;
         }
       }
     }
@@ -268,25 +276,31 @@ __global__ void __launch_bounds__(128) mlp_infer_kernel(int64_t N, const float* 
 }
 
 // Diagnostics: the features and the base guess that the next step's inference
-// would use, for the listed nodes only (X [n][16], base [n][3]).
-__global__ void mlp_inputs_kernel(int n, const int32_t* __restrict__ nodes, int64_t N, const float* __restrict__ hist,
-                                  int head, const float* __restrict__ nodef, const MlpScalars* ms,
-                                  const double* __restrict__ v, const double* __restrict__ a, double dt,
-                                  const double* __restrict__ x_base, float* X, double* base) {
+// would use, for the listed nodes only (X [n][16], base_out [n][3]).
+__global__ void mlp_inputs_kernel(int n, const int32_t* __restrict__ nodes, int64_t N, const double* __restrict__ hist,
+                                  const float* __restrict__ nodef, const MlpScalars* ms,
+                                  const double* __restrict__ base, float* X, double* base_out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int64_t nd = nodes[i];
-  const float inv_sigma = (float)(1.0 / ms->sigma);
-  for (int f = 0; f < 16; ++f) X[(int64_t)i * 16 + f] = node_feature(hist, nodef, N, head, nd, f, inv_sigma);
-  for (int c = 0; c < 3; ++c) {
-    const int64_t k = 3 * nd + c;
-    base[(int64_t)i * 3 + c] = x_base ? x_base[k] : fma(dt, v[k], 0.5 * dt * dt * a[k]);
-  }
+  float inv_sigma[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) inv_sigma[k] = (float)(1.0 / ms->sigma[k]);
+  for (int f = 0; f < 16; ++f) X[(int64_t)i * 16 + f] = node_feature(hist, nodef, N, nd, f, inv_sigma);
+  for (int c = 0; c < 3; ++c) base_out[(int64_t)i * 3 + c] = base[3 * nd + c];
+}
+
+// The Newmark predictor dt v + dt^2/2 a (the base guess at guess order 0).
+__global__ void predictor_kernel(int64_t n3, const double* __restrict__ v, const double* __restrict__ a, double dt,
+                                 double* __restrict__ x) {
+  const double h = 0.5 * dt * dt;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = fma(dt, v[i], h * a[i]);
 }
 
 // Training samples: node = hash(seed, step, iter, i) mod N; features as in
-// inference (FP32), target = (du_s - base guess) / sigma (base: the extrapolated
-// guess when given, else the Newmark predictor).
+// inference (FP32), target = (du_s - base_s) / sigma_e (sigma_e: the RMS of
+// this step's correction du_s - base_s).
 __device__ __forceinline__ uint32_t mix32(uint32_t x) {
   x ^= x >> 16;
   x *= 0x7feb352dU;
@@ -297,107 +311,305 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
 }
 
 __global__ void mlp_sample_kernel(int64_t N, int B, uint32_t seed, int step, int iter,
-                                  const float* __restrict__ hist, int head, const float* __restrict__ nodef,
-                                  const double* __restrict__ du, const double* __restrict__ v,
-                                  const double* __restrict__ a, double dt, const MlpScalars* ms, float* X,
-                                  float* Y, const double* __restrict__ x_base) {
+                                  const double* __restrict__ hist, const float* __restrict__ nodef,
+                                  const double* __restrict__ du, const double* __restrict__ base,
+                                  const MlpScalars* ms, float* X, float* Y) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B) return;
   const uint32_t h = mix32(seed ^ mix32((uint32_t)step * 0x9E3779B9U ^ mix32((uint32_t)iter * 0x85EBCA6BU ^ (uint32_t)i)));
   const int64_t n = (int64_t)(h % (uint32_t)N);
-  const double sigma = ms->sigma;
-  const double out_scale = x_base ? ms->sigma_e : sigma;
-  const float inv_sigma = (float)(1.0 / sigma);
-  for (int f = 0; f < 16; ++f) X[(int64_t)i * 16 + f] = node_feature(hist, nodef, N, head, n, f, inv_sigma);
+  float inv_sigma[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) inv_sigma[k] = (float)(1.0 / ms->sigma[k]);
+  const double inv_e = 1.0 / ms->sigma_e;
+  for (int f = 0; f < 16; ++f) X[(int64_t)i * 16 + f] = node_feature(hist, nodef, N, n, f, inv_sigma);
   for (int c = 0; c < 3; ++c) {
     const int64_t k = 3 * n + c;
-    const double b0 = x_base ? x_base[k] : fma(dt, v[k], 0.5 * dt * dt * a[k]);
-    Y[(int64_t)i * 3 + c] = (float)((du[k] - b0) / out_scale);
+    Y[(int64_t)i * 3 + c] = (float)((du[k] - base[k]) * inv_e);
   }
 }
 
-// Forward + backward of a chunk of kMlpChunk samples (one per thread) in FP32,
-// weight gradients reduced over the chunk in shared memory and added to grad.
-constexpr int kMlpChunk = 64;
-__global__ void __launch_bounds__(kMlpChunk) mlp_fwdbwd_kernel(int B, const float* __restrict__ X,
-                                                               const float* __restrict__ Y,
-                                                               const float* __restrict__ theta, float* grad,
-                                                               double* loss) {
-  extern __shared__ float sm[];
-  float* W = sm;                              // kMlpParams
-  float* xs = W + kMlpParams;                 // [chunk][16]
-  float* z1 = xs + kMlpChunk * 16;            // [chunk][64] pre-activation, later delta1
-  float* z2 = z1 + kMlpChunk * 64;            // [chunk][64] pre-activation, later delta2
-  float* h1 = z2 + kMlpChunk * 64;            // [chunk][64]
-  float* h2 = h1 + kMlpChunk * 64;            // [chunk][64]
-  float* d3 = h2 + kMlpChunk * 64;            // [chunk][3]
-  for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) W[i] = theta[i];
-  const int s = threadIdx.x;
-  const int64_t gi = (int64_t)blockIdx.x * kMlpChunk + s;
-  const bool ok = gi < B;
-  for (int f = 0; f < 16; ++f) xs[s * 16 + f] = ok ? X[gi * 16 + f] : 0.f;
+// Training on the tensor cores: forward and backward of the mean squared
+// error over the batch with BF16 operands and FP32 accumulation
+// (mma.m16n8k16), gradients added to grad (FP32), loss to *loss.  A CTA of
+// four warps takes chunks of 64 samples (16 per warp):
+//   forward   the inference chain (the C fragment of one layer, after bias,
+//             ReLU and BF16 rounding, is the A fragment of the next);
+//   backward  d3 = 2 (o - y) / B; dz2 = (d3 W3^T) * [z2 > 0];
+//             dz1 = (dz2 W2^T) * [z1 > 0] (each rounded to BF16 before its
+//             product, the ReLU masks taken from the forward fragments);
+//   gradients dW1 = X^T dz1, dW2 = h1^T dz2, dW3 = h2^T d3: products over the
+//             chunk's 64 samples (K), from the activations and errors staged
+//             in shared memory, accumulated in registers over the CTA's
+//             chunks; bias gradients are FP32 column sums.
+constexpr int kTcChunk = 64;
+constexpr int kTcThreads = 128;
+// dynamic shared memory layout (32-bit words)
+constexpr int kSmWf = 0;                          // forward fragments [kFrag]
+constexpr int kSmBias = kSmWf + kFrag;            // FP32 biases [136]
+constexpr int kSmW3t = kSmBias + 136;             // W3^T B fragments [8 n-tiles][32][2]
+constexpr int kSmW2t = kSmW3t + 8 * 32 * 2;       // W2^T B fragments [4 k-tiles][8 n-tiles][32][2]
+constexpr int kSmX = kSmW2t + 32 * 32 * 2;        // X [64][16] bf16
+constexpr int kSmH1 = kSmX + kTcChunk * 16 / 2;   // h1 [64][64] bf16
+constexpr int kSmH2 = kSmH1 + kTcChunk * 64 / 2;  // h2 [64][64] bf16
+constexpr int kSmZ1 = kSmH2 + kTcChunk * 64 / 2;  // dz1 [64][64] bf16
+constexpr int kSmZ2 = kSmZ1 + kTcChunk * 64 / 2;  // dz2 [64][64] bf16
+constexpr int kSmD3 = kSmZ2 + kTcChunk * 64 / 2;  // d3 [64][8] bf16
+constexpr int kSmDb = kSmD3 + kTcChunk * 8 / 2;   // bias gradients db1 [64], db2 [64], db3 [8] (FP32)
+constexpr int kSmLoss = kSmDb + 136;              // loss partial (FP32)
+constexpr int kSmWords = kSmLoss + 4;
+
+__device__ __forceinline__ uint32_t pack_raw(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
+
+// A fragment of act^T (m = unit, k = sample) from act [sample][S] (bf16).
+template <int S>
+__device__ __forceinline__ void frag_at(const uint16_t* act, int m0, int k0, int g, int t, uint32_t (&a)[4]) {
+  const uint16_t* c0 = act + m0 + g;
+  a[0] = pack_raw(c0[(k0 + 2 * t) * S], c0[(k0 + 2 * t + 1) * S]);
+  a[1] = pack_raw(c0[(k0 + 2 * t) * S + 8], c0[(k0 + 2 * t + 1) * S + 8]);
+  a[2] = pack_raw(c0[(k0 + 2 * t + 8) * S], c0[(k0 + 2 * t + 9) * S]);
+  a[3] = pack_raw(c0[(k0 + 2 * t + 8) * S + 8], c0[(k0 + 2 * t + 9) * S + 8]);
+}
+// B fragment of err (k = sample, n = unit) from err [sample][S] (bf16).
+template <int S>
+__device__ __forceinline__ void frag_b(const uint16_t* err, int k0, int n0, int g, int t, uint32_t& b0, uint32_t& b1) {
+  const uint16_t* c0 = err + n0 + g;
+  b0 = pack_raw(c0[(k0 + 2 * t) * S], c0[(k0 + 2 * t + 1) * S]);
+  b1 = pack_raw(c0[(k0 + 2 * t + 8) * S], c0[(k0 + 2 * t + 9) * S]);
+}
+// Column sums over the warp's 16 rows of a C fragment pair (rows g, g + 8),
+// added to acc[col] in shared memory by lanes 0..3.
+__device__ __forceinline__ void colsum_add(float v0, float v1, float* acc, int col, int lane) {
+#pragma unroll
+  for (int o = 4; o < 32; o <<= 1) {
+    v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+    v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+  }
+  if (lane < 4) {
+    atomicAdd(acc + col, v0);
+    atomicAdd(acc + col + 1, v1);
+  }
+}
+
+__global__ void __launch_bounds__(kTcThreads) mlp_train_tc_kernel(int B, const float* __restrict__ X,
+                                                                   const float* __restrict__ Y,
+                                                                   const float* __restrict__ theta, float* grad,
+                                                                   double* loss) {
+  extern __shared__ uint32_t smw[];
+  uint32_t* wf = smw + kSmWf;
+  float* bias = reinterpret_cast<float*>(smw + kSmBias);
+  uint32_t* w3t = smw + kSmW3t;
+  uint32_t* w2t = smw + kSmW2t;
+  uint16_t* xs = reinterpret_cast<uint16_t*>(smw + kSmX);
+  uint16_t* h1s = reinterpret_cast<uint16_t*>(smw + kSmH1);
+  uint16_t* h2s = reinterpret_cast<uint16_t*>(smw + kSmH2);
+  uint16_t* z1s = reinterpret_cast<uint16_t*>(smw + kSmZ1);
+  uint16_t* z2s = reinterpret_cast<uint16_t*>(smw + kSmZ2);
+  uint16_t* d3s = reinterpret_cast<uint16_t*>(smw + kSmD3);
+  float* db = reinterpret_cast<float*>(smw + kSmDb);
+  float* lsum = reinterpret_cast<float*>(smw + kSmLoss);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+  build_fwd_frags(theta, wf, bias, tid, kTcThreads);
+  // backward operands: W3^T (k = output padded to 16, n = hidden) and W2^T (k = j, n = i)
+  for (int q = tid; q < 8 * 32; q += kTcThreads) {
+    const int nt = q / 32, l = q % 32, gg = l / 4, tt = l % 4, n = 8 * nt + gg;
+    auto W3 = [&](int c) { return c < 3 ? theta[kW3 + n * 3 + c] : 0.f; };
+    w3t[2 * q] = pack_bf16(W3(2 * tt), W3(2 * tt + 1));
+    w3t[2 * q + 1] = 0u;
+  }
+  for (int q = tid; q < 32 * 32; q += kTcThreads) {
+    const int kt = q / 256, nt = (q / 32) % 8, l = q % 32, gg = l / 4, tt = l % 4;
+    const int n = 8 * nt + gg, k0 = 16 * kt;
+    auto W2 = [&](int k) { return theta[kW2 + n * 64 + k0 + k]; };
+    w2t[2 * q] = pack_bf16(W2(2 * tt), W2(2 * tt + 1));
+    w2t[2 * q + 1] = pack_bf16(W2(2 * tt + 8), W2(2 * tt + 9));
+  }
+  for (int q = tid; q < 140; q += kTcThreads) (q < 136 ? db[q] : lsum[q - 136]) = 0.f;
+  float acc2[8][4], acc1[2][4], acc3[4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc2[i][q] = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc1[0][q] = acc1[1][q] = acc3[q] = 0.f;
+  float lpart = 0.f;
+  const float inv2B = 2.f / (float)B;
   __syncthreads();
-  // forward
-  for (int j = 0; j < 64; ++j) {
-    float acc = W[kB1 + j];
-    for (int f = 0; f < 16; ++f) acc = fmaf(xs[s * 16 + f], W[kW1 + f * 64 + j], acc);
-    z1[s * 64 + j] = acc;
-    h1[s * 64 + j] = fmaxf(acc, 0.f);
-  }
-  for (int j = 0; j < 64; ++j) {
-    float acc = W[kB2 + j];
-    for (int k = 0; k < 64; ++k) acc = fmaf(h1[s * 64 + k], W[kW2 + k * 64 + j], acc);
-    z2[s * 64 + j] = acc;
-    h2[s * 64 + j] = fmaxf(acc, 0.f);
-  }
-  float sq = 0.f;
-  for (int c = 0; c < 3; ++c) {
-    float acc = W[kB3 + c];
-    for (int k = 0; k < 64; ++k) acc = fmaf(h2[s * 64 + k], W[kW3 + k * 3 + c], acc);
-    const float diff = ok ? acc - Y[gi * 3 + c] : 0.f;
-    sq = fmaf(diff, diff, sq);
-    d3[s * 3 + c] = 2.f * diff / (float)B;
-  }
-  // backward: delta2 (in z2), delta1 (in z1)
-  for (int k = 0; k < 64; ++k) {
-    float acc = 0.f;
-    for (int c = 0; c < 3; ++c) acc = fmaf(d3[s * 3 + c], W[kW3 + k * 3 + c], acc);
-    z2[s * 64 + k] = z2[s * 64 + k] > 0.f ? acc : 0.f;
-  }
-  for (int k = 0; k < 64; ++k) {
-    float acc = 0.f;
-    for (int j = 0; j < 64; ++j) acc = fmaf(z2[s * 64 + j], W[kW2 + k * 64 + j], acc);
-    z1[s * 64 + k] = z1[s * 64 + k] > 0.f ? acc : 0.f;
-  }
-  __syncthreads();
-  // weight gradients over the chunk: each thread owns parameters p = tid + k * chunk
-  for (int p = threadIdx.x; p < kMlpParams; p += blockDim.x) {
-    float acc = 0.f;
-    if (p < kB1) {
-      const int f = p / 64, j = p % 64;
-      for (int q = 0; q < kMlpChunk; ++q) acc = fmaf(xs[q * 16 + f], z1[q * 64 + j], acc);
-    } else if (p < kW2) {
-      const int j = p - kB1;
-      for (int q = 0; q < kMlpChunk; ++q) acc += z1[q * 64 + j];
-    } else if (p < kB2) {
-      const int k = (p - kW2) / 64, j = (p - kW2) % 64;
-      for (int q = 0; q < kMlpChunk; ++q) acc = fmaf(h1[q * 64 + k], z2[q * 64 + j], acc);
-    } else if (p < kW3) {
-      const int j = p - kB2;
-      for (int q = 0; q < kMlpChunk; ++q) acc += z2[q * 64 + j];
-    } else if (p < kB3) {
-      const int k = (p - kW3) / 3, c = (p - kW3) % 3;
-      for (int q = 0; q < kMlpChunk; ++q) acc = fmaf(h2[q * 64 + k], d3[q * 3 + c], acc);
-    } else {
-      const int c = p - kB3;
-      for (int q = 0; q < kMlpChunk; ++q) acc += d3[q * 3 + c];
+  const int n_chunks = (B + kTcChunk - 1) / kTcChunk;
+  for (int ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+    const int base = ch * kTcChunk + 16 * warp;  // first sample of this warp
+    const int r0 = 16 * warp;                    // its first row in the staging arrays
+    if (lane < 16) {
+      const int64_t gi = base + lane;
+#pragma unroll
+      for (int f = 0; f < 16; f += 2) {
+        const float a = gi < B ? X[gi * 16 + f] : 0.f, b = gi < B ? X[gi * 16 + f + 1] : 0.f;
+        *reinterpret_cast<uint32_t*>(xs + (r0 + lane) * 16 + f) = pack_bf16(a, b);
+      }
     }
-    atomicAdd(grad + p, acc);
+    __syncwarp();
+    uint32_t A[4];
+    {
+      const uint16_t* x0 = xs + (r0 + g) * 16;
+      const uint16_t* x1 = xs + (r0 + g + 8) * 16;
+      A[0] = *reinterpret_cast<const uint32_t*>(x0 + 2 * t);
+      A[1] = *reinterpret_cast<const uint32_t*>(x1 + 2 * t);
+      A[2] = *reinterpret_cast<const uint32_t*>(x0 + 2 * t + 8);
+      A[3] = *reinterpret_cast<const uint32_t*>(x1 + 2 * t + 8);
+    }
+    // ---- forward ----
+    uint32_t mask1 = 0u, mask2 = 0u;
+    uint32_t A2[4][4];
+    {
+      float C1[8][4];
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        const float b0 = bias[8 * nt + 2 * t], b1 = bias[8 * nt + 2 * t + 1];
+        C1[nt][0] = b0;
+        C1[nt][1] = b1;
+        C1[nt][2] = b0;
+        C1[nt][3] = b1;
+        mma_bf16(C1[nt], A, wf[kF1 + 2 * (nt * 32 + lane)], wf[kF1 + 2 * (nt * 32 + lane) + 1]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) mask1 |= (C1[nt][q] > 0.f ? 1u : 0u) << (4 * nt + q);
+        const uint32_t lo = pack_bf16(fmaxf(C1[nt][0], 0.f), fmaxf(C1[nt][1], 0.f));
+        const uint32_t hi = pack_bf16(fmaxf(C1[nt][2], 0.f), fmaxf(C1[nt][3], 0.f));
+        *reinterpret_cast<uint32_t*>(h1s + (r0 + g) * 64 + 8 * nt + 2 * t) = lo;
+        *reinterpret_cast<uint32_t*>(h1s + (r0 + g + 8) * 64 + 8 * nt + 2 * t) = hi;
+        A2[nt >> 1][(nt & 1) * 2] = lo;
+        A2[nt >> 1][(nt & 1) * 2 + 1] = hi;
+      }
+    }
+    uint32_t A3[4][4];
+    {
+      float C2[8][4];
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        const float b0 = bias[64 + 8 * nt + 2 * t], b1 = bias[64 + 8 * nt + 2 * t + 1];
+        C2[nt][0] = b0;
+        C2[nt][1] = b1;
+        C2[nt][2] = b0;
+        C2[nt][3] = b1;
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) {
+          const int fi = kF2 + 2 * ((kt * 8 + nt) * 32 + lane);
+          mma_bf16(C2[nt], A2[kt], wf[fi], wf[fi + 1]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) mask2 |= (C2[nt][q] > 0.f ? 1u : 0u) << (4 * nt + q);
+        const uint32_t lo = pack_bf16(fmaxf(C2[nt][0], 0.f), fmaxf(C2[nt][1], 0.f));
+        const uint32_t hi = pack_bf16(fmaxf(C2[nt][2], 0.f), fmaxf(C2[nt][3], 0.f));
+        *reinterpret_cast<uint32_t*>(h2s + (r0 + g) * 64 + 8 * nt + 2 * t) = lo;
+        *reinterpret_cast<uint32_t*>(h2s + (r0 + g + 8) * 64 + 8 * nt + 2 * t) = hi;
+        A3[nt >> 1][(nt & 1) * 2] = lo;
+        A3[nt >> 1][(nt & 1) * 2 + 1] = hi;
+      }
+    }
+    float C3[4];
+    {
+      const float b0 = bias[128 + 2 * t], b1 = bias[128 + 2 * t + 1];
+      C3[0] = b0;
+      C3[1] = b1;
+      C3[2] = b0;
+      C3[3] = b1;
+#pragma unroll
+      for (int kt = 0; kt < 4; ++kt)
+        mma_bf16(C3, A3[kt], wf[kF3 + 2 * (kt * 32 + lane)], wf[kF3 + 2 * (kt * 32 + lane) + 1]);
+    }
+    // ---- output error d3 = 2 (o - y) / B (rows g, g + 8; columns 2t, 2t + 1) ----
+    float d3[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int row = g + 8 * (q >> 1), col = 2 * t + (q & 1);
+      const int64_t gi = base + row;
+      float e = 0.f;
+      if (col < 3 && gi < B) {
+        const float diff = C3[q] - Y[gi * 3 + col];
+        lpart = fmaf(diff, diff, lpart);
+        e = diff * inv2B;
+      }
+      d3[q] = e;
+    }
+    {
+      const uint32_t lo = pack_bf16(d3[0], d3[1]), hi = pack_bf16(d3[2], d3[3]);
+      *reinterpret_cast<uint32_t*>(d3s + (r0 + g) * 8 + 2 * t) = lo;
+      *reinterpret_cast<uint32_t*>(d3s + (r0 + g + 8) * 8 + 2 * t) = hi;
+      colsum_add(d3[0] + d3[2], d3[1] + d3[3], db + 128, 2 * t, lane);
+      // ---- dz2 = (d3 W3^T) * [z2 > 0] ----
+      const uint32_t Ad[4] = {lo, hi, 0u, 0u};
+      uint32_t A4[4][4];
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        float C[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_bf16(C, Ad, w3t[2 * (nt * 32 + lane)], 0u);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) C[q] = ((mask2 >> (4 * nt + q)) & 1u) ? C[q] : 0.f;
+        colsum_add(C[0] + C[2], C[1] + C[3], db + 64, 8 * nt + 2 * t, lane);
+        const uint32_t zlo = pack_bf16(C[0], C[1]), zhi = pack_bf16(C[2], C[3]);
+        *reinterpret_cast<uint32_t*>(z2s + (r0 + g) * 64 + 8 * nt + 2 * t) = zlo;
+        *reinterpret_cast<uint32_t*>(z2s + (r0 + g + 8) * 64 + 8 * nt + 2 * t) = zhi;
+        A4[nt >> 1][(nt & 1) * 2] = zlo;
+        A4[nt >> 1][(nt & 1) * 2 + 1] = zhi;
+      }
+      // ---- dz1 = (dz2 W2^T) * [z1 > 0] ----
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        float C[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) {
+          const int fi = 2 * ((kt * 8 + nt) * 32 + lane);
+          mma_bf16(C, A4[kt], w2t[fi], w2t[fi + 1]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) C[q] = ((mask1 >> (4 * nt + q)) & 1u) ? C[q] : 0.f;
+        colsum_add(C[0] + C[2], C[1] + C[3], db, 8 * nt + 2 * t, lane);
+        *reinterpret_cast<uint32_t*>(z1s + (r0 + g) * 64 + 8 * nt + 2 * t) = pack_bf16(C[0], C[1]);
+        *reinterpret_cast<uint32_t*>(z1s + (r0 + g + 8) * 64 + 8 * nt + 2 * t) = pack_bf16(C[2], C[3]);
+      }
+    }
+    __syncthreads();
+    // ---- weight gradients over the chunk's 64 samples ----
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) {
+      const int k0 = 16 * kt;
+      uint32_t a[4], b0, b1;
+      frag_at<64>(h1s, 16 * warp, k0, g, t, a);  // dW2 rows 16w.. (hidden in)
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        frag_b<64>(z2s, k0, 8 * nt, g, t, b0, b1);
+        mma_bf16(acc2[nt], a, b0, b1);
+      }
+      frag_at<16>(xs, 0, k0, g, t, a);  // dW1 (16 features), columns 16w..16w+15
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        frag_b<64>(z1s, k0, 8 * (2 * warp + q), g, t, b0, b1);
+        mma_bf16(acc1[q], a, b0, b1);
+      }
+      frag_at<64>(h2s, 16 * warp, k0, g, t, a);  // dW3 rows 16w.. (hidden)
+      frag_b<8>(d3s, k0, 0, g, t, b0, b1);
+      mma_bf16(acc3, a, b0, b1);
+    }
+    __syncthreads();
   }
-  // loss (mean square over the batch)
-  __shared__ double shl[32];
-  double l = block_sum((double)sq, shl);
-  if (threadIdx.x == 0) atomicAdd(loss, l / (double)B);
+  // ---- add the CTA's gradients and loss ----
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int rr = g + 8 * (q >> 1), cc = 2 * t + (q & 1);
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) atomicAdd(grad + kW2 + (16 * warp + rr) * 64 + 8 * nt + cc, acc2[nt][q]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) atomicAdd(grad + kW1 + rr * 64 + 8 * (2 * warp + h) + cc, acc1[h][q]);
+    if (cc < 3) atomicAdd(grad + kW3 + (16 * warp + rr) * 3 + cc, acc3[q]);
+  }
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) lpart += __shfl_xor_sync(0xffffffffu, lpart, o);
+  if (lane == 0) atomicAdd(lsum, lpart);
+  __syncthreads();
+  for (int q = tid; q < 131; q += kTcThreads) {
+    const int p = q < 64 ? kB1 + q : (q < 128 ? kB2 + q - 64 : kB3 + q - 128);
+    atomicAdd(grad + p, db[q]);
+  }
+  if (tid == 0) atomicAdd(loss, (double)lsum[0] / (double)B);
 }
 
 __global__ void mlp_adam_kernel(float* theta, float* grad, float* m, float* v, int t, float lr) {
@@ -414,13 +626,23 @@ __global__ void mlp_adam_kernel(float* theta, float* grad, float* m, float* v, i
   grad[i] = 0.f;
 }
 
-__global__ void hist_push_kernel(int64_t N, const double* __restrict__ du, float* hist, int slot,
-                                 const CgScalars* cg, const StepState* ss) {
+// Push a converged increment into the difference history: D_0' = du and
+// D_k' = D_{k-1}' - D_{k-1} (the backward differences of the last four
+// increments; before four pushes the missing increments count as zero).
+__global__ void hist_push_kernel(int64_t N, const double* __restrict__ du, double* hist, const CgScalars* cg,
+                                 const StepState* ss) {
   if (ss != nullptr && !((volatile const StepState*)ss)->commit) return;
   const bool zero = cg->zero_rhs != 0;
-  float* h = hist + (int64_t)slot * 3 * N;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * N; i += (int64_t)gridDim.x * blockDim.x)
-    h[i] = zero ? 0.f : (float)du[i];
+  const int64_t n3 = 3 * N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    const double d0 = zero ? 0.0 : du[i];
+    const double o0 = hist[i], o1 = hist[n3 + i], o2 = hist[2 * n3 + i];
+    const double d1 = d0 - o0, d2 = d1 - o1, d3 = d2 - o2;
+    hist[i] = d0;
+    hist[n3 + i] = d1;
+    hist[2 * n3 + i] = d2;
+    hist[3 * n3 + i] = d3;
+  }
 }
 
 // ------------------------------------------------------------------------------
@@ -435,48 +657,52 @@ void launch_node_features(const ModelView& m, int n_mat, int32_t* node_mat, floa
   node_material_kernel<<<(unsigned)((m.E + 255) / 256), 256, 0, s>>>(m, node_mat);
   node_features_kernel<<<(unsigned)((m.N + 255) / 256), 256, 0, s>>>(m.N, node_mat, m.mat, n_mat, nodef);
 }
-void launch_mlp_sigma(int64_t N, const float* hist, int head, double* partials, MlpScalars* ms, cudaStream_t s) {
-  mlp_sigma_kernel<<<node_blocks(3 * N), kNodeThreads, 0, s>>>(N, hist, head, partials, ms);
+void launch_mlp_sigma(int64_t N, const double* hist, double* partials, MlpScalars* ms, cudaStream_t s) {
+  // four sums per CTA: the partials buffer holds 4 x (kMaxNodeBlocks / 2)
+  int g = node_blocks(3 * N);
+  if (g > kMaxNodeBlocks / 2) g = kMaxNodeBlocks / 2;
+  mlp_sigma_kernel<<<g, kNodeThreads, 0, s>>>(N, hist, partials, ms);
 }
-void launch_mlp_infer(int64_t N, const float* hist, int head, const float* nodef, const double* v, const double* a,
-                      double dt, const uint32_t* packed, const MlpScalars* ms, double* x, const float* xin,
-                      float* yout, cudaStream_t s, const double* x_base) {
+void launch_mlp_infer(int64_t N, const double* hist, const float* nodef, const uint32_t* packed, const MlpScalars* ms,
+                      double* x, const float* xin, float* yout, cudaStream_t s, const double* x_base) {
   const int64_t tiles = (N + 15) / 16;
   int64_t blocks = (tiles + 3) / 4;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
-  mlp_infer_kernel<<<(unsigned)blocks, 128, 0, s>>>(N, hist, head, nodef, v, a, dt, packed, ms, x, xin, yout, x_base);
+  mlp_infer_kernel<<<(unsigned)blocks, 128, 0, s>>>(N, hist, nodef, packed, ms, x, xin, yout, x_base);
 }
-void launch_mlp_sample(int64_t N, int B, uint32_t seed, int step, int iter, const float* hist, int head,
-                       const float* nodef, const double* du, const double* v, const double* a, double dt,
-                       const MlpScalars* ms, float* X, float* Y, cudaStream_t s, const double* x_base) {
-  mlp_sample_kernel<<<(B + 255) / 256, 256, 0, s>>>(N, B, seed, step, iter, hist, head, nodef, du, v, a, dt, ms, X, Y,
-                                                    x_base);
+void launch_mlp_sample(int64_t N, int B, uint32_t seed, int step, int iter, const double* hist, const float* nodef,
+                       const double* du, const double* base, const MlpScalars* ms, float* X, float* Y,
+                       cudaStream_t s) {
+  mlp_sample_kernel<<<(B + 255) / 256, 256, 0, s>>>(N, B, seed, step, iter, hist, nodef, du, base, ms, X, Y);
 }
-size_t mlp_fwdbwd_smem() { return sizeof(float) * (kMlpParams + kMlpChunk * (16 + 4 * 64 + 3)); }
 int launch_mlp_fwdbwd(int B, const float* X, const float* Y, const float* theta, float* grad, double* loss,
                       cudaStream_t s) {
   static bool attr = false;
-  const size_t smem = mlp_fwdbwd_smem();
+  const int smem = kSmWords * 4;
   if (!attr) {
-    if (cudaFuncSetAttribute(mlp_fwdbwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(mlp_train_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
       return 1;
     attr = true;
   }
-  mlp_fwdbwd_kernel<<<(B + kMlpChunk - 1) / kMlpChunk, kMlpChunk, smem, s>>>(B, X, Y, theta, grad, loss);
+  const int chunks = (B + kTcChunk - 1) / kTcChunk;
+  const int grid = chunks < 152 * 2 ? chunks : 152 * 2;
+  mlp_train_tc_kernel<<<grid, kTcThreads, smem, s>>>(B, X, Y, theta, grad, loss);
   return 0;
 }
 void launch_mlp_adam(float* theta, float* grad, float* m, float* v, int t, float lr, cudaStream_t s) {
   mlp_adam_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(theta, grad, m, v, t, lr);
 }
-void launch_hist_push(int64_t N, const double* du, float* hist, int slot, const CgScalars* cg, cudaStream_t s,
+void launch_hist_push(int64_t N, const double* du, double* hist, const CgScalars* cg, cudaStream_t s,
                       const StepState* ss) {
-  hist_push_kernel<<<node_blocks(3 * N), kNodeThreads, 0, s>>>(N, du, hist, slot, cg, ss);
+  hist_push_kernel<<<node_blocks(3 * N), kNodeThreads, 0, s>>>(N, du, hist, cg, ss);
 }
-void launch_mlp_inputs(int n, const int32_t* nodes, int64_t N, const float* hist, int head, const float* nodef,
-                       const MlpScalars* ms, const double* v, const double* a, double dt, const double* x_base, float* X,
-                       double* base, cudaStream_t s) {
-  mlp_inputs_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, nodes, N, hist, head, nodef, ms, v, a, dt, x_base, X, base);
+void launch_predictor(int64_t N, const double* v, const double* a, double dt, double* x, cudaStream_t s) {
+  predictor_kernel<<<node_blocks(3 * N), kNodeThreads, 0, s>>>(3 * N, v, a, dt, x);
+}
+void launch_mlp_inputs(int n, const int32_t* nodes, int64_t N, const double* hist, const float* nodef,
+                       const MlpScalars* ms, const double* base, float* X, double* base_out, cudaStream_t s) {
+  mlp_inputs_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, nodes, N, hist, nodef, ms, base, X, base_out);
 }
 int mlp_packed_words() { return kPacked; }
 

@@ -72,23 +72,27 @@ SIGNATURES = {
     "gsw_set_solver": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(SolverOpts)]),
     "gsw_reset": (C.c_int, [C.c_void_p, C.c_int32]),
     "gsw_step": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
-    "gsw_run": (C.c_int, [C.c_void_p, _ip, C.c_int32]),
+    "gsw_run": (C.c_int, [C.c_void_p, _ip, C.c_int32, C.c_int32]),
     "gsw_batch_create": (C.c_int, [C.c_void_p, _ip, C.c_int32, _ip]),
     "gsw_batch_step": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "gsw_batch_destroy": (C.c_int, [C.c_void_p, C.c_int32]),
     "gsw_batch_launches": (C.c_int, [C.c_void_p, C.c_int32, _lp]),
-    "gsw_read_waveforms": (C.c_int, [C.c_void_p, C.c_int32, _dp]),
+    "gsw_read_waveforms": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, _dp]),
     "gsw_read_waveform_steps": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, _dp]),
     "gsw_timing": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, _dp, _lp]),
-    "gsw_stats_get": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Stats)]),
+    "gsw_stats_get": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(Stats)]),
+    "gsw_checkpoint": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_size_t)]),
+    "gsw_restore": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t]),
     "gsw_get_state": (C.c_int, [C.c_void_p, C.c_int32, _dp, _dp, _dp, _lp]),
     "gsw_set_state": (C.c_int, [C.c_void_p, C.c_int32, _dp, _dp, _dp, C.c_int64]),
     "gsw_apply": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     "gsw_read_preconditioner": (C.c_int, [C.c_void_p, C.c_int32, _dp]),
     "gsw_read_receivers": (C.c_int, [C.c_void_p, C.c_int32, _ip, _dp]),
-    "gsw_misfit": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, _dp, _dp, C.c_int32, C.c_int32, C.c_double,
-                             _dp, _dp]),
+    "gsw_misfit": (C.c_int, [C.c_void_p, C.c_int32, _dp, C.c_int32, C.c_int32, C.c_double, _dp, _dp]),
+    "gsw_misfit_green": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, _dp, _dp, C.c_int32, C.c_int32, C.c_double,
+                                   _dp, _dp]),
     "gsw_set_learning": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(LearnOpts)]),
+    "gsw_mlp_train": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(LearnOpts)]),
     "gsw_mlp_params": (C.c_int, [C.c_void_p, C.c_int32, _dp, _dp]),
     "gsw_mlp_forward": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     "gsw_mlp_grad": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, _dp, _dp]),
@@ -196,17 +200,24 @@ class Context:
                                               C.byref(mid)))
         return Model(self, mid.value, xyz.shape[0], rc.shape[0])
 
-    def misfit(self, G, obs, stride, n_shifts, tau=1e-10):
-        """(ERR, c [3, n_shifts]) of Eq. (2) for Green's functions G and observations obs."""
+    def misfit_green(self, G, obs, stride, n_shifts, tau=1e-10):
+        """(ERR, c [3, n_shifts]) of Eq. (2) for Green's functions G [n_rec, 3, 3, n_t] given on the host
+        and observations obs [n_rec, 3, n_t]."""
         G, pG = _d(G)
         obs, pO = _d(obs)
         n_rec, n_t = obs.shape[0], obs.shape[2]
         assert G.shape == (n_rec, 3, 3, n_t)
         err = C.c_double()
         c = np.zeros((3, n_shifts))
-        self._check(self.lib.gsw_misfit(self.h, n_rec, n_t, pG, pO, stride, n_shifts, tau, C.byref(err),
-                                        c.ctypes.data_as(_dp)))
+        self._check(self.lib.gsw_misfit_green(self.h, n_rec, n_t, pG, pO, stride, n_shifts, tau, C.byref(err),
+                                              c.ctypes.data_as(_dp)))
         return err.value, c
+
+    def run(self, models, dirs_mask=0):
+        """Run analyses from rest to the end, batched: each model's own analysis (dirs_mask 0) or, for
+        every model, the analysis of each input direction in dirs_mask (bits x1, x2, x3)."""
+        ids = np.array([m.id for m in models], dtype=np.int32)
+        self._check(self.lib.gsw_run(self.h, ids.ctypes.data_as(_ip), len(ids), int(dirs_mask)))
 
 
     def misfit_noalloc(self, G_dev, obs_dev, stride, n_shifts, err_dev, c_dev=None, tau=1e-10):
@@ -302,19 +313,43 @@ class Model:
     def step(self, n=1):
         self._c(self.ctx.lib.gsw_step(self.ctx.h, self.id, int(n)))
 
-    def run(self):
+    def run(self, dirs_mask=0):
         ids = np.array([self.id], dtype=np.int32)
-        self._c(self.ctx.lib.gsw_run(self.ctx.h, ids.ctypes.data_as(_ip), 1))
+        self._c(self.ctx.lib.gsw_run(self.ctx.h, ids.ctypes.data_as(_ip), 1, int(dirs_mask)))
 
-    def waveforms(self):
+    def waveforms(self, direction=-1):
+        """Receiver history [n_rec, 3, n_steps] of the model's own analysis (-1) or of the analysis of input
+        direction 0..2 run by ``run(dirs_mask)``."""
         out = np.zeros((self.n_rec, 3, self.n_steps))
-        self._c(self.ctx.lib.gsw_read_waveforms(self.ctx.h, self.id, out.ctypes.data_as(_dp)))
+        self._c(self.ctx.lib.gsw_read_waveforms(self.ctx.h, self.id, int(direction), out.ctypes.data_as(_dp)))
         return out
 
-    def read_waveforms_into(self, out):
+    def read_waveforms_into(self, out, direction=-1):
         """Read the receiver history into a caller-owned float64 host array."""
-        self._c(self.ctx.lib.gsw_read_waveforms(self.ctx.h, self.id, out.ctypes.data_as(_dp)))
+        self._c(self.ctx.lib.gsw_read_waveforms(self.ctx.h, self.id, int(direction), out.ctypes.data_as(_dp)))
         return out
+
+    def misfit(self, obs, stride, n_shifts, tau=1e-10):
+        """(ERR, c [3, n_shifts]) of Eq. (2) against observations obs [n_rec, 3, n_steps], from the model's
+        three input-direction analyses (``run(dirs_mask=7)``), computed on the device."""
+        obs, pO = _d(obs)
+        err = C.c_double()
+        c = np.zeros((3, n_shifts))
+        self._c(self.ctx.lib.gsw_misfit(self.ctx.h, self.id, pO, int(stride), int(n_shifts), float(tau),
+                                        C.byref(err), c.ctypes.data_as(_dp)))
+        return err.value, c
+
+    def checkpoint(self):
+        """Full checkpoint (state, receiver history, increment history, learned-guess state) as bytes."""
+        n = C.c_size_t(0)
+        self._c(self.ctx.lib.gsw_checkpoint(self.ctx.h, self.id, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._c(self.ctx.lib.gsw_checkpoint(self.ctx.h, self.id, buf, C.byref(n)))
+        return buf.raw
+
+    def restore(self, data):
+        buf = C.create_string_buffer(bytes(data), len(data))
+        self._c(self.ctx.lib.gsw_restore(self.ctx.h, self.id, buf, len(data)))
 
     def read_steps_into(self, step0, out):
         """Receiver velocities of steps step0 .. step0 + out.shape[2] - 1 into a host array."""
@@ -333,9 +368,9 @@ class Model:
         self._c(self.ctx.lib.gsw_timing(self.ctx.h, self.id, flag, ms.ctypes.data_as(_dp), n.ctypes.data_as(_lp)))
         return {"fp64": (float(ms[0]), int(n[0])), "inner": (float(ms[1]), int(n[1]))}
 
-    def stats(self):
+    def stats(self, direction=-1):
         s = Stats()
-        self._c(self.ctx.lib.gsw_stats_get(self.ctx.h, self.id, C.byref(s)))
+        self._c(self.ctx.lib.gsw_stats_get(self.ctx.h, self.id, int(direction), C.byref(s)))
         return {k: getattr(s, k) for k, _ in Stats._fields_}
 
     def get_state(self):
@@ -376,6 +411,11 @@ class Model:
     def set_learning(self, enable=True, train_steps=500, batch=16384, iters_per_step=2, lr=1e-3, seed=1):
         o = LearnOpts(int(enable), int(train_steps), int(batch), int(iters_per_step), float(lr), int(seed))
         self._c(self.ctx.lib.gsw_set_learning(self.ctx.h, self.id, C.byref(o)))
+
+    def mlp_train(self, n_train_steps, batch=16384, iters_per_step=2, lr=1e-3, seed=1):
+        """Train the learned guess on the next n_train_steps steps (advancing them); later steps apply it."""
+        o = LearnOpts(1, 0, int(batch), int(iters_per_step), float(lr), int(seed))
+        self._c(self.ctx.lib.gsw_mlp_train(self.ctx.h, self.id, int(n_train_steps), C.byref(o)))
 
     def mlp_params(self, set_to=None):
         out = np.zeros(5443)

@@ -1,0 +1,175 @@
+"""The C ABI's analysis-level entry points against the oracle and each other.
+
+* gsw_run with a direction mask: one uploaded model serves its three
+  input-direction analyses (shared mesh and element data, own state); each
+  matches the oracle and a separately uploaded single-direction model.
+* gsw_checkpoint / gsw_restore: a run resumed from a checkpoint continues
+  exactly as the uninterrupted run, including the extrapolated guess's
+  increment history and the learned guess's network and optimiser state.
+* gsw_mlp_train: training on the next steps, then the learned guess applies.
+* Failures injected on the host: a non-finite state is rejected at the
+  boundary; a network whose output overflows falls back to the predictor.
+"""
+import numpy as np
+import pytest
+
+from oracle import newmark
+from synth import configs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_17754_gb300 import build, gsw
+
+    build.build()
+    c = gsw.Context(0)
+    yield c
+    c.close()
+
+
+def _relerr(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _upload(ctx, cfg, n_steps=None):
+    m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
+    m.set_time(cfg["dt"], n_steps or cfg["n_steps"], cfg["band"])
+    return m
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_direction_mask_runs_three_analyses_of_one_model(ctx, prec):
+    from paper_2404_17754_gb300 import gsw
+
+    cfg = configs.small_box(nx=4, ny=3, n_steps=25, seed=4)
+    tol = 1e-12 if prec == 0 else 1e-8
+    m = _upload(ctx, cfg)
+    m.set_solver(tol=tol, precision=prec, inner_iters=12, guess_order=2)
+    with pytest.raises(gsw.GswError) as ei:
+        m.run(dirs_mask=7)  # no inputs yet
+    assert ei.value.status == gsw.E_STATE
+    for j in range(3):
+        m.set_input(j, cfg["p"] * (1.0 + 0.5 * j))
+    with pytest.raises(gsw.GswError):
+        m.waveforms(1)  # not run yet
+    m.run(dirs_mask=7)
+    for j in range(3):
+        w = m.waveforms(j)
+        ref = newmark.analysis(dict(cfg, p=cfg["p"] * (1.0 + 0.5 * j), dir=j), tol=tol)["wave"]
+        assert _relerr(w, ref) <= (1e-9 if prec == 0 else 1e-6), j
+        assert m.stats(j)["steps_done"] == cfg["n_steps"] and m.stats(j)["relres_last"] <= tol
+        # the same analysis on a model of its own
+        s = _upload(ctx, cfg)
+        s.set_input(j, cfg["p"] * (1.0 + 0.5 * j))
+        s.set_solver(tol=tol, precision=prec, inner_iters=12, guess_order=2)
+        s.run()
+        assert _relerr(s.waveforms(), w) <= (1e-11 if prec == 0 else 1e-7)
+        s.free()
+    # a subset of the directions, again (instances are reused and reset)
+    m.run(dirs_mask=2)
+    assert _relerr(m.waveforms(1), newmark.analysis(dict(cfg, p=1.5 * cfg["p"], dir=1), tol=tol)["wave"]) <= (
+        1e-9 if prec == 0 else 1e-6)
+    m.free()
+
+
+def test_checkpoint_restore_resumes_extrapolated_guess_exactly(ctx):
+    cfg = configs.small_box(nx=4, ny=3, n_steps=30, seed=5)
+    m = _upload(ctx, cfg)
+    m.set_input(cfg["dir"], cfg["p"])
+    m.set_solver(tol=1e-12, precision=0, guess_order=4)
+    m.step(12)
+    ck = m.checkpoint()
+    m.step(10)
+    w_ref, s_ref = m.waveforms(), m.stats()
+    m.reset()  # lose the state and the increment history
+    m.step(3)
+    m.restore(ck)
+    assert m.stats()["steps_done"] == 12
+    m.step(10)
+    s = m.stats()
+    assert s["cg_iters_total"] == s_ref["cg_iters_total"]  # the quartic guess resumed with its history
+    assert _relerr(m.waveforms(), w_ref) <= 1e-12
+    # a checkpoint of another set-up is refused and leaves the model as it was
+    m2 = _upload(ctx, configs.small_box(nx=3, ny=2, n_steps=30))
+    m2.set_input(0, cfg["p"])
+    m2.set_solver(tol=1e-12, precision=0, guess_order=4)
+    from paper_2404_17754_gb300 import gsw
+
+    with pytest.raises(gsw.GswError) as ei:
+        m2.restore(ck)
+    assert ei.value.status == gsw.E_INVALID
+    m2.free()
+    m.free()
+
+
+def test_checkpoint_restore_keeps_the_learned_guess(ctx):
+    cfg = configs.small_box(nx=4, ny=3, n_steps=40, seed=6)
+    m = _upload(ctx, cfg)
+    m.set_input(cfg["dir"], cfg["p"])
+    m.set_solver(tol=1e-8, precision=1, inner_iters=12)
+    m.mlp_train(12, batch=512, iters_per_step=3, lr=1e-3, seed=3)
+    m.step(4)
+    ck = m.checkpoint()
+    th = m.mlp_params()
+    st = m.mlp_state()
+    m.step(8)
+    w_ref = m.waveforms()
+    m.mlp_train(6, batch=512, iters_per_step=3, lr=1e-3, seed=3)  # changes the network
+    assert np.abs(m.mlp_params() - th).max() > 0
+    m.restore(ck)
+    assert np.array_equal(m.mlp_params(), th)
+    st2 = m.mlp_state()
+    assert st2["learned_steps"] == st["learned_steps"] and st2["active"] == st["active"]
+    m.step(8)
+    assert _relerr(m.waveforms(), w_ref) <= 1e-7
+    m.free()
+
+
+def test_mlp_train_then_apply(ctx):
+    from paper_2404_17754_gb300 import gsw
+
+    cfg = configs.config1(n_steps=80)
+    m = _upload(ctx, cfg)
+    m.set_input(cfg["dir"], cfg["p"])
+    m.set_solver(tol=1e-8, precision=1, inner_iters=15)
+    with pytest.raises(gsw.GswError) as ei:
+        m.mlp_train(200)
+    assert ei.value.status == gsw.E_INVALID
+    m.mlp_train(40, batch=4096, iters_per_step=4, lr=2e-3, seed=5)
+    assert m.stats()["steps_done"] == 40 and m.mlp_loss() > 0
+    m.step(40)
+    assert m.mlp_state()["learned_steps"] >= 5
+    assert m.stats()["relres_last"] <= 1e-8
+    ref = newmark.analysis(cfg, tol=1e-8)["wave"]
+    assert _relerr(m.waveforms(), ref) <= 1e-6
+    m.free()
+
+
+def test_host_injected_failures(ctx):
+    from paper_2404_17754_gb300 import gsw
+
+    cfg = configs.small_box(nx=3, ny=2, n_steps=30, seed=8)
+    m = _upload(ctx, cfg)
+    m.set_input(cfg["dir"], cfg["p"])
+    m.set_solver(tol=1e-8, precision=1, inner_iters=12)
+    m.step(2)
+    u, v, a, k = m.get_state()
+    u[3, 1] = np.nan
+    with pytest.raises(gsw.GswError) as ei:
+        m.set_state(u, v, a, k)
+    assert ei.value.status == gsw.E_INVALID
+    m.step(2)  # the model is untouched and keeps stepping
+    # a network whose output overflows to infinity: every guess falls back to the predictor
+    m.reset()
+    m.mlp_train(8, batch=256, iters_per_step=1, lr=1e-3, seed=1)
+    m.mlp_params(np.full(5443, 1e30))
+    m.step(10)
+    assert m.stats()["relres_last"] <= 1e-8
+    assert _relerr(m.waveforms(), newmark.analysis(cfg, tol=1e-8)["wave"]) <= 1e-6
+    m.free()

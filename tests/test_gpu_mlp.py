@@ -2,8 +2,9 @@
 
 * tensor-core (BF16 operands, FP32 accumulation) inference vs the oracle's
   bf16-rounded forward pass;
-* FP32 training gradients vs the oracle's FP64 analytic backprop (itself
-  pinned by finite differences);
+* tensor-core training gradients (BF16 operands, FP32 accumulation) vs the
+  oracle's gradient with the same rounding points, and vs its exact FP64
+  backprop (pinned by finite differences);
 * a run that trains on its first steps and then applies the guess converges
   every step to the same 1e-8 relative residual and reproduces the plain run;
   the guess quality (initial residual) and CG iterations are compared.
@@ -66,9 +67,14 @@ def test_training_gradient_matches_oracle(model):
     X = rng.standard_normal((4099, 16)).astype(np.float32)
     Y = rng.standard_normal((4099, 3)).astype(np.float32)
     loss, g = model.mlp_grad(X, Y)
-    ref_loss, ref_g = mlp.loss_grad(th, X.astype(np.float64), Y.astype(np.float64))
-    assert abs(loss - ref_loss) <= 1e-5 * ref_loss
-    assert np.linalg.norm(g - ref_g) <= 1e-4 * np.linalg.norm(ref_g)
+    # the tensor-core kernel's arithmetic: BF16 operands, FP32 accumulation
+    ref_loss, ref_g = mlp.loss_grad_bf16(th, X.astype(np.float64), Y.astype(np.float64))
+    assert abs(loss - ref_loss) <= 1e-4 * ref_loss
+    assert np.linalg.norm(g - ref_g) <= 5e-3 * np.linalg.norm(ref_g)
+    # and the exact FP64 backprop (itself pinned by finite differences)
+    ex_loss, ex_g = mlp.loss_grad(th, X.astype(np.float64), Y.astype(np.float64))
+    assert abs(loss - ex_loss) <= 2e-2 * ex_loss
+    assert np.linalg.norm(g - ex_g) <= 3e-2 * np.linalg.norm(ex_g)
 
 
 def test_learned_guess_run_converges_and_matches_plain(ctx):
@@ -117,9 +123,8 @@ def test_learned_guess_data_path_matches_oracle(ctx, order):
     """Features, layer features, sampled training nodes, targets, base guess and output
     scale of the GPU's learned guess against the oracle's data path, both sides solving
     the same small box to relative residual 1e-11.  order 0: the network corrects the
-    Newmark predictor (output scale sigma); order 2: it corrects the quadratic
-    extrapolation of the last three increments (output scale: RMS of the previous
-    step's correction)."""
+    Newmark predictor; order 2: the quadratic extrapolation of the last three
+    increments (output scale in both: the RMS of the previous step's correction)."""
     from oracle import fem
     from paper_2404_17754_gb300 import gsw
 
@@ -153,7 +158,7 @@ def test_learned_guess_data_path_matches_oracle(ctx, order):
     s = n_run - 1  # the last training step
     X_tr, sig = mlp.features([du[s - 1 - j] for j in range(4)], nodef)
     b_s = base_of(s)
-    scale_s = mlp.correction_scale(du[s], b_s, sig) if order > 0 else sig
+    scale_s = mlp.correction_scale(du[s], b_s, sig[0])
     Y_tr = mlp.targets(du[s], b_s, scale_s)
     idx = mlp.sample_nodes(N, B, seed, s, ips - 1)
     assert np.abs(got["x_train"] - X_tr[idx]).max() <= 2e-5 * max(1.0, np.abs(X_tr[idx]).max())
@@ -162,8 +167,8 @@ def test_learned_guess_data_path_matches_oracle(ctx, order):
     # inputs of the next step's inference
     X_n, sig_n = mlp.features([du[s - j] for j in range(4)], nodef)
     b_n = base_of(s + 1)
-    scale_n = mlp.correction_scale(du[s], b_s, sig_n) if order > 0 else sig_n
+    scale_n = mlp.correction_scale(du[s], b_s, sig_n[0])
     assert np.abs(got["x"] - X_n[nodes]).max() <= 2e-5 * max(1.0, np.abs(X_n[nodes]).max())
     assert np.abs(got["base"] - b_n[nodes]).max() <= 1e-8 * np.abs(b_n).max()
-    assert abs(got["sigma"] - sig_n) <= 1e-6 * sig_n
+    assert abs(got["sigma"] - sig_n[0]) <= 1e-6 * sig_n[0]
     assert abs(got["scale"] - scale_n) <= 1e-4 * scale_n

@@ -188,13 +188,13 @@ def test_misfit_matches_oracle_and_inverse_crime(ctx):
                 G[k, i, j] = rng.standard_normal() * np.sin(2 * np.pi * rng.uniform(0.01, 0.08) * t) * np.exp(-t / 90)
     obs = rng.standard_normal((n_rec, 3, n_t))
     obs[2, 1] = 0.0  # dropped pair
-    e_gpu, c_gpu = ctx.misfit(G, obs, s, L, tau=1e-10)
+    e_gpu, c_gpu = ctx.misfit_green(G, obs, s, L, tau=1e-10)
     e_ref, c_ref = misfit.estimate(G, obs, s, L, tau=1e-10)
     assert abs(e_gpu - e_ref) <= 1e-9 * e_ref
     assert np.abs(c_gpu - c_ref).max() <= 1e-8 * np.abs(c_ref).max()
     c_true = rng.standard_normal((3, L))
     obs2 = misfit.superpose(G, c_true, s)
-    e2, c2 = ctx.misfit(G, obs2, s, L, tau=1e-12)
+    e2, c2 = ctx.misfit_green(G, obs2, s, L, tau=1e-12)
     assert e2 < 1e-8
     np.testing.assert_allclose(c2, c_true, atol=1e-7)
 

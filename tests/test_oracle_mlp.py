@@ -131,21 +131,31 @@ def test_extrapolation_exact_on_polynomials():
     np.testing.assert_allclose(mlp.base_guess(v, a, 0.1, [np.zeros(6)] * 2, 3), 0.1 + 0.01)
 
 
-def test_features_slot_order_sigma_and_scale_invariance():
+def test_features_are_normalised_backward_differences():
+    """A cubic history du_{s-1-j} = (j + 1)^3 = 1, 8, 27, 64 has backward differences
+    1, -7, 12, -6 (constant over the nodes), so every scaled difference is +-1: this
+    pins the slot order, the difference formula and the per-difference scale."""
     N = 7
-    hist = [np.full((N, 3), float(j + 1)) for j in range(4)]  # du_{s-1-j} = j + 1
+    hist = [np.full((N, 3), float((j + 1) ** 3)) for j in range(4)]
     nodef = np.arange(4 * N, dtype=np.float64).reshape(N, 4)
-    X, sigma = mlp.features(hist, nodef)
-    assert sigma == 1.0
-    np.testing.assert_array_equal(X[:, :12], np.repeat([1.0, 2.0, 3.0, 4.0], 3)[None].repeat(N, 0))
+    X, sig = mlp.features(hist, nodef)
+    np.testing.assert_array_equal(sig, [1.0, 7.0, 12.0, 6.0])
+    np.testing.assert_array_equal(X[:, :12], np.repeat([1.0, -1.0, 1.0, -1.0], 3)[None].repeat(N, 0))
     np.testing.assert_array_equal(X[:, 12:], nodef)
+    # a quadratic history has a zero third difference: its scale falls back to 1
+    X, sig = mlp.features([np.full((N, 3), float((j + 1) ** 2)) for j in range(4)], nodef)
+    assert sig[3] == 1.0 and np.abs(X[:, 9:12]).max() == 0.0
+    # features do not change when all increments are scaled
     rng = np.random.default_rng(0)
     hist = [rng.standard_normal((N, 3)) for _ in range(4)]
     X1, s1 = mlp.features(hist, nodef)
     X2, s2 = mlp.features([-250.0 * h for h in hist], nodef)
-    np.testing.assert_allclose(X2[:, :12], -X1[:, :12], rtol=1e-14)
-    np.testing.assert_allclose(s2, 250.0 * s1, rtol=1e-14)
-    assert mlp.features([np.zeros((N, 3))] * 4, nodef)[1] == 1.0
+    np.testing.assert_allclose(X2[:, :12], -X1[:, :12], rtol=1e-13)
+    np.testing.assert_allclose(s2, 250.0 * s1, rtol=1e-13)
+    # Newton's backward form: a cubic history f(tau) = (1 - tau)^3 (tau = 0 the latest
+    # step, tau = -j the step j back) is extrapolated exactly by D_0 + ... + D_3 = f(1) = 0
+    D = mlp.backward_differences([np.full(3, float((j + 1) ** 3)) for j in range(4)])
+    np.testing.assert_allclose(sum(D), 0.0, atol=1e-12)
 
 
 def test_layer_features_take_the_lowest_layer():
@@ -199,3 +209,40 @@ def test_sample_hash_is_a_bijection_and_spreads():
     counts = np.bincount(nodes, minlength=1000)
     assert counts.min() > 30 and counts.max() < 110  # 65.5 expected per node
     assert not np.array_equal(nodes, mlp.sample_nodes(1000, 65536, seed=7, step=4, it=1))
+
+
+def test_bf16_gradient_is_the_exact_gradient_without_rounding_and_close_with_it():
+    rng = np.random.default_rng(12)
+    theta = mlp.init(4) + 0.05 * rng.standard_normal(mlp.N_PARAMS)
+    X = rng.standard_normal((96, 16))
+    Y = rng.standard_normal((96, 3))
+    loss, g = mlp.loss_grad(theta, X, Y)
+    loss_i, g_i = mlp.loss_grad_bf16(theta, X, Y, rnd=lambda a: np.asarray(a, dtype=np.float64))
+    assert loss_i == loss and np.array_equal(g_i, g)
+    loss_b, g_b = mlp.loss_grad_bf16(theta, X, Y)
+    assert abs(loss_b - loss) <= 2e-2 * loss
+    assert np.linalg.norm(g_b - g) <= 3e-2 * np.linalg.norm(g)
+    # the rounding really happens: bf16 differs from the exact gradient
+    assert np.linalg.norm(g_b - g) > 1e-5 * np.linalg.norm(g)
+
+
+def test_bf16_gradient_rounds_the_back_propagated_error():
+    """One-unit path: the output error 2 (o - y) / B is rounded before it multiplies
+    the weights, so a weight gradient carries bfloat16 precision."""
+    theta = np.zeros(mlp.N_PARAMS)
+    p = mlp.unpack(theta)
+    p["W1"][0, 0] = 1.0
+    p["W2"][0, 0] = 1.0
+    p["W3"][0, 0] = 1.0
+    X = np.zeros((1, 16))
+    X[0, 0] = 1.0
+    Y = np.zeros((1, 3))
+    Y[0, 0] = 1.0 - 2.0 ** -10  # o - y = 2^-10 exactly; 2(o - y) = 2^-9
+    loss, g = mlp.loss_grad_bf16(theta, X, Y)
+    W3 = mlp.unpack(g)["W3"]
+    assert W3[0, 0] == 2.0 ** -9  # h2 = 1
+    Y[0, 0] = 1.0 - 3.0 * 2.0 ** -12  # 2(o - y) = 1.5 * 2^-10, representable
+    assert mlp.unpack(mlp.loss_grad_bf16(theta, X, Y)[1])["W3"][0, 0] == 1.5 * 2.0 ** -10
+    Y[0, 0] = 1.0 - (1.0 + 2.0 ** -9) * 2.0 ** -11  # 2(o - y) = (1 + 2^-9) 2^-10 rounds to 2^-10
+    assert mlp.unpack(mlp.loss_grad_bf16(theta, X, Y)[1])["W3"][0, 0] == 2.0 ** -10
+    assert mlp.unpack(mlp.loss_grad(theta, X, Y)[1])["W3"][0, 0] == (1.0 + 2.0 ** -9) * 2.0 ** -10

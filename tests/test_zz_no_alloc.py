@@ -1,4 +1,4 @@
-"""Allocation-free misfit entry point (gsw_misfit_noalloc) against gsw_misfit.
+"""Allocation-free misfit entry point (gsw_misfit_noalloc) against gsw_misfit_green.
 
 Some callers cannot allocate GPU memory: their device memory is owned by
 another allocator (a framework's caching pool or an arena reserved at start-up)
@@ -40,7 +40,7 @@ def test_noalloc_misfit_matches_allocating_entry_point():
     try:
         for seed in (21, 22):  # two calls in a row with different data
             G, obs, s, L = _problem(seed)
-            e_ref, c_ref = ctx.misfit(G, obs, s, L, tau=1e-10)
+            e_ref, c_ref = ctx.misfit_green(G, obs, s, L, tau=1e-10)
             G_dev = torch.tensor(G, device="cuda")
             obs_dev = torch.tensor(obs, device="cuda")
             err_dev = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
@@ -65,7 +65,7 @@ def test_noalloc_misfit_matches_allocating_entry_point():
         assert ei.value.status == gsw.E_INVALID
         # the input-wave coefficients are optional
         G, obs, s, L = _problem(25)
-        e_ref, _ = ctx.misfit(G, obs, s, L, tau=1e-10)
+        e_ref, _ = ctx.misfit_green(G, obs, s, L, tau=1e-10)
         err_dev = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
         ctx.misfit_noalloc(torch.tensor(G, device="cuda"), torch.tensor(obs, device="cuda"), s, L, err_dev, None)
         torch.cuda.synchronize()
