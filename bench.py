@@ -11,7 +11,11 @@ element-by-element pass), predictor, preconditioned CG to relative residual
 Metric: DOF.steps/s (higher is better).  Under torchrun each rank runs an
 independent directional analysis (direction = rank mod 3) of the same model:
 weak scaling with no data-path collective; the reported value is the
-whole-job DOF.steps/s over the slowest rank.
+whole-job DOF.steps/s over the slowest rank.  The default line also reports,
+on rank 0, the plain FP64 form over the same window and candidate
+analyses/h of 128 candidates of the mixed-precision ensemble (batched mixed,
+batched FP64, FP64 one after another); `--workload candidates` is that
+ensemble alone, its analyses shared over the ranks by shard.assign.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -33,12 +37,6 @@ sys.path.insert(0, ROOT)
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 EBE_FLOPS_PER_ELEM = 1088      # A-mode element: vertex-gradient stiffness, consistent mass, p.Ap partial
 EBE_FLOPS_PER_FACE = 150
-# algorithmic bytes of one FP64 A p launch: x, y (read + write) once per DOF,
-# connectivity + material id + geometry once per element
-def ebe_bytes(n_nodes, n_elem, n_faces):
-    return n_nodes * 3 * (8 + 8 + 8) + n_elem * (40 + 4 + 80) + n_faces * (24 + 48)
-
-
 def unique_node_bytes(n_nodes, n_elem, n_vert, s_x, s_y):
     """Algorithmic bytes of one element-by-element product with unique data only
     (every shared node read and written once): x and y once per DOF (s_x, s_y
@@ -254,10 +252,11 @@ def run_reference(args, rank):
 
 
 def run_candidates(args, rank, world, dist):
-    """Batched ensemble: `--models` candidate models of the mixed-precision ensemble
-    (120 x 120 x 300 m, 95,817 nodes / 287,451 DOF each, seeded interfaces),
-    one directional analysis each, advanced together by one captured CUDA graph
-    per time step."""
+    """Batched ensemble: `--models` directional analyses per GPU of the
+    mixed-precision ensemble's candidates (120 x 120 x 300 m, 95,817 nodes /
+    287,451 DOF each, seeded interfaces; analysis a is candidate a // 3 in
+    direction a % 3), shared over the ranks by shard.assign, each rank
+    advancing its share together by one captured CUDA graph per time step."""
     import torch
 
     from paper_2404_17754_gb300 import build, gsw, shard
@@ -272,9 +271,14 @@ def run_candidates(args, rank, world, dist):
     n_total = args.warmup + args.steps
     prec = {"fp64": 0, "fp32": 1, "fp16": 2}[args.precision]
     ctx = gsw.Context(local)
+    # the job: world x --models independent analyses (candidate a // 3, input
+    # direction a % 3), each rank taking a DOF-balanced share (all candidates of
+    # this ensemble have 41 x 41 x 57 nodes); no data-path collective
+    n_job = world * args.models
+    mine = shard.assign([3.0 * 41 * 41 * 57] * n_job, world)[rank]
     models, dof = [], 0
-    for l in range(args.models):
-        cfg = configs.config4_candidate(rank * args.models + l, n_steps=n_total, direction=l % 3)
+    for a in mine:
+        cfg = configs.config4_candidate(a // 3, n_steps=n_total, direction=a % 3)
         m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
         m.set_time(cfg["dt"], n_total, cfg["band"])
         m.set_input(cfg["dir"], cfg["p"])

@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gsw.h"
 #include "gsw_internal.cuh"
 #include "gsw_misfit.cuh"
@@ -222,6 +224,12 @@ gsw_status fail(gsw_ctx* c, gsw_status s, const char* fmt, ...) {
                   __FILE__, __LINE__);                                                    \
   } while (0)
 
+// NVTX range over a scope (time step, batch step, CG phase) for profilers.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 struct DeviceGuard {
   int prev = -1;
   explicit DeviceGuard(int dev) {
@@ -354,6 +362,8 @@ gsw_status model_reset(gsw_ctx* ctx, Model* m) {
   m->stats = gsw_stats{};
   if (m->guess_ext) CK(cudaMemsetAsync(m->guess_ext, 0, 2 * sizeof(int), ctx->stream));  // no increment history
   if (m->lo_ready) {
+    // a wait of the inner operator that ran out failed the run; a reset clears it
+    CK(cudaMemsetAsync(&m->isc->err, 0, sizeof(unsigned int), ctx->stream));
     CK(cudaMemcpyAsync(&m->iters_reset, &m->isc->iters, sizeof(m->iters_reset), cudaMemcpyDeviceToHost,
                        ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -381,6 +391,7 @@ void launch_outer(const Model* m, int mode, const ModelView& mv, const double* x
 }
 
 gsw_status step_fp64(gsw_ctx* ctx, Model* m) {
+  NvtxRange nv("gsw step (FP64 PCG)");
   cudaStream_t s = ctx->stream;
   ModelView mv = m->view();
   const double force = 2.0 * m->input[(size_t)m->step];
@@ -469,6 +480,7 @@ gsw_status autotune_lo(gsw_ctx* ctx, Model* m) {
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   launch_to_lo(m->N, m->u, m->d_lo, m->lo_half, m->w32, s);
+  CK(cudaMemsetAsync(&m->isc->err, 0, sizeof(unsigned int), s));
   // rounds interleave the variants so none profits from a cache warmed by
   // another; each variant keeps the median of its rounds
   constexpr int kRounds = 5;
@@ -911,6 +923,7 @@ int64_t inner_solve(Model* m, cudaStream_t s) {
 // on, or where the stream cannot be captured, the launches are issued directly.
 void inner_solve_dev(Model* m, cudaStream_t s);
 int64_t inner_solve_step(Model* m, cudaStream_t s) {
+  NvtxRange nv("gsw inner solve");
   if (m->timing || m->live_tune) return inner_solve(m, s);
   if (m->ig_version != m->version) {
     if (m->ig_exec) cudaGraphExecDestroy(m->ig_exec);
@@ -933,6 +946,7 @@ int64_t inner_solve_step(Model* m, cudaStream_t s) {
 
 // One Newmark step with flexible CG (FP64) preconditioned by the inner solve.
 gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
+  NvtxRange nv("gsw step (flexible CG)");
   cudaStream_t s = ctx->stream;
   ModelView mv = m->view();
   const double force = 2.0 * m->input[(size_t)m->step];
@@ -1756,9 +1770,13 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
     for (int i = 0; i < nm; ++i) b->versions[i] = b->members[i]->version;
     return GSW_OK;
   };
-  if (stale && remaining > 0) TRY(capture());
+  if (stale && remaining > 0) {
+    NvtxRange nvc("gsw batch graph capture");
+    TRY(capture());
+  }
   gsw_status st = GSW_OK;
   const int chunk = 8;
+  NvtxRange nv("gsw batch steps");
   while (remaining > 0) {
     const int launch_n = std::min(remaining, chunk);
     for (int s = 0; s < launch_n; ++s) CK(cudaGraphLaunch(b->exec, b->origin));
@@ -1795,11 +1813,14 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
       if (h.failed && !m->failed) {
         m->failed = true;
         if (st == GSW_OK) {
-          st = h.failed == GSW_E_NOCONV ? GSW_E_NOCONV : (h.failed == GSW_E_NAN ? GSW_E_NAN : GSW_E_STATE);
+          st = (h.failed == GSW_E_NOCONV || h.failed == GSW_E_NAN || h.failed == GSW_E_TIMEOUT) ? (gsw_status)h.failed
+                                                                                                 : GSW_E_STATE;
           fail(ctx, st, "model %d%s failed at step %d (%s)", b->ids[i],
                b->dirs[i] == 0 ? " (direction x1)" : (b->dirs[i] == 1 ? " (direction x2)" :
                                                       (b->dirs[i] == 2 ? " (direction x3)" : "")),
-               h.fail_step, h.failed == GSW_E_NAN ? "non-finite residual" : "no convergence");
+               h.fail_step, h.failed == GSW_E_NAN ? "non-finite residual"
+                            : (h.failed == GSW_E_TIMEOUT ? "a bounded wait of the inner operator ran out"
+                                                         : "no convergence"));
         }
       }
       if (h.needs_host && !m->failed) {

@@ -120,7 +120,7 @@ def test_run_uses_batched_path_for_mixed_models(ctx):
     cfgs = _cfgs(n_steps=15)
     models = [_upload(ctx, cfg, 2) for cfg in cfgs]
     ids = np.array([m.id for m in models], dtype=np.int32)
-    ctx._check(ctx.lib.gsw_run(ctx.h, ids.ctypes.data_as(gsw._ip), len(ids)))
+    ctx._check(ctx.lib.gsw_run(ctx.h, ids.ctypes.data_as(gsw._ip), len(ids), 0))
     for cfg, m in zip(cfgs, models):
         ref = newmark.analysis(cfg, tol=1e-8)["wave"]
         assert _relerr(m.waveforms(), ref) <= 1e-6

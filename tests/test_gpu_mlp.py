@@ -6,8 +6,11 @@
   oracle's gradient with the same rounding points, and vs its exact FP64
   backprop (pinned by finite differences);
 * a run that trains on its first steps and then applies the guess converges
-  every step to the same 1e-8 relative residual and reproduces the plain run;
-  the guess quality (initial residual) and CG iterations are compared.
+  every step to the same 1e-8 relative residual and reproduces the plain run,
+  and the trained network gains: a lower initial residual than the Newmark
+  predictor and no more outer iterations;
+* the data path (features, sampled nodes, targets, base guess, scales)
+  against the oracle's.
 """
 import numpy as np
 import pytest
@@ -108,14 +111,13 @@ def test_learned_guess_run_converges_and_matches_plain(ctx):
     st = runs[1]["state"]
     print("outer iterations over steps 61-120: plain %d, learned %d; mean initial residual: plain %.3e, learned "
           "%.3e; judge: %s" % (runs[0]["iters"], runs[1]["iters"], runs[0]["r0"], runs[1]["r0"], st))
-    assert st["learned_steps"] >= 5
-    # the judge keeps the learned guess only while it beats the plain predictor
-    if st["active"]:
-        assert st["learned_r0"] <= st["plain_r0"]
-    else:
-        assert st["learned_steps"] < 60
-    # and the run as a whole is not made much worse than the plain one
-    assert runs[1]["iters"] <= 1.2 * runs[0]["iters"]
+    # the trained network gains: it stays active (the judge keeps it), its initial
+    # residual is lower than the predictor's, and the solves need no more outer
+    # iterations than plain CG from the predictor
+    assert st["active"] and st["learned_steps"] >= 50
+    assert st["learned_r0"] < st["plain_r0"]
+    assert runs[1]["r0"] < runs[0]["r0"]
+    assert runs[1]["iters"] <= runs[0]["iters"]
 
 
 @pytest.mark.parametrize("order", [0, 2])
