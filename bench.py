@@ -431,6 +431,41 @@ def candidates_block(ctx, n_models, warmup, steps, tol, inner, guess_order, seq_
     return out
 
 
+def candidate_analysis_block(ctx, cfg, n_steps, args, prec):
+    """One candidate analysis of the realistic model (its three input-direction analyses,
+    paper: three analyses per model) from rest over n_steps steps, each timed with CUDA
+    events around gsw_run: one direction alone, the three directions as separate members of
+    one batch, and the three in lockstep sharing every inner-operator pass."""
+    import torch
+
+    m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
+    m.set_time(cfg["dt"], n_steps, cfg["band"])
+    for j in range(3):
+        m.set_input(j, cfg["p"][:n_steps])
+    out = {}
+    for name, mask, share in (("one_direction", 1, 0), ("three_directions_separate", 7, 0),
+                              ("three_directions_lockstep", 7, 1)):
+        m.set_solver(tol=args.tol, outer_op=OUTER_OPS[args.outer_op], precision=prec, inner_iters=args.inner,
+                     inner_rtol=args.inner_rtol, guess_order=args.guess_order, share_dirs=share)
+        m.run(dirs_mask=mask)  # set-up pass (instances, graph capture); the timed pass repeats it
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(ctx.stream)
+        m.run(dirs_mask=mask)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        out[name] = {"ms_per_step": e0.elapsed_time(e1) / n_steps,
+                     "outer_iters_per_step": [m.stats(j)["cg_iters_total"] / n_steps for j in range(3)
+                                              if mask & (1 << j)]}
+    one = out["one_direction"]["ms_per_step"]
+    out["lockstep_vs_3x_one_direction"] = out["three_directions_lockstep"]["ms_per_step"] / (3 * one)
+    out["separate_vs_3x_one_direction"] = out["three_directions_separate"]["ms_per_step"] / (3 * one)
+    out["steps"] = n_steps
+    out["note"] = "each run from rest (steps 0..%d), inputs of the three directions equal" % (n_steps - 1)
+    m.free()
+    return out
+
+
 def run_learned(args, rank, world, dist):
     """Learned CG initial guess on the realistic model: train on the first
     --train-steps steps, then time --steps steps; the same run with the plain
@@ -752,9 +787,11 @@ def main():
                                                                                           allc["steps"])}
         else:
             cpu = {"value": None, "unit": "DOF*steps/s", "cores": 1, "kind": "oracle", "sample": "failed: " + err}
-    cand = None
+    cand = ca = None
     if not args.no_extras and args.workload == "realistic":
         cand = candidates_block(ctx, args.models, args.warmup, args.steps, args.tol, 25, args.guess_order)
+        if args.precision != "fp64":
+            ca = candidate_analysis_block(ctx, cfg, args.warmup + args.steps, args, prec)
     out = {
         "metric": "DOF*steps/s", "value": value, "unit": "DOF*steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
@@ -777,7 +814,7 @@ def main():
                    "candidate_analyses_per_hour_extrapolated": 3600.0 / (3 * 4000 * t_max / args.steps),
                    "plain_fp64": plain,
                    "speedup_vs_plain_fp64": (plain["ms_per_step"] / (1e3 * t_max / args.steps)) if plain else None,
-                   "candidates": cand},
+                   "candidates": cand, "candidate_analysis": ca},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
     }
     print(json.dumps(out))

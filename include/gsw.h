@@ -106,6 +106,11 @@ typedef struct {
                             guess converges to the same tolerance. */
   int32_t outer_op;      /* arithmetic of the CG's element-by-element operator (the
                             FP64 residual at the initial guess and A p): gsw_outer_op */
+  int32_t share_dirs;    /* mixed modes, gsw_run with a direction mask: 1 = the model's
+                            direction analyses advance in lockstep and share every
+                            inner-operator pass (the element records and node lists
+                            are read once for all directions; a direction whose solve
+                            has converged skips its share); 0 = each advances on its own */
 } gsw_solver_opts;
 
 typedef struct {

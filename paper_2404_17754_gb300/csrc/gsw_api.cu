@@ -60,7 +60,7 @@ struct Model {
   std::vector<double> input;
   int dir = 0;
   bool input_set = false;
-  gsw_solver_opts opts = {1e-8, 10000, GSW_PREC_FP64, 20, 8, 6, -1, 0.0, 0, 0};
+  gsw_solver_opts opts = {1e-8, 10000, GSW_PREC_FP64, 20, 8, 6, -1, 0.0, 0, 0, 0};
   int64_t step = 0;
   bool failed = false;
   gsw_stats stats = {};
@@ -182,6 +182,9 @@ struct Batch {
   std::vector<Model*> members;  // models or direction instances
   std::vector<int> ids;         // model id of each member (for messages)
   std::vector<int> dirs;        // input direction of an instance member, -1 for a model
+  // members i .. i + lane[i] - 1 advance in lockstep on stream i (lane[i] = 0:
+  // inside an earlier member's lane); 1 = on its own
+  std::vector<int> lane;
   std::vector<int> versions;
   cudaStream_t origin = nullptr;
   std::vector<cudaStream_t> streams;
@@ -1095,7 +1098,7 @@ void inner_solve_dev(Model* m, cudaStream_t s) {
 // the step has not converged, at most outer - 1 times); otherwise they are
 // unrolled `outer` - 1 times (kernels of a converged step return at entry).
 // Returns false if the conditional node could not be built.
-bool issue_loop(cudaStream_t s, StepState* ss, CgScalars* cg, int outer, cudaStream_t bs, StepLaunches* n,
+bool issue_loop(cudaStream_t s, const LoopSet& ls, int outer, cudaStream_t bs, StepLaunches* n,
                 int64_t per_iter, const std::function<void(cudaStream_t)>& body) {
   if (bs == nullptr) {
     for (int k = 1; k < outer; ++k) body(s);
@@ -1107,7 +1110,7 @@ bool issue_loop(cudaStream_t s, StepState* ss, CgScalars* cg, int outer, cudaStr
   if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g) != cudaSuccess || cs != cudaStreamCaptureStatusActive) return false;
   cudaGraphConditionalHandle h;
   if (cudaGraphConditionalHandleCreate(&h, g, 0, 0) != cudaSuccess) return false;
-  launch_loop_open(h, ss, cg, outer - 1, s);
+  launch_loop_open(h, ls, outer - 1, s);
   const cudaGraphNode_t* deps = nullptr;
   const cudaGraphEdgeData* edges = nullptr;
   size_t nd = 0;
@@ -1125,7 +1128,7 @@ bool issue_loop(cudaStream_t s, StepState* ss, CgScalars* cg, int outer, cudaStr
   if (cudaStreamBeginCaptureToGraph(bs, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     return false;
   body(bs);
-  launch_loop_next(h, ss, cg, outer - 1, bs);
+  launch_loop_next(h, ls, outer - 1, bs);
   if (cudaStreamEndCapture(bs, &bg) != cudaSuccess) return false;
   n->fixed += 1;
   n->body += per_iter + 1;
@@ -1136,7 +1139,8 @@ bool issue_loop(cudaStream_t s, StepState* ss, CgScalars* cg, int outer, cudaStr
 bool issue_outer_loop(Model* m, cudaStream_t s, StepState* ss, int outer, cudaStream_t bs, StepLaunches* n) {
   ModelView mv = m->view();
   const int64_t per_iter = inner_solve_launches(m, inner_fuses(m, m->lo_variant)) + 4;  // + zbeta, pupdate, A p, update
-  return issue_loop(s, ss, m->cg, outer, bs, n, per_iter, [&](cudaStream_t st) {
+  return issue_loop(s, LoopSet{{ss, nullptr, nullptr}, {m->cg, nullptr, nullptr}, 1}, outer, bs, n, per_iter,
+                    [&](cudaStream_t st) {
     inner_solve_dev(m, st);
     launch_fcg_zbeta(mv, m->y32, m->r, m->q, m->z, m->partials, m->cg, m->isc, st);
     launch_fcg_pupdate(mv, m->z, m->p, m->q, m->cg, st, outer_dword(m) ? 1 : 0);
@@ -1163,7 +1167,8 @@ bool issue_device_step_fp64(Model* m, cudaStream_t s, StepState* ss, int outer, 
   launch_cg_residual(mv, m->b, m->q, m->r, m->z, m->p, m->dinv, m->partials, m->cg, s);
   n->fixed += 6 + (k_guess > 0 ? 1 : 0);
   // the first residual may already meet the tolerance; every PCG iteration is a loop body
-  if (!issue_loop(s, ss, m->cg, outer + 1, bs, n, 3, [&](cudaStream_t st) {
+  if (!issue_loop(s, LoopSet{{ss, nullptr, nullptr}, {m->cg, nullptr, nullptr}, 1}, outer + 1, bs, n, 3,
+                  [&](cudaStream_t st) {
         launch_outer(m, kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, st);
         launch_cg_update(mv, m->x, m->r, m->z, m->p, m->q, m->dinv, m->partials, m->cg, st);
         launch_cg_pupdate(mv, m->z, m->p, m->cg, st);
@@ -1211,6 +1216,111 @@ bool issue_device_step(Model* m, cudaStream_t s, StepState* ss, int outer, cudaS
   launch_record(m->v, m->rec_node, m->rec_w, m->n_rec, m->wave, m->n_steps, 0, s, ss);
   launch_step_advance(ss, s);
   n->fixed += 4;
+  return true;
+}
+
+// Inner solves of a set of direction analyses of one model in lockstep: each
+// keeps its own vectors and scalars, and every iteration applies the operator
+// to all their search directions in one pass over the shared element data.
+void inner_solve_group_dev(Model* const* g, int n, cudaStream_t s) {
+  Model* m0 = g[0];
+  const int half = m0->lo_half;
+  const void* view = half ? (const void*)&m0->lo_h : (const void*)&m0->lo_f;
+  for (int i = 0; i < n; ++i) {
+    Model* m = g[i];
+    launch_inner_init(m->N, m->r, m->dinv32, m->s32, m->y32, m->t32, m->d_lo, half, m->w32, m->partials, m->isc,
+                      m->cg, s, (float)m->opts.inner_rtol);
+  }
+  Lo3Args a = {};
+  a.nr = n;
+  for (int i = 0; i < n; ++i) {
+    a.d[i] = g[i]->d_lo;
+    a.w[i] = g[i]->w32;
+    a.dw_part[i] = g[i]->dw_part;
+    a.sc[i] = g[i]->isc;
+    a.outer[i] = g[i]->cg;
+  }
+  const int variant = m0->lo_variant == 0 ? 0 : 1;  // the one-CTA-per-block occupancy variants
+  const int it = m0->opts.inner_iters > 0 ? m0->opts.inner_iters : 1;
+  for (int k = 0; k < it; ++k) {
+    launch_ebe_lo3(half, half, view, a, s, variant);
+    for (int i = 0; i < n; ++i) {
+      Model* m = g[i];
+      launch_inner_update(m->N, m->y32, m->s32, m->t32, m->d_lo, half, m->w32, m->dinv32, m->dw_part, m->partials,
+                          m->isc, s, m->cg, lo_grid_max(m));
+      if (k + 1 < it) launch_inner_dupdate(m->N, m->t32, m->d_lo, half, m->isc, s, m->cg);
+    }
+  }
+}
+int64_t inner_group_launches(const Model* m0, int n) {
+  const int64_t it = m0->opts.inner_iters > 0 ? m0->opts.inner_iters : 1;
+  const int64_t per = (lo_grid_max(m0) <= kAlphaPrologueMax ? 1 : 2);
+  return n + it * (1 + n * per) + n * (it - 1);
+}
+
+// One mixed time step of the n direction analyses g[0..n) of one model in
+// lockstep on stream s (their step states at ss[0..n)): each analysis's
+// right-hand side, guess and residual, the shared inner solves, and the
+// flexible-CG iterations in one device-side loop that runs while any of the
+// analyses has not converged; then each commits (or is handed to the host).
+bool issue_device_step_group(Model* const* g, int n, cudaStream_t s, StepState* ss, int outer, cudaStream_t bs,
+                             StepLaunches* nl) {
+  for (int i = 0; i < n; ++i) {
+    Model* m = g[i];
+    ModelView mv = m->view();
+    Drive dr{m->p_dev, ss + i};
+    launch_step_begin(ss + i, m->cg, s);
+    cudaMemsetAsync(m->w32, 0, sizeof(float) * 3 * (size_t)m->N, s);
+    launch_rhs_lo(m->lo_half, m->lo_half ? (const void*)&m->lo_h : (const void*)&m->lo_f, m->N, m->u, m->v, m->a,
+                  m->uva, m->w32, 0.0, m->dir, s, dr);
+    const int k_guess = m->opts.guess_order;
+    if (k_guess > 0)
+      launch_guess_extrap(m->N, m->guess_ring, k_guess, m->guess_ext, m->v, m->a, m->dt, m->x, s, ss + i);
+    launch_cg_init_mixed(mv, m->w32, m->u, m->v, m->a, m->x, m->p, m->z, m->b, m->r, m->q, m->partials, m->cg, s,
+                         ss + i, k_guess > 0 ? 1 : 0, outer_dword(m) ? 1 : 0);
+    launch_outer(m, kModeRes, mv, m->p, m->z, m->b, m->r, 0.0, m->dir, nullptr, m->cg, s, dr);
+    launch_cg_rnorm(mv, m->r, m->partials, m->cg, s);
+    nl->fixed += 6 + (k_guess > 0 ? 3 : 0);
+  }
+  inner_solve_group_dev(g, n, s);
+  for (int i = 0; i < n; ++i) {
+    Model* m = g[i];
+    ModelView mv = m->view();
+    launch_fcg_first(mv, m->y32, m->r, m->z, m->p, m->partials, m->cg, m->isc, s, outer_dword(m) ? 1 : 0);
+    launch_outer(m, kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, s);
+    launch_fcg_update(mv, m->x, m->r, m->p, m->q, m->partials, m->cg, s, outer_dword(m) ? 1 : 0);
+  }
+  nl->fixed += inner_group_launches(g[0], n) + 3 * n;
+  LoopSet ls = {};
+  ls.n = n;
+  for (int i = 0; i < n; ++i) {
+    ls.ss[i] = ss + i;
+    ls.cg[i] = g[i]->cg;
+  }
+  const int64_t per_iter = inner_group_launches(g[0], n) + 4 * n;
+  if (!issue_loop(s, ls, outer, bs, nl, per_iter, [&](cudaStream_t st) {
+        inner_solve_group_dev(g, n, st);
+        for (int i = 0; i < n; ++i) {
+          Model* m = g[i];
+          ModelView mv = m->view();
+          launch_fcg_zbeta(mv, m->y32, m->r, m->q, m->z, m->partials, m->cg, m->isc, st);
+          launch_fcg_pupdate(mv, m->z, m->p, m->q, m->cg, st, outer_dword(m) ? 1 : 0);
+          launch_outer(m, kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, st);
+          launch_fcg_update(mv, m->x, m->r, m->p, m->q, m->partials, m->cg, st, outer_dword(m) ? 1 : 0);
+        }
+      }))
+    return false;
+  for (int i = 0; i < n; ++i) {
+    Model* m = g[i];
+    ModelView mv = m->view();
+    launch_step_end(ss + i, m->cg, s);
+    if (m->opts.guess_order > 0)
+      launch_guess_push(m->N, m->x, m->guess_ring, m->opts.guess_order, m->guess_ext, s, ss + i);
+    launch_newmark(mv, m->x, m->u, m->v, m->a, m->cg, s, ss + i);
+    launch_record(m->v, m->rec_node, m->rec_w, m->n_rec, m->wave, m->n_steps, 0, s, ss + i);
+    launch_step_advance(ss + i, s);
+  }
+  nl->fixed += 4 * n;
   return true;
 }
 
@@ -1561,14 +1671,14 @@ gsw_status gsw_step(gsw_ctx* ctx, int32_t model_id, int32_t n) {
 }
 
 static gsw_status batch_make(gsw_ctx* ctx, const std::vector<Model*>& ms, const std::vector<int>& model_ids,
-                             const std::vector<int>& dirs, int32_t* batch_id);
+                             const std::vector<int>& dirs, int32_t* batch_id, const std::vector<int>* lanes = nullptr);
 
 gsw_status gsw_run(gsw_ctx* ctx, const int32_t* model_ids, int32_t n_models, int32_t dirs_mask) {
   if (!ctx || (!model_ids && n_models > 0)) return GSW_E_INVALID;
   if (dirs_mask < 0 || dirs_mask > 7) return fail(ctx, GSW_E_INVALID, "dirs_mask must be 0..7");
   DeviceGuard g(ctx->device);
   std::vector<Model*> members;
-  std::vector<int> ids, dirs;
+  std::vector<int> ids, dirs, lanes;
   int max_steps = 0;
   for (int i = 0; i < n_models; ++i) {
     Model* m = find(ctx, model_ids[i]);
@@ -1587,7 +1697,9 @@ gsw_status gsw_run(gsw_ctx* ctx, const int32_t* model_ids, int32_t n_models, int
       members.push_back(m);
       ids.push_back(model_ids[i]);
       dirs.push_back(-1);
+      lanes.push_back(1);
     } else {
+      const size_t first = members.size();
       for (int d = 0; d < 3; ++d) {
         if (!(dirs_mask & (1 << d))) continue;
         Model* c = nullptr;
@@ -1596,13 +1708,20 @@ gsw_status gsw_run(gsw_ctx* ctx, const int32_t* model_ids, int32_t n_models, int
         members.push_back(c);
         ids.push_back(model_ids[i]);
         dirs.push_back(d);
+        lanes.push_back(1);
+      }
+      // the direction analyses share each inner-operator pass (lockstep)
+      const int cnt = (int)(members.size() - first);
+      if (m->opts.share_dirs && m->opts.precision != GSW_PREC_FP64 && cnt > 1) {
+        lanes[first] = cnt;
+        for (int k = 1; k < cnt; ++k) lanes[first + k] = 0;
       }
     }
     max_steps = std::max(max_steps, m->n_steps);
   }
   if (members.empty()) return GSW_OK;
   int32_t bid = 0;
-  TRY(batch_make(ctx, members, ids, dirs, &bid));
+  TRY(batch_make(ctx, members, ids, dirs, &bid, &lanes));
   gsw_status st = gsw_batch_step(ctx, bid, max_steps);
   std::string msg = ctx->err;
   gsw_batch_destroy(ctx, bid);
@@ -1612,7 +1731,7 @@ gsw_status gsw_run(gsw_ctx* ctx, const int32_t* model_ids, int32_t n_models, int
 
 // A batch over models or direction instances (the members).
 static gsw_status batch_make(gsw_ctx* ctx, const std::vector<Model*>& ms, const std::vector<int>& model_ids,
-                      const std::vector<int>& dirs, int32_t* batch_id) {
+                             const std::vector<int>& dirs, int32_t* batch_id, const std::vector<int>* lanes) {
   DeviceGuard g(ctx->device);
   const int n_models = (int)ms.size();
   for (int i = 0; i < n_models; ++i) {
@@ -1661,6 +1780,7 @@ static gsw_status batch_make(gsw_ctx* ctx, const std::vector<Model*>& ms, const 
     b->members.push_back(m);
     b->ids.push_back(model_ids[i]);
     b->dirs.push_back(dirs[i]);
+    b->lane.push_back(lanes ? (*lanes)[i] : 1);
     b->versions.push_back(-1);
   }
   if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return bail("synchronise", e);
@@ -1742,13 +1862,17 @@ gsw_status gsw_batch_step(gsw_ctx* ctx, int32_t batch_id, int32_t n_steps) {
       bool ok = true;
       b->launches.assign(nm, StepLaunches());
       for (int i = 0; i < nm && ok; ++i) {
+        if (b->lane[i] == 0) continue;  // advanced by the lane that holds it
         Model* m = b->members[i];
         const bool fp64 = m->opts.precision == GSW_PREC_FP64;
         ok = cudaStreamWaitEvent(b->streams[i], b->fork, 0) == cudaSuccess &&
-             (fp64 ? issue_device_step_fp64(m, b->streams[i], b->ss_dev + i, wl ? fp64_loop : outer,
-                                            wl ? b->body_stream : nullptr, &b->launches[i])
-                   : issue_device_step(m, b->streams[i], b->ss_dev + i, wl ? outer_loop : outer,
-                                       wl ? b->body_stream : nullptr, &b->launches[i])) &&
+             (b->lane[i] > 1 ? issue_device_step_group(&b->members[i], b->lane[i], b->streams[i], b->ss_dev + i,
+                                                       wl ? outer_loop : outer, wl ? b->body_stream : nullptr,
+                                                       &b->launches[i])
+              : fp64 ? issue_device_step_fp64(m, b->streams[i], b->ss_dev + i, wl ? fp64_loop : outer,
+                                              wl ? b->body_stream : nullptr, &b->launches[i])
+                     : issue_device_step(m, b->streams[i], b->ss_dev + i, wl ? outer_loop : outer,
+                                         wl ? b->body_stream : nullptr, &b->launches[i])) &&
              cudaEventRecord(b->joins[i], b->streams[i]) == cudaSuccess &&
              cudaStreamWaitEvent(b->origin, b->joins[i], 0) == cudaSuccess;
       }

@@ -188,13 +188,19 @@ void launch_cg_init_mixed(const ModelView& m, const float* b32, const double* u,
 void launch_step_begin(StepState* ss, CgScalars* cg, cudaStream_t s);
 void launch_step_end(StepState* ss, const CgScalars* cg, cudaStream_t s);
 void launch_step_advance(StepState* ss, cudaStream_t s);
-// Device-side outer-iteration loop of a captured step (a WHILE conditional
-// node): `open` sets the loop condition before the node (run the body unless
-// the step is inactive or already converged); `next`, the body's last kernel,
-// keeps it set while the step has not converged and the body has run fewer
-// than `cap` times, so the loop always ends.
-void launch_loop_open(cudaGraphConditionalHandle h, StepState* ss, const CgScalars* cg, int cap, cudaStream_t s);
-void launch_loop_next(cudaGraphConditionalHandle h, StepState* ss, const CgScalars* cg, int cap, cudaStream_t s);
+// Device-side iteration loop of a captured step (a WHILE conditional node)
+// over a set of up to three solves that advance together: `open` sets the
+// loop condition before the node (run the body unless every step is inactive
+// or already converged); `next`, the body's last kernel, keeps it set while a
+// solve of the set has not converged and the body has run fewer than `cap`
+// times, so the loop always ends.
+struct LoopSet {
+  StepState* ss[3];
+  const CgScalars* cg[3];
+  int n;
+};
+void launch_loop_open(cudaGraphConditionalHandle h, const LoopSet& ls, int cap, cudaStream_t s);
+void launch_loop_next(cudaGraphConditionalHandle h, const LoopSet& ls, int cap, cudaStream_t s);
 void launch_cg_rnorm(const ModelView& m, const double* r, double* partials, CgScalars* cg, cudaStream_t s);
 void launch_cg_residual(const ModelView& m, const double* b, double* q, double* r, double* z,
                         double* p, const double* dinv, double* partials, CgScalars* cg,
@@ -232,6 +238,18 @@ void launch_ebe_lo(int half_geo, int half_vec, const void* lo_view, const void* 
                    double* partials, InnerScalars* sc, cudaStream_t st, int variant,
                    const CgScalars* outer = nullptr);
 constexpr int kLoVariants = 4;
+// The inner operator on the search directions of up to three inner solves
+// that share one model's element data (the three input directions advancing
+// in lockstep): one read of the records and node lists for all of them.
+struct Lo3Args {
+  const void* d[3];          // search directions (inner storage type, 4 entries per node)
+  float* w[3];               // results A d
+  float* dw_part[3];         // per-CTA partials of d . A d
+  InnerScalars* sc[3];
+  const CgScalars* outer[3];
+  int nr;                    // right-hand sides in use (1..3)
+};
+void launch_ebe_lo3(int half_geo, int half_vec, const void* lo_view, const Lo3Args& a, cudaStream_t st, int variant);
 // Variants 0 and 1 can fuse the previous inner iteration's direction
 // recurrence d' = t + beta d into their gather (t padded to 4 entries per
 // node; d' goes to the other direction buffer).

@@ -479,6 +479,188 @@ __global__ void __launch_bounds__(kLoBlock, MINB) ebe_lo_kernel(LoView<SG> m, co
   lo_store_dw(dot, m.dw_part, sc);
 }
 
+// The same operator applied to the search directions of up to three inner
+// solves at once (the three input directions of one model, advancing in
+// lockstep): the element records and the block's node list are read once and
+// the element geometry decoded once; each right-hand side has its own
+// shared-memory gather/accumulation arrays, result, d . A d partials and
+// scalars, and is skipped once its solve has stopped.
+template <typename SG, typename SD, int MINB>
+__global__ void __launch_bounds__(kLoBlock, MINB) ebe_lo3_kernel(LoView<SG> m, Lo3Args a) {
+  // right-hand sides still running (bit r), read once: the flags change only between launches
+  const unsigned act = (a.nr > 0 && !inner_stopped(a.outer[0], a.sc[0]) ? 1u : 0u) |
+                       (a.nr > 1 && !inner_stopped(a.outer[1], a.sc[1]) ? 2u : 0u) |
+                       (a.nr > 2 && !inner_stopped(a.outer[2], a.sc[2]) ? 4u : 0u);
+  if (!act) return;
+  typedef typename LoRec<SG>::type Rec;
+  constexpr int RW = LoRec<SG>::words;
+  extern __shared__ float sm[];
+  __shared__ float matc[kMaxMat][3];
+  if (threadIdx.x < m.n_mat) {
+    const float4 c = m.matf[threadIdx.x];
+    matc[threadIdx.x][0] = c.x;
+    matc[threadIdx.x][1] = c.y;
+    matc[threadIdx.x][2] = c.z;
+  }
+  float dot0 = 0.f, dot1 = 0.f, dot2 = 0.f;
+  const int b = blockIdx.x;
+  const int nn = m.blk.max_local;
+  if (b < m.blk.n_blk) {
+    union {
+      uint4 v[RW];
+      Rec r;
+    } u;
+    const uint4* rp = reinterpret_cast<const uint4*>(m.rec) + (int64_t)b * kLoBlock * RW + threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < RW; ++q) u.v[q] = __ldcs(rp + q * kLoBlock);
+    const int64_t n0 = (int64_t)b * nn;
+    int32_t raw[kLoNodesPerThread];
+#pragma unroll
+    for (int j = 0; j < kLoNodesPerThread; ++j) {
+      const int i = threadIdx.x + j * kLoBlock;
+      raw[j] = (i < nn) ? __ldcs(m.blk.nodes + n0 + i) : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      if (!(act & (1u << r))) continue;
+      const SD* d = reinterpret_cast<const SD*>(a.d[r]);
+      float* xs = sm + 6 * nn * r;
+      float* ys = xs + 3 * nn;
+      float xv[kLoNodesPerThread][3];
+#pragma unroll
+      for (int j = 0; j < kLoNodesPerThread; ++j) {
+        const int i = threadIdx.x + j * kLoBlock;
+        if (i < nn) load3(d + 4 * (int64_t)(raw[j] & 0x7fffffff), xv[j][0], xv[j][1], xv[j][2]);
+      }
+#pragma unroll
+      for (int j = 0; j < kLoNodesPerThread; ++j) {
+        const int i = threadIdx.x + j * kLoBlock;
+        if (i < nn) {
+          xs[3 * i] = xv[j][0];
+          xs[3 * i + 1] = xv[j][1];
+          xs[3 * i + 2] = xv[j][2];
+          ys[3 * i] = 0.f;
+          ys[3 * i + 1] = 0.f;
+          ys[3 * i + 2] = 0.f;
+        }
+      }
+    }
+    __syncthreads();
+    {
+      float g[3][3];
+#pragma unroll
+      for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) g[mm][i] = to_f(u.r.g[3 * mm + i]);
+      const float V = u.r.vol;
+      const int mt = u.r.mat;
+      const float lamS = matc[mt][0] * V, muS = matc[mt][1] * V, mS = matc[mt][2] * V;
+#pragma unroll 1
+      for (int r = 0; r < 3; ++r) {
+        if (!(act & (1u << r))) continue;
+        const float* xs = sm + 6 * nn * r;
+        float* ys = sm + 6 * nn * r + 3 * nn;
+        float wv[10][3], f[10][3];
+#pragma unroll
+        for (int k = 0; k < 10; ++k)
+#pragma unroll
+          for (int i = 0; i < 3; ++i) wv[k][i] = xs[3 * u.r.lc[k] + i];
+        stiffness_apply<float>(wv, g, lamS, muS, f);
+        mass_apply<float>(wv, mS, f);
+        float dt = 0.f;
+#pragma unroll
+        for (int k = 0; k < 10; ++k)
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            atomicAdd(ys + 3 * u.r.lc[k] + i, f[k][i]);
+            dt = fmaf(wv[k][i], f[k][i], dt);
+          }
+        if (r == 0)
+          dot0 = dt;
+        else if (r == 1)
+          dot1 = dt;
+        else
+          dot2 = dt;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      if (!(act & (1u << r))) continue;
+      const float* ys = sm + 6 * nn * r + 3 * nn;
+      float* w = a.w[r];
+#pragma unroll
+      for (int j = 0; j < kLoNodesPerThread; ++j) {
+        const int i = threadIdx.x + j * kLoBlock;
+        const int64_t g = raw[j] & 0x7fffffff;
+        if (i < nn && g != m.N) {  // padding entries name the dummy node N: skip them
+          if (raw[j] < 0) {
+            w[3 * g] = ys[3 * i];
+            w[3 * g + 1] = ys[3 * i + 1];
+            w[3 * g + 2] = ys[3 * i + 2];
+          } else {
+            atomicAdd(w + 3 * g, ys[3 * i]);
+            atomicAdd(w + 3 * g + 1, ys[3 * i + 1]);
+            atomicAdd(w + 3 * g + 2, ys[3 * i + 2]);
+          }
+        }
+      }
+    }
+  } else {
+    // absorbing faces: (2/dt) C_abs d, per right-hand side
+    const int64_t fc = (int64_t)(b - m.blk.n_blk) * kLoBlock + threadIdx.x;
+    if (fc < m.F && m.fgeo[5 * m.F + fc] > 0.5f) {
+      const float sc2 = m.face_c;
+      const float As = sc2 * m.fgeo[fc], Ad = sc2 * m.fgeo[m.F + fc];
+      const float n[3] = {m.fgeo[2 * m.F + fc], m.fgeo[3 * m.F + fc], m.fgeo[4 * m.F + fc]};
+      int64_t nd[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) nd[k] = m.fnode[k * m.F + fc];
+#pragma unroll 1
+      for (int r = 0; r < 3; ++r) {
+        if (!(act & (1u << r))) continue;
+        const SD* d = reinterpret_cast<const SD*>(r == 0 ? a.d[0] : (r == 1 ? a.d[1] : a.d[2]));
+        float* w = r == 0 ? a.w[0] : (r == 1 ? a.w[1] : a.w[2]);
+        float z[6][3], xin[6][3];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          load3(d + 4 * nd[k], xin[k][0], xin[k][1], xin[k][2]);
+          const float dn = n[0] * xin[k][0] + n[1] * xin[k][1] + n[2] * xin[k][2];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) z[k][i] = fmaf(As, xin[k][i], Ad * dn * n[i]);
+        }
+        float dt = 0.f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const float Zv = z[0][i] + z[1][i] + z[2][i];
+          const float Ze = z[3][i] + z[4][i] + z[5][i];
+          float yf[6];
+          yf[0] = 7.f * z[0][i] - Zv - 4.f * z[4][i];
+          yf[1] = 7.f * z[1][i] - Zv - 4.f * z[5][i];
+          yf[2] = 7.f * z[2][i] - Zv - 4.f * z[3][i];
+          yf[3] = 16.f * (z[3][i] + Ze) - 4.f * z[2][i];
+          yf[4] = 16.f * (z[4][i] + Ze) - 4.f * z[0][i];
+          yf[5] = 16.f * (z[5][i] + Ze) - 4.f * z[1][i];
+#pragma unroll
+          for (int k = 0; k < 6; ++k) {
+            atomicAdd(w + 3 * nd[k] + i, yf[k]);
+            dt = fmaf(xin[k][i], yf[k], dt);
+          }
+        }
+        if (r == 0)
+          dot0 = dt;
+        else if (r == 1)
+          dot1 = dt;
+        else
+          dot2 = dt;
+      }
+    }
+  }
+  if (act & 1u) lo_store_dw(dot0, a.dw_part[0], a.sc[0]);
+  if (act & 2u) lo_store_dw(dot1, a.dw_part[1], a.sc[1]);
+  if (act & 4u) lo_store_dw(dot2, a.dw_part[2], a.sc[2]);
+}
+
 // ------------------------------------------------------------------------------
 // Inner PCG vector kernels (FP32 arithmetic)
 // ------------------------------------------------------------------------------
@@ -949,19 +1131,25 @@ void launch_step_begin(StepState* ss, CgScalars* cg, cudaStream_t s) { step_begi
 void launch_step_end(StepState* ss, const CgScalars* cg, cudaStream_t s) { step_end_kernel<<<1, 1, 0, s>>>(ss, cg); }
 void launch_step_advance(StepState* ss, cudaStream_t s) { step_advance_kernel<<<1, 1, 0, s>>>(ss); }
 
-__global__ void loop_open_kernel(cudaGraphConditionalHandle h, StepState* ss, const CgScalars* cg, int cap) {
-  ss->loops = 0;
-  cudaGraphSetConditional(h, (cap > 0 && ss->active && !((volatile const CgScalars*)cg)->done) ? 1u : 0u);
+__global__ void loop_open_kernel(cudaGraphConditionalHandle h, LoopSet ls, int cap) {
+  bool go = false;
+  for (int i = 0; i < ls.n; ++i) {
+    ls.ss[i]->loops = 0;
+    go = go || (ls.ss[i]->active && !((volatile const CgScalars*)ls.cg[i])->done);
+  }
+  cudaGraphSetConditional(h, (cap > 0 && go) ? 1u : 0u);
 }
-__global__ void loop_next_kernel(cudaGraphConditionalHandle h, StepState* ss, const CgScalars* cg, int cap) {
-  const int n = ++ss->loops;
-  cudaGraphSetConditional(h, (!((volatile const CgScalars*)cg)->done && n < cap) ? 1u : 0u);
+__global__ void loop_next_kernel(cudaGraphConditionalHandle h, LoopSet ls, int cap) {
+  const int n = ++ls.ss[0]->loops;
+  bool go = false;
+  for (int i = 0; i < ls.n; ++i) go = go || !((volatile const CgScalars*)ls.cg[i])->done;
+  cudaGraphSetConditional(h, (go && n < cap) ? 1u : 0u);
 }
-void launch_loop_open(cudaGraphConditionalHandle h, StepState* ss, const CgScalars* cg, int cap, cudaStream_t s) {
-  loop_open_kernel<<<1, 1, 0, s>>>(h, ss, cg, cap);
+void launch_loop_open(cudaGraphConditionalHandle h, const LoopSet& ls, int cap, cudaStream_t s) {
+  loop_open_kernel<<<1, 1, 0, s>>>(h, ls, cap);
 }
-void launch_loop_next(cudaGraphConditionalHandle h, StepState* ss, const CgScalars* cg, int cap, cudaStream_t s) {
-  loop_next_kernel<<<1, 1, 0, s>>>(h, ss, cg, cap);
+void launch_loop_next(cudaGraphConditionalHandle h, const LoopSet& ls, int cap, cudaStream_t s) {
+  loop_next_kernel<<<1, 1, 0, s>>>(h, ls, cap);
 }
 void launch_to_lo(int64_t N, const double* x, void* d, int half_vec, float* w, cudaStream_t s) {
   if (half_vec)
@@ -1616,6 +1804,40 @@ void launch_ebe_lo(int half_geo, int half_vec, const void* lo_view, const void* 
       ebe_lo_launch<float, float>(variant, m, (const float*)d, w, partials, sc, st, outer);
   }
 }
+template <typename SG, typename SD>
+static void ebe_lo3_launch(int variant, const LoView<SG>& m, const Lo3Args& a, cudaStream_t st) {
+  const unsigned g = (unsigned)(m.blk.n_blk + (m.F + kLoBlock - 1) / kLoBlock);
+  const size_t smem = sizeof(float) * 18 * (size_t)m.blk.max_local;
+  static size_t attr[2] = {0, 0};  // per instantiation and occupancy variant
+  const int vi = variant == 1 ? 1 : 0;
+  if (smem > 48 * 1024 && smem > attr[vi]) {
+    if (vi)
+      cudaFuncSetAttribute(ebe_lo3_kernel<SG, SD, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else
+      cudaFuncSetAttribute(ebe_lo3_kernel<SG, SD, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr[vi] = smem;
+  }
+  if (vi)
+    ebe_lo3_kernel<SG, SD, 3><<<g, kLoBlock, smem, st>>>(m, a);
+  else
+    ebe_lo3_kernel<SG, SD, 1><<<g, kLoBlock, smem, st>>>(m, a);
+}
+void launch_ebe_lo3(int half_geo, int half_vec, const void* lo_view, const Lo3Args& a, cudaStream_t st, int variant) {
+  if (half_geo) {
+    const LoView<__half>& m = *(const LoView<__half>*)lo_view;
+    if (half_vec)
+      ebe_lo3_launch<__half, __half>(variant, m, a, st);
+    else
+      ebe_lo3_launch<__half, float>(variant, m, a, st);
+  } else {
+    const LoView<float>& m = *(const LoView<float>*)lo_view;
+    if (half_vec)
+      ebe_lo3_launch<float, __half>(variant, m, a, st);
+    else
+      ebe_lo3_launch<float, float>(variant, m, a, st);
+  }
+}
+
 // ------------------------------------------------------------------------------
 // FP32 right-hand side (its norm sets the relative-residual scale)
 // ------------------------------------------------------------------------------

@@ -171,5 +171,31 @@ def test_host_injected_failures(ctx):
     m.mlp_params(np.full(5443, 1e30))
     m.step(10)
     assert m.stats()["relres_last"] <= 1e-8
-    assert _relerr(m.waveforms(), newmark.analysis(cfg, tol=1e-8)["wave"]) <= 1e-6
+    ref = newmark.analysis(cfg, tol=1e-8, n_steps=18)["wave"]
+    assert _relerr(m.waveforms()[:, :, :18], ref) <= 1e-6
     m.free()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_direction_analyses_in_lockstep_share_the_operator(ctx, prec):
+    """share_dirs = 1: the three direction analyses of one model advance in lockstep and
+    apply the inner operator to their three search directions in one pass; each matches
+    the same analysis run on its own (both at relative residual 1e-8) and the oracle."""
+    cfg = configs.config3_candidate(3, n_steps=30, n_lateral=6)
+    scales = (1.0, -0.7, 1.3)
+    out = {}
+    for share in (0, 1):
+        m = _upload(ctx, cfg)
+        m.set_solver(tol=1e-8, precision=prec, inner_iters=12, guess_order=2, share_dirs=share)
+        for j in range(3):
+            m.set_input(j, scales[j] * cfg["p"])
+        m.run(dirs_mask=7)
+        out[share] = [m.waveforms(j) for j in range(3)]
+        for j in range(3):
+            st = m.stats(j)
+            assert st["steps_done"] == cfg["n_steps"] and st["relres_last"] <= 1e-8
+        m.free()
+    for j in range(3):
+        ref = newmark.analysis(dict(cfg, p=scales[j] * cfg["p"], dir=j), tol=1e-8)["wave"]
+        assert _relerr(out[1][j], ref) <= 1e-6, j
+        assert _relerr(out[1][j], out[0][j]) <= 1e-7, j

@@ -5,10 +5,10 @@
 * tensor-core training gradients (BF16 operands, FP32 accumulation) vs the
   oracle's gradient with the same rounding points, and vs its exact FP64
   backprop (pinned by finite differences);
-* a run that trains on its first steps and then applies the guess converges
-  every step to the same 1e-8 relative residual and reproduces the plain run,
-  and the trained network gains: a lower initial residual than the Newmark
-  predictor and no more outer iterations;
+* a run that trains on its first 500 steps and then applies the guess
+  converges every step to the same 1e-8 relative residual and reproduces the
+  plain run, and the trained network gains: a lower initial residual than the
+  Newmark predictor and fewer outer iterations;
 * the data path (features, sampled nodes, targets, base guess, scales)
   against the oracle's.
 """
@@ -80,44 +80,40 @@ def test_training_gradient_matches_oracle(model):
     assert np.linalg.norm(g - ex_g) <= 3e-2 * np.linalg.norm(ex_g)
 
 
-def test_learned_guess_run_converges_and_matches_plain(ctx):
-    from paper_2404_17754_gb300 import gsw
-
-    cfg = configs.config1(n_steps=120)
+def test_learned_guess_gains_over_the_predictor(ctx):
+    """The realistic model's layers and input on its 120 x 120 m lateral crop (106,875 DOF):
+    500 training steps, then 200 steps with the learned guess on the Newmark predictor,
+    against the same run with the plain predictor (the method without the network).  Both
+    converge every step to relative residual 1e-8 and agree; the trained network stays
+    active, lowers the initial residual at least twofold and saves outer iterations."""
+    cfg = configs.config2(n_steps=700, crop=12)
     runs = {}
     for enable in (0, 1):
         m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
         m.set_time(cfg["dt"], cfg["n_steps"], cfg["band"])
         m.set_input(cfg["dir"], cfg["p"])
-        m.set_solver(tol=1e-8, precision=1, inner_iters=15)
+        m.set_solver(tol=1e-8, precision=2, inner_iters=30, guess_order=0)
         if enable:
-            m.set_learning(True, train_steps=60, batch=4096, iters_per_step=4, lr=2e-3, seed=5)
-        it_train = None
-        m.step(60)
-        s60 = m.stats()
-        if enable:
+            m.mlp_train(500, batch=16384, iters_per_step=2, lr=1e-3, seed=7)
             assert m.mlp_loss() > 0.0
-        m.step(60)
+        else:
+            m.step(500)
+        s0 = m.stats()
+        m.step(200)
         s = m.stats()
-        runs[enable] = dict(wave=m.waveforms(), iters=s["cg_iters_total"] - s60["cg_iters_total"],
-                            r0=(s["init_relres_sum"] - s60["init_relres_sum"]) / 60, relres=s["relres_last"],
+        runs[enable] = dict(wave=m.waveforms(), iters=s["cg_iters_total"] - s0["cg_iters_total"],
+                            r0=(s["init_relres_sum"] - s0["init_relres_sum"]) / 200, relres=s["relres_last"],
                             state=m.mlp_state() if enable else None)
         m.free()
-    assert runs[1]["relres"] <= 1e-8
-    rel = np.linalg.norm(runs[1]["wave"] - runs[0]["wave"]) / np.linalg.norm(runs[0]["wave"])
-    assert rel <= 1e-6
-    ref = newmark.analysis(cfg, tol=1e-8)["wave"]
-    assert np.linalg.norm(runs[1]["wave"] - ref) / np.linalg.norm(ref) <= 1e-6
+    assert runs[0]["relres"] <= 1e-8 and runs[1]["relres"] <= 1e-8
+    assert np.linalg.norm(runs[1]["wave"] - runs[0]["wave"]) <= 1e-6 * np.linalg.norm(runs[0]["wave"])
     st = runs[1]["state"]
-    print("outer iterations over steps 61-120: plain %d, learned %d; mean initial residual: plain %.3e, learned "
-          "%.3e; judge: %s" % (runs[0]["iters"], runs[1]["iters"], runs[0]["r0"], runs[1]["r0"], st))
-    # the trained network gains: it stays active (the judge keeps it), its initial
-    # residual is lower than the predictor's, and the solves need no more outer
-    # iterations than plain CG from the predictor
-    assert st["active"] and st["learned_steps"] >= 50
-    assert st["learned_r0"] < st["plain_r0"]
-    assert runs[1]["r0"] < runs[0]["r0"]
-    assert runs[1]["iters"] <= runs[0]["iters"]
+    print("steps 501-700: outer iterations plain %d, learned %d; mean initial residual plain %.3e, learned %.3e; "
+          "judge %s" % (runs[0]["iters"], runs[1]["iters"], runs[0]["r0"], runs[1]["r0"], st))
+    assert st["active"] and st["learned_steps"] >= 150
+    assert st["learned_r0"] < 0.5 * st["plain_r0"]
+    assert runs[1]["r0"] < 0.5 * runs[0]["r0"]
+    assert runs[1]["iters"] < runs[0]["iters"]
 
 
 @pytest.mark.parametrize("order", [0, 2])
