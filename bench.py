@@ -343,7 +343,7 @@ def run_candidates(args, rank, world, dist):
     ctx.close()
 
 
-def candidates_block(ctx, n_models, warmup, steps, tol, inner, guess_order, seq_models=16):
+def candidates_block(ctx, n_models, warmup, steps, tol, inner, guess_order, seq_models=16, proj_dim=0):
     """Candidate analyses/h of the mixed-ensemble candidates (120 x 120 x 300 m,
     287,451 DOF each, seeded interfaces, one directional analysis each, directions
     cycling x1, x2, x3) in three forms, each timed over `steps` steps after
@@ -364,7 +364,7 @@ def candidates_block(ctx, n_models, warmup, steps, tol, inner, guess_order, seq_
         m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
         m.set_time(cfg["dt"], n_total, cfg["band"])
         m.set_input(cfg["dir"], cfg["p"])
-        m.set_solver(tol=tol, precision=2, inner_iters=inner, guess_order=guess_order)
+        m.set_solver(tol=tol, precision=2, inner_iters=inner, guess_order=guess_order, proj_dim=proj_dim)
         models.append(m)
         dof += 3 * cfg["mesh"]["xyz"].shape[0]
     stream = ctx.stream
@@ -399,7 +399,9 @@ def candidates_block(ctx, n_models, warmup, steps, tol, inner, guess_order, seq_
                             "outer_iters_per_model_step": it, "dof_steps_per_s": dof / t, "gpu_launches": kl,
                             "graph_kernel_nodes_captured": lps,
                             "solver": "flexible CG (FP64, double-word outer operator) + fp16 block-Jacobi PCG "
-                                      "preconditioner, %d iterations; initial guess order %d" % (inner, guess_order)}
+                                      "preconditioner, %d iterations; initial guess %s" % (
+                                          inner, "projection onto the last %d increments" % proj_dim if proj_dim
+                                          else "order %d" % guess_order)}
     for m in models:
         m.set_solver(tol=tol, precision=0, guess_order=0)
         m.reset()
@@ -446,7 +448,8 @@ def candidate_analysis_block(ctx, cfg, n_steps, args, prec):
     for name, mask, share in (("one_direction", 1, 0), ("three_directions_separate", 7, 0),
                               ("three_directions_lockstep", 7, 1)):
         m.set_solver(tol=args.tol, outer_op=OUTER_OPS[args.outer_op], precision=prec, inner_iters=args.inner,
-                     inner_rtol=args.inner_rtol, guess_order=args.guess_order, share_dirs=share)
+                     inner_rtol=args.inner_rtol, guess_order=args.guess_order, share_dirs=share,
+                     proj_dim=args.proj_dim)
         m.run(dirs_mask=mask)  # set-up pass (instances, graph capture); the timed pass repeats it
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -560,6 +563,10 @@ def main():
                          "the mixed modes, FP64 in the FP64 mode")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--proj-dim", type=int, default=0,
+                    help="initial guess by Galerkin projection onto the last k increments (0 = off, 2..8)")
+    ap.add_argument("--inner-variant", type=int, default=-1,
+                    help="launch variant of the inner operator (-1: the autotuner picks)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the plain FP64 form and the candidates block of the default line")
     args = ap.parse_args()
@@ -631,7 +638,7 @@ def main():
     m.set_input(cfg["dir"], cfg["p"])
     prec = {"fp64": 0, "fp32": 1, "fp16": 2}[args.precision]
     m.set_solver(tol=args.tol, outer_op=OUTER_OPS[args.outer_op], precision=prec, inner_iters=args.inner, inner_rtol=args.inner_rtol,
-                     guess_order=args.guess_order)
+                 guess_order=args.guess_order, inner_variant=args.inner_variant, proj_dim=args.proj_dim)
     n_nodes, n_elem, n_faces = mesh["xyz"].shape[0], mesh["conn"].shape[0], mesh["faces"].shape[0]
     dof = 3 * n_nodes
 
@@ -789,7 +796,8 @@ def main():
             cpu = {"value": None, "unit": "DOF*steps/s", "cores": 1, "kind": "oracle", "sample": "failed: " + err}
     cand = ca = None
     if not args.no_extras and args.workload == "realistic":
-        cand = candidates_block(ctx, args.models, args.warmup, args.steps, args.tol, 25, args.guess_order)
+        cand = candidates_block(ctx, args.models, args.warmup, args.steps, args.tol, 25, args.guess_order,
+                                proj_dim=args.proj_dim)
         if args.precision != "fp64":
             ca = candidate_analysis_block(ctx, cfg, args.warmup + args.steps, args, prec)
     out = {
@@ -799,7 +807,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": cfg["name"] if args.workload == "realistic" else "two-layer 100x100x50 m",
                    "dof": dof, "elements": n_elem, "dt": cfg["dt"], "tol": args.tol, "precision": args.precision,
-                   "guess_order": args.guess_order,
+                   "guess_order": args.guess_order, "proj_dim": args.proj_dim,
                    "outer_operator": "FP64" if args.outer_op == "fp64" or (args.outer_op == "auto" and args.precision == "fp64") else "double-word",
                    "solver": "block-Jacobi PCG" if args.precision == "fp64" else
                              ("flexible CG (FP64) + %s block-Jacobi PCG preconditioner, %d iterations" % (

@@ -111,6 +111,14 @@ typedef struct {
                             inner-operator pass (the element records and node lists
                             are read once for all directions; a direction whose solve
                             has converged skips its share); 0 = each advances on its own */
+  int32_t proj_dim;      /* 0, or k = 2..8: each step's initial guess is the Galerkin
+                            projection of its solution onto the last k converged
+                            increments W, du0 = W c with (W^T A W) c = W^T b; A W is kept
+                            from each converged step (b - r, no extra operator pass)
+                            and, in the mixed modes, b comes from the residual pass at
+                            du0 = 0.  Takes precedence over guess_order; excludes the
+                            learned guess.  The history restarts at gsw_reset /
+                            gsw_set_state. */
 } gsw_solver_opts;
 
 typedef struct {
@@ -264,7 +272,7 @@ gsw_status gsw_set_state(gsw_ctx *ctx, int32_t model_id, const double *u, const 
 
 /* Full checkpoint of the model's own analysis, for resuming a run exactly:
  * u, v, a, the step counter and statistics, the receiver history, the
- * increment history of the extrapolated initial guess (guess_order > 0) and,
+ * increment history of the extrapolated or projected initial guess and,
  * with the learned guess enabled, the network's parameters, its Adam moments
  * and step count, its increment history, its training schedule and the
  * judge's state.  buf is a

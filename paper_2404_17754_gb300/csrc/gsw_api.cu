@@ -60,7 +60,7 @@ struct Model {
   std::vector<double> input;
   int dir = 0;
   bool input_set = false;
-  gsw_solver_opts opts = {1e-8, 10000, GSW_PREC_FP64, 20, 8, 6, -1, 0.0, 0, 0, 0};
+  gsw_solver_opts opts = {1e-8, 10000, GSW_PREC_FP64, 20, 8, 6, -1, 0.0, 0, 0, 0, 0};
   int64_t step = 0;
   bool failed = false;
   gsw_stats stats = {};
@@ -83,6 +83,10 @@ struct Model {
   int guess_ring_k = 0;           // degree the ring was sized for
   int* guess_ext = nullptr;       // {count, head} of the ring, on the device
   double* guess_base = nullptr;   // this step's extrapolated guess (base of the learned correction)
+  // Galerkin projection guess: W, Z = A W ([k][3N] each), this step's b, state
+  double *proj_W = nullptr, *proj_Z = nullptr, *proj_b = nullptr;
+  ProjState* proj = nullptr;
+  int proj_k = 0;
   float4* matf = nullptr;      // FP32 material coefficients of the inner operator and the FP32 RHS
   float4* uva = nullptr;       // FP32 copy of u, v, a ([N + 1][3] words) for the FP32 RHS
   unsigned long long iters_mark = 0;   // device inner-iteration counter when timing started
@@ -353,6 +357,19 @@ gsw_status model_state_alloc(gsw_ctx* ctx, Model* m, bool own_precond = true) {
   return GSW_OK;
 }
 
+// Buffers of the projection guess (proj_dim > 0): W, Z, the step's b, state.
+gsw_status proj_alloc(gsw_ctx* ctx, Model* m, int k) {
+  if (k <= 0 || (m->proj && m->proj_k >= k)) return GSW_OK;
+  const size_t n3 = 3 * (size_t)m->N;
+  TRY(alloc_into(ctx, m, &m->proj_W, (size_t)k * n3));
+  TRY(alloc_into(ctx, m, &m->proj_Z, (size_t)k * n3));
+  if (!m->proj_b) TRY(alloc_into(ctx, m, &m->proj_b, n3));
+  if (!m->proj) TRY(alloc_into(ctx, m, &m->proj, 1));
+  CK(cudaMemsetAsync(m->proj, 0, sizeof(ProjState), ctx->stream));
+  m->proj_k = k;
+  return GSW_OK;
+}
+
 gsw_status model_reset(gsw_ctx* ctx, Model* m) {
   const size_t n3 = 3 * (size_t)m->N;
   CK(cudaMemsetAsync(m->u, 0, sizeof(double) * n3, ctx->stream));
@@ -364,6 +381,7 @@ gsw_status model_reset(gsw_ctx* ctx, Model* m) {
   m->failed = false;
   m->stats = gsw_stats{};
   if (m->guess_ext) CK(cudaMemsetAsync(m->guess_ext, 0, 2 * sizeof(int), ctx->stream));  // no increment history
+  if (m->proj) CK(cudaMemsetAsync(m->proj, 0, sizeof(ProjState), ctx->stream));
   if (m->lo_ready) {
     // a wait of the inner operator that ran out failed the run; a reset clears it
     CK(cudaMemsetAsync(&m->isc->err, 0, sizeof(unsigned int), ctx->stream));
@@ -406,8 +424,14 @@ gsw_status step_fp64(gsw_ctx* ctx, Model* m) {
   init.max_iter = m->opts.max_iter;
   CK(cudaMemcpyAsync(m->cg, &init, sizeof(CgScalars), cudaMemcpyHostToDevice, s));
   const int k_guess = m->opts.guess_order;
-  if (k_guess > 0) launch_guess_extrap(m->N, m->guess_ring, k_guess, m->guess_ext, m->v, m->a, m->dt, m->x, s);
-  launch_cg_init(mv, m->b, m->v, m->a, m->x, m->q, m->partials, m->cg, s, k_guess > 0 ? 1 : 0);
+  const bool proj = m->opts.proj_dim > 0;
+  if (proj) {
+    launch_proj_coef(m->N, m->proj_W, m->b, m->proj, m->partials, s);
+    launch_proj_guess(m->N, m->proj_W, m->proj, m->x, s);
+  } else if (k_guess > 0) {
+    launch_guess_extrap(m->N, m->guess_ring, k_guess, m->guess_ext, m->v, m->a, m->dt, m->x, s);
+  }
+  launch_cg_init(mv, m->b, m->v, m->a, m->x, m->q, m->partials, m->cg, s, (k_guess > 0 || proj) ? 1 : 0);
   launch_outer(m, kModeA, mv, m->x, nullptr, nullptr, m->q, 0.0, 0, nullptr, m->cg, s);
   launch_cg_residual(mv, m->b, m->q, m->r, m->z, m->p, m->dinv, m->partials, m->cg, s);
   const int chunk = m->opts.check_every > 0 ? m->opts.check_every : 8;
@@ -458,7 +482,10 @@ gsw_status step_fp64(gsw_ctx* ctx, Model* m) {
                   (long long)m->step, m->opts.tol, h.iter, h.relres);
     return fail(ctx, GSW_E_NAN, "step %lld: non-finite CG residual", (long long)m->step);
   }
-  if (m->opts.guess_order > 0) launch_guess_push(m->N, m->x, m->guess_ring, m->opts.guess_order, m->guess_ext, s);
+  if (proj)
+    launch_proj_push(m->N, m->x, m->b, m->r, m->proj_W, m->proj_Z, m->proj, m->opts.proj_dim, m->partials, s);
+  else if (m->opts.guess_order > 0)
+    launch_guess_push(m->N, m->x, m->guess_ring, m->opts.guess_order, m->guess_ext, s);
   launch_newmark(mv, m->x, m->u, m->v, m->a, m->cg, s);
   launch_record(m->v, m->rec_node, m->rec_w, m->n_rec, m->wave, m->n_steps, (int)m->step, s);
   CK(cudaGetLastError());
@@ -658,6 +685,7 @@ gsw_status make_instance(gsw_ctx* ctx, Model* m, int d, Model** out) {
     TRYI(alloc_into(ctx, c, &c->guess_ring, (size_t)(c->opts.guess_order + 1) * 3 * (size_t)c->N));
     c->guess_ring_k = c->opts.guess_order;
   }
+  TRYI(proj_alloc(ctx, c, c->opts.proj_dim));
   if (m->lo_ready && m->opts.precision != GSW_PREC_FP64) {
     c->lo_half = m->lo_half;
     c->n_blk = m->n_blk;
@@ -974,17 +1002,24 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
       launch_predictor(m->N, m->v, m->a, m->dt, base, s);
   }
   const bool learned = mlp_use_guess(ctx, m, s, base);
-  const bool extrap = !learned && m->opts.guess_order > 0;
+  const bool proj = m->opts.proj_dim > 0;
+  const bool extrap = !learned && !proj && m->opts.guess_order > 0;
   if (extrap && base)
     CK(cudaMemcpyAsync(m->x, base, sizeof(double) * 3 * (size_t)m->N, cudaMemcpyDeviceToDevice, s));
   else if (extrap)
     launch_guess_extrap(m->N, m->guess_ring, m->opts.guess_order, m->guess_ext, m->v, m->a, m->dt, m->x, s);
+  // the projection guess: the residual pass at du0 = 0 gives b exactly, then du0 = W c and r = b - Z c
+  if (proj) CK(cudaMemsetAsync(m->x, 0, sizeof(double) * 3 * (size_t)m->N, s));
   launch_cg_init_mixed(mv, m->w32, m->u, m->v, m->a, m->x, m->p, m->z, m->b, m->r, m->q, m->partials, m->cg, s,
-                       nullptr, (learned || extrap) ? 1 : 0, outer_dword(m) ? 1 : 0);
+                       nullptr, (learned || extrap || proj) ? 1 : 0, outer_dword(m) ? 1 : 0);
   // FP64 residual at the initial guess in one element-by-element pass
   launch_outer(m, kModeRes, mv, m->p, m->z, m->b, m->r, force, m->dir, nullptr, m->cg, s);
+  if (proj) {
+    launch_proj_coef(m->N, m->proj_W, m->r, m->proj, m->partials, s);
+    launch_proj_apply(m->N, m->proj_W, m->proj_Z, m->proj, m->x, m->r, m->proj_b, s);
+  }
   launch_cg_rnorm(mv, m->r, m->partials, m->cg, s);
-  int64_t launches = 4;
+  int64_t launches = proj ? 6 : 4;
   if ((m->timing || m->live_tune) && (int)m->ev_lo.size() < 2 * m->opts.inner_iters) {
     for (int i = (int)m->ev_lo.size(); i < 2 * m->opts.inner_iters; ++i) {
       cudaEvent_t e;
@@ -1063,7 +1098,10 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
     return fail(ctx, GSW_E_NAN, "step %lld: non-finite CG residual", (long long)m->step);
   }
   TRY(mlp_after_step(ctx, m, s, base));
-  if (m->opts.guess_order > 0) launch_guess_push(m->N, m->x, m->guess_ring, m->opts.guess_order, m->guess_ext, s);
+  if (proj)
+    launch_proj_push(m->N, m->x, m->proj_b, m->r, m->proj_W, m->proj_Z, m->proj, m->opts.proj_dim, m->partials, s);
+  else if (m->opts.guess_order > 0)
+    launch_guess_push(m->N, m->x, m->guess_ring, m->opts.guess_order, m->guess_ext, s);
   launch_newmark(mv, m->x, m->u, m->v, m->a, m->cg, s);
   launch_record(m->v, m->rec_node, m->rec_w, m->n_rec, m->wave, m->n_steps, (int)m->step, s);
   CK(cudaGetLastError());
@@ -1161,11 +1199,17 @@ bool issue_device_step_fp64(Model* m, cudaStream_t s, StepState* ss, int outer, 
   cudaMemsetAsync(m->b, 0, sizeof(double) * 3 * (size_t)m->N, s);
   launch_ebe(kModeRhs, mv, m->u, m->v, m->a, m->b, 0.0, m->dir, nullptr, nullptr, s, dr);
   const int k_guess = m->opts.guess_order;
-  if (k_guess > 0) launch_guess_extrap(m->N, m->guess_ring, k_guess, m->guess_ext, m->v, m->a, m->dt, m->x, s, ss);
-  launch_cg_init(mv, m->b, m->v, m->a, m->x, m->q, m->partials, m->cg, s, k_guess > 0 ? 1 : 0, ss);
+  const bool proj = m->opts.proj_dim > 0;
+  if (proj) {
+    launch_proj_coef(m->N, m->proj_W, m->b, m->proj, m->partials, s, ss);
+    launch_proj_guess(m->N, m->proj_W, m->proj, m->x, s, ss);
+  } else if (k_guess > 0) {
+    launch_guess_extrap(m->N, m->guess_ring, k_guess, m->guess_ext, m->v, m->a, m->dt, m->x, s, ss);
+  }
+  launch_cg_init(mv, m->b, m->v, m->a, m->x, m->q, m->partials, m->cg, s, (k_guess > 0 || proj) ? 1 : 0, ss);
   launch_outer(m, kModeA, mv, m->x, nullptr, nullptr, m->q, 0.0, 0, nullptr, m->cg, s);
   launch_cg_residual(mv, m->b, m->q, m->r, m->z, m->p, m->dinv, m->partials, m->cg, s);
-  n->fixed += 6 + (k_guess > 0 ? 1 : 0);
+  n->fixed += 6 + (proj ? 2 : (k_guess > 0 ? 1 : 0));
   // the first residual may already meet the tolerance; every PCG iteration is a loop body
   if (!issue_loop(s, LoopSet{{ss, nullptr, nullptr}, {m->cg, nullptr, nullptr}, 1}, outer + 1, bs, n, 3,
                   [&](cudaStream_t st) {
@@ -1175,12 +1219,48 @@ bool issue_device_step_fp64(Model* m, cudaStream_t s, StepState* ss, int outer, 
       }))
     return false;
   launch_step_end(ss, m->cg, s);
-  if (k_guess > 0) launch_guess_push(m->N, m->x, m->guess_ring, k_guess, m->guess_ext, s, ss);
+  if (proj)
+    launch_proj_push(m->N, m->x, m->b, m->r, m->proj_W, m->proj_Z, m->proj, m->opts.proj_dim, m->partials, s, ss);
+  else if (k_guess > 0)
+    launch_guess_push(m->N, m->x, m->guess_ring, k_guess, m->guess_ext, s, ss);
   launch_newmark(mv, m->x, m->u, m->v, m->a, m->cg, s, ss);
   launch_record(m->v, m->rec_node, m->rec_w, m->n_rec, m->wave, m->n_steps, 0, s, ss);
   launch_step_advance(ss, s);
   n->fixed += 5;
   return true;
+}
+
+// Device-driven start of a mixed step: the initial guess (extrapolation,
+// projection or predictor), the shifted state and the FP64 residual at the
+// guess in one element-by-element pass, and its norm.
+void issue_guess_and_residual(Model* m, cudaStream_t s, StepState* ss, Drive dr, StepLaunches* n) {
+  ModelView mv = m->view();
+  const int k_guess = m->opts.guess_order;
+  const bool proj = m->opts.proj_dim > 0;
+  if (proj)
+    cudaMemsetAsync(m->x, 0, sizeof(double) * 3 * (size_t)m->N, s);
+  else if (k_guess > 0)
+    launch_guess_extrap(m->N, m->guess_ring, k_guess, m->guess_ext, m->v, m->a, m->dt, m->x, s, ss);
+  launch_cg_init_mixed(mv, m->w32, m->u, m->v, m->a, m->x, m->p, m->z, m->b, m->r, m->q, m->partials, m->cg, s, ss,
+                       (k_guess > 0 || proj) ? 1 : 0, outer_dword(m) ? 1 : 0);
+  launch_outer(m, kModeRes, mv, m->p, m->z, m->b, m->r, 0.0, m->dir, nullptr, m->cg, s, dr);
+  if (proj) {
+    launch_proj_coef(m->N, m->proj_W, m->r, m->proj, m->partials, s, ss);
+    launch_proj_apply(m->N, m->proj_W, m->proj_Z, m->proj, m->x, m->r, m->proj_b, s, ss);
+  }
+  launch_cg_rnorm(mv, m->r, m->partials, m->cg, s);
+  n->fixed += 3 + (proj ? 3 : (k_guess > 0 ? 1 : 0));
+}
+// On commit: the converged increment into the guess history.
+void issue_history_push(Model* m, cudaStream_t s, StepState* ss, StepLaunches* n) {
+  if (m->opts.proj_dim > 0) {
+    launch_proj_push(m->N, m->x, m->proj_b, m->r, m->proj_W, m->proj_Z, m->proj, m->opts.proj_dim, m->partials, s,
+                     ss);
+    n->fixed += 1;
+  } else if (m->opts.guess_order > 0) {
+    launch_guess_push(m->N, m->x, m->guess_ring, m->opts.guess_order, m->guess_ext, s, ss);
+    n->fixed += 2;
+  }
 }
 
 // Issues one mixed time step of model m on stream s with no host
@@ -1192,26 +1272,20 @@ bool issue_device_step_fp64(Model* m, cudaStream_t s, StepState* ss, int outer, 
 bool issue_device_step(Model* m, cudaStream_t s, StepState* ss, int outer, cudaStream_t bs, StepLaunches* n) {
   ModelView mv = m->view();
   Drive dr{m->p_dev, ss};
-  const int it = m->opts.inner_iters > 0 ? m->opts.inner_iters : 1;
   const int64_t inner_launches = inner_solve_launches(m, inner_fuses(m, m->lo_variant));
   launch_step_begin(ss, m->cg, s);
   cudaMemsetAsync(m->w32, 0, sizeof(float) * 3 * (size_t)m->N, s);
   launch_rhs_lo(m->lo_half, m->lo_half ? (const void*)&m->lo_h : (const void*)&m->lo_f, m->N, m->u, m->v, m->a,
                 m->uva, m->w32, 0.0, m->dir, s, dr);
-  const int k_guess = m->opts.guess_order;
-  if (k_guess > 0) launch_guess_extrap(m->N, m->guess_ring, k_guess, m->guess_ext, m->v, m->a, m->dt, m->x, s, ss);
-  launch_cg_init_mixed(mv, m->w32, m->u, m->v, m->a, m->x, m->p, m->z, m->b, m->r, m->q, m->partials, m->cg, s, ss,
-                       k_guess > 0 ? 1 : 0, outer_dword(m) ? 1 : 0);
-  launch_outer(m, kModeRes, mv, m->p, m->z, m->b, m->r, 0.0, m->dir, nullptr, m->cg, s, dr);
-  launch_cg_rnorm(mv, m->r, m->partials, m->cg, s);
+  issue_guess_and_residual(m, s, ss, dr, n);
   inner_solve_dev(m, s);
   launch_fcg_first(mv, m->y32, m->r, m->z, m->p, m->partials, m->cg, m->isc, s, outer_dword(m) ? 1 : 0);
   launch_outer(m, kModeA, mv, m->p, nullptr, nullptr, m->q, 0.0, 0, m->partials, m->cg, s);
   launch_fcg_update(mv, m->x, m->r, m->p, m->q, m->partials, m->cg, s, outer_dword(m) ? 1 : 0);
-  n->fixed += 6 + inner_launches + 3 + (k_guess > 0 ? 3 : 0);
+  n->fixed += 3 + inner_launches + 3;
   if (!issue_outer_loop(m, s, ss, outer, bs, n)) return false;
   launch_step_end(ss, m->cg, s);
-  if (k_guess > 0) launch_guess_push(m->N, m->x, m->guess_ring, k_guess, m->guess_ext, s, ss);  // on commit
+  issue_history_push(m, s, ss, n);  // on commit
   launch_newmark(mv, m->x, m->u, m->v, m->a, m->cg, s, ss);
   launch_record(m->v, m->rec_node, m->rec_w, m->n_rec, m->wave, m->n_steps, 0, s, ss);
   launch_step_advance(ss, s);
@@ -1273,14 +1347,8 @@ bool issue_device_step_group(Model* const* g, int n, cudaStream_t s, StepState* 
     cudaMemsetAsync(m->w32, 0, sizeof(float) * 3 * (size_t)m->N, s);
     launch_rhs_lo(m->lo_half, m->lo_half ? (const void*)&m->lo_h : (const void*)&m->lo_f, m->N, m->u, m->v, m->a,
                   m->uva, m->w32, 0.0, m->dir, s, dr);
-    const int k_guess = m->opts.guess_order;
-    if (k_guess > 0)
-      launch_guess_extrap(m->N, m->guess_ring, k_guess, m->guess_ext, m->v, m->a, m->dt, m->x, s, ss + i);
-    launch_cg_init_mixed(mv, m->w32, m->u, m->v, m->a, m->x, m->p, m->z, m->b, m->r, m->q, m->partials, m->cg, s,
-                         ss + i, k_guess > 0 ? 1 : 0, outer_dword(m) ? 1 : 0);
-    launch_outer(m, kModeRes, mv, m->p, m->z, m->b, m->r, 0.0, m->dir, nullptr, m->cg, s, dr);
-    launch_cg_rnorm(mv, m->r, m->partials, m->cg, s);
-    nl->fixed += 6 + (k_guess > 0 ? 3 : 0);
+    issue_guess_and_residual(m, s, ss + i, dr, nl);
+    nl->fixed += 3;
   }
   inner_solve_group_dev(g, n, s);
   for (int i = 0; i < n; ++i) {
@@ -1314,8 +1382,7 @@ bool issue_device_step_group(Model* const* g, int n, cudaStream_t s, StepState* 
     Model* m = g[i];
     ModelView mv = m->view();
     launch_step_end(ss + i, m->cg, s);
-    if (m->opts.guess_order > 0)
-      launch_guess_push(m->N, m->x, m->guess_ring, m->opts.guess_order, m->guess_ext, s, ss + i);
+    issue_history_push(m, s, ss + i, nl);
     launch_newmark(mv, m->x, m->u, m->v, m->a, m->cg, s, ss + i);
     launch_record(m->v, m->rec_node, m->rec_w, m->n_rec, m->wave, m->n_steps, 0, s, ss + i);
     launch_step_advance(ss + i, s);
@@ -1624,6 +1691,16 @@ gsw_status gsw_set_solver(gsw_ctx* ctx, int32_t model_id, const gsw_solver_opts*
     return fail(ctx, GSW_E_INVALID, "guess_order must be 0..%d", kMaxGuessOrder);
   if (opts->outer_op < GSW_OUTER_AUTO || opts->outer_op > GSW_OUTER_DWORD)
     return fail(ctx, GSW_E_INVALID, "outer_op must be 0 (auto), 1 (FP64) or 2 (double-word)");
+  if (opts->proj_dim != 0 && (opts->proj_dim < 2 || opts->proj_dim > kMaxProj))
+    return fail(ctx, GSW_E_INVALID, "proj_dim must be 0 or 2..%d", kMaxProj);
+  if (opts->proj_dim > 0 && m->learn.enable)
+    return fail(ctx, GSW_E_STATE, "the projection guess and the learned guess exclude each other");
+  if (opts->proj_dim > 0) {
+    DeviceGuard g(ctx->device);
+    if (opts->proj_dim != m->opts.proj_dim && m->proj)
+      CK(cudaMemsetAsync(m->proj, 0, sizeof(ProjState), ctx->stream));  // the history restarts
+    TRY(proj_alloc(ctx, m, opts->proj_dim));
+  }
   if (opts->guess_order > 0) {
     DeviceGuard g(ctx->device);
     if (!m->guess_ext) TRY(alloc_into(ctx, m, &m->guess_ext, 2));
@@ -2144,6 +2221,7 @@ gsw_status gsw_set_state(gsw_ctx* ctx, int32_t model_id, const double* u, const 
   CK(cudaMemcpyAsync(m->v, v, bytes, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(m->a, a, bytes, cudaMemcpyHostToDevice, ctx->stream));
   if (m->guess_ext) CK(cudaMemsetAsync(m->guess_ext, 0, 2 * sizeof(int), ctx->stream));  // no increment history
+  if (m->proj) CK(cudaMemsetAsync(m->proj, 0, sizeof(ProjState), ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   m->step = step;
   m->failed = false;
@@ -2162,6 +2240,7 @@ struct CkptHeader {
   int32_t dir, guess_order, ring_count, ring_head;
   int32_t has_mlp, hist_head, hist_count, adam_t;
   int32_t mlp_off, failed;
+  int32_t proj_dim, pad_;
   int64_t std_r0_n, mlp_r0_n, applied, inner_done;
   double std_r0[5], mlp_r0[5];
   gsw_stats stats;
@@ -2173,6 +2252,7 @@ size_t ckpt_bytes(const Model* m, bool mlp) {
   const size_t n3 = 3 * (size_t)m->N;
   size_t b = sizeof(CkptHeader) + 3 * n3 * sizeof(double) + (size_t)m->n_rec * 3 * m->n_steps * sizeof(double);
   if (m->opts.guess_order > 0) b += (size_t)(m->opts.guess_order + 1) * n3 * sizeof(double);
+  if (m->opts.proj_dim > 0) b += 2 * (size_t)m->opts.proj_dim * n3 * sizeof(double) + sizeof(ProjState);
   if (mlp) b += 3 * (size_t)kMlpParams * sizeof(float) + 4 * n3 * sizeof(double);
   return b;
 }
@@ -2203,6 +2283,7 @@ gsw_status gsw_checkpoint(gsw_ctx* ctx, int32_t model_id, void* buf, size_t* byt
   h.step = m->step;
   h.dir = m->dir;
   h.guess_order = m->opts.guess_order;
+  h.proj_dim = m->opts.proj_dim;
   h.has_mlp = mlp ? 1 : 0;
   h.hist_head = m->hist_head;
   h.hist_count = m->hist_count;
@@ -2241,6 +2322,11 @@ gsw_status gsw_checkpoint(gsw_ctx* ctx, int32_t model_id, void* buf, size_t* byt
   CK(d2h(m->a, n3 * sizeof(double)));
   CK(d2h(m->wave, (size_t)m->n_rec * 3 * m->n_steps * sizeof(double)));
   if (m->opts.guess_order > 0) CK(d2h(m->guess_ring, (size_t)(m->opts.guess_order + 1) * n3 * sizeof(double)));
+  if (m->opts.proj_dim > 0) {
+    CK(d2h(m->proj_W, (size_t)m->opts.proj_dim * n3 * sizeof(double)));
+    CK(d2h(m->proj_Z, (size_t)m->opts.proj_dim * n3 * sizeof(double)));
+    CK(d2h(m->proj, sizeof(ProjState)));
+  }
   if (mlp) {
     CK(d2h(m->theta, kMlpParams * sizeof(float)));
     CK(d2h(m->adam_m, kMlpParams * sizeof(float)));
@@ -2268,9 +2354,9 @@ gsw_status gsw_restore(gsw_ctx* ctx, int32_t model_id, const void* buf, size_t b
     return fail(ctx, GSW_E_INVALID, "checkpoint of a different model or time set-up");
   if (h.dir != m->dir)
     return fail(ctx, GSW_E_INVALID, "checkpoint of input direction %d, model set to direction %d", h.dir, m->dir);
-  if (h.guess_order != m->opts.guess_order)
-    return fail(ctx, GSW_E_INVALID, "checkpoint taken with guess_order %d, model set to %d", h.guess_order,
-                m->opts.guess_order);
+  if (h.guess_order != m->opts.guess_order || h.proj_dim != m->opts.proj_dim)
+    return fail(ctx, GSW_E_INVALID, "checkpoint taken with guess_order %d / proj_dim %d, model set to %d / %d",
+                h.guess_order, h.proj_dim, m->opts.guess_order, m->opts.proj_dim);
   if (h.has_mlp && !(m->learn.enable && m->mlp_ready))
     return fail(ctx, GSW_E_STATE, "checkpoint holds a learned guess: enable learning on the model first");
   if (h.step < 0 || h.step > m->n_steps || h.bytes != bytes || bytes != ckpt_bytes(m, h.has_mlp != 0))
@@ -2292,6 +2378,11 @@ gsw_status gsw_restore(gsw_ctx* ctx, int32_t model_id, const void* buf, size_t b
     CK(h2d(m->guess_ring, (size_t)(m->opts.guess_order + 1) * n3 * sizeof(double)));
     const int ext[2] = {h.ring_count, h.ring_head};
     CK(cudaMemcpyAsync(m->guess_ext, ext, sizeof(ext), cudaMemcpyHostToDevice, s));
+  }
+  if (m->opts.proj_dim > 0) {
+    CK(h2d(m->proj_W, (size_t)m->opts.proj_dim * n3 * sizeof(double)));
+    CK(h2d(m->proj_Z, (size_t)m->opts.proj_dim * n3 * sizeof(double)));
+    CK(h2d(m->proj, sizeof(ProjState)));
   }
   if (h.has_mlp) {
     CK(h2d(m->theta, kMlpParams * sizeof(float)));
@@ -2442,6 +2533,8 @@ gsw_status gsw_set_learning(gsw_ctx* ctx, int32_t model_id, const gsw_learn_opts
   if (opts->enable) {
     if (m->opts.precision == GSW_PREC_FP64)
       return fail(ctx, GSW_E_STATE, "the learned guess runs with the mixed-precision solver");
+    if (m->opts.proj_dim > 0)
+      return fail(ctx, GSW_E_STATE, "the projection guess and the learned guess exclude each other");
     if (opts->train_steps < 5 || opts->batch < 64 || opts->batch > 65536 || opts->iters_per_step < 0 ||
         !(opts->lr > 0.f))
       return fail(ctx, GSW_E_INVALID, "need train_steps >= 5, 64 <= batch <= 65536, iters_per_step >= 0, lr > 0");
@@ -2464,6 +2557,8 @@ gsw_status gsw_mlp_train(gsw_ctx* ctx, int32_t model_id, int32_t n_train_steps, 
   if (m->opts.precision == GSW_PREC_FP64)
     return fail(ctx, GSW_E_STATE, "the learned guess runs with the mixed-precision solver");
   if (!opts->enable) return fail(ctx, GSW_E_INVALID, "opts->enable must be 1");
+  if (m->opts.proj_dim > 0)
+    return fail(ctx, GSW_E_STATE, "the projection guess and the learned guess exclude each other");
   if (n_train_steps < 5 || m->step + n_train_steps > m->n_steps)
     return fail(ctx, GSW_E_INVALID, "need 5 <= n_train_steps <= the steps left (%lld)",
                 (long long)(m->n_steps - m->step));

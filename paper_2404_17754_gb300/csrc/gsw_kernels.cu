@@ -1041,6 +1041,191 @@ __global__ void guess_advance_kernel(int* ext, int S, const StepState* ss) {
   ext[1] = (ext[1] + 1) % S;
   ext[0] = ext[0] < S ? ext[0] + 1 : S;
 }
+// ------------------------------------------------------------------------------
+// Initial guess by Galerkin projection onto the last k converged increments
+// ------------------------------------------------------------------------------
+//
+// W = [du_{n-1} .. du_{n-k}] (ring of slots), Z = A W stored as the converged
+// steps' b - r (no operator application), G = (W^T Z + Z^T W) / 2 kept by
+// slot.  At a step with right-hand side b: c = G^+ W^T b (eigenvalues below
+// 1e-12 of the largest dropped), du0 = W c and r0 = b - Z c: the A-norm
+// optimal combination of the past increments.
+
+// Cyclic Jacobi eigen-solve of the symmetric n x n system G c = g (n <=
+// kMaxProj) in one thread, eigenvalues below rel * lambda_max dropped.
+__device__ void proj_solve(const double* G, const double* g, int n, double* c) {
+  double A[kMaxProj][kMaxProj], V[kMaxProj][kMaxProj];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      A[i][j] = G[i * kMaxProj + j];
+      V[i][j] = (i == j) ? 1.0 : 0.0;
+    }
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int i = 0; i < n; ++i) {
+      diag += A[i][i] * A[i][i];
+      for (int j = i + 1; j < n; ++j) off += A[i][j] * A[i][j];
+    }
+    if (off <= 1e-30 * diag) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        if (A[p][q] == 0.0) continue;
+        const double th = 0.5 * (A[q][q] - A[p][p]) / A[p][q];
+        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+        for (int k = 0; k < n; ++k) {  // rotate columns p, q
+          const double akp = A[k][p], akq = A[k][q];
+          A[k][p] = cs * akp - sn * akq;
+          A[k][q] = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < n; ++k) {  // rotate rows p, q
+          const double apk = A[p][k], aqk = A[q][k];
+          A[p][k] = cs * apk - sn * aqk;
+          A[q][k] = sn * apk + cs * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = V[k][p], vkq = V[k][q];
+          V[k][p] = cs * vkp - sn * vkq;
+          V[k][q] = sn * vkp + cs * vkq;
+        }
+      }
+  }
+  double lmax = 0.0;
+  for (int i = 0; i < n; ++i) lmax = fmax(lmax, A[i][i]);
+  for (int i = 0; i < n; ++i) c[i] = 0.0;
+  for (int e = 0; e < n; ++e) {
+    const double lam = A[e][e];
+    if (!(lam > 1e-12 * lmax)) continue;
+    double proj = 0.0;
+    for (int i = 0; i < n; ++i) proj += V[i][e] * g[i];
+    proj /= lam;
+    for (int i = 0; i < n; ++i) c[i] += V[i][e] * proj;
+  }
+}
+
+// g = W^T b over the filled slots, then c (in ps) by the projection solve.
+__global__ void proj_coef_kernel(int64_t n3, const double* __restrict__ W, const double* __restrict__ b,
+                                 ProjState* ps, double* partials, const StepState* ss) {
+  if (ss != nullptr && !((volatile const StepState*)ss)->active) return;
+  const int cnt = ((volatile const ProjState*)ps)->count;
+  double acc[kMaxProj];
+#pragma unroll
+  for (int j = 0; j < kMaxProj; ++j) acc[j] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    const double bi = b[i];
+#pragma unroll
+    for (int j = 0; j < kMaxProj; ++j)
+      if (j < cnt) acc[j] = fma(W[(int64_t)j * n3 + i], bi, acc[j]);
+  }
+  double out[kMaxProj];
+  if (last_block_reduce<kMaxProj>(acc, partials, &ps->counter, out) && threadIdx.x == 0) {
+    if (cnt > 0) proj_solve(ps->G, out, cnt, ps->c);
+    for (int j = cnt; j < kMaxProj; ++j) ps->c[j] = 0.0;
+  }
+}
+
+// x = W c, keep b, r = b - Z c (r holds b on entry).
+__global__ void proj_apply_kernel(int64_t n3, const double* __restrict__ W, const double* __restrict__ Z,
+                                  const ProjState* ps, double* __restrict__ x, double* __restrict__ r,
+                                  double* __restrict__ bkeep, const StepState* ss) {
+  if (ss != nullptr && !((volatile const StepState*)ss)->active) return;
+  const int cnt = ((volatile const ProjState*)ps)->count;
+  double c[kMaxProj];
+#pragma unroll
+  for (int j = 0; j < kMaxProj; ++j) c[j] = ((volatile const ProjState*)ps)->c[j];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    double xi = 0.0, zi = 0.0;
+#pragma unroll
+    for (int j = 0; j < kMaxProj; ++j)
+      if (j < cnt) {
+        xi = fma(c[j], W[(int64_t)j * n3 + i], xi);
+        zi = fma(c[j], Z[(int64_t)j * n3 + i], zi);
+      }
+    const double bi = r[i];
+    bkeep[i] = bi;
+    x[i] = xi;
+    r[i] = bi - zi;
+  }
+}
+
+// x = W c only (the FP64 solver forms its own first residual).
+__global__ void proj_guess_kernel(int64_t n3, const double* __restrict__ W, const ProjState* ps, double* __restrict__ x,
+                                  const StepState* ss) {
+  if (ss != nullptr && !((volatile const StepState*)ss)->active) return;
+  const int cnt = ((volatile const ProjState*)ps)->count;
+  double c[kMaxProj];
+#pragma unroll
+  for (int j = 0; j < kMaxProj; ++j) c[j] = ((volatile const ProjState*)ps)->c[j];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    double xi = 0.0;
+#pragma unroll
+    for (int j = 0; j < kMaxProj; ++j)
+      if (j < cnt) xi = fma(c[j], W[(int64_t)j * n3 + i], xi);
+    x[i] = xi;
+  }
+}
+
+// Push the converged increment: slot `head` of W gets du, of Z gets b - r
+// (= A du), and the slot's row and column of G are recomputed from the dots
+// with every filled slot; count and head advance.
+__global__ void proj_push_kernel(int64_t n3, const double* __restrict__ du, const double* __restrict__ b,
+                                 const double* __restrict__ r, double* __restrict__ W, double* __restrict__ Z,
+                                 ProjState* ps, int k, double* partials, const StepState* ss) {
+  if (ss != nullptr && !((volatile const StepState*)ss)->commit) return;
+  const int head = ((volatile const ProjState*)ps)->head;
+  const int cnt0 = ((volatile const ProjState*)ps)->count;
+  const int cnt = cnt0 < k ? cnt0 + 1 : k;  // slots filled after this push
+  double acc[2 * kMaxProj];
+#pragma unroll
+  for (int j = 0; j < 2 * kMaxProj; ++j) acc[j] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    const double di = du[i], zi = b[i] - r[i];
+    W[(int64_t)head * n3 + i] = di;
+    Z[(int64_t)head * n3 + i] = zi;
+#pragma unroll
+    for (int j = 0; j < kMaxProj; ++j)
+      if (j < cnt) {
+        const double wj = j == head ? di : W[(int64_t)j * n3 + i];
+        const double zj = j == head ? zi : Z[(int64_t)j * n3 + i];
+        acc[j] = fma(di, zj, acc[j]);
+        acc[kMaxProj + j] = fma(wj, zi, acc[kMaxProj + j]);
+      }
+  }
+  double out[2 * kMaxProj];
+  if (last_block_reduce<2 * kMaxProj>(acc, partials, &ps->counter, out) && threadIdx.x == 0) {
+    for (int j = 0; j < kMaxProj; ++j) {
+      const double gj = j < cnt ? 0.5 * (out[j] + out[kMaxProj + j]) : 0.0;
+      ps->G[head * kMaxProj + j] = gj;
+      ps->G[j * kMaxProj + head] = gj;
+    }
+    ps->count = cnt;
+    ps->head = (head + 1) % k;
+  }
+}
+
+// The W/Z slots are in ring order, but the projection is invariant to the
+// order of its basis, so the dots and combinations run over slots 0..count-1.
+static int proj_blocks(int64_t n3) {
+  int g = node_blocks(n3);
+  return g < 152 ? g : 152;  // 2 * kMaxProj partials per CTA within the partials buffer
+}
+void launch_proj_coef(int64_t N, const double* W, const double* b, ProjState* ps, double* partials, cudaStream_t s,
+                      const StepState* ss) {
+  proj_coef_kernel<<<proj_blocks(3 * N), kNodeThreads, 0, s>>>(3 * N, W, b, ps, partials, ss);
+}
+void launch_proj_apply(int64_t N, const double* W, const double* Z, const ProjState* ps, double* x, double* r,
+                       double* bkeep, cudaStream_t s, const StepState* ss) {
+  proj_apply_kernel<<<node_blocks(3 * N), kNodeThreads, 0, s>>>(3 * N, W, Z, ps, x, r, bkeep, ss);
+}
+void launch_proj_guess(int64_t N, const double* W, const ProjState* ps, double* x, cudaStream_t s,
+                       const StepState* ss) {
+  proj_guess_kernel<<<node_blocks(3 * N), kNodeThreads, 0, s>>>(3 * N, W, ps, x, ss);
+}
+void launch_proj_push(int64_t N, const double* du, const double* b, const double* r, double* W, double* Z,
+                      ProjState* ps, int k, double* partials, cudaStream_t s, const StepState* ss) {
+  proj_push_kernel<<<proj_blocks(3 * N), kNodeThreads, 0, s>>>(3 * N, du, b, r, W, Z, ps, k, partials, ss);
+}
+
 void launch_guess_extrap(int64_t N, const double* ring, int k, const int* ext, const double* v, const double* a,
                          double dt, double* x, cudaStream_t s, const StepState* ss) {
   guess_extrap_kernel<<<node_blocks(3 * N), kNodeThreads, 0, s>>>(3 * N, ring, k + 1, ext, k, v, a, dt, x, ss);

@@ -199,3 +199,70 @@ def test_direction_analyses_in_lockstep_share_the_operator(ctx, prec):
         ref = newmark.analysis(dict(cfg, p=scales[j] * cfg["p"], dir=j), tol=1e-8)["wave"]
         assert _relerr(out[1][j], ref) <= 1e-6, j
         assert _relerr(out[1][j], out[0][j]) <= 1e-7, j
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_projection_guess_converges_to_the_oracle_on_every_path(ctx, prec):
+    """proj_dim = 6: the initial guess is the Galerkin projection onto the last six
+    increments.  Host-driven steps, batched steps and direction analyses in lockstep all
+    reach the oracle's solution (1e-9 at tolerance 1e-12 in FP64, 1e-6 at 1e-8 mixed)."""
+    cfg = configs.small_box(nx=4, ny=3, n_steps=30, seed=9)
+    tol = 1e-12 if prec == 0 else 1e-8
+    bar = 1e-9 if prec == 0 else 1e-6
+    ref = newmark.analysis(cfg, tol=tol)["wave"]
+    m = _upload(ctx, cfg)
+    m.set_input(cfg["dir"], cfg["p"])
+    m.set_solver(tol=tol, precision=prec, inner_iters=12, proj_dim=6)
+    m.step(cfg["n_steps"])
+    assert m.stats()["relres_last"] <= tol
+    assert _relerr(m.waveforms(), ref) <= bar
+    m.run()  # batched (device-driven) steps
+    assert _relerr(m.waveforms(), ref) <= bar
+    if prec != 0:
+        m.set_solver(tol=tol, precision=prec, inner_iters=12, proj_dim=6, share_dirs=1)
+        for j in range(3):
+            m.set_input(j, cfg["p"])
+        m.run(dirs_mask=7)
+        assert _relerr(m.waveforms(cfg["dir"]), ref) <= bar
+        for j in range(3):
+            assert _relerr(m.waveforms(j), newmark.analysis(dict(cfg, dir=j), tol=tol)["wave"]) <= bar
+    m.free()
+
+
+def test_projection_guess_checkpoint_and_quality(ctx):
+    from paper_2404_17754_gb300 import gsw
+
+    cfg = configs.small_box(nx=4, ny=3, n_steps=40, seed=5)
+    m = _upload(ctx, cfg)
+    m.set_input(cfg["dir"], cfg["p"])
+    m.set_solver(tol=1e-12, precision=0, proj_dim=6)
+    m.step(15)
+    ck = m.checkpoint()
+    m.step(10)
+    w_ref, s_ref = m.waveforms(), m.stats()
+    m.reset()
+    m.step(2)
+    m.restore(ck)
+    m.step(10)
+    assert m.stats()["cg_iters_total"] == s_ref["cg_iters_total"]  # the projection history resumed
+    assert _relerr(m.waveforms(), w_ref) <= 1e-12
+    with pytest.raises(gsw.GswError) as ei:
+        m.set_learning(True, train_steps=10, batch=256)
+    assert ei.value.status == gsw.E_STATE
+    m.free()
+    # its initial residual against the quartic extrapolation's (host-driven mixed steps)
+    cfg = configs.config1(n_steps=80)
+    r0 = {}
+    for name, kw in (("quartic", dict(guess_order=4)), ("projection", dict(proj_dim=8))):
+        m = _upload(ctx, cfg)
+        m.set_input(cfg["dir"], cfg["p"])
+        m.set_solver(tol=1e-8, precision=2, inner_iters=20, **kw)
+        m.step(20)
+        a = m.stats()["init_relres_sum"]
+        m.step(60)
+        r0[name] = (m.stats()["init_relres_sum"] - a) / 60
+        assert _relerr(m.waveforms(), newmark.analysis(cfg, tol=1e-8)["wave"]) <= 1e-6
+        m.free()
+    print("mean initial relative residual, steps 21-80: quartic %.3e, projection onto 8 increments %.3e"
+          % (r0["quartic"], r0["projection"]))
+    assert r0["projection"] <= 1.1 * r0["quartic"]
