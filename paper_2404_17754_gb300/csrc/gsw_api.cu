@@ -84,7 +84,7 @@ struct Model {
   int* guess_ext = nullptr;       // {count, head} of the ring, on the device
   double* guess_base = nullptr;   // this step's extrapolated guess (base of the learned correction)
   // Galerkin projection guess: W, Z = A W ([k][3N] each), this step's b, state
-  double *proj_W = nullptr, *proj_Z = nullptr, *proj_b = nullptr;
+  double *proj_W = nullptr, *proj_Z = nullptr, *proj_b = nullptr, *proj_part = nullptr;
   ProjState* proj = nullptr;
   int proj_k = 0;
   float4* matf = nullptr;      // FP32 material coefficients of the inner operator and the FP32 RHS
@@ -364,6 +364,7 @@ gsw_status proj_alloc(gsw_ctx* ctx, Model* m, int k) {
   TRY(alloc_into(ctx, m, &m->proj_W, (size_t)k * n3));
   TRY(alloc_into(ctx, m, &m->proj_Z, (size_t)k * n3));
   if (!m->proj_b) TRY(alloc_into(ctx, m, &m->proj_b, n3));
+  if (!m->proj_part) TRY(alloc_into(ctx, m, &m->proj_part, 2 * (size_t)kMaxProj * kMaxNodeBlocks));
   if (!m->proj) TRY(alloc_into(ctx, m, &m->proj, 1));
   CK(cudaMemsetAsync(m->proj, 0, sizeof(ProjState), ctx->stream));
   m->proj_k = k;
@@ -426,7 +427,7 @@ gsw_status step_fp64(gsw_ctx* ctx, Model* m) {
   const int k_guess = m->opts.guess_order;
   const bool proj = m->opts.proj_dim > 0;
   if (proj) {
-    launch_proj_coef(m->N, m->proj_W, m->b, m->proj, m->partials, s);
+    launch_proj_coef(m->N, m->proj_W, m->b, m->proj, m->proj_part, s);
     launch_proj_guess(m->N, m->proj_W, m->proj, m->x, s);
   } else if (k_guess > 0) {
     launch_guess_extrap(m->N, m->guess_ring, k_guess, m->guess_ext, m->v, m->a, m->dt, m->x, s);
@@ -483,7 +484,7 @@ gsw_status step_fp64(gsw_ctx* ctx, Model* m) {
     return fail(ctx, GSW_E_NAN, "step %lld: non-finite CG residual", (long long)m->step);
   }
   if (proj)
-    launch_proj_push(m->N, m->x, m->b, m->r, m->proj_W, m->proj_Z, m->proj, m->opts.proj_dim, m->partials, s);
+    launch_proj_push(m->N, m->x, m->b, m->r, m->proj_W, m->proj_Z, m->proj, m->opts.proj_dim, m->proj_part, s);
   else if (m->opts.guess_order > 0)
     launch_guess_push(m->N, m->x, m->guess_ring, m->opts.guess_order, m->guess_ext, s);
   launch_newmark(mv, m->x, m->u, m->v, m->a, m->cg, s);
@@ -1015,7 +1016,7 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
   // FP64 residual at the initial guess in one element-by-element pass
   launch_outer(m, kModeRes, mv, m->p, m->z, m->b, m->r, force, m->dir, nullptr, m->cg, s);
   if (proj) {
-    launch_proj_coef(m->N, m->proj_W, m->r, m->proj, m->partials, s);
+    launch_proj_coef(m->N, m->proj_W, m->r, m->proj, m->proj_part, s);
     launch_proj_apply(m->N, m->proj_W, m->proj_Z, m->proj, m->x, m->r, m->proj_b, s);
   }
   launch_cg_rnorm(mv, m->r, m->partials, m->cg, s);
@@ -1099,7 +1100,7 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
   }
   TRY(mlp_after_step(ctx, m, s, base));
   if (proj)
-    launch_proj_push(m->N, m->x, m->proj_b, m->r, m->proj_W, m->proj_Z, m->proj, m->opts.proj_dim, m->partials, s);
+    launch_proj_push(m->N, m->x, m->proj_b, m->r, m->proj_W, m->proj_Z, m->proj, m->opts.proj_dim, m->proj_part, s);
   else if (m->opts.guess_order > 0)
     launch_guess_push(m->N, m->x, m->guess_ring, m->opts.guess_order, m->guess_ext, s);
   launch_newmark(mv, m->x, m->u, m->v, m->a, m->cg, s);
@@ -1201,7 +1202,7 @@ bool issue_device_step_fp64(Model* m, cudaStream_t s, StepState* ss, int outer, 
   const int k_guess = m->opts.guess_order;
   const bool proj = m->opts.proj_dim > 0;
   if (proj) {
-    launch_proj_coef(m->N, m->proj_W, m->b, m->proj, m->partials, s, ss);
+    launch_proj_coef(m->N, m->proj_W, m->b, m->proj, m->proj_part, s, ss);
     launch_proj_guess(m->N, m->proj_W, m->proj, m->x, s, ss);
   } else if (k_guess > 0) {
     launch_guess_extrap(m->N, m->guess_ring, k_guess, m->guess_ext, m->v, m->a, m->dt, m->x, s, ss);
@@ -1220,7 +1221,7 @@ bool issue_device_step_fp64(Model* m, cudaStream_t s, StepState* ss, int outer, 
     return false;
   launch_step_end(ss, m->cg, s);
   if (proj)
-    launch_proj_push(m->N, m->x, m->b, m->r, m->proj_W, m->proj_Z, m->proj, m->opts.proj_dim, m->partials, s, ss);
+    launch_proj_push(m->N, m->x, m->b, m->r, m->proj_W, m->proj_Z, m->proj, m->opts.proj_dim, m->proj_part, s, ss);
   else if (k_guess > 0)
     launch_guess_push(m->N, m->x, m->guess_ring, k_guess, m->guess_ext, s, ss);
   launch_newmark(mv, m->x, m->u, m->v, m->a, m->cg, s, ss);
@@ -1245,7 +1246,7 @@ void issue_guess_and_residual(Model* m, cudaStream_t s, StepState* ss, Drive dr,
                        (k_guess > 0 || proj) ? 1 : 0, outer_dword(m) ? 1 : 0);
   launch_outer(m, kModeRes, mv, m->p, m->z, m->b, m->r, 0.0, m->dir, nullptr, m->cg, s, dr);
   if (proj) {
-    launch_proj_coef(m->N, m->proj_W, m->r, m->proj, m->partials, s, ss);
+    launch_proj_coef(m->N, m->proj_W, m->r, m->proj, m->proj_part, s, ss);
     launch_proj_apply(m->N, m->proj_W, m->proj_Z, m->proj, m->x, m->r, m->proj_b, s, ss);
   }
   launch_cg_rnorm(mv, m->r, m->partials, m->cg, s);
@@ -1254,7 +1255,7 @@ void issue_guess_and_residual(Model* m, cudaStream_t s, StepState* ss, Drive dr,
 // On commit: the converged increment into the guess history.
 void issue_history_push(Model* m, cudaStream_t s, StepState* ss, StepLaunches* n) {
   if (m->opts.proj_dim > 0) {
-    launch_proj_push(m->N, m->x, m->proj_b, m->r, m->proj_W, m->proj_Z, m->proj, m->opts.proj_dim, m->partials, s,
+    launch_proj_push(m->N, m->x, m->proj_b, m->r, m->proj_W, m->proj_Z, m->proj, m->opts.proj_dim, m->proj_part, s,
                      ss);
     n->fixed += 1;
   } else if (m->opts.guess_order > 0) {

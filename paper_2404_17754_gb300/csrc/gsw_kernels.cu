@@ -1051,55 +1051,35 @@ __global__ void guess_advance_kernel(int* ext, int S, const StepState* ss) {
 // 1e-12 of the largest dropped), du0 = W c and r0 = b - Z c: the A-norm
 // optimal combination of the past increments.
 
-// Cyclic Jacobi eigen-solve of the symmetric n x n system G c = g (n <=
-// kMaxProj) in one thread, eigenvalues below rel * lambda_max dropped.
+// Solve of the symmetric positive semi-definite n x n system G c = g (n <=
+// kMaxProj) in one thread: Cholesky factorisation of G + ridge I with ridge
+// 1e-12 times the largest diagonal entry, so nearly collinear increments give
+// a bounded combination instead of a breakdown; a pivot that still vanishes
+// drops its direction.
 __device__ void proj_solve(const double* G, const double* g, int n, double* c) {
-  double A[kMaxProj][kMaxProj], V[kMaxProj][kMaxProj];
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) {
-      A[i][j] = G[i * kMaxProj + j];
-      V[i][j] = (i == j) ? 1.0 : 0.0;
+  double L[kMaxProj][kMaxProj], y[kMaxProj];
+  double dmax = 0.0;
+  for (int i = 0; i < n; ++i) dmax = fmax(dmax, G[i * kMaxProj + i]);
+  const double ridge = 1e-12 * dmax;
+  for (int j = 0; j < n; ++j) {
+    double d = G[j * kMaxProj + j] + ridge;
+    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+    L[j][j] = d > ridge ? sqrt(d) : 0.0;
+    for (int i = j + 1; i < n; ++i) {
+      double v = G[i * kMaxProj + j];
+      for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+      L[i][j] = L[j][j] > 0.0 ? v / L[j][j] : 0.0;
     }
-  for (int sweep = 0; sweep < 30; ++sweep) {
-    double off = 0.0, diag = 0.0;
-    for (int i = 0; i < n; ++i) {
-      diag += A[i][i] * A[i][i];
-      for (int j = i + 1; j < n; ++j) off += A[i][j] * A[i][j];
-    }
-    if (off <= 1e-30 * diag) break;
-    for (int p = 0; p < n; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        if (A[p][q] == 0.0) continue;
-        const double th = 0.5 * (A[q][q] - A[p][p]) / A[p][q];
-        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-        const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
-        for (int k = 0; k < n; ++k) {  // rotate columns p, q
-          const double akp = A[k][p], akq = A[k][q];
-          A[k][p] = cs * akp - sn * akq;
-          A[k][q] = sn * akp + cs * akq;
-        }
-        for (int k = 0; k < n; ++k) {  // rotate rows p, q
-          const double apk = A[p][k], aqk = A[q][k];
-          A[p][k] = cs * apk - sn * aqk;
-          A[q][k] = sn * apk + cs * aqk;
-        }
-        for (int k = 0; k < n; ++k) {
-          const double vkp = V[k][p], vkq = V[k][q];
-          V[k][p] = cs * vkp - sn * vkq;
-          V[k][q] = sn * vkp + cs * vkq;
-        }
-      }
   }
-  double lmax = 0.0;
-  for (int i = 0; i < n; ++i) lmax = fmax(lmax, A[i][i]);
-  for (int i = 0; i < n; ++i) c[i] = 0.0;
-  for (int e = 0; e < n; ++e) {
-    const double lam = A[e][e];
-    if (!(lam > 1e-12 * lmax)) continue;
-    double proj = 0.0;
-    for (int i = 0; i < n; ++i) proj += V[i][e] * g[i];
-    proj /= lam;
-    for (int i = 0; i < n; ++i) c[i] += V[i][e] * proj;
+  for (int i = 0; i < n; ++i) {  // L y = g
+    double v = g[i];
+    for (int k = 0; k < i; ++k) v -= L[i][k] * y[k];
+    y[i] = L[i][i] > 0.0 ? v / L[i][i] : 0.0;
+  }
+  for (int i = n - 1; i >= 0; --i) {  // L^T c = y
+    double v = y[i];
+    for (int k = i + 1; k < n; ++k) v -= L[k][i] * c[k];
+    c[i] = L[i][i] > 0.0 ? v / L[i][i] : 0.0;
   }
 }
 
@@ -1205,10 +1185,9 @@ __global__ void proj_push_kernel(int64_t n3, const double* __restrict__ du, cons
 
 // The W/Z slots are in ring order, but the projection is invariant to the
 // order of its basis, so the dots and combinations run over slots 0..count-1.
-static int proj_blocks(int64_t n3) {
-  int g = node_blocks(n3);
-  return g < 152 ? g : 152;  // 2 * kMaxProj partials per CTA within the partials buffer
-}
+// The reductions use the projection's own partials buffer (2 * kMaxProj *
+// kMaxNodeBlocks doubles), so they run on the full node grid.
+static int proj_blocks(int64_t n3) { return node_blocks(n3); }
 void launch_proj_coef(int64_t N, const double* W, const double* b, ProjState* ps, double* partials, cudaStream_t s,
                       const StepState* ss) {
   proj_coef_kernel<<<proj_blocks(3 * N), kNodeThreads, 0, s>>>(3 * N, W, b, ps, partials, ss);
