@@ -193,4 +193,124 @@ __device__ __forceinline__ void mass_apply(const T (&w)[10][3], T ms, T (&y)[10]
   }
 }
 
+// ---- FP32 specialisations on packed component pairs ------------------------
+//
+// Blackwell executes two FP32 operations per instruction on a float2
+// (fma.rn.f32x2, add, mul).  The FP32 element operators therefore carry each
+// 3-vector as (x, y) in a float2 plus z in a float: every component-wise
+// operation is one packed and one scalar instruction instead of three.  The
+// arithmetic is that of the generic templates above, each operation rounded
+// once (round to nearest).
+struct V3 {
+  float2 xy;
+  float z;
+};
+__device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ V3 v3_add(V3 a, V3 b) { return V3{__fadd2_rn(a.xy, b.xy), __fadd_rn(a.z, b.z)}; }
+__device__ __forceinline__ V3 v3_sub(V3 a, V3 b) {
+  return V3{__fadd2_rn(a.xy, make_float2(-b.xy.x, -b.xy.y)), __fsub_rn(a.z, b.z)};
+}
+__device__ __forceinline__ V3 v3_scale(float s, V3 a) { return V3{__fmul2_rn(bc2(s), a.xy), __fmul_rn(s, a.z)}; }
+// s a + c
+__device__ __forceinline__ V3 v3_fma(float s, V3 a, V3 c) {
+  return V3{__ffma2_rn(bc2(s), a.xy, c.xy), __fmaf_rn(s, a.z, c.z)};
+}
+__device__ __forceinline__ V3 v3_neg(V3 a) { return V3{make_float2(-a.xy.x, -a.xy.y), -a.z}; }
+__device__ __forceinline__ V3 v3_zero() { return V3{make_float2(0.f, 0.f), 0.f}; }
+
+template <>
+__device__ __forceinline__ void stiffness_apply<float>(const float (&w3)[10][3], const float (&g)[3][3], float lamS,
+                                                       float muS, float (&y3)[10][3]) {
+  V3 w[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) w[k] = V3{make_float2(w3[k][0], w3[k][1]), w3[k][2]};
+  V3 D0[3];  // u_m - u_0, m = 1..3
+#pragma unroll
+  for (int m = 0; m < 3; ++m) D0[m] = v3_sub(w[m + 1], w[0]);
+  V3 sumT[4], diagT[4], cross[6];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) sumT[m] = v3_zero();
+#pragma unroll
+  for (int e = 0; e < 6; ++e) cross[e] = v3_zero();
+  const float mu2S = 2.0f * muS;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    V3 U[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) U[b] = (b == k) ? w[k] : w[4 + edge_of(k, b)];
+    // column j of H_k over the displacement component i: Hc[j].i = H[i][j]
+    V3 Hc[3];
+#pragma unroll
+    for (int m = 1; m < 4; ++m) {
+      const V3 E = v3_fma(4.0f, v3_sub(U[m], U[0]), v3_neg(D0[m - 1]));
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Hc[j] = (m == 1) ? v3_scale(g[0][j], E) : v3_fma(g[m - 1][j], E, Hc[j]);
+    }
+    const float tr = Hc[0].xy.x + Hc[1].xy.y + Hc[2].z;
+    const float lt = lamS * tr;
+    const float S00 = fmaf(mu2S, Hc[0].xy.x, lt), S11 = fmaf(mu2S, Hc[1].xy.y, lt), S22 = fmaf(mu2S, Hc[2].z, lt);
+    const float S01 = muS * (Hc[1].xy.x + Hc[0].xy.y);
+    const float S02 = muS * (Hc[2].xy.x + Hc[0].z);
+    const float S12 = muS * (Hc[2].xy.y + Hc[1].z);
+    // columns of the symmetric stress
+    const V3 Sc0{make_float2(S00, S01), S02}, Sc1{make_float2(S01, S11), S12}, Sc2{make_float2(S02, S12), S22};
+    V3 Tk[4];
+#pragma unroll
+    for (int m = 1; m < 4; ++m) Tk[m] = v3_fma(g[m - 1][0], Sc0, v3_fma(g[m - 1][1], Sc1, v3_scale(g[m - 1][2], Sc2)));
+    Tk[0] = v3_neg(v3_add(v3_add(Tk[1], Tk[2]), Tk[3]));
+#pragma unroll
+    for (int m = 0; m < 4; ++m) sumT[m] = v3_add(sumT[m], Tk[m]);
+    diagT[k] = Tk[k];
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+      if (b != k) cross[edge_of(k, b)] = v3_add(cross[edge_of(k, b)], Tk[b]);
+  }
+  V3 y[10];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) y[a] = v3_fma(4.0f, diagT[a], v3_neg(sumT[a]));
+#pragma unroll
+  for (int e = 0; e < 6; ++e) y[4 + e] = v3_scale(4.0f, v3_add(v3_add(sumT[edge_a(e)], sumT[edge_b(e)]), cross[e]));
+#pragma unroll
+  for (int k = 0; k < 10; ++k) {
+    y3[k][0] = y[k].xy.x;
+    y3[k][1] = y[k].xy.y;
+    y3[k][2] = y[k].z;
+  }
+}
+
+template <>
+__device__ __forceinline__ void mass_apply<float>(const float (&w3)[10][3], float ms, float (&y3)[10][3]) {
+  V3 w[10], y[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) {
+    w[k] = V3{make_float2(w3[k][0], w3[k][1]), w3[k][2]};
+    y[k] = V3{make_float2(y3[k][0], y3[k][1]), y3[k][2]};
+  }
+  const V3 Xv = v3_add(v3_add(w[0], w[1]), v3_add(w[2], w[3]));
+  const V3 Xe = v3_add(v3_add(v3_add(w[4], w[5]), v3_add(w[6], w[7])), v3_add(w[8], w[9]));
+  const V3 tv = v3_fma(-6.0f, Xe, Xv);
+  const V3 te = v3_fma(16.0f, Xe, v3_scale(-6.0f, Xv));
+  // vertex a: 5 w_a + 2 (edges at a) + Xv - 6 Xe
+  const V3 P0 = v3_fma(5.0f, w[0], v3_fma(2.0f, v3_add(v3_add(w[4], w[6]), w[7]), tv));
+  const V3 P1 = v3_fma(5.0f, w[1], v3_fma(2.0f, v3_add(v3_add(w[4], w[5]), w[8]), tv));
+  const V3 P2 = v3_fma(5.0f, w[2], v3_fma(2.0f, v3_add(v3_add(w[5], w[6]), w[9]), tv));
+  const V3 P3 = v3_fma(5.0f, w[3], v3_fma(2.0f, v3_add(v3_add(w[7], w[8]), w[9]), tv));
+  y[0] = v3_fma(ms, P0, y[0]);
+  y[1] = v3_fma(ms, P1, y[1]);
+  y[2] = v3_fma(ms, P2, y[2]);
+  y[3] = v3_fma(ms, P3, y[3]);
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    const int a = edge_a(e), b = edge_b(e), o = edge_opp(e);
+    const V3 P = v3_fma(2.0f, v3_add(w[a], w[b]), v3_fma(16.0f, w[4 + e], v3_fma(-8.0f, w[4 + o], te)));
+    y[4 + e] = v3_fma(ms, P, y[4 + e]);
+  }
+#pragma unroll
+  for (int k = 0; k < 10; ++k) {
+    y3[k][0] = y[k].xy.x;
+    y3[k][1] = y[k].xy.y;
+    y3[k][2] = y[k].z;
+  }
+}
+
 }  // namespace gsw
