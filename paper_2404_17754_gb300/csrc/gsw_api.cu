@@ -364,7 +364,7 @@ gsw_status proj_alloc(gsw_ctx* ctx, Model* m, int k) {
   TRY(alloc_into(ctx, m, &m->proj_W, (size_t)k * n3));
   TRY(alloc_into(ctx, m, &m->proj_Z, (size_t)k * n3));
   if (!m->proj_b) TRY(alloc_into(ctx, m, &m->proj_b, n3));
-  if (!m->proj_part) TRY(alloc_into(ctx, m, &m->proj_part, (size_t)kMaxProj * (kMaxProj + 1) / 2 * kMaxNodeBlocks));
+  if (!m->proj_part) TRY(alloc_into(ctx, m, &m->proj_part, 2 * (size_t)kMaxProj * kMaxNodeBlocks));
   if (!m->proj) TRY(alloc_into(ctx, m, &m->proj, 1));
   CK(cudaMemsetAsync(m->proj, 0, sizeof(ProjState), ctx->stream));
   m->proj_k = k;

@@ -172,15 +172,14 @@ void launch_guess_extrap(int64_t N, const double* ring, int k, const int* ext, c
 void launch_guess_push(int64_t N, const double* du, double* ring, int k, int* ext, cudaStream_t s,
                        const StepState* ss = nullptr);
 // Initial guess by Galerkin projection onto the last k <= kMaxProj converged
-// increments, kept as their backward differences W with Z = A W (from each
-// step's b - r): c = G^+ W^T b, G = sym(W^T Z), du0 = W c.  W, Z: [k][3N]
-// doubles.
+// increments W with Z = A W (kept from each step's b - r): c = G^+ W^T b,
+// G = W^T Z, du0 = W c.  W, Z: [k][3N] doubles.
 constexpr int kMaxProj = 8;
 struct ProjState {
-  int count, head;          // filled differences (head unused)
+  int count, head;          // filled slots, next slot
   unsigned int counter;     // arrival counter of the last-block reductions
   unsigned int pad;
-  double G[kMaxProj * kMaxProj];  // sym(W^T Z) over the differences
+  double G[kMaxProj * kMaxProj];  // by slot
   double c[kMaxProj];             // coefficients of the current step
 };
 void launch_proj_coef(int64_t N, const double* W, const double* b, ProjState* ps, double* partials, cudaStream_t s,
@@ -190,7 +189,7 @@ void launch_proj_apply(int64_t N, const double* W, const double* Z, const ProjSt
                        double* bkeep, cudaStream_t s, const StepState* ss = nullptr);
 void launch_proj_guess(int64_t N, const double* W, const ProjState* ps, double* x, cudaStream_t s,
                        const StepState* ss = nullptr);
-// on commit: the differences W, Z updated with du and b - r, G recomputed
+// on commit: W[head] = du, Z[head] = b - r, G row/column of head, advance
 void launch_proj_push(int64_t N, const double* du, const double* b, const double* r, double* W, double* Z,
                       ProjState* ps, int k, double* partials, cudaStream_t s, const StepState* ss = nullptr);
 void launch_cg_init(const ModelView& m, const double* b, const double* v, const double* a,

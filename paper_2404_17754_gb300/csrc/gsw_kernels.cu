@@ -1045,48 +1045,45 @@ __global__ void guess_advance_kernel(int* ext, int S, const StepState* ss) {
 // Initial guess by Galerkin projection onto the last k converged increments
 // ------------------------------------------------------------------------------
 //
-// The span of the last k increments is kept as their backward differences
-// W_j = sum_i (-1)^i C(j, i) du_{n-1-i} (j = 0..k-1; the same span, far
-// better conditioned than the nearly collinear increments themselves), with
-// Z_j = A W_j formed from each converged step's b - r (no operator
-// application) by the same differences, and G = sym(W^T Z).  At a step with
-// right-hand side b: c = G^+ W^T b, du0 = W c and r0 = b - Z c: the A-norm
+// W = [du_{n-1} .. du_{n-k}] (ring of slots), Z = A W stored as the converged
+// steps' b - r (no operator application), G = (W^T Z + Z^T W) / 2 kept by
+// slot.  At a step with right-hand side b: c = G^+ W^T b (eigenvalues below
+// 1e-12 of the largest dropped), du0 = W c and r0 = b - Z c: the A-norm
 // optimal combination of the past increments.
 
 // Solve of the symmetric positive semi-definite n x n system G c = g (n <=
-// kMaxProj) in one thread: scaled to a unit diagonal, then Cholesky of the
-// scaled matrix + 1e-12 I; a pivot that still vanishes drops its direction.
+// kMaxProj) in one thread: Cholesky factorisation of G + ridge I with ridge
+// 1e-12 times the largest diagonal entry, so nearly collinear increments give
+// a bounded combination instead of a breakdown; a pivot that still vanishes
+// drops its direction.
 __device__ void proj_solve(const double* G, const double* g, int n, double* c) {
-  double L[kMaxProj][kMaxProj], y[kMaxProj], sc[kMaxProj];
-  for (int i = 0; i < n; ++i) {
-    const double d = G[i * kMaxProj + i];
-    sc[i] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
-  }
-  const double ridge = 1e-12;
+  double L[kMaxProj][kMaxProj], y[kMaxProj];
+  double dmax = 0.0;
+  for (int i = 0; i < n; ++i) dmax = fmax(dmax, G[i * kMaxProj + i]);
+  const double ridge = 1e-12 * dmax;
   for (int j = 0; j < n; ++j) {
-    double d = G[j * kMaxProj + j] * sc[j] * sc[j] + ridge;
+    double d = G[j * kMaxProj + j] + ridge;
     for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
-    L[j][j] = (sc[j] > 0.0 && d > ridge) ? sqrt(d) : 0.0;
+    L[j][j] = d > ridge ? sqrt(d) : 0.0;
     for (int i = j + 1; i < n; ++i) {
-      double v = G[i * kMaxProj + j] * sc[i] * sc[j];
+      double v = G[i * kMaxProj + j];
       for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
       L[i][j] = L[j][j] > 0.0 ? v / L[j][j] : 0.0;
     }
   }
-  for (int i = 0; i < n; ++i) {  // L y = S g
-    double v = g[i] * sc[i];
+  for (int i = 0; i < n; ++i) {  // L y = g
+    double v = g[i];
     for (int k = 0; k < i; ++k) v -= L[i][k] * y[k];
     y[i] = L[i][i] > 0.0 ? v / L[i][i] : 0.0;
   }
-  for (int i = n - 1; i >= 0; --i) {  // L^T (S^-1 c) = y
+  for (int i = n - 1; i >= 0; --i) {  // L^T c = y
     double v = y[i];
     for (int k = i + 1; k < n; ++k) v -= L[k][i] * c[k];
     c[i] = L[i][i] > 0.0 ? v / L[i][i] : 0.0;
   }
-  for (int i = 0; i < n; ++i) c[i] *= sc[i];
 }
 
-// g = W^T b over the filled differences, then c (in ps) by the projection solve.
+// g = W^T b over the filled slots, then c (in ps) by the projection solve.
 __global__ void proj_coef_kernel(int64_t n3, const double* __restrict__ W, const double* __restrict__ b,
                                  ProjState* ps, double* partials, const StepState* ss) {
   if (ss != nullptr && !((volatile const StepState*)ss)->active) return;
@@ -1148,58 +1145,47 @@ __global__ void proj_guess_kernel(int64_t n3, const double* __restrict__ W, cons
   }
 }
 
-// Push the converged increment: W_0' = du, W_j' = W_{j-1}' - W_{j-1} (and
-// likewise Z from z = b - r = A du), in place; then G' = sym(W'^T Z') over
-// the filled differences (the upper triangle, kMaxProj (kMaxProj + 1) / 2
-// sums); count advances.
-constexpr int kProjPairs = kMaxProj * (kMaxProj + 1) / 2;
+// Push the converged increment: slot `head` of W gets du, of Z gets b - r
+// (= A du), and the slot's row and column of G are recomputed from the dots
+// with every filled slot; count and head advance.
 __global__ void proj_push_kernel(int64_t n3, const double* __restrict__ du, const double* __restrict__ b,
                                  const double* __restrict__ r, double* __restrict__ W, double* __restrict__ Z,
                                  ProjState* ps, int k, double* partials, const StepState* ss) {
   if (ss != nullptr && !((volatile const StepState*)ss)->commit) return;
+  const int head = ((volatile const ProjState*)ps)->head;
   const int cnt0 = ((volatile const ProjState*)ps)->count;
-  const int cnt = cnt0 < k ? cnt0 + 1 : k;  // differences filled after this push
-  double acc[kProjPairs];
+  const int cnt = cnt0 < k ? cnt0 + 1 : k;  // slots filled after this push
+  double acc[2 * kMaxProj];
 #pragma unroll
-  for (int q = 0; q < kProjPairs; ++q) acc[q] = 0.0;
+  for (int j = 0; j < 2 * kMaxProj; ++j) acc[j] = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
-    double w[kMaxProj], z[kMaxProj];
-    double wn = du[i], zn = b[i] - r[i];
+    const double di = du[i], zi = b[i] - r[i];
+    W[(int64_t)head * n3 + i] = di;
+    Z[(int64_t)head * n3 + i] = zi;
 #pragma unroll
-    for (int j = 0; j < kMaxProj; ++j) {
+    for (int j = 0; j < kMaxProj; ++j)
       if (j < cnt) {
-        const double wo = W[(int64_t)j * n3 + i], zo = Z[(int64_t)j * n3 + i];
-        W[(int64_t)j * n3 + i] = wn;
-        Z[(int64_t)j * n3 + i] = zn;
-        w[j] = wn;
-        z[j] = zn;
-        wn -= wo;
-        zn -= zo;
-      } else {
-        w[j] = 0.0;
-        z[j] = 0.0;
+        const double wj = j == head ? di : W[(int64_t)j * n3 + i];
+        const double zj = j == head ? zi : Z[(int64_t)j * n3 + i];
+        acc[j] = fma(di, zj, acc[j]);
+        acc[kMaxProj + j] = fma(wj, zi, acc[kMaxProj + j]);
       }
-    }
-    int q = 0;
-#pragma unroll
-    for (int a = 0; a < kMaxProj; ++a)
-#pragma unroll
-      for (int c = a; c < kMaxProj; ++c, ++q) acc[q] = fma(w[a], z[c], fma(w[c], z[a], acc[q]));
   }
-  double out[kProjPairs];
-  if (last_block_reduce<kProjPairs>(acc, partials, &ps->counter, out) && threadIdx.x == 0) {
-    int q = 0;
-    for (int a = 0; a < kMaxProj; ++a)
-      for (int c = a; c < kMaxProj; ++c, ++q) {
-        const double v = (a < cnt && c < cnt) ? 0.5 * out[q] : 0.0;
-        ps->G[a * kMaxProj + c] = v;
-        ps->G[c * kMaxProj + a] = v;
-      }
+  double out[2 * kMaxProj];
+  if (last_block_reduce<2 * kMaxProj>(acc, partials, &ps->counter, out) && threadIdx.x == 0) {
+    for (int j = 0; j < kMaxProj; ++j) {
+      const double gj = j < cnt ? 0.5 * (out[j] + out[kMaxProj + j]) : 0.0;
+      ps->G[head * kMaxProj + j] = gj;
+      ps->G[j * kMaxProj + head] = gj;
+    }
     ps->count = cnt;
+    ps->head = (head + 1) % k;
   }
 }
 
-// The reductions use the projection's own partials buffer (kProjPairs *
+// The W/Z slots are in ring order, but the projection is invariant to the
+// order of its basis, so the dots and combinations run over slots 0..count-1.
+// The reductions use the projection's own partials buffer (2 * kMaxProj *
 // kMaxNodeBlocks doubles), so they run on the full node grid.
 static int proj_blocks(int64_t n3) { return node_blocks(n3); }
 void launch_proj_coef(int64_t N, const double* W, const double* b, ProjState* ps, double* partials, cudaStream_t s,
