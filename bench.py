@@ -565,6 +565,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--proj-dim", type=int, default=0,
                     help="initial guess by Galerkin projection onto the last k increments (0 = off, 2..8)")
+    ap.add_argument("--coarse-weight", type=float, default=0.0,
+                    help="mixed modes: weight of the two-level inner preconditioner's first-order coarse "
+                         "correction (0 = block Jacobi alone)")
     ap.add_argument("--inner-variant", type=int, default=-1,
                     help="launch variant of the inner operator (-1: the autotuner picks)")
     ap.add_argument("--no-extras", action="store_true",
@@ -638,7 +641,8 @@ def main():
     m.set_input(cfg["dir"], cfg["p"])
     prec = {"fp64": 0, "fp32": 1, "fp16": 2}[args.precision]
     m.set_solver(tol=args.tol, outer_op=OUTER_OPS[args.outer_op], precision=prec, inner_iters=args.inner, inner_rtol=args.inner_rtol,
-                 guess_order=args.guess_order, inner_variant=args.inner_variant, proj_dim=args.proj_dim)
+                 guess_order=args.guess_order, inner_variant=args.inner_variant, proj_dim=args.proj_dim,
+                 coarse_weight=args.coarse_weight)
     n_nodes, n_elem, n_faces = mesh["xyz"].shape[0], mesh["conn"].shape[0], mesh["faces"].shape[0]
     dof = 3 * n_nodes
 
@@ -800,6 +804,8 @@ def main():
                                 proj_dim=args.proj_dim)
         if args.precision != "fp64":
             ca = candidate_analysis_block(ctx, cfg, args.warmup + args.steps, args, prec)
+    inner_pc = ("two-level (block Jacobi + %g x first-order coarse block Jacobi)" % args.coarse_weight
+                if args.coarse_weight > 0 else "block-Jacobi")
     out = {
         "metric": "DOF*steps/s", "value": value, "unit": "DOF*steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
@@ -807,13 +813,13 @@ def main():
         "data": "synthetic",
         "config": {"workload": cfg["name"] if args.workload == "realistic" else "two-layer 100x100x50 m",
                    "dof": dof, "elements": n_elem, "dt": cfg["dt"], "tol": args.tol, "precision": args.precision,
-                   "guess_order": args.guess_order, "proj_dim": args.proj_dim,
+                   "guess_order": args.guess_order, "proj_dim": args.proj_dim, "coarse_weight": args.coarse_weight,
                    "outer_operator": "FP64" if args.outer_op == "fp64" or (args.outer_op == "auto" and args.precision == "fp64") else "double-word",
                    "solver": "block-Jacobi PCG" if args.precision == "fp64" else
-                             ("flexible CG (FP64) + %s block-Jacobi PCG preconditioner, %d iterations" % (
-                                 args.precision, args.inner) if args.inner_rtol <= 0 else
-                              "flexible CG (FP64) + %s block-Jacobi PCG preconditioner to relative %g (at most %d "
-                              "iterations)" % (args.precision, args.inner_rtol, args.inner)),
+                             ("flexible CG (FP64) + %s %s PCG preconditioner, %d iterations" % (
+                                 args.precision, inner_pc, args.inner) if args.inner_rtol <= 0 else
+                              "flexible CG (FP64) + %s %s PCG preconditioner to relative %g (at most %d "
+                              "iterations)" % (args.precision, inner_pc, args.inner_rtol, args.inner)),
                    "inner_iters_per_step": (st["inner_iters_total"] - inner0) / args.steps,
                    "inner_operator_variant": m_info["inner_variant"], "parallelism": "independent directional analyses, 1 per GPU",
                    "cg_iters_per_step": iters / args.steps,

@@ -119,6 +119,13 @@ typedef struct {
                             du0 = 0.  Takes precedence over guess_order; excludes the
                             learned guess.  The history restarts at gsw_reset /
                             gsw_set_state. */
+  double coarse_weight;  /* mixed modes: 0 = the inner PCG's preconditioner is the
+                            3x3 nodal block Jacobi D^-1; omega > 0 = the two-level
+                            preconditioner D^-1 + omega P D_c^-1 P^T, with P the
+                            interpolation from the vertices (first-order coarse
+                            level, Section 3's multi-level solver) to the quadratic
+                            nodes and D_c the nodal diagonal blocks of P^T A P;
+                            must be finite and in [0, 4] */
 } gsw_solver_opts;
 
 typedef struct {
@@ -301,7 +308,10 @@ gsw_status gsw_timing(gsw_ctx *ctx, int32_t model_id, int32_t enable, double *ms
  *  which = 4: y = A x by the reduced-precision inner operator of the model's
  *  current mixed precision mode (x rounded to the inner storage type,
  *  FP32 arithmetic and accumulation); GSW_E_STATE in FP64 mode;
- *  which = 5: y = A x in double-word arithmetic (GSW_OUTER_DWORD).
+ *  which = 5: y = A x in double-word arithmetic (GSW_OUTER_DWORD);
+ *  which = 6: y = P D_c^-1 P^T x, the coarse correction of the two-level inner
+ *  preconditioner (FP32 arithmetic; GSW_E_STATE unless a mixed mode with
+ *  coarse_weight > 0 is set).
  * x_dev, y_dev device pointers; y is overwritten. */
 gsw_status gsw_apply(gsw_ctx *ctx, int32_t model_id, int32_t which, const double *x_dev,
                      double *y_dev);

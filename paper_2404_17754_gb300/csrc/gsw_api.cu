@@ -60,7 +60,7 @@ struct Model {
   std::vector<double> input;
   int dir = 0;
   bool input_set = false;
-  gsw_solver_opts opts = {1e-8, 10000, GSW_PREC_FP64, 20, 8, 6, -1, 0.0, 0, 0, 0, 0};
+  gsw_solver_opts opts = {1e-8, 10000, GSW_PREC_FP64, 20, 8, 6, -1, 0.0, 0, 0, 0, 0, 0.0};
   int64_t step = 0;
   bool failed = false;
   gsw_stats stats = {};
@@ -87,6 +87,17 @@ struct Model {
   double *proj_W = nullptr, *proj_Z = nullptr, *proj_b = nullptr, *proj_part = nullptr;
   ProjState* proj = nullptr;
   int proj_k = 0;
+  // two-level inner preconditioner (opts.coarse_weight > 0): the first-order
+  // coarse level (structure and blocks shared with the direction instances;
+  // zc is each analysis's own)
+  int64_t Nv = 0;
+  int32_t *cv_node = nullptr, *cv_ptr = nullptr, *cv_mid = nullptr, *c_vid = nullptr;
+  int2* c_pair = nullptr;
+  double *cblk = nullptr, *cinv = nullptr;  // [Nv][6] coarse diagonal blocks and their inverses
+  float* cdc = nullptr;                     // [Nv][6] omega D_c^-1 / mean(D^-1)
+  float4* zc = nullptr;                     // [Nv] coarse correction of the current inner iteration
+  bool coarse() const { return opts.coarse_weight > 0.0 && opts.precision != GSW_PREC_FP64 && zc != nullptr; }
+  CoarseView cview() const { return CoarseView{Nv, cv_node, cv_ptr, cv_mid, c_pair, cdc}; }
   float4* matf = nullptr;      // FP32 material coefficients of the inner operator and the FP32 RHS
   float4* uva = nullptr;       // FP32 copy of u, v, a ([N + 1][3] words) for the FP32 RHS
   unsigned long long iters_mark = 0;   // device inner-iteration counter when timing started
@@ -551,6 +562,91 @@ gsw_status autotune_lo(gsw_ctx* ctx, Model* m) {
 // Element blocks with local numbering and the reduced-precision copies of the
 // operator data and preconditioner (built once per model; the conversion is
 // redone when dt changes).
+// First-order coarse level of the two-level inner preconditioner: the
+// vertices (the first four nodes of each element), the vertex pair each fine
+// node interpolates and, per vertex, the mid-edge nodes of its edges (CSR, in
+// ascending node order) are built on first use from the connectivity; the
+// blocks of P^T A P and omega D_c^-1 again with every rebuild of the inner
+// operator (they depend on dt, the materials and omega).
+gsw_status build_coarse(gsw_ctx* ctx, Model* m) {
+  cudaStream_t s = ctx->stream;
+  if (!m->cv_node) {
+    static const int ea[6] = {0, 1, 0, 0, 1, 2}, eb[6] = {1, 2, 2, 3, 3, 3};  // the element's edge order
+    const int64_t N = m->N, E = m->E;
+    std::vector<int32_t> conn((size_t)10 * E);  // [10][E]
+    CK(cudaMemcpyAsync(conn.data(), m->conn, sizeof(int32_t) * conn.size(), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<int32_t> vid((size_t)N, -1), vnode;
+    for (int k = 0; k < 4; ++k)
+      for (int64_t e = 0; e < E; ++e) vid[(size_t)conn[(size_t)(k * E + e)]] = 0;
+    int32_t nv = 0;
+    for (int64_t n = 0; n < N; ++n)
+      if (vid[(size_t)n] == 0) {
+        vid[(size_t)n] = nv++;
+        vnode.push_back((int32_t)n);
+      }
+    std::vector<int2> pair((size_t)N, make_int2(-1, -1));
+    for (int64_t n = 0; n < N; ++n)
+      if (vid[(size_t)n] >= 0) pair[(size_t)n] = make_int2(vid[(size_t)n], vid[(size_t)n]);
+    for (int k = 0; k < 6; ++k)
+      for (int64_t e = 0; e < E; ++e) {
+        const int32_t mn = conn[(size_t)((4 + k) * E + e)];
+        int32_t a = vid[(size_t)conn[(size_t)(ea[k] * E + e)]], b = vid[(size_t)conn[(size_t)(eb[k] * E + e)]];
+        if (a > b) std::swap(a, b);
+        if (vid[(size_t)mn] >= 0)
+          return fail(ctx, GSW_E_INVALID, "node %d is both a vertex and a mid-edge node", mn);
+        int2& p = pair[(size_t)mn];
+        if (p.x < 0)
+          p = make_int2(a, b);
+        else if (p.x != a || p.y != b)
+          return fail(ctx, GSW_E_INVALID, "mid-edge node %d lies on two different edges", mn);
+      }
+    std::vector<int32_t> ptr((size_t)nv + 1, 0);
+    for (int64_t n = 0; n < N; ++n) {
+      const int2 p = pair[(size_t)n];
+      if (p.x < 0) return fail(ctx, GSW_E_INVALID, "node %lld belongs to no element", (long long)n);
+      if (p.x != p.y) {
+        ptr[(size_t)p.x + 1] += 1;
+        ptr[(size_t)p.y + 1] += 1;
+      }
+    }
+    for (int32_t v = 0; v < nv; ++v) ptr[(size_t)v + 1] += ptr[(size_t)v];
+    std::vector<int32_t> mid((size_t)std::max(ptr[(size_t)nv], 1), 0), fill(ptr.begin(), ptr.end() - 1);
+    for (int64_t n = 0; n < N; ++n) {
+      const int2 p = pair[(size_t)n];
+      if (p.x != p.y) {
+        mid[(size_t)fill[(size_t)p.x]++] = (int32_t)n;
+        mid[(size_t)fill[(size_t)p.y]++] = (int32_t)n;
+      }
+    }
+    const size_t nvs = (size_t)std::max(nv, 1);
+    TRY(alloc_into(ctx, m, &m->cv_node, nvs));
+    TRY(alloc_into(ctx, m, &m->cv_ptr, (size_t)nv + 1));
+    TRY(alloc_into(ctx, m, &m->cv_mid, mid.size()));
+    TRY(alloc_into(ctx, m, &m->c_pair, (size_t)N));
+    TRY(alloc_into(ctx, m, &m->c_vid, (size_t)N));
+    TRY(alloc_into(ctx, m, &m->cblk, 6 * nvs));
+    TRY(alloc_into(ctx, m, &m->cinv, 6 * nvs));
+    TRY(alloc_into(ctx, m, &m->cdc, 6 * nvs));
+    TRY(alloc_into(ctx, m, &m->zc, nvs));
+    CK(cudaMemcpyAsync(m->cv_node, vnode.data(), sizeof(int32_t) * (size_t)nv, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(m->cv_ptr, ptr.data(), sizeof(int32_t) * ptr.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(m->cv_mid, mid.data(), sizeof(int32_t) * mid.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(m->c_pair, pair.data(), sizeof(int2) * (size_t)N, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(m->c_vid, vid.data(), sizeof(int32_t) * (size_t)N, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(m->zc, 0, sizeof(float4) * nvs, s));
+    CK(cudaStreamSynchronize(s));  // the host vectors go out of scope
+    m->Nv = nv;
+  }
+  CK(cudaMemsetAsync(m->cblk, 0, sizeof(double) * 6 * (size_t)m->Nv, s));
+  CK(cudaMemsetAsync(m->err, 0, sizeof(int), s));
+  launch_coarse_blocks(m->view(), m->c_vid, m->cblk, s);
+  launch_invert_blocks(m->Nv, m->cblk, m->cinv, m->err, s);
+  launch_coarse_lo(m->Nv, m->cinv, m->isc, m->opts.coarse_weight, m->cdc, s);
+  CK(cudaGetLastError());
+  return check_device_err(ctx, m, "coarse preconditioner");
+}
+
 gsw_status build_lo(gsw_ctx* ctx, Model* m, int half) {
   cudaStream_t s = ctx->stream;
   ModelView mv = m->view();
@@ -625,6 +721,7 @@ gsw_status build_lo(gsw_ctx* ctx, Model* m, int half) {
                           m->dw_part, face_c};
   m->lo_h = LoView<__half>{m->N, m->E, m->F, m->n_mat, bv, m->geo_lo, m->matf, m->fnode, m->fgeo32, m->dt,
                            m->dw_part, face_c};
+  if (m->opts.coarse_weight > 0.0) TRY(build_coarse(ctx, m));
   m->live_tune = (m->opts.inner_variant < 0);
   return autotune_lo(ctx, m);
 }
@@ -698,6 +795,15 @@ gsw_status make_instance(gsw_ctx* ctx, Model* m, int d, Model** out) {
     c->fgeo32 = m->fgeo32;
     c->dinv32 = m->dinv32;
     c->matf = m->matf;
+    if (m->zc) {
+      c->Nv = m->Nv;
+      c->cv_node = m->cv_node;
+      c->cv_ptr = m->cv_ptr;
+      c->cv_mid = m->cv_mid;
+      c->c_pair = m->c_pair;
+      c->cdc = m->cdc;
+      TRYI(alloc_into(ctx, c, &c->zc, (size_t)std::max<int64_t>(m->Nv, 1)));
+    }
     c->lo_variant = m->lo_variant;
     for (int v = 0; v < kLoVariants; ++v) c->lo_variant_ms[v] = m->lo_variant_ms[v];
     const size_t n3 = 3 * (size_t)c->N;
@@ -858,7 +964,7 @@ int lo_grid_max(const Model* m) { return m->n_blk + (int)((m->F + kLoBlock - 1) 
 // small models, where launches dominate: on the 2.42 M-element model the fused
 // operator costs more than the recurrence kernel it replaces.
 bool inner_fuses(const Model* m, int variant) {
-  return lo_variant_fuses(variant) && lo_grid_max(m) <= kAlphaPrologueMax;
+  return !m->coarse() && lo_variant_fuses(variant) && lo_grid_max(m) <= kAlphaPrologueMax;
 }
 // Kernel launches of one inner solve: initialisation, then per iteration the
 // operator, the update (+ a one-CTA alpha kernel for large models) and,
@@ -866,7 +972,36 @@ bool inner_fuses(const Model* m, int variant) {
 int64_t inner_solve_launches(const Model* m, bool fuse) {
   const int64_t it = m->opts.inner_iters > 0 ? m->opts.inner_iters : 1;
   const int64_t per = (lo_grid_max(m) <= kAlphaPrologueMax ? 2 : 3);
+  if (m->coarse()) return 3 + per * it + 2 * (it - 1);  // + restriction and recurrence at the start and per iteration
   return 1 + per * it + (fuse ? 0 : it - 1);
+}
+// Start of an inner solve: s (the scaled outer residual), y = 0, t = D^-1 s,
+// d = t; with the two-level preconditioner also z_c and d = t + P z_c.
+void inner_begin(Model* m, cudaStream_t s, float rtol) {
+  launch_inner_init(m->N, m->r, m->dinv32, m->s32, m->y32, m->t32, m->d_lo, m->lo_half, m->w32, m->partials, m->isc,
+                    m->cg, s, rtol);
+  if (m->coarse()) {
+    launch_coarse_restrict(m->cview(), m->s32, m->zc, m->partials, m->isc, m->cg, 1, s);
+    launch_inner_dupdate(m->N, m->t32, m->d_lo, m->lo_half, m->isc, s, m->cg, m->c_pair, m->zc);
+  }
+}
+// After inner iteration k's operator product (d_k in dk): y, s and t, then,
+// except after the last iteration, the next direction (unless the operator
+// fuses the recurrence).
+void inner_after_op(Model* m, cudaStream_t s, const void* dk, int k, int it, bool fuse) {
+  const int half = m->lo_half;
+  if (m->coarse()) {
+    launch_inner_update_coarse(m->N, m->y32, m->s32, m->t32, dk, half, m->w32, m->dinv32, m->dw_part, m->partials,
+                               m->isc, s, m->cg, lo_grid_max(m));
+    if (k + 1 < it) {
+      launch_coarse_restrict(m->cview(), m->s32, m->zc, m->partials, m->isc, m->cg, 0, s);
+      launch_inner_dupdate(m->N, m->t32, m->d_lo, half, m->isc, s, m->cg, m->c_pair, m->zc);
+    }
+    return;
+  }
+  launch_inner_update(m->N, m->y32, m->s32, m->t32, dk, half, m->w32, m->dinv32, m->dw_part, m->partials, m->isc, s,
+                      m->cg, lo_grid_max(m));
+  if (!fuse && k + 1 < it) launch_inner_dupdate(m->N, m->t32, m->d_lo, half, m->isc, s, m->cg);
 }
 // Operator product of inner iteration k; returns the direction buffer that
 // holds d_k.  With a fusing variant, iteration k > 0 forms d_k = t + beta
@@ -894,8 +1029,7 @@ int64_t inner_solve(Model* m, cudaStream_t s) {
   // take turns (in the cache state of a real solve) and the fastest median
   // wins; that solve runs all inner_iters iterations
   const bool tune = m->live_tune && it >= 2 * kLoVariants && (int)m->ev_lo.size() >= 2 * it;
-  launch_inner_init(m->N, m->r, m->dinv32, m->s32, m->y32, m->t32, m->d_lo, half, m->w32, m->partials, m->isc,
-                    m->cg, s, tune ? 0.f : (float)m->opts.inner_rtol);
+  inner_begin(m, s, tune ? 0.f : (float)m->opts.inner_rtol);
   const bool timed = (m->timing || tune) && (int)m->ev_lo.size() >= 2 * it;
   const bool fuse = !tune && inner_fuses(m, m->lo_variant);
   for (int k = 0; k < it; ++k) {
@@ -903,9 +1037,7 @@ int64_t inner_solve(Model* m, cudaStream_t s) {
     if (timed) cudaEventRecord(m->ev_lo[2 * k], s);
     void* dk = inner_operator_step(m, s, view, k, variant, fuse);
     if (timed) cudaEventRecord(m->ev_lo[2 * k + 1], s);
-    launch_inner_update(m->N, m->y32, m->s32, m->t32, dk, half, m->w32, m->dinv32, m->dw_part, m->partials, m->isc, s,
-                        m->cg, lo_grid_max(m));
-    if (!fuse && k + 1 < it) launch_inner_dupdate(m->N, m->t32, m->d_lo, half, m->isc, s, m->cg);
+    inner_after_op(m, s, dk, k, it, fuse);
   }
   m->stats.inner_iters_total += it;
   if (timed) {
@@ -1120,15 +1252,12 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
 void inner_solve_dev(Model* m, cudaStream_t s) {
   const int half = m->lo_half;
   const void* view = half ? (const void*)&m->lo_h : (const void*)&m->lo_f;
-  launch_inner_init(m->N, m->r, m->dinv32, m->s32, m->y32, m->t32, m->d_lo, half, m->w32, m->partials, m->isc,
-                    m->cg, s, (float)m->opts.inner_rtol);
+  inner_begin(m, s, (float)m->opts.inner_rtol);
   const int it = m->opts.inner_iters > 0 ? m->opts.inner_iters : 1;
   const bool fuse = inner_fuses(m, m->lo_variant);
   for (int k = 0; k < it; ++k) {
     void* dk = inner_operator_step(m, s, view, k, m->lo_variant, fuse);
-    launch_inner_update(m->N, m->y32, m->s32, m->t32, dk, half, m->w32, m->dinv32, m->dw_part, m->partials, m->isc, s,
-                        m->cg, lo_grid_max(m));
-    if (!fuse && k + 1 < it) launch_inner_dupdate(m->N, m->t32, m->d_lo, half, m->isc, s, m->cg);
+    inner_after_op(m, s, dk, k, it, fuse);
   }
 }
 
@@ -1301,11 +1430,7 @@ void inner_solve_group_dev(Model* const* g, int n, cudaStream_t s) {
   Model* m0 = g[0];
   const int half = m0->lo_half;
   const void* view = half ? (const void*)&m0->lo_h : (const void*)&m0->lo_f;
-  for (int i = 0; i < n; ++i) {
-    Model* m = g[i];
-    launch_inner_init(m->N, m->r, m->dinv32, m->s32, m->y32, m->t32, m->d_lo, half, m->w32, m->partials, m->isc,
-                      m->cg, s, (float)m->opts.inner_rtol);
-  }
+  for (int i = 0; i < n; ++i) inner_begin(g[i], s, (float)g[i]->opts.inner_rtol);
   Lo3Args a = {};
   a.nr = n;
   for (int i = 0; i < n; ++i) {
@@ -1319,17 +1444,13 @@ void inner_solve_group_dev(Model* const* g, int n, cudaStream_t s) {
   const int it = m0->opts.inner_iters > 0 ? m0->opts.inner_iters : 1;
   for (int k = 0; k < it; ++k) {
     launch_ebe_lo3(half, half, view, a, s, variant);
-    for (int i = 0; i < n; ++i) {
-      Model* m = g[i];
-      launch_inner_update(m->N, m->y32, m->s32, m->t32, m->d_lo, half, m->w32, m->dinv32, m->dw_part, m->partials,
-                          m->isc, s, m->cg, lo_grid_max(m));
-      if (k + 1 < it) launch_inner_dupdate(m->N, m->t32, m->d_lo, half, m->isc, s, m->cg);
-    }
+    for (int i = 0; i < n; ++i) inner_after_op(g[i], s, g[i]->d_lo, k, it, false);
   }
 }
 int64_t inner_group_launches(const Model* m0, int n) {
   const int64_t it = m0->opts.inner_iters > 0 ? m0->opts.inner_iters : 1;
   const int64_t per = (lo_grid_max(m0) <= kAlphaPrologueMax ? 1 : 2);
+  if (m0->coarse()) return 3 * n + it * (1 + n * per) + 2 * n * (it - 1);
   return n + it * (1 + n * per) + n * (it - 1);
 }
 
@@ -1692,6 +1813,8 @@ gsw_status gsw_set_solver(gsw_ctx* ctx, int32_t model_id, const gsw_solver_opts*
     return fail(ctx, GSW_E_INVALID, "guess_order must be 0..%d", kMaxGuessOrder);
   if (opts->outer_op < GSW_OUTER_AUTO || opts->outer_op > GSW_OUTER_DWORD)
     return fail(ctx, GSW_E_INVALID, "outer_op must be 0 (auto), 1 (FP64) or 2 (double-word)");
+  if (!(opts->coarse_weight >= 0.0 && opts->coarse_weight <= 4.0))
+    return fail(ctx, GSW_E_INVALID, "coarse_weight must be in [0, 4]");
   if (opts->proj_dim != 0 && (opts->proj_dim < 2 || opts->proj_dim > kMaxProj))
     return fail(ctx, GSW_E_INVALID, "proj_dim must be 0 or 2..%d", kMaxProj);
   if (opts->proj_dim > 0 && m->learn.enable)
@@ -2427,7 +2550,19 @@ gsw_status gsw_apply(gsw_ctx* ctx, int32_t model_id, int32_t which, const double
   Model* m = find(ctx, model_id);
   if (!m) return fail(ctx, GSW_E_INVALID, "unknown model %d", model_id);
   if (!m->time_set) return fail(ctx, GSW_E_STATE, "call gsw_set_time first");
-  if (which < 0 || which > 5) return fail(ctx, GSW_E_INVALID, "which must be 0..5");
+  if (which < 0 || which > 6) return fail(ctx, GSW_E_INVALID, "which must be 0..6");
+  if (which == 6) {
+    if (!m->coarse() || !m->lo_ready)
+      return fail(ctx, GSW_E_STATE, "the coarse correction needs a mixed precision mode with coarse_weight > 0");
+    double dm = 0.0;
+    CK(cudaMemcpyAsync(&dm, &m->isc->dinv_mean, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    launch_to_f32(3 * m->N, x_dev, m->s32, ctx->stream);
+    launch_coarse_restrict(m->cview(), m->s32, m->zc, nullptr, nullptr, nullptr, 0, ctx->stream);
+    launch_coarse_prolong(m->N, m->c_pair, m->zc, dm / m->opts.coarse_weight, y_dev, ctx->stream);
+    CK(cudaGetLastError());
+    return GSW_OK;
+  }
   if (which == 4) {
     if (m->opts.precision == GSW_PREC_FP64 || !m->lo_ready)
       return fail(ctx, GSW_E_STATE, "the reduced-precision operator needs a mixed precision mode");

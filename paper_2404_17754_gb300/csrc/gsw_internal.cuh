@@ -111,6 +111,21 @@ struct InnerScalars {
   float rtol2;        // squared relative stopping factor (0: fixed iteration count)
   unsigned int idone; // 1 once the current inner solve has met rtol
   unsigned long long iters;  // inner iterations executed (all solves)
+  double st_f;        // s . D^-1 s, the fine part of s . t (two-level preconditioner)
+};
+
+// First-order (vertex) coarse level of the two-level inner preconditioner
+// t = D^-1 s + omega P D_c^-1 P^T s: P interpolates vertex values to the
+// quadratic nodes (a vertex node takes its vertex's value, a mid-edge node the
+// mean of its edge's two vertices), D_c are the 3x3 nodal diagonal blocks of
+// P^T A P (the linear-tetrahedron operator on the same vertices).
+struct CoarseView {
+  int64_t Nv;            // vertices
+  const int32_t* vnode;  // [Nv] fine node of each vertex
+  const int32_t* ptr;    // [Nv + 1] CSR: the mid-edge nodes on each vertex's edges
+  const int32_t* mid;    // [ptr[Nv]]
+  const int2* pair;      // [N] the two vertices a fine node interpolates (a vertex node: its own twice)
+  const float* dc;       // [Nv][6] omega D_c^-1 / mean(D^-1) (xx yy zz xy xz yz)
 };
 
 // Element blocks with local node numbering: block b holds elements
@@ -152,6 +167,10 @@ void launch_material(MatCoef* mat, const double* raw, int n_mat, double dt, doub
                      cudaStream_t s);
 void launch_block_jacobi(const ModelView& m, double* dblk, double* dinv, int* err,
                          cudaStream_t s);
+// 3x3 nodal diagonal blocks of P^T A P on the vertices (vid: vertex index of
+// each fine node, -1 elsewhere; cblk zeroed by the caller) and their inverses
+void launch_coarse_blocks(const ModelView& m, const int32_t* vid, double* cblk, cudaStream_t s);
+void launch_invert_blocks(int64_t n, const double* blk, double* inv, int* err, cudaStream_t s);
 void launch_receivers(const ModelView& m, const double* xyz, double px, double py,
                       const double* rec_xy, int n_rec, int32_t* rec_face, int32_t* rec_node,
                       double* rec_w, int* err, cudaStream_t s);
@@ -285,7 +304,24 @@ void launch_inner_update(int64_t N, float* y, float* s, void* t, const void* d, 
                          float* w, const void* dinv_lo, const float* dw_part, double* partials,
                          InnerScalars* sc, cudaStream_t st, const CgScalars* outer, int n_dw_max);
 void launch_inner_dupdate(int64_t N, const void* t, void* d, int half_vec, const InnerScalars* sc,
-                          cudaStream_t st, const CgScalars* outer);
+                          cudaStream_t st, const CgScalars* outer, const int2* pair = nullptr,
+                          const float4* zc = nullptr);
+// Two-level inner preconditioner.  With coarse = 1 the update kernel leaves
+// s . t, beta and the stopping test to the restriction kernel (it stores the
+// fine part s . D^-1 s in st_f); the restriction forms z_c = omega D_c^-1 P^T s
+// and completes s . t (first = 1: at the start of an inner solve, beta = 0);
+// the direction update (pair, zc) adds P z_c to t.
+void launch_inner_update_coarse(int64_t N, float* y, float* s, void* t, const void* d, int half_vec, float* w,
+                                const void* dinv_lo, const float* dw_part, double* partials, InnerScalars* sc,
+                                cudaStream_t st, const CgScalars* outer, int n_dw_max);
+void launch_coarse_restrict(const CoarseView& c, const float* s, float4* zc, double* partials, InnerScalars* sc,
+                            const CgScalars* outer, int first, cudaStream_t st);
+// y = scale * P z_c (FP64 output, diagnostics)
+void launch_coarse_prolong(int64_t N, const int2* pair, const float4* zc, double scale, double* y, cudaStream_t st);
+// dc = omega * cinv / mean(D^-1) in FP32
+void launch_coarse_lo(int64_t Nv, const double* cinv, const InnerScalars* sc, double omega, float* dc,
+                      cudaStream_t st);
+void launch_to_f32(int64_t n, const double* x, float* y, cudaStream_t st);
 // conversions for the standalone reduced-precision operator (tests)
 void launch_to_lo(int64_t N, const double* x, void* d, int half_vec, float* w, cudaStream_t s);
 void launch_from_f32(int64_t N, const float* w, double* y, cudaStream_t s);

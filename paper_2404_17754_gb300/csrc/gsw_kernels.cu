@@ -214,6 +214,55 @@ __global__ void diag_blocks_kernel(ModelView m, double* __restrict__ dblk) {
   }
 }
 
+// Diagonal 3x3 blocks of P^T A P at the vertices, P the interpolation from
+// vertex values to the quadratic nodes.  On straight-sided elements the
+// vertex's linear hat function is N_a + 1/2 sum_b N_ab, so the blocks are those
+// of the linear (4-node) tetrahedron: K_aa = (lam + mu) G + mu tr(G) I with
+// G = V g_a g_a^T, M_aa = rho V / 10 I, and per absorbing face the linear
+// triangle's (2/dt) (area / 6) T.
+__global__ void coarse_blocks_kernel(ModelView m, const int32_t* __restrict__ vid, double* __restrict__ cblk) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < m.E) {
+    const int64_t e = t;
+    double g[4][3];
+    for (int i = 0; i < 3; ++i) {
+      g[1][i] = m.geo[(0 + i) * m.E + e];
+      g[2][i] = m.geo[(3 + i) * m.E + e];
+      g[3][i] = m.geo[(6 + i) * m.E + e];
+      g[0][i] = -(g[1][i] + g[2][i] + g[3][i]);
+    }
+    const double V = m.geo[9 * m.E + e];
+    const MatCoef mc = m.mat[m.emat[e]];
+    const double kl = mc.cK * (mc.lam + mc.mu) * V, km = mc.cK * mc.mu * V;
+    const double md = mc.cM * mc.rho * V / 10.0;
+    for (int k = 0; k < 4; ++k) {
+      const double tr = g[k][0] * g[k][0] + g[k][1] * g[k][1] + g[k][2] * g[k][2];
+      double* d = cblk + 6 * (int64_t)vid[m.conn[k * m.E + e]];
+      atomicAdd(d + 0, kl * g[k][0] * g[k][0] + km * tr + md);
+      atomicAdd(d + 1, kl * g[k][1] * g[k][1] + km * tr + md);
+      atomicAdd(d + 2, kl * g[k][2] * g[k][2] + km * tr + md);
+      atomicAdd(d + 3, kl * g[k][0] * g[k][1]);
+      atomicAdd(d + 4, kl * g[k][0] * g[k][2]);
+      atomicAdd(d + 5, kl * g[k][1] * g[k][2]);
+    }
+  } else if (t < m.E + m.F) {
+    const int64_t f = t - m.E;
+    if (m.fgeo[5 * m.F + f] < 0.5) return;  // free surface
+    const double As = m.fgeo[f], Ad = m.fgeo[m.F + f];
+    const double n0 = m.fgeo[2 * m.F + f], n1 = m.fgeo[3 * m.F + f], n2 = m.fgeo[4 * m.F + f];
+    const double w = 2.0 / m.dt / 6.0;
+    for (int k = 0; k < 3; ++k) {
+      double* d = cblk + 6 * (int64_t)vid[m.fnode[k * m.F + f]];
+      atomicAdd(d + 0, w * (As + Ad * n0 * n0));
+      atomicAdd(d + 1, w * (As + Ad * n1 * n1));
+      atomicAdd(d + 2, w * (As + Ad * n2 * n2));
+      atomicAdd(d + 3, w * Ad * n0 * n1);
+      atomicAdd(d + 4, w * Ad * n0 * n2);
+      atomicAdd(d + 5, w * Ad * n1 * n2);
+    }
+  }
+}
+
 __global__ void invert_blocks_kernel(int64_t N, const double* __restrict__ dblk,
                                      double* __restrict__ dinv, int* err) {
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N;
@@ -934,6 +983,13 @@ void launch_block_jacobi(const ModelView& m, double* dblk, double* dinv, int* er
   if (m.E + m.F > 0)
     diag_blocks_kernel<<<(unsigned)((m.E + m.F + 127) / 128), 128, 0, s>>>(m, dblk);
   invert_blocks_kernel<<<node_blocks(m.N), kNodeThreads, 0, s>>>(m.N, dblk, dinv, err);
+}
+void launch_coarse_blocks(const ModelView& m, const int32_t* vid, double* cblk, cudaStream_t s) {
+  if (m.E + m.F > 0)
+    coarse_blocks_kernel<<<(unsigned)((m.E + m.F + 127) / 128), 128, 0, s>>>(m, vid, cblk);
+}
+void launch_invert_blocks(int64_t n, const double* blk, double* inv, int* err, cudaStream_t s) {
+  invert_blocks_kernel<<<node_blocks(n), kNodeThreads, 0, s>>>(n, blk, inv, err);
 }
 void launch_receivers(const ModelView& m, const double* xyz, double px, double py,
                       const double* rec_xy, int n_rec, int32_t* rec_face, int32_t* rec_node,

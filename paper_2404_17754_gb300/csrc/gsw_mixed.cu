@@ -714,6 +714,7 @@ __global__ void inner_init_kernel(int64_t N, const double* __restrict__ r, const
   if (last_block_reduce_f<1>(vals, reinterpret_cast<float*>(partials), &sc->counter, out) && threadIdx.x == 0) {
     sc->st = out[0];
     sc->st0 = out[0];
+    sc->st_f = out[0];
     sc->scale = scale;
     sc->rtol2 = rtol * rtol;
     sc->idone = (rtol > 0.f && !(out[0] > 0.f)) ? 1u : 0u;
@@ -827,7 +828,7 @@ __global__ void inner_alpha_kernel(const float* __restrict__ dw_part, InnerScala
 // block forms beta and tests the relative stopping factor.  With PRO (few
 // operator partials, i.e. a small model) every CTA forms alpha itself in a
 // prologue and no separate alpha kernel is launched.
-template <typename SD, bool PRO = false>
+template <typename SD, bool PRO = false, bool COARSE = false>
 __global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __restrict__ s, SD* __restrict__ t,
                                     const SD* __restrict__ d, float* __restrict__ w, const SD* __restrict__ dinv,
                                     double* partials, InnerScalars* sc, const CgScalars* outer,
@@ -904,6 +905,11 @@ __global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __r
   }
   float vals[1] = {st}, out[1];
   if (last_block_reduce_f<1>(vals, reinterpret_cast<float*>(partials), &sc->counter, out) && threadIdx.x == 0) {
+    if (COARSE) {  // s . t, beta and the stopping test follow in the restriction kernel
+      sc->st_f = out[0];
+      sc->iters += 1ull;
+      return;
+    }
     const double st_old = ((volatile InnerScalars*)sc)->st;
     const double beta = (st_old != 0.0) ? out[0] / st_old : 0.0;
     sc->beta = beta;
@@ -915,10 +921,22 @@ __global__ void inner_update_kernel(int64_t N, float* __restrict__ y, float* __r
   }
 }
 
-// d = t + beta d (the padding entry of each node stays 0).
-template <typename SD>
+// P z_c at fine node n: the mean of its two vertices' coarse values (a vertex
+// node names its own vertex twice).
+__device__ __forceinline__ void prolong_add(const float4* __restrict__ zc, int a, int b, float* v) {
+  const float4 za = __ldg(zc + a), zb = __ldg(zc + b);
+  v[0] += 0.5f * (za.x + zb.x);
+  v[1] += 0.5f * (za.y + zb.y);
+  v[2] += 0.5f * (za.z + zb.z);
+}
+
+// d = t + beta d (the padding entry of each node stays 0); with CO (the
+// two-level preconditioner) t is the fine part D^-1 s and the coarse part
+// P z_c is added on the fly: d = t + P z_c + beta d.
+template <typename SD, bool CO = false>
 __global__ void inner_dupdate_kernel(int64_t N, const SD* __restrict__ t, SD* __restrict__ d,
-                                     const InnerScalars* sc, const CgScalars* outer) {
+                                     const InnerScalars* sc, const CgScalars* outer,
+                                     const int2* __restrict__ pair = nullptr, const float4* __restrict__ zc = nullptr) {
   if (inner_stopped(outer, sc)) return;
   const float beta = ((volatile const InnerScalars*)sc)->beta_f;
   const int64_t g0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -927,6 +945,14 @@ __global__ void inner_dupdate_kernel(int64_t N, const SD* __restrict__ t, SD* __
     float tv[16], dv[16];
     ld_dir(t + 16 * g, tv);
     ld_dir(d + 16 * g, dv);
+    if (CO) {
+      const int4* pp = reinterpret_cast<const int4*>(pair + 4 * g);
+      const int4 p01 = __ldg(pp), p23 = __ldg(pp + 1);
+      prolong_add(zc, p01.x, p01.y, tv);
+      prolong_add(zc, p01.z, p01.w, tv + 4);
+      prolong_add(zc, p23.x, p23.y, tv + 8);
+      prolong_add(zc, p23.z, p23.w, tv + 12);
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -934,10 +960,97 @@ __global__ void inner_dupdate_kernel(int64_t N, const SD* __restrict__ t, SD* __
     st_dir(d + 16 * g, dv);
   }
   if (g0 == 0) {
-    for (int64_t n = 4 * G4; n < N; ++n)
+    for (int64_t n = 4 * G4; n < N; ++n) {
+      float tn[3] = {to_f(t[4 * n]), to_f(t[4 * n + 1]), to_f(t[4 * n + 2])};
+      if (CO) prolong_add(zc, pair[n].x, pair[n].y, tn);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) d[4 * n + i] = from_f<SD>(fmaf(beta, to_f(d[4 * n + i]), to_f(t[4 * n + i])));
+      for (int i = 0; i < 3; ++i) d[4 * n + i] = from_f<SD>(fmaf(beta, to_f(d[4 * n + i]), tn[i]));
+    }
   }
+}
+
+// ------------------------------------------------------------------------------
+// Two-level inner preconditioner: first-order (vertex) coarse level
+// ------------------------------------------------------------------------------
+//
+// t = D^-1 s + omega P D_c^-1 P^T s.  The update kernel forms the fine part
+// (t = D^-1 s and s . D^-1 s); this kernel forms z_c = omega D_c^-1 P^T s,
+// (P^T s)_v = s_v + 1/2 sum of s over the mid-edge nodes on v's edges (a
+// gather over the vertex's CSR row: deterministic, no atomics), and completes
+// s . t = s . D^-1 s + (P^T s) . z_c; the direction update adds P z_c.  With
+// sc == nullptr it only forms z_c (diagnostics).  first: the start of an inner
+// solve (s . t becomes the reference of the stopping test, beta = 0).
+__global__ void coarse_restrict_kernel(CoarseView c, const float* __restrict__ s, float4* __restrict__ zc,
+                                       double* partials, InnerScalars* sc, const CgScalars* outer, int first) {
+  if (sc != nullptr && inner_stopped(outer, sc)) return;
+  float acc = 0.f;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < c.Nv; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = __ldg(c.vnode + v);
+    float h[3] = {0.f, 0.f, 0.f};
+    const int j1 = __ldg(c.ptr + v + 1);
+    for (int j = __ldg(c.ptr + v); j < j1; ++j) {
+      const int64_t mnode = __ldg(c.mid + j);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) h[i] += s[3 * mnode + i];
+    }
+    float r[3], z[3], D[6];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) r[i] = fmaf(0.5f, h[i], s[3 * n + i]);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) D[k] = __ldg(c.dc + 6 * v + k);
+    dinv_apply_f(D, r, z);
+    zc[v] = make_float4(z[0], z[1], z[2], 0.f);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) acc = fmaf(r[i], z[i], acc);
+  }
+  if (sc == nullptr) return;
+  float vals[1] = {acc}, out[1];
+  if (last_block_reduce_f<1>(vals, reinterpret_cast<float*>(partials), &sc->counter, out) && threadIdx.x == 0) {
+    const volatile InnerScalars* vs = sc;
+    const double st = vs->st_f + (double)out[0];
+    const float r2 = vs->rtol2;
+    if (first) {
+      sc->st = st;
+      sc->st0 = st;
+      sc->beta = 0.0;
+      sc->beta_f = 0.f;
+      sc->idone = (r2 > 0.f && !(st > 0.0)) ? 1u : 0u;
+    } else {
+      const double st_old = vs->st;
+      const double beta = (st_old != 0.0) ? st / st_old : 0.0;
+      sc->beta = beta;
+      sc->beta_f = (float)beta;
+      sc->st = st;
+      if (r2 > 0.f && st <= (double)r2 * vs->st0) sc->idone = 1u;
+    }
+  }
+}
+
+// y = scale * P z_c in FP64 (diagnostics).
+__global__ void coarse_prolong_kernel(int64_t N, const int2* __restrict__ pair, const float4* __restrict__ zc,
+                                      double scale, double* __restrict__ y) {
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+    const int2 p = pair[n];
+    const float4 a = zc[p.x], b = zc[p.y];
+    y[3 * n] = scale * 0.5 * ((double)a.x + (double)b.x);
+    y[3 * n + 1] = scale * 0.5 * ((double)a.y + (double)b.y);
+    y[3 * n + 2] = scale * 0.5 * ((double)a.z + (double)b.z);
+  }
+}
+
+// omega D_c^-1 in FP32, divided by the mean diagonal entry of D^-1 like the
+// fine blocks (the inner right-hand side is scaled to match).
+__global__ void coarse_lo_kernel(int64_t n6, const double* __restrict__ cinv, const InnerScalars* sc, double omega,
+                                 float* __restrict__ dc) {
+  const double dm = ((volatile const InnerScalars*)sc)->dinv_mean;
+  const double f = omega / (dm > 0.0 ? dm : 1.0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n6; i += (int64_t)gridDim.x * blockDim.x)
+    dc[i] = (float)(cinv[i] * f);
+}
+
+__global__ void to_f32_kernel(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
 }
 
 // ------------------------------------------------------------------------------
@@ -2040,8 +2153,61 @@ void launch_inner_update(int64_t N, float* y, float* s, void* t, const void* d, 
         N, y, s, (float*)t, (const float*)d, w, (const float*)dinv_lo, partials, sc, outer);
   }
 }
+void launch_inner_update_coarse(int64_t N, float* y, float* s, void* t, const void* d, int half_vec, float* w,
+                                const void* dinv_lo, const float* dw_part, double* partials, InnerScalars* sc,
+                                cudaStream_t st, const CgScalars* outer, int n_dw_max) {
+  if (n_dw_max <= kAlphaPrologueMax) {
+    if (half_vec) {
+      static const unsigned cap = persistent_cap((const void*)inner_update_kernel<__half, true, true>);
+      inner_update_kernel<__half, true, true><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(
+          N, y, s, (__half*)t, (const __half*)d, w, (const __half*)dinv_lo, partials, sc, outer, dw_part);
+    } else {
+      static const unsigned cap = persistent_cap((const void*)inner_update_kernel<float, true, true>);
+      inner_update_kernel<float, true, true><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(
+          N, y, s, (float*)t, (const float*)d, w, (const float*)dinv_lo, partials, sc, outer, dw_part);
+    }
+    return;
+  }
+  inner_alpha_kernel<<<1, 1024, 0, st>>>(dw_part, sc, outer);
+  if (half_vec) {
+    static const unsigned cap = persistent_cap((const void*)inner_update_kernel<__half, false, true>);
+    inner_update_kernel<__half, false, true><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(
+        N, y, s, (__half*)t, (const __half*)d, w, (const __half*)dinv_lo, partials, sc, outer);
+  } else {
+    static const unsigned cap = persistent_cap((const void*)inner_update_kernel<float, false, true>);
+    inner_update_kernel<float, false, true><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(
+        N, y, s, (float*)t, (const float*)d, w, (const float*)dinv_lo, partials, sc, outer);
+  }
+}
+void launch_coarse_restrict(const CoarseView& c, const float* s, float4* zc, double* partials, InnerScalars* sc,
+                            const CgScalars* outer, int first, cudaStream_t st) {
+  if (c.Nv <= 0) return;
+  coarse_restrict_kernel<<<node_blocks(c.Nv), kNodeThreads, 0, st>>>(c, s, zc, partials, sc, outer, first);
+}
+void launch_coarse_prolong(int64_t N, const int2* pair, const float4* zc, double scale, double* y, cudaStream_t st) {
+  coarse_prolong_kernel<<<node_blocks(N), kNodeThreads, 0, st>>>(N, pair, zc, scale, y);
+}
+void launch_coarse_lo(int64_t Nv, const double* cinv, const InnerScalars* sc, double omega, float* dc,
+                      cudaStream_t st) {
+  coarse_lo_kernel<<<node_blocks(6 * Nv), kNodeThreads, 0, st>>>(6 * Nv, cinv, sc, omega, dc);
+}
+void launch_to_f32(int64_t n, const double* x, float* y, cudaStream_t st) {
+  to_f32_kernel<<<node_blocks(n), kNodeThreads, 0, st>>>(n, x, y);
+}
 void launch_inner_dupdate(int64_t N, const void* t, void* d, int half_vec, const InnerScalars* sc,
-                          cudaStream_t st, const CgScalars* outer) {
+                          cudaStream_t st, const CgScalars* outer, const int2* pair, const float4* zc) {
+  if (zc != nullptr) {
+    if (half_vec) {
+      static const unsigned cap = persistent_cap((const void*)inner_dupdate_kernel<__half, true>);
+      inner_dupdate_kernel<__half, true><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(N, (const __half*)t, (__half*)d,
+                                                                                   sc, outer, pair, zc);
+    } else {
+      static const unsigned cap = persistent_cap((const void*)inner_dupdate_kernel<float, true>);
+      inner_dupdate_kernel<float, true><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(N, (const float*)t, (float*)d,
+                                                                                  sc, outer, pair, zc);
+    }
+    return;
+  }
   if (half_vec) {
     static const unsigned cap = persistent_cap((const void*)inner_dupdate_kernel<__half>);
     inner_dupdate_kernel<__half><<<quad_grid(N, cap), kNodeThreads, 0, st>>>(N, (const __half*)t, (__half*)d, sc,

@@ -32,7 +32,8 @@ class SolverOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("precision", C.c_int32),
                 ("inner_iters", C.c_int32), ("check_every", C.c_int32), ("batch_outer", C.c_int32),
                 ("inner_variant", C.c_int32), ("inner_rtol", C.c_double), ("guess_order", C.c_int32),
-                ("outer_op", C.c_int32), ("share_dirs", C.c_int32), ("proj_dim", C.c_int32)]
+                ("outer_op", C.c_int32), ("share_dirs", C.c_int32), ("proj_dim", C.c_int32),
+                ("coarse_weight", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -303,9 +304,9 @@ class Model:
 
     def set_solver(self, tol=1e-8, max_iter=10000, precision=PREC_FP64, inner_iters=20, check_every=8,
                    batch_outer=6, inner_variant=-1, inner_rtol=0.0, guess_order=0, outer_op=OUTER_AUTO,
-                   share_dirs=0, proj_dim=0):
+                   share_dirs=0, proj_dim=0, coarse_weight=0.0):
         o = SolverOpts(tol, max_iter, precision, inner_iters, check_every, batch_outer, inner_variant, inner_rtol,
-                       guess_order, outer_op, int(share_dirs), int(proj_dim))
+                       guess_order, outer_op, int(share_dirs), int(proj_dim), float(coarse_weight))
         self._c(self.ctx.lib.gsw_set_solver(self.ctx.h, self.id, C.byref(o)))
 
     def reset(self):
@@ -388,8 +389,9 @@ class Model:
         self._c(self.ctx.lib.gsw_set_state(self.ctx.h, self.id, pu, pv, pa, int(step)))
 
     def apply(self, which, x):
-        """y = A x (0), K x (1), M x (2), C x (3), A x by the inner reduced-precision operator (4), or A x
-        in double-word arithmetic (5)."""
+        """y = A x (0), K x (1), M x (2), C x (3), A x by the inner reduced-precision operator (4), A x
+        in double-word arithmetic (5), or the two-level inner preconditioner's coarse correction
+        P D_c^-1 P^T x (6)."""
         torch = self.ctx._torch
         assert x.is_cuda and x.dtype == torch.float64 and x.is_contiguous() and x.numel() == 3 * self.n_nodes
         y = torch.empty_like(x)
