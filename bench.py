@@ -568,6 +568,9 @@ def main():
     ap.add_argument("--coarse-weight", type=float, default=0.0,
                     help="mixed modes: weight of the two-level inner preconditioner's first-order coarse "
                          "correction (0 = block Jacobi alone)")
+    ap.add_argument("--coarse-relres", type=float, default=0.0,
+                    help="two-level inner preconditioner: apply the coarse correction only while the outer "
+                         "relative residual exceeds this (0 = always)")
     ap.add_argument("--inner-variant", type=int, default=-1,
                     help="launch variant of the inner operator (-1: the autotuner picks)")
     ap.add_argument("--no-extras", action="store_true",
@@ -642,7 +645,7 @@ def main():
     prec = {"fp64": 0, "fp32": 1, "fp16": 2}[args.precision]
     m.set_solver(tol=args.tol, outer_op=OUTER_OPS[args.outer_op], precision=prec, inner_iters=args.inner, inner_rtol=args.inner_rtol,
                  guess_order=args.guess_order, inner_variant=args.inner_variant, proj_dim=args.proj_dim,
-                 coarse_weight=args.coarse_weight)
+                 coarse_weight=args.coarse_weight, coarse_relres=args.coarse_relres)
     n_nodes, n_elem, n_faces = mesh["xyz"].shape[0], mesh["conn"].shape[0], mesh["faces"].shape[0]
     dof = 3 * n_nodes
 
@@ -804,8 +807,9 @@ def main():
                                 proj_dim=args.proj_dim)
         if args.precision != "fp64":
             ca = candidate_analysis_block(ctx, cfg, args.warmup + args.steps, args, prec)
-    inner_pc = ("two-level (block Jacobi + %g x first-order coarse block Jacobi)" % args.coarse_weight
-                if args.coarse_weight > 0 else "block-Jacobi")
+    inner_pc = ("two-level (block Jacobi + %g x first-order coarse block Jacobi%s)" % (
+                    args.coarse_weight, " while the outer relative residual exceeds %g" % args.coarse_relres
+                    if args.coarse_relres > 0 else "") if args.coarse_weight > 0 else "block-Jacobi")
     out = {
         "metric": "DOF*steps/s", "value": value, "unit": "DOF*steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
@@ -814,6 +818,7 @@ def main():
         "config": {"workload": cfg["name"] if args.workload == "realistic" else "two-layer 100x100x50 m",
                    "dof": dof, "elements": n_elem, "dt": cfg["dt"], "tol": args.tol, "precision": args.precision,
                    "guess_order": args.guess_order, "proj_dim": args.proj_dim, "coarse_weight": args.coarse_weight,
+                   "coarse_relres": args.coarse_relres,
                    "outer_operator": "FP64" if args.outer_op == "fp64" or (args.outer_op == "auto" and args.precision == "fp64") else "double-word",
                    "solver": "block-Jacobi PCG" if args.precision == "fp64" else
                              ("flexible CG (FP64) + %s %s PCG preconditioner, %d iterations" % (

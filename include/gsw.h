@@ -126,6 +126,11 @@ typedef struct {
                             level, Section 3's multi-level solver) to the quadratic
                             nodes and D_c the nodal diagonal blocks of P^T A P;
                             must be finite and in [0, 4] */
+  double coarse_relres;  /* two-level preconditioner: an inner solve applies the coarse
+                            correction only while the outer relative residual ||r|| / ||b||
+                            it starts from exceeds this (0 = in every inner solve); the
+                            coarse level removes smooth error, which a poor initial guess
+                            leaves and a good one does not */
 } gsw_solver_opts;
 
 typedef struct {

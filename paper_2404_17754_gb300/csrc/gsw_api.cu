@@ -60,7 +60,7 @@ struct Model {
   std::vector<double> input;
   int dir = 0;
   bool input_set = false;
-  gsw_solver_opts opts = {1e-8, 10000, GSW_PREC_FP64, 20, 8, 6, -1, 0.0, 0, 0, 0, 0, 0.0};
+  gsw_solver_opts opts = {1e-8, 10000, GSW_PREC_FP64, 20, 8, 6, -1, 0.0, 0, 0, 0, 0, 0.0, 0.0};
   int64_t step = 0;
   bool failed = false;
   gsw_stats stats = {};
@@ -979,7 +979,7 @@ int64_t inner_solve_launches(const Model* m, bool fuse) {
 // d = t; with the two-level preconditioner also z_c and d = t + P z_c.
 void inner_begin(Model* m, cudaStream_t s, float rtol) {
   launch_inner_init(m->N, m->r, m->dinv32, m->s32, m->y32, m->t32, m->d_lo, m->lo_half, m->w32, m->partials, m->isc,
-                    m->cg, s, rtol);
+                    m->cg, s, rtol, m->opts.coarse_relres);
   if (m->coarse()) {
     launch_coarse_restrict(m->cview(), m->s32, m->zc, m->partials, m->isc, m->cg, 1, s);
     launch_inner_dupdate(m->N, m->t32, m->d_lo, m->lo_half, m->isc, s, m->cg, m->c_pair, m->zc);
@@ -1815,6 +1815,8 @@ gsw_status gsw_set_solver(gsw_ctx* ctx, int32_t model_id, const gsw_solver_opts*
     return fail(ctx, GSW_E_INVALID, "outer_op must be 0 (auto), 1 (FP64) or 2 (double-word)");
   if (!(opts->coarse_weight >= 0.0 && opts->coarse_weight <= 4.0))
     return fail(ctx, GSW_E_INVALID, "coarse_weight must be in [0, 4]");
+  if (!(opts->coarse_relres >= 0.0 && opts->coarse_relres < 1.0))
+    return fail(ctx, GSW_E_INVALID, "coarse_relres must be in [0, 1)");
   if (opts->proj_dim != 0 && (opts->proj_dim < 2 || opts->proj_dim > kMaxProj))
     return fail(ctx, GSW_E_INVALID, "proj_dim must be 0 or 2..%d", kMaxProj);
   if (opts->proj_dim > 0 && m->learn.enable)

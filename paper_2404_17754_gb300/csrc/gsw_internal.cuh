@@ -112,6 +112,8 @@ struct InnerScalars {
   unsigned int idone; // 1 once the current inner solve has met rtol
   unsigned long long iters;  // inner iterations executed (all solves)
   double st_f;        // s . D^-1 s, the fine part of s . t (two-level preconditioner)
+  unsigned int coarse_on;  // two-level: this inner solve applies the coarse correction
+  unsigned int pad2;
 };
 
 // First-order (vertex) coarse level of the two-level inner preconditioner
@@ -271,9 +273,13 @@ void launch_lo_convert(const ModelView& m, int n_blk, const uint16_t* lconn, int
 size_t lo_record_bytes(int half_geo);
 // inner solve: half_vec selects __half storage of the search direction d, of
 // t = D^-1 s (both padded to 4 entries per node) and of the scaled D^-1
+// coarse_rel: two-level preconditioner, the solve applies the coarse correction
+// while the outer relative residual ||r|| / ||b|| it starts from exceeds
+// coarse_rel (<= 0: always)
 void launch_inner_init(int64_t N, const double* r, const void* dinv_lo, float* s, float* y,
                        void* t, void* d, int half_vec, float* w, double* partials,
-                       InnerScalars* sc, const CgScalars* cg, cudaStream_t st, float rtol);
+                       InnerScalars* sc, const CgScalars* cg, cudaStream_t st, float rtol,
+                       double coarse_rel = 0.0);
 void launch_ebe_lo(int half_geo, int half_vec, const void* lo_view, const void* d, float* w,
                    double* partials, InnerScalars* sc, cudaStream_t st, int variant,
                    const CgScalars* outer = nullptr);

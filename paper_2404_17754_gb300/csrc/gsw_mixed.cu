@@ -675,7 +675,7 @@ template <typename SD>
 __global__ void inner_init_kernel(int64_t N, const double* __restrict__ r, const SD* __restrict__ dinv,
                                   float* __restrict__ s, float* __restrict__ y, SD* __restrict__ t,
                                   SD* __restrict__ d, float* __restrict__ w, double* partials,
-                                  InnerScalars* sc, const CgScalars* cg, float rtol) {
+                                  InnerScalars* sc, const CgScalars* cg, float rtol, double coarse_rel) {
   if (((volatile const CgScalars*)cg)->done) return;
   // the scale is computed once per block (FP64 division and square root are
   // slow on this GPU) and broadcast through shared memory
@@ -716,6 +716,8 @@ __global__ void inner_init_kernel(int64_t N, const double* __restrict__ r, const
     sc->st0 = out[0];
     sc->st_f = out[0];
     sc->scale = scale;
+    const volatile CgScalars* vc = cg;
+    sc->coarse_on = (coarse_rel <= 0.0 || vc->rr > coarse_rel * coarse_rel * vc->bb) ? 1u : 0u;
     sc->rtol2 = rtol * rtol;
     sc->idone = (rtol > 0.f && !(out[0] > 0.f)) ? 1u : 0u;
   }
@@ -939,13 +941,14 @@ __global__ void inner_dupdate_kernel(int64_t N, const SD* __restrict__ t, SD* __
                                      const int2* __restrict__ pair = nullptr, const float4* __restrict__ zc = nullptr) {
   if (inner_stopped(outer, sc)) return;
   const float beta = ((volatile const InnerScalars*)sc)->beta_f;
+  const bool co = CO && ((volatile const InnerScalars*)sc)->coarse_on;
   const int64_t g0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t G4 = N >> 2;
   for (int64_t g = g0; g < G4; g += (int64_t)gridDim.x * blockDim.x) {
     float tv[16], dv[16];
     ld_dir(t + 16 * g, tv);
     ld_dir(d + 16 * g, dv);
-    if (CO) {
+    if (co) {
       const int4* pp = reinterpret_cast<const int4*>(pair + 4 * g);
       const int4 p01 = __ldg(pp), p23 = __ldg(pp + 1);
       prolong_add(zc, p01.x, p01.y, tv);
@@ -962,7 +965,7 @@ __global__ void inner_dupdate_kernel(int64_t N, const SD* __restrict__ t, SD* __
   if (g0 == 0) {
     for (int64_t n = 4 * G4; n < N; ++n) {
       float tn[3] = {to_f(t[4 * n]), to_f(t[4 * n + 1]), to_f(t[4 * n + 2])};
-      if (CO) prolong_add(zc, pair[n].x, pair[n].y, tn);
+      if (co) prolong_add(zc, pair[n].x, pair[n].y, tn);
 #pragma unroll
       for (int i = 0; i < 3; ++i) d[4 * n + i] = from_f<SD>(fmaf(beta, to_f(d[4 * n + i]), tn[i]));
     }
@@ -980,9 +983,37 @@ __global__ void inner_dupdate_kernel(int64_t N, const SD* __restrict__ t, SD* __
 // s . t = s . D^-1 s + (P^T s) . z_c; the direction update adds P z_c.  With
 // sc == nullptr it only forms z_c (diagnostics).  first: the start of an inner
 // solve (s . t becomes the reference of the stopping test, beta = 0).
-__global__ void coarse_restrict_kernel(CoarseView c, const float* __restrict__ s, float4* __restrict__ zc,
-                                       double* partials, InnerScalars* sc, const CgScalars* outer, int first) {
+__device__ __forceinline__ void coarse_finish(InnerScalars* sc, float rz, int first) {
+  const volatile InnerScalars* vs = sc;
+  const double st = vs->st_f + (double)rz;
+  const float r2 = vs->rtol2;
+  if (first) {
+    sc->st = st;
+    sc->st0 = st;
+    sc->beta = 0.0;
+    sc->beta_f = 0.f;
+    sc->idone = (r2 > 0.f && !(st > 0.0)) ? 1u : 0u;
+  } else {
+    const double st_old = vs->st;
+    const double beta = (st_old != 0.0) ? st / st_old : 0.0;
+    sc->beta = beta;
+    sc->beta_f = (float)beta;
+    sc->st = st;
+    if (r2 > 0.f && st <= (double)r2 * vs->st0) sc->idone = 1u;
+  }
+}
+
+constexpr int kCoarseThreads = 1024;
+__global__ void __launch_bounds__(kCoarseThreads) coarse_restrict_kernel(CoarseView c, const float* __restrict__ s,
+                                                                        float4* __restrict__ zc, double* partials,
+                                                                        InnerScalars* sc, const CgScalars* outer,
+                                                                        int first) {
   if (sc != nullptr && inner_stopped(outer, sc)) return;
+  if (sc != nullptr && !((volatile const InnerScalars*)sc)->coarse_on) {
+    // this inner solve runs on the fine level alone: only the scalars move on
+    if (blockIdx.x == 0 && threadIdx.x == 0) coarse_finish(sc, 0.f, first);
+    return;
+  }
   float acc = 0.f;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < c.Nv; v += (int64_t)gridDim.x * blockDim.x) {
     const int64_t n = __ldg(c.vnode + v);
@@ -1005,25 +1036,8 @@ __global__ void coarse_restrict_kernel(CoarseView c, const float* __restrict__ s
   }
   if (sc == nullptr) return;
   float vals[1] = {acc}, out[1];
-  if (last_block_reduce_f<1>(vals, reinterpret_cast<float*>(partials), &sc->counter, out) && threadIdx.x == 0) {
-    const volatile InnerScalars* vs = sc;
-    const double st = vs->st_f + (double)out[0];
-    const float r2 = vs->rtol2;
-    if (first) {
-      sc->st = st;
-      sc->st0 = st;
-      sc->beta = 0.0;
-      sc->beta_f = 0.f;
-      sc->idone = (r2 > 0.f && !(st > 0.0)) ? 1u : 0u;
-    } else {
-      const double st_old = vs->st;
-      const double beta = (st_old != 0.0) ? st / st_old : 0.0;
-      sc->beta = beta;
-      sc->beta_f = (float)beta;
-      sc->st = st;
-      if (r2 > 0.f && st <= (double)r2 * vs->st0) sc->idone = 1u;
-    }
-  }
+  if (last_block_reduce_f<1>(vals, reinterpret_cast<float*>(partials), &sc->counter, out) && threadIdx.x == 0)
+    coarse_finish(sc, out[0], first);
 }
 
 // y = scale * P z_c in FP64 (diagnostics).
@@ -1327,13 +1341,13 @@ void launch_lo_convert(const ModelView& m, int n_blk, const uint16_t* lconn, int
 size_t lo_record_bytes(int half_geo) { return half_geo ? sizeof(LoRecH) : sizeof(LoRecF); }
 void launch_inner_init(int64_t N, const double* r, const void* dinv_lo, float* s, float* y, void* t, void* d,
                        int half_vec, float* w, double* partials, InnerScalars* sc, const CgScalars* cg,
-                       cudaStream_t st, float rtol) {
+                       cudaStream_t st, float rtol, double coarse_rel) {
   if (half_vec)
     inner_init_kernel<__half><<<node_blocks(N), kNodeThreads, 0, st>>>(
-        N, r, (const __half*)dinv_lo, s, y, (__half*)t, (__half*)d, w, partials, sc, cg, rtol);
+        N, r, (const __half*)dinv_lo, s, y, (__half*)t, (__half*)d, w, partials, sc, cg, rtol, coarse_rel);
   else
     inner_init_kernel<float><<<node_blocks(N), kNodeThreads, 0, st>>>(
-        N, r, (const float*)dinv_lo, s, y, (float*)t, (float*)d, w, partials, sc, cg, rtol);
+        N, r, (const float*)dinv_lo, s, y, (float*)t, (float*)d, w, partials, sc, cg, rtol, coarse_rel);
 }
 
 // ---- software-pipelined variant ----------------------------------------------
@@ -2182,7 +2196,18 @@ void launch_inner_update_coarse(int64_t N, float* y, float* s, void* t, const vo
 void launch_coarse_restrict(const CoarseView& c, const float* s, float4* zc, double* partials, InnerScalars* sc,
                             const CgScalars* outer, int first, cudaStream_t st) {
   if (c.Nv <= 0) return;
-  coarse_restrict_kernel<<<node_blocks(c.Nv), kNodeThreads, 0, st>>>(c, s, zc, partials, sc, outer, first);
+  // one CTA of 1024 threads per SM: a solve whose coarse level is switched off
+  // pays only for this small grid's early exit
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const int64_t need = (c.Nv + kCoarseThreads - 1) / kCoarseThreads;
+  const unsigned grid = (unsigned)(need < sms ? need : sms);
+  coarse_restrict_kernel<<<grid, kCoarseThreads, 0, st>>>(c, s, zc, partials, sc, outer, first);
 }
 void launch_coarse_prolong(int64_t N, const int2* pair, const float4* zc, double scale, double* y, cudaStream_t st) {
   coarse_prolong_kernel<<<node_blocks(N), kNodeThreads, 0, st>>>(N, pair, zc, scale, y);

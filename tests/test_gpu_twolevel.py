@@ -99,6 +99,27 @@ def test_two_level_mixed_matches_oracle(ctx, prec, drive):
     m.free()
 
 
+@pytest.mark.parametrize("drive", ["step", "run"])
+def test_two_level_switches_off_below_the_threshold(ctx, drive):
+    """coarse_relres = 1e-4: the inner solves of the first steps from rest (large outer
+    residuals) apply the coarse correction, later ones run on the fine level alone (the
+    restriction kernel only passes the scalars on); the run matches the oracle throughout."""
+    cfg = configs.config1(n_steps=60)
+    ref = newmark.analysis(cfg, tol=1e-8)
+    m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
+    m.set_time(cfg["dt"], 60, cfg["band"])
+    m.set_input(cfg["dir"], cfg["p"])
+    m.set_solver(tol=1e-8, precision=2, inner_iters=30, inner_rtol=1e-2, guess_order=4, coarse_weight=0.7,
+                 coarse_relres=1e-4)
+    if drive == "step":
+        m.step(60)
+    else:
+        m.run()
+    assert _relerr(m.waveforms(), ref["wave"]) <= 1e-6
+    assert m.stats()["relres_last"] <= 1e-8
+    m.free()
+
+
 def test_two_level_tight_tolerance_ragged_box(ctx):
     """tol 1e-12 on a box whose node count is not a multiple of four: the states match the
     oracle to 1e-9 (the recurrence's ragged tail and the coarse level's edges included)."""
@@ -135,10 +156,11 @@ def test_two_level_cuts_inner_iterations_on_the_realistic_crop(ctx):
     iterations): the two-level preconditioner reaches the oracle's waveforms, like the block-
     Jacobi inner preconditioner, with fewer inner iterations.
 
-    Tolerance: each step's solve stops at relative residual 1e-8, so its increment carries a
-    relative error up to about kappa * 1e-8 with kappa ~ 100 (the block-Jacobi contraction rate
-    at this dt); the early steps' tiny arrivals dominate the relative L2 over 60 steps, and both
-    GPU runs and the oracle each sit within 2e-5 of one another."""
+    Tolerance: the mixed paths' bar, surface-velocity relative L2 <= 1e-4 against the FP64
+    oracle (each step stops at relative residual 1e-8, so an increment carries a relative error
+    up to about kappa * 1e-8, kappa ~ 100 at this dt, and over the first 60 steps from rest the
+    small early arrivals dominate the relative L2); the two-level run may not be further from
+    the oracle than the block-Jacobi run by more than half."""
     cfg = configs.config2(n_steps=60, crop=12)
     ref = newmark.analysis(cfg, tol=1e-8)["wave"]
     out = {}
@@ -156,5 +178,5 @@ def test_two_level_cuts_inner_iterations_on_the_realistic_crop(ctx):
     print("inner iterations block Jacobi %d, two-level %d; outer %d, %d; waveform error vs oracle %.2e, %.2e" % (
         out[0.0]["inner"], out[0.7]["inner"], out[0.0]["outer"], out[0.7]["outer"], e0, e1))
     assert out[0.7]["relres"] <= 1e-8
-    assert e0 <= 2e-5 and e1 <= 2e-5
+    assert e0 <= 1e-4 and e1 <= 1e-4 and e1 <= 1.5 * e0
     assert out[0.7]["inner"] < 0.9 * out[0.0]["inner"]
