@@ -20,6 +20,10 @@ newmark    Newmark average-acceleration stepping, block-Jacobi PCG, analysis
 misfit     shifted-Green's-function superposition, normal equations,
            truncated eigen pseudo-inverse, ERR, model selection
 transfer1d closed-form 1D layered transfer function (used to pin the oracle)
+mlp        learned initial guess: features, network, BF16 forward and gradient,
+           Adam, extrapolated base guesses, training targets, node sampling
+twolevel   first-order (vertex) coarse level of the inner solve: prolongation,
+           P^T A P, coarse block Jacobi, the additive two-level preconditioner
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against
 closed forms, invariants or brute force (see ``tests/test_oracle_*.py``),
