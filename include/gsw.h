@@ -329,6 +329,16 @@ gsw_status gsw_read_preconditioner(gsw_ctx *ctx, int32_t model_id, double *out);
  * 6-node surface triangle containing each receiver. */
 gsw_status gsw_read_receivers(gsw_ctx *ctx, int32_t model_id, int32_t *nodes, double *weights);
 
+/* Failure-detection self-test (no counterpart in the paper).  Runs the bounded
+ * mbarrier wait that guards the warp-specialised inner operator's pipeline
+ * stages on a barrier that expects one arrival which never comes, with `limit`
+ * attempts (1 .. 2^22; each attempt may suspend the thread for a short,
+ * hardware-bounded time).  The wait must run out: the call returns
+ * GSW_E_TIMEOUT, the status a solve whose wait ran out reports, and the context
+ * stays usable.  GSW_OK would mean the wait completed without an arrival;
+ * GSW_E_INVALID for a limit outside the range. */
+gsw_status gsw_wait_probe(gsw_ctx *ctx, int64_t limit);
+
 /* ---- learned initial guess ------------------------------------------------
  * A per-node MLP (16 -> 64 -> 64 -> 3, ReLU) corrects the step's base guess
  * (the Newmark predictor dt v + dt^2/2 a, or the guess_order extrapolation):

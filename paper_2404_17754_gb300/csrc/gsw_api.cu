@@ -2598,6 +2598,28 @@ gsw_status gsw_read_preconditioner(gsw_ctx* ctx, int32_t model_id, double* out) 
   return GSW_OK;
 }
 
+gsw_status gsw_wait_probe(gsw_ctx* ctx, int64_t limit) {
+  if (!ctx) return GSW_E_INVALID;
+  if (limit < 1 || limit > (int64_t)1 << 22) return fail(ctx, GSW_E_INVALID, "limit must be 1 .. 2^22");
+  DeviceGuard g(ctx->device);
+  unsigned* out = (unsigned*)dev_alloc(ctx, nullptr, 2 * sizeof(unsigned));
+  if (!out) return fail(ctx, GSW_E_NOMEM, "device allocation failed (wait probe)");
+  unsigned h[2] = {0u, 0u};
+  cudaStream_t s = ctx->stream;
+  cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(unsigned), s);
+  if (e == cudaSuccess) {
+    launch_wait_probe((long long)limit, out, s);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, out, sizeof h, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dev_free(ctx, out);
+  if (e != cudaSuccess) return fail(ctx, GSW_E_CUDA, "wait probe: %s", cudaGetErrorString(e));
+  if (h[0] == 1u) return fail(ctx, GSW_E_TIMEOUT, "bounded wait ran out after %lld attempts (expected)",
+                              (long long)limit);
+  return GSW_OK;
+}
+
 gsw_status gsw_read_receivers(gsw_ctx* ctx, int32_t model_id, int32_t* nodes, double* weights) {
   if (!ctx || !nodes || !weights) return GSW_E_INVALID;
   DeviceGuard g(ctx->device);

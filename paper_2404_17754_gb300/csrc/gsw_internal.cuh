@@ -328,6 +328,8 @@ void launch_coarse_prolong(int64_t N, const int2* pair, const float4* zc, double
 void launch_coarse_lo(int64_t Nv, const double* cinv, const InnerScalars* sc, double omega, float* dc,
                       cudaStream_t st);
 void launch_to_f32(int64_t n, const double* x, float* y, cudaStream_t st);
+// failure-detection self-test of the bounded mbarrier wait (out[2] on the device)
+void launch_wait_probe(long long limit, unsigned* out, cudaStream_t st);
 // conversions for the standalone reduced-precision operator (tests)
 void launch_to_lo(int64_t N, const double* x, void* d, int half_vec, float* w, cudaStream_t s);
 void launch_from_f32(int64_t N, const float* w, double* y, cudaStream_t s);

@@ -1597,10 +1597,25 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, unsigned parity) {
   return ok != 0;
 }
 // bounded wait for the phase of the given parity; false if it ran out
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
-  for (long long it = 0; it < kWsSpin; ++it)
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, long long limit = kWsSpin) {
+  for (long long it = 0; it < limit; ++it)
     if (mbar_try(b, parity)) return true;
   return false;
+}
+
+// Failure-detection self-test: the bounded wait above on an mbarrier that
+// expects one arrival which never comes.  The wait runs out after `limit`
+// attempts; out[0] = 1 if it did, out[1] = 1 if it (wrongly) completed.
+__global__ void wait_probe_kernel(long long limit, unsigned* out) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1u);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    const bool done = mbar_wait(&bar, 0u, limit);
+    out[0] = done ? 0u : 1u;
+    out[1] = done ? 1u : 0u;
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_u32(&bar)) : "memory");
+  }
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
   asm volatile(
@@ -2262,6 +2277,10 @@ void launch_fcg_zbeta(const ModelView& m, const float* y, const double* r, const
 void launch_fcg_pupdate(const ModelView& m, const double* z, double* p, double* q, const CgScalars* cg,
                         cudaStream_t s, int dwp) {
   fcg_pupdate_kernel<<<node_blocks(3 * m.N), kNodeThreads, 0, s>>>(m.N, z, p, q, cg, dwp);
+}
+
+void launch_wait_probe(long long limit, unsigned* out, cudaStream_t st) {
+  wait_probe_kernel<<<1, 32, 0, st>>>(limit, out);
 }
 
 }  // namespace gsw

@@ -89,6 +89,7 @@ SIGNATURES = {
     "gsw_apply": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     "gsw_read_preconditioner": (C.c_int, [C.c_void_p, C.c_int32, _dp]),
     "gsw_read_receivers": (C.c_int, [C.c_void_p, C.c_int32, _ip, _dp]),
+    "gsw_wait_probe": (C.c_int, [C.c_void_p, C.c_int64]),
     "gsw_misfit": (C.c_int, [C.c_void_p, C.c_int32, _dp, C.c_int32, C.c_int32, C.c_double, _dp, _dp]),
     "gsw_misfit_green": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, _dp, _dp, C.c_int32, C.c_int32, C.c_double,
                                    _dp, _dp]),
@@ -213,6 +214,11 @@ class Context:
         self._check(self.lib.gsw_misfit_green(self.h, n_rec, n_t, pG, pO, stride, n_shifts, tau, C.byref(err),
                                               c.ctypes.data_as(_dp)))
         return err.value, c
+
+    def wait_probe(self, limit):
+        """Failure-detection self-test: the bounded device-side wait on a barrier nothing completes.
+        Returns the library status (``E_TIMEOUT`` expected) without raising."""
+        return int(self.lib.gsw_wait_probe(self.h, int(limit)))
 
     def run(self, models, dirs_mask=0):
         """Run analyses from rest to the end, batched: each model's own analysis (dirs_mask 0) or, for

@@ -176,6 +176,28 @@ def test_host_injected_failures(ctx):
     m.free()
 
 
+def test_bounded_wait_runs_out_and_the_context_stays_usable(ctx):
+    """The bounded mbarrier wait that guards the warp-specialised inner operator's stages, on a
+    barrier that nothing completes: it runs out and reports GSW_E_TIMEOUT (not a hang, not a
+    fault); afterwards the same context solves on the warp-specialised variant as before, and
+    limits outside 1 .. 2^22 are rejected."""
+    from paper_2404_17754_gb300 import gsw
+
+    for limit in (1, 1000):
+        assert ctx.wait_probe(limit) == gsw.E_TIMEOUT
+    assert ctx.wait_probe(0) == gsw.E_INVALID
+    assert ctx.wait_probe((1 << 22) + 1) == gsw.E_INVALID
+    cfg = configs.small_box(nx=3, ny=2, n_steps=12, seed=8)
+    m = _upload(ctx, cfg)
+    m.set_input(cfg["dir"], cfg["p"])
+    m.set_solver(tol=1e-8, precision=2, inner_iters=12, inner_variant=3)
+    m.step(12)
+    assert m.stats()["relres_last"] <= 1e-8
+    ref = newmark.analysis(cfg, tol=1e-8)["wave"]
+    assert _relerr(m.waveforms(), ref) <= 1e-6
+    m.free()
+
+
 @pytest.mark.parametrize("prec", [1, 2])
 def test_direction_analyses_in_lockstep_share_the_operator(ctx, prec):
     """share_dirs = 1: the three direction analyses of one model advance in lockstep and
