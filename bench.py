@@ -386,7 +386,8 @@ def run_candidates(args, rank, world, dist):
     ctx.close()
 
 
-def candidates_block(ctx, n_models, warmup, steps, tol, inner, guess_order, seq_models=16, proj_dim=0):
+def candidates_block(ctx, n_models, warmup, steps, tol, inner, guess_order, seq_models=16, proj_dim=0,
+                     coarse_weight=0.0, coarse_relres=0.0):
     """Candidate analyses/h of the mixed-ensemble candidates (120 x 120 x 300 m,
     287,451 DOF each, seeded interfaces, one directional analysis each, directions
     cycling x1, x2, x3) in three forms, each timed over `steps` steps after
@@ -407,7 +408,8 @@ def candidates_block(ctx, n_models, warmup, steps, tol, inner, guess_order, seq_
         m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
         m.set_time(cfg["dt"], n_total, cfg["band"])
         m.set_input(cfg["dir"], cfg["p"])
-        m.set_solver(tol=tol, precision=2, inner_iters=inner, guess_order=guess_order, proj_dim=proj_dim)
+        m.set_solver(tol=tol, precision=2, inner_iters=inner, guess_order=guess_order, proj_dim=proj_dim,
+                     coarse_weight=coarse_weight, coarse_relres=coarse_relres)
         models.append(m)
         dof += 3 * cfg["mesh"]["xyz"].shape[0]
     stream = ctx.stream
@@ -441,8 +443,10 @@ def candidates_block(ctx, n_models, warmup, steps, tol, inner, guess_order, seq_
     out["batched_mixed"] = {"candidate_analyses_per_hour": cah(t), "ms_per_step": 1e3 * t,
                             "outer_iters_per_model_step": it, "dof_steps_per_s": dof / t, "gpu_launches": kl,
                             "graph_kernel_nodes_captured": lps,
-                            "solver": "flexible CG (FP64, double-word outer operator) + fp16 block-Jacobi PCG "
+                            "solver": "flexible CG (FP64, double-word outer operator) + fp16 %s PCG "
                                       "preconditioner, %d iterations; initial guess %s" % (
+                                          "two-level (coarse level while the outer relative residual exceeds "
+                                          "%g)" % coarse_relres if coarse_weight > 0 else "block-Jacobi",
                                           inner, "projection onto the last %d increments" % proj_dim if proj_dim
                                           else "order %d" % guess_order)}
     for m in models:
@@ -635,9 +639,10 @@ def main():
         args.inner_rtol = 0.0
     if args.coarse_weight < 0:
         # measured on GB300 (steps 5-24 from rest / 200-219): the coarse level, applied while
-        # the outer relative residual exceeds 1e-5, takes 23.6 to 21.3 ms per step from rest and
-        # costs about 1 % in the middle of the run, where the quartic guess leaves no smooth error
-        args.coarse_weight = 1.0 if args.workload == "realistic" else 0.0
+        # the outer relative residual exceeds 1e-5, takes the realistic model from 23.6 to 21.3 ms
+        # per step from rest and the 128-candidate batch from 146 to 129 ms, and costs 1-2 % in
+        # the middle of the run, where the quartic guess leaves no smooth error
+        args.coarse_weight = 1.0 if args.workload in ("realistic", "candidates") else 0.0
     if args.coarse_relres < 0:
         args.coarse_relres = 1e-5 if args.coarse_weight > 0 else 0.0
     assert args.warmup >= 3, "at least 3 warm-up steps"
@@ -856,7 +861,8 @@ def main():
     cand = ca = None
     if not args.no_extras and args.workload == "realistic":
         cand = candidates_block(ctx, args.models, args.warmup, args.steps, args.tol, 25, args.guess_order,
-                                proj_dim=args.proj_dim)
+                                proj_dim=args.proj_dim, coarse_weight=args.coarse_weight,
+                                coarse_relres=args.coarse_relres)
         if args.precision != "fp64":
             ca = candidate_analysis_block(ctx, cfg, args.warmup + args.steps, args, prec)
     inner_pc = ("two-level (block Jacobi + %g x first-order coarse block Jacobi%s)" % (
