@@ -131,6 +131,13 @@ typedef struct {
                             it starts from exceeds this (0 = in every inner solve); the
                             coarse level removes smooth error, which a poor initial guess
                             leaves and a good one does not */
+  double proj_relres;    /* 0, or with proj_dim > 0 and guess_order > 0: the projection
+                            guess hands over, for the rest of the run, to the degree-
+                            guess_order extrapolation once a step starts from an initial
+                            relative residual below this (the projection pays while the
+                            motion is young and the extrapolation is poor); the history
+                            restarts, and the projection with it, at gsw_reset /
+                            gsw_set_state */
 } gsw_solver_opts;
 
 typedef struct {

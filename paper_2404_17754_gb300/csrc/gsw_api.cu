@@ -60,7 +60,7 @@ struct Model {
   std::vector<double> input;
   int dir = 0;
   bool input_set = false;
-  gsw_solver_opts opts = {1e-8, 10000, GSW_PREC_FP64, 20, 8, 6, -1, 0.0, 0, 0, 0, 0, 0.0, 0.0};
+  gsw_solver_opts opts = {1e-8, 10000, GSW_PREC_FP64, 20, 8, 6, -1, 0.0, 0, 0, 0, 0, 0.0, 0.0, 0.0};
   int64_t step = 0;
   bool failed = false;
   gsw_stats stats = {};
@@ -368,6 +368,12 @@ gsw_status model_state_alloc(gsw_ctx* ctx, Model* m, bool own_precond = true) {
   return GSW_OK;
 }
 
+// The projection guess hands over to the extrapolation of order guess_order
+// once a step starts from an initial relative residual below proj_relres.
+bool proj_hands_over(const Model* m) {
+  return m->opts.proj_dim > 0 && m->opts.proj_relres > 0.0 && m->opts.guess_order > 0;
+}
+
 // Buffers of the projection guess (proj_dim > 0): W, Z, the step's b, state.
 gsw_status proj_alloc(gsw_ctx* ctx, Model* m, int k) {
   if (k <= 0 || (m->proj && m->proj_k >= k)) return GSW_OK;
@@ -438,6 +444,9 @@ gsw_status step_fp64(gsw_ctx* ctx, Model* m) {
   const int k_guess = m->opts.guess_order;
   const bool proj = m->opts.proj_dim > 0;
   if (proj) {
+    // the successor guess first; the projection kernels overwrite it until they retire
+    if (proj_hands_over(m))
+      launch_guess_extrap(m->N, m->guess_ring, k_guess, m->guess_ext, m->v, m->a, m->dt, m->x, s);
     launch_proj_coef(m->N, m->proj_W, m->b, m->proj, m->proj_part, s);
     launch_proj_guess(m->N, m->proj_W, m->proj, m->x, s);
   } else if (k_guess > 0) {
@@ -495,8 +504,9 @@ gsw_status step_fp64(gsw_ctx* ctx, Model* m) {
     return fail(ctx, GSW_E_NAN, "step %lld: non-finite CG residual", (long long)m->step);
   }
   if (proj)
-    launch_proj_push(m->N, m->x, m->b, m->r, m->proj_W, m->proj_Z, m->proj, m->opts.proj_dim, m->proj_part, s);
-  else if (m->opts.guess_order > 0)
+    launch_proj_push(m->N, m->x, m->b, m->r, m->proj_W, m->proj_Z, m->proj, m->opts.proj_dim, m->proj_part, s,
+                     nullptr, m->cg, m->opts.proj_relres);
+  if ((!proj || proj_hands_over(m)) && m->opts.guess_order > 0)
     launch_guess_push(m->N, m->x, m->guess_ring, m->opts.guess_order, m->guess_ext, s);
   launch_newmark(mv, m->x, m->u, m->v, m->a, m->cg, s);
   launch_record(m->v, m->rec_node, m->rec_w, m->n_rec, m->wave, m->n_steps, (int)m->step, s);
@@ -1142,7 +1152,12 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
   else if (extrap)
     launch_guess_extrap(m->N, m->guess_ring, m->opts.guess_order, m->guess_ext, m->v, m->a, m->dt, m->x, s);
   // the projection guess: the residual pass at du0 = 0 gives b exactly, then du0 = W c and r = b - Z c
-  if (proj) CK(cudaMemsetAsync(m->x, 0, sizeof(double) * 3 * (size_t)m->N, s));
+  // (once it has handed over, the extrapolation kernel writes the extrapolated guess instead of 0)
+  if (proj && proj_hands_over(m))
+    launch_guess_extrap(m->N, m->guess_ring, m->opts.guess_order, m->guess_ext, m->v, m->a, m->dt, m->x, s, nullptr,
+                        m->proj);
+  else if (proj)
+    CK(cudaMemsetAsync(m->x, 0, sizeof(double) * 3 * (size_t)m->N, s));
   launch_cg_init_mixed(mv, m->w32, m->u, m->v, m->a, m->x, m->p, m->z, m->b, m->r, m->q, m->partials, m->cg, s,
                        nullptr, (learned || extrap || proj) ? 1 : 0, outer_dword(m) ? 1 : 0);
   // FP64 residual at the initial guess in one element-by-element pass
@@ -1152,7 +1167,7 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
     launch_proj_apply(m->N, m->proj_W, m->proj_Z, m->proj, m->x, m->r, m->proj_b, s);
   }
   launch_cg_rnorm(mv, m->r, m->partials, m->cg, s);
-  int64_t launches = proj ? 6 : 4;
+  int64_t launches = proj ? (proj_hands_over(m) ? 7 : 6) : 4;
   if ((m->timing || m->live_tune) && (int)m->ev_lo.size() < 2 * m->opts.inner_iters) {
     for (int i = (int)m->ev_lo.size(); i < 2 * m->opts.inner_iters; ++i) {
       cudaEvent_t e;
@@ -1232,8 +1247,9 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
   }
   TRY(mlp_after_step(ctx, m, s, base));
   if (proj)
-    launch_proj_push(m->N, m->x, m->proj_b, m->r, m->proj_W, m->proj_Z, m->proj, m->opts.proj_dim, m->proj_part, s);
-  else if (m->opts.guess_order > 0)
+    launch_proj_push(m->N, m->x, m->proj_b, m->r, m->proj_W, m->proj_Z, m->proj, m->opts.proj_dim, m->proj_part, s,
+                     nullptr, m->cg, m->opts.proj_relres);
+  if ((!proj || proj_hands_over(m)) && m->opts.guess_order > 0)
     launch_guess_push(m->N, m->x, m->guess_ring, m->opts.guess_order, m->guess_ext, s);
   launch_newmark(mv, m->x, m->u, m->v, m->a, m->cg, s);
   launch_record(m->v, m->rec_node, m->rec_w, m->n_rec, m->wave, m->n_steps, (int)m->step, s);
@@ -1331,6 +1347,8 @@ bool issue_device_step_fp64(Model* m, cudaStream_t s, StepState* ss, int outer, 
   const int k_guess = m->opts.guess_order;
   const bool proj = m->opts.proj_dim > 0;
   if (proj) {
+    if (proj_hands_over(m))
+      launch_guess_extrap(m->N, m->guess_ring, k_guess, m->guess_ext, m->v, m->a, m->dt, m->x, s, ss);
     launch_proj_coef(m->N, m->proj_W, m->b, m->proj, m->proj_part, s, ss);
     launch_proj_guess(m->N, m->proj_W, m->proj, m->x, s, ss);
   } else if (k_guess > 0) {
@@ -1339,7 +1357,7 @@ bool issue_device_step_fp64(Model* m, cudaStream_t s, StepState* ss, int outer, 
   launch_cg_init(mv, m->b, m->v, m->a, m->x, m->q, m->partials, m->cg, s, (k_guess > 0 || proj) ? 1 : 0, ss);
   launch_outer(m, kModeA, mv, m->x, nullptr, nullptr, m->q, 0.0, 0, nullptr, m->cg, s);
   launch_cg_residual(mv, m->b, m->q, m->r, m->z, m->p, m->dinv, m->partials, m->cg, s);
-  n->fixed += 6 + (proj ? 2 : (k_guess > 0 ? 1 : 0));
+  n->fixed += 6 + (proj ? (proj_hands_over(m) ? 3 : 2) : (k_guess > 0 ? 1 : 0));
   // the first residual may already meet the tolerance; every PCG iteration is a loop body
   if (!issue_loop(s, LoopSet{{ss, nullptr, nullptr}, {m->cg, nullptr, nullptr}, 1}, outer + 1, bs, n, 3,
                   [&](cudaStream_t st) {
@@ -1350,8 +1368,9 @@ bool issue_device_step_fp64(Model* m, cudaStream_t s, StepState* ss, int outer, 
     return false;
   launch_step_end(ss, m->cg, s);
   if (proj)
-    launch_proj_push(m->N, m->x, m->b, m->r, m->proj_W, m->proj_Z, m->proj, m->opts.proj_dim, m->proj_part, s, ss);
-  else if (k_guess > 0)
+    launch_proj_push(m->N, m->x, m->b, m->r, m->proj_W, m->proj_Z, m->proj, m->opts.proj_dim, m->proj_part, s, ss,
+                     m->cg, m->opts.proj_relres);
+  if ((!proj || proj_hands_over(m)) && k_guess > 0)
     launch_guess_push(m->N, m->x, m->guess_ring, k_guess, m->guess_ext, s, ss);
   launch_newmark(mv, m->x, m->u, m->v, m->a, m->cg, s, ss);
   launch_record(m->v, m->rec_node, m->rec_w, m->n_rec, m->wave, m->n_steps, 0, s, ss);
@@ -1367,7 +1386,9 @@ void issue_guess_and_residual(Model* m, cudaStream_t s, StepState* ss, Drive dr,
   ModelView mv = m->view();
   const int k_guess = m->opts.guess_order;
   const bool proj = m->opts.proj_dim > 0;
-  if (proj)
+  if (proj && proj_hands_over(m))
+    launch_guess_extrap(m->N, m->guess_ring, k_guess, m->guess_ext, m->v, m->a, m->dt, m->x, s, ss, m->proj);
+  else if (proj)
     cudaMemsetAsync(m->x, 0, sizeof(double) * 3 * (size_t)m->N, s);
   else if (k_guess > 0)
     launch_guess_extrap(m->N, m->guess_ring, k_guess, m->guess_ext, m->v, m->a, m->dt, m->x, s, ss);
@@ -1379,15 +1400,17 @@ void issue_guess_and_residual(Model* m, cudaStream_t s, StepState* ss, Drive dr,
     launch_proj_apply(m->N, m->proj_W, m->proj_Z, m->proj, m->x, m->r, m->proj_b, s, ss);
   }
   launch_cg_rnorm(mv, m->r, m->partials, m->cg, s);
-  n->fixed += 3 + (proj ? 3 : (k_guess > 0 ? 1 : 0));
+  n->fixed += 3 + (proj ? (proj_hands_over(m) ? 4 : 3) : (k_guess > 0 ? 1 : 0));
 }
 // On commit: the converged increment into the guess history.
 void issue_history_push(Model* m, cudaStream_t s, StepState* ss, StepLaunches* n) {
-  if (m->opts.proj_dim > 0) {
+  const bool proj = m->opts.proj_dim > 0;
+  if (proj) {
     launch_proj_push(m->N, m->x, m->proj_b, m->r, m->proj_W, m->proj_Z, m->proj, m->opts.proj_dim, m->proj_part, s,
-                     ss);
+                     ss, m->cg, m->opts.proj_relres);
     n->fixed += 1;
-  } else if (m->opts.guess_order > 0) {
+  }
+  if ((!proj || proj_hands_over(m)) && m->opts.guess_order > 0) {
     launch_guess_push(m->N, m->x, m->guess_ring, m->opts.guess_order, m->guess_ext, s, ss);
     n->fixed += 2;
   }
@@ -1819,6 +1842,11 @@ gsw_status gsw_set_solver(gsw_ctx* ctx, int32_t model_id, const gsw_solver_opts*
     return fail(ctx, GSW_E_INVALID, "coarse_relres must be in [0, 1)");
   if (opts->proj_dim != 0 && (opts->proj_dim < 2 || opts->proj_dim > kMaxProj))
     return fail(ctx, GSW_E_INVALID, "proj_dim must be 0 or 2..%d", kMaxProj);
+  if (!(opts->proj_relres >= 0.0 && opts->proj_relres < 1.0))
+    return fail(ctx, GSW_E_INVALID, "proj_relres must be in [0, 1)");
+  if (opts->proj_relres > 0.0 && (opts->proj_dim == 0 || opts->guess_order == 0))
+    return fail(ctx, GSW_E_INVALID, "proj_relres hands the projection guess over to the extrapolation: it needs "
+                                    "proj_dim > 0 and guess_order > 0");
   if (opts->proj_dim > 0 && m->learn.enable)
     return fail(ctx, GSW_E_STATE, "the projection guess and the learned guess exclude each other");
   if (opts->proj_dim > 0) {

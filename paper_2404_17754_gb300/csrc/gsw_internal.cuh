@@ -38,6 +38,7 @@ struct CgScalars {
   int pad1;
   unsigned int counter;  // arrival counter of the last-block reductions
   unsigned int pad2;
+  double relres0;  // ||r|| / ||b|| at the step's initial guess
 };
 
 // Scalars of the learned initial guess (one set per model).
@@ -188,8 +189,12 @@ void launch_ebe_dw(int mode, int dw_in, const ModelView& m, const double* x, con
 // Initial guess from the last k+1 increments (degree-k extrapolation), k <=
 // kMaxGuessOrder; ring: [k+1][3N] doubles, ext: {count, head} on the device.
 constexpr int kMaxGuessOrder = 6;
+struct ProjState;
+// ps: a projection guess that hands over to the extrapolation; while it has not
+// retired the kernel writes du0 = 0 (the residual pass then yields b for it)
 void launch_guess_extrap(int64_t N, const double* ring, int k, const int* ext, const double* v, const double* a,
-                         double dt, double* x, cudaStream_t s, const StepState* ss = nullptr);
+                         double dt, double* x, cudaStream_t s, const StepState* ss = nullptr,
+                         const ProjState* ps = nullptr);
 void launch_guess_push(int64_t N, const double* du, double* ring, int k, int* ext, cudaStream_t s,
                        const StepState* ss = nullptr);
 // Initial guess by Galerkin projection onto the last k <= kMaxProj converged
@@ -202,6 +207,8 @@ struct ProjState {
   unsigned int pad;
   double G[kMaxProj * kMaxProj];  // by slot
   double c[kMaxProj];             // coefficients of the current step
+  int retired;                    // 1: the extrapolated guess has taken over for the rest of the run
+  int pad2;
 };
 void launch_proj_coef(int64_t N, const double* W, const double* b, ProjState* ps, double* partials, cudaStream_t s,
                       const StepState* ss = nullptr);
@@ -210,9 +217,13 @@ void launch_proj_apply(int64_t N, const double* W, const double* Z, const ProjSt
                        double* bkeep, cudaStream_t s, const StepState* ss = nullptr);
 void launch_proj_guess(int64_t N, const double* W, const ProjState* ps, double* x, cudaStream_t s,
                        const StepState* ss = nullptr);
-// on commit: W[head] = du, Z[head] = b - r, G row/column of head, advance
+// on commit: W[head] = du, Z[head] = b - r, G row/column of head, advance; with
+// handover > 0 the projection retires once a step started from an initial
+// relative residual (cg->relres0) below handover.  All projection kernels
+// return at entry once it has retired.
 void launch_proj_push(int64_t N, const double* du, const double* b, const double* r, double* W, double* Z,
-                      ProjState* ps, int k, double* partials, cudaStream_t s, const StepState* ss = nullptr);
+                      ProjState* ps, int k, double* partials, cudaStream_t s, const StepState* ss = nullptr,
+                      const CgScalars* cg = nullptr, double handover = 0.0);
 void launch_cg_init(const ModelView& m, const double* b, const double* v, const double* a,
                     double* x, double* q, double* partials, CgScalars* cg, cudaStream_t s, int use_guess = 0,
                     const StepState* ss = nullptr);

@@ -821,6 +821,7 @@ __global__ void cg_rnorm_kernel(int64_t N, const double* __restrict__ r, double*
   if (last_block_reduce<1>(vals, partials, &cg->counter, out) && threadIdx.x == 0) {
     cg->rr = out[0];
     cg->relres = sqrt(out[0] / cg->bb);
+    cg->relres0 = cg->relres;
     if (!isfinite(out[0])) {
       cg->status = -5;
       cg->done = 1;
@@ -857,6 +858,7 @@ __global__ void cg_residual_kernel(int64_t N, const double* __restrict__ b, doub
     cg->rr = out[0];
     cg->rz = out[1];
     cg->relres = sqrt(out[0] / cg->bb);
+    cg->relres0 = cg->relres;
     if (!isfinite(out[0]) || !isfinite(out[1])) {
       cg->status = -5;
       cg->done = 1;
@@ -1060,8 +1062,14 @@ void launch_cg_init(const ModelView& m, const double* b, const double* v, const 
 // Until k+1 increments exist the Newmark predictor dt v + dt^2/2 a is used.
 __global__ void guess_extrap_kernel(int64_t n3, const double* __restrict__ ring, int S, const int* ext, int k,
                                     const double* __restrict__ v, const double* __restrict__ a, double dt,
-                                    double* __restrict__ x, const StepState* ss) {
+                                    double* __restrict__ x, const StepState* ss, const ProjState* ps) {
   if (ss != nullptr && !((volatile const StepState*)ss)->active) return;
+  if (ps != nullptr && !((volatile const ProjState*)ps)->retired) {
+    // the projection guess still acts: du0 = 0, so the residual pass yields b
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
+      x[i] = 0.0;
+    return;
+  }
   const int count = ((volatile const int*)ext)[0], head = ((volatile const int*)ext)[1];
   const bool ok = count >= k + 1;
   double c[kMaxGuessOrder + 1];
@@ -1143,6 +1151,7 @@ __device__ void proj_solve(const double* G, const double* g, int n, double* c) {
 __global__ void proj_coef_kernel(int64_t n3, const double* __restrict__ W, const double* __restrict__ b,
                                  ProjState* ps, double* partials, const StepState* ss) {
   if (ss != nullptr && !((volatile const StepState*)ss)->active) return;
+  if (((volatile const ProjState*)ps)->retired) return;
   const int cnt = ((volatile const ProjState*)ps)->count;
   double acc[kMaxProj];
 #pragma unroll
@@ -1165,6 +1174,7 @@ __global__ void proj_apply_kernel(int64_t n3, const double* __restrict__ W, cons
                                   const ProjState* ps, double* __restrict__ x, double* __restrict__ r,
                                   double* __restrict__ bkeep, const StepState* ss) {
   if (ss != nullptr && !((volatile const StepState*)ss)->active) return;
+  if (((volatile const ProjState*)ps)->retired) return;
   const int cnt = ((volatile const ProjState*)ps)->count;
   double c[kMaxProj];
 #pragma unroll
@@ -1188,6 +1198,7 @@ __global__ void proj_apply_kernel(int64_t n3, const double* __restrict__ W, cons
 __global__ void proj_guess_kernel(int64_t n3, const double* __restrict__ W, const ProjState* ps, double* __restrict__ x,
                                   const StepState* ss) {
   if (ss != nullptr && !((volatile const StepState*)ss)->active) return;
+  if (((volatile const ProjState*)ps)->retired) return;
   const int cnt = ((volatile const ProjState*)ps)->count;
   double c[kMaxProj];
 #pragma unroll
@@ -1206,8 +1217,10 @@ __global__ void proj_guess_kernel(int64_t n3, const double* __restrict__ W, cons
 // with every filled slot; count and head advance.
 __global__ void proj_push_kernel(int64_t n3, const double* __restrict__ du, const double* __restrict__ b,
                                  const double* __restrict__ r, double* __restrict__ W, double* __restrict__ Z,
-                                 ProjState* ps, int k, double* partials, const StepState* ss) {
+                                 ProjState* ps, int k, double* partials, const StepState* ss,
+                                 const CgScalars* cg, double handover) {
   if (ss != nullptr && !((volatile const StepState*)ss)->commit) return;
+  if (((volatile const ProjState*)ps)->retired) return;
   const int head = ((volatile const ProjState*)ps)->head;
   const int cnt0 = ((volatile const ProjState*)ps)->count;
   const int cnt = cnt0 < k ? cnt0 + 1 : k;  // slots filled after this push
@@ -1236,6 +1249,8 @@ __global__ void proj_push_kernel(int64_t n3, const double* __restrict__ du, cons
     }
     ps->count = cnt;
     ps->head = (head + 1) % k;
+    // hand over to the extrapolation once a step started close enough
+    if (handover > 0.0 && cg != nullptr && ((volatile const CgScalars*)cg)->relres0 < handover) ps->retired = 1;
   }
 }
 
@@ -1257,13 +1272,15 @@ void launch_proj_guess(int64_t N, const double* W, const ProjState* ps, double* 
   proj_guess_kernel<<<node_blocks(3 * N), kNodeThreads, 0, s>>>(3 * N, W, ps, x, ss);
 }
 void launch_proj_push(int64_t N, const double* du, const double* b, const double* r, double* W, double* Z,
-                      ProjState* ps, int k, double* partials, cudaStream_t s, const StepState* ss) {
-  proj_push_kernel<<<proj_blocks(3 * N), kNodeThreads, 0, s>>>(3 * N, du, b, r, W, Z, ps, k, partials, ss);
+                      ProjState* ps, int k, double* partials, cudaStream_t s, const StepState* ss,
+                      const CgScalars* cg, double handover) {
+  proj_push_kernel<<<proj_blocks(3 * N), kNodeThreads, 0, s>>>(3 * N, du, b, r, W, Z, ps, k, partials, ss, cg,
+                                                               handover);
 }
 
 void launch_guess_extrap(int64_t N, const double* ring, int k, const int* ext, const double* v, const double* a,
-                         double dt, double* x, cudaStream_t s, const StepState* ss) {
-  guess_extrap_kernel<<<node_blocks(3 * N), kNodeThreads, 0, s>>>(3 * N, ring, k + 1, ext, k, v, a, dt, x, ss);
+                         double dt, double* x, cudaStream_t s, const StepState* ss, const ProjState* ps) {
+  guess_extrap_kernel<<<node_blocks(3 * N), kNodeThreads, 0, s>>>(3 * N, ring, k + 1, ext, k, v, a, dt, x, ss, ps);
 }
 void launch_guess_push(int64_t N, const double* du, double* ring, int k, int* ext, cudaStream_t s,
                        const StepState* ss) {

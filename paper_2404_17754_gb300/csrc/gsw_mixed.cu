@@ -1085,6 +1085,7 @@ __global__ void fcg_residual_kernel(int64_t N, const double* __restrict__ b, dou
   if (last_block_reduce<1>(vals, partials, &cg->counter, out) && threadIdx.x == 0) {
     cg->rr = out[0];
     cg->relres = sqrt(out[0] / cg->bb);
+    cg->relres0 = cg->relres;
     if (!isfinite(out[0])) {
       cg->status = -5;
       cg->done = 1;

@@ -33,7 +33,7 @@ class SolverOpts(C.Structure):
                 ("inner_iters", C.c_int32), ("check_every", C.c_int32), ("batch_outer", C.c_int32),
                 ("inner_variant", C.c_int32), ("inner_rtol", C.c_double), ("guess_order", C.c_int32),
                 ("outer_op", C.c_int32), ("share_dirs", C.c_int32), ("proj_dim", C.c_int32),
-                ("coarse_weight", C.c_double), ("coarse_relres", C.c_double)]
+                ("coarse_weight", C.c_double), ("coarse_relres", C.c_double), ("proj_relres", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -310,10 +310,10 @@ class Model:
 
     def set_solver(self, tol=1e-8, max_iter=10000, precision=PREC_FP64, inner_iters=20, check_every=8,
                    batch_outer=6, inner_variant=-1, inner_rtol=0.0, guess_order=0, outer_op=OUTER_AUTO,
-                   share_dirs=0, proj_dim=0, coarse_weight=0.0, coarse_relres=0.0):
+                   share_dirs=0, proj_dim=0, coarse_weight=0.0, coarse_relres=0.0, proj_relres=0.0):
         o = SolverOpts(tol, max_iter, precision, inner_iters, check_every, batch_outer, inner_variant, inner_rtol,
                        guess_order, outer_op, int(share_dirs), int(proj_dim), float(coarse_weight),
-                       float(coarse_relres))
+                       float(coarse_relres), float(proj_relres))
         self._c(self.ctx.lib.gsw_set_solver(self.ctx.h, self.id, C.byref(o)))
 
     def reset(self):

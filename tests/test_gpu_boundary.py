@@ -93,8 +93,10 @@ def test_checkpoint_restore_resumes_extrapolated_guess_exactly(ctx):
     assert m.stats()["steps_done"] == 12
     m.step(10)
     s = m.stats()
-    assert s["cg_iters_total"] == s_ref["cg_iters_total"]  # the quartic guess resumed with its history
-    assert _relerr(m.waveforms(), w_ref) <= 1e-12
+    # the quartic guess resumed with its history (the FP64 scatter's atomics may move a step's
+    # count by one between otherwise equal runs; a lost history costs many more)
+    assert abs(s["cg_iters_total"] - s_ref["cg_iters_total"]) <= 2
+    assert _relerr(m.waveforms(), w_ref) <= 1e-11
     # a checkpoint of another set-up is refused and leaves the model as it was
     m2 = _upload(ctx, configs.small_box(nx=3, ny=2, n_steps=30))
     m2.set_input(0, cfg["p"])
@@ -251,6 +253,62 @@ def test_projection_guess_converges_to_the_oracle_on_every_path(ctx, prec):
     m.free()
 
 
+def test_projection_hands_over_to_the_extrapolation(ctx):
+    """proj_relres: the projection guess acts until a step starts from an initial relative
+    residual below the threshold, then the quartic extrapolation takes over for good (its ring
+    is filled all along).  A threshold that the first projected step already meets gives the
+    quartic run; the handover survives a checkpoint; host-driven and device-driven mixed steps
+    with a mid-run handover reach the oracle; inconsistent options are rejected."""
+    from paper_2404_17754_gb300 import gsw
+
+    cfg = configs.small_box(nx=4, ny=3, n_steps=40, seed=5)
+    runs = {}
+    for name, kw in (("quartic", dict(guess_order=4)),
+                     ("handover", dict(guess_order=4, proj_dim=6, proj_relres=0.999))):
+        m = _upload(ctx, cfg)
+        m.set_input(cfg["dir"], cfg["p"])
+        m.set_solver(tol=1e-12, precision=0, **kw)
+        m.step(2)  # step 1 differs: the projection onto one increment against the predictor
+        it2 = m.stats()["cg_iters_total"]
+        m.step(cfg["n_steps"] - 2)
+        runs[name] = (m.waveforms(), m.stats()["cg_iters_total"] - it2)
+        if name == "handover":
+            # checkpoint after the handover, resume after a reset: same iterations and waveforms
+            m.reset()
+            m.step(20)
+            ck = m.checkpoint()
+            m.step(10)
+            w_ref, it_ref = m.waveforms(), m.stats()["cg_iters_total"]
+            m.reset()
+            m.step(3)
+            m.restore(ck)
+            m.step(10)
+            assert abs(m.stats()["cg_iters_total"] - it_ref) <= 2
+            assert _relerr(m.waveforms(), w_ref) <= 1e-11
+        m.free()
+    assert _relerr(runs["handover"][0], runs["quartic"][0]) <= 1e-9
+    # after the handover both runs use the same guesses (solutions equal to ~1e-12, so a
+    # step's count may differ by one now and then)
+    assert abs(runs["handover"][1] - runs["quartic"][1]) <= 3
+    # a handover in the middle of the run, mixed precision, host- and device-driven
+    cfg = configs.config1(n_steps=60)
+    ref = newmark.analysis(cfg, tol=1e-8)["wave"]
+    m = _upload(ctx, cfg)
+    m.set_input(cfg["dir"], cfg["p"])
+    m.set_solver(tol=1e-8, precision=2, inner_iters=20, guess_order=4, proj_dim=8, proj_relres=1e-3)
+    m.step(60)
+    assert m.stats()["relres_last"] <= 1e-8
+    assert _relerr(m.waveforms(), ref) <= 1e-6
+    m.run()
+    assert _relerr(m.waveforms(), ref) <= 1e-6
+    for bad in (dict(proj_dim=0, guess_order=4, proj_relres=1e-3), dict(proj_dim=8, guess_order=0, proj_relres=1e-3),
+                dict(proj_dim=8, guess_order=4, proj_relres=1.0)):
+        with pytest.raises(gsw.GswError) as ei:
+            m.set_solver(tol=1e-8, precision=2, inner_iters=20, **bad)
+        assert ei.value.status == gsw.E_INVALID
+    m.free()
+
+
 def test_projection_guess_checkpoint_and_quality(ctx):
     from paper_2404_17754_gb300 import gsw
 
@@ -266,8 +324,10 @@ def test_projection_guess_checkpoint_and_quality(ctx):
     m.step(2)
     m.restore(ck)
     m.step(10)
-    assert m.stats()["cg_iters_total"] == s_ref["cg_iters_total"]  # the projection history resumed
-    assert _relerr(m.waveforms(), w_ref) <= 1e-12
+    # the projection history resumed (a lost history costs tens of iterations; the FP64
+    # scatter's atomics make a step's count vary by one between otherwise equal runs)
+    assert abs(m.stats()["cg_iters_total"] - s_ref["cg_iters_total"]) <= 2
+    assert _relerr(m.waveforms(), w_ref) <= 1e-11
     with pytest.raises(gsw.GswError) as ei:
         m.set_learning(True, train_steps=10, batch=256)
     assert ei.value.status == gsw.E_STATE
