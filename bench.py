@@ -326,7 +326,7 @@ def run_candidates(args, rank, world, dist):
         m.set_input(cfg["dir"], cfg["p"])
         m.set_solver(tol=args.tol, outer_op=OUTER_OPS[args.outer_op], precision=prec, inner_iters=args.inner, batch_outer=args.batch_outer,
                      inner_rtol=args.inner_rtol, guess_order=args.guess_order, coarse_weight=args.coarse_weight,
-                     coarse_relres=args.coarse_relres)
+                     coarse_relres=args.coarse_relres, proj_dim=args.proj_dim, proj_relres=args.proj_relres)
         models.append(m)
         dof += 3 * cfg["mesh"]["xyz"].shape[0]
     # every form advances the candidates together, one captured graph launch per step
