@@ -563,7 +563,7 @@ def run_learned(args, rank, world, dist):
                        "outer_iters_per_step": (s1["cg_iters_total"] - s0["cg_iters_total"]) / args.steps,
                        "mean_initial_relres": (s1["init_relres_sum"] - s0["init_relres_sum"]) / args.steps,
                        "relres_last": s1["relres_last"], "train_phase_s": t_train,
-                       "judge": m.mlp_state() if enable else None}
+                       "referee": m.mlp_state() if enable else None}
         m.free()
     if rank == 0:
         dof = 3 * cfg["mesh"]["xyz"].shape[0]

@@ -294,7 +294,7 @@ gsw_status gsw_set_state(gsw_ctx *ctx, int32_t model_id, const double *u, const 
  * increment history of the extrapolated or projected initial guess and,
  * with the learned guess enabled, the network's parameters, its Adam moments
  * and step count, its increment history, its training schedule and the
- * judge's state.  buf is a
+ * referee's state.  buf is a
  * host buffer of *bytes bytes; buf = NULL returns the size needed in *bytes.
  * gsw_restore needs the same model sizes, n_steps, input direction and
  * guess_order (and learning enabled when the checkpoint holds a network);
@@ -360,7 +360,7 @@ gsw_status gsw_wait_probe(gsw_ctx *ctx, int64_t limit);
  * cores (BF16 operands, FP32 accumulation), as does the inference that
  * supplies the initial guess afterwards.  The CG always iterates to the same
  * relative-residual tolerance; a non-finite guess falls back to the
- * predictor, and the plain base guess stays the judge (see gsw_mlp_state).
+ * predictor, and the plain base guess stays the referee (see gsw_mlp_state).
  * Host-driven stepping (gsw_step) only. */
 typedef struct {
   int32_t enable;          /* 0: plain predictor; 1: learned guess */
@@ -390,12 +390,12 @@ gsw_status gsw_mlp_forward(gsw_ctx *ctx, int32_t model_id, int32_t n, const floa
 gsw_status gsw_mlp_grad(gsw_ctx *ctx, int32_t model_id, int32_t n, const float *x, const float *y,
                         double *loss, double *grad);
 /* State of the learned guess, out[5]: [0] mean training loss of the last
- * training step, [1] 1 while the guess is applied (0 once the judge has
+ * training step, [1] 1 while the guess is applied (0 once the referee has
  * reverted to the predictor, or when disabled), [2] mean initial relative
  * residual of the plain predictor over its last (up to 5) steps, [3] the same
  * for the learned guess, [4] number of steps that used the learned guess.
  * After training, every 10th step is a probe with the plain predictor; the
- * judge reverts to the predictor for good when [3] (over 5 steps) exceeds [2]. */
+ * referee reverts to the predictor for good when [3] (over 5 steps) exceeds [2]. */
 gsw_status gsw_mlp_state(gsw_ctx *ctx, int32_t model_id, double *out);
 
 /* Diagnostics of the learned guess's data path (tests), between steps of a

@@ -115,7 +115,7 @@ struct Model {
   MlpScalars* ms = nullptr;
   MlpScalars ms_host = {};
   int hist_head = 3, hist_count = 0, adam_t = 0;
-  // judge of the learned guess: initial residuals of the plain predictor
+  // referee of the learned guess: initial residuals of the plain predictor
   // (training phase) and of the learned guess (application phase)
   double std_r0_recent[5] = {0, 0, 0, 0, 0}, mlp_r0_recent[5] = {0, 0, 0, 0, 0};
   int64_t std_r0_n = 0, mlp_r0_n = 0, applied = 0;
@@ -931,7 +931,7 @@ bool mlp_use_guess(gsw_ctx* ctx, Model* m, cudaStream_t s, const double* base) {
   if (!m->learn.enable || !m->mlp_ready || m->mlp_off || m->hist_count < 4 || m->step < m->learn.train_steps)
     return false;
   // every 10th step of the application phase is a probe with the plain
-  // predictor, keeping the judge's baseline current
+  // predictor, keeping the referee's baseline current
   if ((m->applied++ % 10) == 9) return false;
   launch_mlp_sigma(m->N, m->hist, m->partials, m->ms, s);
   launch_mlp_infer(m->N, m->hist, m->nodef, m->packed, m->ms, m->x, nullptr, nullptr, s, base);
@@ -1180,7 +1180,7 @@ gsw_status step_mixed(gsw_ctx* ctx, Model* m) {
   CK(cudaStreamSynchronize(s));
   m->stats.init_relres_sum += m->cg_host->relres;
   if (m->learn.enable && !m->cg_host->zero_rhs) {
-    // judge: the learned guess stays while the mean initial residual of its
+    // referee: the learned guess stays while the mean initial residual of its
     // last 5 steps beats that of the plain predictor's last 5 steps (the last
     // training steps, then the probe steps)
     double* buf = learned ? m->mlp_r0_recent : m->std_r0_recent;

@@ -110,7 +110,7 @@ def test_learned_guess_gains_over_the_predictor(ctx):
     assert np.linalg.norm(runs[1]["wave"] - runs[0]["wave"]) <= 1e-6 * np.linalg.norm(runs[0]["wave"])
     st = runs[1]["state"]
     print("steps 501-700: outer iterations plain %d, learned %d; mean initial residual plain %.3e, learned %.3e; "
-          "judge %s" % (runs[0]["iters"], runs[1]["iters"], runs[0]["r0"], runs[1]["r0"], st))
+          "referee %s" % (runs[0]["iters"], runs[1]["iters"], runs[0]["r0"], runs[1]["r0"], st))
     assert st["active"] and st["learned_steps"] >= 150
     assert st["learned_r0"] < 0.5 * st["plain_r0"]
     assert runs[1]["r0"] < 0.5 * runs[0]["r0"]
