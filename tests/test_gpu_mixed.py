@@ -80,17 +80,26 @@ def test_mixed_small_box_tight_tolerance(ctx):
     m.free()
 
 
-def test_mixed_full_size_true_residual(ctx):
-    """Realistic 9.93 M DOF model, FP16 inner solve: the FP64 Newmark residual of a step is <= 2e-8."""
+BENCH_SOLVER = dict(inner_iters=45, inner_rtol=0.0125, guess_order=4, coarse_weight=1.0, coarse_relres=1e-5,
+                    proj_dim=8, proj_relres=1e-5)
+
+
+@pytest.mark.parametrize("solver,k", [(dict(inner_iters=20), 2), (BENCH_SOLVER, 2), (BENCH_SOLVER, 260)],
+                         ids=["block_jacobi", "bench_default_from_rest", "bench_default_step_260"])
+def test_mixed_full_size_true_residual(ctx, solver, k):
+    """Realistic 9.93 M DOF model, FP16 inner solve: the FP64 Newmark residual of step k is <= 2e-8,
+    with the plain block-Jacobi inner preconditioner and with the bench's solver: at step 2 from
+    rest its coarse level and projection guess act, at step 260 it runs on the fine level from the
+    quartic guess after the handover."""
     import torch
 
-    cfg = configs.config2(n_steps=3)
+    cfg = configs.config2(n_steps=k + 1)
     mesh = cfg["mesh"]
     m = ctx.upload(mesh, cfg["mat"], cfg["rec_xy"])
-    m.set_time(cfg["dt"], 3, cfg["band"])
+    m.set_time(cfg["dt"], k + 1, cfg["band"])
     m.set_input(cfg["dir"], cfg["p"])
-    m.set_solver(tol=1e-8, precision=2, inner_iters=20)
-    m.step(2)
+    m.set_solver(tol=1e-8, precision=2, **solver)
+    m.step(k)
     u0, v0, a0, _ = m.get_state()
     m.step(1)
     u1, v1, a1, _ = m.get_state()
@@ -100,7 +109,7 @@ def test_mixed_full_size_true_residual(ctx):
                              face_elem=np.zeros(int(base_faces.sum()), dtype=np.int32),
                              face_tag=mesh["face_tag"][base_faces]),
                         np.repeat(cfg["mat"][-1:], cfg["mat"].shape[0], axis=0), cfg["band"])
-    f = 2.0 * cfg["p"][2] * base["w"][cfg["dir"]]
+    f = 2.0 * cfg["p"][k] * base["w"][cfg["dir"]]
     tt = lambda a: torch.tensor(a, device="cuda")
     lhs = (m.apply(2, tt(a1)) + m.apply(3, tt(v1)) + m.apply(1, tt(u1))).cpu().numpy().ravel()
     res = f - lhs
