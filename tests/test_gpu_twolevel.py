@@ -180,3 +180,23 @@ def test_two_level_cuts_inner_iterations_on_the_realistic_crop(ctx):
     assert out[0.7]["relres"] <= 1e-8
     assert e0 <= 1e-4 and e1 <= 1e-4 and e1 <= 1.5 * e0
     assert out[0.7]["inner"] < 0.9 * out[0.0]["inner"]
+
+
+def test_two_level_in_a_batch_of_models(ctx):
+    """Three different models advance as one batch (one captured graph per step, the coarse
+    level switched per member by its own outer residual): each matches its oracle run."""
+    cfgs = [configs.small_box(nx=4, ny=3, n_steps=30, seed=s, direction=s % 3) for s in (3, 4, 5)]
+    ms = []
+    for cfg in cfgs:
+        m = ctx.upload(cfg["mesh"], cfg["mat"], cfg["rec_xy"])
+        m.set_time(cfg["dt"], cfg["n_steps"], cfg["band"])
+        m.set_input(cfg["dir"], cfg["p"])
+        m.set_solver(tol=1e-8, precision=2, inner_iters=20, inner_rtol=1e-2, guess_order=4, coarse_weight=1.0,
+                     coarse_relres=1e-5)
+        ms.append(m)
+    ctx.run(ms)
+    for cfg, m in zip(cfgs, ms):
+        ref = newmark.analysis(cfg, tol=1e-8)["wave"]
+        assert _relerr(m.waveforms(), ref) <= 1e-6
+        assert m.stats()["relres_last"] <= 1e-8
+        m.free()
