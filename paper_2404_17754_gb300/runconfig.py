@@ -16,8 +16,9 @@ default below, and an unknown key is an error (a typo must not pass silently):
 The workload kinds are the seeded synthetic models of ``synth.configs`` (the paper's models are
 not published): a small two-layer box, the two-layer 100 x 100 x 50 m model, the three-layer
 1.2 x 1.2 x 0.3 km model (optionally its lateral crop), and a candidate of the mixed-precision
-ensemble; ``seed`` null keeps the workload's own seed.  The time step is the workload's own (its input samples are made for it); ``band``
-(the Rayleigh-fit band) defaults to the workload's.  The solver section maps one to one
+ensemble; ``seed`` null keeps the workload's own seed.  The time step is the workload's own
+(its input samples are made for it); ``band`` (the Rayleigh-fit band) defaults to the
+workload's.  The solver section maps one to one
 onto ``gsw_solver_opts`` (``solver_kwargs``).  ``run`` uploads the model, runs the analyses of
 the listed input directions (one batch), and returns the receiver histories and a summary that
 repeats the resolved configuration, so every output carries the configuration that made it.
